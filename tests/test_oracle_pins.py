@@ -1,0 +1,449 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test fixes one function of the oracle with a closed form, an invariant,
+an independent library routine (scipy / numpy) or brute force, so that a
+plausible slip in the oracle (dropped term, wrong sign or index, transposed
+operand) fails at least one of them.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy import ndimage, stats
+from scipy.sparse.csgraph import maximum_flow
+
+import oracle as O
+from paper_1008_0502_b300 import synth
+
+BINOM = np.array([1, 4, 6, 4, 1], float) / 16.0
+
+
+# ---------------------------------------------------------------- features
+def test_features_closed_forms():
+    px = np.array([[[255, 0, 0], [255, 255, 0], [0, 0, 255], [0, 255, 0], [90, 90, 90],
+                    [5, 5, 5]]], np.uint8)
+    I, RG, BY = O.features(px)
+    assert np.allclose(I[0], px[0].sum(1) / 765.0, rtol=0, atol=1e-15)
+    # pure red: rn=3 -> R=3, G=0, B=0, Y=0
+    assert RG[0, 0] == 3.0 and BY[0, 0] == 0.0
+    # pure yellow: rn=gn=1.5 -> R=G=0.75, Y=1.5, B=0
+    assert RG[0, 1] == 0.0 and BY[0, 1] == -1.5
+    # pure blue: B=3, Y=0
+    assert RG[0, 2] == 0.0 and BY[0, 2] == 3.0
+    # pure green: G=3 -> RG=-3; Y = (0+3)/2 - 3/2 - 0 = 0
+    assert RG[0, 3] == -3.0 and BY[0, 3] == 0.0
+    # grey gives exactly zero opponents; a pixel at or below a tenth of the
+    # maximum intensity (15 <= 76.5) gets no hue at all
+    assert RG[0, 4] == 0.0 and BY[0, 4] == 0.0
+    assert RG[0, 5] == 0.0 and BY[0, 5] == 0.0
+
+
+def test_features_hue_threshold_is_integer_exact():
+    # max sum = 765; a pixel with sum 76 is below a tenth, 77 is above
+    px = np.array([[[255, 255, 255], [76, 0, 0], [77, 0, 0]]], np.uint8)
+    _, RG, _ = O.features(px)
+    assert RG[0, 1] == 0.0 and RG[0, 2] == 3.0
+
+
+def test_grey_image_has_no_colour_opponents():
+    g = synth.noise_background(np.random.default_rng(3), 40, 50)
+    rgb = np.repeat(g[:, :, None], 3, 2)
+    _, RG, BY = O.features(rgb)
+    assert not RG.any() and not BY.any()
+
+
+# ---------------------------------------------------------------- pyramid
+def test_reduce_matches_scipy_correlate():
+    rng = np.random.default_rng(0)
+    for h, w in [(17, 23), (8, 8), (5, 3), (1, 7), (2, 2)]:
+        img = rng.random((h, w))
+        ref = ndimage.correlate(img, np.outer(BINOM, BINOM), mode="nearest")[::2, ::2]
+        assert O.reduce(img).shape == ((h + 1) // 2, (w + 1) // 2)
+        np.testing.assert_allclose(O.reduce(img), ref, rtol=0, atol=1e-14)
+
+
+def test_reduce_impulse_closed_form():
+    img = np.zeros((20, 20))
+    img[8, 10] = 1.0  # even position -> taps 1,6,1 per axis
+    out = O.reduce(img)
+    exp = np.zeros((10, 10))
+    exp[3:6, 4:7] = np.outer([1, 6, 1], [1, 6, 1]) / 256.0
+    np.testing.assert_allclose(out, exp, atol=1e-16)
+    img = np.zeros((20, 20))
+    img[9, 11] = 1.0  # odd position -> taps 4,4 per axis
+    out = O.reduce(img)
+    exp = np.zeros((10, 10))
+    exp[4:6, 5:7] = 16 / 256.0
+    np.testing.assert_allclose(out, exp, atol=1e-16)
+
+
+def test_reduce_constant_and_linear():
+    c = np.full((13, 9), 0.37)
+    np.testing.assert_allclose(O.reduce(c), 0.37, rtol=0, atol=1e-15)
+    a, b = np.random.default_rng(1).random((2, 11, 14))
+    np.testing.assert_allclose(O.reduce(2 * a - 3 * b), 2 * O.reduce(a) - 3 * O.reduce(b), atol=1e-14)
+
+
+def test_level_dims_ceil_halving():
+    assert [O.level_dim(640, l) for l in range(9)] == [640, 320, 160, 80, 40, 20, 10, 5, 3]
+    assert [O.level_dim(480, l) for l in range(9)] == [480, 240, 120, 60, 30, 15, 8, 4, 2]
+
+
+# ---------------------------------------------------------------- Gabor
+@pytest.mark.parametrize("k", range(4))
+def test_gabor_kernel_zero_mean_rank2_normalised(k):
+    th = k * np.pi / 4
+    g = O.gabor_kernel(th)
+    assert abs(g.sum()) < 1e-15
+    sv = np.linalg.svd(g, compute_uv=False)
+    assert sv[2] < 1e-12 * sv[0]              # rank 2: modulated Gaussian minus DC Gaussian
+    # envelope: |k| + DC part equals the normalised Gaussian times |carrier| = 1
+    u = np.arange(-6, 7)
+    G = np.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / 8.0)
+    kappa = (G * np.exp(1j * np.pi / 2 * (u[None, :] * np.cos(th) + u[:, None] * np.sin(th)))).sum() / G.sum()
+    np.testing.assert_allclose(np.abs(g + kappa * G / G.sum()), G / G.sum(), atol=1e-15)
+
+
+def test_gabor_matches_scipy_correlate_and_constant_is_zero():
+    rng = np.random.default_rng(2)
+    img = rng.random((31, 27))
+    for k in range(4):
+        th = k * np.pi / 4
+        g = O.gabor_kernel(th)
+        re = ndimage.correlate(img, g.real, mode="nearest")
+        im = ndimage.correlate(img, g.imag, mode="nearest")
+        np.testing.assert_allclose(O.gabor(img, th), np.hypot(re, im), atol=1e-13)
+        assert np.abs(O.gabor(np.full((20, 20), 0.8), th)).max() < 1e-14
+
+
+def test_gabor_orientation_selectivity_and_transpose():
+    y, x = np.mgrid[0:48, 0:48]
+    grating = 0.5 + 0.5 * np.cos(2 * np.pi * x / 4.0)  # varies along x: theta = 0
+    r0 = O.gabor(grating, 0.0)[16:32, 16:32].mean()
+    r90 = O.gabor(grating, np.pi / 2)[16:32, 16:32].mean()
+    assert r0 > 50 * r90
+    img = np.random.default_rng(5).random((24, 24))
+    np.testing.assert_allclose(O.gabor(img.T, np.pi / 2), O.gabor(img, 0.0).T, atol=1e-13)
+    np.testing.assert_allclose(O.gabor(img.T, np.pi / 4), O.gabor(img, np.pi / 4).T, atol=1e-13)
+    np.testing.assert_allclose(O.gabor(img.T, 3 * np.pi / 4), O.gabor(img, 3 * np.pi / 4).T, atol=1e-13)
+
+
+# ---------------------------------------------------------------- upsample
+def test_upsample_matches_map_coordinates():
+    rng = np.random.default_rng(4)
+    src = rng.random((5, 7))
+    for hd, wd in [(9, 13), (20, 28), (5, 7), (3, 4)]:
+        sy = np.clip((np.arange(hd) + 0.5) * 5 / hd - 0.5, 0, 4)
+        sx = np.clip((np.arange(wd) + 0.5) * 7 / wd - 0.5, 0, 6)
+        yy, xx = np.meshgrid(sy, sx, indexing="ij")
+        ref = ndimage.map_coordinates(src, [yy, xx], order=1, mode="nearest")
+        np.testing.assert_allclose(O.upsample(src, hd, wd), ref, atol=1e-14)
+    np.testing.assert_allclose(O.upsample(src, 5, 7), src, atol=1e-15)
+
+
+# ---------------------------------------------------------------- N(.)
+def test_normalize_single_peak_and_two_peaks():
+    v = np.zeros((16, 24))  # 2 x 3 tiles of 8
+    v[3, 3] = 5.0
+    np.testing.assert_allclose(O.normalize(v), v / 5.0)  # mbar = 0
+    v[12, 20] = 5.0  # second equal peak in another tile: mbar = 1/5
+    np.testing.assert_allclose(O.normalize(v), v / 5.0 * (1 - 1 / 5) ** 2)
+
+
+def test_normalize_matches_numpy_tiles_and_is_affine_invariant():
+    rng = np.random.default_rng(6)
+    for h, w in [(30, 40), (15, 20), (8, 8), (3, 2), (1, 1)]:
+        v = rng.random((h, w))
+        mn, mx = v.min(), v.max()
+        ref = np.zeros_like(v)
+        if mx > mn:
+            vp = (v - mn) / (mx - mn)
+            pad = np.zeros((-(-h // 8) * 8, -(-w // 8) * 8))
+            pad[:h, :w] = vp
+            tm = pad.reshape(pad.shape[0] // 8, 8, pad.shape[1] // 8, 8).max(axis=(1, 3))
+            nt = tm.size
+            mbar = (tm.sum() - 1) / (nt - 1) if nt > 1 else 0.0
+            ref = vp * (1 - mbar) ** 2
+        np.testing.assert_allclose(O.normalize(v), ref, atol=1e-14)
+        np.testing.assert_allclose(O.normalize(3.5 * v + 1.25), O.normalize(v), atol=1e-12)
+
+
+def test_normalize_flat_map_is_zero():
+    assert not O.normalize(np.full((9, 9), 2.0)).any()
+    v = np.full((9, 9), 2.0)
+    v[0, 0] += 1e-7  # range below the flat threshold
+    assert not O.normalize(v, flat=1e-5).any()
+
+
+# ---------------------------------------------------------------- saliency map
+def test_saliency_constant_frame_is_zero():
+    for rgb in [(97, 97, 97), (200, 30, 60)]:
+        f = synth.constant_frame(48, 64, rgb)
+        s = O.saliency(f, O.CONFIG_SMALL)
+        assert np.abs(s).max() == 0.0
+
+
+def test_saliency_grey_frame_has_no_colour_conspicuity():
+    g = synth.noise_background(np.random.default_rng(8), 120, 160)
+    rgb = np.repeat(g[:, :, None], 3, 2)
+    _, dbg = O.saliency(rgb, O.CONFIG_SMALL, debug=True)
+    assert not dbg["consp"][1].any() and not dbg["consp"][2].any()
+    assert dbg["consp"][0].max() > 0 and dbg["consp"][3].max() > 0
+
+
+def test_saliency_transpose_equivariance():
+    rgb = synth.random_frame(64, 64, 11)
+    a = O.saliency(rgb, O.CONFIG_SMALL)
+    b = O.saliency(np.ascontiguousarray(rgb.transpose(1, 0, 2)), O.CONFIG_SMALL)
+    np.testing.assert_allclose(b, a.T, atol=1e-12)
+
+
+def test_saliency_debug_pyramid_consistent():
+    frames, _ = synth.clip_small(2)
+    sal, dbg = O.saliency(frames[1], O.CONFIG_SMALL, debug=True)
+    I, RG, BY = O.features(frames[1])
+    np.testing.assert_array_equal(dbg["pyr"][0][0], I)
+    np.testing.assert_allclose(dbg["pyr"][1][2], O.reduce(O.reduce(RG)), atol=1e-15)
+    np.testing.assert_allclose(dbg["ori"][1][3], O.gabor(dbg["pyr"][0][3], np.pi / 4), atol=1e-15)
+    np.testing.assert_allclose(O.upsample(dbg["S"], 120, 160), sal, atol=1e-15)
+    w = O.CONFIG_SMALL["w"]
+    np.testing.assert_allclose(sum(w[k] * dbg["consp"][k] for k in range(4)), dbg["S"], atol=1e-14)
+
+
+def test_saliency_finds_the_red_disk():
+    frames, gt = synth.clip_small(3)
+    for t in range(3):
+        s = O.saliency(frames[t], O.CONFIG_SMALL)
+        assert gt[t][np.unravel_index(np.argmax(s), s.shape)] == 1
+
+
+# ---------------------------------------------------------------- Kalman prior
+def test_paper_parameters_golden():
+    txt = open(__file__.replace("test_oracle_pins.py", "golden/paper_parameters.txt")).read()
+    vals = dict(l.split("=") for l in txt.splitlines() if "=" in l and not l.startswith("#"))
+    assert float(vals["sigma1"]) == O.CONFIG_VGA["sigma1"] == 0.03
+    assert float(vals["sigma2"]) == O.CONFIG_VGA["sigma2"] == 0.035
+
+
+def test_kalman_is_the_product_of_two_gaussians():
+    # the update combines f (variance sigma2^2 + P) and q (variance sigma1^2) by
+    # precision weighting: 1/P_t = 1/V_f + 1/V_q, weight on f = (1/V_f) P_t
+    s1, s2 = 0.03, 0.035
+    P = float("inf")
+    for t in range(30):
+        Pt, wf = O.kalman_step(t, P, s1, s2)
+        if t == 0:
+            assert wf == 0.0 and Pt == pytest.approx(s1 * s1, rel=1e-15)
+        else:
+            Vf, Vq = s2 * s2 + P, s1 * s1
+            Pp = 1.0 / (1.0 / Vf + 1.0 / Vq)
+            assert Pt == pytest.approx(Pp, rel=1e-13)
+            assert wf == pytest.approx(Pp / Vf, rel=1e-13)
+        P = Pt
+
+
+def test_kalman_steady_state_closed_form():
+    a, b = 0.03 ** 2, 0.035 ** 2
+    Pstar = (-b + math.sqrt(b * b + 4 * a * b)) / 2
+    P = float("inf")
+    seq = []
+    for t in range(200):
+        P, wf = O.kalman_step(t, P, 0.03, 0.035)
+        seq.append(P)
+    assert P == pytest.approx(Pstar, rel=1e-12)
+    assert wf == pytest.approx(a / (a + b + Pstar), rel=1e-12)
+    assert Pstar == pytest.approx(6.030888e-4, rel=1e-6) and wf == pytest.approx(0.329901, rel=1e-5)
+    assert all(x > y for x, y in zip(seq[:5], seq[1:6]))  # monotone decrease from sigma1^2
+
+
+def test_kalman_limits():
+    # sigma1 -> 0: the prior is the saliency prior q; sigma2 -> 0 with P = 0: it is f
+    _, wf = O.kalman_step(3, 1e-4, 1e-9, 0.035)
+    assert wf < 1e-12
+    _, wf = O.kalman_step(3, 0.0, 0.03, 0.0)
+    assert wf == 1.0
+
+
+def test_smooth_mask_matches_scipy():
+    m = (np.random.default_rng(9).random((30, 41)) > 0.7).astype(np.uint8)
+    u = np.arange(-6, 7)
+    g = np.exp(-u ** 2 / 8.0)
+    g2 = np.outer(g, g) / np.outer(g, g).sum()
+    ref = ndimage.correlate(m.astype(float), g2, mode="nearest")
+    np.testing.assert_allclose(O.smooth_mask(m), ref, atol=1e-14)
+
+
+def test_prior_convex_and_border():
+    rng = np.random.default_rng(10)
+    sal = rng.random((20, 30)) * 3
+    prev = (rng.random((20, 30)) > 0.5).astype(np.uint8)
+    q, pr = O.prior(sal, prev, 0.3)
+    assert (q[0] == 1e-4).all() and (q[:, -1] == 1e-4).all()
+    np.testing.assert_allclose(q[1:-1, 1:-1], sal[1:-1, 1:-1] / sal.max(), atol=1e-15)
+    np.testing.assert_allclose(pr, 0.3 * O.smooth_mask(prev) + 0.7 * q, atol=1e-15)
+    assert pr.min() >= 0 and pr.max() <= 1
+    q0, pr0 = O.prior(sal, None, 0.0)
+    np.testing.assert_array_equal(pr0, q0)
+
+
+# ---------------------------------------------------------------- MRF terms
+def test_colour_models_match_numpy_weighted_cov():
+    rng = np.random.default_rng(12)
+    rgb = rng.integers(0, 256, (25, 31, 3)).astype(np.uint8)
+    pr = rng.random((25, 31))
+    mu, cov, deg = O.colour_models(pr, rgb)
+    assert deg == 0
+    C = rgb.reshape(-1, 3) / 255.0
+    for a, w in [(1, pr.ravel()), (0, 1 - pr.ravel())]:
+        np.testing.assert_allclose(mu[a], np.average(C, axis=0, weights=w), atol=1e-14)
+        ref = np.cov(C.T, aweights=w, bias=True) + 1e-4 * np.eye(3)
+        np.testing.assert_allclose(cov[a], ref, atol=1e-14)
+
+
+def test_terms_match_scipy_logpdf():
+    rng = np.random.default_rng(13)
+    rgb = rng.integers(0, 256, (12, 17, 3)).astype(np.uint8)
+    pr = rng.random((12, 17))
+    cs, ct, nc, D0, D1 = O.terms(rgb, pr, O.CONFIG_SMALL)
+    mu, cov, _ = O.colour_models(pr, rgb)
+    C = rgb.reshape(-1, 3) / 255.0
+    eps = 1e-4
+    for a, D in [(0, D0), (1, D1)]:
+        p = pr.ravel() if a else 1 - pr.ravel()
+        ref = -stats.multivariate_normal(mu[a], cov[a]).logpdf(C) - np.log(np.clip(p, eps, 1 - eps))
+        np.testing.assert_allclose(D.ravel(), ref, rtol=1e-12, atol=1e-12)
+    m = np.minimum(D0, D1)
+    np.testing.assert_array_equal(cs, np.floor(1000 * (D0 - m) + 0.5).astype(np.int32))
+    np.testing.assert_array_equal(ct, np.floor(1000 * (D1 - m) + 0.5).astype(np.int32))
+    assert (np.minimum(cs, ct) == 0).all()
+
+
+def test_ncap_closed_form():
+    assert O.ncap_value(0, 0) == 1500
+    assert O.ncap_value(0, 1) == round(1500 / math.sqrt(2))
+    assert O.ncap_value(765, 0) == 0
+    d = 20
+    assert O.ncap_value(d, 0) == O.ncap_value(-d, 0) == math.floor(
+        1500 * math.exp(-(d / 765) ** 2 / (2 * 0.05 ** 2)) + 0.5)
+    assert O.ncap_value(0, 0, lambda_p=0.25) == 1750
+
+
+def test_terms_ncap_layout():
+    rng = np.random.default_rng(14)
+    rgb = rng.integers(0, 256, (6, 7, 3)).astype(np.uint8)
+    _, _, nc, _, _ = O.terms(rgb, np.full((6, 7), 0.5), O.CONFIG_VGA)
+    s = rgb.astype(int).sum(2)
+    assert nc.shape == (4, 6, 7)
+    assert nc[0, 2, 3] == O.ncap_value(s[2, 3] - s[2, 4], 0)
+    assert nc[1, 2, 3] == O.ncap_value(s[2, 3] - s[3, 3], 0)
+    assert nc[2, 2, 3] == O.ncap_value(s[2, 3] - s[3, 4], 1)
+    assert nc[3, 2, 3] == O.ncap_value(s[2, 3] - s[3, 2], 1)
+    assert not nc[0, :, 6].any() and not nc[1, 5].any() and not nc[3, :, 0].any()
+
+
+# ---------------------------------------------------------------- min cut
+def _scipy_flow(cs, ct, nc):
+    H, W = cs.shape
+    n = H * W
+    s, t = n, n + 1
+    rows, cols, vals = [], [], []
+    for v in range(n):
+        rows += [s, v]
+        cols += [v, t]
+        vals += [int(cs.flat[v]), int(ct.flat[v])]
+    dx, dy = [1, 0, 1, -1], [0, 1, 1, 1]
+    for k in range(nc.shape[0]):
+        for y in range(H):
+            for x in range(W):
+                xx, yy = x + dx[k], y + dy[k]
+                if 0 <= xx < W and yy < H:
+                    c = int(nc[k, y, x])
+                    rows += [y * W + x, yy * W + xx]
+                    cols += [yy * W + xx, y * W + x]
+                    vals += [c, c]
+    A = sp.coo_array((np.array(vals, np.int32), (rows, cols)), shape=(n + 2, n + 2)).tocsr()
+    A.sum_duplicates()
+    return maximum_flow(A, s, t).flow_value
+
+
+@pytest.mark.parametrize("nbr", [4, 8])
+def test_bruteforce_equals_bk_and_ek(nbr):
+    for seed in range(40):
+        h, w = [(4, 4), (3, 5), (2, 2), (1, 6), (4, 3)][seed % 5]
+        cs, ct, nc = synth.random_grid_caps(h, w, nbr, seed, tmax=60, nmax=40, p_zero=0.2)
+        e, m, cnt = O.bruteforce(cs, ct, nc)
+        assert O.cut_energy(cs, ct, nc, m) == e  # the intersection of minimisers is a minimiser
+        for method in ("bk", "ek"):
+            v, mm = O.maxflow(cs, ct, nc, method)
+            assert v == e
+            np.testing.assert_array_equal(mm, m)
+
+
+@pytest.mark.parametrize("nbr", [4, 8])
+def test_maxflow_value_matches_scipy_and_duality(nbr):
+    for seed in range(6):
+        cs, ct, nc = synth.random_grid_caps(13, 19, nbr, 100 + seed, tmax=500, nmax=200)
+        vb, mb = O.maxflow(cs, ct, nc, "bk")
+        ve, me = O.maxflow(cs, ct, nc, "ek")
+        assert vb == ve == _scipy_flow(cs, ct, nc)
+        assert O.cut_energy(cs, ct, nc, mb) == vb
+        np.testing.assert_array_equal(mb, me)
+
+
+def test_maxflow_blob_grids_bk_equals_ek():
+    for nbr in (4, 8):
+        cs, ct, nc = synth.blob_grid_caps(40, 50, nbr, 7)
+        vb, mb = O.maxflow(cs, ct, nc, "bk")
+        ve, me = O.maxflow(cs, ct, nc, "ek")
+        assert vb == ve == O.cut_energy(cs, ct, nc, mb)
+        np.testing.assert_array_equal(mb, me)
+
+
+def test_maxflow_no_nlinks_closed_form():
+    cs, ct, nc = synth.random_grid_caps(9, 11, 8, 21, tmax=9)
+    nc[:] = 0
+    v, m = O.maxflow(cs, ct, nc)
+    assert v == int(np.minimum(cs, ct).sum())
+    np.testing.assert_array_equal(m, (cs > ct).astype(np.uint8))  # ties go to background
+
+
+def test_maxflow_chain_matches_dynamic_programming():
+    # a 1 x N 4-neighbour chain is solvable exactly by a two-state Viterbi pass
+    rng = np.random.default_rng(22)
+    for _ in range(5):
+        N = 200
+        cs = rng.integers(0, 100, (1, N)).astype(np.int32)
+        ct = rng.integers(0, 100, (1, N)).astype(np.int32)
+        nc = np.zeros((2, 1, N), np.int32)
+        nc[0, 0, :-1] = rng.integers(0, 60, N - 1)
+        cost = [int(cs[0, 0]), int(ct[0, 0])]  # label 0 pays cs, label 1 pays ct
+        for i in range(1, N):
+            w = int(nc[0, 0, i - 1])
+            cost = [min(cost[0], cost[1] + w) + int(cs[0, i]), min(cost[1], cost[0] + w) + int(ct[0, i])]
+        v, _ = O.maxflow(cs, ct, nc)
+        assert v == min(cost)
+
+
+def test_maxflow_edge_cases():
+    z = np.zeros((1, 1), np.int32)
+    assert O.maxflow(z, z, np.zeros((2, 1, 1), np.int32))[0] == 0
+    big = np.full((3, 3), 1 << 24, np.int32)
+    nc = np.full((4, 3, 3), 1 << 24, np.int32)
+    nc[0, :, 2] = nc[1, 2] = nc[2, 2] = nc[2, :, 2] = nc[3, 2] = nc[3, :, 0] = 0
+    v, m = O.maxflow(big, big, nc)
+    assert v == 9 * (1 << 24) and not m.any()
+
+
+# ---------------------------------------------------------------- regression guard
+def test_small_clip_regression_golden():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_small_clip.json")))
+    frames, gt = synth.clip_small()
+    sg = O.Segmenter(120, 160, O.CONFIG_SMALL)
+    for row in g["frames"]:
+        sal, pr, mask, cut = sg.push(frames[row["t"]])
+        assert cut == row["cut"] and int(mask.sum()) == row["mask_area"]
+        assert float(sal.sum()) == pytest.approx(row["saliency_sum"], rel=1e-12)
+        assert float(pr.sum()) == pytest.approx(row["prior_sum"], rel=1e-12)
