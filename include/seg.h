@@ -1,0 +1,179 @@
+/*
+ * seg.h -- C ABI of the B300 (sm_103a) per-frame path of Akamine, Fukuchi,
+ * Kimura and Takagi, "Fully automatic extraction of salient objects from
+ * videos in near real-time" (arXiv:1008.0502):
+ *
+ *   RGB8 frame --(Sec. 3, Sec. 7.2: Itti-style saliency map)--> saliency
+ *     --(Sec. 5: saliency prior q; Sec. 6: sequential Kalman update with the
+ *        previous segmentation)--> prior p-hat
+ *     --(Sec. 4, Eqs. 1-4; Sec. 5: MRF data and smoothness terms)--> int32 graph
+ *     --(Sec. 4: exact s-t minimum cut)--> mask, cut value.
+ *
+ * Conventions (all entry points):
+ *  - Return SEG_OK (0) or a negative SEG_E* code; seg_strerror() names it.
+ *  - "dev" pointers are CUDA device pointers on the context's device; "host"
+ *    pointers are host memory (pinned memory gives asynchronous copies).
+ *  - Images are row-major, pixel (y, x) at y*W + x.  RGB8 frames are
+ *    interleaved H x W x 3 bytes.  Masks are H x W bytes, 1 = object (the
+ *    source side of the cut), 0 = background.
+ *  - Grid n-link capacities (ncap) are nbr/2 planes of H x W int32, ordered
+ *    E (x+1, y), S (x, y+1), SE (x+1, y+1), SW (x-1, y+1); an entry whose
+ *    neighbour lies outside the grid is ignored.  Each undirected n-link has
+ *    the same capacity in both directions (Sec. 4 footnote: a pair of directed
+ *    edges).  Every capacity must lie in [0, 2^24].
+ *  - The caller owns every input/output buffer.  A context owns its workspace,
+ *    allocated once in seg_create; per-frame calls allocate nothing.
+ *  - Work is enqueued asynchronously on the context's stream; outputs are
+ *    valid once that stream has been synchronised (seg_sync does it and also
+ *    reports device-side failures).  A context is not thread-safe.
+ *  - Cuts are exact: the returned mask is the unique minimal source set (the
+ *    intersection of all minimum cuts), so equal-energy ties go to background.
+ */
+#ifndef SEG_H
+#define SEG_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEG_OK 0
+#define SEG_EINVAL (-1)        /* bad argument, size or parameter */
+#define SEG_ENOMEM (-2)        /* device memory allocation failed */
+#define SEG_ENOTCONVERGED (-3) /* the min-cut hit its cycle cap (max_cycles) */
+#define SEG_ECUDA (-4)         /* a CUDA runtime call failed */
+#define SEG_ETIMEOUT (-5)      /* a bounded device-side wait ran out (kernel returned early) */
+#define SEG_ECAPACITY (-6)     /* an input capacity lies outside [0, 2^24] */
+
+typedef struct seg_ctx seg_ctx;
+
+/* Parameters of the method.  Defaults (seg_default_params) are the 640x480
+ * reading: 9 pyramid images, centers c in 2..4, surrounds s = c + 3..4, an
+ * 8-neighbour grid. */
+typedef struct seg_params {
+  int32_t levels;          /* pyramid images incl. base: sigma = 0 .. levels-1 (<= 16) */
+  int32_t c_min, c_max;    /* center scales (1 <= c_min <= c_max) */
+  int32_t d_min, d_max;    /* surround s = c + d, c_max + d_max <= levels-1 */
+  int32_t n_orient;        /* Gabor orientations theta_k = k*pi/n_orient (1..8) */
+  float gabor_lambda;      /* carrier wavelength in pixels of each level (4) */
+  float gabor_sigma;       /* isotropic envelope sigma (2) */
+  int32_t gabor_radius;    /* taps per axis = 2r+1 (6; <= 8) */
+  int32_t norm_tile;       /* N(.) local-maximum tile side (8) */
+  float norm_flat;         /* maps with range <= norm_flat normalise to 0 (1e-5) */
+  float w[4];              /* channel weights I, RG, BY, O (1/3, 1/6, 1/6, 1/3) */
+  int32_t cs_opponent_sum; /* 1: RG/BY center-surround |X(c) + up X(s)| (literal Itti), 0: |X(c) - up X(s)| */
+  int32_t border_px;       /* frame-edge band with saliency prior eps (1) */
+  double sigma1, sigma2;   /* Kalman noise std-devs (0.03, 0.035: Sec. 8.1) */
+  float f_sigma;           /* Gaussian smoothing of the previous mask (2) */
+  int32_t f_radius;        /* its radius (6; <= 8) */
+  float eps;               /* clamp for logs and the border prior (1e-4) */
+  float lambda_u;          /* colour-likelihood weight (1) */
+  float lambda_p;          /* Potts constant xi_2 (0) */
+  float lambda_s;          /* contrast weight of psi_2 (1.5) */
+  float sigma_I;           /* contrast intensity scale (0.05) */
+  float cap_scale;         /* K: capacity = min(2^24, floor(K*cost + 1/2)) (1000) */
+  int32_t neighbourhood;   /* 4 or 8 */
+  int32_t max_cycles;      /* min-cut cycle cap -> SEG_ENOTCONVERGED (20000) */
+  int32_t global_relabel_every; /* min-cut cycles between global relabels (4) */
+  int32_t local_iters;     /* push/relabel iterations per tile visit (16) */
+} seg_params;
+
+/* Fills *p with the defaults above.  Returns SEG_EINVAL if p is NULL. */
+int seg_default_params(seg_params* p);
+
+/* Creates a context for H x W frames on the current CUDA device, enqueuing on
+ * `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates the whole
+ * workspace (about 120 bytes per pixel).  Errors: SEG_EINVAL (H or W < 1,
+ * H*W > 2^26, invalid params), SEG_ENOMEM, SEG_ECUDA.  *out is NULL on error. */
+int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out);
+
+/* Frees the context and its workspace (synchronises its stream first). */
+int seg_destroy(seg_ctx* ctx);
+
+/* Starts a new video: forgets the previous mask and the prior variance, so the
+ * next frame is t = 0 (Sec. 6 with P_{-1} = +inf: p-hat = q). */
+int seg_reset(seg_ctx* ctx);
+
+/* One frame of the whole method (Fig. 3; Secs. 3-6).
+ *   rgb_dev      H*W*3 uint8 input frame (device).
+ *   saliency_dev H*W float: the saliency map upsampled to frame size (device).
+ *   prior_dev    H*W float: p-hat(A_x,t = 1) of Sec. 6 (device).
+ *   mask_dev     H*W uint8: the minimum-cut segmentation (device).
+ *   cut_dev      one int64: the minimum cut value of the integer graph (device).
+ * Any output pointer except mask_dev may be NULL.  The mask is kept inside the
+ * context as A_{t-1} of the next frame and the Kalman variance advances.
+ * Errors found on the host return immediately; device-side failures (cycle
+ * cap, wait timeout, capacity range) are reported by the next seg_sync. */
+int seg_push_frame(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev, float* prior_dev,
+                   uint8_t* mask_dev, int64_t* cut_dev);
+
+/* seg_push_frame with HOST buffers: copies the frame to the device, runs the
+ * frame, copies mask and cut value (and saliency/prior when non-NULL) back,
+ * then synchronises the stream.  Returns the frame's device status. */
+int seg_push_frame_host(seg_ctx* ctx, const uint8_t* rgb_host, float* saliency_host,
+                        float* prior_host, uint8_t* mask_host, int64_t* cut_host);
+
+/* Synchronises the context's stream and returns the first device-side status
+ * recorded since the last seg_sync (SEG_OK, SEG_ENOTCONVERGED, SEG_ETIMEOUT,
+ * SEG_ECAPACITY), or SEG_ECUDA.  *cycles (nullable) receives the last min-cut's
+ * cycle count. */
+int seg_sync(seg_ctx* ctx, int* cycles);
+
+/* Temporal state (Sec. 6: A_{t-1} and sigma^2_xi1(t-1), plus the frame index)
+ * as an opaque byte string.  seg_get_state with buf == NULL stores the needed
+ * size in *n.  Both synchronise the stream.  Errors: SEG_EINVAL (size). */
+int seg_get_state(seg_ctx* ctx, void* buf, size_t* n);
+int seg_set_state(seg_ctx* ctx, const void* buf, size_t n);
+
+const char* seg_strerror(int code);
+
+/* ---- stage entry points: the same kernels as seg_push_frame, one stage at a
+ * time, with every input explicit.  They use the context's workspace and do
+ * not touch its temporal state. ---- */
+
+/* Sec. 3 / Sec. 7.2: saliency map of one frame into saliency_dev (H*W float). */
+int seg_saliency(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev);
+
+/* Sec. 5 + Sec. 6: p-hat = w_f * f(prev_mask) + (1 - w_f) * q(saliency), with
+ * q = saliency / max(saliency) and eps on the border band.  prev_mask_dev may be
+ * NULL when w_f == 0. */
+int seg_prior(seg_ctx* ctx, const float* saliency_dev, const uint8_t* prev_mask_dev, double w_f,
+              float* prior_dev);
+
+/* Sec. 4 Eqs. 1-4 + Sec. 5: int32 t-links cs = c(s,v), ct = c(v,t) (H*W each)
+ * and n-links ncap (nbr/2 planes) from the frame and the prior. */
+int seg_terms(seg_ctx* ctx, const uint8_t* rgb_dev, const float* prior_dev, int32_t* cs_dev,
+              int32_t* ct_dev, int32_t* ncap_dev);
+
+/* Sec. 4: exact minimum cut of the context's H x W grid (its neighbourhood)
+ * with the given capacities; writes mask and cut value.  Device-side status is
+ * reported by seg_sync. */
+int seg_mincut(seg_ctx* ctx, const int32_t* cs_dev, const int32_t* ct_dev, const int32_t* ncap_dev,
+               uint8_t* mask_dev, int64_t* cut_dev);
+
+/* Sec. 4: standalone exact minimum cut of an H x W grid with neighbourhood nbr
+ * (4 or 8).  Allocates and frees its own workspace, synchronises `stream`, and
+ * returns the device status (SEG_ENOTCONVERGED after max_cycles cycles;
+ * max_cycles <= 0 selects the default).  *cycles (nullable) receives the
+ * number of cycles used. */
+int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_t* cs_dev,
+                    const int32_t* ct_dev, const int32_t* ncap_dev, uint8_t* mask_dev,
+                    int64_t* cut_dev, int max_cycles, int* cycles);
+
+/* Copies an intermediate map of the last seg_saliency/seg_push_frame into
+ * dst_host (float, n elements), for stage-by-stage parity checks:
+ *   which 0: pyramid channel index / 16 (0 I, 1 RG, 2 BY) at level index % 16 (levels >= 1)
+ *   which 1: orientation map theta = index / 16 at level index % 16
+ *   which 2: normalised conspicuity map index (0 I, 1 RG, 2 BY, 3 O) at sigma_S = c_max
+ *   which 3: S at sigma_S (index ignored)
+ * Synchronises the stream.  Errors: SEG_EINVAL (unknown map or wrong n). */
+int seg_debug_copy(seg_ctx* ctx, int which, int index, float* dst_host, size_t n);
+
+/* Size of pyramid level `level` along an n-pixel axis: ceil-halving. */
+int seg_level_dim(int n, int level);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

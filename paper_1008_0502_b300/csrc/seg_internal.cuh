@@ -1,0 +1,227 @@
+// seg_internal.cuh -- shared declarations of the CUDA path (sm_103a).
+//
+// The library is one shared object built from saliency.cu, prior_terms.cu,
+// maxflow.cu and seg_api.cu.  This header holds the context layout, the
+// kernel-argument structs and small device helpers.  Nothing here is shared
+// with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/seg.h"
+
+#define SEG_MAX_LEVELS 16
+#define SEG_MAX_ORIENT 8
+#define SEG_MAX_TAPS 17  // radius <= 8
+#define SEG_MAX_PAIRS 64
+#define SEG_MAX_MAPS (SEG_MAX_PAIRS * (3 + SEG_MAX_ORIENT))
+#define SEG_INF_H 0x3fffffff
+
+#define SEG_CUDA_TRY(expr)                   \
+  do {                                       \
+    cudaError_t _e = (expr);                 \
+    if (_e != cudaSuccess) return SEG_ECUDA; \
+  } while (0)
+
+__device__ __forceinline__ int seg_clampi(int v, int lo, int hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Source coordinate of the half-pixel-centred resampling used by every
+// across-scale interpolation: src = (dst + 0.5) * ns / nd - 0.5, clamped to
+// [0, ns-1].  Computed from integers, so the cell index is exact and the
+// fraction carries a single rounding.
+__device__ __forceinline__ void seg_src_coord(int d, int ns, int nd, int& i0, int& i1, float& f) {
+  int num = (2 * d + 1) * ns - nd;  // src = num / (2 nd)
+  if (num <= 0) {
+    i0 = 0;
+    i1 = 0;
+    f = 0.f;
+    return;
+  }
+  int den = 2 * nd;
+  int q = num / den;
+  if (q >= ns - 1) {
+    i0 = ns - 1;
+    i1 = ns - 1;
+    f = 0.f;
+    return;
+  }
+  i0 = q;
+  i1 = q + 1;
+  f = (float)(num - q * den) / (float)den;
+}
+
+__device__ __forceinline__ float seg_bilinear(const float* src, int hs, int ws, int y, int x,
+                                              int hd, int wd) {
+  int y0, y1, x0, x1;
+  float fy, fx;
+  seg_src_coord(y, hs, hd, y0, y1, fy);
+  seg_src_coord(x, ws, wd, x0, x1, fx);
+  float top = (1.f - fx) * src[y0 * ws + x0] + fx * src[y0 * ws + x1];
+  float bot = (1.f - fx) * src[y1 * ws + x0] + fx * src[y1 * ws + x1];
+  return (1.f - fy) * top + fy * bot;
+}
+
+__device__ __forceinline__ double seg_warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float seg_warp_max_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float seg_warp_min_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float seg_warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- saliency
+// Separable factors of the zero-mean complex Gabor (rank 2 per orientation):
+//   k_theta(u,v) = hx(u) vy(v) - kappa * g0(u) g0(v)
+// with hx(u) = g(u) e^{i w u cos theta}/sum g, vy(v) = g(v) e^{i w v sin theta}/sum g,
+// g0 = g / sum g and kappa = (sum hx)(sum vy).
+struct GaborTaps {
+  int R;
+  int no;
+  float g0[SEG_MAX_TAPS];
+  float hx_re[SEG_MAX_ORIENT][SEG_MAX_TAPS], hx_im[SEG_MAX_ORIENT][SEG_MAX_TAPS];
+  float vy_re[SEG_MAX_ORIENT][SEG_MAX_TAPS], vy_im[SEG_MAX_ORIENT][SEG_MAX_TAPS];
+  float kap_re[SEG_MAX_ORIENT], kap_im[SEG_MAX_ORIENT];
+};
+
+// Per-context saliency workspace.  Level-0 feature planes are never stored:
+// the first kernel fuses feature extraction with the first REDUCE.
+struct SalWS {
+  int H, W, L, c_min, c_max, d_min, d_max, no, s_max, sS, tile;
+  int opp_sum;
+  float flat;
+  float w[4];
+  int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
+  float* pyr[3][SEG_MAX_LEVELS];              // levels 1..L-1
+  float* ori[SEG_MAX_ORIENT][SEG_MAX_LEVELS];  // levels c_min..s_max
+  int npairs, nch, nmaps;                      // nch = 3 + no channels, nmaps = npairs * nch
+  int pair_c[SEG_MAX_PAIRS], pair_s[SEG_MAX_PAIRS];
+  unsigned* mm;  // [nmaps][2]: min and max as float bits (maps are >= 0)
+  float* tpart;  // [nbands_total]: per-band sums of tile maxima
+  int nbands_total;
+  float* nab;     // [nmaps][2]: N(.) as the affine map a*v + b
+  float* acc[2];  // ping-pong channel accumulators at scale c (nch planes)
+  float* consp;   // 4 planes at sigma_S: N(C_I), N(C_RG), N(C_BY), N(C_O)
+  float* csum;    // scratch plane at sigma_S
+  float* S;       // combined map at sigma_S
+  unsigned* salmax;  // max of the upsampled saliency (float bits)
+  int* smax;         // frame max of r+g+b
+  GaborTaps taps;
+};
+
+// ---------------------------------------------------------------- prior / terms
+struct KalmanDev {
+  double P;  // sigma^2_xi1(t-1)
+  int t;     // frame index
+  int pad;
+};
+
+struct GaussDev {
+  double mu[2][3];
+  float muf[2][3];
+  float linv[2][6];  // lower-triangular inverse Cholesky factor: l00 l10 l11 l20 l21 l22
+  float lconst[2];   // 1/2 log det + 3/2 log 2 pi
+  int degenerate;    // bit a: label a has zero total weight
+};
+
+// ---------------------------------------------------------------- max-flow
+#define MF_TW 32
+#define MF_TH 16
+#define MF_THREADS (MF_TW * MF_TH)
+
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+struct MFArgs {
+  int H, W, N, ndir;
+  int ntx, nty;
+  const int32_t* cs;
+  const int32_t* ct;
+  const int32_t* ncap;
+  int* e;
+  int* h;
+  int* rt;
+  int* r;             // ndir planes of N residual capacities
+  unsigned char* rm;  // residual bitmask per node
+  unsigned char* z;   // reach flags
+  uint8_t* mask_out;
+  uint8_t* mask_state;  // nullable second copy of the mask
+  long long* cut_out;   // nullable
+  unsigned long long* cut_acc;
+  unsigned int* flags;  // [3] rotating round counters
+  GridBar* bar;
+  int* status;  // [0] error code, [1] cycles, [2] global relabels, [3] bfs rounds
+  int max_cycles, gr_every, local_iters;
+  long long timeout_ns;
+};
+
+struct MFWS {
+  int* e;
+  int* h;
+  int* rt;
+  int* r;
+  unsigned char* rm;
+  unsigned char* z;
+  unsigned long long* cut_acc;
+  unsigned int* flags;
+  GridBar* bar;
+};
+
+// ---------------------------------------------------------------- context
+struct seg_ctx {
+  cudaStream_t stream;
+  int device;
+  int H, W, N;
+  seg_params p;
+  void* arena;
+  SalWS sal;
+  KalmanDev* kal;
+  GaussDev* gauss;
+  double* mom_part;
+  int mom_blocks;
+  int* lut;  // [766][2] n-link capacities by |delta(r+g+b)| and diagonal flag
+  uint8_t* prev_mask;
+  int32_t *cs, *ct, *ncap;
+  float *sal_buf, *prior_buf;
+  uint8_t* mask_buf;
+  int64_t* cut_buf;
+  uint8_t* rgb_stage;
+  MFWS mf;
+  int mf_grid;
+  int* status;       // device [4]
+  int* status_host;  // pinned [4]
+};
+
+// ---------------------------------------------------------------- launchers
+int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes);
+void sal_bind(SalWS& s, char* base);
+int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);
+
+int pt_mom_blocks(int H, int W);
+int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
+                    double wf_host, float* prior);
+int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int advance_kalman,
+                            int32_t* cs, int32_t* ct, int32_t* ncap);
+void pt_fill_lut(const seg_params& p, int* lut_host);
+
+size_t mf_bytes(int H, int W, int ndir);
+void mf_bind(MFWS& m, char* base, int H, int W, int ndir);
+int mf_grid_size(int H, int W, int* grid);
+int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
+              const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
+              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters);
+
+static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }
