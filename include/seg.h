@@ -68,11 +68,11 @@ typedef struct seg_params {
   float f_sigma;           /* Gaussian smoothing of the previous mask (2) */
   int32_t f_radius;        /* its radius (6; <= 8) */
   float eps;               /* clamp for logs and the border prior (1e-4) */
-  float lambda_u;          /* colour-likelihood weight (1) */
-  float lambda_p;          /* Potts constant xi_2 (0) */
-  float lambda_s;          /* contrast weight of psi_2 (1.5) */
-  float sigma_I;           /* contrast intensity scale (0.05) */
-  float cap_scale;         /* K: capacity = min(2^24, floor(K*cost + 1/2)) (1000) */
+  double lambda_u;         /* colour-likelihood weight (1) */
+  double lambda_p;         /* Potts constant xi_2 (0) */
+  double lambda_s;         /* contrast weight of psi_2 (1.5) */
+  double sigma_I;          /* contrast intensity scale (0.05) */
+  double cap_scale;        /* K: capacity = min(2^24, floor(K*cost + 1/2)) (1000) */
   int32_t neighbourhood;   /* 4 or 8 */
   int32_t max_cycles;      /* min-cut cycle cap -> SEG_ENOTCONVERGED (20000) */
   int32_t global_relabel_every; /* min-cut cycles between global relabels (4) */

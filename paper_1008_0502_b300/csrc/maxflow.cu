@@ -1,0 +1,467 @@
+// maxflow.cu -- exact s-t minimum cut of the pixel grid (Sec. 4) on sm_103a.
+//
+// One persistent cooperative kernel per cut (k_maxflow):
+//
+//  1. Init: residual capacities of every directed n-link from the undirected
+//     capacities; the source arcs are saturated at once and s->v->t flow is
+//     cancelled per pixel, so a node starts with excess cs - min(cs, ct) and
+//     sink residual ct - min(cs, ct).
+//  2. Push-relabel on the "max preflow" (Goldberg-Tarjan first phase): a node is
+//     active while it has excess and height < N.  The grid is cut into 32x16
+//     tiles coloured by (tile_y mod 2, tile_x mod 2).  In each of the four
+//     phases of a cycle only tiles of one colour run; no two of them share a
+//     node or an edge, and every node outside a running tile stays fixed, so a
+//     phase is a set of independent region discharges (each CTA runs up to
+//     local_iters synchronous push / relabel sweeps over its tile in shared
+//     memory; pushes into a neighbouring, idle tile go straight to global
+//     memory).  A grid barrier separates phases.
+//  3. Global relabel every gr_every cycles: exact BFS distances to the sink in
+//     the residual graph, computed as a monotone fixpoint (tile-local
+//     relaxation in shared memory, rounds of tiles until no value changes);
+//     unreachable nodes get height INF and never become active again.
+//  4. Stop when a whole cycle does no push and no relabel: no active node is
+//     left, the preflow is maximum.  The minimal source set is then the
+//     residual closure of the nodes that still hold excess (their height is
+//     >= N, so they cannot reach t); every minimum cut contains it and it is
+//     itself a minimum cut, so the mask is unique.  The cut value is the flow
+//     that reached t.
+//
+// Every grid barrier waits with a time limit; on expiry the kernel records
+// SEG_ETIMEOUT and every CTA returns.  A cycle cap records SEG_ENOTCONVERGED.
+#include <string.h>
+
+#include "seg_internal.cuh"
+
+#define MF_HX (MF_TW + 2)
+#define MF_HY (MF_TH + 2)
+#define MF_HN (MF_HX * MF_HY)
+
+__constant__ int c_dx[8] = {1, -1, 0, 0, 1, -1, -1, 1};   // E W S N SE NW SW NE
+__constant__ int c_dy[8] = {0, 0, 1, -1, 1, -1, 1, -1};  // opposite direction = d ^ 1
+
+struct MFShared {
+  int h[MF_HN];  // heights (or BFS distances) with a one-node halo
+  int e[MF_THREADS];
+  int rt[MF_THREADS];
+  int r[8][MF_THREADS];
+  unsigned char b[MF_HN];  // residual bitmasks with halo
+  unsigned char z[MF_HN];  // reach flags with halo
+  int ok;
+};
+
+__device__ __forceinline__ long long mf_now() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
+// the CTA) once any CTA has recorded a timeout.
+__device__ bool mf_grid_sync(const MFArgs& a, MFShared& s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* genp = &a.bar->gen;
+    unsigned int g = *genp;
+    __threadfence();
+    unsigned int arrived = atomicAdd(&a.bar->count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(&a.bar->count, 0u);
+      __threadfence();
+      atomicAdd(&a.bar->gen, 1u);
+    } else {
+      long long t0 = mf_now();
+      while (*genp == g) {
+        if (mf_now() - t0 > a.timeout_ns) {
+          atomicCAS(&a.status[0], 0, SEG_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)&a.status[0] == SEG_ETIMEOUT) ok = 0;
+    s.ok = ok;
+  }
+  __syncthreads();
+  return s.ok != 0;
+}
+
+__device__ __forceinline__ unsigned int mf_flag_read(const MFArgs& a, unsigned int epoch) {
+  return *(volatile unsigned int*)&a.flags[epoch % 3];
+}
+
+// Block-uniform: start a flag round (clears the slot the NEXT round will use).
+__device__ __forceinline__ void mf_flag_begin(const MFArgs& a, unsigned int epoch) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(epoch + 1) % 3] = 0u;
+}
+
+// ---------------------------------------------------------------- BFS to the sink
+// d(u) = 1 if u has residual to t, else 1 + min over residual arcs u->v of d(v):
+// relaxed to the local fixpoint with the halo fixed at its current global value.
+__device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty) {
+  const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
+  for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
+    int hy = i / MF_HX, hx = i - hy * MF_HX;
+    int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
+    s.h[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) ? a.h[gy * a.W + gx] : SEG_INF_H;
+  }
+  const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
+  const int gy = Y0 + ly, gx = X0 + lx;
+  const bool valid = gy < a.H && gx < a.W;
+  const int g = gy * a.W + gx;
+  const int hi = (ly + 1) * MF_HX + lx + 1;
+  const unsigned bits = valid ? a.rm[g] : 0u;
+  __syncthreads();
+  bool any = false;
+  for (;;) {
+    int ch = 0;
+    if (valid) {
+      int cur = s.h[hi], nd = cur;
+      for (int d = 0; d < a.ndir; ++d)
+        if ((bits >> d) & 1u) nd = min(nd, s.h[hi + c_dy[d] * MF_HX + c_dx[d]] + 1);
+      if (nd < cur) {
+        s.h[hi] = nd;
+        ch = 1;
+      }
+    }
+    if (!__syncthreads_or(ch)) break;
+    any = true;
+  }
+  if (valid) a.h[g] = s.h[hi];
+  __syncthreads();  // the next tile reuses the shared arrays
+  return any;
+}
+
+// z(v) = 1 if some residual arc u->v has z(u) = 1 (pull form, halo bitmasks).
+__device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty) {
+  const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
+  for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
+    int hy = i / MF_HX, hx = i - hy * MF_HX;
+    int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
+    bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    s.z[i] = in ? a.z[gy * a.W + gx] : 0;
+    s.b[i] = in ? a.rm[gy * a.W + gx] : 0;
+  }
+  const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
+  const int gy = Y0 + ly, gx = X0 + lx;
+  const bool valid = gy < a.H && gx < a.W;
+  const int hi = (ly + 1) * MF_HX + lx + 1;
+  __syncthreads();
+  bool any = false;
+  for (;;) {
+    int ch = 0;
+    if (valid && !s.z[hi]) {
+      for (int d = 0; d < a.ndir; ++d) {
+        int nb = hi + c_dy[d] * MF_HX + c_dx[d];
+        if (s.z[nb] && ((s.b[nb] >> (d ^ 1)) & 1u)) {
+          s.z[hi] = 1;
+          ch = 1;
+          break;
+        }
+      }
+    }
+    if (!__syncthreads_or(ch)) break;
+    any = true;
+  }
+  if (valid && any) a.z[gy * a.W + gx] = s.z[hi];
+  __syncthreads();  // the next tile reuses the shared arrays
+  return any;
+}
+
+// ---------------------------------------------------------------- region discharge
+// Up to local_iters synchronous sweeps over one tile: push along admissible
+// arcs (h(u) = h(v) + 1, t has height 0), then relabel every node still active
+// to 1 + min over residual arcs.  Returns whether any push or relabel happened.
+__device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty) {
+  const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
+  const int N = a.N, W = a.W;
+  for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
+    int hy = i / MF_HX, hx = i - hy * MF_HX;
+    int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
+    s.h[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < W) ? a.h[gy * W + gx] : SEG_INF_H;
+  }
+  const int tid = threadIdx.x;
+  const int ly = tid / MF_TW, lx = tid - ly * MF_TW;
+  const int gy = Y0 + ly, gx = X0 + lx;
+  const bool valid = gy < a.H && gx < W;
+  const int g = gy * W + gx;
+  const int hi = (ly + 1) * MF_HX + lx + 1;
+  s.e[tid] = valid ? a.e[g] : 0;
+  s.rt[tid] = valid ? a.rt[g] : 0;
+  for (int d = 0; d < a.ndir; ++d) s.r[d][tid] = valid ? a.r[d * N + g] : 0;
+  __syncthreads();
+  int work = 0;
+  for (int it = 0; it < a.local_iters; ++it) {
+    // push
+    if (valid) {
+      const int e0 = s.e[tid], hu = s.h[hi];
+      if (e0 > 0 && hu < N) {
+        int ex = e0;
+        if (hu == 1) {
+          int rtv = s.rt[tid];
+          if (rtv > 0) {
+            int dl = min(ex, rtv);
+            s.rt[tid] = rtv - dl;
+            ex -= dl;
+          }
+        }
+        for (int d = 0; d < a.ndir && ex > 0; ++d) {
+          int rr = s.r[d][tid];
+          if (rr <= 0 || hu != s.h[hi + c_dy[d] * MF_HX + c_dx[d]] + 1) continue;
+          int dl = min(ex, rr);
+          s.r[d][tid] = rr - dl;
+          ex -= dl;
+          int nly = ly + c_dy[d], nlx = lx + c_dx[d];
+          if (nly >= 0 && nly < MF_TH && nlx >= 0 && nlx < MF_TW) {
+            int nt = nly * MF_TW + nlx;
+            atomicAdd(&s.e[nt], dl);
+            s.r[d ^ 1][nt] += dl;  // only this node writes the reverse arc in this sweep
+          } else {
+            int gv = g + c_dy[d] * W + c_dx[d];
+            atomicAdd(&a.e[gv], dl);
+            atomicAdd(&a.r[(d ^ 1) * N + gv], dl);
+          }
+        }
+        if (ex != e0) {
+          atomicAdd(&s.e[tid], ex - e0);
+          work = 1;
+        }
+      }
+    }
+    __syncthreads();
+    // relabel
+    bool act = false;
+    if (valid && s.e[tid] > 0) {
+      int cur = s.h[hi];
+      if (cur < N) {
+        int nh = s.rt[tid] > 0 ? 1 : SEG_INF_H;
+        for (int d = 0; d < a.ndir; ++d)
+          if (s.r[d][tid] > 0) nh = min(nh, s.h[hi + c_dy[d] * MF_HX + c_dx[d]] + 1);
+        nh = min(nh, SEG_INF_H);
+        if (nh > cur) {
+          s.h[hi] = nh;
+          work = 1;
+          cur = nh;
+        }
+        act = cur < N;
+      }
+    }
+    if (!__syncthreads_or(act)) break;
+  }
+  __syncthreads();
+  if (valid) {
+    a.e[g] = s.e[tid];
+    a.rt[g] = s.rt[tid];
+    a.h[g] = s.h[hi];
+    for (int d = 0; d < a.ndir; ++d) a.r[d * N + g] = s.r[d][tid];
+  }
+  return __syncthreads_or(work);
+}
+
+// ---------------------------------------------------------------- the kernel
+__device__ __forceinline__ bool cap_ok(int c) { return c >= 0 && c <= (1 << 24); }
+
+__global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
+  __shared__ MFShared s;
+  const int N = a.N, W = a.W, H = a.H;
+  const int nthr = gridDim.x * blockDim.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ntiles = a.ntx * a.nty;
+
+  // ---- 1. init
+  for (int u = gtid; u < N; u += nthr) {
+    int y = u / W, x = u - y * W;
+    int cs = a.cs[u], ct = a.ct[u];
+    bool bad = !cap_ok(cs) || !cap_ok(ct);
+    int m = min(cs, ct);
+    a.e[u] = cs - m;
+    a.rt[u] = ct - m;
+    int cE = x + 1 < W ? a.ncap[u] : 0;
+    int cS = y + 1 < H ? a.ncap[N + u] : 0;
+    bad |= !cap_ok(cE) || !cap_ok(cS);
+    a.r[0 * N + u] = cE;
+    a.r[1 * N + u] = x > 0 ? a.ncap[u - 1] : 0;
+    a.r[2 * N + u] = cS;
+    a.r[3 * N + u] = y > 0 ? a.ncap[N + u - W] : 0;
+    if (a.ndir == 8) {
+      int cSE = (x + 1 < W && y + 1 < H) ? a.ncap[2 * N + u] : 0;
+      int cSW = (x > 0 && y + 1 < H) ? a.ncap[3 * N + u] : 0;
+      bad |= !cap_ok(cSE) || !cap_ok(cSW);
+      a.r[4 * N + u] = cSE;
+      a.r[5 * N + u] = (x > 0 && y > 0) ? a.ncap[2 * N + u - W - 1] : 0;
+      a.r[6 * N + u] = cSW;
+      a.r[7 * N + u] = (x + 1 < W && y > 0) ? a.ncap[3 * N + u - W + 1] : 0;
+    }
+    if (bad) atomicCAS(&a.status[0], 0, SEG_ECAPACITY);
+  }
+  if (!mf_grid_sync(a, s)) return;
+  if (*(volatile int*)&a.status[0] == SEG_ECAPACITY) return;
+
+  unsigned int epoch = 0;
+  int cycle = 0, n_gr = 0, n_rounds = 0;
+  bool converged = false;
+  for (;;) {
+    // ---- 3. global relabel
+    if (cycle % a.gr_every == 0) {
+      for (int u = gtid; u < N; u += nthr) {
+        unsigned bits = 0;
+        for (int d = 0; d < a.ndir; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
+        a.rm[u] = (unsigned char)bits;
+        a.h[u] = a.rt[u] > 0 ? 1 : SEG_INF_H;
+      }
+      if (!mf_grid_sync(a, s)) return;
+      for (;;) {
+        mf_flag_begin(a, epoch);
+        bool ch = false;
+        for (int k = blockIdx.x; k < ntiles; k += gridDim.x)
+          ch |= mf_tile_bfs(a, s, k % a.ntx, k / a.ntx);
+        if (ch && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
+        if (!mf_grid_sync(a, s)) return;
+        unsigned int f = mf_flag_read(a, epoch);
+        ++epoch;
+        ++n_rounds;
+        if (f == 0u) break;
+      }
+      ++n_gr;
+    }
+    // ---- 2. one cycle of the four colour phases
+    mf_flag_begin(a, epoch);
+    for (int color = 0; color < 4; ++color) {
+      const int cy = color >> 1, cx = color & 1;
+      const int ntx_c = (a.ntx - cx + 1) / 2, nty_c = (a.nty - cy + 1) / 2;
+      const int ntc = ntx_c * nty_c;
+      bool work = false;
+      for (int k = blockIdx.x; k < ntc; k += gridDim.x)
+        work |= mf_discharge(a, s, 2 * (k % ntx_c) + cx, 2 * (k / ntx_c) + cy);
+      if (work && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
+      if (!mf_grid_sync(a, s)) return;
+    }
+    unsigned int w = mf_flag_read(a, epoch);
+    ++epoch;
+    ++cycle;
+    if (w == 0u) {
+      converged = true;
+      break;
+    }
+    if (cycle >= a.max_cycles) break;
+  }
+
+  // ---- 4. minimal source set and cut value
+  long long flow_t = 0;
+  for (int u = gtid; u < N; u += nthr) {
+    unsigned bits = 0;
+    for (int d = 0; d < a.ndir; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
+    a.rm[u] = (unsigned char)bits;
+    a.z[u] = a.e[u] > 0 ? 1 : 0;
+    flow_t += (long long)a.ct[u] - a.rt[u];
+  }
+  for (int o = 16; o > 0; o >>= 1) flow_t += __shfl_xor_sync(0xffffffffu, flow_t, o);
+  if ((threadIdx.x & 31) == 0 && flow_t != 0)
+    atomicAdd(a.cut_acc, (unsigned long long)flow_t);
+  if (!mf_grid_sync(a, s)) return;
+  for (;;) {
+    mf_flag_begin(a, epoch);
+    bool ch = false;
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) ch |= mf_tile_reach(a, s, k % a.ntx, k / a.ntx);
+    if (ch && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
+    if (!mf_grid_sync(a, s)) return;
+    unsigned int f = mf_flag_read(a, epoch);
+    ++epoch;
+    ++n_rounds;
+    if (f == 0u) break;
+  }
+  for (int u = gtid; u < N; u += nthr) {
+    uint8_t v = a.z[u];
+    a.mask_out[u] = v;
+    if (a.mask_state) a.mask_state[u] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (a.cut_out) *a.cut_out = (long long)*(volatile unsigned long long*)a.cut_acc;
+    if (!converged) atomicCAS(&a.status[0], 0, SEG_ENOTCONVERGED);
+    a.status[1] = cycle;
+    a.status[2] = n_gr;
+    a.status[3] = n_rounds;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+size_t mf_bytes(int H, int W, int ndir) {
+  size_t N = (size_t)H * W;
+  return seg_align(N * 4) * 3 + seg_align(N * 4 * ndir) + seg_align(N) * 2 + seg_align(8) +
+         seg_align(16) + seg_align(sizeof(GridBar));
+}
+
+void mf_bind(MFWS& m, char* base, int H, int W, int ndir) {
+  size_t N = (size_t)H * W, off = 0;
+  auto take = [&](size_t b) {
+    char* p = base + off;
+    off += seg_align(b);
+    return p;
+  };
+  m.e = (int*)take(N * 4);
+  m.h = (int*)take(N * 4);
+  m.rt = (int*)take(N * 4);
+  m.r = (int*)take(N * 4 * ndir);
+  m.rm = (unsigned char*)take(N);
+  m.z = (unsigned char*)take(N);
+  m.cut_acc = (unsigned long long*)take(8);
+  m.flags = (unsigned int*)take(16);
+  m.bar = (GridBar*)take(sizeof(GridBar));
+}
+
+int mf_grid_size(int H, int W, int* grid) {
+  int dev, nsm, per_sm = 0, coop = 0;
+  SEG_CUDA_TRY(cudaGetDevice(&dev));
+  SEG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  SEG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return SEG_ECUDA;
+  SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_maxflow, MF_THREADS, 0));
+  if (per_sm < 1) return SEG_ECUDA;
+  int ntx = (W + MF_TW - 1) / MF_TW, nty = (H + MF_TH - 1) / MF_TH;
+  int per_color = ((ntx + 1) / 2) * ((nty + 1) / 2);
+  int g = per_sm * nsm;
+  *grid = per_color < g ? per_color : g;
+  return SEG_OK;
+}
+
+int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
+              const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
+              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters) {
+  MFArgs a;
+  memset(&a, 0, sizeof(a));
+  a.H = H;
+  a.W = W;
+  a.N = H * W;
+  a.ndir = nbr;
+  a.ntx = (W + MF_TW - 1) / MF_TW;
+  a.nty = (H + MF_TH - 1) / MF_TH;
+  a.cs = cs;
+  a.ct = ct;
+  a.ncap = ncap;
+  a.e = m.e;
+  a.h = m.h;
+  a.rt = m.rt;
+  a.r = m.r;
+  a.rm = m.rm;
+  a.z = m.z;
+  a.mask_out = mask_out;
+  a.mask_state = mask_state;
+  a.cut_out = cut_out;
+  a.cut_acc = m.cut_acc;
+  a.flags = m.flags;
+  a.bar = m.bar;
+  a.status = status;
+  a.max_cycles = max_cycles;
+  a.gr_every = gr_every < 1 ? 1 : gr_every;
+  a.local_iters = local_iters < 1 ? 1 : local_iters;
+  a.timeout_ns = 4000000000LL;
+  SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8, st));
+  SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));
+  SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), st));
+  void* args[] = {&a};
+  SEG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_maxflow, dim3(grid), dim3(MF_THREADS), args,
+                                           0, st));
+  return SEG_OK;
+}

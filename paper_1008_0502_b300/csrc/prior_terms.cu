@@ -1,0 +1,418 @@
+// prior_terms.cu -- saliency prior, Kalman update and MRF terms on sm_103a.
+//
+//   k_prior      Sec. 5 + Sec. 6: q = saliency / max (eps on the border band),
+//                f = separable Gaussian of the previous mask (shared-memory halo
+//                tile), p-hat = w_f f + (1 - w_f) q.  w_f comes from the device
+//                Kalman state, so a frame needs no host round trip.
+//   k_mom1       first pass of the prior-weighted colour moments (Sec. 5: all
+//                pixels, weighted by p-hat for the object, 1 - p-hat for the
+//                background): weight sums and weighted colour sums
+//   k_mom_fin1   means; advances the Kalman variance (Sec. 6 equations)
+//   k_mom2       second pass: centred weighted second moments (no cancellation)
+//   k_mom_fin2   covariance + 1e-4 I, Cholesky, inverse factor, log-determinant
+//   k_terms      Eqs. 1-4: t-links from D(a) = lambda_u psi_1(a) + xi_1(a),
+//                shifted by min_a D(a) and quantised; n-links from a host-built
+//                FP64 table indexed by |delta(r+g+b)| and the diagonal flag.
+#include <math.h>
+#include <string.h>
+
+#include "seg_internal.cuh"
+
+#define PR_TX 32
+#define PR_TY 16
+#define PR_MAXR 8
+#define MOM_PX 8  // pixels per thread in the moment passes
+
+struct PriorArgs {
+  const float* sal;
+  const unsigned* salmax;
+  const uint8_t* prev;
+  const KalmanDev* kal;  // nullable: use wf_host
+  double wf_host;
+  double a, b;  // sigma1^2, sigma2^2
+  int H, W, border;
+  float eps;
+  int fR;
+  float ftap[2 * PR_MAXR + 1];
+  float* prior;
+};
+
+__global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
+  __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
+  __shared__ float sH[PR_TY + 2 * PR_MAXR][PR_TX];
+  double wf = a.wf_host;
+  if (a.kal) {
+    int t = a.kal->t;
+    double P = a.kal->P;
+    wf = t == 0 ? 0.0 : a.a / (a.a + a.b + P);  // Sec. 6: weight on f(A_{t-1})
+  }
+  const float wff = (float)wf;
+  const int X0 = blockIdx.x * PR_TX, Y0 = blockIdx.y * PR_TY;
+  const int R = a.fR, iny = PR_TY + 2 * R;
+  const bool use_f = wf != 0.0 && a.prev != nullptr;
+  if (use_f) {
+    const int inx = PR_TX + 2 * R;
+    for (int i = threadIdx.x; i < iny * inx; i += blockDim.x) {
+      int ry = i / inx, rx = i - ry * inx;
+      int gy = seg_clampi(Y0 - R + ry, 0, a.H - 1), gx = seg_clampi(X0 - R + rx, 0, a.W - 1);
+      sM[ry][rx] = (float)a.prev[(size_t)gy * a.W + gx];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < iny * PR_TX; i += blockDim.x) {
+      int ry = i / PR_TX, x = i - ry * PR_TX;
+      float acc = 0.f;
+      for (int u = 0; u <= 2 * R; ++u) acc += a.ftap[u] * sM[ry][x + u];
+      sH[ry][x] = acc;
+    }
+    __syncthreads();
+  }
+  const float mx = __uint_as_float(*a.salmax);
+  for (int i = threadIdx.x; i < PR_TY * PR_TX; i += blockDim.x) {
+    int y = i / PR_TX, x = i - y * PR_TX;
+    int gy = Y0 + y, gx = X0 + x;
+    if (gy >= a.H || gx >= a.W) continue;
+    size_t g = (size_t)gy * a.W + gx;
+    bool edge = gy < a.border || gy >= a.H - a.border || gx < a.border || gx >= a.W - a.border;
+    float q = edge ? a.eps : (mx > 0.f ? a.sal[g] / mx : 0.f);
+    float p = (1.f - wff) * q;
+    if (use_f) {
+      float f = 0.f;
+      for (int v = 0; v <= 2 * R; ++v) f += a.ftap[v] * sH[y + v][x];
+      p += wff * f;
+    }
+    a.prior[g] = p;
+  }
+}
+
+// Block reduction of NV doubles per thread into part[blockIdx.x * NV + k].
+template <int NV>
+__device__ __forceinline__ void block_sum_to(double* v, double* part) {
+  __shared__ double red[32][NV];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = seg_warp_sum_d(v[k]);
+    if (lane == 0) red[wid][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    part[blockIdx.x * NV + threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
+                                              const float* __restrict__ prior, int N,
+                                              double* part) {
+  float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // label 0: w, wr, wg, wb; label 1: same
+  int base = (blockIdx.x * blockDim.x + threadIdx.x);
+  int stride = gridDim.x * blockDim.x;
+  for (int i = base; i < N; i += stride) {
+    float p = prior[i];
+    float r = rgb[3 * i] / 255.f, g = rgb[3 * i + 1] / 255.f, b = rgb[3 * i + 2] / 255.f;
+    float w0 = 1.f - p;
+    s[0] += w0;
+    s[1] += w0 * r;
+    s[2] += w0 * g;
+    s[3] += w0 * b;
+    s[4] += p;
+    s[5] += p * r;
+    s[6] += p * g;
+    s[7] += p * b;
+  }
+  double d[8];
+  for (int k = 0; k < 8; ++k) d[k] = s[k];
+  block_sum_to<8>(d, part);
+}
+
+struct MomFinArgs {
+  const double* part;
+  int nblocks;
+  GaussDev* gauss;
+  KalmanDev* kal;  // nullable: advance the variance recursion
+  double a, b;
+};
+
+// Deterministic fixed-order reduction of the per-block partials (one CTA).
+template <int NV>
+__device__ void reduce_parts(const double* part, int nblocks, double* out) {
+  __shared__ double red[256][NV];
+  double s[NV];
+  for (int k = 0; k < NV; ++k) s[k] = 0.0;
+  for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x)
+    for (int k = 0; k < NV; ++k) s[k] += part[bk * NV + k];
+  for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = s[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < NV; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NV; ++k) out[k] = red[0][k];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_mom_fin1(MomFinArgs a) {
+  __shared__ double tot[8];
+  reduce_parts<8>(a.part, a.nblocks, tot);
+  if (threadIdx.x != 0) return;
+  GaussDev* g = a.gauss;
+  g->degenerate = 0;
+  for (int lab = 0; lab < 2; ++lab) {
+    double sw = tot[4 * lab];
+    if (!(sw > 0.0)) g->degenerate |= 1 << lab;
+    for (int k = 0; k < 3; ++k) {
+      double m = sw > 0.0 ? tot[4 * lab + 1 + k] / sw : 0.0;
+      g->mu[lab][k] = m;
+      g->muf[lab][k] = (float)m;
+    }
+    g->sw[lab] = sw;
+  }
+  if (a.kal) {  // Sec. 6: sigma^2_xi1(t) = a (b + P) / (a + b + P); at t = 0, P_{-1} = inf gives a
+    KalmanDev* k = a.kal;
+    double P = k->P;
+    k->P = k->t == 0 ? a.a : a.a * (a.b + P) / (a.a + a.b + P);
+    k->t += 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
+                                              const float* __restrict__ prior, int N,
+                                              const GaussDev* __restrict__ gauss, double* part) {
+  float m0r = gauss->muf[0][0], m0g = gauss->muf[0][1], m0b = gauss->muf[0][2];
+  float m1r = gauss->muf[1][0], m1g = gauss->muf[1][1], m1b = gauss->muf[1][2];
+  float s[12];
+  for (int k = 0; k < 12; ++k) s[k] = 0.f;
+  int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    float p = prior[i];
+    float r = rgb[3 * i] / 255.f, g = rgb[3 * i + 1] / 255.f, b = rgb[3 * i + 2] / 255.f;
+    float w0 = 1.f - p;
+    float dr = r - m0r, dg = g - m0g, db = b - m0b;
+    s[0] += w0 * dr * dr;
+    s[1] += w0 * dg * dr;
+    s[2] += w0 * dg * dg;
+    s[3] += w0 * db * dr;
+    s[4] += w0 * db * dg;
+    s[5] += w0 * db * db;
+    dr = r - m1r;
+    dg = g - m1g;
+    db = b - m1b;
+    s[6] += p * dr * dr;
+    s[7] += p * dg * dr;
+    s[8] += p * dg * dg;
+    s[9] += p * db * dr;
+    s[10] += p * db * dg;
+    s[11] += p * db * db;
+  }
+  double d[12];
+  for (int k = 0; k < 12; ++k) d[k] = s[k];
+  block_sum_to<12>(d, part);
+}
+
+__global__ void __launch_bounds__(256) k_mom_fin2(MomFinArgs a) {
+  __shared__ double tot[12];
+  reduce_parts<12>(a.part, a.nblocks, tot);
+  if (threadIdx.x != 0) return;
+  GaussDev* g = a.gauss;
+  for (int lab = 0; lab < 2; ++lab) {
+    double sw = g->sw[lab];
+    if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
+      for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
+      g->lconst[lab] = 0.f;
+      continue;
+    }
+    const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
+    double c00 = m[0] / sw + 1e-4, c10 = m[1] / sw, c11 = m[2] / sw + 1e-4;
+    double c20 = m[3] / sw, c21 = m[4] / sw, c22 = m[5] / sw + 1e-4;
+    // Cholesky Sigma = L L^T
+    double l00 = sqrt(c00);
+    double l10 = c10 / l00, l20 = c20 / l00;
+    double l11 = sqrt(c11 - l10 * l10);
+    double l21 = (c21 - l20 * l10) / l11;
+    double l22 = sqrt(c22 - l20 * l20 - l21 * l21);
+    // inverse of the lower-triangular factor
+    double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
+    double i10 = -l10 * i00 / l11;
+    double i21 = -l21 * i11 / l22;
+    double i20 = -(l20 * i00 + l21 * i10) / l22;
+    g->linv[lab][0] = (float)i00;
+    g->linv[lab][1] = (float)i10;
+    g->linv[lab][2] = (float)i11;
+    g->linv[lab][3] = (float)i20;
+    g->linv[lab][4] = (float)i21;
+    g->linv[lab][5] = (float)i22;
+    // psi_1 constant: 1/2 log det Sigma + 3/2 log 2 pi, log det = 2 sum log l_ii
+    g->lconst[lab] = (float)(log(l00) + log(l11) + log(l22) + 1.5 * log(2.0 * M_PI));
+  }
+}
+
+struct TermsArgs {
+  const uint8_t* rgb;
+  const float* prior;
+  const GaussDev* gauss;
+  const int* lut;
+  int H, W, nk;
+  float eps, lambda_u, K;
+  int32_t* cs;
+  int32_t* ct;
+  int32_t* ncap;
+};
+
+__device__ __forceinline__ int32_t quant_cap(float K, float x) {
+  float v = floorf(K * x + 0.5f);
+  v = fminf(v, 16777216.f);
+  return (int32_t)fmaxf(v, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
+  __shared__ int sLut[766 * 2];
+  for (int i = threadIdx.x; i < 766 * 2; i += blockDim.x) sLut[i] = a.lut[i];
+  __syncthreads();
+  int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= a.W || y >= a.H) return;
+  size_t N = (size_t)a.H * a.W, g = (size_t)y * a.W + x;
+  const uint8_t* p = a.rgb + 3 * g;
+  int r8 = p[0], g8 = p[1], b8 = p[2];
+  float C[3] = {r8 / 255.f, g8 / 255.f, b8 / 255.f};
+  float pr = a.prior[g];
+  float D[2];
+  for (int lab = 0; lab < 2; ++lab) {
+    const float* li = a.gauss->linv[lab];
+    float d0 = C[0] - a.gauss->muf[lab][0], d1 = C[1] - a.gauss->muf[lab][1],
+          d2 = C[2] - a.gauss->muf[lab][2];
+    float y0 = li[0] * d0;
+    float y1 = li[1] * d0 + li[2] * d1;
+    float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
+    float psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + a.gauss->lconst[lab];
+    float pl = lab ? pr : 1.f - pr;
+    float xi = -logf(fminf(fmaxf(pl, a.eps), 1.f - a.eps));
+    D[lab] = a.lambda_u * psi + xi;
+  }
+  float m = fminf(D[0], D[1]);
+  a.cs[g] = quant_cap(a.K, D[0] - m);  // c(s, v) = D(0): paid when v is background
+  a.ct[g] = quant_cap(a.K, D[1] - m);  // c(v, t) = D(1): paid when v is object
+  int s0 = r8 + g8 + b8;
+  const int dx[4] = {1, 0, 1, -1}, dy[4] = {0, 1, 1, 1};
+  for (int k = 0; k < a.nk; ++k) {
+    int xx = x + dx[k], yy = y + dy[k];
+    int32_t c = 0;
+    if (xx >= 0 && xx < a.W && yy < a.H) {
+      const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
+      int ds = abs(s0 - (q[0] + q[1] + q[2]));
+      c = sLut[2 * ds + (k >= 2)];
+    }
+    a.ncap[k * N + g] = c;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+// n-link capacity table, FP64 on the host so the integer capacities are exact:
+// lut[2*ds + diag] = min(2^24, floor(K (lambda_p + lambda_s exp(-(ds/765)^2 /
+// (2 sigma_I^2)) / |x-y|) + 1/2)), |x-y| = 1 or sqrt 2 (Eq. 2 with the contrast
+// term of Sec. 4).
+void pt_fill_lut(const seg_params& p, int* lut) {
+  for (int ds = 0; ds <= 765; ++ds)
+    for (int diag = 0; diag < 2; ++diag) {
+      double dI = ds / 765.0;
+      double dist = diag ? sqrt(2.0) : 1.0;
+      double c = p.lambda_p + p.lambda_s * exp(-dI * dI / (2.0 * p.sigma_I * p.sigma_I)) / dist;
+      double v = floor(p.cap_scale * c + 0.5);
+      if (v > 16777216.0) v = 16777216.0;
+      if (v < 0) v = 0;
+      lut[2 * ds + diag] = (int)v;
+    }
+}
+
+int pt_mom_blocks(int H, int W) {
+  int n = H * W;
+  int b = (n + 256 * MOM_PX - 1) / (256 * MOM_PX);
+  return b < 1 ? 1 : (b > 2048 ? 2048 : b);
+}
+
+__global__ void k_map_max(const float* __restrict__ v, int n, unsigned* out) {
+  float m = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = fmaxf(m, v[i]);
+  m = seg_warp_max_f(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// max of a non-negative saliency map (float bits order like the values)
+int pt_launch_salmax(seg_ctx* c, const float* sal) {
+  SEG_CUDA_TRY(cudaMemsetAsync(c->sal.salmax, 0, sizeof(unsigned), c->stream));
+  int nb = (c->N + 1023) / 1024;
+  nb = nb > 1184 ? 1184 : nb;
+  k_map_max<<<nb, 256, 0, c->stream>>>(sal, c->N, c->sal.salmax);
+  SEG_CUDA_TRY(cudaGetLastError());
+  return SEG_OK;
+}
+
+int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
+                    double wf_host, float* prior) {
+  const seg_params& p = c->p;
+  PriorArgs a;
+  memset(&a, 0, sizeof(a));
+  a.sal = sal;
+  a.salmax = c->sal.salmax;
+  a.prev = prev_mask;
+  a.kal = use_kalman ? c->kal : nullptr;
+  a.wf_host = wf_host;
+  a.a = p.sigma1 * p.sigma1;
+  a.b = p.sigma2 * p.sigma2;
+  a.H = c->H;
+  a.W = c->W;
+  a.border = p.border_px;
+  a.eps = p.eps;
+  a.fR = p.f_radius;
+  double g[2 * PR_MAXR + 1], sg = 0;
+  for (int u = -p.f_radius; u <= p.f_radius; ++u) {
+    g[u + p.f_radius] = exp(-(double)(u * u) / (2.0 * p.f_sigma * p.f_sigma));
+    sg += g[u + p.f_radius];
+  }
+  for (int u = 0; u <= 2 * p.f_radius; ++u) a.ftap[u] = (float)(g[u] / sg);
+  a.prior = prior;
+  dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY);
+  k_prior<<<grid, 256, 0, c->stream>>>(a);
+  SEG_CUDA_TRY(cudaGetLastError());
+  return SEG_OK;
+}
+
+int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int advance_kalman,
+                            int32_t* cs, int32_t* ct, int32_t* ncap) {
+  const seg_params& p = c->p;
+  cudaStream_t st = c->stream;
+  int N = c->N;
+  MomFinArgs fa;
+  fa.part = c->mom_part;
+  fa.nblocks = c->mom_blocks;
+  fa.gauss = c->gauss;
+  fa.kal = advance_kalman ? c->kal : nullptr;
+  fa.a = p.sigma1 * p.sigma1;
+  fa.b = p.sigma2 * p.sigma2;
+  k_mom1<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, c->mom_part);
+  k_mom_fin1<<<1, 256, 0, st>>>(fa);
+  k_mom2<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, c->gauss, c->mom_part);
+  fa.kal = nullptr;
+  k_mom_fin2<<<1, 256, 0, st>>>(fa);
+  TermsArgs ta;
+  ta.rgb = rgb;
+  ta.prior = prior;
+  ta.gauss = c->gauss;
+  ta.lut = c->lut;
+  ta.H = c->H;
+  ta.W = c->W;
+  ta.nk = p.neighbourhood / 2;
+  ta.eps = p.eps;
+  ta.lambda_u = (float)p.lambda_u;
+  ta.K = (float)p.cap_scale;
+  ta.cs = cs;
+  ta.ct = ct;
+  ta.ncap = ncap;
+  dim3 grid((c->W + 31) / 32, (c->H + 7) / 8);
+  k_terms<<<grid, 256, 0, st>>>(ta);
+  SEG_CUDA_TRY(cudaGetLastError());
+  return SEG_OK;
+}

@@ -1,0 +1,649 @@
+// saliency.cu -- the saliency map of Sec. 3 / Sec. 7.2 on sm_103a.
+//
+// Pipeline per frame (all kernels stream-ordered, no host round trip):
+//   k_rgb_max       frame max of r+g+b (the hue-normalisation threshold)
+//   k_feat_reduce1  RGB8 -> I, RG, BY features fused with the first REDUCE:
+//                   level 0 never leaves shared memory
+//   k_reduce3       Gaussian pyramid, levels 2..L-1 (separable [1 4 6 4 1]/16,
+//                   clamp-to-edge, keep even samples)
+//   k_gabor         |complex Gabor| at levels c_min..c_max+d_max, 4 orientations,
+//                   evaluated as a rank-2 separable filter from shared memory
+//   k_cs_stats      center-surround maps |X(c) -/+ up X(s)| computed on the fly;
+//                   per-map min, max and T x T tile maxima for N(.)
+//   k_cs_norm       N(.) of every map as an affine map a*v + b
+//   k_cs_accum      across-scale sum: B_c = sum_s N(CS(c,s)) + REDUCE(B_{c-1})
+//                   (REDUCE is linear, so reducing the sum equals summing the
+//                   reduced maps)
+//   k_consp         one CTA per frame at sigma_S: orientation conspicuity,
+//                   N(C_k), S = sum_k w_k N(C_k)
+//   k_upsample      S -> frame-size saliency (bilinear) and its maximum
+#include <math.h>
+#include <string.h>
+
+#include <type_traits>
+
+#include "seg_internal.cuh"
+
+#define RED_TX 32
+#define RED_TY 16
+#define RED_IN_X (2 * RED_TX + 3)
+#define RED_IN_Y (2 * RED_TY + 3)
+
+__constant__ float c_binom[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+
+// ------------------------------------------------------------------ k_rgb_max
+__global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, unsigned* mm,
+                          int nmaps) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < nmaps) {  // N(.) statistics start empty: min = +max float, max = 0
+    mm[2 * tid] = 0x7f7fffffu;
+    mm[2 * tid + 1] = 0u;
+  }
+  int m = 0;
+  for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
+    int s = rgb[3 * i] + rgb[3 * i + 1] + rgb[3 * i + 2];
+    m = max(m, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(smax, m);
+}
+
+// ------------------------------------------------------------------ features + REDUCE
+// Sec. 7.2 step 1 (features) and step 2 (pyramid).  I = (r+g+b)/765; where
+// 10*(r+g+b) > max(r+g+b) the normalised colour rn = 3r/(r+g+b) etc. (else
+// 0); R, G, B, Y broadly tuned channels clamped at 0; RG = R-G, BY = B-Y.
+__global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict__ rgb, int H, int W,
+                                                      const int* __restrict__ smax_p,
+                                                      float* __restrict__ I1, float* __restrict__ RG1,
+                                                      float* __restrict__ BY1, int h1, int w1) {
+  __shared__ float sF[3][RED_IN_Y][RED_IN_X];
+  __shared__ float sH[3][RED_IN_Y][RED_TX];
+  const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
+  const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
+  const int smax = *smax_p;
+  for (int i = threadIdx.x; i < RED_IN_Y * RED_IN_X; i += blockDim.x) {
+    int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
+    int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
+    const uint8_t* p = rgb + 3 * ((size_t)gy * W + gx);
+    int r = p[0], g = p[1], b = p[2];
+    int s = r + g + b;
+    float rn = 0.f, gn = 0.f, bn = 0.f;
+    if (10 * s > smax) {
+      float fs = (float)s;
+      rn = (float)(3 * r) / fs;
+      gn = (float)(3 * g) / fs;
+      bn = (float)(3 * b) / fs;
+    }
+    float R = fmaxf(0.f, rn - (gn + bn) / 2.f);
+    float G = fmaxf(0.f, gn - (rn + bn) / 2.f);
+    float B = fmaxf(0.f, bn - (rn + gn) / 2.f);
+    float Y = fmaxf(0.f, (rn + gn) / 2.f - fabsf(rn - gn) / 2.f - bn);
+    sF[0][ry][rx] = (float)s / 765.f;
+    sF[1][ry][rx] = R - G;
+    sF[2][ry][rx] = B - Y;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * RED_IN_Y * RED_TX; i += blockDim.x) {
+    int ch = i / (RED_IN_Y * RED_TX);
+    int rem = i - ch * RED_IN_Y * RED_TX;
+    int ry = rem / RED_TX, x = rem - ry * RED_TX;
+    const float* row = &sF[ch][ry][2 * x];
+    sH[ch][ry][x] = c_binom[0] * row[0] + c_binom[1] * row[1] + c_binom[2] * row[2] +
+                    c_binom[3] * row[3] + c_binom[4] * row[4];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * RED_TY * RED_TX; i += blockDim.x) {
+    int ch = i / (RED_TY * RED_TX);
+    int rem = i - ch * RED_TY * RED_TX;
+    int y = rem / RED_TX, x = rem - y * RED_TX;
+    int oy = Y0 + y, ox = X0 + x;
+    if (oy >= h1 || ox >= w1) continue;
+    float v = c_binom[0] * sH[ch][2 * y][x] + c_binom[1] * sH[ch][2 * y + 1][x] +
+              c_binom[2] * sH[ch][2 * y + 2][x] + c_binom[3] * sH[ch][2 * y + 3][x] +
+              c_binom[4] * sH[ch][2 * y + 4][x];
+    float* out = ch == 0 ? I1 : (ch == 1 ? RG1 : BY1);
+    out[(size_t)oy * w1 + ox] = v;
+  }
+}
+
+struct Reduce3Args {
+  const float* in[3];
+  float* out[3];
+  int h, w, h2, w2;
+};
+
+// One REDUCE step of one channel per CTA (blockIdx.z = channel).
+__global__ void __launch_bounds__(256) k_reduce3(Reduce3Args a) {
+  __shared__ float sF[RED_IN_Y][RED_IN_X];
+  __shared__ float sH[RED_IN_Y][RED_TX];
+  const float* __restrict__ in = a.in[blockIdx.z];
+  float* __restrict__ out = a.out[blockIdx.z];
+  const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
+  const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
+  for (int i = threadIdx.x; i < RED_IN_Y * RED_IN_X; i += blockDim.x) {
+    int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
+    int gy = seg_clampi(gy0 + ry, 0, a.h - 1), gx = seg_clampi(gx0 + rx, 0, a.w - 1);
+    sF[ry][rx] = in[(size_t)gy * a.w + gx];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RED_IN_Y * RED_TX; i += blockDim.x) {
+    int ry = i / RED_TX, x = i - ry * RED_TX;
+    const float* row = &sF[ry][2 * x];
+    sH[ry][x] = c_binom[0] * row[0] + c_binom[1] * row[1] + c_binom[2] * row[2] +
+                c_binom[3] * row[3] + c_binom[4] * row[4];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RED_TY * RED_TX; i += blockDim.x) {
+    int y = i / RED_TX, x = i - y * RED_TX;
+    int oy = Y0 + y, ox = X0 + x;
+    if (oy >= a.h2 || ox >= a.w2) continue;
+    out[(size_t)oy * a.w2 + ox] = c_binom[0] * sH[2 * y][x] + c_binom[1] * sH[2 * y + 1][x] +
+                                  c_binom[2] * sH[2 * y + 2][x] + c_binom[3] * sH[2 * y + 3][x] +
+                                  c_binom[4] * sH[2 * y + 4][x];
+  }
+}
+
+// ------------------------------------------------------------------ Gabor
+#define GB_TX 32
+#define GB_TY 16
+#define GB_MAXR 8
+#define GB_IN_X (GB_TX + 2 * GB_MAXR)
+#define GB_IN_Y (GB_TY + 2 * GB_MAXR)
+
+struct GaborArgs {
+  const float* in[SEG_MAX_LEVELS];
+  float* out[SEG_MAX_ORIENT][SEG_MAX_LEVELS];
+  int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
+  int lvl_first, lvl_last;
+  int blk_off[SEG_MAX_LEVELS + 1];  // prefix of tile counts from lvl_first
+};
+
+// Sec. 7.2 (edge orientation): O(sigma, theta) = |k_theta * I(sigma)| with the
+// zero-mean complex Gabor factored into two separable complex terms.
+__global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
+  __shared__ float sIn[GB_IN_Y][GB_IN_X];
+  __shared__ float sH0[GB_IN_Y][GB_TX];
+  __shared__ float sHr[GB_IN_Y][GB_TX], sHi[GB_IN_Y][GB_TX];
+  int b = blockIdx.x, l = a.lvl_first;
+  while (l < a.lvl_last && b >= a.blk_off[l - a.lvl_first + 1]) ++l;
+  b -= a.blk_off[l - a.lvl_first];
+  const int h = a.hl[l], w = a.wl[l];
+  const int ntx = (w + GB_TX - 1) / GB_TX;
+  const int X0 = (b % ntx) * GB_TX, Y0 = (b / ntx) * GB_TY;
+  const int R = t.R, K = 2 * R + 1;
+  const int iny = GB_TY + 2 * R, inx = GB_TX + 2 * R;
+  const float* __restrict__ in = a.in[l];
+  for (int i = threadIdx.x; i < iny * inx; i += blockDim.x) {
+    int ry = i / inx, rx = i - ry * inx;
+    sIn[ry][rx] = in[(size_t)seg_clampi(Y0 - R + ry, 0, h - 1) * w + seg_clampi(X0 - R + rx, 0, w - 1)];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < iny * GB_TX; i += blockDim.x) {
+    int ry = i / GB_TX, x = i - ry * GB_TX;
+    float acc = 0.f;
+    for (int u = 0; u < K; ++u) acc += t.g0[u] * sIn[ry][x + u];
+    sH0[ry][x] = acc;
+  }
+  for (int k = 0; k < t.no; ++k) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < iny * GB_TX; i += blockDim.x) {
+      int ry = i / GB_TX, x = i - ry * GB_TX;
+      float re = 0.f, im = 0.f;
+      for (int u = 0; u < K; ++u) {
+        float p = sIn[ry][x + u];
+        re += t.hx_re[k][u] * p;
+        im += t.hx_im[k][u] * p;
+      }
+      sHr[ry][x] = re;
+      sHi[ry][x] = im;
+    }
+    __syncthreads();
+    float* __restrict__ out = a.out[k][l];
+    for (int i = threadIdx.x; i < GB_TY * GB_TX; i += blockDim.x) {
+      int y = i / GB_TX, x = i - y * GB_TX;
+      int oy = Y0 + y, ox = X0 + x;
+      if (oy >= h || ox >= w) continue;
+      float re = 0.f, im = 0.f, dc = 0.f;
+      for (int v = 0; v < K; ++v) {
+        float hr = sHr[y + v][x], hi = sHi[y + v][x];
+        re += t.vy_re[k][v] * hr - t.vy_im[k][v] * hi;
+        im += t.vy_re[k][v] * hi + t.vy_im[k][v] * hr;
+        dc += t.g0[v] * sH0[y + v][x];
+      }
+      re -= t.kap_re[k] * dc;
+      im -= t.kap_im[k] * dc;
+      out[(size_t)oy * w + ox] = sqrtf(re * re + im * im);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ center-surround
+struct CSArgs {
+  const float* X[3 + SEG_MAX_ORIENT][SEG_MAX_LEVELS];  // channel planes per level
+  int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
+  int pair_c[SEG_MAX_PAIRS], pair_s[SEG_MAX_PAIRS];
+  int pair_band_off[SEG_MAX_PAIRS + 1];  // prefix of (row bands x channels) per pair
+  int npairs, nch, tile, opp_sum;
+  unsigned* mm;
+  float* tpart;
+  const float* nab;
+};
+
+__device__ __forceinline__ float cs_value(const CSArgs& a, int f, int c, int s, int y, int x) {
+  const float* cen = a.X[f][c];
+  float u = seg_bilinear(a.X[f][s], a.hl[s], a.wl[s], y, x, a.hl[c], a.wl[c]);
+  float v = cen[y * a.wl[c] + x];
+  return (a.opp_sum && (f == 1 || f == 2)) ? fabsf(v + u) : fabsf(v - u);
+}
+
+#define CS_MAX_TILES_X 1024
+
+// Per (map, band of `tile` rows): min, max and the sum of the band's T x T tile
+// maxima (Sec. 7.2 step 3: block-wise extrema).  Maps are non-negative, so the
+// float bit patterns order like the values.
+__global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
+  __shared__ unsigned sTmax[CS_MAX_TILES_X];
+  __shared__ float sMin[8], sMax[8];
+  int b = blockIdx.x, p = 0;
+  while (p < a.npairs - 1 && b >= a.pair_band_off[p + 1]) ++p;
+  int c = a.pair_c[p], s = a.pair_s[p];
+  int hc = a.hl[c], wc = a.wl[c], T = a.tile;
+  int nb = (hc + T - 1) / T, ntx = (wc + T - 1) / T;
+  int local = b - a.pair_band_off[p];
+  int f = local / nb, band = local - f * nb;
+  int m = p * a.nch + f;
+  for (int i = threadIdx.x; i < ntx; i += blockDim.x) sTmax[i] = 0u;
+  __syncthreads();
+  int y0 = band * T, rows = min(T, hc - y0);
+  float mn = 3.0e38f, mx = 0.f;
+  for (int i = threadIdx.x; i < rows * wc; i += blockDim.x) {
+    int y = y0 + i / wc, x = i % wc;
+    float v = cs_value(a, f, c, s, y, x);
+    mn = fminf(mn, v);
+    mx = fmaxf(mx, v);
+    atomicMax(&sTmax[x / T], __float_as_uint(v));
+  }
+  mn = seg_warp_min_f(mn);
+  mx = seg_warp_max_f(mx);
+  if ((threadIdx.x & 31) == 0) {
+    sMin[threadIdx.x >> 5] = mn;
+    sMax[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int nw = blockDim.x >> 5;
+    float a0 = threadIdx.x < nw ? sMin[threadIdx.x] : 3.0e38f;
+    float a1 = threadIdx.x < nw ? sMax[threadIdx.x] : 0.f;
+    float ts = 0.f;
+    for (int i = threadIdx.x; i < ntx; i += 32) ts += __uint_as_float(sTmax[i]);
+    a0 = seg_warp_min_f(a0);
+    a1 = seg_warp_max_f(a1);
+    ts = seg_warp_sum_f(ts);
+    if (threadIdx.x == 0) {
+      atomicMin(&a.mm[2 * m], __float_as_uint(a0));
+      atomicMax(&a.mm[2 * m + 1], __float_as_uint(a1));
+      a.tpart[b] = ts;
+    }
+  }
+}
+
+// N(v) = a v + b with a = (1 - mbar)^2 / (max - min), b = -min a, where mbar is
+// the mean of the tile maxima of the rescaled map without one copy of its
+// maximum 1; a flat map (range <= flat) gives a = b = 0.
+__device__ __forceinline__ void norm_affine(double mn, double mx, double sum_tmax, int nt,
+                                            double flat, float* ab) {
+  double range = mx - mn;
+  if (!(range > flat)) {
+    ab[0] = 0.f;
+    ab[1] = 0.f;
+    return;
+  }
+  double st = (sum_tmax - nt * mn) / range;
+  double mbar = nt > 1 ? (st - 1.0) / (nt - 1) : 0.0;
+  double a = (1.0 - mbar) * (1.0 - mbar) / range;
+  ab[0] = (float)a;
+  ab[1] = (float)(-mn * a);
+}
+
+__global__ void k_cs_norm(CSArgs a, float flat, float* nab) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.npairs * a.nch) return;
+  int p = m / a.nch, f = m - p * a.nch;
+  int c = a.pair_c[p];
+  int T = a.tile, nb = (a.hl[c] + T - 1) / T, ntx = (a.wl[c] + T - 1) / T;
+  double sum = 0.0;
+  const float* tp = a.tpart + a.pair_band_off[p] + f * nb;
+  for (int i = 0; i < nb; ++i) sum += tp[i];
+  norm_affine(__uint_as_float(a.mm[2 * m]), __uint_as_float(a.mm[2 * m + 1]), sum, nb * ntx, flat,
+              nab + 2 * m);
+}
+
+// B_c(f) = sum over pairs (c, s) of N(CS_f(c, s)) + REDUCE(B_{c-1}(f)).
+__global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* __restrict__ prev,
+                                                  int hp, int wp, float* __restrict__ out) {
+  int f = blockIdx.z;
+  int hc = a.hl[c], wc = a.wl[c];
+  int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= wc || y >= hc) return;
+  float acc = 0.f;
+  for (int p = 0; p < a.npairs; ++p) {
+    if (a.pair_c[p] != c) continue;
+    int m = p * a.nch + f;
+    acc += a.nab[2 * m] * cs_value(a, f, c, a.pair_s[p], y, x) + a.nab[2 * m + 1];
+  }
+  if (prev) {
+    const float* pl = prev + (size_t)f * hp * wp;
+    float r = 0.f;
+    for (int j = 0; j < 5; ++j) {
+      const float* row = pl + (size_t)seg_clampi(2 * y + j - 2, 0, hp - 1) * wp;
+      float hsum = 0.f;
+      for (int i = 0; i < 5; ++i) hsum += c_binom[i] * row[seg_clampi(2 * x + i - 2, 0, wp - 1)];
+      r += c_binom[j] * hsum;
+    }
+    acc += r;
+  }
+  out[(size_t)f * hc * wc + (size_t)y * wc + x] = acc;
+}
+
+// ------------------------------------------------------------------ conspicuity, S
+__device__ void block_norm_ab(const float* v, int h, int w, int T, float flat, float* ab_sh,
+                              double* red) {
+  int n = h * w;
+  float mn = 3.0e38f, mx = -3.0e38f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    mn = fminf(mn, v[i]);
+    mx = fmaxf(mx, v[i]);
+  }
+  int ntx = (w + T - 1) / T, nty = (h + T - 1) / T, nt = ntx * nty;
+  double ts = 0.0;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    int ty = t / ntx, tx = t - ty * ntx;
+    float m = -3.0e38f;
+    for (int y = ty * T; y < min(h, ty * T + T); ++y)
+      for (int x = tx * T; x < min(w, tx * T + T); ++x) m = fmaxf(m, v[y * w + x]);
+    ts += m;
+  }
+  mn = seg_warp_min_f(mn);
+  mx = seg_warp_max_f(mx);
+  ts = seg_warp_sum_d(ts);
+  int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[3 * wid] = mn;
+    red[3 * wid + 1] = mx;
+    red[3 * wid + 2] = ts;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = red[0], a1 = red[1], a2 = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      a0 = fmin(a0, red[3 * i]);
+      a1 = fmax(a1, red[3 * i + 1]);
+      a2 += red[3 * i + 2];
+    }
+    norm_affine(a0, a1, a2, nt, flat, ab_sh);
+  }
+  __syncthreads();
+}
+
+struct ConspArgs {
+  const float* acc;  // nch planes at sigma_S
+  int h, w, nch, tile;
+  float flat;
+  float wgt[4];
+  float* csum;
+  float* consp;
+  float* S;
+};
+
+__global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
+  __shared__ float ab[2];
+  __shared__ double red[3 * 32];
+  int n = a.h * a.w;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.csum[i] = 0.f;
+  for (int k = 3; k < a.nch; ++k) {
+    const float* v = a.acc + (size_t)k * n;
+    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a.csum[i] += ab[0] * v[i] + ab[1];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.S[i] = 0.f;
+  for (int k = 0; k < 4; ++k) {
+    const float* v = k < 3 ? a.acc + (size_t)k * n : a.csum;
+    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float nv = ab[0] * v[i] + ab[1];
+      a.consp[(size_t)k * n + i] = nv;
+      a.S[i] += a.wgt[k] * nv;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, int hs, int ws, int H,
+                                                  int W, float* __restrict__ sal, unsigned* salmax) {
+  int x = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
+  float v = 0.f;
+  if (x < W && y < H) {
+    v = seg_bilinear(S, hs, ws, y, x, H, W);
+    sal[(size_t)y * W + x] = v;
+  }
+  v = seg_warp_max_f(fmaxf(v, 0.f));
+  if ((threadIdx.x & 31) == 0) atomicMax(salmax, __float_as_uint(v));
+}
+
+// ------------------------------------------------------------------ host side
+static void make_taps(const seg_params& p, GaborTaps& t) {
+  memset(&t, 0, sizeof(t));
+  int R = p.gabor_radius;
+  t.R = R;
+  t.no = p.n_orient;
+  double g[SEG_MAX_TAPS], sg = 0;
+  for (int u = -R; u <= R; ++u) {
+    g[u + R] = exp(-(double)(u * u) / (2.0 * p.gabor_sigma * p.gabor_sigma));
+    sg += g[u + R];
+  }
+  double w = 2.0 * M_PI / p.gabor_lambda;
+  for (int u = 0; u <= 2 * R; ++u) t.g0[u] = (float)(g[u] / sg);
+  for (int k = 0; k < p.n_orient; ++k) {
+    double th = k * M_PI / p.n_orient, cx = cos(th), sy = sin(th);
+    double hr = 0, hi = 0, vr = 0, vi = 0;
+    for (int u = -R; u <= R; ++u) {
+      double a = g[u + R] / sg;
+      double ar = a * cos(w * cx * u), ai = a * sin(w * cx * u);
+      double br = a * cos(w * sy * u), bi = a * sin(w * sy * u);
+      t.hx_re[k][u + R] = (float)ar;
+      t.hx_im[k][u + R] = (float)ai;
+      t.vy_re[k][u + R] = (float)br;
+      t.vy_im[k][u + R] = (float)bi;
+      hr += ar;
+      hi += ai;
+      vr += br;
+      vi += bi;
+    }
+    t.kap_re[k] = (float)(hr * vr - hi * vi);
+    t.kap_im[k] = (float)(hr * vi + hi * vr);
+  }
+}
+
+int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes) {
+  memset(&s, 0, sizeof(s));
+  s.H = H;
+  s.W = W;
+  s.L = p.levels;
+  s.c_min = p.c_min;
+  s.c_max = p.c_max;
+  s.d_min = p.d_min;
+  s.d_max = p.d_max;
+  s.no = p.n_orient;
+  s.s_max = p.c_max + p.d_max;
+  s.sS = p.c_max;
+  s.tile = p.norm_tile;
+  s.flat = p.norm_flat;
+  s.opp_sum = p.cs_opponent_sum;
+  for (int k = 0; k < 4; ++k) s.w[k] = p.w[k];
+  for (int l = 0; l < s.L; ++l) {
+    s.hl[l] = seg_level_dim(H, l);
+    s.wl[l] = seg_level_dim(W, l);
+  }
+  s.nch = 3 + s.no;
+  s.npairs = 0;
+  for (int c = s.c_min; c <= s.c_max; ++c)
+    for (int d = s.d_min; d <= s.d_max; ++d) {
+      if (s.npairs >= SEG_MAX_PAIRS) return SEG_EINVAL;
+      s.pair_c[s.npairs] = c;
+      s.pair_s[s.npairs] = c + d;
+      s.npairs++;
+    }
+  s.nmaps = s.npairs * s.nch;
+  s.nbands_total = 0;
+  for (int i = 0; i < s.npairs; ++i) {
+    int c = s.pair_c[i];
+    if ((s.wl[c] + s.tile - 1) / s.tile > CS_MAX_TILES_X) return SEG_EINVAL;
+    s.nbands_total += s.nch * ((s.hl[c] + s.tile - 1) / s.tile);
+  }
+  make_taps(p, s.taps);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += seg_align(b);
+    return o;
+  };
+  // record offsets in the pointer fields (bound later)
+  for (int ch = 0; ch < 3; ++ch)
+    for (int l = 1; l < s.L; ++l) s.pyr[ch][l] = (float*)take(sizeof(float) * s.hl[l] * s.wl[l]);
+  for (int k = 0; k < s.no; ++k)
+    for (int l = s.c_min; l <= s.s_max; ++l) s.ori[k][l] = (float*)take(sizeof(float) * s.hl[l] * s.wl[l]);
+  s.mm = (unsigned*)take(sizeof(unsigned) * 2 * s.nmaps);
+  s.tpart = (float*)take(sizeof(float) * s.nbands_total);
+  s.nab = (float*)take(sizeof(float) * 2 * s.nmaps);
+  size_t big = (size_t)s.hl[s.c_min] * s.wl[s.c_min] * s.nch;
+  s.acc[0] = (float*)take(sizeof(float) * big);
+  s.acc[1] = (float*)take(sizeof(float) * big);
+  size_t nS = (size_t)s.hl[s.sS] * s.wl[s.sS];
+  s.consp = (float*)take(sizeof(float) * 4 * nS);
+  s.csum = (float*)take(sizeof(float) * nS);
+  s.S = (float*)take(sizeof(float) * nS);
+  s.salmax = (unsigned*)take(sizeof(unsigned));
+  s.smax = (int*)take(sizeof(int));
+  *bytes = off;
+  return SEG_OK;
+}
+
+void sal_bind(SalWS& s, char* base) {
+  auto fix = [&](auto*& ptr) {
+    using T = std::remove_reference_t<decltype(ptr)>;
+    ptr = (T)(base + (size_t)ptr);
+  };
+  for (int ch = 0; ch < 3; ++ch)
+    for (int l = 1; l < s.L; ++l) fix(s.pyr[ch][l]);
+  for (int k = 0; k < s.no; ++k)
+    for (int l = s.c_min; l <= s.s_max; ++l) fix(s.ori[k][l]);
+  fix(s.mm);
+  fix(s.tpart);
+  fix(s.nab);
+  fix(s.acc[0]);
+  fix(s.acc[1]);
+  fix(s.consp);
+  fix(s.csum);
+  fix(s.S);
+  fix(s.salmax);
+  fix(s.smax);
+}
+
+static void fill_cs_args(const SalWS& s, CSArgs& a) {
+  memset(&a, 0, sizeof(a));
+  for (int l = 0; l < s.L; ++l) {
+    a.hl[l] = s.hl[l];
+    a.wl[l] = s.wl[l];
+    for (int ch = 0; ch < 3; ++ch) a.X[ch][l] = l >= 1 ? s.pyr[ch][l] : nullptr;
+    for (int k = 0; k < s.no; ++k) a.X[3 + k][l] = (l >= s.c_min && l <= s.s_max) ? s.ori[k][l] : nullptr;
+  }
+  a.npairs = s.npairs;
+  a.nch = s.nch;
+  a.tile = s.tile;
+  a.opp_sum = s.opp_sum;
+  int off = 0;
+  for (int i = 0; i < s.npairs; ++i) {
+    a.pair_c[i] = s.pair_c[i];
+    a.pair_s[i] = s.pair_s[i];
+    a.pair_band_off[i] = off;
+    off += s.nch * ((s.hl[s.pair_c[i]] + s.tile - 1) / s.tile);
+  }
+  a.pair_band_off[s.npairs] = off;
+  a.mm = s.mm;
+  a.tpart = s.tpart;
+  a.nab = s.nab;
+}
+
+int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
+  SalWS& s = c->sal;
+  cudaStream_t st = c->stream;
+  const int H = s.H, W = s.W, N = H * W;
+  SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, sizeof(int), st));
+  SEG_CUDA_TRY(cudaMemsetAsync(s.salmax, 0, sizeof(unsigned), st));
+  int nb = min((N + 255) / 256, 148 * 8);
+  nb = max(nb, (s.nmaps + 255) / 256);
+  k_rgb_max<<<nb, 256, 0, st>>>(rgb, N, s.smax, s.mm, s.nmaps);
+  dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY);
+  k_feat_reduce1<<<g1, 256, 0, st>>>(rgb, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1], s.hl[1],
+                                     s.wl[1]);
+  for (int l = 1; l + 1 < s.L; ++l) {
+    Reduce3Args ra;
+    for (int ch = 0; ch < 3; ++ch) {
+      ra.in[ch] = s.pyr[ch][l];
+      ra.out[ch] = s.pyr[ch][l + 1];
+    }
+    ra.h = s.hl[l];
+    ra.w = s.wl[l];
+    ra.h2 = s.hl[l + 1];
+    ra.w2 = s.wl[l + 1];
+    dim3 g((ra.w2 + RED_TX - 1) / RED_TX, (ra.h2 + RED_TY - 1) / RED_TY, 3);
+    k_reduce3<<<g, 256, 0, st>>>(ra);
+  }
+  GaborArgs ga;
+  memset(&ga, 0, sizeof(ga));
+  ga.lvl_first = s.c_min;
+  ga.lvl_last = s.s_max;
+  int tot = 0;
+  for (int l = s.c_min; l <= s.s_max; ++l) {
+    ga.in[l] = s.pyr[0][l];
+    ga.hl[l] = s.hl[l];
+    ga.wl[l] = s.wl[l];
+    for (int k = 0; k < s.no; ++k) ga.out[k][l] = s.ori[k][l];
+    ga.blk_off[l - s.c_min] = tot;
+    tot += ((s.wl[l] + GB_TX - 1) / GB_TX) * ((s.hl[l] + GB_TY - 1) / GB_TY);
+  }
+  ga.blk_off[s.s_max - s.c_min + 1] = tot;
+  k_gabor<<<tot, 256, 0, st>>>(ga, s.taps);
+  CSArgs ca;
+  fill_cs_args(s, ca);
+  k_cs_stats<<<s.nbands_total, 256, 0, st>>>(ca);
+  k_cs_norm<<<(s.nmaps + 127) / 128, 128, 0, st>>>(ca, s.flat, s.nab);
+  int cur = 0;
+  const float* prev = nullptr;
+  int hp = 0, wp = 0;
+  for (int cc = s.c_min; cc <= s.c_max; ++cc) {
+    dim3 g((s.wl[cc] + 31) / 32, (s.hl[cc] + 7) / 8, s.nch);
+    k_cs_accum<<<g, 256, 0, st>>>(ca, cc, prev, hp, wp, s.acc[cur]);
+    prev = s.acc[cur];
+    hp = s.hl[cc];
+    wp = s.wl[cc];
+    cur ^= 1;
+  }
+  ConspArgs pa;
+  pa.acc = prev;
+  pa.h = s.hl[s.sS];
+  pa.w = s.wl[s.sS];
+  pa.nch = s.nch;
+  pa.tile = s.tile;
+  pa.flat = s.flat;
+  for (int k = 0; k < 4; ++k) pa.wgt[k] = s.w[k];
+  pa.csum = s.csum;
+  pa.consp = s.consp;
+  pa.S = s.S;
+  k_consp<<<1, 1024, 0, st>>>(pa);
+  dim3 gu((W + 63) / 64, (H + 3) / 4);
+  k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, s.salmax);
+  SEG_CUDA_TRY(cudaGetLastError());
+  return SEG_OK;
+}

@@ -1,0 +1,351 @@
+// seg_api.cu -- the extern "C" entry points declared in include/seg.h.
+//
+// A context owns one device arena, carved into the saliency workspace, the
+// prior/terms buffers and the min-cut state at creation; no entry point below
+// allocates device memory except seg_create and the standalone
+// seg_mincut_grid.
+#include <stdlib.h>
+#include <string.h>
+
+#include "seg_internal.cuh"
+
+extern "C" int seg_level_dim(int n, int level) {
+  for (int l = 0; l < level; ++l) n = (n + 1) / 2;
+  return n;
+}
+
+extern "C" int seg_default_params(seg_params* p) {
+  if (!p) return SEG_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->levels = 9;
+  p->c_min = 2;
+  p->c_max = 4;
+  p->d_min = 3;
+  p->d_max = 4;
+  p->n_orient = 4;
+  p->gabor_lambda = 4.0f;
+  p->gabor_sigma = 2.0f;
+  p->gabor_radius = 6;
+  p->norm_tile = 8;
+  p->norm_flat = 1e-5f;
+  p->w[0] = 1.0f / 3.0f;
+  p->w[1] = 1.0f / 6.0f;
+  p->w[2] = 1.0f / 6.0f;
+  p->w[3] = 1.0f / 3.0f;
+  p->cs_opponent_sum = 1;
+  p->border_px = 1;
+  p->sigma1 = 0.03;
+  p->sigma2 = 0.035;
+  p->f_sigma = 2.0f;
+  p->f_radius = 6;
+  p->eps = 1e-4f;
+  p->lambda_u = 1.0;
+  p->lambda_p = 0.0;
+  p->lambda_s = 1.5;
+  p->sigma_I = 0.05;
+  p->cap_scale = 1000.0;
+  p->neighbourhood = 8;
+  p->max_cycles = 20000;
+  p->global_relabel_every = 4;
+  p->local_iters = 16;
+  return SEG_OK;
+}
+
+extern "C" const char* seg_strerror(int code) {
+  switch (code) {
+    case SEG_OK: return "ok";
+    case SEG_EINVAL: return "invalid argument";
+    case SEG_ENOMEM: return "device memory allocation failed";
+    case SEG_ENOTCONVERGED: return "min-cut did not converge within max_cycles";
+    case SEG_ECUDA: return "CUDA runtime error";
+    case SEG_ETIMEOUT: return "device-side wait timed out";
+    case SEG_ECAPACITY: return "capacity outside [0, 2^24]";
+    default: return "unknown error";
+  }
+}
+
+static int check_params(const seg_params* p, int H, int W) {
+  if (!p) return SEG_EINVAL;
+  if (H < 1 || W < 1 || (long long)H * W > (1LL << 26)) return SEG_EINVAL;
+  if (p->levels < 2 || p->levels > SEG_MAX_LEVELS) return SEG_EINVAL;
+  if (p->c_min < 1 || p->c_max < p->c_min || p->d_min < 1 || p->d_max < p->d_min) return SEG_EINVAL;
+  if (p->c_max + p->d_max > p->levels - 1) return SEG_EINVAL;
+  if ((p->c_max - p->c_min + 1) * (p->d_max - p->d_min + 1) > SEG_MAX_PAIRS) return SEG_EINVAL;
+  if (p->n_orient < 1 || p->n_orient > SEG_MAX_ORIENT) return SEG_EINVAL;
+  if (p->gabor_radius < 0 || p->gabor_radius > 8 || !(p->gabor_sigma > 0) || !(p->gabor_lambda > 0))
+    return SEG_EINVAL;
+  if (p->f_radius < 0 || p->f_radius > 8 || !(p->f_sigma > 0)) return SEG_EINVAL;
+  if (p->norm_tile < 1 || p->border_px < 0) return SEG_EINVAL;
+  if (p->neighbourhood != 4 && p->neighbourhood != 8) return SEG_EINVAL;
+  if (!(p->sigma1 >= 0) || !(p->sigma2 >= 0) || !(p->sigma_I > 0) || !(p->cap_scale > 0)) return SEG_EINVAL;
+  if (!(p->eps > 0) || !(p->eps < 0.5f)) return SEG_EINVAL;
+  if (p->max_cycles < 1 || p->global_relabel_every < 1 || p->local_iters < 1) return SEG_EINVAL;
+  return SEG_OK;
+}
+
+extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out) {
+  if (!out) return SEG_EINVAL;
+  *out = nullptr;
+  int rc = check_params(p, H, W);
+  if (rc) return rc;
+  seg_ctx* c = (seg_ctx*)calloc(1, sizeof(seg_ctx));
+  if (!c) return SEG_ENOMEM;
+  c->stream = (cudaStream_t)stream;
+  c->H = H;
+  c->W = W;
+  c->N = H * W;
+  c->p = *p;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    free(c);
+    return SEG_ECUDA;
+  }
+  size_t sal_bytes = 0;
+  rc = sal_layout(c->sal, H, W, *p, &sal_bytes);
+  if (rc) {
+    free(c);
+    return rc;
+  }
+  const size_t N = (size_t)c->N;
+  const int nk = p->neighbourhood / 2;
+  c->mom_blocks = pt_mom_blocks(H, W);
+  size_t off = seg_align(sal_bytes);
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += seg_align(b);
+    return o;
+  };
+  size_t o_kal = take(sizeof(KalmanDev)), o_gauss = take(sizeof(GaussDev));
+  size_t o_mom = take(sizeof(double) * 12 * c->mom_blocks), o_lut = take(sizeof(int) * 766 * 2);
+  size_t o_prev = take(N), o_cs = take(4 * N), o_ct = take(4 * N), o_ncap = take(4 * N * nk);
+  size_t o_sal = take(4 * N), o_prior = take(4 * N), o_mask = take(N), o_cut = take(8);
+  size_t o_rgb = take(3 * N), o_status = take(16);
+  size_t o_mf = take(mf_bytes(H, W, p->neighbourhood));
+  char* base = nullptr;
+  if (cudaMalloc((void**)&base, off) != cudaSuccess) {
+    free(c);
+    return SEG_ENOMEM;
+  }
+  c->arena = base;
+  sal_bind(c->sal, base);
+  c->kal = (KalmanDev*)(base + o_kal);
+  c->gauss = (GaussDev*)(base + o_gauss);
+  c->mom_part = (double*)(base + o_mom);
+  c->lut = (int*)(base + o_lut);
+  c->prev_mask = (uint8_t*)(base + o_prev);
+  c->cs = (int32_t*)(base + o_cs);
+  c->ct = (int32_t*)(base + o_ct);
+  c->ncap = (int32_t*)(base + o_ncap);
+  c->sal_buf = (float*)(base + o_sal);
+  c->prior_buf = (float*)(base + o_prior);
+  c->mask_buf = (uint8_t*)(base + o_mask);
+  c->cut_buf = (int64_t*)(base + o_cut);
+  c->rgb_stage = (uint8_t*)(base + o_rgb);
+  c->status = (int*)(base + o_status);
+  mf_bind(c->mf, base + o_mf, H, W, p->neighbourhood);
+  int* lut = (int*)malloc(sizeof(int) * 766 * 2);
+  pt_fill_lut(*p, lut);
+  bool ok = cudaMemcpy(c->lut, lut, sizeof(int) * 766 * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+  free(lut);
+  ok = ok && cudaMemset(c->kal, 0, sizeof(KalmanDev)) == cudaSuccess;
+  ok = ok && cudaMemset(c->prev_mask, 0, N) == cudaSuccess;
+  ok = ok && cudaMemset(c->status, 0, 16) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&c->status_host, 16) == cudaSuccess;
+  ok = ok && mf_grid_size(H, W, &c->mf_grid) == SEG_OK;
+  if (!ok) {
+    if (c->status_host) cudaFreeHost(c->status_host);
+    cudaFree(base);
+    free(c);
+    return SEG_ECUDA;
+  }
+  *out = c;
+  return SEG_OK;
+}
+
+extern "C" int seg_destroy(seg_ctx* c) {
+  if (!c) return SEG_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->arena);
+  cudaFreeHost(c->status_host);
+  free(c);
+  return SEG_OK;
+}
+
+extern "C" int seg_reset(seg_ctx* c) {
+  if (!c) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, sizeof(KalmanDev), c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask, 0, c->N, c->stream));
+  return SEG_OK;
+}
+
+static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
+                      uint8_t* mask, uint8_t* mask_state, int64_t* cut) {
+  return mf_launch(c->stream, c->mf, c->mf_grid, c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
+                   mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
+                   c->p.global_relabel_every, c->p.local_iters);
+}
+
+extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float* prior, uint8_t* mask,
+                              int64_t* cut) {
+  if (!c || !rgb || !mask) return SEG_EINVAL;
+  float* s = sal ? sal : c->sal_buf;
+  float* pr = prior ? prior : c->prior_buf;
+  int rc = sal_launch(c, rgb, s);
+  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr);
+  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 1, c->cs, c->ct, c->ncap);
+  if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
+  return rc;
+}
+
+extern "C" int seg_sync(seg_ctx* c, int* cycles) {
+  if (!c) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  SEG_CUDA_TRY(cudaMemcpy(c->status_host, c->status, 16, cudaMemcpyDeviceToHost));
+  if (cycles) *cycles = c->status_host[1];
+  int code = c->status_host[0];
+  if (code) SEG_CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
+  return code;
+}
+
+extern "C" int seg_push_frame_host(seg_ctx* c, const uint8_t* rgb_host, float* sal_host,
+                                   float* prior_host, uint8_t* mask_host, int64_t* cut_host) {
+  if (!c || !rgb_host || !mask_host) return SEG_EINVAL;
+  cudaStream_t st = c->stream;
+  size_t N = c->N;
+  SEG_CUDA_TRY(cudaMemcpyAsync(c->rgb_stage, rgb_host, 3 * N, cudaMemcpyHostToDevice, st));
+  int rc = seg_push_frame(c, c->rgb_stage, c->sal_buf, c->prior_buf, c->mask_buf, c->cut_buf);
+  if (rc) return rc;
+  SEG_CUDA_TRY(cudaMemcpyAsync(mask_host, c->mask_buf, N, cudaMemcpyDeviceToHost, st));
+  if (cut_host) SEG_CUDA_TRY(cudaMemcpyAsync(cut_host, c->cut_buf, 8, cudaMemcpyDeviceToHost, st));
+  if (sal_host) SEG_CUDA_TRY(cudaMemcpyAsync(sal_host, c->sal_buf, 4 * N, cudaMemcpyDeviceToHost, st));
+  if (prior_host)
+    SEG_CUDA_TRY(cudaMemcpyAsync(prior_host, c->prior_buf, 4 * N, cudaMemcpyDeviceToHost, st));
+  return seg_sync(c, nullptr);
+}
+
+#define SEG_STATE_MAGIC 0x53454731u  // "SEG1"
+
+extern "C" int seg_get_state(seg_ctx* c, void* buf, size_t* n) {
+  if (!c || !n) return SEG_EINVAL;
+  size_t need = 24 + (size_t)c->N;
+  if (!buf) {
+    *n = need;
+    return SEG_OK;
+  }
+  if (*n < need) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  KalmanDev k;
+  SEG_CUDA_TRY(cudaMemcpy(&k, c->kal, sizeof(k), cudaMemcpyDeviceToHost));
+  char* b = (char*)buf;
+  uint32_t hdr[4] = {SEG_STATE_MAGIC, (uint32_t)c->H, (uint32_t)c->W, (uint32_t)k.t};
+  memcpy(b, hdr, 16);
+  memcpy(b + 16, &k.P, 8);
+  SEG_CUDA_TRY(cudaMemcpy(b + 24, c->prev_mask, c->N, cudaMemcpyDeviceToHost));
+  *n = need;
+  return SEG_OK;
+}
+
+extern "C" int seg_set_state(seg_ctx* c, const void* buf, size_t n) {
+  if (!c || !buf || n != 24 + (size_t)c->N) return SEG_EINVAL;
+  const char* b = (const char*)buf;
+  uint32_t hdr[4];
+  memcpy(hdr, b, 16);
+  if (hdr[0] != SEG_STATE_MAGIC || hdr[1] != (uint32_t)c->H || hdr[2] != (uint32_t)c->W) return SEG_EINVAL;
+  KalmanDev k;
+  memset(&k, 0, sizeof(k));
+  k.t = (int)hdr[3];
+  memcpy(&k.P, b + 16, 8);
+  SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  SEG_CUDA_TRY(cudaMemcpy(c->kal, &k, sizeof(k), cudaMemcpyHostToDevice));
+  SEG_CUDA_TRY(cudaMemcpy(c->prev_mask, b + 24, c->N, cudaMemcpyHostToDevice));
+  return SEG_OK;
+}
+
+extern "C" int seg_saliency(seg_ctx* c, const uint8_t* rgb, float* sal) {
+  if (!c || !rgb || !sal) return SEG_EINVAL;
+  return sal_launch(c, rgb, sal);
+}
+
+extern "C" int seg_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, double w_f,
+                         float* prior) {
+  if (!c || !sal || !prior || !(w_f >= 0.0 && w_f <= 1.0)) return SEG_EINVAL;
+  if (w_f != 0.0 && !prev_mask) return SEG_EINVAL;
+  int rc = pt_launch_salmax(c, sal);  // q = saliency / max(saliency) of THIS map
+  return rc ? rc : pt_launch_prior(c, sal, prev_mask, 0, w_f, prior);
+}
+
+extern "C" int seg_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct,
+                         int32_t* ncap) {
+  if (!c || !rgb || !prior || !cs || !ct || !ncap) return SEG_EINVAL;
+  return pt_launch_moments_terms(c, rgb, prior, 0, cs, ct, ncap);
+}
+
+extern "C" int seg_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
+                          uint8_t* mask, int64_t* cut) {
+  if (!c || !cs || !ct || !ncap || !mask) return SEG_EINVAL;
+  return run_mincut(c, cs, ct, ncap, mask, nullptr, cut);
+}
+
+extern "C" int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_t* cs, const int32_t* ct,
+                               const int32_t* ncap, uint8_t* mask, int64_t* cut, int max_cycles,
+                               int* cycles) {
+  if (H < 1 || W < 1 || (long long)H * W > (1LL << 26) || (nbr != 4 && nbr != 8)) return SEG_EINVAL;
+  if (!cs || !ct || !ncap || !mask) return SEG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  seg_params d;
+  seg_default_params(&d);
+  int grid = 0;
+  int rc = mf_grid_size(H, W, &grid);
+  if (rc) return rc;
+  size_t mfb = mf_bytes(H, W, nbr);
+  char* base = nullptr;
+  if (cudaMalloc((void**)&base, mfb + 256 + 256) != cudaSuccess) return SEG_ENOMEM;
+  MFWS m;
+  mf_bind(m, base, H, W, nbr);
+  int* status = (int*)(base + seg_align(mfb));
+  long long* cut_tmp = (long long*)(base + seg_align(mfb) + 128);
+  rc = SEG_OK;
+  if (cudaMemsetAsync(status, 0, 16, st) != cudaSuccess) rc = SEG_ECUDA;
+  if (!rc)
+    rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, cut ? (long long*)cut : cut_tmp,
+                   status, max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every,
+                   d.local_iters);
+  int hs[4] = {0, 0, 0, 0};
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = SEG_ECUDA;
+  if (!rc && cudaMemcpy(hs, status, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SEG_ECUDA;
+  cudaFree(base);
+  if (rc) return rc;
+  if (cycles) *cycles = hs[1];
+  return hs[0];
+}
+
+extern "C" int seg_debug_copy(seg_ctx* c, int which, int index, float* dst, size_t n) {
+  if (!c || !dst) return SEG_EINVAL;
+  const SalWS& s = c->sal;
+  const float* src = nullptr;
+  size_t cnt = 0;
+  int sS = s.sS;
+  if (which == 0) {
+    int ch = index / 16, l = index % 16;
+    if (ch < 0 || ch > 2 || l < 1 || l >= s.L) return SEG_EINVAL;
+    src = s.pyr[ch][l];
+    cnt = (size_t)s.hl[l] * s.wl[l];
+  } else if (which == 1) {
+    int k = index / 16, l = index % 16;
+    if (k < 0 || k >= s.no || l < s.c_min || l > s.s_max) return SEG_EINVAL;
+    src = s.ori[k][l];
+    cnt = (size_t)s.hl[l] * s.wl[l];
+  } else if (which == 2) {
+    if (index < 0 || index > 3) return SEG_EINVAL;
+    cnt = (size_t)s.hl[sS] * s.wl[sS];
+    src = s.consp + index * cnt;
+  } else if (which == 3) {
+    src = s.S;
+    cnt = (size_t)s.hl[sS] * s.wl[sS];
+  } else {
+    return SEG_EINVAL;
+  }
+  if (n != cnt) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  SEG_CUDA_TRY(cudaMemcpy(dst, src, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+  return SEG_OK;
+}

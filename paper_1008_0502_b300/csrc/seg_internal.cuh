@@ -129,6 +129,7 @@ struct KalmanDev {
 
 struct GaussDev {
   double mu[2][3];
+  double sw[2];      // total prior weight per label
   float muf[2][3];
   float linv[2][6];  // lower-triangular inverse Cholesky factor: l00 l10 l11 l20 l21 l22
   float lconst[2];   // 1/2 log det + 3/2 log 2 pi
@@ -211,6 +212,7 @@ void sal_bind(SalWS& s, char* base);
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);
 
 int pt_mom_blocks(int H, int W);
+int pt_launch_salmax(seg_ctx* c, const float* sal);
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
                     double wf_host, float* prior);
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int advance_kalman,
