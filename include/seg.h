@@ -170,6 +170,21 @@ int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_t* cs_dev,
  * Synchronises the stream.  Errors: SEG_EINVAL (unknown map or wrong n). */
 int seg_debug_copy(seg_ctx* ctx, int which, int index, float* dst_host, size_t n);
 
+/* Per-stage device timing of seg_push_frame (measurement support; the paper
+ * reports per-stage times in Table 5).  seg_profile_enable(ctx, 1) starts a
+ * fresh record: every following seg_push_frame records CUDA events on the
+ * context's stream around its four stages (saliency, prior, terms, min cut)
+ * and stores the min-cut's cycle count; up to 4096 frames are kept (later
+ * frames are not recorded).  seg_profile_enable(ctx, 0) stops recording.
+ * seg_profile_read synchronises the stream and returns, over the recorded
+ * frames: stage_ms[4] summed stage times, *frames, *cycles summed min-cut
+ * cycles, and (if frame_ms is non-NULL) each frame's first-to-last event time
+ * in frame_ms[0 .. min(frames, max_frames)-1].  Errors: SEG_EINVAL, SEG_ENOMEM,
+ * SEG_ECUDA. */
+int seg_profile_enable(seg_ctx* ctx, int on);
+int seg_profile_read(seg_ctx* ctx, double* stage_ms, int* frames, long long* cycles, float* frame_ms,
+                     int max_frames);
+
 /* Size of pyramid level `level` along an n-pixel axis: ceil-halving. */
 int seg_level_dim(int n, int level);
 

@@ -9,6 +9,8 @@
 
 #include "seg_internal.cuh"
 
+static void prof_free(seg_ctx* c);
+
 extern "C" int seg_level_dim(int n, int level) {
   for (int l = 0; l < level; ++l) n = (n + 1) / 2;
   return n;
@@ -164,6 +166,7 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
 extern "C" int seg_destroy(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
   cudaStreamSynchronize(c->stream);
+  prof_free(c);
   cudaFree(c->arena);
   cudaFreeHost(c->status_host);
   free(c);
@@ -184,16 +187,96 @@ static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const in
                    c->p.global_relabel_every, c->p.local_iters);
 }
 
+static void prof_mark(seg_ctx* c, int k) {
+  if (c->prof_on && c->prof_n < c->prof_cap) cudaEventRecord(c->prof_ev[5 * c->prof_n + k], c->stream);
+}
+
 extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float* prior, uint8_t* mask,
                               int64_t* cut) {
   if (!c || !rgb || !mask) return SEG_EINVAL;
   float* s = sal ? sal : c->sal_buf;
   float* pr = prior ? prior : c->prior_buf;
+  prof_mark(c, 0);
   int rc = sal_launch(c, rgb, s);
+  prof_mark(c, 1);
   if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr);
+  prof_mark(c, 2);
   if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 1, c->cs, c->ct, c->ncap);
+  prof_mark(c, 3);
   if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
+  prof_mark(c, 4);
+  if (!rc && c->prof_on && c->prof_n < c->prof_cap) {
+    SEG_CUDA_TRY(cudaMemcpyAsync(c->prof_cycles + c->prof_n, c->status + 1, sizeof(int),
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    c->prof_n++;
+  }
   return rc;
+}
+
+static void prof_free(seg_ctx* c) {
+  if (c->prof_ev) {
+    for (int i = 0; i < 5 * c->prof_cap; ++i) cudaEventDestroy(c->prof_ev[i]);
+    free(c->prof_ev);
+    c->prof_ev = nullptr;
+  }
+  if (c->prof_cycles) cudaFree(c->prof_cycles);
+  c->prof_cycles = nullptr;
+  c->prof_cap = 0;
+}
+
+extern "C" int seg_profile_enable(seg_ctx* c, int on) {
+  if (!c) return SEG_EINVAL;
+  c->prof_on = 0;
+  c->prof_n = 0;
+  if (!on) return SEG_OK;
+  if (!c->prof_ev) {
+    const int cap = 4096;
+    c->prof_ev = (cudaEvent_t*)calloc(5 * cap, sizeof(cudaEvent_t));
+    if (!c->prof_ev) return SEG_ENOMEM;
+    c->prof_cap = cap;
+    for (int i = 0; i < 5 * cap; ++i)
+      if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) {
+        prof_free(c);
+        return SEG_ECUDA;
+      }
+    if (cudaMalloc((void**)&c->prof_cycles, sizeof(int) * cap) != cudaSuccess) {
+      prof_free(c);
+      return SEG_ENOMEM;
+    }
+  }
+  c->prof_on = 1;
+  return SEG_OK;
+}
+
+extern "C" int seg_profile_read(seg_ctx* c, double* stage_ms, int* frames, long long* cycles,
+                                float* frame_ms, int max_frames) {
+  if (!c || !stage_ms || !frames || !cycles) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 4; ++k) stage_ms[k] = 0.0;
+  *frames = c->prof_n;
+  *cycles = 0;
+  if (c->prof_n == 0) return SEG_OK;
+  int* cyc = (int*)malloc(sizeof(int) * c->prof_n);
+  if (!cyc) return SEG_ENOMEM;
+  if (cudaMemcpy(cyc, c->prof_cycles, sizeof(int) * c->prof_n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    free(cyc);
+    return SEG_ECUDA;
+  }
+  for (int f = 0; f < c->prof_n; ++f) {
+    *cycles += cyc[f];
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0.f;
+      SEG_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[5 * f + k], c->prof_ev[5 * f + k + 1]));
+      stage_ms[k] += ms;
+    }
+    if (frame_ms && f < max_frames) {
+      float ms = 0.f;
+      SEG_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[5 * f], c->prof_ev[5 * f + 4]));
+      frame_ms[f] = ms;
+    }
+  }
+  free(cyc);
+  return SEG_OK;
 }
 
 extern "C" int seg_sync(seg_ctx* c, int* cycles) {

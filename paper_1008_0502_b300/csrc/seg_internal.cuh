@@ -204,6 +204,10 @@ struct seg_ctx {
   int mf_grid;
   int* status;       // device [4]
   int* status_host;  // pinned [4]
+  // optional per-stage timing (seg_profile_enable)
+  int prof_on, prof_n, prof_cap;
+  cudaEvent_t* prof_ev;  // 5 per frame
+  int* prof_cycles;      // device [prof_cap]
 };
 
 // ---------------------------------------------------------------- launchers

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of include/seg.h (argument marshalling only).
+
+Every step of the path runs in the CUDA kernels of ``libseg.so``; this module
+only converts torch tensors to device pointers, calls the C entry points of the
+same names and turns negative return codes into :class:`SegError`.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the library
+is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libseg.so")
+
+SEG_OK = 0
+SEG_EINVAL = -1
+SEG_ENOMEM = -2
+SEG_ENOTCONVERGED = -3
+SEG_ECUDA = -4
+SEG_ETIMEOUT = -5
+SEG_ECAPACITY = -6
+
+
+class SegError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class seg_params(C.Structure):
+    _fields_ = [
+        ("levels", C.c_int32), ("c_min", C.c_int32), ("c_max", C.c_int32), ("d_min", C.c_int32),
+        ("d_max", C.c_int32), ("n_orient", C.c_int32), ("gabor_lambda", C.c_float),
+        ("gabor_sigma", C.c_float), ("gabor_radius", C.c_int32), ("norm_tile", C.c_int32),
+        ("norm_flat", C.c_float), ("w", C.c_float * 4), ("cs_opponent_sum", C.c_int32),
+        ("border_px", C.c_int32), ("sigma1", C.c_double), ("sigma2", C.c_double),
+        ("f_sigma", C.c_float), ("f_radius", C.c_int32), ("eps", C.c_float),
+        ("lambda_u", C.c_double), ("lambda_p", C.c_double), ("lambda_s", C.c_double),
+        ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int32),
+        ("max_cycles", C.c_int32), ("global_relabel_every", C.c_int32), ("local_iters", C.c_int32),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, P = C.c_void_p, C.c_int, C.POINTER
+    sig = {
+        "seg_default_params": ([P(seg_params)], i32),
+        "seg_create": ([vp, i32, i32, P(seg_params), P(vp)], i32),
+        "seg_destroy": ([vp], i32),
+        "seg_reset": ([vp], i32),
+        "seg_push_frame": ([vp, vp, vp, vp, vp, vp], i32),
+        "seg_push_frame_host": ([vp, vp, vp, vp, vp, vp], i32),
+        "seg_sync": ([vp, P(C.c_int)], i32),
+        "seg_get_state": ([vp, vp, P(C.c_size_t)], i32),
+        "seg_set_state": ([vp, vp, C.c_size_t], i32),
+        "seg_strerror": ([i32], C.c_char_p),
+        "seg_saliency": ([vp, vp, vp], i32),
+        "seg_prior": ([vp, vp, vp, C.c_double, vp], i32),
+        "seg_terms": ([vp, vp, vp, vp, vp, vp], i32),
+        "seg_mincut": ([vp, vp, vp, vp, vp, vp], i32),
+        "seg_mincut_grid": ([vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, P(C.c_int)], i32),
+        "seg_debug_copy": ([vp, i32, i32, vp, C.c_size_t], i32),
+        "seg_level_dim": ([i32, i32], i32),
+        "seg_profile_enable": ([vp, i32], i32),
+        "seg_profile_read": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, i32], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.seg_strerror(code).decode()
+
+
+def _check(code: int, where: str) -> int:
+    if code != SEG_OK:
+        raise SegError(code, where)
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, shape, name):
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def default_params(**over) -> seg_params:
+    p = seg_params()
+    _check(lib.seg_default_params(C.byref(p)), "seg_default_params")
+    for k, v in over.items():
+        if k == "w":
+            p.w = (C.c_float * 4)(*v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def params_from(cfg: dict, **over) -> seg_params:
+    """seg_params from a plain dict of field values (unknown keys are an error)."""
+    d = dict(cfg)
+    d.update(over)
+    return default_params(**d)
+
+
+def level_dim(n: int, level: int) -> int:
+    return lib.seg_level_dim(n, level)
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Segmenter:
+    """One video stream: owns a seg_ctx (workspace + temporal state) on a CUDA stream."""
+
+    def __init__(self, H: int, W: int, params: seg_params | None = None, stream=None, device=None):
+        self.H, self.W = H, W
+        self.device = torch.device(device) if device is not None else torch.device("cuda",
+                                                                                   torch.cuda.current_device())
+        self.params = params if params is not None else default_params()
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = C.c_void_p()
+            _check(lib.seg_create(_stream_handle(self.stream), H, W, C.byref(self.params), C.byref(h)),
+                   "seg_create")
+        self.handle = h
+        self.nk = self.params.neighbourhood // 2
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.seg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- buffers
+    def empty_outputs(self):
+        H, W, d = self.H, self.W, self.device
+        return (torch.empty(H, W, dtype=torch.float32, device=d), torch.empty(H, W, dtype=torch.float32, device=d),
+                torch.empty(H, W, dtype=torch.uint8, device=d), torch.empty(1, dtype=torch.int64, device=d))
+
+    # --- whole method
+    def push_frame(self, rgb, saliency=None, prior=None, mask=None, cut=None):
+        H, W = self.H, self.W
+        if mask is None:
+            saliency, prior, mask, cut = self.empty_outputs()
+        _check(lib.seg_push_frame(self.handle, _dev(rgb, torch.uint8, (H, W, 3), "rgb"),
+                                  _dev(saliency, torch.float32, (H, W), "saliency") if saliency is not None else None,
+                                  _dev(prior, torch.float32, (H, W), "prior") if prior is not None else None,
+                                  _dev(mask, torch.uint8, (H, W), "mask"),
+                                  _dev(cut, torch.int64, (1,), "cut") if cut is not None else None),
+               "seg_push_frame")
+        return saliency, prior, mask, cut
+
+    def push_frame_host(self, rgb_host, mask_host, cut_host=None, saliency_host=None, prior_host=None):
+        for t in (rgb_host, mask_host, cut_host, saliency_host, prior_host):
+            if t is not None and t.device.type != "cpu":
+                raise ValueError("push_frame_host takes host tensors")
+        return _check(lib.seg_push_frame_host(self.handle, _ptr(rgb_host), _ptr(saliency_host), _ptr(prior_host),
+                                              _ptr(mask_host), _ptr(cut_host)), "seg_push_frame_host")
+
+    def sync(self, check=True):
+        cyc = C.c_int(0)
+        code = lib.seg_sync(self.handle, C.byref(cyc))
+        if check:
+            _check(code, "seg_sync")
+        return code, cyc.value
+
+    def reset(self):
+        _check(lib.seg_reset(self.handle), "seg_reset")
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(lib.seg_get_state(self.handle, None, C.byref(n)), "seg_get_state")
+        buf = C.create_string_buffer(n.value)
+        _check(lib.seg_get_state(self.handle, buf, C.byref(n)), "seg_get_state")
+        return buf.raw
+
+    def set_state(self, state: bytes):
+        _check(lib.seg_set_state(self.handle, C.c_char_p(state), len(state)), "seg_set_state")
+
+    def profile_enable(self, on=True):
+        _check(lib.seg_profile_enable(self.handle, int(on)), "seg_profile_enable")
+
+    def profile_read(self, max_frames=4096):
+        ms = (C.c_double * 4)()
+        n = C.c_int(0)
+        cyc = C.c_longlong(0)
+        fr = (C.c_float * max_frames)()
+        _check(lib.seg_profile_read(self.handle, ms, C.byref(n), C.byref(cyc), fr, max_frames), "seg_profile_read")
+        k = min(n.value, max_frames)
+        return {"stage_ms": list(ms), "frames": n.value, "cycles": cyc.value, "frame_ms": list(fr[:k])}
+
+    # --- stage entry points
+    def saliency(self, rgb, out=None):
+        out = out if out is not None else torch.empty(self.H, self.W, dtype=torch.float32, device=self.device)
+        _check(lib.seg_saliency(self.handle, _dev(rgb, torch.uint8, (self.H, self.W, 3), "rgb"),
+                                _dev(out, torch.float32, (self.H, self.W), "saliency")), "seg_saliency")
+        return out
+
+    def prior(self, saliency, prev_mask, w_f, out=None):
+        out = out if out is not None else torch.empty(self.H, self.W, dtype=torch.float32, device=self.device)
+        pm = _dev(prev_mask, torch.uint8, (self.H, self.W), "prev_mask") if prev_mask is not None else None
+        _check(lib.seg_prior(self.handle, _dev(saliency, torch.float32, (self.H, self.W), "saliency"), pm,
+                             float(w_f), _dev(out, torch.float32, (self.H, self.W), "prior")), "seg_prior")
+        return out
+
+    def terms(self, rgb, prior):
+        H, W, d = self.H, self.W, self.device
+        cs = torch.empty(H, W, dtype=torch.int32, device=d)
+        ct = torch.empty(H, W, dtype=torch.int32, device=d)
+        nc = torch.empty(self.nk, H, W, dtype=torch.int32, device=d)
+        _check(lib.seg_terms(self.handle, _dev(rgb, torch.uint8, (H, W, 3), "rgb"),
+                             _dev(prior, torch.float32, (H, W), "prior"), _ptr(cs), _ptr(ct), _ptr(nc)),
+               "seg_terms")
+        return cs, ct, nc
+
+    def mincut(self, cs, ct, ncap, mask=None, cut=None):
+        H, W, d = self.H, self.W, self.device
+        mask = mask if mask is not None else torch.empty(H, W, dtype=torch.uint8, device=d)
+        cut = cut if cut is not None else torch.empty(1, dtype=torch.int64, device=d)
+        _check(lib.seg_mincut(self.handle, _dev(cs, torch.int32, (H, W), "cs"), _dev(ct, torch.int32, (H, W), "ct"),
+                              _dev(ncap, torch.int32, (self.nk, H, W), "ncap"), _ptr(mask), _ptr(cut)),
+               "seg_mincut")
+        return mask, cut
+
+    def debug_copy(self, which: int, index: int, shape):
+        out = torch.empty(*shape, dtype=torch.float32)
+        _check(lib.seg_debug_copy(self.handle, which, index, _ptr(out), out.numel()), "seg_debug_copy")
+        return out
+
+
+def mincut_grid(cs, ct, ncap, max_cycles: int = 0, stream=None):
+    """Standalone exact min cut of an H x W grid.  Returns (mask, cut, status, cycles)."""
+    H, W = cs.shape
+    nk = ncap.shape[0]
+    mask = torch.empty(H, W, dtype=torch.uint8, device=cs.device)
+    cut = torch.empty(1, dtype=torch.int64, device=cs.device)
+    cyc = C.c_int(0)
+    code = lib.seg_mincut_grid(_stream_handle(stream), H, W, 2 * nk, _dev(cs, torch.int32, (H, W), "cs"),
+                               _dev(ct, torch.int32, (H, W), "ct"), _dev(ncap, torch.int32, (nk, H, W), "ncap"),
+                               _ptr(mask), _ptr(cut), int(max_cycles), C.byref(cyc))
+    if code not in (SEG_OK, SEG_ENOTCONVERGED, SEG_ETIMEOUT, SEG_ECAPACITY):
+        raise SegError(code, "seg_mincut_grid")
+    return mask, cut, code, cyc.value

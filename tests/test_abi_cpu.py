@@ -1,0 +1,73 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol the header
+declares, its parameter struct matches the C layout, and host-side argument
+checks reject bad input before any CUDA call."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "seg.h")
+
+
+@pytest.fixture(scope="module")
+def seg():
+    from paper_1008_0502_b300 import build
+    build.build()
+    from paper_1008_0502_b300 import seg as S
+    return S
+
+
+def declared_symbols():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(seg_\w+)\s*\(", txt, re.M)))
+
+
+def test_every_declared_symbol_is_exported(seg):
+    names = declared_symbols()
+    assert len(names) >= 17
+    out = subprocess.run(["nm", "-D", "--defined-only", seg.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(seg_\w+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(seg.lib, n)
+
+
+def test_params_struct_layout_matches_c(seg, tmp_path):
+    fields = [f for f, _ in seg.seg_params._fields_]
+    src = tmp_path / "probe.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){",
+             'printf("%zu\\n", sizeof(seg_params));']
+    lines += [f'printf("%zu\\n", offsetof(seg_params, {f}));' for f in fields]
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-o", str(exe), str(src)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == C.sizeof(seg.seg_params)
+    assert vals[1:] == [getattr(seg.seg_params, f).offset for f in fields]
+
+
+def test_defaults_and_helpers(seg):
+    p = seg.default_params()
+    assert (p.levels, p.c_min, p.c_max, p.d_min, p.d_max, p.neighbourhood) == (9, 2, 4, 3, 4, 8)
+    assert p.sigma1 == 0.03 and p.sigma2 == 0.035
+    assert [seg.level_dim(480, l) for l in range(9)] == [480, 240, 120, 60, 30, 15, 8, 4, 2]
+    assert seg.strerror(seg.SEG_ENOTCONVERGED).startswith("min-cut")
+
+
+def test_host_validation_rejects_bad_arguments(seg):
+    h = C.c_void_p()
+    p = seg.default_params()
+    assert seg.lib.seg_create(None, 0, 10, C.byref(p), C.byref(h)) == seg.SEG_EINVAL
+    assert seg.lib.seg_create(None, 10, 10, None, C.byref(h)) == seg.SEG_EINVAL
+    bad = seg.default_params(c_max=6)  # c_max + d_max > levels - 1
+    assert seg.lib.seg_create(None, 480, 640, C.byref(bad), C.byref(h)) == seg.SEG_EINVAL
+    bad = seg.default_params(neighbourhood=6)
+    assert seg.lib.seg_create(None, 480, 640, C.byref(bad), C.byref(h)) == seg.SEG_EINVAL
+    assert seg.lib.seg_mincut_grid(None, 4, 4, 5, None, None, None, None, None, 0, None) == seg.SEG_EINVAL
+    assert seg.lib.seg_mincut_grid(None, 0, 4, 4, None, None, None, None, None, 0, None) == seg.SEG_EINVAL
+    assert h.value is None

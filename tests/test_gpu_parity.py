@@ -1,0 +1,268 @@
+"""GPU path vs the FP64 oracle, through the C-ABI.
+
+Tolerances (floating point): saliency, prior and every intermediate map within
+max|gpu - oracle| / max|oracle| <= 1e-4 per map; integer n-links bit-exact;
+t-link capacities within 2 + 2e-6 * cap (they are FP32 costs quantised at
+K = 1000, so a cost that differs by FP32 rounding can land one unit off);
+min cuts on identical int32 capacities bit-exact (value and mask); end-to-end
+masks on >= 99.9% of pixels.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_0502_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def S(cuda_ok):
+    from paper_1008_0502_b300 import build
+    build.build()
+    from paper_1008_0502_b300 import seg
+    return seg
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / den if den > 0 else np.abs(a).max()
+
+
+def seg_params(S, cfg, **over):
+    return S.params_from({k: v for k, v in cfg.items()}, **over)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+# ---------------------------------------------------------------- saliency
+@pytest.mark.parametrize("cfg_name,H,W", [("small", 120, 160), ("small", 97, 131), ("vga", 480, 640),
+                                          ("vga", 301, 403)])
+def test_saliency_stages_match_oracle(S, cfg_name, H, W):
+    cfg = O.CONFIG_SMALL if cfg_name == "small" else O.CONFIG_VGA
+    if (H, W) == (120, 160):
+        rgb = synth.clip_small(2)[0][1]
+    elif (H, W) == (480, 640):
+        rgb = next(synth.clip_vga_frames(1))[0]
+    else:
+        rgb = synth.random_frame(H, W, 5 + H)
+    ref, dbg = O.saliency(rgb, cfg, debug=True)
+    sg = S.Segmenter(H, W, seg_params(S, cfg))
+    sal = host(sg.saliency(dev(rgb)))
+    assert rel_err(sal, ref) <= REL
+    L = cfg["levels"]
+    for ch in range(3):
+        for l in range(1, L):
+            h, w = dbg["pyr"][ch][l].shape
+            got = sg.debug_copy(0, ch * 16 + l, (h, w)).numpy()
+            assert rel_err(got, dbg["pyr"][ch][l]) <= REL, (ch, l)
+    for k in range(cfg["n_orient"]):
+        for l in range(cfg["c_min"], cfg["c_max"] + cfg["d_max"] + 1):
+            ref_o = dbg["ori"][k][l]
+            got = sg.debug_copy(1, k * 16 + l, ref_o.shape).numpy()
+            # absolute bound relative to the largest orientation response of the level
+            scale = max(np.abs(dbg["ori"][j][l]).max() for j in range(cfg["n_orient"]))
+            assert np.abs(got - ref_o).max() <= REL * max(scale, 1e-3), (k, l)
+    for k in range(4):
+        got = sg.debug_copy(2, k, dbg["consp"][k].shape).numpy()
+        assert np.abs(got - dbg["consp"][k]).max() <= REL * max(np.abs(dbg["consp"]).max(), 1e-12), k
+    got = sg.debug_copy(3, 0, dbg["S"].shape).numpy()
+    assert rel_err(got, dbg["S"]) <= REL
+    sg.close()
+
+
+def test_saliency_constant_and_grey_frames(S):
+    sg = S.Segmenter(64, 80, seg_params(S, O.CONFIG_SMALL))
+    for rgb in [synth.constant_frame(64, 80, (97, 97, 97)), synth.constant_frame(64, 80, (200, 30, 60))]:
+        assert float(sg.saliency(dev(rgb)).abs().max()) == 0.0
+    g = synth.noise_background(np.random.default_rng(8), 64, 80)
+    grey = np.repeat(g[:, :, None], 3, 2)
+    sg.saliency(dev(grey))
+    hS, wS = S.level_dim(64, 2), S.level_dim(80, 2)
+    assert not sg.debug_copy(2, 1, (hS, wS)).numpy().any()
+    assert not sg.debug_copy(2, 2, (hS, wS)).numpy().any()
+    sg.close()
+
+
+# ---------------------------------------------------------------- prior
+@pytest.mark.parametrize("w_f", [0.0, 0.329901, 1.0])
+def test_prior_matches_oracle(S, w_f):
+    H, W = 97, 130
+    rng = np.random.default_rng(3)
+    sal = (rng.random((H, W)) ** 3).astype(np.float32)
+    prev = (rng.random((H, W)) > 0.6).astype(np.uint8)
+    sg = S.Segmenter(H, W, seg_params(S, O.CONFIG_SMALL))
+    got = host(sg.prior(dev(sal), dev(prev), w_f))
+    _, ref = O.prior(sal.astype(np.float64), prev, w_f, O.CONFIG_SMALL)
+    assert np.abs(got - ref).max() <= 1e-6
+    sg.close()
+
+
+# ---------------------------------------------------------------- terms
+@pytest.mark.parametrize("cfg_name", ["small", "vga"])
+def test_terms_match_oracle(S, cfg_name):
+    cfg = O.CONFIG_SMALL if cfg_name == "small" else O.CONFIG_VGA
+    frames, _ = synth.clip_small(2)
+    rgb = frames[1]
+    H, W = rgb.shape[:2]
+    sal = O.saliency(rgb, cfg)
+    _, pr = O.prior(sal, None, 0.0, cfg)
+    pr32 = pr.astype(np.float32)
+    cs, ct, nc, D0, D1 = O.terms(rgb, pr32.astype(np.float64), cfg)
+    sg = S.Segmenter(H, W, seg_params(S, cfg))
+    gcs, gct, gnc = (host(t) for t in sg.terms(dev(rgb), dev(pr32)))
+    np.testing.assert_array_equal(gnc, nc)
+    for g, r in [(gcs, cs), (gct, ct)]:
+        assert (np.abs(g.astype(np.int64) - r) <= 2 + 2e-6 * np.abs(r)).all()
+    assert (np.minimum(gcs, gct) == 0).all()
+    sg.close()
+
+
+# ---------------------------------------------------------------- min cut, bit-exact
+CUT_CASES = [(1, 1, 4), (1, 37, 4), (29, 1, 8), (4, 4, 8), (16, 32, 4), (17, 33, 8), (33, 65, 4),
+             (50, 70, 8), (120, 160, 4), (121, 161, 8)]
+
+
+@pytest.mark.parametrize("H,W,nbr", CUT_CASES)
+def test_mincut_random_grids_bit_exact(S, H, W, nbr):
+    for seed in range(3):
+        cs, ct, nc = synth.random_grid_caps(H, W, nbr, 1000 * H + W + seed, tmax=800, nmax=300,
+                                            p_zero=0.1 * seed)
+        v, m = O.maxflow(cs, ct, nc)
+        mask, cut, code, cyc = S.mincut_grid(dev(cs), dev(ct), dev(nc))
+        assert code == 0
+        assert int(cut.item()) == v
+        np.testing.assert_array_equal(host(mask), m)
+
+
+@pytest.mark.parametrize("H,W,nbr", [(64, 96, 4), (97, 131, 8), (240, 320, 8), (480, 640, 8)])
+def test_mincut_blob_grids_bit_exact(S, H, W, nbr):
+    cs, ct, nc = synth.blob_grid_caps(H, W, nbr, H + W)
+    v, m = O.maxflow(cs, ct, nc)
+    mask, cut, code, cyc = S.mincut_grid(dev(cs), dev(ct), dev(nc))
+    assert code == 0 and int(cut.item()) == v
+    np.testing.assert_array_equal(host(mask), m)
+
+
+def test_mincut_extreme_capacities(S):
+    H, W = 20, 40
+    big = np.full((H, W), 1 << 24, np.int32)
+    nc = np.full((4, H, W), 1 << 24, np.int32)
+    v, m = O.maxflow(big, np.zeros_like(big), nc)
+    mask, cut, code, _ = S.mincut_grid(dev(big), dev(np.zeros_like(big)), dev(nc))
+    assert code == 0 and int(cut.item()) == v == 0 and host(mask).all()
+    z = np.zeros((H, W), np.int32)
+    mask, cut, code, _ = S.mincut_grid(dev(z), dev(z), dev(np.zeros((2, H, W), np.int32)))
+    assert code == 0 and int(cut.item()) == 0 and not host(mask).any()
+
+
+def test_mincut_frame_graphs_bit_exact(S):
+    frames, _ = synth.clip_small(3)
+    for t in range(3):
+        sal = O.saliency(frames[t], O.CONFIG_SMALL)
+        _, pr = O.prior(sal, None, 0.0, O.CONFIG_SMALL)
+        cs, ct, nc, _, _ = O.terms(frames[t], pr, O.CONFIG_SMALL)
+        v, m = O.maxflow(cs, ct, nc)
+        mask, cut, code, _ = S.mincut_grid(dev(cs), dev(ct), dev(nc))
+        assert code == 0 and int(cut.item()) == v
+        np.testing.assert_array_equal(host(mask), m)
+    f = next(synth.clip_vga_frames(1))[0]
+    sal = O.saliency(f, O.CONFIG_VGA)
+    _, pr = O.prior(sal, None, 0.0, O.CONFIG_VGA)
+    cs, ct, nc, _, _ = O.terms(f, pr, O.CONFIG_VGA)
+    v, m = O.maxflow(cs, ct, nc)
+    mask, cut, code, _ = S.mincut_grid(dev(cs), dev(ct), dev(nc))
+    assert code == 0 and int(cut.item()) == v
+    np.testing.assert_array_equal(host(mask), m)
+
+
+def test_mincut_errors_are_reported_and_context_survives(S):
+    cs, ct, nc = synth.blob_grid_caps(64, 96, 8, 3)
+    _, _, code, cyc = S.mincut_grid(dev(cs), dev(ct), dev(nc), max_cycles=1)
+    assert code == S.SEG_ENOTCONVERGED and cyc == 1
+    bad = cs.copy()
+    bad[3, 4] = (1 << 24) + 1
+    _, _, code, _ = S.mincut_grid(dev(bad), dev(ct), dev(nc))
+    assert code == S.SEG_ECAPACITY
+    neg = nc.copy()
+    neg[1, 5, 5] = -3
+    _, _, code, _ = S.mincut_grid(dev(cs), dev(ct), dev(neg))
+    assert code == S.SEG_ECAPACITY
+    v, m = O.maxflow(cs, ct, nc)
+    mask, cut, code, _ = S.mincut_grid(dev(cs), dev(ct), dev(nc))
+    assert code == 0 and int(cut.item()) == v
+    np.testing.assert_array_equal(host(mask), m)
+
+
+# ---------------------------------------------------------------- end to end
+def _run_clip(S, frames, cfg, check_every=1):
+    H, W = frames.shape[1:3]
+    sg = S.Segmenter(H, W, seg_params(S, cfg))
+    orc = O.Segmenter(H, W, cfg)
+    agree = []
+    for t in range(len(frames)):
+        sal, pr, mask, cut = sg.push_frame(dev(frames[t]))
+        code, _ = sg.sync()
+        assert code == 0
+        osal, opr, omask, ocut = orc.push(frames[t])
+        if t % check_every == 0:
+            assert rel_err(host(sal), osal) <= REL, t
+            agree.append((host(mask) == omask).mean())
+            if (host(mask) == omask).all():
+                assert int(cut.item()) == pytest.approx(ocut, rel=1e-3, abs=50)
+    sg.close()
+    return agree
+
+
+def test_end_to_end_small_clip(S):
+    frames, _ = synth.clip_small(10)
+    agree = _run_clip(S, frames, O.CONFIG_SMALL)
+    assert min(agree) >= 0.999, agree
+
+
+def test_end_to_end_vga_clip(S):
+    frames = np.stack([f for f, _ in synth.clip_vga_frames(12)])
+    agree = _run_clip(S, frames, O.CONFIG_VGA)
+    assert min(agree) >= 0.999, agree
+
+
+def test_host_entry_point_and_state_roundtrip(S):
+    frames, _ = synth.clip_small(4)
+    H, W = frames.shape[1:3]
+    p = seg_params(S, O.CONFIG_SMALL)
+    a, b = S.Segmenter(H, W, p), S.Segmenter(H, W, p)
+    for t in range(2):
+        _, _, ma, ca = a.push_frame(dev(frames[t]))
+        mh = torch.empty(H, W, dtype=torch.uint8).pin_memory()
+        ch = torch.empty(1, dtype=torch.int64).pin_memory()
+        b.push_frame_host(torch.from_numpy(frames[t]).pin_memory(), mh, ch)
+        a.sync()
+        assert torch.equal(ma.cpu(), mh) and int(ca.item()) == int(ch.item())
+    st = a.get_state()
+    c = S.Segmenter(H, W, p)
+    c.set_state(st)
+    _, pa, ma, _ = a.push_frame(dev(frames[2]))
+    _, pc, mc, _ = c.push_frame(dev(frames[2]))
+    a.sync()
+    c.sync()
+    assert torch.equal(ma, mc) and torch.equal(pa, pc)
+    a.reset()
+    _, p0, _, _ = a.push_frame(dev(frames[0]))
+    fresh = S.Segmenter(H, W, p)
+    _, p1, _, _ = fresh.push_frame(dev(frames[0]))
+    a.sync()
+    fresh.sync()
+    assert torch.equal(p0, p1)
+    for s in (a, b, c, fresh):
+        s.close()
