@@ -35,6 +35,7 @@
 #define MF_HX (MF_TW + 2)
 #define MF_HY (MF_TH + 2)
 #define MF_HN (MF_HX * MF_HY)
+#define MF_ROUND_CAP (1 << 20)  // fixpoint rounds per cut; uniform across CTAs
 
 __constant__ int c_dx[8] = {1, -1, 0, 0, 1, -1, -1, 1};   // E W S N SE NW SW NE
 __constant__ int c_dy[8] = {0, 0, 1, -1, 1, -1, 1, -1};  // opposite direction = d ^ 1
@@ -323,6 +324,10 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
         ++epoch;
         ++n_rounds;
         if (f == 0u) break;
+        if (n_rounds >= MF_ROUND_CAP) {
+          if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.status[0], 0, SEG_ENOTCONVERGED);
+          return;
+        }
       }
       ++n_gr;
     }
@@ -371,6 +376,10 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
     ++epoch;
     ++n_rounds;
     if (f == 0u) break;
+    if (n_rounds >= MF_ROUND_CAP) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.status[0], 0, SEG_ENOTCONVERGED);
+      return;
+    }
   }
   for (int u = gtid; u < N; u += nthr) {
     uint8_t v = a.z[u];
