@@ -23,6 +23,7 @@ SEG_ENOTCONVERGED = -3
 SEG_ECUDA = -4
 SEG_ETIMEOUT = -5
 SEG_ECAPACITY = -6
+SEG_MINCUT_STATIC_MAX_PIXELS = 131072
 
 
 class SegError(RuntimeError):
@@ -66,6 +67,7 @@ def _load():
         "seg_terms": ([vp, vp, vp, vp, vp, vp], i32),
         "seg_mincut": ([vp, vp, vp, vp, vp, vp], i32),
         "seg_mincut_grid": ([vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, P(C.c_int)], i32),
+        "seg_mincut_grid_static": ([vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, P(C.c_int)], i32),
         "seg_debug_copy": ([vp, i32, i32, vp, C.c_size_t], i32),
         "seg_level_dim": ([i32, i32], i32),
         "seg_profile_enable": ([vp, i32], i32),
@@ -276,4 +278,24 @@ def mincut_grid(cs, ct, ncap, max_cycles: int = 0, stream=None):
                                _ptr(mask), _ptr(cut), int(max_cycles), C.byref(cyc))
     if code not in (SEG_OK, SEG_ENOTCONVERGED, SEG_ETIMEOUT, SEG_ECAPACITY):
         raise SegError(code, "seg_mincut_grid")
+    return mask, cut, code, cyc.value
+
+
+def mincut_grid_static(cs, ct, ncap, max_cycles: int = 0, stream=None, mask=None, cut=None):
+    """seg_mincut_grid_static: the standalone min cut with the library's fixed
+    device scratch instead of an allocation (H*W <= SEG_MINCUT_STATIC_MAX_PIXELS).
+    Pass preallocated ``mask``/``cut`` tensors to keep the call allocation-free.
+    Returns (mask, cut, status, cycles)."""
+    H, W = cs.shape
+    nk = ncap.shape[0]
+    mask = mask if mask is not None else torch.empty(H, W, dtype=torch.uint8, device=cs.device)
+    cut = cut if cut is not None else torch.empty(1, dtype=torch.int64, device=cs.device)
+    cyc = C.c_int(0)
+    code = lib.seg_mincut_grid_static(_stream_handle(stream), H, W, 2 * nk, _dev(cs, torch.int32, (H, W), "cs"),
+                                      _dev(ct, torch.int32, (H, W), "ct"),
+                                      _dev(ncap, torch.int32, (nk, H, W), "ncap"),
+                                      _dev(mask, torch.uint8, (H, W), "mask"), _dev(cut, torch.int64, (1,), "cut"),
+                                      int(max_cycles), C.byref(cyc))
+    if code not in (SEG_OK, SEG_ENOTCONVERGED, SEG_ETIMEOUT, SEG_ECAPACITY):
+        raise SegError(code, "seg_mincut_grid_static")
     return mask, cut, code, cyc.value
