@@ -75,7 +75,7 @@ typedef struct seg_params {
   double cap_scale;        /* K: capacity = min(2^24, floor(K*cost + 1/2)) (1000) */
   int32_t neighbourhood;   /* 4 or 8 */
   int32_t max_cycles;      /* min-cut cycle cap -> SEG_ENOTCONVERGED (20000) */
-  int32_t global_relabel_every; /* min-cut cycles between global relabels (4) */
+  int32_t global_relabel_every; /* min-cut cycles between global relabels (2) */
   int32_t local_iters;     /* push/relabel iterations per tile visit (16) */
 } seg_params;
 
@@ -204,6 +204,13 @@ int seg_debug_copy(seg_ctx* ctx, int which, int index, float* dst_host, size_t n
 int seg_profile_enable(seg_ctx* ctx, int on);
 int seg_profile_read(seg_ctx* ctx, double* stage_ms, int* frames, long long* cycles, float* frame_ms,
                      int max_frames);
+/* seg_profile_read plus, per recorded frame f < max_frames (if mincut_stats is
+ * non-NULL), seven int32 min-cut statistics in mincut_stats[7f .. 7f+6]:
+ * cycles, global relabels, fixpoint rounds, then the time spent in
+ * initialisation, global relabels, discharge cycles and the final reach pass
+ * (units of 0.1 us, read from the device timer). */
+int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* cycles, float* frame_ms,
+                        int* mincut_stats, int max_frames);
 
 /* Size of pyramid level `level` along an n-pixel axis: ceil-halving. */
 int seg_level_dim(int n, int level);

@@ -37,8 +37,16 @@
 #define MF_HN (MF_HX * MF_HY)
 #define MF_ROUND_CAP (1 << 20)  // fixpoint rounds per cut; uniform across CTAs
 
-__constant__ int c_dx[8] = {1, -1, 0, 0, 1, -1, -1, 1};   // E W S N SE NW SW NE
-__constant__ int c_dy[8] = {0, 0, 1, -1, 1, -1, 1, -1};  // opposite direction = d ^ 1
+// Directions E W S N SE NW SW NE; the opposite of d is d ^ 1.  The kernel is
+// instantiated for 4 and 8 neighbours so every direction loop unrolls and these
+// fold to constants.
+__device__ __forceinline__ constexpr int mf_dx(int d) {
+  return d == 0 ? 1 : d == 1 ? -1 : d == 2 ? 0 : d == 3 ? 0 : d == 4 ? 1 : d == 5 ? -1 : d == 6 ? -1 : 1;
+}
+__device__ __forceinline__ constexpr int mf_dy(int d) {
+  return d == 0 ? 0 : d == 1 ? 0 : d == 2 ? 1 : d == 3 ? -1 : d == 4 ? 1 : d == 5 ? -1 : d == 6 ? 1 : -1;
+}
+__device__ __forceinline__ constexpr int mf_hoff(int d) { return mf_dy(d) * MF_HX + mf_dx(d); }
 
 struct MFShared {
   int h[MF_HN];  // heights (or BFS distances) with a one-node halo
@@ -98,9 +106,21 @@ __device__ __forceinline__ void mf_flag_begin(const MFArgs& a, unsigned int epoc
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(epoch + 1) % 3] = 0u;
 }
 
+// Block-uniform: did this tile or one of its 8 neighbours change in a round
+// with epoch >= since?  (A tile's fixpoint can only move when its halo moved.)
+__device__ bool mf_tile_dirty(const MFArgs& a, MFShared& s, int tx, int ty, int since) {
+  int d = 0;
+  if (threadIdx.x < 9) {
+    int x = tx + (int)threadIdx.x % 3 - 1, y = ty + (int)threadIdx.x / 3 - 1;
+    if (x >= 0 && x < a.ntx && y >= 0 && y < a.nty) d = *(volatile int*)&a.tstamp[y * a.ntx + x] >= since;
+  }
+  return __syncthreads_or(d) != 0;
+}
+
 // ---------------------------------------------------------------- BFS to the sink
 // d(u) = 1 if u has residual to t, else 1 + min over residual arcs u->v of d(v):
 // relaxed to the local fixpoint with the halo fixed at its current global value.
+template <int ND>
 __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
@@ -118,10 +138,11 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty) {
   bool any = false;
   for (;;) {
     int ch = 0;
-    if (valid) {
+    if (bits) {
       int cur = s.h[hi], nd = cur;
-      for (int d = 0; d < a.ndir; ++d)
-        if ((bits >> d) & 1u) nd = min(nd, s.h[hi + c_dy[d] * MF_HX + c_dx[d]] + 1);
+#pragma unroll
+      for (int d = 0; d < ND; ++d)
+        if ((bits >> d) & 1u) nd = min(nd, s.h[hi + mf_hoff(d)] + 1);
       if (nd < cur) {
         s.h[hi] = nd;
         ch = 1;
@@ -130,12 +151,13 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty) {
     if (!__syncthreads_or(ch)) break;
     any = true;
   }
-  if (valid) a.h[g] = s.h[hi];
+  if (valid && any) a.h[g] = s.h[hi];
   __syncthreads();  // the next tile reuses the shared arrays
   return any;
 }
 
 // z(v) = 1 if some residual arc u->v has z(u) = 1 (pull form, halo bitmasks).
+template <int ND>
 __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
@@ -154,13 +176,15 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty) {
   for (;;) {
     int ch = 0;
     if (valid && !s.z[hi]) {
-      for (int d = 0; d < a.ndir; ++d) {
-        int nb = hi + c_dy[d] * MF_HX + c_dx[d];
-        if (s.z[nb] && ((s.b[nb] >> (d ^ 1)) & 1u)) {
-          s.z[hi] = 1;
-          ch = 1;
-          break;
-        }
+      bool hit = false;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        int nb = hi + mf_hoff(d);
+        hit |= s.z[nb] && ((s.b[nb] >> (d ^ 1)) & 1u);
+      }
+      if (hit) {
+        s.z[hi] = 1;
+        ch = 1;
       }
     }
     if (!__syncthreads_or(ch)) break;
@@ -175,7 +199,8 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty) {
 // Up to local_iters synchronous sweeps over one tile: push along admissible
 // arcs (h(u) = h(v) + 1, t has height 0), then relabel every node still active
 // to 1 + min over residual arcs.  Returns whether any push or relabel happened.
-__device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty) {
+template <int ND>
+__device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, bool* still_active) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   const int N = a.N, W = a.W;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
@@ -191,44 +216,51 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty) {
   const int hi = (ly + 1) * MF_HX + lx + 1;
   s.e[tid] = valid ? a.e[g] : 0;
   s.rt[tid] = valid ? a.rt[g] : 0;
-  for (int d = 0; d < a.ndir; ++d) s.r[d][tid] = valid ? a.r[d * N + g] : 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) s.r[d][tid] = valid ? a.r[d * N + g] : 0;
   __syncthreads();
   int work = 0;
+  bool remain = true;
   for (int it = 0; it < a.local_iters; ++it) {
     // push
-    if (valid) {
-      const int e0 = s.e[tid], hu = s.h[hi];
-      if (e0 > 0 && hu < N) {
-        int ex = e0;
-        if (hu == 1) {
-          int rtv = s.rt[tid];
-          if (rtv > 0) {
-            int dl = min(ex, rtv);
-            s.rt[tid] = rtv - dl;
-            ex -= dl;
-          }
-        }
-        for (int d = 0; d < a.ndir && ex > 0; ++d) {
-          int rr = s.r[d][tid];
-          if (rr <= 0 || hu != s.h[hi + c_dy[d] * MF_HX + c_dx[d]] + 1) continue;
-          int dl = min(ex, rr);
-          s.r[d][tid] = rr - dl;
+    const int e0 = s.e[tid], hu = s.h[hi];
+    if (valid && e0 > 0 && hu < N) {
+      int hn[ND], rr[ND];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        hn[d] = s.h[hi + mf_hoff(d)];
+        rr[d] = s.r[d][tid];
+      }
+      int ex = e0;
+      if (hu == 1) {
+        int rtv = s.rt[tid];
+        if (rtv > 0) {
+          int dl = min(ex, rtv);
+          s.rt[tid] = rtv - dl;
           ex -= dl;
-          int nly = ly + c_dy[d], nlx = lx + c_dx[d];
-          if (nly >= 0 && nly < MF_TH && nlx >= 0 && nlx < MF_TW) {
-            int nt = nly * MF_TW + nlx;
-            atomicAdd(&s.e[nt], dl);
-            s.r[d ^ 1][nt] += dl;  // only this node writes the reverse arc in this sweep
-          } else {
-            int gv = g + c_dy[d] * W + c_dx[d];
-            atomicAdd(&a.e[gv], dl);
-            atomicAdd(&a.r[(d ^ 1) * N + gv], dl);
-          }
         }
-        if (ex != e0) {
-          atomicAdd(&s.e[tid], ex - e0);
-          work = 1;
+      }
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        if (ex <= 0 || rr[d] <= 0 || hu != hn[d] + 1) continue;
+        int dl = min(ex, rr[d]);
+        s.r[d][tid] = rr[d] - dl;
+        ex -= dl;
+        int nly = ly + mf_dy(d), nlx = lx + mf_dx(d);
+        if (nly >= 0 && nly < MF_TH && nlx >= 0 && nlx < MF_TW) {
+          int nt = nly * MF_TW + nlx;
+          atomicAdd(&s.e[nt], dl);
+          s.r[d ^ 1][nt] += dl;  // only this node writes the reverse arc in this sweep
+        } else {
+          int gv = g + mf_dy(d) * W + mf_dx(d);
+          atomicAdd(&a.e[gv], dl);
+          atomicAdd(&a.r[(d ^ 1) * N + gv], dl);
+          a.tact[((gy + mf_dy(d)) / MF_TH) * a.ntx + (gx + mf_dx(d)) / MF_TW] = 1;
         }
+      }
+      if (ex != e0) {
+        atomicAdd(&s.e[tid], ex - e0);
+        work = 1;
       }
     }
     __syncthreads();
@@ -238,8 +270,9 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty) {
       int cur = s.h[hi];
       if (cur < N) {
         int nh = s.rt[tid] > 0 ? 1 : SEG_INF_H;
-        for (int d = 0; d < a.ndir; ++d)
-          if (s.r[d][tid] > 0) nh = min(nh, s.h[hi + c_dy[d] * MF_HX + c_dx[d]] + 1);
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+          if (s.r[d][tid] > 0) nh = min(nh, s.h[hi + mf_hoff(d)] + 1);
         nh = min(nh, SEG_INF_H);
         if (nh > cur) {
           s.h[hi] = nh;
@@ -249,14 +282,19 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty) {
         act = cur < N;
       }
     }
-    if (!__syncthreads_or(act)) break;
+    if (!__syncthreads_or(act)) {
+      remain = false;
+      break;
+    }
   }
+  *still_active = remain;
   __syncthreads();
   if (valid) {
     a.e[g] = s.e[tid];
     a.rt[g] = s.rt[tid];
     a.h[g] = s.h[hi];
-    for (int d = 0; d < a.ndir; ++d) a.r[d * N + g] = s.r[d][tid];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) a.r[d * N + g] = s.r[d][tid];
   }
   return __syncthreads_or(work);
 }
@@ -264,13 +302,15 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty) {
 // ---------------------------------------------------------------- the kernel
 __device__ __forceinline__ bool cap_ok(int c) { return c >= 0 && c <= (1 << 24); }
 
-__global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
+template <int ND>
+__global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   __shared__ MFShared s;
   const int N = a.N, W = a.W, H = a.H;
   const int nthr = gridDim.x * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int ntiles = a.ntx * a.nty;
 
+  const long long t_start = mf_now();
   // ---- 1. init
   for (int u = gtid; u < N; u += nthr) {
     int y = u / W, x = u - y * W;
@@ -286,7 +326,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
     a.r[1 * N + u] = x > 0 ? a.ncap[u - 1] : 0;
     a.r[2 * N + u] = cS;
     a.r[3 * N + u] = y > 0 ? a.ncap[N + u - W] : 0;
-    if (a.ndir == 8) {
+    if (ND == 8) {
       int cSE = (x + 1 < W && y + 1 < H) ? a.ncap[2 * N + u] : 0;
       int cSW = (x > 0 && y + 1 < H) ? a.ncap[3 * N + u] : 0;
       bad |= !cap_ok(cSE) || !cap_ok(cSW);
@@ -297,27 +337,50 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
     }
     if (bad) atomicCAS(&a.status[0], 0, SEG_ECAPACITY);
   }
+  for (int t = gtid; t < ntiles; t += nthr) {
+    a.tstamp[t] = -2;
+    a.tact[t] = 1;
+  }
   if (!mf_grid_sync(a, s)) return;
   if (*(volatile int*)&a.status[0] == SEG_ECAPACITY) return;
 
   unsigned int epoch = 0;
   int cycle = 0, n_gr = 0, n_rounds = 0;
   bool converged = false;
+  // phase timing on one thread (the grid moves in lock-step between barriers):
+  // [0] init, [1] global relabels, [2] discharge cycles, [3] final reach + mask
+  long long t_acc[4] = {0, 0, 0, 0};
+  long long t_last = t_start;
+  auto lap = [&](int slot) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      long long t = mf_now();
+      t_acc[slot] += t - t_last;
+      t_last = t;
+    }
+  };
+  lap(0);
   for (;;) {
     // ---- 3. global relabel
     if (cycle % a.gr_every == 0) {
       for (int u = gtid; u < N; u += nthr) {
         unsigned bits = 0;
-        for (int d = 0; d < a.ndir; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
         a.rm[u] = (unsigned char)bits;
         a.h[u] = a.rt[u] > 0 ? 1 : SEG_INF_H;
       }
       if (!mf_grid_sync(a, s)) return;
-      for (;;) {
+      for (bool first = true;; first = false) {
         mf_flag_begin(a, epoch);
         bool ch = false;
-        for (int k = blockIdx.x; k < ntiles; k += gridDim.x)
-          ch |= mf_tile_bfs(a, s, k % a.ntx, k / a.ntx);
+        for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+          int tx = k % a.ntx, ty = k / a.ntx;
+          if (!first && !mf_tile_dirty(a, s, tx, ty, (int)epoch - 1)) continue;
+          if (mf_tile_bfs<ND>(a, s, tx, ty)) {
+            ch = true;
+            if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
+          }
+        }
         if (ch && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
         if (!mf_grid_sync(a, s)) return;
         unsigned int f = mf_flag_read(a, epoch);
@@ -330,6 +393,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
         }
       }
       ++n_gr;
+      lap(1);
     }
     // ---- 2. one cycle of the four colour phases
     mf_flag_begin(a, epoch);
@@ -338,11 +402,18 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
       const int ntx_c = (a.ntx - cx + 1) / 2, nty_c = (a.nty - cy + 1) / 2;
       const int ntc = ntx_c * nty_c;
       bool work = false;
-      for (int k = blockIdx.x; k < ntc; k += gridDim.x)
-        work |= mf_discharge(a, s, 2 * (k % ntx_c) + cx, 2 * (k / ntx_c) + cy);
+      for (int k = blockIdx.x; k < ntc; k += gridDim.x) {
+        const int tx = 2 * (k % ntx_c) + cx, ty = 2 * (k / ntx_c) + cy, t = ty * a.ntx + tx;
+        if (!*(volatile unsigned char*)&a.tact[t]) continue;  // no active node can be in it
+        bool remain;
+        work |= mf_discharge<ND>(a, s, tx, ty, &remain);
+        __syncthreads();
+        if (threadIdx.x == 0) a.tact[t] = remain ? 1 : 0;
+      }
       if (work && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
       if (!mf_grid_sync(a, s)) return;
     }
+    lap(2);
     unsigned int w = mf_flag_read(a, epoch);
     ++epoch;
     ++cycle;
@@ -357,7 +428,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
   long long flow_t = 0;
   for (int u = gtid; u < N; u += nthr) {
     unsigned bits = 0;
-    for (int d = 0; d < a.ndir; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
     a.rm[u] = (unsigned char)bits;
     a.z[u] = a.e[u] > 0 ? 1 : 0;
     flow_t += (long long)a.ct[u] - a.rt[u];
@@ -366,10 +438,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
   if ((threadIdx.x & 31) == 0 && flow_t != 0)
     atomicAdd(a.cut_acc, (unsigned long long)flow_t);
   if (!mf_grid_sync(a, s)) return;
-  for (;;) {
+  for (bool first = true;; first = false) {
     mf_flag_begin(a, epoch);
     bool ch = false;
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) ch |= mf_tile_reach(a, s, k % a.ntx, k / a.ntx);
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+      int tx = k % a.ntx, ty = k / a.ntx;
+      if (!first && !mf_tile_dirty(a, s, tx, ty, (int)epoch - 1)) continue;
+      if (mf_tile_reach<ND>(a, s, tx, ty)) {
+        ch = true;
+        if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
+      }
+    }
     if (ch && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
     if (!mf_grid_sync(a, s)) return;
     unsigned int f = mf_flag_read(a, epoch);
@@ -392,14 +471,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_maxflow(MFArgs a) {
     a.status[1] = cycle;
     a.status[2] = n_gr;
     a.status[3] = n_rounds;
+    lap(3);
+    for (int k = 0; k < 4; ++k) a.status[4 + k] = (int)(t_acc[k] / 100);  // units of 0.1 us
   }
 }
 
 // ---------------------------------------------------------------- host side
 size_t mf_bytes(int H, int W, int ndir) {
   size_t N = (size_t)H * W;
+  size_t nt = (size_t)((W + MF_TW - 1) / MF_TW) * ((H + MF_TH - 1) / MF_TH);
   return seg_align(N * 4) * 3 + seg_align(N * 4 * ndir) + seg_align(N) * 2 + seg_align(8) +
-         seg_align(16) + seg_align(sizeof(GridBar));
+         seg_align(16) + seg_align(nt * 4) + seg_align(nt) + seg_align(sizeof(GridBar));
 }
 
 void mf_bind(MFWS& m, char* base, int H, int W, int ndir) {
@@ -417,6 +499,9 @@ void mf_bind(MFWS& m, char* base, int H, int W, int ndir) {
   m.z = (unsigned char*)take(N);
   m.cut_acc = (unsigned long long*)take(8);
   m.flags = (unsigned int*)take(16);
+  size_t nt = (size_t)((W + MF_TW - 1) / MF_TW) * ((H + MF_TH - 1) / MF_TH);
+  m.tstamp = (int*)take(nt * 4);
+  m.tact = (unsigned char*)take(nt);
   m.bar = (GridBar*)take(sizeof(GridBar));
 }
 
@@ -426,7 +511,10 @@ int mf_grid_size(int H, int W, int* grid) {
   SEG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   SEG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return SEG_ECUDA;
-  SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_maxflow, MF_THREADS, 0));
+  SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_maxflow<8>, MF_THREADS, 0));
+  int per_sm4 = 0;
+  SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, k_maxflow<4>, MF_THREADS, 0));
+  per_sm = per_sm4 < per_sm ? per_sm4 : per_sm;
   if (per_sm < 1) return SEG_ECUDA;
   int ntx = (W + MF_TW - 1) / MF_TW, nty = (H + MF_TH - 1) / MF_TH;
   int per_color = ((ntx + 1) / 2) * ((nty + 1) / 2);
@@ -460,6 +548,8 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   a.cut_out = cut_out;
   a.cut_acc = m.cut_acc;
   a.flags = m.flags;
+  a.tstamp = m.tstamp;
+  a.tact = m.tact;
   a.bar = m.bar;
   a.status = status;
   a.max_cycles = max_cycles;
@@ -470,7 +560,8 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));
   SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), st));
   void* args[] = {&a};
-  SEG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_maxflow, dim3(grid), dim3(MF_THREADS), args,
+  SEG_CUDA_TRY(cudaLaunchCooperativeKernel(nbr == 8 ? (const void*)k_maxflow<8> : (const void*)k_maxflow<4>,
+                                           dim3(grid), dim3(MF_THREADS), args,
                                            0, st));
   return SEG_OK;
 }

@@ -66,7 +66,7 @@ extern "C" int seg_mincut_grid_static(void* stream, int H, int W, int nbr, const
   int* status = (int*)(base + seg_align(mfb));
   // every array the kernel reads before writing starts at zero: status words
   // here, the barrier, round flags and cut accumulator inside mf_launch
-  if (cudaMemsetAsync(status, 0, 16, st) != cudaSuccess) return SEG_ECUDA;
+  if (cudaMemsetAsync(status, 0, 32, st) != cudaSuccess) return SEG_ECUDA;
   seg_params d;
   seg_default_params(&d);
   rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, (long long*)cut, status,

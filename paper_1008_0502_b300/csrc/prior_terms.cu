@@ -4,12 +4,15 @@
 //                f = separable Gaussian of the previous mask (shared-memory halo
 //                tile), p-hat = w_f f + (1 - w_f) q.  w_f comes from the device
 //                Kalman state, so a frame needs no host round trip.
-//   k_mom1       first pass of the prior-weighted colour moments (Sec. 5: all
-//                pixels, weighted by p-hat for the object, 1 - p-hat for the
-//                background): weight sums and weighted colour sums
-//   k_mom_fin1   means; advances the Kalman variance (Sec. 6 equations)
-//   k_mom2       second pass: centred weighted second moments (no cancellation)
-//   k_mom_fin2   covariance + 1e-4 I, Cholesky, inverse factor, log-determinant
+//                In seg_push_frame it also runs the first pass of the
+//                prior-weighted colour moments (Sec. 5: all pixels, weighted by
+//                p-hat for the object and 1 - p-hat for the background); its last
+//                CTA reduces the per-CTA partials in a fixed order into the means
+//                and advances the Kalman variance (Sec. 6 equations).
+//   k_mom1       the same first pass alone (stage entry seg_terms)
+//   k_mom2       second pass: centred weighted second moments (no cancellation);
+//                its last CTA forms covariance + 1e-4 I, the Cholesky factor,
+//                its inverse and the log-determinant
 //   k_terms      Eqs. 1-4: t-links from D(a) = lambda_u psi_1(a) + xi_1(a),
 //                shifted by min_a D(a) and quantised; n-links from a host-built
 //                FP64 table indexed by |delta(r+g+b)| and the diagonal flag.
@@ -35,7 +38,41 @@ struct PriorArgs {
   int fR;
   float ftap[2 * PR_MAXR + 1];
   float* prior;
+  // fused first moment pass (rgb == nullptr: off)
+  const uint8_t* rgb;
+  double* part;
+  unsigned* counter;
+  GaussDev* gauss;
+  KalmanDev* kal_adv;  // nullable: advance the variance recursion
 };
+
+struct MomFinArgs {
+  double* part;
+  unsigned* counter;
+  GaussDev* gauss;
+  KalmanDev* kal;  // nullable: advance the variance recursion
+  double a, b;
+};
+
+__device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
+  float r = px[0] / 255.f, g = px[1] / 255.f, b = px[2] / 255.f;
+  float w0 = 1.f - p;
+  s[0] += w0;
+  s[1] += w0 * r;
+  s[2] += w0 * g;
+  s[3] += w0 * b;
+  s[4] += p;
+  s[5] += p * r;
+  s[6] += p * g;
+  s[7] += p * b;
+}
+
+template <int NV>
+__device__ void reduce_parts(const double* part, int nblocks, double* out);
+template <int NV>
+__device__ bool block_partial_last(const double* v, double* part, unsigned* counter, int bid,
+                                   int nblocks);
+__device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b);
 
 __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
   __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
@@ -67,6 +104,7 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     __syncthreads();
   }
   const float mx = __uint_as_float(*a.salmax);
+  float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < PR_TY * PR_TX; i += blockDim.x) {
     int y = i / PR_TX, x = i - y * PR_TX;
     int gy = Y0 + y, gx = X0 + x;
@@ -81,13 +119,27 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
       p += wff * f;
     }
     a.prior[g] = p;
+    if (a.rgb) mom1_add(p, a.rgb + 3 * g, ms);
+  }
+  if (a.rgb) {
+    double d[8];
+    for (int k = 0; k < 8; ++k) d[k] = ms[k];
+    const int nb = gridDim.x * gridDim.y;
+    if (block_partial_last<8>(d, a.part, a.counter, blockIdx.y * gridDim.x + blockIdx.x, nb)) {
+      __shared__ double tot[8];
+      reduce_parts<8>(a.part, nb, tot);
+      if (threadIdx.x == 0) finalize_means(tot, a.gauss, a.kal_adv, a.a, a.b);
+    }
   }
 }
 
-// Block reduction of NV doubles per thread into part[blockIdx.x * NV + k].
+// Writes this CTA's NV partial sums to part[bid*NV ..] and returns true in
+// every thread of exactly one CTA, the last to finish (threadfence reduction).
 template <int NV>
-__device__ __forceinline__ void block_sum_to(double* v, double* part) {
+__device__ bool block_partial_last(const double* v, double* part, unsigned* counter, int bid,
+                                   int nblocks) {
   __shared__ double red[32][NV];
+  __shared__ int is_last;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -98,50 +150,28 @@ __device__ __forceinline__ void block_sum_to(double* v, double* part) {
   if (threadIdx.x < NV) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    part[blockIdx.x * NV + threadIdx.x] = s;
+    part[bid * NV + threadIdx.x] = s;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    is_last = prev == (unsigned)nblocks - 1u;
+    if (is_last) *counter = 0u;  // ready for the next launch
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
 }
 
-__global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
-                                              const float* __restrict__ prior, int N,
-                                              double* part) {
-  float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // label 0: w, wr, wg, wb; label 1: same
-  int base = (blockIdx.x * blockDim.x + threadIdx.x);
-  int stride = gridDim.x * blockDim.x;
-  for (int i = base; i < N; i += stride) {
-    float p = prior[i];
-    float r = rgb[3 * i] / 255.f, g = rgb[3 * i + 1] / 255.f, b = rgb[3 * i + 2] / 255.f;
-    float w0 = 1.f - p;
-    s[0] += w0;
-    s[1] += w0 * r;
-    s[2] += w0 * g;
-    s[3] += w0 * b;
-    s[4] += p;
-    s[5] += p * r;
-    s[6] += p * g;
-    s[7] += p * b;
-  }
-  double d[8];
-  for (int k = 0; k < 8; ++k) d[k] = s[k];
-  block_sum_to<8>(d, part);
-}
-
-struct MomFinArgs {
-  const double* part;
-  int nblocks;
-  GaussDev* gauss;
-  KalmanDev* kal;  // nullable: advance the variance recursion
-  double a, b;
-};
-
-// Deterministic fixed-order reduction of the per-block partials (one CTA).
+// Deterministic fixed-order reduction of the per-CTA partials (one CTA).
 template <int NV>
 __device__ void reduce_parts(const double* part, int nblocks, double* out) {
   __shared__ double red[256][NV];
   double s[NV];
   for (int k = 0; k < NV; ++k) s[k] = 0.0;
   for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x)
-    for (int k = 0; k < NV; ++k) s[k] += part[bk * NV + k];
+    for (int k = 0; k < NV; ++k) s[k] += ((volatile double*)part)[bk * NV + k];
   for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = s[k];
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -154,11 +184,9 @@ __device__ void reduce_parts(const double* part, int nblocks, double* out) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_mom_fin1(MomFinArgs a) {
-  __shared__ double tot[8];
-  reduce_parts<8>(a.part, a.nblocks, tot);
-  if (threadIdx.x != 0) return;
-  GaussDev* g = a.gauss;
+// Weighted means per label; advances sigma^2_xi1 (Sec. 6):
+// P_t = a (b + P) / (a + b + P), and at t = 0 (P_{-1} = inf) P_0 = a.
+__device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b) {
   g->degenerate = 0;
   for (int lab = 0; lab < 2; ++lab) {
     double sw = tot[4 * lab];
@@ -170,17 +198,61 @@ __global__ void __launch_bounds__(256) k_mom_fin1(MomFinArgs a) {
     }
     g->sw[lab] = sw;
   }
-  if (a.kal) {  // Sec. 6: sigma^2_xi1(t) = a (b + P) / (a + b + P); at t = 0, P_{-1} = inf gives a
-    KalmanDev* k = a.kal;
-    double P = k->P;
-    k->P = k->t == 0 ? a.a : a.a * (a.b + P) / (a.a + a.b + P);
-    k->t += 1;
+  if (kal) {
+    double P = kal->P;
+    kal->P = kal->t == 0 ? a : a * (b + P) / (a + b + P);
+    kal->t += 1;
+  }
+}
+
+// Covariance + 1e-4 I, Cholesky factor L, L^-1 and 1/2 log det + 3/2 log 2 pi.
+__device__ void finalize_cov(const double* tot, GaussDev* g) {
+  for (int lab = 0; lab < 2; ++lab) {
+    double sw = g->sw[lab];
+    if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
+      for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
+      g->lconst[lab] = 0.f;
+      continue;
+    }
+    const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
+    double c00 = m[0] / sw + 1e-4, c10 = m[1] / sw, c11 = m[2] / sw + 1e-4;
+    double c20 = m[3] / sw, c21 = m[4] / sw, c22 = m[5] / sw + 1e-4;
+    double l00 = sqrt(c00);
+    double l10 = c10 / l00, l20 = c20 / l00;
+    double l11 = sqrt(c11 - l10 * l10);
+    double l21 = (c21 - l20 * l10) / l11;
+    double l22 = sqrt(c22 - l20 * l20 - l21 * l21);
+    double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
+    double i10 = -l10 * i00 / l11;
+    double i21 = -l21 * i11 / l22;
+    double i20 = -(l20 * i00 + l21 * i10) / l22;
+    g->linv[lab][0] = (float)i00;
+    g->linv[lab][1] = (float)i10;
+    g->linv[lab][2] = (float)i11;
+    g->linv[lab][3] = (float)i20;
+    g->linv[lab][4] = (float)i21;
+    g->linv[lab][5] = (float)i22;
+    g->lconst[lab] = (float)(log(l00 * l11 * l22) + 1.5 * log(2.0 * M_PI));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
+                                              const float* __restrict__ prior, int N, MomFinArgs f) {
+  float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    mom1_add(prior[i], rgb + 3 * (size_t)i, s);
+  double d[8];
+  for (int k = 0; k < 8; ++k) d[k] = s[k];
+  if (block_partial_last<8>(d, f.part, f.counter, blockIdx.x, gridDim.x)) {
+    __shared__ double tot[8];
+    reduce_parts<8>(f.part, gridDim.x, tot);
+    if (threadIdx.x == 0) finalize_means(tot, f.gauss, f.kal, f.a, f.b);
   }
 }
 
 __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
-                                              const float* __restrict__ prior, int N,
-                                              const GaussDev* __restrict__ gauss, double* part) {
+                                              const float* __restrict__ prior, int N, MomFinArgs f) {
+  const GaussDev* gauss = f.gauss;
   float m0r = gauss->muf[0][0], m0g = gauss->muf[0][1], m0b = gauss->muf[0][2];
   float m1r = gauss->muf[1][0], m1g = gauss->muf[1][1], m1b = gauss->muf[1][2];
   float s[12];
@@ -209,43 +281,10 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
   }
   double d[12];
   for (int k = 0; k < 12; ++k) d[k] = s[k];
-  block_sum_to<12>(d, part);
-}
-
-__global__ void __launch_bounds__(256) k_mom_fin2(MomFinArgs a) {
-  __shared__ double tot[12];
-  reduce_parts<12>(a.part, a.nblocks, tot);
-  if (threadIdx.x != 0) return;
-  GaussDev* g = a.gauss;
-  for (int lab = 0; lab < 2; ++lab) {
-    double sw = g->sw[lab];
-    if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
-      for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
-      g->lconst[lab] = 0.f;
-      continue;
-    }
-    const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
-    double c00 = m[0] / sw + 1e-4, c10 = m[1] / sw, c11 = m[2] / sw + 1e-4;
-    double c20 = m[3] / sw, c21 = m[4] / sw, c22 = m[5] / sw + 1e-4;
-    // Cholesky Sigma = L L^T
-    double l00 = sqrt(c00);
-    double l10 = c10 / l00, l20 = c20 / l00;
-    double l11 = sqrt(c11 - l10 * l10);
-    double l21 = (c21 - l20 * l10) / l11;
-    double l22 = sqrt(c22 - l20 * l20 - l21 * l21);
-    // inverse of the lower-triangular factor
-    double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
-    double i10 = -l10 * i00 / l11;
-    double i21 = -l21 * i11 / l22;
-    double i20 = -(l20 * i00 + l21 * i10) / l22;
-    g->linv[lab][0] = (float)i00;
-    g->linv[lab][1] = (float)i10;
-    g->linv[lab][2] = (float)i11;
-    g->linv[lab][3] = (float)i20;
-    g->linv[lab][4] = (float)i21;
-    g->linv[lab][5] = (float)i22;
-    // psi_1 constant: 1/2 log det Sigma + 3/2 log 2 pi, log det = 2 sum log l_ii
-    g->lconst[lab] = (float)(log(l00) + log(l11) + log(l22) + 1.5 * log(2.0 * M_PI));
+  if (block_partial_last<12>(d, f.part, f.counter, blockIdx.x, gridDim.x)) {
+    __shared__ double tot[12];
+    reduce_parts<12>(f.part, gridDim.x, tot);
+    if (threadIdx.x == 0) finalize_cov(tot, f.gauss);
   }
 }
 
@@ -351,7 +390,7 @@ int pt_launch_salmax(seg_ctx* c, const float* sal) {
 }
 
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
-                    double wf_host, float* prior) {
+                    double wf_host, float* prior, const uint8_t* rgb_moments) {
   const seg_params& p = c->p;
   PriorArgs a;
   memset(&a, 0, sizeof(a));
@@ -374,29 +413,31 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   }
   for (int u = 0; u <= 2 * p.f_radius; ++u) a.ftap[u] = (float)(g[u] / sg);
   a.prior = prior;
+  a.rgb = rgb_moments;
+  a.part = c->mom_part;
+  a.counter = c->mom_counter;
+  a.gauss = c->gauss;
+  a.kal_adv = (use_kalman && rgb_moments) ? c->kal : nullptr;
   dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY);
   k_prior<<<grid, 256, 0, c->stream>>>(a);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }
 
-int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int advance_kalman,
+int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
                             int32_t* cs, int32_t* ct, int32_t* ncap) {
   const seg_params& p = c->p;
   cudaStream_t st = c->stream;
   int N = c->N;
   MomFinArgs fa;
   fa.part = c->mom_part;
-  fa.nblocks = c->mom_blocks;
+  fa.counter = c->mom_counter;
   fa.gauss = c->gauss;
-  fa.kal = advance_kalman ? c->kal : nullptr;
+  fa.kal = nullptr;
   fa.a = p.sigma1 * p.sigma1;
   fa.b = p.sigma2 * p.sigma2;
-  k_mom1<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, c->mom_part);
-  k_mom_fin1<<<1, 256, 0, st>>>(fa);
-  k_mom2<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, c->gauss, c->mom_part);
-  fa.kal = nullptr;
-  k_mom_fin2<<<1, 256, 0, st>>>(fa);
+  if (first_pass) k_mom1<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, fa);
+  k_mom2<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, fa);
   TermsArgs ta;
   ta.rgb = rgb;
   ta.prior = prior;
@@ -415,4 +456,10 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   k_terms<<<grid, 256, 0, st>>>(ta);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
+}
+
+int pt_part_doubles(int H, int W) {
+  int prior_blocks = ((W + PR_TX - 1) / PR_TX) * ((H + PR_TY - 1) / PR_TY);
+  int mb = pt_mom_blocks(H, W);
+  return 12 * (prior_blocks > mb ? prior_blocks : mb);
 }

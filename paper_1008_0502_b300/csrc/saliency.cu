@@ -346,39 +346,53 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
 }
 
 // ------------------------------------------------------------------ conspicuity, S
-__device__ void block_norm_ab(const float* v, int h, int w, int T, float flat, float* ab_sh,
-                              double* red) {
-  int n = h * w;
+#define CONSP_MAX_TILES 4096
+
+// Order-preserving map from float to unsigned (so atomicMax works for any sign).
+__device__ __forceinline__ unsigned f2key(float x) {
+  unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// N(.) parameters of one map held in global memory, computed by the whole CTA:
+// min, max and the T x T tile maxima (shared-memory atomics), then the affine
+// form on thread 0.
+__device__ void block_norm_ab(const float* v, int h, int w, int T, float flat, float* ab_sh, float* red,
+                              unsigned* tmax) {
+  const int n = h * w, ntx = (w + T - 1) / T, nt = ntx * ((h + T - 1) / T);
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) tmax[t] = 0u;
+  __syncthreads();
   float mn = 3.0e38f, mx = -3.0e38f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    mn = fminf(mn, v[i]);
-    mx = fmaxf(mx, v[i]);
-  }
-  int ntx = (w + T - 1) / T, nty = (h + T - 1) / T, nt = ntx * nty;
-  double ts = 0.0;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    int ty = t / ntx, tx = t - ty * ntx;
-    float m = -3.0e38f;
-    for (int y = ty * T; y < min(h, ty * T + T); ++y)
-      for (int x = tx * T; x < min(w, tx * T + T); ++x) m = fmaxf(m, v[y * w + x]);
-    ts += m;
+    float x = v[i];
+    mn = fminf(mn, x);
+    mx = fmaxf(mx, x);
+    int yy = i / w, xx = i - yy * w;
+    atomicMax(&tmax[(yy / T) * ntx + xx / T], f2key(x));
   }
   mn = seg_warp_min_f(mn);
   mx = seg_warp_max_f(mx);
-  ts = seg_warp_sum_d(ts);
-  int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    red[3 * wid] = mn;
-    red[3 * wid + 1] = mx;
-    red[3 * wid + 2] = ts;
+    red[wid] = mn;
+    red[32 + wid] = mx;
   }
   __syncthreads();
+  float ts = 0.f;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) ts += key2f(tmax[t]);
+  ts = seg_warp_sum_f(ts);
+  if ((threadIdx.x & 31) == 0) red[64 + wid] = ts;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double a0 = red[0], a1 = red[1], a2 = 0.0;
+    float a0 = red[0], a1 = red[32];
+    double a2 = 0.0;
     for (int i = 0; i < nw; ++i) {
-      a0 = fmin(a0, red[3 * i]);
-      a1 = fmax(a1, red[3 * i + 1]);
-      a2 += red[3 * i + 2];
+      a0 = fminf(a0, red[i]);
+      a1 = fmaxf(a1, red[32 + i]);
+      a2 += red[64 + i];
     }
     norm_affine(a0, a1, a2, nt, flat, ab_sh);
   }
@@ -397,19 +411,20 @@ struct ConspArgs {
 
 __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   __shared__ float ab[2];
-  __shared__ double red[3 * 32];
+  __shared__ float red[3 * 32];
+  __shared__ unsigned tmax[CONSP_MAX_TILES];
   int n = a.h * a.w;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.csum[i] = 0.f;
   for (int k = 3; k < a.nch; ++k) {
     const float* v = a.acc + (size_t)k * n;
-    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red);
+    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red, tmax);
     for (int i = threadIdx.x; i < n; i += blockDim.x) a.csum[i] += ab[0] * v[i] + ab[1];
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.S[i] = 0.f;
   for (int k = 0; k < 4; ++k) {
     const float* v = k < 3 ? a.acc + (size_t)k * n : a.csum;
-    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red);
+    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red, tmax);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       float nv = ab[0] * v[i] + ab[1];
       a.consp[(size_t)k * n + i] = nv;
@@ -500,6 +515,10 @@ int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes) {
     int c = s.pair_c[i];
     if ((s.wl[c] + s.tile - 1) / s.tile > CS_MAX_TILES_X) return SEG_EINVAL;
     s.nbands_total += s.nch * ((s.hl[c] + s.tile - 1) / s.tile);
+  }
+  {
+    int hS = s.hl[s.sS], wS = s.wl[s.sS];
+    if (((hS + s.tile - 1) / s.tile) * ((wS + s.tile - 1) / s.tile) > CONSP_MAX_TILES) return SEG_EINVAL;
   }
   make_taps(p, s.taps);
   size_t off = 0;

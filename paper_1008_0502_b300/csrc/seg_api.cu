@@ -48,7 +48,7 @@ extern "C" int seg_default_params(seg_params* p) {
   p->cap_scale = 1000.0;
   p->neighbourhood = 8;
   p->max_cycles = 20000;
-  p->global_relabel_every = 4;
+  p->global_relabel_every = 2;
   p->local_iters = 16;
   return SEG_OK;
 }
@@ -117,10 +117,11 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
     return o;
   };
   size_t o_kal = take(sizeof(KalmanDev)), o_gauss = take(sizeof(GaussDev));
-  size_t o_mom = take(sizeof(double) * 12 * c->mom_blocks), o_lut = take(sizeof(int) * 766 * 2);
+  size_t o_mom = take(sizeof(double) * pt_part_doubles(H, W)), o_lut = take(sizeof(int) * 766 * 2);
+  size_t o_cnt = take(sizeof(unsigned));
   size_t o_prev = take(N), o_cs = take(4 * N), o_ct = take(4 * N), o_ncap = take(4 * N * nk);
   size_t o_sal = take(4 * N), o_prior = take(4 * N), o_mask = take(N), o_cut = take(8);
-  size_t o_rgb = take(3 * N), o_status = take(16);
+  size_t o_rgb = take(3 * N), o_status = take(32);
   size_t o_mf = take(mf_bytes(H, W, p->neighbourhood));
   char* base = nullptr;
   if (cudaMalloc((void**)&base, off) != cudaSuccess) {
@@ -132,6 +133,7 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
   c->kal = (KalmanDev*)(base + o_kal);
   c->gauss = (GaussDev*)(base + o_gauss);
   c->mom_part = (double*)(base + o_mom);
+  c->mom_counter = (unsigned*)(base + o_cnt);
   c->lut = (int*)(base + o_lut);
   c->prev_mask = (uint8_t*)(base + o_prev);
   c->cs = (int32_t*)(base + o_cs);
@@ -150,8 +152,9 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
   free(lut);
   ok = ok && cudaMemset(c->kal, 0, sizeof(KalmanDev)) == cudaSuccess;
   ok = ok && cudaMemset(c->prev_mask, 0, N) == cudaSuccess;
-  ok = ok && cudaMemset(c->status, 0, 16) == cudaSuccess;
-  ok = ok && cudaMallocHost((void**)&c->status_host, 16) == cudaSuccess;
+  ok = ok && cudaMemset(c->status, 0, 32) == cudaSuccess;
+  ok = ok && cudaMemset(c->mom_counter, 0, sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
   ok = ok && mf_grid_size(H, W, &c->mf_grid) == SEG_OK;
   if (!ok) {
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -199,14 +202,14 @@ extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float*
   prof_mark(c, 0);
   int rc = sal_launch(c, rgb, s);
   prof_mark(c, 1);
-  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr);
+  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb);
   prof_mark(c, 2);
-  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 1, c->cs, c->ct, c->ncap);
+  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
   prof_mark(c, 3);
   if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
   prof_mark(c, 4);
   if (!rc && c->prof_on && c->prof_n < c->prof_cap) {
-    SEG_CUDA_TRY(cudaMemcpyAsync(c->prof_cycles + c->prof_n, c->status + 1, sizeof(int),
+    SEG_CUDA_TRY(cudaMemcpyAsync(c->prof_cycles + 7 * c->prof_n, c->status + 1, 7 * sizeof(int),
                                  cudaMemcpyDeviceToDevice, c->stream));
     c->prof_n++;
   }
@@ -239,7 +242,7 @@ extern "C" int seg_profile_enable(seg_ctx* c, int on) {
         prof_free(c);
         return SEG_ECUDA;
       }
-    if (cudaMalloc((void**)&c->prof_cycles, sizeof(int) * cap) != cudaSuccess) {
+    if (cudaMalloc((void**)&c->prof_cycles, 7 * sizeof(int) * cap) != cudaSuccess) {
       prof_free(c);
       return SEG_ENOMEM;
     }
@@ -250,20 +253,27 @@ extern "C" int seg_profile_enable(seg_ctx* c, int on) {
 
 extern "C" int seg_profile_read(seg_ctx* c, double* stage_ms, int* frames, long long* cycles,
                                 float* frame_ms, int max_frames) {
+  return seg_profile_read_ex(c, stage_ms, frames, cycles, frame_ms, nullptr, max_frames);
+}
+
+extern "C" int seg_profile_read_ex(seg_ctx* c, double* stage_ms, int* frames, long long* cycles,
+                                   float* frame_ms, int* mincut_stats, int max_frames) {
   if (!c || !stage_ms || !frames || !cycles) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
   for (int k = 0; k < 4; ++k) stage_ms[k] = 0.0;
   *frames = c->prof_n;
   *cycles = 0;
   if (c->prof_n == 0) return SEG_OK;
-  int* cyc = (int*)malloc(sizeof(int) * c->prof_n);
+  int* cyc = (int*)malloc(7 * sizeof(int) * c->prof_n);
   if (!cyc) return SEG_ENOMEM;
-  if (cudaMemcpy(cyc, c->prof_cycles, sizeof(int) * c->prof_n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+  if (cudaMemcpy(cyc, c->prof_cycles, 7 * sizeof(int) * c->prof_n, cudaMemcpyDeviceToHost) != cudaSuccess) {
     free(cyc);
     return SEG_ECUDA;
   }
   for (int f = 0; f < c->prof_n; ++f) {
-    *cycles += cyc[f];
+    *cycles += cyc[7 * f];
+    if (mincut_stats && f < max_frames)
+      for (int k = 0; k < 7; ++k) mincut_stats[7 * f + k] = cyc[7 * f + k];
     for (int k = 0; k < 4; ++k) {
       float ms = 0.f;
       SEG_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[5 * f + k], c->prof_ev[5 * f + k + 1]));
@@ -282,7 +292,7 @@ extern "C" int seg_profile_read(seg_ctx* c, double* stage_ms, int* frames, long 
 extern "C" int seg_sync(seg_ctx* c, int* cycles) {
   if (!c) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  SEG_CUDA_TRY(cudaMemcpy(c->status_host, c->status, 16, cudaMemcpyDeviceToHost));
+  SEG_CUDA_TRY(cudaMemcpy(c->status_host, c->status, 32, cudaMemcpyDeviceToHost));
   if (cycles) *cycles = c->status_host[1];
   int code = c->status_host[0];
   if (code) SEG_CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
@@ -353,13 +363,13 @@ extern "C" int seg_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask,
   if (!c || !sal || !prior || !(w_f >= 0.0 && w_f <= 1.0)) return SEG_EINVAL;
   if (w_f != 0.0 && !prev_mask) return SEG_EINVAL;
   int rc = pt_launch_salmax(c, sal);  // q = saliency / max(saliency) of THIS map
-  return rc ? rc : pt_launch_prior(c, sal, prev_mask, 0, w_f, prior);
+  return rc ? rc : pt_launch_prior(c, sal, prev_mask, 0, w_f, prior, nullptr);
 }
 
 extern "C" int seg_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct,
                          int32_t* ncap) {
   if (!c || !rgb || !prior || !cs || !ct || !ncap) return SEG_EINVAL;
-  return pt_launch_moments_terms(c, rgb, prior, 0, cs, ct, ncap);
+  return pt_launch_moments_terms(c, rgb, prior, 1, cs, ct, ncap);
 }
 
 extern "C" int seg_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
@@ -381,13 +391,13 @@ extern "C" int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_
   if (rc) return rc;
   size_t mfb = mf_bytes(H, W, nbr);
   char* base = nullptr;
-  if (cudaMalloc((void**)&base, mfb + 256 + 256) != cudaSuccess) return SEG_ENOMEM;
+  if (cudaMalloc((void**)&base, seg_align(mfb) + 256) != cudaSuccess) return SEG_ENOMEM;
   MFWS m;
   mf_bind(m, base, H, W, nbr);
   int* status = (int*)(base + seg_align(mfb));
   long long* cut_tmp = (long long*)(base + seg_align(mfb) + 128);
   rc = SEG_OK;
-  if (cudaMemsetAsync(status, 0, 16, st) != cudaSuccess) rc = SEG_ECUDA;
+  if (cudaMemsetAsync(status, 0, 32, st) != cudaSuccess) rc = SEG_ECUDA;
   if (!rc)
     rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, cut ? (long long*)cut : cut_tmp,
                    status, max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every,

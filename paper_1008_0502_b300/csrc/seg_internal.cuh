@@ -163,8 +163,11 @@ struct MFArgs {
   long long* cut_out;   // nullable
   unsigned long long* cut_acc;
   unsigned int* flags;  // [3] rotating round counters
+  int* tstamp;           // per tile: last round (epoch) in which a fixpoint changed it
+  unsigned char* tact;   // per tile: may hold an active node
   GridBar* bar;
-  int* status;  // [0] error code, [1] cycles, [2] global relabels, [3] bfs rounds
+  int* status;  // [0] error code, [1] cycles, [2] global relabels, [3] fixpoint rounds,
+               // [4..7] time in init / global relabel / discharge / reach, 0.1 us units
   int max_cycles, gr_every, local_iters;
   long long timeout_ns;
 };
@@ -178,6 +181,8 @@ struct MFWS {
   unsigned char* z;
   unsigned long long* cut_acc;
   unsigned int* flags;
+  int* tstamp;
+  unsigned char* tact;
   GridBar* bar;
 };
 
@@ -192,6 +197,7 @@ struct seg_ctx {
   KalmanDev* kal;
   GaussDev* gauss;
   double* mom_part;
+  unsigned* mom_counter;  // last-CTA counter of the moment passes (returns to 0)
   int mom_blocks;
   int* lut;  // [766][2] n-link capacities by |delta(r+g+b)| and diagonal flag
   uint8_t* prev_mask;
@@ -202,8 +208,8 @@ struct seg_ctx {
   uint8_t* rgb_stage;
   MFWS mf;
   int mf_grid;
-  int* status;       // device [4]
-  int* status_host;  // pinned [4]
+  int* status;       // device [8]
+  int* status_host;  // pinned [8]
   // optional per-stage timing (seg_profile_enable)
   int prof_on, prof_n, prof_cap;
   cudaEvent_t* prof_ev;  // 5 per frame
@@ -217,10 +223,13 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);
 
 int pt_mom_blocks(int H, int W);
 int pt_launch_salmax(seg_ctx* c, const float* sal);
+// rgb_moments != nullptr: also run the first moment pass (and, with use_kalman,
+// advance the Kalman variance) inside the prior kernel
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
-                    double wf_host, float* prior);
-int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int advance_kalman,
+                    double wf_host, float* prior, const uint8_t* rgb_moments);
+int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
                             int32_t* cs, int32_t* ct, int32_t* ncap);
+int pt_part_doubles(int H, int W);
 void pt_fill_lut(const seg_params& p, int* lut_host);
 
 size_t mf_bytes(int H, int W, int ndir);

@@ -72,6 +72,7 @@ def _load():
         "seg_level_dim": ([i32, i32], i32),
         "seg_profile_enable": ([vp, i32], i32),
         "seg_profile_read": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, i32], i32),
+        "seg_profile_read_ex": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -223,9 +224,12 @@ class Segmenter:
         n = C.c_int(0)
         cyc = C.c_longlong(0)
         fr = (C.c_float * max_frames)()
-        _check(lib.seg_profile_read(self.handle, ms, C.byref(n), C.byref(cyc), fr, max_frames), "seg_profile_read")
+        st = (C.c_int * (7 * max_frames))()
+        _check(lib.seg_profile_read_ex(self.handle, ms, C.byref(n), C.byref(cyc), fr, st, max_frames),
+               "seg_profile_read_ex")
         k = min(n.value, max_frames)
-        return {"stage_ms": list(ms), "frames": n.value, "cycles": cyc.value, "frame_ms": list(fr[:k])}
+        return {"stage_ms": list(ms), "frames": n.value, "cycles": cyc.value, "frame_ms": list(fr[:k]),
+                "mincut_stats": [tuple(st[7 * i:7 * i + 7]) for i in range(k)]}
 
     # --- stage entry points
     def saliency(self, rgb, out=None):
