@@ -70,7 +70,7 @@ __device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
 template <int NV>
 __device__ void reduce_parts(const double* part, int nblocks, double* out);
 template <int NV>
-__device__ bool block_partial_last(const double* v, double* part, unsigned* counter, int bid,
+__device__ bool block_partial_last(const float* v, double* part, unsigned* counter, int bid,
                                    int nblocks);
 __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b);
 
@@ -122,10 +122,8 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     if (a.rgb) mom1_add(p, a.rgb + 3 * g, ms);
   }
   if (a.rgb) {
-    double d[8];
-    for (int k = 0; k < 8; ++k) d[k] = ms[k];
     const int nb = gridDim.x * gridDim.y;
-    if (block_partial_last<8>(d, a.part, a.counter, blockIdx.y * gridDim.x + blockIdx.x, nb)) {
+    if (block_partial_last<8>(ms, a.part, a.counter, blockIdx.y * gridDim.x + blockIdx.x, nb)) {
       __shared__ double tot[8];
       reduce_parts<8>(a.part, nb, tot);
       if (threadIdx.x == 0) finalize_means(tot, a.gauss, a.kal_adv, a.a, a.b);
@@ -135,15 +133,17 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
 
 // Writes this CTA's NV partial sums to part[bid*NV ..] and returns true in
 // every thread of exactly one CTA, the last to finish (threadfence reduction).
+// Sums inside the CTA are FP32 (a CTA covers at most a few thousand pixels);
+// the per-CTA partials and everything across CTAs are FP64.
 template <int NV>
-__device__ bool block_partial_last(const double* v, double* part, unsigned* counter, int bid,
+__device__ bool block_partial_last(const float* v, double* part, unsigned* counter, int bid,
                                    int nblocks) {
-  __shared__ double red[32][NV];
+  __shared__ float red[32][NV];
   __shared__ int is_last;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = seg_warp_sum_d(v[k]);
+    float s = seg_warp_sum_f(v[k]);
     if (lane == 0) red[wid][k] = s;
   }
   __syncthreads();
@@ -241,9 +241,7 @@ __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
   float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
     mom1_add(prior[i], rgb + 3 * (size_t)i, s);
-  double d[8];
-  for (int k = 0; k < 8; ++k) d[k] = s[k];
-  if (block_partial_last<8>(d, f.part, f.counter, blockIdx.x, gridDim.x)) {
+  if (block_partial_last<8>(s, f.part, f.counter, blockIdx.x, gridDim.x)) {
     __shared__ double tot[8];
     reduce_parts<8>(f.part, gridDim.x, tot);
     if (threadIdx.x == 0) finalize_means(tot, f.gauss, f.kal, f.a, f.b);
@@ -279,9 +277,7 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
     s[10] += p * db * dg;
     s[11] += p * db * db;
   }
-  double d[12];
-  for (int k = 0; k < 12; ++k) d[k] = s[k];
-  if (block_partial_last<12>(d, f.part, f.counter, blockIdx.x, gridDim.x)) {
+  if (block_partial_last<12>(s, f.part, f.counter, blockIdx.x, gridDim.x)) {
     __shared__ double tot[12];
     reduce_parts<12>(f.part, gridDim.x, tot);
     if (threadIdx.x == 0) finalize_cov(tot, f.gauss);

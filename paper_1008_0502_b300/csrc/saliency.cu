@@ -143,6 +143,38 @@ __global__ void __launch_bounds__(256) k_reduce3(Reduce3Args a) {
   }
 }
 
+// The small pyramid levels in one launch: CTA = channel, levels computed one
+// after another from global memory (L1/L2 resident), a barrier between levels.
+struct PyrTailArgs {
+  float* lvl[3][SEG_MAX_LEVELS];
+  int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
+  int from, to;  // produce levels from+1 .. to
+};
+
+__global__ void __launch_bounds__(1024) k_pyr_tail(PyrTailArgs a) {
+  const int ch = blockIdx.x;
+  for (int l = a.from; l < a.to; ++l) {
+    const float* __restrict__ in = a.lvl[ch][l];
+    float* __restrict__ out = a.lvl[ch][l + 1];
+    const int h = a.hl[l], w = a.wl[l], h2 = a.hl[l + 1], w2 = a.wl[l + 1];
+    for (int i = threadIdx.x; i < h2 * w2; i += blockDim.x) {
+      int y = i / w2, x = i - y * w2;
+      int xs[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) xs[k] = seg_clampi(2 * x + k - 2, 0, w - 1);
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        const float* row = in + (size_t)seg_clampi(2 * y + j - 2, 0, h - 1) * w;
+        acc += c_binom[j] * (c_binom[0] * row[xs[0]] + c_binom[1] * row[xs[1]] + c_binom[2] * row[xs[2]] +
+                             c_binom[3] * row[xs[3]] + c_binom[4] * row[xs[4]]);
+      }
+      out[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ Gabor
 #define GB_TX 32
 #define GB_TY 16
@@ -305,31 +337,31 @@ __device__ __forceinline__ void norm_affine(double mn, double mx, double sum_tma
   ab[1] = (float)(-mn * a);
 }
 
-__global__ void k_cs_norm(CSArgs a, float flat, float* nab) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= a.npairs * a.nch) return;
-  int p = m / a.nch, f = m - p * a.nch;
+// N(.) of map m = (pair p, channel f) as a*v + b from its statistics.
+__device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* ab) {
   int c = a.pair_c[p];
   int T = a.tile, nb = (a.hl[c] + T - 1) / T, ntx = (a.wl[c] + T - 1) / T;
+  int m = p * a.nch + f;
   double sum = 0.0;
   const float* tp = a.tpart + a.pair_band_off[p] + f * nb;
   for (int i = 0; i < nb; ++i) sum += tp[i];
-  norm_affine(__uint_as_float(a.mm[2 * m]), __uint_as_float(a.mm[2 * m + 1]), sum, nb * ntx, flat,
-              nab + 2 * m);
+  norm_affine(__uint_as_float(a.mm[2 * m]), __uint_as_float(a.mm[2 * m + 1]), sum, nb * ntx, flat, ab);
 }
 
 // B_c(f) = sum over pairs (c, s) of N(CS_f(c, s)) + REDUCE(B_{c-1}(f)).
-__global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* __restrict__ prev,
+__global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, float flat, const float* __restrict__ prev,
                                                   int hp, int wp, float* __restrict__ out) {
+  __shared__ float sab[SEG_MAX_PAIRS][2];
   int f = blockIdx.z;
+  if ((int)threadIdx.x < a.npairs && a.pair_c[threadIdx.x] == c) cs_map_affine(a, threadIdx.x, f, flat, sab[threadIdx.x]);
+  __syncthreads();
   int hc = a.hl[c], wc = a.wl[c];
   int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= wc || y >= hc) return;
   float acc = 0.f;
   for (int p = 0; p < a.npairs; ++p) {
     if (a.pair_c[p] != c) continue;
-    int m = p * a.nch + f;
-    acc += a.nab[2 * m] * cs_value(a, f, c, a.pair_s[p], y, x) + a.nab[2 * m + 1];
+    acc += sab[p][0] * cs_value(a, f, c, a.pair_s[p], y, x) + sab[p][1];
   }
   if (prev) {
     const float* pl = prev + (size_t)f * hp * wp;
@@ -346,7 +378,6 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
 }
 
 // ------------------------------------------------------------------ conspicuity, S
-#define CONSP_MAX_TILES 4096
 
 // Order-preserving map from float to unsigned (so atomicMax works for any sign).
 __device__ __forceinline__ unsigned f2key(float x) {
@@ -357,44 +388,60 @@ __device__ __forceinline__ float key2f(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// N(.) parameters of one map held in global memory, computed by the whole CTA:
-// min, max and the T x T tile maxima (shared-memory atomics), then the affine
-// form on thread 0.
-__device__ void block_norm_ab(const float* v, int h, int w, int T, float flat, float* ab_sh, float* red,
-                              unsigned* tmax) {
+#define CONSP_TILES 1024  // N(.) tiles per map at sigma_S
+
+// N(.) parameters of up to four maps held in global memory, computed by the
+// whole CTA in one pass over the pixels: min, max and the T x T tile maxima
+// (shared-memory atomics on order-preserving keys), then each map's affine
+// form on one thread.  ab[2m], ab[2m+1] receive map m's a and b.
+__device__ void block_norm_multi(const float* const* v, int nm, int h, int w, int T, float flat,
+                                 float* ab, float* red, unsigned* tmax) {
   const int n = h * w, ntx = (w + T - 1) / T, nt = ntx * ((h + T - 1) / T);
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) tmax[t] = 0u;
+  for (int t = threadIdx.x; t < nm * CONSP_TILES; t += blockDim.x) tmax[t] = 0u;
   __syncthreads();
-  float mn = 3.0e38f, mx = -3.0e38f;
+  float mn[4] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f}, mx[4] = {-3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float x = v[i];
-    mn = fminf(mn, x);
-    mx = fmaxf(mx, x);
-    int yy = i / w, xx = i - yy * w;
-    atomicMax(&tmax[(yy / T) * ntx + xx / T], f2key(x));
+    int yy = i / w, xx = i - yy * w, tile = (yy / T) * ntx + xx / T;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (m >= nm) break;
+      float x = v[m][i];
+      mn[m] = fminf(mn[m], x);
+      mx[m] = fmaxf(mx[m], x);
+      atomicMax(&tmax[m * CONSP_TILES + tile], f2key(x));
+    }
   }
-  mn = seg_warp_min_f(mn);
-  mx = seg_warp_max_f(mx);
   const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[wid] = mn;
-    red[32 + wid] = mx;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float a0 = seg_warp_min_f(mn[m]), a1 = seg_warp_max_f(mx[m]);
+    if ((threadIdx.x & 31) == 0) {
+      red[(3 * m) * 32 + wid] = a0;
+      red[(3 * m + 1) * 32 + wid] = a1;
+    }
   }
   __syncthreads();
-  float ts = 0.f;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) ts += key2f(tmax[t]);
-  ts = seg_warp_sum_f(ts);
-  if ((threadIdx.x & 31) == 0) red[64 + wid] = ts;
+  float ts[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int t = threadIdx.x; t < nt; t += blockDim.x)
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (m < nm) ts[m] += key2f(tmax[m * CONSP_TILES + t]);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float a2 = seg_warp_sum_f(ts[m]);
+    if ((threadIdx.x & 31) == 0) red[(3 * m + 2) * 32 + wid] = a2;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float a0 = red[0], a1 = red[32];
+  if ((int)threadIdx.x < nm) {
+    const int m = threadIdx.x;
+    float a0 = red[(3 * m) * 32], a1 = red[(3 * m + 1) * 32];
     double a2 = 0.0;
     for (int i = 0; i < nw; ++i) {
-      a0 = fminf(a0, red[i]);
-      a1 = fmaxf(a1, red[32 + i]);
-      a2 += red[64 + i];
+      a0 = fminf(a0, red[(3 * m) * 32 + i]);
+      a1 = fmaxf(a1, red[(3 * m + 1) * 32 + i]);
+      a2 += red[(3 * m + 2) * 32 + i];
     }
-    norm_affine(a0, a1, a2, nt, flat, ab_sh);
+    norm_affine(a0, a1, a2, nt, flat, ab + 2 * m);
   }
   __syncthreads();
 }
@@ -409,28 +456,39 @@ struct ConspArgs {
   float* S;
 };
 
+// Orientation conspicuity sum_theta N(B_theta), then N of the four conspicuity
+// maps and S = sum_k w_k N(C_k): two normalisation passes of up to 4 maps each.
 __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
-  __shared__ float ab[2];
-  __shared__ float red[3 * 32];
-  __shared__ unsigned tmax[CONSP_MAX_TILES];
-  int n = a.h * a.w;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a.csum[i] = 0.f;
-  for (int k = 3; k < a.nch; ++k) {
-    const float* v = a.acc + (size_t)k * n;
-    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red, tmax);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a.csum[i] += ab[0] * v[i] + ab[1];
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a.S[i] = 0.f;
-  for (int k = 0; k < 4; ++k) {
-    const float* v = k < 3 ? a.acc + (size_t)k * n : a.csum;
-    block_norm_ab(v, a.h, a.w, a.tile, a.flat, ab, red, tmax);
+  __shared__ float ab[8];
+  __shared__ float red[12 * 32];
+  __shared__ unsigned tmax[4 * CONSP_TILES];
+  const int n = a.h * a.w;
+  const float* v[4];
+  for (int k0 = 3; k0 < a.nch; k0 += 4) {
+    const int nm = min(4, a.nch - k0);
+    for (int m = 0; m < nm; ++m) v[m] = a.acc + (size_t)(k0 + m) * n;
+    block_norm_multi(v, nm, a.h, a.w, a.tile, a.flat, ab, red, tmax);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      float nv = ab[0] * v[i] + ab[1];
-      a.consp[(size_t)k * n + i] = nv;
-      a.S[i] += a.wgt[k] * nv;
+      float acc = k0 == 3 ? 0.f : a.csum[i];
+      for (int m = 0; m < nm; ++m) acc += ab[2 * m] * v[m][i] + ab[2 * m + 1];
+      a.csum[i] = acc;
     }
     __syncthreads();
+  }
+  v[0] = a.acc;
+  v[1] = a.acc + n;
+  v[2] = a.acc + 2 * (size_t)n;
+  v[3] = a.csum;
+  block_norm_multi(v, 4, a.h, a.w, a.tile, a.flat, ab, red, tmax);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float S = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float nv = ab[2 * k] * v[k][i] + ab[2 * k + 1];
+      a.consp[(size_t)k * n + i] = nv;
+      S += a.wgt[k] * nv;
+    }
+    a.S[i] = S;
   }
 }
 
@@ -518,7 +576,7 @@ int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes) {
   }
   {
     int hS = s.hl[s.sS], wS = s.wl[s.sS];
-    if (((hS + s.tile - 1) / s.tile) * ((wS + s.tile - 1) / s.tile) > CONSP_MAX_TILES) return SEG_EINVAL;
+    if (((hS + s.tile - 1) / s.tile) * ((wS + s.tile - 1) / s.tile) > CONSP_TILES) return SEG_EINVAL;
   }
   make_taps(p, s.taps);
   size_t off = 0;
@@ -606,7 +664,14 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY);
   k_feat_reduce1<<<g1, 256, 0, st>>>(rgb, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1], s.hl[1],
                                      s.wl[1]);
-  for (int l = 1; l + 1 < s.L; ++l) {
+  // tiled launches while the produced level is large; one tail launch for the rest
+  int tail_from = s.L - 1;
+  for (int l = 1; l + 1 < s.L; ++l)
+    if ((long long)s.hl[l + 1] * s.wl[l + 1] <= 8192) {
+      tail_from = l;
+      break;
+    }
+  for (int l = 1; l + 1 < s.L && l < tail_from; ++l) {
     Reduce3Args ra;
     for (int ch = 0; ch < 3; ++ch) {
       ra.in[ch] = s.pyr[ch][l];
@@ -618,6 +683,18 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
     ra.w2 = s.wl[l + 1];
     dim3 g((ra.w2 + RED_TX - 1) / RED_TX, (ra.h2 + RED_TY - 1) / RED_TY, 3);
     k_reduce3<<<g, 256, 0, st>>>(ra);
+  }
+  if (tail_from < s.L - 1) {
+    PyrTailArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    for (int l = 1; l < s.L; ++l) {
+      for (int ch = 0; ch < 3; ++ch) ta.lvl[ch][l] = s.pyr[ch][l];
+      ta.hl[l] = s.hl[l];
+      ta.wl[l] = s.wl[l];
+    }
+    ta.from = tail_from;
+    ta.to = s.L - 1;
+    k_pyr_tail<<<3, 1024, 0, st>>>(ta);
   }
   GaborArgs ga;
   memset(&ga, 0, sizeof(ga));
@@ -637,13 +714,12 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   CSArgs ca;
   fill_cs_args(s, ca);
   k_cs_stats<<<s.nbands_total, 256, 0, st>>>(ca);
-  k_cs_norm<<<(s.nmaps + 127) / 128, 128, 0, st>>>(ca, s.flat, s.nab);
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;
   for (int cc = s.c_min; cc <= s.c_max; ++cc) {
     dim3 g((s.wl[cc] + 31) / 32, (s.hl[cc] + 7) / 8, s.nch);
-    k_cs_accum<<<g, 256, 0, st>>>(ca, cc, prev, hp, wp, s.acc[cur]);
+    k_cs_accum<<<g, 256, 0, st>>>(ca, cc, s.flat, prev, hp, wp, s.acc[cur]);
     prev = s.acc[cur];
     hp = s.hl[cc];
     wp = s.wl[cc];
