@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "640x480 frames/s (saliency+Kalman+min-cut, 1 B300) vs plain; p99 frame latency"
 H, W = 480, 640
 BYTES_MINCUT_SWEEP_PX = 24  # excess 4 B + height 4 B + 4 undirected n-link flows x 4 B (8-neighbour)
+# DRAM bytes (read + write) of one k_maxflow<8> launch on a 640x480 frame graph, from the
+# ncu capture summarised in profiles/k_maxflow_640x480.md; None once the kernel changes
+TRAFFIC_MAXFLOW = 7408896
 VGA = dict(levels=9, c_min=2, c_max=4, d_min=3, d_max=4, n_orient=4, gabor_lambda=4.0, gabor_sigma=2.0,
            gabor_radius=6, norm_tile=8, norm_flat=1e-5, w=(1 / 3, 1 / 6, 1 / 6, 1 / 3), cs_opponent_sum=1,
            border_px=1, sigma1=0.03, sigma2=0.035, f_sigma=2.0, f_radius=6, eps=1e-4, lambda_u=1.0,
@@ -112,9 +115,20 @@ def peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
-def kernels_per_frame(p):
-    sal = 1 + 1 + (p["levels"] - 2) + 1 + 1 + 1 + (p["c_max"] - p["c_min"] + 1) + 1 + 1
-    return sal + 4  # + prior (with the first moment pass), second moment pass, terms, min cut
+def kernels_per_frame(p, H=480, W=640, graph=True):
+    """Kernels one seg_push_frame launches (memsets excluded), as the library sequences them."""
+    dims = [(H, W)]
+    for _ in range(p["levels"] - 1):
+        h, w = dims[-1]
+        dims.append(((h + 1) // 2, (w + 1) // 2))
+    tiled = 0
+    for l in range(1, p["levels"] - 1):
+        if dims[l + 1][0] * dims[l + 1][1] <= 8192:
+            break
+        tiled += 1
+    tail = 1 if 1 + tiled < p["levels"] - 1 else 0
+    sal = 2 + tiled + tail + 1 + 1 + (p["c_max"] - p["c_min"] + 1) + 1 + 1
+    return sal + 3 + 1 + (1 if graph else 0)  # prior, moments, terms; min cut; frame-pointer record
 
 
 def cpu_baseline(clip, seconds, max_frames=None):
@@ -193,6 +207,7 @@ def run_b300(a):
     p = seg.params_from(VGA)
     sg = seg.Segmenter(H, W, p)
     sal, pr, mask, cut = sg.empty_outputs()
+    st = sg.stream
     for i in range(a.warmup):
         f = i % len(clip)
         if f == 0:
@@ -202,20 +217,24 @@ def run_b300(a):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    sg.profile_enable(True)
+    # timed region: per-frame CUDA graph replays on the context's stream, one
+    # event pair per frame for the latency distribution
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     clk = Clocks(local)
     time.sleep(0.3)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
+    ev0.record(st)
     for i in range(a.steps):
         f = (a.warmup + i) % len(clip)
         if f == 0:
             sg.reset()
+        evs[i][0].record(st)
         sg.push_frame(clip_dev[f], sal, pr, mask, cut)
-    ev1.record()
+        evs[i][1].record(st)
+    ev1.record(st)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -224,11 +243,18 @@ def run_b300(a):
     if code != 0:
         raise RuntimeError(f"device status {seg.strerror(code)}")
     value, t = aggregate(ev0.elapsed_time(ev1) / 1e3, a.steps, ws, device="cuda")
+    lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+
+    # per-stage split and min-cut statistics: a second pass over the clip with
+    # events between the stages (eager launches)
+    sg.reset()
+    sg.profile_enable(True)
+    for f in range(min(a.steps, len(clip))):
+        sg.push_frame(clip_dev[f], sal, pr, mask, cut)
     prof = sg.profile_read()
     sg.profile_enable(False)
     nfr = prof["frames"]
-    stage = [s / nfr for s in prof["stage_ms"]]
-    lat = np.array(prof["frame_ms"])
+    stage = [x / nfr for x in prof["stage_ms"]]
     cycles = prof["cycles"] / nfr
 
     # end to end through the host-buffer entry point
@@ -248,20 +274,14 @@ def run_b300(a):
     pk, pk_kind = peaks()
     hbm = float(pk["hbm_gbs"])
     names = ["saliency", "prior", "terms", "mincut"]
-    dom = int(np.argmax(stage))
+    # the dominant kernel (largest share of the ncu launch list) is k_maxflow: the
+    # min-cut stage is that one kernel plus three small memsets
     mincut_bytes = BYTES_MINCUT_SWEEP_PX * H * W * cycles
-    if names[dom] == "mincut":
-        ach = mincut_bytes / (stage[3] * 1e-3) / 1e9
-        roof = {"kernel": "k_maxflow", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None,
-                "algorithmic_bytes": f"{BYTES_MINCUT_SWEEP_PX} B/px/sweep x {H * W} px x {cycles:.1f} sweeps",
-                "peak_kind": pk_kind}
-    else:
-        per_px = {"saliency": 7, "prior": 9, "terms": 3 + 4 + 24 + 4}[names[dom]]
-        ach = per_px * H * W / (stage[dom] * 1e-3) / 1e9
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "algorithmic_bytes": f"{per_px} B/px x {H * W} px",
-                "peak_kind": pk_kind}
+    ach = mincut_bytes / (stage[3] * 1e-3) / 1e9
+    roof = {"kernel": "k_maxflow<8>", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": TRAFFIC_MAXFLOW,
+            "algorithmic_bytes": f"{BYTES_MINCUT_SWEEP_PX} B/px/sweep x {H * W} px x {cycles:.2f} sweeps",
+            "peak_kind": pk_kind}
     n_cpu, dt_cpu = cpu_baseline(clip, a.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": a.steps,

@@ -77,6 +77,8 @@ typedef struct seg_params {
   int32_t max_cycles;      /* min-cut cycle cap -> SEG_ENOTCONVERGED (20000) */
   int32_t global_relabel_every; /* min-cut cycles between global relabels (2) */
   int32_t local_iters;     /* push/relabel iterations per tile visit (16) */
+  int32_t use_graph;       /* 1: seg_push_frame replays one captured CUDA graph per frame (when the
+                              context's stream is not the legacy default stream); 0: eager launches */
 } seg_params;
 
 /* Fills *p with the defaults above.  Returns SEG_EINVAL if p is NULL. */

@@ -460,13 +460,15 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
       return;
     }
   }
+  uint8_t* mask_out = a.mask_out ? a.mask_out : a.io->mask;
   for (int u = gtid; u < N; u += nthr) {
     uint8_t v = a.z[u];
-    a.mask_out[u] = v;
+    mask_out[u] = v;
     if (a.mask_state) a.mask_state[u] = v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (a.cut_out) *a.cut_out = (long long)*(volatile unsigned long long*)a.cut_acc;
+    long long* cut_out = a.cut_out ? a.cut_out : (a.io ? a.io->cut : nullptr);
+    if (cut_out) *cut_out = (long long)*(volatile unsigned long long*)a.cut_acc;
     if (!converged) atomicCAS(&a.status[0], 0, SEG_ENOTCONVERGED);
     a.status[1] = cycle;
     a.status[2] = n_gr;
@@ -525,7 +527,8 @@ int mf_grid_size(int H, int W, int* grid) {
 
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
-              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters) {
+              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
+              const SegIO* io) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
   a.H = H;
@@ -546,6 +549,7 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   a.mask_out = mask_out;
   a.mask_state = mask_state;
   a.cut_out = cut_out;
+  a.io = io;
   a.cut_acc = m.cut_acc;
   a.flags = m.flags;
   a.tstamp = m.tstamp;

@@ -44,6 +44,7 @@ struct PriorArgs {
   unsigned* counter;
   GaussDev* gauss;
   KalmanDev* kal_adv;  // nullable: advance the variance recursion
+  const SegIO* io;     // sal / prior / rgb == nullptr: take them from here
 };
 
 struct MomFinArgs {
@@ -52,6 +53,7 @@ struct MomFinArgs {
   GaussDev* gauss;
   KalmanDev* kal;  // nullable: advance the variance recursion
   double a, b;
+  const SegIO* io;  // rgb / prior == nullptr: take them from here
 };
 
 __device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
@@ -75,6 +77,11 @@ __device__ bool block_partial_last(const float* v, double* part, unsigned* count
 __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b);
 
 __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
+  if (a.io) {
+    if (!a.sal) a.sal = a.io->sal;
+    if (!a.prior) a.prior = a.io->prior;
+    if (!a.rgb) a.rgb = a.io->rgb;
+  }
   __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
   __shared__ float sH[PR_TY + 2 * PR_MAXR][PR_TX];
   double wf = a.wf_host;
@@ -250,6 +257,8 @@ __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
 
 __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
                                               const float* __restrict__ prior, int N, MomFinArgs f) {
+  if (!rgb) rgb = f.io->rgb;
+  if (!prior) prior = f.io->prior;
   const GaussDev* gauss = f.gauss;
   float m0r = gauss->muf[0][0], m0g = gauss->muf[0][1], m0b = gauss->muf[0][2];
   float m1r = gauss->muf[1][0], m1g = gauss->muf[1][1], m1b = gauss->muf[1][2];
@@ -294,6 +303,7 @@ struct TermsArgs {
   int32_t* cs;
   int32_t* ct;
   int32_t* ncap;
+  const SegIO* io;  // rgb / prior == nullptr: take them from here
 };
 
 __device__ __forceinline__ int32_t quant_cap(float K, float x) {
@@ -303,6 +313,8 @@ __device__ __forceinline__ int32_t quant_cap(float K, float x) {
 }
 
 __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
+  if (!a.rgb) a.rgb = a.io->rgb;
+  if (!a.prior) a.prior = a.io->prior;
   __shared__ int sLut[766 * 2];
   for (int i = threadIdx.x; i < 766 * 2; i += blockDim.x) sLut[i] = a.lut[i];
   __syncthreads();
@@ -413,7 +425,8 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   a.part = c->mom_part;
   a.counter = c->mom_counter;
   a.gauss = c->gauss;
-  a.kal_adv = (use_kalman && rgb_moments) ? c->kal : nullptr;
+  a.kal_adv = (use_kalman && (rgb_moments || c->io_mode)) ? c->kal : nullptr;
+  a.io = c->io_mode ? c->io : nullptr;
   dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY);
   k_prior<<<grid, 256, 0, c->stream>>>(a);
   SEG_CUDA_TRY(cudaGetLastError());
@@ -432,6 +445,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   fa.kal = nullptr;
   fa.a = p.sigma1 * p.sigma1;
   fa.b = p.sigma2 * p.sigma2;
+  fa.io = c->io_mode ? c->io : nullptr;
   if (first_pass) k_mom1<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, fa);
   k_mom2<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, fa);
   TermsArgs ta;
@@ -448,6 +462,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.cs = cs;
   ta.ct = ct;
   ta.ncap = ncap;
+  ta.io = c->io_mode ? c->io : nullptr;
   dim3 grid((c->W + 31) / 32, (c->H + 7) / 8);
   k_terms<<<grid, 256, 0, st>>>(ta);
   SEG_CUDA_TRY(cudaGetLastError());

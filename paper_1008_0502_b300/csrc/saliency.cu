@@ -33,7 +33,8 @@ __constant__ float c_binom[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
 
 // ------------------------------------------------------------------ k_rgb_max
 __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, unsigned* mm,
-                          int nmaps) {
+                          int nmaps, const SegIO* io) {
+  if (!rgb) rgb = io->rgb;
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid < nmaps) {  // N(.) statistics start empty: min = +max float, max = 0
     mm[2 * tid] = 0x7f7fffffu;
@@ -55,7 +56,9 @@ __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, uns
 __global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict__ rgb, int H, int W,
                                                       const int* __restrict__ smax_p,
                                                       float* __restrict__ I1, float* __restrict__ RG1,
-                                                      float* __restrict__ BY1, int h1, int w1) {
+                                                      float* __restrict__ BY1, int h1, int w1,
+                                                      const SegIO* io) {
+  if (!rgb) rgb = io->rgb;
   __shared__ float sF[3][RED_IN_Y][RED_IN_X];
   __shared__ float sH[3][RED_IN_Y][RED_TX];
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
@@ -493,7 +496,9 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, int hs, int ws, int H,
-                                                  int W, float* __restrict__ sal, unsigned* salmax) {
+                                                  int W, float* __restrict__ sal, unsigned* salmax,
+                                                  const SegIO* io) {
+  if (!sal) sal = io->sal;
   int x = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
   float v = 0.f;
   if (x < W && y < H) {
@@ -660,10 +665,11 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   SEG_CUDA_TRY(cudaMemsetAsync(s.salmax, 0, sizeof(unsigned), st));
   int nb = min((N + 255) / 256, 148 * 8);
   nb = max(nb, (s.nmaps + 255) / 256);
-  k_rgb_max<<<nb, 256, 0, st>>>(rgb, N, s.smax, s.mm, s.nmaps);
+  const SegIO* io = c->io_mode ? c->io : nullptr;
+  k_rgb_max<<<nb, 256, 0, st>>>(rgb, N, s.smax, s.mm, s.nmaps, io);
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY);
   k_feat_reduce1<<<g1, 256, 0, st>>>(rgb, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1], s.hl[1],
-                                     s.wl[1]);
+                                     s.wl[1], io);
   // tiled launches while the produced level is large; one tail launch for the rest
   int tail_from = s.L - 1;
   for (int l = 1; l + 1 < s.L; ++l)
@@ -738,7 +744,7 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   pa.S = s.S;
   k_consp<<<1, 1024, 0, st>>>(pa);
   dim3 gu((W + 63) / 64, (H + 3) / 4);
-  k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, s.salmax);
+  k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, s.salmax, io);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }

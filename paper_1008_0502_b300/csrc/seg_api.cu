@@ -50,6 +50,7 @@ extern "C" int seg_default_params(seg_params* p) {
   p->max_cycles = 20000;
   p->global_relabel_every = 2;
   p->local_iters = 16;
+  p->use_graph = 1;
   return SEG_OK;
 }
 
@@ -121,7 +122,7 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
   size_t o_cnt = take(sizeof(unsigned));
   size_t o_prev = take(N), o_cs = take(4 * N), o_ct = take(4 * N), o_ncap = take(4 * N * nk);
   size_t o_sal = take(4 * N), o_prior = take(4 * N), o_mask = take(N), o_cut = take(8);
-  size_t o_rgb = take(3 * N), o_status = take(32);
+  size_t o_rgb = take(3 * N), o_status = take(32), o_io = take(sizeof(SegIO));
   size_t o_mf = take(mf_bytes(H, W, p->neighbourhood));
   char* base = nullptr;
   if (cudaMalloc((void**)&base, off) != cudaSuccess) {
@@ -145,6 +146,7 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
   c->cut_buf = (int64_t*)(base + o_cut);
   c->rgb_stage = (uint8_t*)(base + o_rgb);
   c->status = (int*)(base + o_status);
+  c->io = (SegIO*)(base + o_io);
   mf_bind(c->mf, base + o_mf, H, W, p->neighbourhood);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
   pt_fill_lut(*p, lut);
@@ -169,6 +171,7 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
 extern "C" int seg_destroy(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
   cudaStreamSynchronize(c->stream);
+  if (c->graph_state == 1) cudaGraphExecDestroy(c->gexec);
   prof_free(c);
   cudaFree(c->arena);
   cudaFreeHost(c->status_host);
@@ -185,9 +188,55 @@ extern "C" int seg_reset(seg_ctx* c) {
 
 static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
                       uint8_t* mask, uint8_t* mask_state, int64_t* cut) {
+  if (c->io_mode)  // mask and cut come from the frame's SegIO
+    return mf_launch(c->stream, c->mf, c->mf_grid, c->H, c->W, c->p.neighbourhood, cs, ct, ncap, nullptr,
+                     mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
+                     c->p.local_iters, c->io);
   return mf_launch(c->stream, c->mf, c->mf_grid, c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
                    c->p.global_relabel_every, c->p.local_iters);
+}
+
+// The launch sequence of one frame.  With c->io_mode set (graph capture) every
+// frame pointer is nullptr and the kernels read them from c->io.
+static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, uint8_t* mask,
+                         int64_t* cut) {
+  int rc = sal_launch(c, rgb, s);
+  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb);
+  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
+  if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
+  return rc;
+}
+
+__global__ void k_set_io(SegIO* io, SegIO v) { *io = v; }
+
+// Captures push_launches once into a CUDA graph (needs a stream that can be
+// captured, i.e. not the legacy default stream).  On any failure the context
+// stays on eager launches.
+static void build_graph(seg_ctx* c) {
+  c->graph_state = -1;
+  if (!c->p.use_graph || c->stream == nullptr) return;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c->io_mode = 1;
+  int rc = push_launches(c, nullptr, nullptr, nullptr, nullptr, nullptr);
+  c->io_mode = 0;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (rc || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return;
+  }
+  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c->graph_state = 1;
 }
 
 static void prof_mark(seg_ctx* c, int k) {
@@ -199,6 +248,16 @@ extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float*
   if (!c || !rgb || !mask) return SEG_EINVAL;
   float* s = sal ? sal : c->sal_buf;
   float* pr = prior ? prior : c->prior_buf;
+  if (!c->prof_on) {
+    if (c->graph_state == 0) build_graph(c);
+    if (c->graph_state == 1) {
+      SegIO v = {rgb, s, pr, mask, (long long*)(cut ? cut : c->cut_buf)};
+      k_set_io<<<1, 1, 0, c->stream>>>(c->io, v);
+      SEG_CUDA_TRY(cudaGetLastError());
+      SEG_CUDA_TRY(cudaGraphLaunch(c->gexec, c->stream));
+      return SEG_OK;
+    }
+  }
   prof_mark(c, 0);
   int rc = sal_launch(c, rgb, s);
   prof_mark(c, 1);

@@ -120,6 +120,16 @@ struct SalWS {
   GaborTaps taps;
 };
 
+// Frame-varying pointers of seg_push_frame, read by the kernels of the captured
+// per-frame CUDA graph (a kernel argument that is nullptr is taken from here).
+struct SegIO {
+  const uint8_t* rgb;
+  float* sal;
+  float* prior;
+  uint8_t* mask;
+  long long* cut;
+};
+
 // ---------------------------------------------------------------- prior / terms
 struct KalmanDev {
   double P;  // sigma^2_xi1(t-1)
@@ -161,6 +171,7 @@ struct MFArgs {
   uint8_t* mask_out;
   uint8_t* mask_state;  // nullable second copy of the mask
   long long* cut_out;   // nullable
+  const SegIO* io;      // mask_out / cut_out == nullptr: take them from here
   unsigned long long* cut_acc;
   unsigned int* flags;  // [3] rotating round counters
   int* tstamp;           // per tile: last round (epoch) in which a fixpoint changed it
@@ -208,6 +219,11 @@ struct seg_ctx {
   uint8_t* rgb_stage;
   MFWS mf;
   int mf_grid;
+  // captured per-frame graph of seg_push_frame
+  SegIO* io;
+  int io_mode;       // launchers pass nullptr for frame pointers (graph capture)
+  int graph_state;   // 0 not built, 1 ready, -1 unavailable (eager launches)
+  cudaGraphExec_t gexec;
   int* status;       // device [8]
   int* status_host;  // pinned [8]
   // optional per-stage timing (seg_profile_enable)
@@ -219,7 +235,7 @@ struct seg_ctx {
 // ---------------------------------------------------------------- launchers
 int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes);
 void sal_bind(SalWS& s, char* base);
-int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);
+int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);  // nullptr + c->io_mode: from c->io
 
 int pt_mom_blocks(int H, int W);
 int pt_launch_salmax(seg_ctx* c, const float* sal);
@@ -237,6 +253,7 @@ void mf_bind(MFWS& m, char* base, int H, int W, int ndir);
 int mf_grid_size(int H, int W, int* grid);
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
-              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters);
+              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
+              const SegIO* io = nullptr);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }

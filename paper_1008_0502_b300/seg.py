@@ -43,6 +43,7 @@ class seg_params(C.Structure):
         ("lambda_u", C.c_double), ("lambda_p", C.c_double), ("lambda_s", C.c_double),
         ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int32),
         ("max_cycles", C.c_int32), ("global_relabel_every", C.c_int32), ("local_iters", C.c_int32),
+        ("use_graph", C.c_int32),
     ]
 
 
@@ -146,12 +147,28 @@ class Segmenter:
                                                                                    torch.cuda.current_device())
         self.params = params if params is not None else default_params()
         with torch.cuda.device(self.device):
-            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            # a stream of its own (not the legacy default stream) lets the library replay
+            # one captured CUDA graph per frame; it is a blocking stream, so work queued on
+            # the default stream before a call is ordered before it
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             h = C.c_void_p()
             _check(lib.seg_create(_stream_handle(self.stream), H, W, C.byref(self.params), C.byref(h)),
                    "seg_create")
         self.handle = h
         self.nk = self.params.neighbourhood // 2
+
+    # The context runs on its own stream; every call orders it after the caller's
+    # current stream (inputs ready) and the caller's stream after it (outputs ready),
+    # so tensors can be used on the current stream as usual.
+    def _begin(self):
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+        return cur
+
+    def _end(self, cur):
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -181,12 +198,14 @@ class Segmenter:
         H, W = self.H, self.W
         if mask is None:
             saliency, prior, mask, cut = self.empty_outputs()
+        cur = self._begin()
         _check(lib.seg_push_frame(self.handle, _dev(rgb, torch.uint8, (H, W, 3), "rgb"),
                                   _dev(saliency, torch.float32, (H, W), "saliency") if saliency is not None else None,
                                   _dev(prior, torch.float32, (H, W), "prior") if prior is not None else None,
                                   _dev(mask, torch.uint8, (H, W), "mask"),
                                   _dev(cut, torch.int64, (1,), "cut") if cut is not None else None),
                "seg_push_frame")
+        self._end(cur)
         return saliency, prior, mask, cut
 
     def push_frame_host(self, rgb_host, mask_host, cut_host=None, saliency_host=None, prior_host=None):
@@ -204,7 +223,9 @@ class Segmenter:
         return code, cyc.value
 
     def reset(self):
+        cur = self._begin()
         _check(lib.seg_reset(self.handle), "seg_reset")
+        self._end(cur)
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)
@@ -234,15 +255,19 @@ class Segmenter:
     # --- stage entry points
     def saliency(self, rgb, out=None):
         out = out if out is not None else torch.empty(self.H, self.W, dtype=torch.float32, device=self.device)
+        cur = self._begin()
         _check(lib.seg_saliency(self.handle, _dev(rgb, torch.uint8, (self.H, self.W, 3), "rgb"),
                                 _dev(out, torch.float32, (self.H, self.W), "saliency")), "seg_saliency")
+        self._end(cur)
         return out
 
     def prior(self, saliency, prev_mask, w_f, out=None):
         out = out if out is not None else torch.empty(self.H, self.W, dtype=torch.float32, device=self.device)
         pm = _dev(prev_mask, torch.uint8, (self.H, self.W), "prev_mask") if prev_mask is not None else None
+        cur = self._begin()
         _check(lib.seg_prior(self.handle, _dev(saliency, torch.float32, (self.H, self.W), "saliency"), pm,
                              float(w_f), _dev(out, torch.float32, (self.H, self.W), "prior")), "seg_prior")
+        self._end(cur)
         return out
 
     def terms(self, rgb, prior):
@@ -250,18 +275,22 @@ class Segmenter:
         cs = torch.empty(H, W, dtype=torch.int32, device=d)
         ct = torch.empty(H, W, dtype=torch.int32, device=d)
         nc = torch.empty(self.nk, H, W, dtype=torch.int32, device=d)
+        cur = self._begin()
         _check(lib.seg_terms(self.handle, _dev(rgb, torch.uint8, (H, W, 3), "rgb"),
                              _dev(prior, torch.float32, (H, W), "prior"), _ptr(cs), _ptr(ct), _ptr(nc)),
                "seg_terms")
+        self._end(cur)
         return cs, ct, nc
 
     def mincut(self, cs, ct, ncap, mask=None, cut=None):
         H, W, d = self.H, self.W, self.device
         mask = mask if mask is not None else torch.empty(H, W, dtype=torch.uint8, device=d)
         cut = cut if cut is not None else torch.empty(1, dtype=torch.int64, device=d)
+        cur = self._begin()
         _check(lib.seg_mincut(self.handle, _dev(cs, torch.int32, (H, W), "cs"), _dev(ct, torch.int32, (H, W), "ct"),
                               _dev(ncap, torch.int32, (self.nk, H, W), "ncap"), _ptr(mask), _ptr(cut)),
                "seg_mincut")
+        self._end(cur)
         return mask, cut
 
     def debug_copy(self, which: int, index: int, shape):

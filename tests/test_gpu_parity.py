@@ -266,3 +266,21 @@ def test_host_entry_point_and_state_roundtrip(S):
     assert torch.equal(p0, p1)
     for s in (a, b, c, fresh):
         s.close()
+
+
+def test_graph_replay_equals_eager_launches(S):
+    """seg_push_frame replays a captured CUDA graph; it must give exactly what
+    eager launches of the same kernels give (same workspace, same order)."""
+    frames, _ = synth.clip_small(5)
+    H, W = frames.shape[1:3]
+    g = S.Segmenter(H, W, seg_params(S, O.CONFIG_SMALL))
+    e = S.Segmenter(H, W, seg_params(S, O.CONFIG_SMALL, use_graph=0))
+    for t in range(5):
+        outs_g = g.push_frame(dev(frames[t]))
+        outs_e = e.push_frame(dev(frames[t]))
+        g.sync()
+        e.sync()
+        for a, b in zip(outs_g, outs_e):
+            assert torch.equal(a, b), t
+    g.close()
+    e.close()
