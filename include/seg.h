@@ -90,12 +90,24 @@ int seg_default_params(seg_params* p);
  * H*W > 2^26, invalid params), SEG_ENOMEM, SEG_ECUDA.  *out is NULL on error. */
 int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out);
 
+/* A batch context: B independent video streams of the same size H x W, all
+ * advanced by one seg_push_frame (one frame of every stream per call, one
+ * launch per kernel for the whole batch).  Every per-frame input/output is B
+ * frames back to back: rgb B x H x W x 3, saliency/prior B x H x W, mask
+ * B x H x W, cut B int64.  Stream b's results equal those of a single context
+ * fed the same frames.  The stage entry points seg_prior, seg_terms and
+ * seg_mincut need B == 1.  seg_create(...) is seg_create_batch(..., 1, ...).
+ * Errors as seg_create, plus SEG_EINVAL for B < 1 or B*H*W > 2^26. */
+int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg_ctx** out);
+
 /* Frees the context and its workspace (synchronises its stream first). */
 int seg_destroy(seg_ctx* ctx);
 
 /* Starts a new video: forgets the previous mask and the prior variance, so the
  * next frame is t = 0 (Sec. 6 with P_{-1} = +inf: p-hat = q). */
 int seg_reset(seg_ctx* ctx);
+/* seg_reset for stream b of a batch context only (a new video on that slot). */
+int seg_reset_stream(seg_ctx* ctx, int b);
 
 /* One frame of the whole method (Fig. 3; Secs. 3-6).
  *   rgb_dev      H*W*3 uint8 input frame (device).

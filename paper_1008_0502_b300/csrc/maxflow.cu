@@ -424,19 +424,24 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     if (cycle >= a.max_cycles) break;
   }
 
-  // ---- 4. minimal source set and cut value
-  long long flow_t = 0;
+  // ---- 4. minimal source set and cut value (the flow that reached t, per frame
+  // of a stacked batch: rows fb*frame_h .. fb*frame_h + frame_h - 1)
   for (int u = gtid; u < N; u += nthr) {
     unsigned bits = 0;
 #pragma unroll
     for (int d = 0; d < ND; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
     a.rm[u] = (unsigned char)bits;
     a.z[u] = a.e[u] > 0 ? 1 : 0;
-    flow_t += (long long)a.ct[u] - a.rt[u];
   }
-  for (int o = 16; o > 0; o >>= 1) flow_t += __shfl_xor_sync(0xffffffffu, flow_t, o);
-  if ((threadIdx.x & 31) == 0 && flow_t != 0)
-    atomicAdd(a.cut_acc, (unsigned long long)flow_t);
+  {
+    const int nf = a.frame_h * W;  // nodes per frame
+    for (int fb = 0; fb < a.nframes; ++fb) {
+      long long flow_t = 0;
+      for (int u = fb * nf + gtid; u < (fb + 1) * nf; u += nthr) flow_t += (long long)a.ct[u] - a.rt[u];
+      for (int o = 16; o > 0; o >>= 1) flow_t += __shfl_xor_sync(0xffffffffu, flow_t, o);
+      if ((threadIdx.x & 31) == 0 && flow_t != 0) atomicAdd(&a.cut_acc[fb], (unsigned long long)flow_t);
+    }
+  }
   if (!mf_grid_sync(a, s)) return;
   for (bool first = true;; first = false) {
     mf_flag_begin(a, epoch);
@@ -466,9 +471,11 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     mask_out[u] = v;
     if (a.mask_state) a.mask_state[u] = v;
   }
+  long long* cut_out = a.cut_out ? a.cut_out : (a.io ? a.io->cut : nullptr);
+  if (cut_out && blockIdx.x == 0)
+    for (int fb = threadIdx.x; fb < a.nframes; fb += blockDim.x)
+      cut_out[fb] = (long long)*(volatile unsigned long long*)&a.cut_acc[fb];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    long long* cut_out = a.cut_out ? a.cut_out : (a.io ? a.io->cut : nullptr);
-    if (cut_out) *cut_out = (long long)*(volatile unsigned long long*)a.cut_acc;
     if (!converged) atomicCAS(&a.status[0], 0, SEG_ENOTCONVERGED);
     a.status[1] = cycle;
     a.status[2] = n_gr;
@@ -479,14 +486,14 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
 }
 
 // ---------------------------------------------------------------- host side
-size_t mf_bytes(int H, int W, int ndir) {
+size_t mf_bytes(int H, int W, int ndir, int nframes) {
   size_t N = (size_t)H * W;
   size_t nt = (size_t)((W + MF_TW - 1) / MF_TW) * ((H + MF_TH - 1) / MF_TH);
-  return seg_align(N * 4) * 3 + seg_align(N * 4 * ndir) + seg_align(N) * 2 + seg_align(8) +
+  return seg_align(N * 4) * 3 + seg_align(N * 4 * ndir) + seg_align(N) * 2 + seg_align(8 * nframes) +
          seg_align(16) + seg_align(nt * 4) + seg_align(nt) + seg_align(sizeof(GridBar));
 }
 
-void mf_bind(MFWS& m, char* base, int H, int W, int ndir) {
+void mf_bind(MFWS& m, char* base, int H, int W, int ndir, int nframes) {
   size_t N = (size_t)H * W, off = 0;
   auto take = [&](size_t b) {
     char* p = base + off;
@@ -499,7 +506,8 @@ void mf_bind(MFWS& m, char* base, int H, int W, int ndir) {
   m.r = (int*)take(N * 4 * ndir);
   m.rm = (unsigned char*)take(N);
   m.z = (unsigned char*)take(N);
-  m.cut_acc = (unsigned long long*)take(8);
+  m.cut_acc = (unsigned long long*)take(8 * nframes);
+  m.nframes = nframes;
   m.flags = (unsigned int*)take(16);
   size_t nt = (size_t)((W + MF_TW - 1) / MF_TW) * ((H + MF_TH - 1) / MF_TH);
   m.tstamp = (int*)take(nt * 4);
@@ -531,6 +539,9 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
               const SegIO* io) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
+  if (H % m.nframes) return SEG_EINVAL;
+  a.nframes = m.nframes;
+  a.frame_h = H / m.nframes;
   a.H = H;
   a.W = W;
   a.N = H * W;
@@ -560,7 +571,7 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   a.gr_every = gr_every < 1 ? 1 : gr_every;
   a.local_iters = local_iters < 1 ? 1 : local_iters;
   a.timeout_ns = 4000000000LL;
-  SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8, st));
+  SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, st));
   SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));
   SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), st));
   void* args[] = {&a};

@@ -41,6 +41,7 @@ struct PriorArgs {
   // fused first moment pass (rgb == nullptr: off)
   const uint8_t* rgb;
   double* part;
+  int part_stride;     // doubles of partials per frame
   unsigned* counter;
   GaussDev* gauss;
   KalmanDev* kal_adv;  // nullable: advance the variance recursion
@@ -49,6 +50,7 @@ struct PriorArgs {
 
 struct MomFinArgs {
   double* part;
+  int part_stride;  // doubles of partials per frame
   unsigned* counter;
   GaussDev* gauss;
   KalmanDev* kal;  // nullable: advance the variance recursion
@@ -84,6 +86,20 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
   }
   __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
   __shared__ float sH[PR_TY + 2 * PR_MAXR][PR_TX];
+  {  // frame of the batch
+    const int fb = blockIdx.z;
+    const size_t n = (size_t)a.H * a.W;
+    a.sal += fb * n;
+    a.prior += fb * n;
+    if (a.prev) a.prev += fb * n;
+    if (a.rgb) a.rgb += fb * 3 * n;
+    a.salmax += fb;
+    if (a.kal) a.kal += fb;
+    if (a.kal_adv) a.kal_adv += fb;
+    a.gauss += fb;
+    a.part += (size_t)fb * a.part_stride;
+    a.counter += fb;
+  }
   double wf = a.wf_host;
   if (a.kal) {
     int t = a.kal->t;
@@ -245,6 +261,13 @@ __device__ void finalize_cov(const double* tot, GaussDev* g) {
 
 __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
                                               const float* __restrict__ prior, int N, MomFinArgs f) {
+  const int fb = blockIdx.y;  // frame of the batch
+  rgb += (size_t)fb * 3 * N;
+  prior += (size_t)fb * N;
+  f.part += (size_t)fb * f.part_stride;
+  f.counter += fb;
+  f.gauss += fb;
+  if (f.kal) f.kal += fb;
   float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
     mom1_add(prior[i], rgb + 3 * (size_t)i, s);
@@ -259,6 +282,12 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
                                               const float* __restrict__ prior, int N, MomFinArgs f) {
   if (!rgb) rgb = f.io->rgb;
   if (!prior) prior = f.io->prior;
+  const int fb = blockIdx.y;  // frame of the batch
+  rgb += (size_t)fb * 3 * N;
+  prior += (size_t)fb * N;
+  f.part += (size_t)fb * f.part_stride;
+  f.counter += fb;
+  f.gauss += fb;
   const GaussDev* gauss = f.gauss;
   float m0r = gauss->muf[0][0], m0g = gauss->muf[0][1], m0b = gauss->muf[0][2];
   float m1r = gauss->muf[1][0], m1g = gauss->muf[1][1], m1b = gauss->muf[1][2];
@@ -298,7 +327,7 @@ struct TermsArgs {
   const float* prior;
   const GaussDev* gauss;
   const int* lut;
-  int H, W, nk;
+  int H, W, nk, B;
   float eps, lambda_u, K;
   int32_t* cs;
   int32_t* ct;
@@ -320,7 +349,18 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   __syncthreads();
   int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= a.W || y >= a.H) return;
-  size_t N = (size_t)a.H * a.W, g = (size_t)y * a.W + x;
+  // frame fb of the batch: its n-link planes are rows fb*H .. fb*H+H-1 of the
+  // stacked (B*H) x W grid the min cut sees; links leaving the frame stay 0
+  const int fb = blockIdx.z;
+  const size_t N = (size_t)a.H * a.W;
+  a.rgb += fb * 3 * N;
+  a.prior += fb * N;
+  a.gauss += fb;
+  a.cs += fb * N;
+  a.ct += fb * N;
+  a.ncap += fb * N;
+  const size_t NB = N * a.B;  // plane stride of the stacked n-link planes
+  size_t g = (size_t)y * a.W + x;
   const uint8_t* p = a.rgb + 3 * g;
   int r8 = p[0], g8 = p[1], b8 = p[2];
   float C[3] = {r8 / 255.f, g8 / 255.f, b8 / 255.f};
@@ -351,7 +391,7 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
       int ds = abs(s0 - (q[0] + q[1] + q[2]));
       c = sLut[2 * ds + (k >= 2)];
     }
-    a.ncap[k * N + g] = c;
+    a.ncap[k * NB + g] = c;
   }
 }
 
@@ -425,9 +465,10 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   a.part = c->mom_part;
   a.counter = c->mom_counter;
   a.gauss = c->gauss;
+  a.part_stride = pt_part_doubles(c->H, c->W);
   a.kal_adv = (use_kalman && (rgb_moments || c->io_mode)) ? c->kal : nullptr;
   a.io = c->io_mode ? c->io : nullptr;
-  dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY);
+  dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY, c->B);
   k_prior<<<grid, 256, 0, c->stream>>>(a);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
@@ -440,14 +481,15 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   int N = c->N;
   MomFinArgs fa;
   fa.part = c->mom_part;
+  fa.part_stride = pt_part_doubles(c->H, c->W);
   fa.counter = c->mom_counter;
   fa.gauss = c->gauss;
   fa.kal = nullptr;
   fa.a = p.sigma1 * p.sigma1;
   fa.b = p.sigma2 * p.sigma2;
   fa.io = c->io_mode ? c->io : nullptr;
-  if (first_pass) k_mom1<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, fa);
-  k_mom2<<<c->mom_blocks, 256, 0, st>>>(rgb, prior, N, fa);
+  if (first_pass) k_mom1<<<dim3(c->mom_blocks, c->B), 256, 0, st>>>(rgb, prior, N, fa);
+  k_mom2<<<dim3(c->mom_blocks, c->B), 256, 0, st>>>(rgb, prior, N, fa);
   TermsArgs ta;
   ta.rgb = rgb;
   ta.prior = prior;
@@ -456,6 +498,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.H = c->H;
   ta.W = c->W;
   ta.nk = p.neighbourhood / 2;
+  ta.B = c->B;
   ta.eps = p.eps;
   ta.lambda_u = (float)p.lambda_u;
   ta.K = (float)p.cap_scale;
@@ -463,7 +506,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.ct = ct;
   ta.ncap = ncap;
   ta.io = c->io_mode ? c->io : nullptr;
-  dim3 grid((c->W + 31) / 32, (c->H + 7) / 8);
+  dim3 grid((c->W + 31) / 32, (c->H + 7) / 8, c->B);
   k_terms<<<grid, 256, 0, st>>>(ta);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;

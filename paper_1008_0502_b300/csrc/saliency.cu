@@ -35,6 +35,10 @@ __constant__ float c_binom[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
 __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, unsigned* mm,
                           int nmaps, const SegIO* io) {
   if (!rgb) rgb = io->rgb;
+  const int fb = blockIdx.y;  // frame of the batch
+  rgb += (size_t)fb * 3 * n;
+  smax += fb;
+  mm += (size_t)fb * 2 * nmaps;
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid < nmaps) {  // N(.) statistics start empty: min = +max float, max = 0
     mm[2 * tid] = 0x7f7fffffu;
@@ -42,7 +46,7 @@ __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, uns
   }
   int m = 0;
   for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
-    int s = rgb[3 * i] + rgb[3 * i + 1] + rgb[3 * i + 2];
+    int s = rgb[3 * (size_t)i] + rgb[3 * (size_t)i + 1] + rgb[3 * (size_t)i + 2];
     m = max(m, s);
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -61,9 +65,15 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict_
   if (!rgb) rgb = io->rgb;
   __shared__ float sF[3][RED_IN_Y][RED_IN_X];
   __shared__ float sH[3][RED_IN_Y][RED_TX];
+  const int fb = blockIdx.z;  // frame of the batch
+  rgb += (size_t)fb * 3 * H * W;
+  const size_t o1 = (size_t)fb * h1 * w1;
+  I1 += o1;
+  RG1 += o1;
+  BY1 += o1;
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
   const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
-  const int smax = *smax_p;
+  const int smax = smax_p[fb];
   for (int i = threadIdx.x; i < RED_IN_Y * RED_IN_X; i += blockDim.x) {
     int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
     int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
@@ -115,12 +125,13 @@ struct Reduce3Args {
   int h, w, h2, w2;
 };
 
-// One REDUCE step of one channel per CTA (blockIdx.z = channel).
+// One REDUCE step of one channel per CTA (blockIdx.z = channel + 3 * frame).
 __global__ void __launch_bounds__(256) k_reduce3(Reduce3Args a) {
   __shared__ float sF[RED_IN_Y][RED_IN_X];
   __shared__ float sH[RED_IN_Y][RED_TX];
-  const float* __restrict__ in = a.in[blockIdx.z];
-  float* __restrict__ out = a.out[blockIdx.z];
+  const int ch = blockIdx.z % 3, fb = blockIdx.z / 3;
+  const float* __restrict__ in = a.in[ch] + (size_t)fb * a.h * a.w;
+  float* __restrict__ out = a.out[ch] + (size_t)fb * a.h2 * a.w2;
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
   const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
   for (int i = threadIdx.x; i < RED_IN_Y * RED_IN_X; i += blockDim.x) {
@@ -155,11 +166,11 @@ struct PyrTailArgs {
 };
 
 __global__ void __launch_bounds__(1024) k_pyr_tail(PyrTailArgs a) {
-  const int ch = blockIdx.x;
+  const int ch = blockIdx.x % 3, fb = blockIdx.x / 3;
   for (int l = a.from; l < a.to; ++l) {
-    const float* __restrict__ in = a.lvl[ch][l];
-    float* __restrict__ out = a.lvl[ch][l + 1];
     const int h = a.hl[l], w = a.wl[l], h2 = a.hl[l + 1], w2 = a.wl[l + 1];
+    const float* __restrict__ in = a.lvl[ch][l] + (size_t)fb * h * w;
+    float* __restrict__ out = a.lvl[ch][l + 1] + (size_t)fb * h2 * w2;
     for (int i = threadIdx.x; i < h2 * w2; i += blockDim.x) {
       int y = i / w2, x = i - y * w2;
       int xs[5];
@@ -203,11 +214,12 @@ __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
   while (l < a.lvl_last && b >= a.blk_off[l - a.lvl_first + 1]) ++l;
   b -= a.blk_off[l - a.lvl_first];
   const int h = a.hl[l], w = a.wl[l];
+  const size_t fo = (size_t)blockIdx.y * h * w;  // frame of the batch
   const int ntx = (w + GB_TX - 1) / GB_TX;
   const int X0 = (b % ntx) * GB_TX, Y0 = (b / ntx) * GB_TY;
   const int R = t.R, K = 2 * R + 1;
   const int iny = GB_TY + 2 * R, inx = GB_TX + 2 * R;
-  const float* __restrict__ in = a.in[l];
+  const float* __restrict__ in = a.in[l] + fo;
   for (int i = threadIdx.x; i < iny * inx; i += blockDim.x) {
     int ry = i / inx, rx = i - ry * inx;
     sIn[ry][rx] = in[(size_t)seg_clampi(Y0 - R + ry, 0, h - 1) * w + seg_clampi(X0 - R + rx, 0, w - 1)];
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
       sHi[ry][x] = im;
     }
     __syncthreads();
-    float* __restrict__ out = a.out[k][l];
+    float* __restrict__ out = a.out[k][l] + fo;
     for (int i = threadIdx.x; i < GB_TY * GB_TX; i += blockDim.x) {
       int y = i / GB_TX, x = i - y * GB_TX;
       int oy = Y0 + y, ox = X0 + x;
@@ -259,14 +271,14 @@ struct CSArgs {
   int pair_c[SEG_MAX_PAIRS], pair_s[SEG_MAX_PAIRS];
   int pair_band_off[SEG_MAX_PAIRS + 1];  // prefix of (row bands x channels) per pair
   int npairs, nch, tile, opp_sum;
+  int nbands_total;
   unsigned* mm;
   float* tpart;
-  const float* nab;
 };
 
-__device__ __forceinline__ float cs_value(const CSArgs& a, int f, int c, int s, int y, int x) {
-  const float* cen = a.X[f][c];
-  float u = seg_bilinear(a.X[f][s], a.hl[s], a.wl[s], y, x, a.hl[c], a.wl[c]);
+__device__ __forceinline__ float cs_value(const CSArgs& a, int f, int c, int s, int y, int x, int fb) {
+  const float* cen = a.X[f][c] + (size_t)fb * a.hl[c] * a.wl[c];
+  float u = seg_bilinear(a.X[f][s] + (size_t)fb * a.hl[s] * a.wl[s], a.hl[s], a.wl[s], y, x, a.hl[c], a.wl[c]);
   float v = cen[y * a.wl[c] + x];
   return (a.opp_sum && (f == 1 || f == 2)) ? fabsf(v + u) : fabsf(v - u);
 }
@@ -287,13 +299,16 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
   int local = b - a.pair_band_off[p];
   int f = local / nb, band = local - f * nb;
   int m = p * a.nch + f;
+  const int fb = blockIdx.y;  // frame of the batch
+  unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * a.nch;
+  float* tpart = a.tpart + (size_t)fb * a.nbands_total;
   for (int i = threadIdx.x; i < ntx; i += blockDim.x) sTmax[i] = 0u;
   __syncthreads();
   int y0 = band * T, rows = min(T, hc - y0);
   float mn = 3.0e38f, mx = 0.f;
   for (int i = threadIdx.x; i < rows * wc; i += blockDim.x) {
     int y = y0 + i / wc, x = i % wc;
-    float v = cs_value(a, f, c, s, y, x);
+    float v = cs_value(a, f, c, s, y, x, fb);
     mn = fminf(mn, v);
     mx = fmaxf(mx, v);
     atomicMax(&sTmax[x / T], __float_as_uint(v));
@@ -315,9 +330,9 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
     a1 = seg_warp_max_f(a1);
     ts = seg_warp_sum_f(ts);
     if (threadIdx.x == 0) {
-      atomicMin(&a.mm[2 * m], __float_as_uint(a0));
-      atomicMax(&a.mm[2 * m + 1], __float_as_uint(a1));
-      a.tpart[b] = ts;
+      atomicMin(&mm[2 * m], __float_as_uint(a0));
+      atomicMax(&mm[2 * m + 1], __float_as_uint(a1));
+      tpart[b] = ts;
     }
   }
 }
@@ -341,30 +356,34 @@ __device__ __forceinline__ void norm_affine(double mn, double mx, double sum_tma
 }
 
 // N(.) of map m = (pair p, channel f) as a*v + b from its statistics.
-__device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* ab) {
+__device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* ab, int fb) {
   int c = a.pair_c[p];
   int T = a.tile, nb = (a.hl[c] + T - 1) / T, ntx = (a.wl[c] + T - 1) / T;
   int m = p * a.nch + f;
+  const unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * a.nch;
   double sum = 0.0;
-  const float* tp = a.tpart + a.pair_band_off[p] + f * nb;
+  const float* tp = a.tpart + (size_t)fb * a.nbands_total + a.pair_band_off[p] + f * nb;
   for (int i = 0; i < nb; ++i) sum += tp[i];
-  norm_affine(__uint_as_float(a.mm[2 * m]), __uint_as_float(a.mm[2 * m + 1]), sum, nb * ntx, flat, ab);
+  norm_affine(__uint_as_float(mm[2 * m]), __uint_as_float(mm[2 * m + 1]), sum, nb * ntx, flat, ab);
 }
 
 // B_c(f) = sum over pairs (c, s) of N(CS_f(c, s)) + REDUCE(B_{c-1}(f)).
 __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, float flat, const float* __restrict__ prev,
                                                   int hp, int wp, float* __restrict__ out) {
   __shared__ float sab[SEG_MAX_PAIRS][2];
-  int f = blockIdx.z;
-  if ((int)threadIdx.x < a.npairs && a.pair_c[threadIdx.x] == c) cs_map_affine(a, threadIdx.x, f, flat, sab[threadIdx.x]);
+  const int f = blockIdx.z % a.nch, fb = blockIdx.z / a.nch;  // channel, frame of the batch
+  if ((int)threadIdx.x < a.npairs && a.pair_c[threadIdx.x] == c)
+    cs_map_affine(a, threadIdx.x, f, flat, sab[threadIdx.x], fb);
   __syncthreads();
   int hc = a.hl[c], wc = a.wl[c];
+  if (prev) prev += (size_t)fb * a.nch * hp * wp;
+  out += (size_t)fb * a.nch * hc * wc;
   int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= wc || y >= hc) return;
   float acc = 0.f;
   for (int p = 0; p < a.npairs; ++p) {
     if (a.pair_c[p] != c) continue;
-    acc += sab[p][0] * cs_value(a, f, c, a.pair_s[p], y, x) + sab[p][1];
+    acc += sab[p][0] * cs_value(a, f, c, a.pair_s[p], y, x, fb) + sab[p][1];
   }
   if (prev) {
     const float* pl = prev + (size_t)f * hp * wp;
@@ -466,6 +485,11 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   __shared__ float red[12 * 32];
   __shared__ unsigned tmax[4 * CONSP_TILES];
   const int n = a.h * a.w;
+  const int fb = blockIdx.x;  // frame of the batch
+  a.acc += (size_t)fb * a.nch * n;
+  a.csum += (size_t)fb * n;
+  a.consp += (size_t)fb * 4 * n;
+  a.S += (size_t)fb * n;
   const float* v[4];
   for (int k0 = 3; k0 < a.nch; k0 += 4) {
     const int nm = min(4, a.nch - k0);
@@ -499,6 +523,10 @@ __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, i
                                                   int W, float* __restrict__ sal, unsigned* salmax,
                                                   const SegIO* io) {
   if (!sal) sal = io->sal;
+  const int fb = blockIdx.z;  // frame of the batch
+  S += (size_t)fb * hs * ws;
+  sal += (size_t)fb * H * W;
+  salmax += fb;
   int x = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
   float v = 0.f;
   if (x < W && y < H) {
@@ -543,8 +571,9 @@ static void make_taps(const seg_params& p, GaborTaps& t) {
   }
 }
 
-int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes) {
+int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes) {
   memset(&s, 0, sizeof(s));
+  s.B = B;
   s.H = H;
   s.W = W;
   s.L = p.levels;
@@ -590,23 +619,25 @@ int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes) {
     off += seg_align(b);
     return o;
   };
-  // record offsets in the pointer fields (bound later)
+  // record offsets in the pointer fields (bound later); every per-frame buffer
+  // holds B frames back to back
+  const size_t Bz = (size_t)B;
   for (int ch = 0; ch < 3; ++ch)
-    for (int l = 1; l < s.L; ++l) s.pyr[ch][l] = (float*)take(sizeof(float) * s.hl[l] * s.wl[l]);
+    for (int l = 1; l < s.L; ++l) s.pyr[ch][l] = (float*)take(Bz * sizeof(float) * s.hl[l] * s.wl[l]);
   for (int k = 0; k < s.no; ++k)
-    for (int l = s.c_min; l <= s.s_max; ++l) s.ori[k][l] = (float*)take(sizeof(float) * s.hl[l] * s.wl[l]);
-  s.mm = (unsigned*)take(sizeof(unsigned) * 2 * s.nmaps);
-  s.tpart = (float*)take(sizeof(float) * s.nbands_total);
-  s.nab = (float*)take(sizeof(float) * 2 * s.nmaps);
+    for (int l = s.c_min; l <= s.s_max; ++l)
+      s.ori[k][l] = (float*)take(Bz * sizeof(float) * s.hl[l] * s.wl[l]);
+  s.mm = (unsigned*)take(Bz * sizeof(unsigned) * 2 * s.nmaps);
+  s.tpart = (float*)take(Bz * sizeof(float) * s.nbands_total);
   size_t big = (size_t)s.hl[s.c_min] * s.wl[s.c_min] * s.nch;
-  s.acc[0] = (float*)take(sizeof(float) * big);
-  s.acc[1] = (float*)take(sizeof(float) * big);
+  s.acc[0] = (float*)take(Bz * sizeof(float) * big);
+  s.acc[1] = (float*)take(Bz * sizeof(float) * big);
   size_t nS = (size_t)s.hl[s.sS] * s.wl[s.sS];
-  s.consp = (float*)take(sizeof(float) * 4 * nS);
-  s.csum = (float*)take(sizeof(float) * nS);
-  s.S = (float*)take(sizeof(float) * nS);
-  s.salmax = (unsigned*)take(sizeof(unsigned));
-  s.smax = (int*)take(sizeof(int));
+  s.consp = (float*)take(Bz * sizeof(float) * 4 * nS);
+  s.csum = (float*)take(Bz * sizeof(float) * nS);
+  s.S = (float*)take(Bz * sizeof(float) * nS);
+  s.salmax = (unsigned*)take(Bz * sizeof(unsigned));
+  s.smax = (int*)take(Bz * sizeof(int));
   *bytes = off;
   return SEG_OK;
 }
@@ -622,7 +653,6 @@ void sal_bind(SalWS& s, char* base) {
     for (int l = s.c_min; l <= s.s_max; ++l) fix(s.ori[k][l]);
   fix(s.mm);
   fix(s.tpart);
-  fix(s.nab);
   fix(s.acc[0]);
   fix(s.acc[1]);
   fix(s.consp);
@@ -644,6 +674,7 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
   a.nch = s.nch;
   a.tile = s.tile;
   a.opp_sum = s.opp_sum;
+  a.nbands_total = s.nbands_total;
   int off = 0;
   for (int i = 0; i < s.npairs; ++i) {
     a.pair_c[i] = s.pair_c[i];
@@ -654,20 +685,19 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
   a.pair_band_off[s.npairs] = off;
   a.mm = s.mm;
   a.tpart = s.tpart;
-  a.nab = s.nab;
 }
 
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   SalWS& s = c->sal;
   cudaStream_t st = c->stream;
-  const int H = s.H, W = s.W, N = H * W;
-  SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, sizeof(int), st));
-  SEG_CUDA_TRY(cudaMemsetAsync(s.salmax, 0, sizeof(unsigned), st));
-  int nb = min((N + 255) / 256, 148 * 8);
+  const int H = s.H, W = s.W, N = H * W, B = s.B;
+  SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, B * sizeof(int), st));
+  SEG_CUDA_TRY(cudaMemsetAsync(s.salmax, 0, B * sizeof(unsigned), st));
+  int nb = min((N + 255) / 256, B > 1 ? 148 : 148 * 8);
   nb = max(nb, (s.nmaps + 255) / 256);
   const SegIO* io = c->io_mode ? c->io : nullptr;
-  k_rgb_max<<<nb, 256, 0, st>>>(rgb, N, s.smax, s.mm, s.nmaps, io);
-  dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY);
+  k_rgb_max<<<dim3(nb, B), 256, 0, st>>>(rgb, N, s.smax, s.mm, s.nmaps, io);
+  dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);
   k_feat_reduce1<<<g1, 256, 0, st>>>(rgb, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1], s.hl[1],
                                      s.wl[1], io);
   // tiled launches while the produced level is large; one tail launch for the rest
@@ -687,7 +717,7 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
     ra.w = s.wl[l];
     ra.h2 = s.hl[l + 1];
     ra.w2 = s.wl[l + 1];
-    dim3 g((ra.w2 + RED_TX - 1) / RED_TX, (ra.h2 + RED_TY - 1) / RED_TY, 3);
+    dim3 g((ra.w2 + RED_TX - 1) / RED_TX, (ra.h2 + RED_TY - 1) / RED_TY, 3 * B);
     k_reduce3<<<g, 256, 0, st>>>(ra);
   }
   if (tail_from < s.L - 1) {
@@ -700,7 +730,7 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
     }
     ta.from = tail_from;
     ta.to = s.L - 1;
-    k_pyr_tail<<<3, 1024, 0, st>>>(ta);
+    k_pyr_tail<<<3 * B, 1024, 0, st>>>(ta);
   }
   GaborArgs ga;
   memset(&ga, 0, sizeof(ga));
@@ -716,15 +746,15 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
     tot += ((s.wl[l] + GB_TX - 1) / GB_TX) * ((s.hl[l] + GB_TY - 1) / GB_TY);
   }
   ga.blk_off[s.s_max - s.c_min + 1] = tot;
-  k_gabor<<<tot, 256, 0, st>>>(ga, s.taps);
+  k_gabor<<<dim3(tot, B), 256, 0, st>>>(ga, s.taps);
   CSArgs ca;
   fill_cs_args(s, ca);
-  k_cs_stats<<<s.nbands_total, 256, 0, st>>>(ca);
+  k_cs_stats<<<dim3(s.nbands_total, B), 256, 0, st>>>(ca);
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;
   for (int cc = s.c_min; cc <= s.c_max; ++cc) {
-    dim3 g((s.wl[cc] + 31) / 32, (s.hl[cc] + 7) / 8, s.nch);
+    dim3 g((s.wl[cc] + 31) / 32, (s.hl[cc] + 7) / 8, s.nch * B);
     k_cs_accum<<<g, 256, 0, st>>>(ca, cc, s.flat, prev, hp, wp, s.acc[cur]);
     prev = s.acc[cur];
     hp = s.hl[cc];
@@ -742,8 +772,8 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   pa.csum = s.csum;
   pa.consp = s.consp;
   pa.S = s.S;
-  k_consp<<<1, 1024, 0, st>>>(pa);
-  dim3 gu((W + 63) / 64, (H + 3) / 4);
+  k_consp<<<B, 1024, 0, st>>>(pa);
+  dim3 gu((W + 63) / 64, (H + 3) / 4, B);
   k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, s.salmax, io);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;

@@ -87,13 +87,19 @@ static int check_params(const seg_params* p, int H, int W) {
 }
 
 extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out) {
+  return seg_create_batch(stream, 1, H, W, p, out);
+}
+
+extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg_ctx** out) {
   if (!out) return SEG_EINVAL;
   *out = nullptr;
   int rc = check_params(p, H, W);
   if (rc) return rc;
+  if (B < 1 || (long long)B * H * W > (1LL << 26)) return SEG_EINVAL;
   seg_ctx* c = (seg_ctx*)calloc(1, sizeof(seg_ctx));
   if (!c) return SEG_ENOMEM;
   c->stream = (cudaStream_t)stream;
+  c->B = B;
   c->H = H;
   c->W = W;
   c->N = H * W;
@@ -103,12 +109,12 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
     return SEG_ECUDA;
   }
   size_t sal_bytes = 0;
-  rc = sal_layout(c->sal, H, W, *p, &sal_bytes);
+  rc = sal_layout(c->sal, B, H, W, *p, &sal_bytes);
   if (rc) {
     free(c);
     return rc;
   }
-  const size_t N = (size_t)c->N;
+  const size_t N = (size_t)c->N, BN = N * B;
   const int nk = p->neighbourhood / 2;
   c->mom_blocks = pt_mom_blocks(H, W);
   size_t off = seg_align(sal_bytes);
@@ -117,13 +123,13 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
     off += seg_align(b);
     return o;
   };
-  size_t o_kal = take(sizeof(KalmanDev)), o_gauss = take(sizeof(GaussDev));
-  size_t o_mom = take(sizeof(double) * pt_part_doubles(H, W)), o_lut = take(sizeof(int) * 766 * 2);
-  size_t o_cnt = take(sizeof(unsigned));
-  size_t o_prev = take(N), o_cs = take(4 * N), o_ct = take(4 * N), o_ncap = take(4 * N * nk);
-  size_t o_sal = take(4 * N), o_prior = take(4 * N), o_mask = take(N), o_cut = take(8);
-  size_t o_rgb = take(3 * N), o_status = take(32), o_io = take(sizeof(SegIO));
-  size_t o_mf = take(mf_bytes(H, W, p->neighbourhood));
+  size_t o_kal = take(B * sizeof(KalmanDev)), o_gauss = take(B * sizeof(GaussDev));
+  size_t o_mom = take((size_t)B * sizeof(double) * pt_part_doubles(H, W)), o_lut = take(sizeof(int) * 766 * 2);
+  size_t o_cnt = take(B * sizeof(unsigned));
+  size_t o_prev = take(BN), o_cs = take(4 * BN), o_ct = take(4 * BN), o_ncap = take(4 * BN * nk);
+  size_t o_sal = take(4 * BN), o_prior = take(4 * BN), o_mask = take(BN), o_cut = take(8 * B);
+  size_t o_rgb = take(3 * BN), o_status = take(32), o_io = take(sizeof(SegIO));
+  size_t o_mf = take(mf_bytes(B * H, W, p->neighbourhood, B));
   char* base = nullptr;
   if (cudaMalloc((void**)&base, off) != cudaSuccess) {
     free(c);
@@ -147,17 +153,17 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
   c->rgb_stage = (uint8_t*)(base + o_rgb);
   c->status = (int*)(base + o_status);
   c->io = (SegIO*)(base + o_io);
-  mf_bind(c->mf, base + o_mf, H, W, p->neighbourhood);
+  mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
   pt_fill_lut(*p, lut);
   bool ok = cudaMemcpy(c->lut, lut, sizeof(int) * 766 * 2, cudaMemcpyHostToDevice) == cudaSuccess;
   free(lut);
-  ok = ok && cudaMemset(c->kal, 0, sizeof(KalmanDev)) == cudaSuccess;
-  ok = ok && cudaMemset(c->prev_mask, 0, N) == cudaSuccess;
+  ok = ok && cudaMemset(c->kal, 0, B * sizeof(KalmanDev)) == cudaSuccess;
+  ok = ok && cudaMemset(c->prev_mask, 0, BN) == cudaSuccess;
   ok = ok && cudaMemset(c->status, 0, 32) == cudaSuccess;
-  ok = ok && cudaMemset(c->mom_counter, 0, sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMemset(c->mom_counter, 0, B * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
-  ok = ok && mf_grid_size(H, W, &c->mf_grid) == SEG_OK;
+  ok = ok && mf_grid_size(B * H, W, &c->mf_grid) == SEG_OK;
   if (!ok) {
     if (c->status_host) cudaFreeHost(c->status_host);
     cudaFree(base);
@@ -181,18 +187,28 @@ extern "C" int seg_destroy(seg_ctx* c) {
 
 extern "C" int seg_reset(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
-  SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, sizeof(KalmanDev), c->stream));
-  SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask, 0, c->N, c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, c->B * sizeof(KalmanDev), c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask, 0, (size_t)c->B * c->N, c->stream));
   return SEG_OK;
 }
 
+extern "C" int seg_reset_stream(seg_ctx* c, int b) {
+  if (!c || b < 0 || b >= c->B) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaMemsetAsync(c->kal + b, 0, sizeof(KalmanDev), c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask + (size_t)b * c->N, 0, c->N, c->stream));
+  return SEG_OK;
+}
+
+// The B frames of a batch form one (B*H) x W grid for the min cut: links that
+// would join two frames have capacity 0 (the terms kernel writes 0 for every
+// neighbour outside the frame), so the stacked cut is the B cuts side by side.
 static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
                       uint8_t* mask, uint8_t* mask_state, int64_t* cut) {
   if (c->io_mode)  // mask and cut come from the frame's SegIO
-    return mf_launch(c->stream, c->mf, c->mf_grid, c->H, c->W, c->p.neighbourhood, cs, ct, ncap, nullptr,
-                     mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
+    return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
+                     nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
                      c->p.local_iters, c->io);
-  return mf_launch(c->stream, c->mf, c->mf_grid, c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
+  return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
                    c->p.global_relabel_every, c->p.local_iters);
 }
@@ -362,53 +378,67 @@ extern "C" int seg_push_frame_host(seg_ctx* c, const uint8_t* rgb_host, float* s
                                    float* prior_host, uint8_t* mask_host, int64_t* cut_host) {
   if (!c || !rgb_host || !mask_host) return SEG_EINVAL;
   cudaStream_t st = c->stream;
-  size_t N = c->N;
+  size_t N = (size_t)c->N * c->B;
   SEG_CUDA_TRY(cudaMemcpyAsync(c->rgb_stage, rgb_host, 3 * N, cudaMemcpyHostToDevice, st));
   int rc = seg_push_frame(c, c->rgb_stage, c->sal_buf, c->prior_buf, c->mask_buf, c->cut_buf);
   if (rc) return rc;
   SEG_CUDA_TRY(cudaMemcpyAsync(mask_host, c->mask_buf, N, cudaMemcpyDeviceToHost, st));
-  if (cut_host) SEG_CUDA_TRY(cudaMemcpyAsync(cut_host, c->cut_buf, 8, cudaMemcpyDeviceToHost, st));
+  if (cut_host) SEG_CUDA_TRY(cudaMemcpyAsync(cut_host, c->cut_buf, 8 * c->B, cudaMemcpyDeviceToHost, st));
   if (sal_host) SEG_CUDA_TRY(cudaMemcpyAsync(sal_host, c->sal_buf, 4 * N, cudaMemcpyDeviceToHost, st));
   if (prior_host)
     SEG_CUDA_TRY(cudaMemcpyAsync(prior_host, c->prior_buf, 4 * N, cudaMemcpyDeviceToHost, st));
   return seg_sync(c, nullptr);
 }
 
-#define SEG_STATE_MAGIC 0x53454731u  // "SEG1"
+#define SEG_STATE_MAGIC 0x53454732u  // "SEG2"
+
+// Byte layout: {magic, H, W, B} (4 x u32), then per stream {t (i32), pad, P (f64)},
+// then the B previous masks (B*H*W bytes).
+static size_t state_bytes(const seg_ctx* c) { return 16 + 16 * (size_t)c->B + (size_t)c->B * c->N; }
 
 extern "C" int seg_get_state(seg_ctx* c, void* buf, size_t* n) {
   if (!c || !n) return SEG_EINVAL;
-  size_t need = 24 + (size_t)c->N;
+  size_t need = state_bytes(c);
   if (!buf) {
     *n = need;
     return SEG_OK;
   }
   if (*n < need) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  KalmanDev k;
-  SEG_CUDA_TRY(cudaMemcpy(&k, c->kal, sizeof(k), cudaMemcpyDeviceToHost));
   char* b = (char*)buf;
-  uint32_t hdr[4] = {SEG_STATE_MAGIC, (uint32_t)c->H, (uint32_t)c->W, (uint32_t)k.t};
+  uint32_t hdr[4] = {SEG_STATE_MAGIC, (uint32_t)c->H, (uint32_t)c->W, (uint32_t)c->B};
   memcpy(b, hdr, 16);
-  memcpy(b + 16, &k.P, 8);
-  SEG_CUDA_TRY(cudaMemcpy(b + 24, c->prev_mask, c->N, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < c->B; ++i) {
+    KalmanDev k;
+    SEG_CUDA_TRY(cudaMemcpy(&k, c->kal + i, sizeof(k), cudaMemcpyDeviceToHost));
+    int32_t rec[2] = {k.t, 0};
+    memcpy(b + 16 + 16 * i, rec, 8);
+    memcpy(b + 16 + 16 * i + 8, &k.P, 8);
+  }
+  SEG_CUDA_TRY(cudaMemcpy(b + 16 + 16 * (size_t)c->B, c->prev_mask, (size_t)c->B * c->N, cudaMemcpyDeviceToHost));
   *n = need;
   return SEG_OK;
 }
 
 extern "C" int seg_set_state(seg_ctx* c, const void* buf, size_t n) {
-  if (!c || !buf || n != 24 + (size_t)c->N) return SEG_EINVAL;
+  if (!c || !buf || n != state_bytes(c)) return SEG_EINVAL;
   const char* b = (const char*)buf;
   uint32_t hdr[4];
   memcpy(hdr, b, 16);
-  if (hdr[0] != SEG_STATE_MAGIC || hdr[1] != (uint32_t)c->H || hdr[2] != (uint32_t)c->W) return SEG_EINVAL;
-  KalmanDev k;
-  memset(&k, 0, sizeof(k));
-  k.t = (int)hdr[3];
-  memcpy(&k.P, b + 16, 8);
+  if (hdr[0] != SEG_STATE_MAGIC || hdr[1] != (uint32_t)c->H || hdr[2] != (uint32_t)c->W ||
+      hdr[3] != (uint32_t)c->B)
+    return SEG_EINVAL;
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  SEG_CUDA_TRY(cudaMemcpy(c->kal, &k, sizeof(k), cudaMemcpyHostToDevice));
-  SEG_CUDA_TRY(cudaMemcpy(c->prev_mask, b + 24, c->N, cudaMemcpyHostToDevice));
+  for (int i = 0; i < c->B; ++i) {
+    KalmanDev k;
+    memset(&k, 0, sizeof(k));
+    int32_t rec[2];
+    memcpy(rec, b + 16 + 16 * i, 8);
+    k.t = rec[0];
+    memcpy(&k.P, b + 16 + 16 * i + 8, 8);
+    SEG_CUDA_TRY(cudaMemcpy(c->kal + i, &k, sizeof(k), cudaMemcpyHostToDevice));
+  }
+  SEG_CUDA_TRY(cudaMemcpy(c->prev_mask, b + 16 + 16 * (size_t)c->B, (size_t)c->B * c->N, cudaMemcpyHostToDevice));
   return SEG_OK;
 }
 
@@ -419,7 +449,7 @@ extern "C" int seg_saliency(seg_ctx* c, const uint8_t* rgb, float* sal) {
 
 extern "C" int seg_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, double w_f,
                          float* prior) {
-  if (!c || !sal || !prior || !(w_f >= 0.0 && w_f <= 1.0)) return SEG_EINVAL;
+  if (!c || !sal || !prior || !(w_f >= 0.0 && w_f <= 1.0) || c->B != 1) return SEG_EINVAL;
   if (w_f != 0.0 && !prev_mask) return SEG_EINVAL;
   int rc = pt_launch_salmax(c, sal);  // q = saliency / max(saliency) of THIS map
   return rc ? rc : pt_launch_prior(c, sal, prev_mask, 0, w_f, prior, nullptr);
@@ -427,13 +457,13 @@ extern "C" int seg_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask,
 
 extern "C" int seg_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct,
                          int32_t* ncap) {
-  if (!c || !rgb || !prior || !cs || !ct || !ncap) return SEG_EINVAL;
+  if (!c || !rgb || !prior || !cs || !ct || !ncap || c->B != 1) return SEG_EINVAL;
   return pt_launch_moments_terms(c, rgb, prior, 1, cs, ct, ncap);
 }
 
 extern "C" int seg_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
                           uint8_t* mask, int64_t* cut) {
-  if (!c || !cs || !ct || !ncap || !mask) return SEG_EINVAL;
+  if (!c || !cs || !ct || !ncap || !mask || c->B != 1) return SEG_EINVAL;
   return run_mincut(c, cs, ct, ncap, mask, nullptr, cut);
 }
 

@@ -98,6 +98,7 @@ struct GaborTaps {
 // Per-context saliency workspace.  Level-0 feature planes are never stored:
 // the first kernel fuses feature extraction with the first REDUCE.
 struct SalWS {
+  int B;  // frames of the batch (same size); every per-frame buffer holds B frames
   int H, W, L, c_min, c_max, d_min, d_max, no, s_max, sS, tile;
   int opp_sum;
   float flat;
@@ -110,7 +111,6 @@ struct SalWS {
   unsigned* mm;  // [nmaps][2]: min and max as float bits (maps are >= 0)
   float* tpart;  // [nbands_total]: per-band sums of tile maxima
   int nbands_total;
-  float* nab;     // [nmaps][2]: N(.) as the affine map a*v + b
   float* acc[2];  // ping-pong channel accumulators at scale c (nch planes)
   float* consp;   // 4 planes at sigma_S: N(C_I), N(C_RG), N(C_BY), N(C_O)
   float* csum;    // scratch plane at sigma_S
@@ -158,6 +158,7 @@ struct GridBar {
 
 struct MFArgs {
   int H, W, N, ndir;
+  int nframes, frame_h;  // a batch of frames stacked vertically: H = nframes * frame_h
   int ntx, nty;
   const int32_t* cs;
   const int32_t* ct;
@@ -190,17 +191,19 @@ struct MFWS {
   int* r;
   unsigned char* rm;
   unsigned char* z;
-  unsigned long long* cut_acc;
+  unsigned long long* cut_acc;  // [nframes]
   unsigned int* flags;
   int* tstamp;
   unsigned char* tact;
   GridBar* bar;
+  int nframes;
 };
 
 // ---------------------------------------------------------------- context
 struct seg_ctx {
   cudaStream_t stream;
   int device;
+  int B;  // streams (frames per step) of the batch, all H x W
   int H, W, N;
   seg_params p;
   void* arena;
@@ -233,7 +236,7 @@ struct seg_ctx {
 };
 
 // ---------------------------------------------------------------- launchers
-int sal_layout(SalWS& s, int H, int W, const seg_params& p, size_t* bytes);
+int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes);
 void sal_bind(SalWS& s, char* base);
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);  // nullptr + c->io_mode: from c->io
 
@@ -248,8 +251,9 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
 int pt_part_doubles(int H, int W);
 void pt_fill_lut(const seg_params& p, int* lut_host);
 
-size_t mf_bytes(int H, int W, int ndir);
-void mf_bind(MFWS& m, char* base, int H, int W, int ndir);
+// H is the stacked height (nframes frames of H / nframes rows each)
+size_t mf_bytes(int H, int W, int ndir, int nframes = 1);
+void mf_bind(MFWS& m, char* base, int H, int W, int ndir, int nframes = 1);
 int mf_grid_size(int H, int W, int* grid);
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,

@@ -55,6 +55,8 @@ def _load():
     sig = {
         "seg_default_params": ([P(seg_params)], i32),
         "seg_create": ([vp, i32, i32, P(seg_params), P(vp)], i32),
+        "seg_create_batch": ([vp, i32, i32, i32, P(seg_params), P(vp)], i32),
+        "seg_reset_stream": ([vp, i32], i32),
         "seg_destroy": ([vp], i32),
         "seg_reset": ([vp], i32),
         "seg_push_frame": ([vp, vp, vp, vp, vp, vp], i32),
@@ -141,8 +143,9 @@ def _stream_handle(stream):
 class Segmenter:
     """One video stream: owns a seg_ctx (workspace + temporal state) on a CUDA stream."""
 
-    def __init__(self, H: int, W: int, params: seg_params | None = None, stream=None, device=None):
-        self.H, self.W = H, W
+    def __init__(self, H: int, W: int, params: seg_params | None = None, stream=None, device=None,
+                 batch: int = 1):
+        self.H, self.W, self.B = H, W, batch
         self.device = torch.device(device) if device is not None else torch.device("cuda",
                                                                                    torch.cuda.current_device())
         self.params = params if params is not None else default_params()
@@ -152,8 +155,8 @@ class Segmenter:
             # the default stream before a call is ordered before it
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             h = C.c_void_p()
-            _check(lib.seg_create(_stream_handle(self.stream), H, W, C.byref(self.params), C.byref(h)),
-                   "seg_create")
+            _check(lib.seg_create_batch(_stream_handle(self.stream), batch, H, W, C.byref(self.params),
+                                        C.byref(h)), "seg_create_batch")
         self.handle = h
         self.nk = self.params.neighbourhood // 2
 
@@ -188,22 +191,28 @@ class Segmenter:
         self.close()
 
     # --- buffers
+    def _shape(self, *tail):
+        return (self.H, self.W) + tail if self.B == 1 else (self.B, self.H, self.W) + tail
+
     def empty_outputs(self):
-        H, W, d = self.H, self.W, self.device
-        return (torch.empty(H, W, dtype=torch.float32, device=d), torch.empty(H, W, dtype=torch.float32, device=d),
-                torch.empty(H, W, dtype=torch.uint8, device=d), torch.empty(1, dtype=torch.int64, device=d))
+        d = self.device
+        return (torch.empty(self._shape(), dtype=torch.float32, device=d),
+                torch.empty(self._shape(), dtype=torch.float32, device=d),
+                torch.empty(self._shape(), dtype=torch.uint8, device=d),
+                torch.empty(self.B, dtype=torch.int64, device=d))
 
     # --- whole method
     def push_frame(self, rgb, saliency=None, prior=None, mask=None, cut=None):
-        H, W = self.H, self.W
+        """One frame of every stream (rgb (H,W,3), or (B,H,W,3) for a batch)."""
         if mask is None:
             saliency, prior, mask, cut = self.empty_outputs()
         cur = self._begin()
-        _check(lib.seg_push_frame(self.handle, _dev(rgb, torch.uint8, (H, W, 3), "rgb"),
-                                  _dev(saliency, torch.float32, (H, W), "saliency") if saliency is not None else None,
-                                  _dev(prior, torch.float32, (H, W), "prior") if prior is not None else None,
-                                  _dev(mask, torch.uint8, (H, W), "mask"),
-                                  _dev(cut, torch.int64, (1,), "cut") if cut is not None else None),
+        _check(lib.seg_push_frame(self.handle, _dev(rgb, torch.uint8, self._shape(3), "rgb"),
+                                  _dev(saliency, torch.float32, self._shape(), "saliency") if saliency is not None
+                                  else None,
+                                  _dev(prior, torch.float32, self._shape(), "prior") if prior is not None else None,
+                                  _dev(mask, torch.uint8, self._shape(), "mask"),
+                                  _dev(cut, torch.int64, (self.B,), "cut") if cut is not None else None),
                "seg_push_frame")
         self._end(cur)
         return saliency, prior, mask, cut
@@ -222,9 +231,12 @@ class Segmenter:
             _check(code, "seg_sync")
         return code, cyc.value
 
-    def reset(self):
+    def reset(self, stream_index=None):
         cur = self._begin()
-        _check(lib.seg_reset(self.handle), "seg_reset")
+        if stream_index is None:
+            _check(lib.seg_reset(self.handle), "seg_reset")
+        else:
+            _check(lib.seg_reset_stream(self.handle, int(stream_index)), "seg_reset_stream")
         self._end(cur)
 
     def get_state(self) -> bytes:
@@ -254,10 +266,10 @@ class Segmenter:
 
     # --- stage entry points
     def saliency(self, rgb, out=None):
-        out = out if out is not None else torch.empty(self.H, self.W, dtype=torch.float32, device=self.device)
+        out = out if out is not None else torch.empty(self._shape(), dtype=torch.float32, device=self.device)
         cur = self._begin()
-        _check(lib.seg_saliency(self.handle, _dev(rgb, torch.uint8, (self.H, self.W, 3), "rgb"),
-                                _dev(out, torch.float32, (self.H, self.W), "saliency")), "seg_saliency")
+        _check(lib.seg_saliency(self.handle, _dev(rgb, torch.uint8, self._shape(3), "rgb"),
+                                _dev(out, torch.float32, self._shape(), "saliency")), "seg_saliency")
         self._end(cur)
         return out
 
