@@ -55,6 +55,10 @@ def args():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--frames", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the batched-context measurements")
+    ap.add_argument("--only", choices=["saliency_b32"], default=None,
+                    help="run one sub-measurement alone and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -159,6 +163,94 @@ def aggregate(t_local: float, frames_local: int, ws: int, device="cpu"):
     return frames_local / t_local, t_local
 
 
+def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
+    """Batch contexts against plain per-stream contexts (extra keys of the bench line)."""
+    from paper_1008_0502_b300 import synth
+    out = {}
+    p = seg.params_from(VGA)
+
+    def timed(fn, steps, warm=3, streams=()):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    # 8 streams of 640x480 in one batch context
+    B = 8
+    sgb = seg.Segmenter(H, W, p, batch=B)
+    outs = sgb.empty_outputs()
+    idx = [(37 * k) % clip_dev.shape[0] for k in range(B)]
+    frames = torch.stack([clip_dev[i] for i in idx])
+    steps = 40
+    t = timed(lambda: sgb.push_frame(frames, *outs), steps)
+    code, _ = sgb.sync()
+    out["vga_b8"] = {"streams": "8 x 640x480", "frames_per_s": B * steps / t, "vs_plain": B * steps / t / plain_fps,
+                     "status": code}
+    sgb.close()
+
+    # frame-batched saliency, 32 x 640x480 in one call: HBM roofline of the stage
+    B = 32
+    sgs = seg.Segmenter(H, W, p, batch=B)
+    fr32 = torch.stack([clip_dev[(9 * k) % clip_dev.shape[0]] for k in range(B)])
+    sal32 = torch.empty(B, H, W, dtype=torch.float32, device="cuda")
+    reps = 20
+    t = timed(lambda: sgs.saliency(fr32, sal32), reps)
+    byts = 7 * B * H * W  # RGB8 in + FP32 saliency out
+    ach = byts * reps / t / 1e9
+    out["saliency_b32"] = {"frames": "32 x 640x480", "ms_per_call": t / reps * 1e3, "algorithmic_bytes": byts,
+                           "achieved_GBps": ach, "frac_of_hbm": ach / hbm}
+    sgs.close()
+
+    # the mixed 64-stream workload: one batch context per resolution, each on its own CUDA stream
+    groups = [(24, 240, 320), (24, 480, 640), (16, 720, 1280)]
+    nfr = 4
+    data, ctxs, plain = [], [], []
+    for gi, (nb, h, w) in enumerate(groups):
+        clip = np.stack([f for f, _ in synth.clip_vga_frames(nfr + nb, h, w, seed=synth.SEED_BASE + 4 + gi)])
+        # stream k of the group sees frames k .. k+nfr-1 of the group's clip
+        fr = torch.from_numpy(np.stack([clip[t:t + nb] for t in range(nfr)])).cuda()  # (nfr, nb, h, w, 3)
+        sg = seg.Segmenter(h, w, p, batch=nb, stream=torch.cuda.Stream())
+        data.append(fr)
+        ctxs.append((sg, sg.empty_outputs()))
+        plain.append([seg.Segmenter(h, w, p) for _ in range(nb)])
+    step = [0]
+
+    def batched_step():
+        t_ = step[0] % nfr
+        for (sg, o), fr in zip(ctxs, data):
+            sg.push_frame(fr[t_], *o)
+        step[0] += 1
+
+    steps = 12
+    tb = timed(batched_step, steps)
+    pouts = [[sgp.empty_outputs() for sgp in grp] for grp in plain]
+    pstep = [0]
+
+    def plain_step():
+        t_ = pstep[0] % nfr
+        for grp, fr, po in zip(plain, data, pouts):
+            for k, sgp in enumerate(grp):
+                sgp.push_frame(fr[t_][k], *po[k])
+        pstep[0] += 1
+
+    tp = timed(plain_step, steps)
+    n = sum(g[0] for g in groups)
+    codes = [sg.sync()[0] for sg, _ in ctxs]
+    out["mixed64"] = {"streams": "24 x 320x240 + 24 x 640x480 + 16 x 1280x720", "frames_per_s": n * steps / tb,
+                      "plain_frames_per_s": n * steps / tp, "vs_plain": tp / tb, "steps": steps,
+                      "status": max(codes, key=abs)}
+    for sg, _ in ctxs:
+        sg.close()
+    for grp in plain:
+        for sgp in grp:
+            sgp.close()
+    return out
+
+
 def dist_setup(backend):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -195,6 +287,28 @@ def run_reference(a):
                          "sample": f"{a.steps} consecutive frames of the 640x480 clip, single-threaded C"},
         "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def run_only(a):
+    import torch
+    from paper_1008_0502_b300 import seg
+    pk, _ = peaks()
+    clip_dev = torch.from_numpy(make_clip(40)).cuda()
+    B = 32
+    sgs = seg.Segmenter(H, W, seg.params_from(VGA), batch=B)
+    fr32 = torch.stack([clip_dev[k] for k in range(B)])
+    sal32 = torch.empty(B, H, W, dtype=torch.float32, device="cuda")
+    for _ in range(a.warmup):
+        sgs.saliency(fr32, sal32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        sgs.saliency(fr32, sal32)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    byts = 7 * B * H * W
+    print(json.dumps({"only": a.only, "ms_per_call": t / a.steps * 1e3,
+                      "achieved_GBps": byts * a.steps / t / 1e9, "frac": byts * a.steps / t / 1e9 / pk["hbm_gbs"]}))
 
 
 def run_b300(a):
@@ -282,6 +396,7 @@ def run_b300(a):
             "frac": ach / hbm, "traffic": TRAFFIC_MAXFLOW,
             "algorithmic_bytes": f"{BYTES_MINCUT_SWEEP_PX} B/px/sweep x {H * W} px x {cycles:.2f} sweeps",
             "peak_kind": pk_kind}
+    batched = batched_suite(seg, torch, clip_dev, value / ws, hbm) if a.batched else None
     n_cpu, dt_cpu = cpu_baseline(clip, a.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": a.steps,
@@ -297,6 +412,7 @@ def run_b300(a):
                          "sample": f"first {n_cpu} frames of the same clip, single-threaded FP64 C oracle"},
         "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": H * W + 8},
+        "batched": batched,
         "gpu_launches": a.steps * kernels_per_frame(VGA),
         "clocks": clocks,
     }
@@ -305,7 +421,9 @@ def run_b300(a):
 
 def main():
     a = args()
-    if a.impl == "reference":
+    if a.only:
+        run_only(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_b300(a)

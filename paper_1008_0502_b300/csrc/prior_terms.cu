@@ -27,7 +27,9 @@
 #define MOM_PX 8  // pixels per thread in the moment passes
 
 struct PriorArgs {
-  const float* sal;
+  float* sal;      // input map, or (from_S) the saliency output (nullable)
+  const float* S;  // from_S: the combined map at sigma_S, hS x wS per frame
+  int hS, wS, from_S;
   const unsigned* salmax;
   const uint8_t* prev;
   const KalmanDev* kal;  // nullable: use wf_host
@@ -89,7 +91,8 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
   {  // frame of the batch
     const int fb = blockIdx.z;
     const size_t n = (size_t)a.H * a.W;
-    a.sal += fb * n;
+    if (a.sal) a.sal += fb * n;
+    if (a.from_S) a.S += (size_t)fb * a.hS * a.wS;
     a.prior += fb * n;
     if (a.prev) a.prev += fb * n;
     if (a.rgb) a.rgb += fb * 3 * n;
@@ -134,7 +137,14 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     if (gy >= a.H || gx >= a.W) continue;
     size_t g = (size_t)gy * a.W + gx;
     bool edge = gy < a.border || gy >= a.H - a.border || gx < a.border || gx >= a.W - a.border;
-    float q = edge ? a.eps : (mx > 0.f ? a.sal[g] / mx : 0.f);
+    float sv;
+    if (a.from_S) {  // the saliency map at this pixel: bilinear up-sampling of S
+      sv = seg_bilinear(a.S, a.hS, a.wS, gy, gx, a.H, a.W);
+      if (a.sal) a.sal[g] = sv;
+    } else {
+      sv = a.sal[g];
+    }
+    float q = edge ? a.eps : (mx > 0.f ? sv / mx : 0.f);
     float p = (1.f - wff) * q;
     if (use_f) {
       float f = 0.f;
@@ -438,11 +448,15 @@ int pt_launch_salmax(seg_ctx* c, const float* sal) {
 }
 
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
-                    double wf_host, float* prior, const uint8_t* rgb_moments) {
+                    double wf_host, float* prior, const uint8_t* rgb_moments, bool from_S) {
   const seg_params& p = c->p;
   PriorArgs a;
   memset(&a, 0, sizeof(a));
-  a.sal = sal;
+  a.sal = const_cast<float*>(sal);
+  a.from_S = from_S ? 1 : 0;
+  a.S = c->sal.S;
+  a.hS = c->sal.hl[c->sal.sS];
+  a.wS = c->sal.wl[c->sal.sS];
   a.salmax = c->sal.salmax;
   a.prev = prev_mask;
   a.kal = use_kalman ? c->kal : nullptr;

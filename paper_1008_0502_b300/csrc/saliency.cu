@@ -16,7 +16,8 @@
 //                   reduced maps)
 //   k_consp         one CTA per frame at sigma_S: orientation conspicuity,
 //                   N(C_k), S = sum_k w_k N(C_k)
-//   k_upsample      S -> frame-size saliency (bilinear) and its maximum
+//   k_upsample      S -> frame-size saliency (bilinear); seg_push_frame skips it
+//                   and lets the prior kernel evaluate the saliency on the fly
 #include <math.h>
 #include <string.h>
 
@@ -50,7 +51,13 @@ __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, uns
     m = max(m, s);
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(smax, m);
+  __shared__ int wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
+    if (m > 0) atomicMax(smax, m);
+  }
 }
 
 // ------------------------------------------------------------------ features + REDUCE
@@ -82,10 +89,10 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict_
     int s = r + g + b;
     float rn = 0.f, gn = 0.f, bn = 0.f;
     if (10 * s > smax) {
-      float fs = (float)s;
-      rn = (float)(3 * r) / fs;
-      gn = (float)(3 * g) / fs;
-      bn = (float)(3 * b) / fs;
+      float inv = 3.f / (float)s;
+      rn = (float)r * inv;
+      gn = (float)g * inv;
+      bn = (float)b * inv;
     }
     float R = fmaxf(0.f, rn - (gn + bn) / 2.f);
     float G = fmaxf(0.f, gn - (rn + bn) / 2.f);
@@ -274,6 +281,7 @@ struct CSArgs {
   int nbands_total;
   unsigned* mm;
   float* tpart;
+  float* nab;  // [frame][map][2]: N(.) as a*v + b
 };
 
 __device__ __forceinline__ float cs_value(const CSArgs& a, int f, int c, int s, int y, int x, int fb) {
@@ -286,11 +294,11 @@ __device__ __forceinline__ float cs_value(const CSArgs& a, int f, int c, int s, 
 #define CS_MAX_TILES_X 1024
 
 // Per (map, band of `tile` rows): min, max and the sum of the band's T x T tile
-// maxima (Sec. 7.2 step 3: block-wise extrema).  Maps are non-negative, so the
-// float bit patterns order like the values.
+// maxima (Sec. 7.2 step 3: block-wise extrema).  One warp reduces one tile at a
+// time with shuffles; maps are non-negative, so their float bit patterns order
+// like the values for the global min/max atomics.
 __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
-  __shared__ unsigned sTmax[CS_MAX_TILES_X];
-  __shared__ float sMin[8], sMax[8];
+  __shared__ float sMin[8], sMax[8], sTs[8];
   int b = blockIdx.x, p = 0;
   while (p < a.npairs - 1 && b >= a.pair_band_off[p + 1]) ++p;
   int c = a.pair_c[p], s = a.pair_s[p];
@@ -302,38 +310,39 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
   const int fb = blockIdx.y;  // frame of the batch
   unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * a.nch;
   float* tpart = a.tpart + (size_t)fb * a.nbands_total;
-  for (int i = threadIdx.x; i < ntx; i += blockDim.x) sTmax[i] = 0u;
-  __syncthreads();
-  int y0 = band * T, rows = min(T, hc - y0);
-  float mn = 3.0e38f, mx = 0.f;
-  for (int i = threadIdx.x; i < rows * wc; i += blockDim.x) {
-    int y = y0 + i / wc, x = i % wc;
-    float v = cs_value(a, f, c, s, y, x, fb);
-    mn = fminf(mn, v);
-    mx = fmaxf(mx, v);
-    atomicMax(&sTmax[x / T], __float_as_uint(v));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int y0 = band * T, rows = min(T, hc - y0);
+  float mn = 3.0e38f, mx = 0.f, ts = 0.f;
+  for (int tx = wid; tx < ntx; tx += nw) {
+    const int x0 = tx * T, cols = min(T, wc - x0);
+    float tm = 0.f;
+    for (int i = lane; i < rows * cols; i += 32) {
+      int yy = i / cols;
+      float v = cs_value(a, f, c, s, y0 + yy, x0 + (i - yy * cols), fb);
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+      tm = fmaxf(tm, v);
+    }
+    ts += seg_warp_max_f(tm);  // every lane holds the tile maximum
   }
   mn = seg_warp_min_f(mn);
   mx = seg_warp_max_f(mx);
-  if ((threadIdx.x & 31) == 0) {
-    sMin[threadIdx.x >> 5] = mn;
-    sMax[threadIdx.x >> 5] = mx;
+  if (lane == 0) {
+    sMin[wid] = mn;
+    sMax[wid] = mx;
+    sTs[wid] = ts;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    int nw = blockDim.x >> 5;
-    float a0 = threadIdx.x < nw ? sMin[threadIdx.x] : 3.0e38f;
-    float a1 = threadIdx.x < nw ? sMax[threadIdx.x] : 0.f;
-    float ts = 0.f;
-    for (int i = threadIdx.x; i < ntx; i += 32) ts += __uint_as_float(sTmax[i]);
-    a0 = seg_warp_min_f(a0);
-    a1 = seg_warp_max_f(a1);
-    ts = seg_warp_sum_f(ts);
-    if (threadIdx.x == 0) {
-      atomicMin(&mm[2 * m], __float_as_uint(a0));
-      atomicMax(&mm[2 * m + 1], __float_as_uint(a1));
-      tpart[b] = ts;
+  if (threadIdx.x == 0) {
+    float a0 = sMin[0], a1 = sMax[0], a2 = 0.f;
+    for (int w = 0; w < nw; ++w) {
+      a0 = fminf(a0, sMin[w]);
+      a1 = fmaxf(a1, sMax[w]);
+      a2 += sTs[w];
     }
+    atomicMin(&mm[2 * m], __float_as_uint(a0));
+    atomicMax(&mm[2 * m + 1], __float_as_uint(a1));
+    tpart[b] = a2;
   }
 }
 
@@ -367,14 +376,19 @@ __device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* 
   norm_affine(__uint_as_float(mm[2 * m]), __uint_as_float(mm[2 * m + 1]), sum, nb * ntx, flat, ab);
 }
 
+__global__ void k_cs_norm(CSArgs a, float flat, float* nab, int nframes) {
+  const int nm = a.npairs * a.nch;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nm * nframes) return;
+  const int fb = i / nm, m = i - fb * nm;
+  cs_map_affine(a, m / a.nch, m % a.nch, flat, nab + 2 * (size_t)i, fb);
+}
+
 // B_c(f) = sum over pairs (c, s) of N(CS_f(c, s)) + REDUCE(B_{c-1}(f)).
 __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, float flat, const float* __restrict__ prev,
                                                   int hp, int wp, float* __restrict__ out) {
-  __shared__ float sab[SEG_MAX_PAIRS][2];
   const int f = blockIdx.z % a.nch, fb = blockIdx.z / a.nch;  // channel, frame of the batch
-  if ((int)threadIdx.x < a.npairs && a.pair_c[threadIdx.x] == c)
-    cs_map_affine(a, threadIdx.x, f, flat, sab[threadIdx.x], fb);
-  __syncthreads();
+  const float* nab = a.nab + (size_t)fb * 2 * a.npairs * a.nch;
   int hc = a.hl[c], wc = a.wl[c];
   if (prev) prev += (size_t)fb * a.nch * hp * wp;
   out += (size_t)fb * a.nch * hc * wc;
@@ -383,7 +397,8 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, float flat, c
   float acc = 0.f;
   for (int p = 0; p < a.npairs; ++p) {
     if (a.pair_c[p] != c) continue;
-    acc += sab[p][0] * cs_value(a, f, c, a.pair_s[p], y, x, fb) + sab[p][1];
+    const int m = p * a.nch + f;
+    acc += nab[2 * m] * cs_value(a, f, c, a.pair_s[p], y, x, fb) + nab[2 * m + 1];
   }
   if (prev) {
     const float* pl = prev + (size_t)f * hp * wp;
@@ -471,6 +486,8 @@ __device__ void block_norm_multi(const float* const* v, int nm, int h, int w, in
 struct ConspArgs {
   const float* acc;  // nch planes at sigma_S
   int h, w, nch, tile;
+  int H, W;          // frame size of the up-sampled saliency
+  unsigned* salmax;  // per frame: max of the up-sampled saliency (float bits, >= 0)
   float flat;
   float wgt[4];
   float* csum;
@@ -517,24 +534,52 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
     }
     a.S[i] = S;
   }
+  __syncthreads();
+  // Maximum of the bilinear up-sampling of S to H x W without visiting every
+  // pixel: within one source cell the interpolant is bilinear in (y, x), so over
+  // the output samples of that cell it peaks at its first or last sample row and
+  // column.  Only those rows and columns are evaluated (same arithmetic as the
+  // up-sampling itself, so the value is identical).
+  int* crow = (int*)tmax;
+  int* ccol = crow + 2048;
+  __shared__ int nr, nc;
+  if (threadIdx.x == 0) nr = nc = 0;
+  __syncthreads();
+  auto cell = [](int d, int ns, int nd) {
+    int i0, i1;
+    float f;
+    seg_src_coord(d, ns, nd, i0, i1, f);
+    return (i0 == i1) ? (i0 == 0 && d < nd / 2 ? -1 : ns) : i0;
+  };
+  for (int y = threadIdx.x; y < a.H; y += blockDim.x) {
+    int id = cell(y, a.h, a.H);
+    if (y == 0 || y == a.H - 1 || cell(y - 1, a.h, a.H) != id || cell(y + 1, a.h, a.H) != id) crow[atomicAdd(&nr, 1)] = y;
+  }
+  for (int x = threadIdx.x; x < a.W; x += blockDim.x) {
+    int id = cell(x, a.w, a.W);
+    if (x == 0 || x == a.W - 1 || cell(x - 1, a.w, a.W) != id || cell(x + 1, a.w, a.W) != id) ccol[atomicAdd(&nc, 1)] = x;
+  }
+  __syncthreads();
+  float mxv = 0.f;
+  for (int k = threadIdx.x; k < nr * nc; k += blockDim.x)
+    mxv = fmaxf(mxv, seg_bilinear(a.S, a.h, a.w, crow[k / nc], ccol[k % nc], a.H, a.W));
+  mxv = seg_warp_max_f(mxv);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mxv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mxv = fmaxf(mxv, red[w]);
+    a.salmax[blockIdx.x] = __float_as_uint(fmaxf(red[0], mxv));
+  }
 }
 
 __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, int hs, int ws, int H,
-                                                  int W, float* __restrict__ sal, unsigned* salmax,
-                                                  const SegIO* io) {
+                                                  int W, float* __restrict__ sal, const SegIO* io) {
   if (!sal) sal = io->sal;
   const int fb = blockIdx.z;  // frame of the batch
   S += (size_t)fb * hs * ws;
   sal += (size_t)fb * H * W;
-  salmax += fb;
   int x = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
-  float v = 0.f;
-  if (x < W && y < H) {
-    v = seg_bilinear(S, hs, ws, y, x, H, W);
-    sal[(size_t)y * W + x] = v;
-  }
-  v = seg_warp_max_f(fmaxf(v, 0.f));
-  if ((threadIdx.x & 31) == 0) atomicMax(salmax, __float_as_uint(v));
+  if (x < W && y < H) sal[(size_t)y * W + x] = seg_bilinear(S, hs, ws, y, x, H, W);
 }
 
 // ------------------------------------------------------------------ host side
@@ -611,6 +656,7 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
   {
     int hS = s.hl[s.sS], wS = s.wl[s.sS];
     if (((hS + s.tile - 1) / s.tile) * ((wS + s.tile - 1) / s.tile) > CONSP_TILES) return SEG_EINVAL;
+    if (2 * hS + 4 > 2048 || 2 * wS + 4 > 2048) return SEG_EINVAL;  // candidate rows / columns of the max
   }
   make_taps(p, s.taps);
   size_t off = 0;
@@ -629,6 +675,7 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
       s.ori[k][l] = (float*)take(Bz * sizeof(float) * s.hl[l] * s.wl[l]);
   s.mm = (unsigned*)take(Bz * sizeof(unsigned) * 2 * s.nmaps);
   s.tpart = (float*)take(Bz * sizeof(float) * s.nbands_total);
+  s.nab = (float*)take(Bz * sizeof(float) * 2 * s.nmaps);
   size_t big = (size_t)s.hl[s.c_min] * s.wl[s.c_min] * s.nch;
   s.acc[0] = (float*)take(Bz * sizeof(float) * big);
   s.acc[1] = (float*)take(Bz * sizeof(float) * big);
@@ -653,6 +700,7 @@ void sal_bind(SalWS& s, char* base) {
     for (int l = s.c_min; l <= s.s_max; ++l) fix(s.ori[k][l]);
   fix(s.mm);
   fix(s.tpart);
+  fix(s.nab);
   fix(s.acc[0]);
   fix(s.acc[1]);
   fix(s.consp);
@@ -685,14 +733,14 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
   a.pair_band_off[s.npairs] = off;
   a.mm = s.mm;
   a.tpart = s.tpart;
+  a.nab = s.nab;
 }
 
-int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
+int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
   SalWS& s = c->sal;
   cudaStream_t st = c->stream;
   const int H = s.H, W = s.W, N = H * W, B = s.B;
   SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, B * sizeof(int), st));
-  SEG_CUDA_TRY(cudaMemsetAsync(s.salmax, 0, B * sizeof(unsigned), st));
   int nb = min((N + 255) / 256, B > 1 ? 148 : 148 * 8);
   nb = max(nb, (s.nmaps + 255) / 256);
   const SegIO* io = c->io_mode ? c->io : nullptr;
@@ -750,6 +798,7 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   CSArgs ca;
   fill_cs_args(s, ca);
   k_cs_stats<<<dim3(s.nbands_total, B), 256, 0, st>>>(ca);
+  k_cs_norm<<<(s.nmaps * B + 127) / 128, 128, 0, st>>>(ca, s.flat, s.nab, B);
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;
@@ -772,9 +821,14 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out) {
   pa.csum = s.csum;
   pa.consp = s.consp;
   pa.S = s.S;
+  pa.H = H;
+  pa.W = W;
+  pa.salmax = s.salmax;
   k_consp<<<B, 1024, 0, st>>>(pa);
-  dim3 gu((W + 63) / 64, (H + 3) / 4, B);
-  k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, s.salmax, io);
+  if (upsample) {
+    dim3 gu((W + 63) / 64, (H + 3) / 4, B);
+    k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io);
+  }
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }

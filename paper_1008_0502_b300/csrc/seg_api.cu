@@ -217,8 +217,8 @@ static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const in
 // frame pointer is nullptr and the kernels read them from c->io.
 static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, uint8_t* mask,
                          int64_t* cut) {
-  int rc = sal_launch(c, rgb, s);
-  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb);
+  int rc = sal_launch(c, rgb, s, false);
+  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb, true);
   if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
   if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
   return rc;
@@ -275,9 +275,9 @@ extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float*
     }
   }
   prof_mark(c, 0);
-  int rc = sal_launch(c, rgb, s);
+  int rc = sal_launch(c, rgb, s, false);
   prof_mark(c, 1);
-  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb);
+  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb, true);
   prof_mark(c, 2);
   if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
   prof_mark(c, 3);
@@ -444,7 +444,7 @@ extern "C" int seg_set_state(seg_ctx* c, const void* buf, size_t n) {
 
 extern "C" int seg_saliency(seg_ctx* c, const uint8_t* rgb, float* sal) {
   if (!c || !rgb || !sal) return SEG_EINVAL;
-  return sal_launch(c, rgb, sal);
+  return sal_launch(c, rgb, sal, true);
 }
 
 extern "C" int seg_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, double w_f,

@@ -111,6 +111,7 @@ struct SalWS {
   unsigned* mm;  // [nmaps][2]: min and max as float bits (maps are >= 0)
   float* tpart;  // [nbands_total]: per-band sums of tile maxima
   int nbands_total;
+  float* nab;     // [frame][map][2]: N(.) as the affine map a*v + b
   float* acc[2];  // ping-pong channel accumulators at scale c (nch planes)
   float* consp;   // 4 planes at sigma_S: N(C_I), N(C_RG), N(C_BY), N(C_O)
   float* csum;    // scratch plane at sigma_S
@@ -238,14 +239,18 @@ struct seg_ctx {
 // ---------------------------------------------------------------- launchers
 int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes);
 void sal_bind(SalWS& s, char* base);
-int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out);  // nullptr + c->io_mode: from c->io
+// upsample == false: stop at S and the saliency maximum (the prior kernel then
+// evaluates the saliency map itself); nullptr + c->io_mode: pointers from c->io
+int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample);
 
 int pt_mom_blocks(int H, int W);
 int pt_launch_salmax(seg_ctx* c, const float* sal);
 // rgb_moments != nullptr: also run the first moment pass (and, with use_kalman,
 // advance the Kalman variance) inside the prior kernel
+// from_S: compute the saliency map from the context's S (writing it to sal when
+// sal is non-null) instead of reading sal
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
-                    double wf_host, float* prior, const uint8_t* rgb_moments);
+                    double wf_host, float* prior, const uint8_t* rgb_moments, bool from_S = false);
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
                             int32_t* cs, int32_t* ct, int32_t* ncap);
 int pt_part_doubles(int H, int W);
