@@ -30,6 +30,8 @@ struct PriorArgs {
   float* sal;      // input map, or (from_S) the saliency output (nullable)
   const float* S;  // from_S: the combined map at sigma_S, hS x wS per frame
   int hS, wS, from_S;
+  const int2* frow;  // from_S: up-sampling tables S -> H x W
+  const int2* fcol;
   const unsigned* salmax;
   const uint8_t* prev;
   const KalmanDev* kal;  // nullable: use wf_host
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     bool edge = gy < a.border || gy >= a.H - a.border || gx < a.border || gx >= a.W - a.border;
     float sv;
     if (a.from_S) {  // the saliency map at this pixel: bilinear up-sampling of S
-      sv = seg_bilinear(a.S, a.hS, a.wS, gy, gx, a.H, a.W);
+      sv = seg_bilinear_t(a.S, a.wS, a.frow[gy], a.fcol[gx]);
       if (a.sal) a.sal[g] = sv;
     } else {
       sv = a.sal[g];
@@ -457,6 +459,8 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   a.S = c->sal.S;
   a.hS = c->sal.hl[c->sal.sS];
   a.wS = c->sal.wl[c->sal.sS];
+  a.frow = c->sal.rs + c->sal.rs_frow;
+  a.fcol = c->sal.rs + c->sal.rs_fcol;
   a.salmax = c->sal.salmax;
   a.prev = prev_mask;
   a.kal = use_kalman ? c->kal : nullptr;

@@ -19,6 +19,7 @@
 //   k_upsample      S -> frame-size saliency (bilinear); seg_push_frame skips it
 //                   and lets the prior kernel evaluate the saliency on the fly
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <type_traits>
@@ -81,11 +82,26 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict_
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
   const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
   const int smax = smax_p[fb];
-  for (int i = threadIdx.x; i < RED_IN_Y * RED_IN_X; i += blockDim.x) {
+  // all of this thread's input pixels are loaded first (independent loads in
+  // flight together), then turned into features
+  constexpr int NIN = RED_IN_Y * RED_IN_X, PER = (NIN + 255) / 256;
+  unsigned pk[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    int i = threadIdx.x + k * 256;
+    if (i < NIN) {
+      int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
+      int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
+      const uint8_t* p = rgb + 3 * ((size_t)gy * W + gx);
+      pk[k] = (unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    int i = threadIdx.x + k * 256;
+    if (i >= NIN) break;
     int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
-    int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
-    const uint8_t* p = rgb + 3 * ((size_t)gy * W + gx);
-    int r = p[0], g = p[1], b = p[2];
+    int r = pk[k] & 255, g = (pk[k] >> 8) & 255, b = pk[k] >> 16;
     int s = r + g + b;
     float rn = 0.f, gn = 0.f, bn = 0.f;
     if (10 * s > smax) {
@@ -238,7 +254,10 @@ __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
     for (int u = 0; u < K; ++u) acc += t.g0[u] * sIn[ry][x + u];
     sH0[ry][x] = acc;
   }
-  for (int k = 0; k < t.no; ++k) {
+  // one orientation per CTA when the grid has one z-slice per orientation (single
+  // frame), otherwise every orientation in turn from the same staged tile
+  const int k_begin = gridDim.z == 1 ? 0 : blockIdx.z, k_end = gridDim.z == 1 ? t.no : blockIdx.z + 1;
+  for (int k = k_begin; k < k_end; ++k) {
     __syncthreads();
     for (int i = threadIdx.x; i < iny * GB_TX; i += blockDim.x) {
       int ry = i / GB_TX, x = i - ry * GB_TX;
@@ -282,67 +301,92 @@ struct CSArgs {
   unsigned* mm;
   float* tpart;
   float* nab;  // [frame][map][2]: N(.) as a*v + b
+  const int2* rs;
+  int rs_row[SEG_MAX_PAIRS], rs_col[SEG_MAX_PAIRS];
 };
 
-__device__ __forceinline__ float cs_value(const CSArgs& a, int f, int c, int s, int y, int x, int fb) {
-  const float* cen = a.X[f][c] + (size_t)fb * a.hl[c] * a.wl[c];
-  float u = seg_bilinear(a.X[f][s] + (size_t)fb * a.hl[s] * a.wl[s], a.hl[s], a.wl[s], y, x, a.hl[c], a.wl[c]);
-  float v = cen[y * a.wl[c] + x];
-  return (a.opp_sum && (f == 1 || f == 2)) ? fabsf(v + u) : fabsf(v - u);
-}
 
 #define CS_MAX_TILES_X 1024
 
-// Per (map, band of `tile` rows): min, max and the sum of the band's T x T tile
-// maxima (Sec. 7.2 step 3: block-wise extrema).  One warp reduces one tile at a
-// time with shuffles; maps are non-negative, so their float bit patterns order
-// like the values for the global min/max atomics.
+// Per (center-surround pair, band of `tile` rows), for all NCH channels at once
+// (they share the pair's resampling coordinates): min, max and the sum of the
+// band's T x T tile maxima (Sec. 7.2 step 3: block-wise extrema).  One warp
+// reduces one tile at a time with shuffles; maps are non-negative, so their
+// float bit patterns order like the values for the global min/max atomics.
+template <int NCH, int CPB>
 __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
-  __shared__ float sMin[8], sMax[8], sTs[8];
-  int b = blockIdx.x, p = 0;
-  while (p < a.npairs - 1 && b >= a.pair_band_off[p + 1]) ++p;
-  int c = a.pair_c[p], s = a.pair_s[p];
-  int hc = a.hl[c], wc = a.wl[c], T = a.tile;
-  int nb = (hc + T - 1) / T, ntx = (wc + T - 1) / T;
-  int local = b - a.pair_band_off[p];
-  int f = local / nb, band = local - f * nb;
-  int m = p * a.nch + f;
+  __shared__ float sMin[8][CPB], sMax[8][CPB], sTs[8][CPB];
+  constexpr int G = NCH / CPB;  // channel groups per (pair, band)
+  const int f0 = (blockIdx.x % G) * CPB;
+  int b = blockIdx.x / G, p = 0;
+  while (p < a.npairs - 1 && b >= a.pair_band_off[p + 1] / NCH) ++p;
+  const int c = a.pair_c[p], sv = a.pair_s[p];
+  const int hc = a.hl[c], wc = a.wl[c], hs = a.hl[sv], ws = a.wl[sv], T = a.tile;
+  const int nb = (hc + T - 1) / T, ntx = (wc + T - 1) / T;
+  const int band = b - a.pair_band_off[p] / NCH;
   const int fb = blockIdx.y;  // frame of the batch
-  unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * a.nch;
+  unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * NCH;
   float* tpart = a.tpart + (size_t)fb * a.nbands_total;
+  const float* cen[CPB];
+  const float* sur[CPB];
+#pragma unroll
+  for (int f = 0; f < CPB; ++f) {
+    cen[f] = a.X[f0 + f][c] + (size_t)fb * hc * wc;
+    sur[f] = a.X[f0 + f][sv] + (size_t)fb * hs * ws;
+  }
+  const int2* trow = a.rs + a.rs_row[p];
+  const int2* tcol = a.rs + a.rs_col[p];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int y0 = band * T, rows = min(T, hc - y0);
-  float mn = 3.0e38f, mx = 0.f, ts = 0.f;
+  float mn[CPB], mx[CPB], ts[CPB];
+#pragma unroll
+  for (int f = 0; f < CPB; ++f) {
+    mn[f] = 3.0e38f;
+    mx[f] = 0.f;
+    ts[f] = 0.f;
+  }
   for (int tx = wid; tx < ntx; tx += nw) {
     const int x0 = tx * T, cols = min(T, wc - x0);
-    float tm = 0.f;
+    float tm[CPB];
+#pragma unroll
+    for (int f = 0; f < CPB; ++f) tm[f] = 0.f;
     for (int i = lane; i < rows * cols; i += 32) {
-      int yy = i / cols;
-      float v = cs_value(a, f, c, s, y0 + yy, x0 + (i - yy * cols), fb);
-      mn = fminf(mn, v);
-      mx = fmaxf(mx, v);
-      tm = fmaxf(tm, v);
+      const int yy = i / cols, y = y0 + yy, x = x0 + (i - yy * cols);
+      const int2 ry = trow[y], rx = tcol[x];
+#pragma unroll
+      for (int f = 0; f < CPB; ++f) {
+        float u = seg_bilinear_t(sur[f], ws, ry, rx), v0 = cen[f][y * wc + x];
+        const int ch = f0 + f;
+        float v = (a.opp_sum && (ch == 1 || ch == 2)) ? fabsf(v0 + u) : fabsf(v0 - u);
+        mn[f] = fminf(mn[f], v);
+        mx[f] = fmaxf(mx[f], v);
+        tm[f] = fmaxf(tm[f], v);
+      }
     }
-    ts += seg_warp_max_f(tm);  // every lane holds the tile maximum
+#pragma unroll
+    for (int f = 0; f < CPB; ++f) ts[f] += seg_warp_max_f(tm[f]);  // every lane holds the tile maximum
   }
-  mn = seg_warp_min_f(mn);
-  mx = seg_warp_max_f(mx);
-  if (lane == 0) {
-    sMin[wid] = mn;
-    sMax[wid] = mx;
-    sTs[wid] = ts;
+#pragma unroll
+  for (int f = 0; f < CPB; ++f) {
+    float a0 = seg_warp_min_f(mn[f]), a1 = seg_warp_max_f(mx[f]);
+    if (lane == 0) {
+      sMin[wid][f] = a0;
+      sMax[wid][f] = a1;
+      sTs[wid][f] = ts[f];
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float a0 = sMin[0], a1 = sMax[0], a2 = 0.f;
+  if ((int)threadIdx.x < CPB) {
+    const int f = threadIdx.x, m = p * NCH + f0 + f;
+    float a0 = sMin[0][f], a1 = sMax[0][f], a2 = 0.f;
     for (int w = 0; w < nw; ++w) {
-      a0 = fminf(a0, sMin[w]);
-      a1 = fmaxf(a1, sMax[w]);
-      a2 += sTs[w];
+      a0 = fminf(a0, sMin[w][f]);
+      a1 = fmaxf(a1, sMax[w][f]);
+      a2 += sTs[w][f];
     }
     atomicMin(&mm[2 * m], __float_as_uint(a0));
     atomicMax(&mm[2 * m + 1], __float_as_uint(a1));
-    tpart[b] = a2;
+    tpart[a.pair_band_off[p] + (f0 + f) * nb + band] = a2;
   }
 }
 
@@ -385,33 +429,70 @@ __global__ void k_cs_norm(CSArgs a, float flat, float* nab, int nframes) {
 }
 
 // B_c(f) = sum over pairs (c, s) of N(CS_f(c, s)) + REDUCE(B_{c-1}(f)).
-__global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, float flat, const float* __restrict__ prev,
-                                                  int hp, int wp, float* __restrict__ out) {
-  const int f = blockIdx.z % a.nch, fb = blockIdx.z / a.nch;  // channel, frame of the batch
-  const float* nab = a.nab + (size_t)fb * 2 * a.npairs * a.nch;
-  int hc = a.hl[c], wc = a.wl[c];
-  if (prev) prev += (size_t)fb * a.nch * hp * wp;
-  out += (size_t)fb * a.nch * hc * wc;
-  int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (x >= wc || y >= hc) return;
-  float acc = 0.f;
-  for (int p = 0; p < a.npairs; ++p) {
-    if (a.pair_c[p] != c) continue;
-    const int m = p * a.nch + f;
-    acc += nab[2 * m] * cs_value(a, f, c, a.pair_s[p], y, x, fb) + nab[2 * m + 1];
+#define ACC_TX 32
+#define ACC_TY 8
+// B_c = sum over pairs (c, s) of N(CS(c, s)) + REDUCE(B_{c-1}), all NCH channels
+// of a 32 x 8 output tile per CTA; the REDUCE input tile (with its 2-pixel
+// halo) is staged in shared memory one channel at a time.
+template <int NCH, int CPB>
+__global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* __restrict__ prev, int hp,
+                                                  int wp, float* __restrict__ out) {
+  __shared__ float sP[2 * ACC_TY + 3][2 * ACC_TX + 3];
+  __shared__ float sH[2 * ACC_TY + 3][ACC_TX];
+  constexpr int G = NCH / CPB;                  // channel groups
+  const int fb = blockIdx.z / G;                // frame of the batch
+  const int f0 = (blockIdx.z % G) * CPB;        // first channel of this CTA
+  const float* nab = a.nab + (size_t)fb * 2 * a.npairs * NCH;
+  const int hc = a.hl[c], wc = a.wl[c];
+  if (prev) prev += (size_t)fb * NCH * hp * wp;
+  out += (size_t)fb * NCH * hc * wc;
+  const int X0 = blockIdx.x * ACC_TX, Y0 = blockIdx.y * ACC_TY;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const int x = X0 + lx, y = Y0 + ly;
+  const bool in = x < wc && y < hc;
+  float acc[CPB];
+#pragma unroll
+  for (int f = 0; f < CPB; ++f) acc[f] = 0.f;
+  if (in) {
+    for (int p = 0; p < a.npairs; ++p) {
+      if (a.pair_c[p] != c) continue;
+      const int sv = a.pair_s[p], hs = a.hl[sv], ws = a.wl[sv];
+      const int2 ry = a.rs[a.rs_row[p] + y], rx = a.rs[a.rs_col[p] + x];
+#pragma unroll
+      for (int f = 0; f < CPB; ++f) {
+        const int ch = f0 + f, m = p * NCH + ch;
+        float u = seg_bilinear_t(a.X[ch][sv] + (size_t)fb * hs * ws, ws, ry, rx);
+        float v0 = a.X[ch][c][(size_t)fb * hc * wc + (size_t)y * wc + x];
+        float v = (a.opp_sum && (ch == 1 || ch == 2)) ? fabsf(v0 + u) : fabsf(v0 - u);
+        acc[f] += nab[2 * m] * v + nab[2 * m + 1];
+      }
+    }
   }
   if (prev) {
-    const float* pl = prev + (size_t)f * hp * wp;
-    float r = 0.f;
-    for (int j = 0; j < 5; ++j) {
-      const float* row = pl + (size_t)seg_clampi(2 * y + j - 2, 0, hp - 1) * wp;
-      float hsum = 0.f;
-      for (int i = 0; i < 5; ++i) hsum += c_binom[i] * row[seg_clampi(2 * x + i - 2, 0, wp - 1)];
-      r += c_binom[j] * hsum;
+    const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
+#pragma unroll
+    for (int f = 0; f < CPB; ++f) {
+      const float* pl = prev + (size_t)(f0 + f) * hp * wp;
+      for (int i = threadIdx.x; i < (2 * ACC_TY + 3) * (2 * ACC_TX + 3); i += blockDim.x) {
+        int ry = i / (2 * ACC_TX + 3), rx = i - ry * (2 * ACC_TX + 3);
+        sP[ry][rx] = pl[(size_t)seg_clampi(gy0 + ry, 0, hp - 1) * wp + seg_clampi(gx0 + rx, 0, wp - 1)];
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < (2 * ACC_TY + 3) * ACC_TX; i += blockDim.x) {
+        int ry = i / ACC_TX, xx = i - ry * ACC_TX;
+        const float* row = &sP[ry][2 * xx];
+        sH[ry][xx] = c_binom[0] * row[0] + c_binom[1] * row[1] + c_binom[2] * row[2] + c_binom[3] * row[3] +
+                     c_binom[4] * row[4];
+      }
+      __syncthreads();
+      acc[f] += c_binom[0] * sH[2 * ly][lx] + c_binom[1] * sH[2 * ly + 1][lx] + c_binom[2] * sH[2 * ly + 2][lx] +
+                c_binom[3] * sH[2 * ly + 3][lx] + c_binom[4] * sH[2 * ly + 4][lx];
+      __syncthreads();
     }
-    acc += r;
   }
-  out[(size_t)f * hc * wc + (size_t)y * wc + x] = acc;
+  if (in)
+#pragma unroll
+    for (int f = 0; f < CPB; ++f) out[(size_t)(f0 + f) * hc * wc + (size_t)y * wc + x] = acc[f];
 }
 
 // ------------------------------------------------------------------ conspicuity, S
@@ -488,6 +569,8 @@ struct ConspArgs {
   int h, w, nch, tile;
   int H, W;          // frame size of the up-sampled saliency
   unsigned* salmax;  // per frame: max of the up-sampled saliency (float bits, >= 0)
+  const int2* frow;  // final up-sampling tables
+  const int2* fcol;
   float flat;
   float wgt[4];
   float* csum;
@@ -562,7 +645,7 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   __syncthreads();
   float mxv = 0.f;
   for (int k = threadIdx.x; k < nr * nc; k += blockDim.x)
-    mxv = fmaxf(mxv, seg_bilinear(a.S, a.h, a.w, crow[k / nc], ccol[k % nc], a.H, a.W));
+    mxv = fmaxf(mxv, seg_bilinear_t(a.S, a.w, a.frow[crow[k / nc]], a.fcol[ccol[k % nc]]));
   mxv = seg_warp_max_f(mxv);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mxv;
   __syncthreads();
@@ -573,13 +656,14 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, int hs, int ws, int H,
-                                                  int W, float* __restrict__ sal, const SegIO* io) {
+                                                  int W, float* __restrict__ sal, const SegIO* io,
+                                                  const int2* __restrict__ frow, const int2* __restrict__ fcol) {
   if (!sal) sal = io->sal;
   const int fb = blockIdx.z;  // frame of the batch
   S += (size_t)fb * hs * ws;
   sal += (size_t)fb * H * W;
   int x = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
-  if (x < W && y < H) sal[(size_t)y * W + x] = seg_bilinear(S, hs, ws, y, x, H, W);
+  if (x < W && y < H) sal[(size_t)y * W + x] = seg_bilinear_t(S, ws, frow[y], fcol[x]);
 }
 
 // ------------------------------------------------------------------ host side
@@ -685,6 +769,19 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
   s.S = (float*)take(Bz * sizeof(float) * nS);
   s.salmax = (unsigned*)take(Bz * sizeof(unsigned));
   s.smax = (int*)take(Bz * sizeof(int));
+  int nrs = 0;
+  for (int i = 0; i < s.npairs; ++i) {
+    s.rs_row[i] = nrs;
+    nrs += s.hl[s.pair_c[i]];
+    s.rs_col[i] = nrs;
+    nrs += s.wl[s.pair_c[i]];
+  }
+  s.rs_frow = nrs;
+  nrs += H;
+  s.rs_fcol = nrs;
+  nrs += W;
+  s.rs_n = nrs;
+  s.rs = (int2*)take(sizeof(int2) * nrs);
   *bytes = off;
   return SEG_OK;
 }
@@ -708,6 +805,23 @@ void sal_bind(SalWS& s, char* base) {
   fix(s.S);
   fix(s.salmax);
   fix(s.smax);
+  fix(s.rs);
+}
+
+int sal_upload_tables(const SalWS& s) {
+  int2* t = (int2*)malloc(sizeof(int2) * s.rs_n);
+  if (!t) return SEG_ENOMEM;
+  for (int i = 0; i < s.npairs; ++i) {
+    int c = s.pair_c[i], sv = s.pair_s[i];
+    for (int y = 0; y < s.hl[c]; ++y) t[s.rs_row[i] + y] = seg_rs_entry(y, s.hl[sv], s.hl[c]);
+    for (int x = 0; x < s.wl[c]; ++x) t[s.rs_col[i] + x] = seg_rs_entry(x, s.wl[sv], s.wl[c]);
+  }
+  int hS = s.hl[s.sS], wS = s.wl[s.sS];
+  for (int y = 0; y < s.H; ++y) t[s.rs_frow + y] = seg_rs_entry(y, hS, s.H);
+  for (int x = 0; x < s.W; ++x) t[s.rs_fcol + x] = seg_rs_entry(x, wS, s.W);
+  cudaError_t e = cudaMemcpy(s.rs, t, sizeof(int2) * s.rs_n, cudaMemcpyHostToDevice);
+  free(t);
+  return e == cudaSuccess ? SEG_OK : SEG_ECUDA;
 }
 
 static void fill_cs_args(const SalWS& s, CSArgs& a) {
@@ -734,6 +848,11 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
   a.mm = s.mm;
   a.tpart = s.tpart;
   a.nab = s.nab;
+  a.rs = s.rs;
+  for (int i = 0; i < s.npairs; ++i) {
+    a.rs_row[i] = s.rs_row[i];
+    a.rs_col[i] = s.rs_col[i];
+  }
 }
 
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
@@ -794,17 +913,50 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
     tot += ((s.wl[l] + GB_TX - 1) / GB_TX) * ((s.hl[l] + GB_TY - 1) / GB_TY);
   }
   ga.blk_off[s.s_max - s.c_min + 1] = tot;
-  k_gabor<<<dim3(tot, B), 256, 0, st>>>(ga, s.taps);
+  k_gabor<<<dim3(tot, B, B == 1 ? s.no : 1), 256, 0, st>>>(ga, s.taps);
   CSArgs ca;
   fill_cs_args(s, ca);
-  k_cs_stats<<<dim3(s.nbands_total, B), 256, 0, st>>>(ca);
+  {
+    // one channel per CTA for a single frame (more CTAs), all channels of a pair
+    // per CTA for a batch (shared resampling coordinates, fewer CTAs)
+    const bool per_ch = B == 1;
+    const dim3 g((s.nbands_total / s.nch) * (per_ch ? s.nch : 1), B);
+    switch (s.nch) {
+#define SEG_CS_STATS(n)                                 \
+  case n:                                               \
+    if (per_ch)                                         \
+      k_cs_stats<n, 1><<<g, 256, 0, st>>>(ca);          \
+    else                                                \
+      k_cs_stats<n, n><<<g, 256, 0, st>>>(ca);          \
+    break;
+      SEG_CS_STATS(4) SEG_CS_STATS(5) SEG_CS_STATS(6) SEG_CS_STATS(7)
+      SEG_CS_STATS(8) SEG_CS_STATS(9) SEG_CS_STATS(10) SEG_CS_STATS(11)
+#undef SEG_CS_STATS
+      default:
+        return SEG_EINVAL;
+    }
+  }
   k_cs_norm<<<(s.nmaps * B + 127) / 128, 128, 0, st>>>(ca, s.flat, s.nab, B);
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;
   for (int cc = s.c_min; cc <= s.c_max; ++cc) {
-    dim3 g((s.wl[cc] + 31) / 32, (s.hl[cc] + 7) / 8, s.nch * B);
-    k_cs_accum<<<g, 256, 0, st>>>(ca, cc, s.flat, prev, hp, wp, s.acc[cur]);
+    const bool per_ch = B == 1;
+    dim3 g((s.wl[cc] + ACC_TX - 1) / ACC_TX, (s.hl[cc] + ACC_TY - 1) / ACC_TY, B * (per_ch ? s.nch : 1));
+    switch (s.nch) {
+#define SEG_CS_ACC(n)                                                          \
+  case n:                                                                      \
+    if (per_ch)                                                                \
+      k_cs_accum<n, 1><<<g, 256, 0, st>>>(ca, cc, prev, hp, wp, s.acc[cur]);   \
+    else                                                                       \
+      k_cs_accum<n, n><<<g, 256, 0, st>>>(ca, cc, prev, hp, wp, s.acc[cur]);   \
+    break;
+      SEG_CS_ACC(4) SEG_CS_ACC(5) SEG_CS_ACC(6) SEG_CS_ACC(7)
+      SEG_CS_ACC(8) SEG_CS_ACC(9) SEG_CS_ACC(10) SEG_CS_ACC(11)
+#undef SEG_CS_ACC
+      default:
+        return SEG_EINVAL;
+    }
     prev = s.acc[cur];
     hp = s.hl[cc];
     wp = s.wl[cc];
@@ -824,10 +976,13 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
   pa.H = H;
   pa.W = W;
   pa.salmax = s.salmax;
+  pa.frow = s.rs + s.rs_frow;
+  pa.fcol = s.rs + s.rs_fcol;
   k_consp<<<B, 1024, 0, st>>>(pa);
   if (upsample) {
     dim3 gu((W + 63) / 64, (H + 3) / 4, B);
-    k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io);
+    k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,
+                                   s.rs + s.rs_fcol);
   }
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;

@@ -157,6 +157,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
   pt_fill_lut(*p, lut);
   bool ok = cudaMemcpy(c->lut, lut, sizeof(int) * 766 * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && sal_upload_tables(c->sal) == SEG_OK;
   free(lut);
   ok = ok && cudaMemset(c->kal, 0, B * sizeof(KalmanDev)) == cudaSuccess;
   ok = ok && cudaMemset(c->prev_mask, 0, BN) == cudaSuccess;

@@ -64,6 +64,48 @@ __device__ __forceinline__ float seg_bilinear(const float* src, int hs, int ws, 
   return (1.f - fy) * top + fy * bot;
 }
 
+// Precomputed form of seg_src_coord for every output row/column of one
+// resampling: .x packs i0 | i1 << 16, .y holds the fraction's bits.  Built on
+// the host with the same integer arithmetic and one IEEE division, so a table
+// lookup gives exactly what seg_src_coord computes.
+__host__ __device__ inline int2 seg_rs_entry(int d, int ns, int nd) {
+  int i0, i1;
+  float f;
+  int num = (2 * d + 1) * ns - nd;
+  if (num <= 0) {
+    i0 = i1 = 0;
+    f = 0.f;
+  } else {
+    int den = 2 * nd, q = num / den;
+    if (q >= ns - 1) {
+      i0 = i1 = ns - 1;
+      f = 0.f;
+    } else {
+      i0 = q;
+      i1 = q + 1;
+      f = (float)(num - q * den) / (float)den;
+    }
+  }
+  int2 e;
+  e.x = i0 | (i1 << 16);
+  union {
+    float f;
+    int i;
+  } u;
+  u.f = f;
+  e.y = u.i;
+  return e;
+}
+
+// Bilinear sample (same arithmetic as seg_bilinear) from row/column tables.
+__device__ __forceinline__ float seg_bilinear_t(const float* src, int ws, int2 ry, int2 rx) {
+  const int y0 = ry.x & 0xffff, y1 = ry.x >> 16, x0 = rx.x & 0xffff, x1 = rx.x >> 16;
+  const float fy = __int_as_float(ry.y), fx = __int_as_float(rx.y);
+  float top = (1.f - fx) * src[y0 * ws + x0] + fx * src[y0 * ws + x1];
+  float bot = (1.f - fx) * src[y1 * ws + x0] + fx * src[y1 * ws + x1];
+  return (1.f - fy) * top + fy * bot;
+}
+
 __device__ __forceinline__ double seg_warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -119,6 +161,11 @@ struct SalWS {
   unsigned* salmax;  // max of the upsampled saliency (float bits)
   int* smax;         // frame max of r+g+b
   GaborTaps taps;
+  // resampling tables (seg_rs_entry): per center-surround pair p, rows
+  // hl[s]->hl[c] at rs + rs_row[p] and columns wl[s]->wl[c] at rs + rs_col[p];
+  // the final up-sampling S -> H x W at rs + rs_frow / rs + rs_fcol
+  int2* rs;
+  int rs_row[SEG_MAX_PAIRS], rs_col[SEG_MAX_PAIRS], rs_frow, rs_fcol, rs_n;
 };
 
 // Frame-varying pointers of seg_push_frame, read by the kernels of the captured
@@ -239,6 +286,7 @@ struct seg_ctx {
 // ---------------------------------------------------------------- launchers
 int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes);
 void sal_bind(SalWS& s, char* base);
+int sal_upload_tables(const SalWS& s);
 // upsample == false: stop at S and the saliency maximum (the prior kernel then
 // evaluates the saliency map itself); nullptr + c->io_mode: pointers from c->io
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample);
