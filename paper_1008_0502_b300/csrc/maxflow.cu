@@ -311,30 +311,57 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   const int ntiles = a.ntx * a.nty;
 
   const long long t_start = mf_now();
-  // ---- 1. init
+  // ---- 1. init.  Cold: all n-link flows 0.  Warm (a.flow and the frame's warm
+  // flag): the previous frame's n-link flows, clamped to the new capacities; a
+  // node left with more outflow than its source capacity gets the deficit added
+  // to both of its terminal links, which adds the same constant to every cut
+  // (minimum cuts unchanged), and the cut value sum(ct - residual to t) with the
+  // original ct removes that constant again.
   for (int u = gtid; u < N; u += nthr) {
     int y = u / W, x = u - y * W;
     int cs = a.cs[u], ct = a.ct[u];
     bool bad = !cap_ok(cs) || !cap_ok(ct);
-    int m = min(cs, ct);
-    a.e[u] = cs - m;
-    a.rt[u] = ct - m;
-    int cE = x + 1 < W ? a.ncap[u] : 0;
-    int cS = y + 1 < H ? a.ncap[N + u] : 0;
+    const int cE = x + 1 < W ? a.ncap[u] : 0;
+    const int cW = x > 0 ? a.ncap[u - 1] : 0;
+    const int cS = y + 1 < H ? a.ncap[N + u] : 0;
+    const int cN = y > 0 ? a.ncap[N + u - W] : 0;
     bad |= !cap_ok(cE) || !cap_ok(cS);
-    a.r[0 * N + u] = cE;
-    a.r[1 * N + u] = x > 0 ? a.ncap[u - 1] : 0;
-    a.r[2 * N + u] = cS;
-    a.r[3 * N + u] = y > 0 ? a.ncap[N + u - W] : 0;
+    const bool warm = a.flow != nullptr && a.warm[y / a.frame_h];
+    auto clampf = [](int f, int c) { return f > c ? c : (f < -c ? -c : f); };
+    // forward flows leave u (E, S, SE, SW); backward ones (W, N, NW, NE) enter u
+    const int fE = warm && x + 1 < W ? clampf(a.flow[u], cE) : 0;
+    const int fW = warm && x > 0 ? clampf(a.flow[u - 1], cW) : 0;
+    const int fS = warm && y + 1 < H ? clampf(a.flow[N + u], cS) : 0;
+    const int fN = warm && y > 0 ? clampf(a.flow[N + u - W], cN) : 0;
+    int net_out = fE - fW + fS - fN;
+    a.r[0 * N + u] = cE - fE;
+    a.r[1 * N + u] = cW + fW;
+    a.r[2 * N + u] = cS - fS;
+    a.r[3 * N + u] = cN + fN;
     if (ND == 8) {
-      int cSE = (x + 1 < W && y + 1 < H) ? a.ncap[2 * N + u] : 0;
-      int cSW = (x > 0 && y + 1 < H) ? a.ncap[3 * N + u] : 0;
+      const int cSE = (x + 1 < W && y + 1 < H) ? a.ncap[2 * N + u] : 0;
+      const int cNW = (x > 0 && y > 0) ? a.ncap[2 * N + u - W - 1] : 0;
+      const int cSW = (x > 0 && y + 1 < H) ? a.ncap[3 * N + u] : 0;
+      const int cNE = (x + 1 < W && y > 0) ? a.ncap[3 * N + u - W + 1] : 0;
       bad |= !cap_ok(cSE) || !cap_ok(cSW);
-      a.r[4 * N + u] = cSE;
-      a.r[5 * N + u] = (x > 0 && y > 0) ? a.ncap[2 * N + u - W - 1] : 0;
-      a.r[6 * N + u] = cSW;
-      a.r[7 * N + u] = (x + 1 < W && y > 0) ? a.ncap[3 * N + u - W + 1] : 0;
+      const int fSE = warm && x + 1 < W && y + 1 < H ? clampf(a.flow[2 * N + u], cSE) : 0;
+      const int fNW = warm && x > 0 && y > 0 ? clampf(a.flow[2 * N + u - W - 1], cNW) : 0;
+      const int fSW = warm && x > 0 && y + 1 < H ? clampf(a.flow[3 * N + u], cSW) : 0;
+      const int fNE = warm && x + 1 < W && y > 0 ? clampf(a.flow[3 * N + u - W + 1], cNE) : 0;
+      net_out += fSE - fNW + fSW - fNE;
+      a.r[4 * N + u] = cSE - fSE;
+      a.r[5 * N + u] = cNW + fNW;
+      a.r[6 * N + u] = cSW - fSW;
+      a.r[7 * N + u] = cNE + fNE;
     }
+    int e0 = cs - net_out, cte = ct;
+    if (e0 < 0) {  // deficit
+      cte = ct - e0;
+      e0 = 0;
+    }
+    const int m = min(e0, cte);
+    a.e[u] = e0 - m;
+    a.rt[u] = cte - m;
     if (bad) atomicCAS(&a.status[0], 0, SEG_ECAPACITY);
   }
   for (int t = gtid; t < ntiles; t += nthr) {
@@ -470,7 +497,18 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     uint8_t v = a.z[u];
     mask_out[u] = v;
     if (a.mask_state) a.mask_state[u] = v;
+    if (a.flow) {  // n-link flows of this cut, the next frame's warm start
+      const int y = u / W, x = u - y * W;
+      a.flow[u] = x + 1 < W ? a.ncap[u] - a.r[0 * N + u] : 0;
+      a.flow[N + u] = y + 1 < H ? a.ncap[N + u] - a.r[2 * N + u] : 0;
+      if (ND == 8) {
+        a.flow[2 * N + u] = (x + 1 < W && y + 1 < H) ? a.ncap[2 * N + u] - a.r[4 * N + u] : 0;
+        a.flow[3 * N + u] = (x > 0 && y + 1 < H) ? a.ncap[3 * N + u] - a.r[6 * N + u] : 0;
+      }
+    }
   }
+  if (a.flow && blockIdx.x == 0)
+    for (int fb = threadIdx.x; fb < a.nframes; fb += blockDim.x) a.warm[fb] = 1;
   long long* cut_out = a.cut_out ? a.cut_out : (a.io ? a.io->cut : nullptr);
   if (cut_out && blockIdx.x == 0)
     for (int fb = threadIdx.x; fb < a.nframes; fb += blockDim.x)
@@ -536,9 +574,11 @@ int mf_grid_size(int H, int W, int* grid) {
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io) {
+              const SegIO* io, int* flow, unsigned char* warm) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
+  a.flow = flow;
+  a.warm = warm;
   if (H % m.nframes) return SEG_EINVAL;
   a.nframes = m.nframes;
   a.frame_h = H / m.nframes;

@@ -51,6 +51,7 @@ extern "C" int seg_default_params(seg_params* p) {
   p->global_relabel_every = 2;
   p->local_iters = 16;
   p->use_graph = 1;
+  p->warm_start = 1;
   return SEG_OK;
 }
 
@@ -129,6 +130,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   size_t o_prev = take(BN), o_cs = take(4 * BN), o_ct = take(4 * BN), o_ncap = take(4 * BN * nk);
   size_t o_sal = take(4 * BN), o_prior = take(4 * BN), o_mask = take(BN), o_cut = take(8 * B);
   size_t o_rgb = take(3 * BN), o_status = take(32), o_io = take(sizeof(SegIO));
+  size_t o_flow = take(4 * BN * nk), o_warm = take(B);
   size_t o_mf = take(mf_bytes(B * H, W, p->neighbourhood, B));
   char* base = nullptr;
   if (cudaMalloc((void**)&base, off) != cudaSuccess) {
@@ -153,6 +155,8 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   c->rgb_stage = (uint8_t*)(base + o_rgb);
   c->status = (int*)(base + o_status);
   c->io = (SegIO*)(base + o_io);
+  c->flow = (int*)(base + o_flow);
+  c->warm = (unsigned char*)(base + o_warm);
   mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
   pt_fill_lut(*p, lut);
@@ -163,6 +167,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   ok = ok && cudaMemset(c->prev_mask, 0, BN) == cudaSuccess;
   ok = ok && cudaMemset(c->status, 0, 32) == cudaSuccess;
   ok = ok && cudaMemset(c->mom_counter, 0, B * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMemset(c->warm, 0, B) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
   ok = ok && mf_grid_size(B * H, W, &c->mf_grid) == SEG_OK;
   if (!ok) {
@@ -190,6 +195,7 @@ extern "C" int seg_reset(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, c->B * sizeof(KalmanDev), c->stream));
   SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask, 0, (size_t)c->B * c->N, c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->warm, 0, c->B, c->stream));
   return SEG_OK;
 }
 
@@ -197,6 +203,7 @@ extern "C" int seg_reset_stream(seg_ctx* c, int b) {
   if (!c || b < 0 || b >= c->B) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaMemsetAsync(c->kal + b, 0, sizeof(KalmanDev), c->stream));
   SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask + (size_t)b * c->N, 0, c->N, c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->warm + b, 0, 1, c->stream));
   return SEG_OK;
 }
 
@@ -205,13 +212,16 @@ extern "C" int seg_reset_stream(seg_ctx* c, int b) {
 // neighbour outside the frame), so the stacked cut is the B cuts side by side.
 static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
                       uint8_t* mask, uint8_t* mask_state, int64_t* cut) {
+  // the per-stream path (mask_state set) warm-starts from the stream's last cut
+  int* flow = (mask_state && c->p.warm_start) ? c->flow : nullptr;
+  unsigned char* warm = flow ? c->warm : nullptr;
   if (c->io_mode)  // mask and cut come from the frame's SegIO
     return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
                      nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
-                     c->p.local_iters, c->io);
+                     c->p.local_iters, c->io, flow, warm);
   return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
-                   c->p.global_relabel_every, c->p.local_iters);
+                   c->p.global_relabel_every, c->p.local_iters, nullptr, flow, warm);
 }
 
 // The launch sequence of one frame.  With c->io_mode set (graph capture) every
@@ -440,6 +450,7 @@ extern "C" int seg_set_state(seg_ctx* c, const void* buf, size_t n) {
     SEG_CUDA_TRY(cudaMemcpy(c->kal + i, &k, sizeof(k), cudaMemcpyHostToDevice));
   }
   SEG_CUDA_TRY(cudaMemcpy(c->prev_mask, b + 16 + 16 * (size_t)c->B, (size_t)c->B * c->N, cudaMemcpyHostToDevice));
+  SEG_CUDA_TRY(cudaMemset(c->warm, 0, c->B));  // flows are not part of the state: next cut starts cold
   return SEG_OK;
 }
 

@@ -221,6 +221,8 @@ struct MFArgs {
   uint8_t* mask_state;  // nullable second copy of the mask
   long long* cut_out;   // nullable
   const SegIO* io;      // mask_out / cut_out == nullptr: take them from here
+  int* flow;            // nullable: nbr/2 planes of n-link flows (warm start in, final out)
+  unsigned char* warm;  // per frame: flow holds the previous frame's flows
   unsigned long long* cut_acc;
   unsigned int* flags;  // [3] rotating round counters
   int* tstamp;           // per tile: last round (epoch) in which a fixpoint changed it
@@ -277,6 +279,8 @@ struct seg_ctx {
   cudaGraphExec_t gexec;
   int* status;       // device [8]
   int* status_host;  // pinned [8]
+  int* flow;            // warm start: nbr/2 planes of B*N n-link flows
+  unsigned char* warm;  // [B] flow valid for the stream
   // optional per-stage timing (seg_profile_enable)
   int prof_on, prof_n, prof_cap;
   cudaEvent_t* prof_ev;  // 5 per frame
@@ -311,6 +315,6 @@ int mf_grid_size(int H, int W, int* grid);
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io = nullptr);
+              const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -284,3 +284,21 @@ def test_graph_replay_equals_eager_launches(S):
             assert torch.equal(a, b), t
     g.close()
     e.close()
+
+
+@pytest.mark.parametrize("start", [0, 232])
+def test_warm_start_equals_cold_start(S, start):
+    """Dynamic graph cuts: starting each cut from the previous frame's n-link flows
+    must give exactly the cold-start result (mask, cut value, and so prior)."""
+    frames = np.stack([f for f, _ in synth.clip_vga_frames(start + 10)])[start:]
+    warm = S.Segmenter(480, 640, seg_params(S, O.CONFIG_VGA))
+    cold = S.Segmenter(480, 640, seg_params(S, O.CONFIG_VGA, warm_start=0))
+    assert warm.params.warm_start == 1
+    for t in range(len(frames)):
+        ow = warm.push_frame(dev(frames[t]))
+        oc = cold.push_frame(dev(frames[t]))
+        assert warm.sync()[0] == 0 and cold.sync()[0] == 0
+        for a, b in zip(ow, oc):
+            assert torch.equal(a, b), t
+    warm.close()
+    cold.close()
