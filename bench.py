@@ -251,6 +251,38 @@ def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
     return out
 
 
+def serving_suite(seg, torch, horizon_s=1.0, budget_gb=32.0):
+    """The serving workload: Poisson arrivals (20 streams/s) of streams lasting
+    60-600 frames at 640x480, 1280x720 or 1920x1080, served by the
+    continuous-batching server with admission by HBM footprint."""
+    from paper_1008_0502_b300 import serve, synth
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 5))
+    sizes = [(480, 640), (720, 1280), (1080, 1920)]
+    pools = {}
+    for k, (h, w) in enumerate(sizes):
+        pools[(h, w)] = torch.from_numpy(
+            np.stack([f for f, _ in synth.clip_vga_frames(8, h, w, seed=synth.SEED_BASE + 6 + k)])).cuda()
+    reqs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / 20.0)
+        if t >= horizon_s:
+            break
+        h, w = sizes[int(rng.integers(0, 3))]
+        n = int(rng.integers(60, 601))
+        off = int(rng.integers(0, 8))
+        pool = pools[(h, w)]
+        reqs.append(serve.Request(len(reqs), (lambda tt, pool=pool, off=off: pool[(off + tt) % 8]), n, t))
+    srv = serve.Server(seg.params_from(VGA), int(budget_gb * 2**30), slots=8)
+    stats = srv.run(reqs, clock="wall")
+    waits = [r.admitted - r.arrival for r in srv.results.values()]
+    srv.close()
+    stats.update({"arrivals_per_s": 20, "horizon_s": horizon_s, "hbm_budget_gb": budget_gb,
+                  "admission_wait_ms": {"p50": float(np.percentile(waits, 50)) * 1e3,
+                                        "max": float(np.max(waits)) * 1e3},
+                  "mix": "Poisson arrivals, 60-600 frames, 640x480 / 1280x720 / 1920x1080, 8 slots per group"})
+    return stats
+
+
 def dist_setup(backend):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -397,6 +429,7 @@ def run_b300(a):
             "algorithmic_bytes": f"{BYTES_MINCUT_SWEEP_PX} B/px/sweep x {H * W} px x {cycles:.2f} sweeps",
             "peak_kind": pk_kind}
     batched = batched_suite(seg, torch, clip_dev, value / ws, hbm) if a.batched else None
+    serving = serving_suite(seg, torch) if a.batched else None
     n_cpu, dt_cpu = cpu_baseline(clip, a.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": a.steps,
@@ -413,6 +446,7 @@ def run_b300(a):
         "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": H * W + 8},
         "batched": batched,
+        "serving": serving,
         "gpu_launches": a.steps * kernels_per_frame(VGA),
         "clocks": clocks,
     }

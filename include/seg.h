@@ -103,6 +103,10 @@ int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out);
  * Errors as seg_create, plus SEG_EINVAL for B < 1 or B*H*W > 2^26. */
 int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg_ctx** out);
 
+/* Device bytes seg_create_batch(B, H, W, p) would allocate for its workspace
+ * (for admission control by HBM footprint).  Errors as seg_create_batch. */
+int seg_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes);
+
 /* Frees the context and its workspace (synchronises its stream first). */
 int seg_destroy(seg_ctx* ctx);
 

@@ -87,6 +87,60 @@ static int check_params(const seg_params* p, int H, int W) {
   return SEG_OK;
 }
 
+// Byte offsets of every buffer in a context's single device arena.
+struct ArenaLayout {
+  size_t kal, gauss, mom, lut, cnt, prev, cs, ct, ncap, sal, prior, mask, cut, rgb, status, io, flow, warm, mf;
+  size_t total;
+};
+
+static int arena_layout(SalWS& sal, int B, int H, int W, const seg_params& p, ArenaLayout& L) {
+  size_t sal_bytes = 0;
+  int rc = sal_layout(sal, B, H, W, p, &sal_bytes);
+  if (rc) return rc;
+  const size_t BN = (size_t)H * W * B;
+  const int nk = p.neighbourhood / 2;
+  size_t off = seg_align(sal_bytes);
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += seg_align(b);
+    return o;
+  };
+  L.kal = take(B * sizeof(KalmanDev));
+  L.gauss = take(B * sizeof(GaussDev));
+  L.mom = take((size_t)B * sizeof(double) * pt_part_doubles(H, W));
+  L.lut = take(sizeof(int) * 766 * 2);
+  L.cnt = take(B * sizeof(unsigned));
+  L.prev = take(BN);
+  L.cs = take(4 * BN);
+  L.ct = take(4 * BN);
+  L.ncap = take(4 * BN * nk);
+  L.sal = take(4 * BN);
+  L.prior = take(4 * BN);
+  L.mask = take(BN);
+  L.cut = take(8 * B);
+  L.rgb = take(3 * BN);
+  L.status = take(32);
+  L.io = take(sizeof(SegIO));
+  L.flow = take(4 * BN * nk);
+  L.warm = take(B);
+  L.mf = take(mf_bytes(B * H, W, p.neighbourhood, B));
+  L.total = off;
+  return SEG_OK;
+}
+
+extern "C" int seg_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes) {
+  if (!bytes) return SEG_EINVAL;
+  int rc = check_params(p, H, W);
+  if (rc) return rc;
+  if (B < 1 || (long long)B * H * W > (1LL << 26)) return SEG_EINVAL;
+  SalWS sal;
+  ArenaLayout L;
+  rc = arena_layout(sal, B, H, W, *p, L);
+  if (rc) return rc;
+  *bytes = L.total;
+  return SEG_OK;
+}
+
 extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out) {
   return seg_create_batch(stream, 1, H, W, p, out);
 }
@@ -109,29 +163,19 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
     free(c);
     return SEG_ECUDA;
   }
-  size_t sal_bytes = 0;
-  rc = sal_layout(c->sal, B, H, W, *p, &sal_bytes);
+  ArenaLayout L;
+  rc = arena_layout(c->sal, B, H, W, *p, L);
   if (rc) {
     free(c);
     return rc;
   }
   const size_t N = (size_t)c->N, BN = N * B;
-  const int nk = p->neighbourhood / 2;
   c->mom_blocks = pt_mom_blocks(H, W);
-  size_t off = seg_align(sal_bytes);
-  auto take = [&](size_t b) {
-    size_t o = off;
-    off += seg_align(b);
-    return o;
-  };
-  size_t o_kal = take(B * sizeof(KalmanDev)), o_gauss = take(B * sizeof(GaussDev));
-  size_t o_mom = take((size_t)B * sizeof(double) * pt_part_doubles(H, W)), o_lut = take(sizeof(int) * 766 * 2);
-  size_t o_cnt = take(B * sizeof(unsigned));
-  size_t o_prev = take(BN), o_cs = take(4 * BN), o_ct = take(4 * BN), o_ncap = take(4 * BN * nk);
-  size_t o_sal = take(4 * BN), o_prior = take(4 * BN), o_mask = take(BN), o_cut = take(8 * B);
-  size_t o_rgb = take(3 * BN), o_status = take(32), o_io = take(sizeof(SegIO));
-  size_t o_flow = take(4 * BN * nk), o_warm = take(B);
-  size_t o_mf = take(mf_bytes(B * H, W, p->neighbourhood, B));
+  const size_t off = L.total;
+  size_t o_kal = L.kal, o_gauss = L.gauss, o_mom = L.mom, o_lut = L.lut, o_cnt = L.cnt, o_prev = L.prev;
+  size_t o_cs = L.cs, o_ct = L.ct, o_ncap = L.ncap, o_sal = L.sal, o_prior = L.prior, o_mask = L.mask;
+  size_t o_cut = L.cut, o_rgb = L.rgb, o_status = L.status, o_io = L.io, o_flow = L.flow, o_warm = L.warm;
+  size_t o_mf = L.mf;
   char* base = nullptr;
   if (cudaMalloc((void**)&base, off) != cudaSuccess) {
     free(c);

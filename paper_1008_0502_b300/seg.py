@@ -57,6 +57,7 @@ def _load():
         "seg_create": ([vp, i32, i32, P(seg_params), P(vp)], i32),
         "seg_create_batch": ([vp, i32, i32, i32, P(seg_params), P(vp)], i32),
         "seg_reset_stream": ([vp, i32], i32),
+        "seg_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
         "seg_destroy": ([vp], i32),
         "seg_reset": ([vp], i32),
         "seg_push_frame": ([vp, vp, vp, vp, vp, vp], i32),
@@ -129,6 +130,12 @@ def params_from(cfg: dict, **over) -> seg_params:
     d = dict(cfg)
     d.update(over)
     return default_params(**d)
+
+
+def workspace_bytes(B: int, H: int, W: int, params: seg_params) -> int:
+    n = C.c_size_t(0)
+    _check(lib.seg_workspace_bytes(B, H, W, C.byref(params), C.byref(n)), "seg_workspace_bytes")
+    return n.value
 
 
 def level_dim(n: int, level: int) -> int:
