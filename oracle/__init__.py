@@ -29,7 +29,13 @@ class OrcParams(C.Structure):
         ("f_sigma", C.c_double), ("f_radius", C.c_int), ("eps", C.c_double),
         ("lambda_u", C.c_double), ("lambda_p", C.c_double), ("lambda_s", C.c_double),
         ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int),
+        ("gmm_components", C.c_int), ("em_iters", C.c_int),
     ]
+
+
+class OrcGmm(C.Structure):
+    _fields_ = [("M", C.c_int), ("pi", C.c_double * 3), ("mu", (C.c_double * 3) * 3),
+                ("cov", ((C.c_double * 3) * 3) * 3)]
 
 
 class OrcDebug(C.Structure):
@@ -47,7 +53,8 @@ CONFIG_VGA = dict(levels=9, c_min=2, c_max=4, d_min=3, d_max=4, n_orient=4, gabo
                   gabor_sigma=2.0, gabor_radius=6, norm_tile=8, norm_flat=1e-5,
                   w=(1 / 3, 1 / 6, 1 / 6, 1 / 3), cs_opponent_sum=1, border_px=1, sigma1=0.03,
                   sigma2=0.035, f_sigma=2.0, f_radius=6, eps=1e-4, lambda_u=1.0, lambda_p=0.0,
-                  lambda_s=1.5, sigma_I=0.05, cap_scale=1000.0, neighbourhood=8)
+                  lambda_s=1.5, sigma_I=0.05, cap_scale=1000.0, neighbourhood=8, gmm_components=1,
+                  em_iters=5)
 CONFIG_SMALL = dict(CONFIG_VGA, levels=6, c_min=1, c_max=2, d_min=2, d_max=3, neighbourhood=4)
 
 
@@ -85,6 +92,16 @@ def lib():
             getattr(L, name).restype = C.c_int64
         L.orc_bruteforce.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, P(C.c_int32)]
         L.orc_bruteforce.restype = C.c_int64
+        for name in ("orc_gmm_init", "orc_gmm_fit"):
+            getattr(L, name).restype = None
+        L.orc_gmm_init.argtypes = [vp, vp, C.c_int, C.c_int, P(OrcGmm)]
+        L.orc_gmm_fit.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, P(OrcGmm)]
+        L.orc_gmm_em_step.argtypes = [vp, vp, C.c_int, P(OrcGmm)]
+        L.orc_gmm_em_step.restype = None
+        L.orc_gmm_loglik.argtypes = [vp, vp, C.c_int, P(OrcGmm)]
+        L.orc_gmm_loglik.restype = C.c_double
+        L.orc_gmm_logpdf.argtypes = [P(OrcGmm), vp]
+        L.orc_gmm_logpdf.restype = C.c_double
         L.orc_push_frame.argtypes = [P(OrcParams), C.c_int, C.c_int, P(OrcState), vp, vp, vp, vp]
         L.orc_push_frame.restype = C.c_int64
         _lib = L
@@ -243,6 +260,47 @@ def terms(rgb, prior_map, cfg=None, **over):
     D0, D1 = np.empty((H, W)), np.empty((H, W))
     lib().orc_terms(C.byref(P), H, W, _p(rgb), _p(prior_map), _p(cs), _p(ct), _p(nc), _p(D0), _p(D1))
     return cs, ct, nc, D0, D1
+
+
+def _gmm_out(g):
+    M = g.M
+    return (np.array(g.pi[:M]), np.array([[g.mu[m][k] for k in range(3)] for m in range(M)]),
+            np.array([[[g.cov[m][k][j] for j in range(3)] for k in range(3)] for m in range(M)]))
+
+
+def gmm_fit(rgb, w, M=3, iters=5):
+    """Prior-weighted GMM over C = RGB/255: returns (pi, mu, cov)."""
+    rgb = _c(rgb, np.uint8).reshape(-1, 3)
+    w = _c(w, np.float64).ravel()
+    g = OrcGmm()
+    lib().orc_gmm_fit(_p(rgb), _p(w), w.size, M, iters, C.byref(g))
+    return _gmm_out(g)
+
+
+def gmm_em_trace(rgb, w, M=3, iters=5):
+    """Weighted log-likelihood after init and after each EM step."""
+    rgb = _c(rgb, np.uint8).reshape(-1, 3)
+    w = _c(w, np.float64).ravel()
+    g = OrcGmm()
+    lib().orc_gmm_init(_p(rgb), _p(w), w.size, M, C.byref(g))
+    out = [lib().orc_gmm_loglik(_p(rgb), _p(w), w.size, C.byref(g))]
+    for _ in range(iters):
+        lib().orc_gmm_em_step(_p(rgb), _p(w), w.size, C.byref(g))
+        out.append(lib().orc_gmm_loglik(_p(rgb), _p(w), w.size, C.byref(g)))
+    return out
+
+
+def gmm_logpdf(pi, mu, cov, c):
+    g = OrcGmm()
+    g.M = len(pi)
+    for m in range(g.M):
+        g.pi[m] = pi[m]
+        for k in range(3):
+            g.mu[m][k] = mu[m][k]
+            for j in range(3):
+                g.cov[m][k][j] = cov[m][k][j]
+    c = _c(c, np.float64)
+    return lib().orc_gmm_logpdf(C.byref(g), _p(c))
 
 
 def ncap_value(dsum, diagonal, cfg=None, **over):

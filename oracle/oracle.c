@@ -434,6 +434,130 @@ static void inv3(double m[3][3], double out[3][3]) {
   out[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) / d;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sec. 4 + Sec. 7.3: the colour likelihood p(C|A) as a Gaussian mixture of M
+ * components per label, fitted by EM to all pixels weighted by the prior
+ * (Sec. 5).  M = 3 in the paper's experiments (Sec. 8.1).
+ * Reading (the paper initialises EM by k-means on the CPU, unspecified): a
+ * deterministic initialisation without any argmax -- the means start on the
+ * grey axis g = (1,1,1)/sqrt3 through the weighted mean, at (m - (M-1)/2) * 1.5
+ * sigma_g with sigma_g^2 = g^T Sigma g; every covariance starts at the weighted
+ * global covariance (+ 1e-4 I), every weight at 1/M.  Then a fixed number of
+ * EM iterations: E-step responsibilities r_m = pi_m N_m / sum_k pi_k N_k;
+ * M-step with the pixel weights w: N_m = sum w r_m, pi_m = N_m / sum_k N_k,
+ * mu_m = sum w r_m C / N_m, Sigma_m = sum w r_m (C - mu_m)(C - mu_m)^T / N_m
+ * + 1e-4 I.  A component with N_m < 1e-6 sum(w) keeps its parameters. */
+static void gmm_pdf_terms(const orc_gmm* g, const double c[3], double* logp) {
+  for (int m = 0; m < g->M; ++m) {
+    double A[3][3], Ai[3][3];
+    memcpy(A, g->cov[m], sizeof(A));
+    double d = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+               A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    Ai[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / d;
+    Ai[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / d;
+    Ai[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / d;
+    Ai[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / d;
+    Ai[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / d;
+    Ai[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / d;
+    Ai[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / d;
+    Ai[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / d;
+    Ai[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / d;
+    double q = 0, dv[3];
+    for (int k = 0; k < 3; ++k) dv[k] = c[k] - g->mu[m][k];
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j) q += dv[k] * Ai[k][j] * dv[j];
+    logp[m] = log(g->pi[m]) - 0.5 * q - 0.5 * log(d) - 1.5 * log(2.0 * M_PI);
+  }
+}
+
+/* log sum_m pi_m N(c; mu_m, Sigma_m) */
+double orc_gmm_logpdf(const orc_gmm* g, const double c[3]) {
+  double lp[3], mx = -DBL_MAX, s = 0;
+  gmm_pdf_terms(g, c, lp);
+  for (int m = 0; m < g->M; ++m) mx = maxd(mx, lp[m]);
+  for (int m = 0; m < g->M; ++m) s += exp(lp[m] - mx);
+  return mx + log(s);
+}
+
+void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, orc_gmm* g) {
+  double sw = 0, mu[3] = {0, 0, 0}, cv[3][3] = {{0}};
+  for (int i = 0; i < n; ++i) {
+    sw += w[i];
+    for (int k = 0; k < 3; ++k) mu[k] += w[i] * (rgb[3 * i + k] / 255.0);
+  }
+  for (int k = 0; k < 3; ++k) mu[k] /= sw;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j)
+        cv[k][j] += w[i] * (rgb[3 * i + k] / 255.0 - mu[k]) * (rgb[3 * i + j] / 255.0 - mu[j]);
+  double sg2 = 0;
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) {
+      cv[k][j] = cv[k][j] / sw + (k == j ? 1e-4 : 0.0);
+      sg2 += cv[k][j] / 3.0;  /* g^T Sigma g with g = (1,1,1)/sqrt3 */
+    }
+  g->M = M;
+  for (int m = 0; m < M; ++m) {
+    double off = (m - (M - 1) / 2.0) * 1.5 * sqrt(sg2) / sqrt(3.0);
+    g->pi[m] = 1.0 / M;
+    for (int k = 0; k < 3; ++k) g->mu[m][k] = mu[k] + off;
+    memcpy(g->cov[m], cv, sizeof(cv));
+  }
+}
+
+double orc_gmm_loglik(const uint8_t* rgb, const double* w, int n, const orc_gmm* g) {
+  double L = 0;
+  for (int i = 0; i < n; ++i) {
+    double c[3] = {rgb[3 * i] / 255.0, rgb[3 * i + 1] / 255.0, rgb[3 * i + 2] / 255.0};
+    L += w[i] * orc_gmm_logpdf(g, c);
+  }
+  return L;
+}
+
+void orc_gmm_em_step(const uint8_t* rgb, const double* w, int n, orc_gmm* g) {
+  int M = g->M;
+  double* r = (double*)malloc(sizeof(double) * (size_t)n * M);
+  double Nm[3] = {0, 0, 0}, sw = 0;
+  for (int i = 0; i < n; ++i) {  /* E-step */
+    double c[3] = {rgb[3 * i] / 255.0, rgb[3 * i + 1] / 255.0, rgb[3 * i + 2] / 255.0};
+    double lp[3], mx = -DBL_MAX, s = 0;
+    gmm_pdf_terms(g, c, lp);
+    for (int m = 0; m < M; ++m) mx = maxd(mx, lp[m]);
+    for (int m = 0; m < M; ++m) s += exp(lp[m] - mx);
+    for (int m = 0; m < M; ++m) {
+      r[(size_t)i * M + m] = exp(lp[m] - mx) / s;
+      Nm[m] += w[i] * r[(size_t)i * M + m];
+    }
+    sw += w[i];
+  }
+  double Ntot = 0;
+  for (int m = 0; m < M; ++m) Ntot += Nm[m];
+  for (int m = 0; m < M; ++m) {  /* M-step, two passes per component */
+    g->pi[m] = Nm[m] / Ntot;
+    if (!(Nm[m] >= 1e-6 * sw)) continue;
+    double mu[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < 3; ++k) mu[k] += w[i] * r[(size_t)i * M + m] * (rgb[3 * i + k] / 255.0);
+    for (int k = 0; k < 3; ++k) mu[k] /= Nm[m];
+    double cv[3][3] = {{0}};
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j)
+          cv[k][j] += w[i] * r[(size_t)i * M + m] * (rgb[3 * i + k] / 255.0 - mu[k]) * (rgb[3 * i + j] / 255.0 - mu[j]);
+    for (int k = 0; k < 3; ++k) {
+      g->mu[m][k] = mu[k];
+      for (int j = 0; j < 3; ++j) g->cov[m][k][j] = cv[k][j] / Nm[m] + (k == j ? 1e-4 : 0.0);
+    }
+  }
+  free(r);
+}
+
+void orc_gmm_fit(const uint8_t* rgb, const double* w, int n, int M, int iters, orc_gmm* g) {
+  orc_gmm_init(rgb, w, n, M, g);
+  for (int it = 0; it < iters; ++it) orc_gmm_em_step(rgb, w, n, g);
+}
+
 static int32_t quantize(double K, double x) {
   /* Reading: integer capacity = min(2^24, floor(K x + 1/2)). */
   double v = floor(K * x + 0.5);
@@ -470,6 +594,16 @@ void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const doub
   int n = H * W;
   double mu[2][3], cov[2][3][3], icov[2][3][3], lconst[2];
   int degenerate = orc_colour_models(prior, rgb, n, mu, cov);
+  orc_gmm gm[2];
+  if (P->gmm_components > 1) {  /* Sec. 4 / Sec. 7.3: M-component EM per label */
+    double* w = (double*)malloc(sizeof(double) * n);
+    for (int a = 0; a < 2; ++a) {
+      if (degenerate & (1 << a)) continue;
+      for (int i = 0; i < n; ++i) w[i] = a ? prior[i] : 1.0 - prior[i];
+      orc_gmm_fit(rgb, w, n, P->gmm_components, P->em_iters, &gm[a]);
+    }
+    free(w);
+  }
   for (int a = 0; a < 2; ++a) {
     inv3(cov[a], icov[a]);
     lconst[a] = 0.5 * log(det3(cov[a])) + 1.5 * log(2.0 * M_PI);
@@ -481,7 +615,10 @@ void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const doub
       double p = a ? prior[i] : 1.0 - prior[i];
       double xi = -log(mind(maxd(p, eps), 1.0 - eps));
       double psi = 0.0;
-      if (!(degenerate & (1 << a))) {
+      if (!(degenerate & (1 << a)) && P->gmm_components > 1) {
+        double c[3] = {rgb[3 * i] / 255.0, rgb[3 * i + 1] / 255.0, rgb[3 * i + 2] / 255.0};
+        psi = -orc_gmm_logpdf(&gm[a], c);
+      } else if (!(degenerate & (1 << a))) {
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = rgb[3 * i + k] / 255.0 - mu[a][k];
         double q = 0;

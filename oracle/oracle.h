@@ -43,7 +43,17 @@ typedef struct orc_params {
   double sigma_I;      /* contrast term intensity scale */
   double cap_scale;    /* K: integer capacity = round(K * cost) */
   int neighbourhood;   /* 4 or 8 */
+  int gmm_components;  /* Gaussians per label in the colour likelihood: 1 or 3 */
+  int em_iters;        /* EM iterations when gmm_components > 1 */
 } orc_params;
+
+/* A prior-weighted Gaussian mixture over C = RGB/255 (one label). */
+typedef struct orc_gmm {
+  int M;
+  double pi[3];
+  double mu[3][3];
+  double cov[3][3][3];
+} orc_gmm;
 
 /* Debug outputs of orc_saliency_ex (any pointer may be NULL). */
 typedef struct orc_saliency_debug {
@@ -78,6 +88,11 @@ int orc_colour_models(const double* prior, const uint8_t* rgb, int n, double mu[
                       double cov[2][3][3]);
 void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const double* prior,
                int32_t* cs, int32_t* ct, int32_t* ncap, double* D0, double* D1);
+void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, orc_gmm* g);
+double orc_gmm_loglik(const uint8_t* rgb, const double* w, int n, const orc_gmm* g);
+void orc_gmm_em_step(const uint8_t* rgb, const double* w, int n, orc_gmm* g);
+void orc_gmm_fit(const uint8_t* rgb, const double* w, int n, int M, int iters, orc_gmm* g);
+double orc_gmm_logpdf(const orc_gmm* g, const double c[3]);
 int32_t orc_ncap_value(const orc_params* P, int dsum, int diagonal);
 
 /* --- Sec. 4: exact s-t min cut on the grid graph --- */

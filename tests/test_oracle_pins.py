@@ -447,3 +447,60 @@ def test_small_clip_regression_golden():
         assert cut == row["cut"] and int(mask.sum()) == row["mask_area"]
         assert float(sal.sum()) == pytest.approx(row["saliency_sum"], rel=1e-12)
         assert float(pr.sum()) == pytest.approx(row["prior_sum"], rel=1e-12)
+
+
+# ---------------------------------------------------------------- M-component colour model (EM)
+def _clustered_rgb(seed, n=3000):
+    rng = np.random.default_rng(seed)
+    centers = np.array([[50, 50, 50], [128, 128, 128], [210, 190, 170]], float)
+    lab = rng.integers(0, 3, n)
+    x = centers[lab] + rng.normal(0, 6, (n, 3))
+    return np.clip(np.rint(x), 0, 255).astype(np.uint8), lab, centers
+
+
+def test_em_single_component_is_the_weighted_gaussian():
+    rng = np.random.default_rng(31)
+    rgb = rng.integers(0, 256, (40, 50, 3)).astype(np.uint8)
+    w = rng.random((40, 50))
+    pi, mu, cov = O.gmm_fit(rgb, w, M=1, iters=4)
+    mu1, cov1, _ = O.colour_models(w, rgb)
+    np.testing.assert_allclose(pi, [1.0])
+    np.testing.assert_allclose(mu[0], mu1[1], atol=1e-13)
+    np.testing.assert_allclose(cov[0], cov1[1], atol=1e-13)
+
+
+def test_em_loglik_never_decreases_and_weight_scale_invariant():
+    rgb, _, _ = _clustered_rgb(32)
+    w = np.random.default_rng(33).random(rgb.shape[0])
+    trace = O.gmm_em_trace(rgb, w, M=3, iters=8)
+    assert all(b >= a - 1e-9 * abs(a) for a, b in zip(trace, trace[1:]))
+    a = O.gmm_fit(rgb, w, 3, 5)
+    b = O.gmm_fit(rgb, 3.7 * w, 3, 5)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, rtol=1e-10, atol=1e-13)
+
+
+def test_em_recovers_separated_clusters():
+    rgb, lab, centers = _clustered_rgb(34)
+    pi, mu, cov = O.gmm_fit(rgb, np.ones(rgb.shape[0]), M=3, iters=30)
+    order = np.argsort(mu[:, 0])
+    np.testing.assert_allclose(mu[order] * 255, centers, atol=1.0)
+    np.testing.assert_allclose(pi[order], np.bincount(lab) / lab.size, atol=0.01)
+
+
+def test_gmm_logpdf_and_terms_match_scipy():
+    from scipy.special import logsumexp
+    rgb, _, _ = _clustered_rgb(35, n=1200)
+    img = rgb.reshape(30, 40, 3)
+    pr = np.random.default_rng(36).random((30, 40))
+    cfg = dict(O.CONFIG_SMALL, gmm_components=3, em_iters=5)
+    cs, ct, nc, D0, D1 = O.terms(img, pr, cfg)
+    C = img.reshape(-1, 3) / 255.0
+    for a, D in [(0, D0), (1, D1)]:
+        w = pr.ravel() if a else 1 - pr.ravel()
+        pi, mu, cov = O.gmm_fit(img, w.reshape(30, 40), 3, 5)
+        lp = logsumexp([np.log(pi[m]) + stats.multivariate_normal(mu[m], cov[m]).logpdf(C) for m in range(3)],
+                       axis=0)
+        assert O.gmm_logpdf(pi, mu, cov, C[7]) == pytest.approx(lp[7], rel=1e-12)
+        ref = -lp - np.log(np.clip(w, 1e-4, 1 - 1e-4))
+        np.testing.assert_allclose(D.ravel(), ref, rtol=1e-11, atol=1e-11)
