@@ -205,6 +205,20 @@ def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
                            "achieved_GBps": ach, "frac_of_hbm": ach / hbm}
     sgs.close()
 
+    # the paper's M = 3 EM colour mixtures (Sec. 4 / Sec. 7.3), single 640x480 stream
+    sg3 = seg.Segmenter(H, W, seg.params_from(VGA, gmm_components=3, em_iters=5))
+    o3 = sg3.empty_outputs()
+    pos = [0]
+
+    def step3():
+        sg3.push_frame(clip_dev[pos[0] % clip_dev.shape[0]], *o3)
+        pos[0] += 1
+
+    t = timed(step3, 100)
+    out["gmm3"] = {"streams": "1 x 640x480, M = 3 EM (5 iterations)", "frames_per_s": 100 / t,
+                   "status": sg3.sync()[0]}
+    sg3.close()
+
     # the mixed 64-stream workload: one batch context per resolution, each on its own CUDA stream
     groups = [(24, 240, 320), (24, 480, 640), (16, 720, 1280)]
     nfr = 4

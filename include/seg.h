@@ -79,6 +79,9 @@ typedef struct seg_params {
   int32_t local_iters;     /* push/relabel iterations per tile visit (16) */
   int32_t use_graph;       /* 1: seg_push_frame replays one captured CUDA graph per frame (when the
                               context's stream is not the legacy default stream); 0: eager launches */
+  int32_t gmm_components;  /* Gaussians per label in the colour likelihood psi_1: 1 (closed form) or 3
+                              (EM, Sec. 4 / Sec. 7.3; M = 3 in Sec. 8.1) */
+  int32_t em_iters;        /* EM iterations when gmm_components > 1 (5) */
   int32_t warm_start;      /* 1: each stream's min cut starts from its previous frame's n-link flows
                               (dynamic graph cuts, Sec. 1 / Sec. 8.2 prior art); results are identical
                               to a cold start; 0: cold start every frame */

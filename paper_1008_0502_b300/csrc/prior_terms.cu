@@ -60,6 +60,8 @@ struct MomFinArgs {
   KalmanDev* kal;  // nullable: advance the variance recursion
   double a, b;
   const SegIO* io;  // rgb / prior == nullptr: take them from here
+  GmmDev* gmm;      // nullable: initialise the M-component mixtures from the M = 1 fit
+  int M;
 };
 
 __device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
@@ -240,8 +242,32 @@ __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, d
   }
 }
 
+// Cholesky factor of a 3x3 covariance, the inverse factor (6 floats) and log det.
+__device__ double chol_inv(double c00, double c10, double c11, double c20, double c21, double c22, float* li) {
+  double l00 = sqrt(c00);
+  double l10 = c10 / l00, l20 = c20 / l00;
+  double l11 = sqrt(c11 - l10 * l10);
+  double l21 = (c21 - l20 * l10) / l11;
+  double l22 = sqrt(c22 - l20 * l20 - l21 * l21);
+  double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
+  double i10 = -l10 * i00 / l11;
+  double i21 = -l21 * i11 / l22;
+  double i20 = -(l20 * i00 + l21 * i10) / l22;
+  li[0] = (float)i00;
+  li[1] = (float)i10;
+  li[2] = (float)i11;
+  li[3] = (float)i20;
+  li[4] = (float)i21;
+  li[5] = (float)i22;
+  return 2.0 * log(l00 * l11 * l22);
+}
+
 // Covariance + 1e-4 I, Cholesky factor L, L^-1 and 1/2 log det + 3/2 log 2 pi.
-__device__ void finalize_cov(const double* tot, GaussDev* g) {
+// With gmm: also the EM initialisation of the M-component mixtures (reading of
+// the paper's k-means start): means on the grey axis through the weighted mean
+// at (m - (M-1)/2) * 1.5 sigma_g, sigma_g^2 = g^T Sigma g, g = (1,1,1)/sqrt3;
+// every covariance = Sigma; every weight = 1/M.
+__device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M) {
   for (int lab = 0; lab < 2; ++lab) {
     double sw = g->sw[lab];
     if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
@@ -252,6 +278,19 @@ __device__ void finalize_cov(const double* tot, GaussDev* g) {
     const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
     double c00 = m[0] / sw + 1e-4, c10 = m[1] / sw, c11 = m[2] / sw + 1e-4;
     double c20 = m[3] / sw, c21 = m[4] / sw, c22 = m[5] / sw + 1e-4;
+    if (gmm) {
+      GmmDev& q = gmm[lab];
+      double sg2 = (c00 + c11 + c22 + 2.0 * (c10 + c20 + c21)) / 3.0;
+      float li[6];
+      double ld = chol_inv(c00, c10, c11, c20, c21, c22, li);
+      for (int k = 0; k < M; ++k) {
+        double off = (k - (M - 1) / 2.0) * 1.5 * sqrt(sg2) / sqrt(3.0);
+        for (int j = 0; j < 3; ++j) q.mu[k][j] = (float)(g->mu[lab][j] + off);
+        for (int j = 0; j < 6; ++j) q.linv[k][j] = li[j];
+        q.logdet[k] = ld;
+        q.lc[k] = (float)(log(1.0 / M) - 0.5 * ld - 1.5 * log(2.0 * M_PI));
+      }
+    }
     double l00 = sqrt(c00);
     double l10 = c10 / l00, l20 = c20 / l00;
     double l11 = sqrt(c11 - l10 * l10);
@@ -330,7 +369,116 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
   if (block_partial_last<12>(s, f.part, f.counter, blockIdx.x, gridDim.x)) {
     __shared__ double tot[12];
     reduce_parts<12>(f.part, gridDim.x, tot);
-    if (threadIdx.x == 0) finalize_cov(tot, f.gauss);
+    if (threadIdx.x == 0) finalize_cov(tot, f.gauss, f.gmm ? f.gmm + 2 * fb : nullptr, f.M);
+  }
+}
+
+// ------------------------------------------------------------------ EM (M components)
+#define EM_NV 30  // per component: weight, 3 shifted first moments, 6 shifted second moments
+
+struct EMArgs {
+  const uint8_t* rgb;
+  const float* prior;
+  int N, M;
+  GmmDev* gmm;        // [frame][label]
+  const GaussDev* gauss;
+  double* part;       // [frame][label][blocks * EM_NV]
+  int part_stride;
+  unsigned* counter;  // [frame][label]
+  const SegIO* io;
+};
+
+// Fixed-order sum of NV partials over the CTAs, one thread per value.
+template <int NV>
+__device__ void reduce_parts_serial(const double* part, int nblocks, double* out) {
+  if ((int)threadIdx.x < NV) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += ((volatile double*)part)[b * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// One EM iteration for label a of frame fb (blockIdx.y = 2 fb + a): E-step
+// responsibilities from the current mixture, moments of every component about
+// its current mean (so the update has no large cancellation); the last CTA
+// forms pi, mu, Sigma (+ 1e-4 I) per component.  Components whose weight is
+// below 1e-6 of the label's total keep their mean and covariance.
+template <int M>
+__global__ void __launch_bounds__(256) k_em_step(EMArgs a) {
+  const int lab = blockIdx.y & 1, fb = blockIdx.y >> 1;
+  const GaussDev* gd = a.gauss + fb;
+  if (gd->degenerate & (1 << lab)) return;  // uniform over the grid: no partials, no finalise
+  const uint8_t* rgb = (a.rgb ? a.rgb : a.io->rgb) + (size_t)fb * 3 * a.N;
+  const float* prior = (a.prior ? a.prior : a.io->prior) + (size_t)fb * a.N;
+  GmmDev* g = a.gmm + 2 * fb + lab;
+  float mu[M][3], li[M][6], lc[M];
+  for (int m = 0; m < M; ++m) {
+    for (int k = 0; k < 3; ++k) mu[m][k] = g->mu[m][k];
+    for (int k = 0; k < 6; ++k) li[m][k] = g->linv[m][k];
+    lc[m] = g->lc[m];
+  }
+  float s[EM_NV];
+#pragma unroll
+  for (int k = 0; k < EM_NV; ++k) s[k] = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+    float p = prior[i];
+    float w = lab ? p : 1.f - p;
+    float c[3] = {rgb[3 * (size_t)i] / 255.f, rgb[3 * (size_t)i + 1] / 255.f, rgb[3 * (size_t)i + 2] / 255.f};
+    float lp[M], d[M][3], mx = -3.0e38f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) d[m][k] = c[k] - mu[m][k];
+      float y0 = li[m][0] * d[m][0];
+      float y1 = li[m][1] * d[m][0] + li[m][2] * d[m][1];
+      float y2 = li[m][3] * d[m][0] + li[m][4] * d[m][1] + li[m][5] * d[m][2];
+      lp[m] = lc[m] - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2);
+      mx = fmaxf(mx, lp[m]);
+    }
+    float z = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      lp[m] = expf(lp[m] - mx);
+      z += lp[m];
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float wr = w * lp[m] / z;
+      float* t = s + 10 * m;
+      t[0] += wr;
+      t[1] += wr * d[m][0];
+      t[2] += wr * d[m][1];
+      t[3] += wr * d[m][2];
+      t[4] += wr * d[m][0] * d[m][0];
+      t[5] += wr * d[m][1] * d[m][0];
+      t[6] += wr * d[m][1] * d[m][1];
+      t[7] += wr * d[m][2] * d[m][0];
+      t[8] += wr * d[m][2] * d[m][1];
+      t[9] += wr * d[m][2] * d[m][2];
+    }
+  }
+  double* part = a.part + (size_t)(2 * fb + lab) * a.part_stride;
+  if (block_partial_last<EM_NV>(s, part, a.counter + 2 * fb + lab, blockIdx.x, gridDim.x)) {
+    __shared__ double tot[EM_NV];
+    reduce_parts_serial<EM_NV>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      double ntot = 0.0;
+      for (int m = 0; m < M; ++m) ntot += tot[10 * m];
+      for (int m = 0; m < M; ++m) {
+        const double* t = tot + 10 * m;
+        const double nm = t[0], pim = nm / ntot;
+        double ld = g->logdet[m];
+        if (nm >= 1e-6 * ntot) {
+          double dx = t[1] / nm, dy = t[2] / nm, dz = t[3] / nm;
+          for (int k = 0; k < 3; ++k) g->mu[m][k] = (float)((double)mu[m][k] + (k == 0 ? dx : k == 1 ? dy : dz));
+          ld = chol_inv(t[4] / nm - dx * dx + 1e-4, t[5] / nm - dy * dx, t[6] / nm - dy * dy + 1e-4,
+                        t[7] / nm - dz * dx, t[8] / nm - dz * dy, t[9] / nm - dz * dz + 1e-4, g->linv[m]);
+          g->logdet[m] = ld;
+        }
+        g->lc[m] = (float)(log(pim) - 0.5 * ld - 1.5 * log(2.0 * M_PI));
+      }
+    }
   }
 }
 
@@ -345,6 +493,8 @@ struct TermsArgs {
   int32_t* ct;
   int32_t* ncap;
   const SegIO* io;  // rgb / prior == nullptr: take them from here
+  const GmmDev* gmm;  // M > 1: [frame][label] colour mixtures
+  int M;
 };
 
 __device__ __forceinline__ int32_t quant_cap(float K, float x) {
@@ -379,13 +529,31 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   float pr = a.prior[g];
   float D[2];
   for (int lab = 0; lab < 2; ++lab) {
-    const float* li = a.gauss->linv[lab];
-    float d0 = C[0] - a.gauss->muf[lab][0], d1 = C[1] - a.gauss->muf[lab][1],
-          d2 = C[2] - a.gauss->muf[lab][2];
-    float y0 = li[0] * d0;
-    float y1 = li[1] * d0 + li[2] * d1;
-    float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
-    float psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + a.gauss->lconst[lab];
+    float psi;
+    if (a.M > 1 && !(a.gauss->degenerate & (1 << lab))) {  // -log sum_m pi_m N_m(C)
+      const GmmDev& q = a.gmm[2 * fb + lab];
+      float lp[SEG_MAX_GMM], mx = -3.0e38f;
+      for (int m = 0; m < a.M; ++m) {
+        const float* li = q.linv[m];
+        float d0 = C[0] - q.mu[m][0], d1 = C[1] - q.mu[m][1], d2 = C[2] - q.mu[m][2];
+        float y0 = li[0] * d0;
+        float y1 = li[1] * d0 + li[2] * d1;
+        float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
+        lp[m] = q.lc[m] - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2);
+        mx = fmaxf(mx, lp[m]);
+      }
+      float z = 0.f;
+      for (int m = 0; m < a.M; ++m) z += expf(lp[m] - mx);
+      psi = -(mx + logf(z));
+    } else {
+      const float* li = a.gauss->linv[lab];
+      float d0 = C[0] - a.gauss->muf[lab][0], d1 = C[1] - a.gauss->muf[lab][1],
+            d2 = C[2] - a.gauss->muf[lab][2];
+      float y0 = li[0] * d0;
+      float y1 = li[1] * d0 + li[2] * d1;
+      float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
+      psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + a.gauss->lconst[lab];
+    }
     float pl = lab ? pr : 1.f - pr;
     float xi = -logf(fminf(fmaxf(pl, a.eps), 1.f - a.eps));
     D[lab] = a.lambda_u * psi + xi;
@@ -506,8 +674,30 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   fa.a = p.sigma1 * p.sigma1;
   fa.b = p.sigma2 * p.sigma2;
   fa.io = c->io_mode ? c->io : nullptr;
+  const int M = p.gmm_components;
+  fa.gmm = M > 1 ? c->gmm : nullptr;
+  fa.M = M;
   if (first_pass) k_mom1<<<dim3(c->mom_blocks, c->B), 256, 0, st>>>(rgb, prior, N, fa);
   k_mom2<<<dim3(c->mom_blocks, c->B), 256, 0, st>>>(rgb, prior, N, fa);
+  if (M > 1) {  // Sec. 4 / Sec. 7.3: EM of the M-component colour mixtures
+    EMArgs ea;
+    ea.rgb = rgb;
+    ea.prior = prior;
+    ea.N = N;
+    ea.M = M;
+    ea.gmm = c->gmm;
+    ea.gauss = c->gauss;
+    ea.part = c->em_part;
+    ea.part_stride = pt_em_part_doubles(c->H, c->W);
+    ea.counter = c->em_counter;
+    ea.io = c->io_mode ? c->io : nullptr;
+    for (int it = 0; it < p.em_iters; ++it) {
+      if (M == 2)
+        k_em_step<2><<<dim3(c->mom_blocks, 2 * c->B), 256, 0, st>>>(ea);
+      else
+        k_em_step<3><<<dim3(c->mom_blocks, 2 * c->B), 256, 0, st>>>(ea);
+    }
+  }
   TermsArgs ta;
   ta.rgb = rgb;
   ta.prior = prior;
@@ -524,11 +714,15 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.ct = ct;
   ta.ncap = ncap;
   ta.io = c->io_mode ? c->io : nullptr;
+  ta.gmm = c->gmm;
+  ta.M = p.gmm_components;
   dim3 grid((c->W + 31) / 32, (c->H + 7) / 8, c->B);
   k_terms<<<grid, 256, 0, st>>>(ta);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }
+
+int pt_em_part_doubles(int H, int W) { return EM_NV * pt_mom_blocks(H, W); }
 
 int pt_part_doubles(int H, int W) {
   int prior_blocks = ((W + PR_TX - 1) / PR_TX) * ((H + PR_TY - 1) / PR_TY);

@@ -51,6 +51,8 @@ extern "C" int seg_default_params(seg_params* p) {
   p->global_relabel_every = 2;
   p->local_iters = 16;
   p->use_graph = 1;
+  p->gmm_components = 1;
+  p->em_iters = 5;
   p->warm_start = 1;
   return SEG_OK;
 }
@@ -84,12 +86,15 @@ static int check_params(const seg_params* p, int H, int W) {
   if (!(p->sigma1 >= 0) || !(p->sigma2 >= 0) || !(p->sigma_I > 0) || !(p->cap_scale > 0)) return SEG_EINVAL;
   if (!(p->eps > 0) || !(p->eps < 0.5f)) return SEG_EINVAL;
   if (p->max_cycles < 1 || p->global_relabel_every < 1 || p->local_iters < 1) return SEG_EINVAL;
+  if (p->gmm_components < 1 || p->gmm_components > SEG_MAX_GMM || p->em_iters < 0 || p->em_iters > 100)
+    return SEG_EINVAL;
   return SEG_OK;
 }
 
 // Byte offsets of every buffer in a context's single device arena.
 struct ArenaLayout {
   size_t kal, gauss, mom, lut, cnt, prev, cs, ct, ncap, sal, prior, mask, cut, rgb, status, io, flow, warm, mf;
+  size_t gmm, empart, emcnt;
   size_t total;
 };
 
@@ -124,6 +129,9 @@ static int arena_layout(SalWS& sal, int B, int H, int W, const seg_params& p, Ar
   L.flow = take(4 * BN * nk);
   L.warm = take(B);
   L.mf = take(mf_bytes(B * H, W, p.neighbourhood, B));
+  L.gmm = take((size_t)B * 2 * sizeof(GmmDev));
+  L.empart = take((size_t)B * 2 * sizeof(double) * pt_em_part_doubles(H, W));
+  L.emcnt = take((size_t)B * 2 * sizeof(unsigned));
   L.total = off;
   return SEG_OK;
 }
@@ -200,6 +208,9 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   c->status = (int*)(base + o_status);
   c->io = (SegIO*)(base + o_io);
   c->flow = (int*)(base + o_flow);
+  c->gmm = (GmmDev*)(base + L.gmm);
+  c->em_part = (double*)(base + L.empart);
+  c->em_counter = (unsigned*)(base + L.emcnt);
   c->warm = (unsigned char*)(base + o_warm);
   mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
@@ -212,6 +223,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   ok = ok && cudaMemset(c->status, 0, 32) == cudaSuccess;
   ok = ok && cudaMemset(c->mom_counter, 0, B * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMemset(c->warm, 0, B) == cudaSuccess;
+  ok = ok && cudaMemset(c->em_counter, 0, (size_t)B * 2 * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
   ok = ok && mf_grid_size(B * H, W, &c->mf_grid) == SEG_OK;
   if (!ok) {

@@ -194,6 +194,15 @@ struct GaussDev {
   int degenerate;    // bit a: label a has zero total weight
 };
 
+// M-component colour model of one label of one frame (Sec. 4 / Sec. 7.3 EM).
+#define SEG_MAX_GMM 3
+struct GmmDev {
+  float mu[SEG_MAX_GMM][3];
+  float linv[SEG_MAX_GMM][6];  // inverse Cholesky factor, l00 l10 l11 l20 l21 l22
+  float lc[SEG_MAX_GMM];       // log pi - 1/2 log det Sigma - 3/2 log 2 pi
+  double logdet[SEG_MAX_GMM];  // log det Sigma (reused by components that stop moving)
+};
+
 // ---------------------------------------------------------------- max-flow
 #define MF_TW 32
 #define MF_TH 16
@@ -262,6 +271,9 @@ struct seg_ctx {
   GaussDev* gauss;
   double* mom_part;
   unsigned* mom_counter;  // last-CTA counter of the moment passes (returns to 0)
+  GmmDev* gmm;            // [B][2] colour mixtures (gmm_components > 1)
+  double* em_part;        // [B][2][em partial doubles]
+  unsigned* em_counter;   // [B][2]
   int mom_blocks;
   int* lut;  // [766][2] n-link capacities by |delta(r+g+b)| and diagonal flag
   uint8_t* prev_mask;
@@ -306,6 +318,7 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
                             int32_t* cs, int32_t* ct, int32_t* ncap);
 int pt_part_doubles(int H, int W);
+int pt_em_part_doubles(int H, int W);
 void pt_fill_lut(const seg_params& p, int* lut_host);
 
 // H is the stacked height (nframes frames of H / nframes rows each)

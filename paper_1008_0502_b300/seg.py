@@ -43,7 +43,8 @@ class seg_params(C.Structure):
         ("lambda_u", C.c_double), ("lambda_p", C.c_double), ("lambda_s", C.c_double),
         ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int32),
         ("max_cycles", C.c_int32), ("global_relabel_every", C.c_int32), ("local_iters", C.c_int32),
-        ("use_graph", C.c_int32), ("warm_start", C.c_int32),
+        ("use_graph", C.c_int32), ("gmm_components", C.c_int32), ("em_iters", C.c_int32),
+        ("warm_start", C.c_int32),
     ]
 
 

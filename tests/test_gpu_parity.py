@@ -110,9 +110,10 @@ def test_prior_matches_oracle(S, w_f):
 
 
 # ---------------------------------------------------------------- terms
-@pytest.mark.parametrize("cfg_name", ["small", "vga"])
-def test_terms_match_oracle(S, cfg_name):
-    cfg = O.CONFIG_SMALL if cfg_name == "small" else O.CONFIG_VGA
+@pytest.mark.parametrize("cfg_name,M", [("small", 1), ("vga", 1), ("small", 3), ("vga", 3)])
+def test_terms_match_oracle(S, cfg_name, M):
+    """M = 3: the paper's EM colour mixtures (Sec. 4, Sec. 7.3), same tolerance."""
+    cfg = dict(O.CONFIG_SMALL if cfg_name == "small" else O.CONFIG_VGA, gmm_components=M, em_iters=5)
     frames, _ = synth.clip_small(2)
     rgb = frames[1]
     H, W = rgb.shape[:2]
@@ -228,6 +229,12 @@ def _run_clip(S, frames, cfg, check_every=1):
 def test_end_to_end_small_clip(S):
     frames, _ = synth.clip_small(10)
     agree = _run_clip(S, frames, O.CONFIG_SMALL)
+    assert min(agree) >= 0.999, agree
+
+
+def test_end_to_end_small_clip_gmm3(S):
+    frames, _ = synth.clip_small(10)
+    agree = _run_clip(S, frames, dict(O.CONFIG_SMALL, gmm_components=3, em_iters=5))
     assert min(agree) >= 0.999, agree
 
 
