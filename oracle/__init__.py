@@ -102,6 +102,14 @@ def lib():
         L.orc_gmm_loglik.restype = C.c_double
         L.orc_gmm_logpdf.argtypes = [P(OrcGmm), vp]
         L.orc_gmm_logpdf.restype = C.c_double
+        L.orc_kalman_chain.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, vp, vp, vp]
+        L.orc_kalman_chain.restype = None
+        L.orc_prior_clip_f.argtypes = [P(OrcParams), C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_double,
+                                       C.c_double, vp, vp]
+        L.orc_prior_clip_f.restype = None
+        L.orc_prior_clip_grad.argtypes = [P(OrcParams), C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_double,
+                                          C.c_double, vp, vp, vp, vp, P(C.c_double), P(C.c_double)]
+        L.orc_prior_clip_grad.restype = None
         L.orc_push_frame.argtypes = [P(OrcParams), C.c_int, C.c_int, P(OrcState), vp, vp, vp, vp]
         L.orc_push_frame.restype = C.c_int64
         _lib = L
@@ -239,6 +247,45 @@ def prior(sal, prev_mask, w_f, cfg=None, **over):
     pm = _c(prev_mask, np.uint8) if prev_mask is not None else None
     lib().orc_prior(C.byref(P), H, W, _p(sal), _p(pm) if pm is not None else None, w_f, _p(q), _p(pr))
     return q, pr
+
+
+def kalman_chain(T, Q, R, t0=0):
+    """w_f(t) and its derivatives dw_f/dQ, dw_f/dR for t = t0 .. t0+T-1 (Sec. 6, from
+    P(-1) = inf), Q = sigma1^2, R = sigma2^2."""
+    wf, dq, dr = np.empty(T), np.empty(T), np.empty(T)
+    lib().orc_kalman_chain(t0, T, Q, R, _p(wf), _p(dq), _p(dr))
+    return wf, dq, dr
+
+
+def prior_clip(rgb, Q, R, fmap=None, t0=0, cfg=None, **over):
+    """Backward form's forward (Secs. 3, 5, 6): saliency and Kalman-updated prior of
+    T floating-point frames (T, H, W, 3) in [0, 255] at clip times t0..t0+T-1;
+    fmap = smoothed previous masks (T, H, W) or None.  Returns (saliency, prior)."""
+    rgb = _c(rgb, np.float64)
+    T, H, W = rgb.shape[:3]
+    fm = _c(fmap, np.float64) if fmap is not None else None
+    P = params(cfg, **over)
+    sal, pr = np.empty((T, H, W)), np.empty((T, H, W))
+    lib().orc_prior_clip_f(C.byref(P), T, t0, H, W, _p(rgb), _p(fm) if fm is not None else None, Q, R,
+                           _p(sal), _p(pr))
+    return sal, pr
+
+
+def prior_clip_grad(rgb, Q, R, g_prior, g_sal=None, fmap=None, t0=0, cfg=None, **over):
+    """Gradient of L = sum_t <g_prior_t, prior_t> + <g_sal_t, saliency_t> with respect to
+    the frames, the four channel weights w, Q and R.  Returns (g_rgb, g_w (4,), g_Q, g_R)."""
+    rgb = _c(rgb, np.float64)
+    T, H, W = rgb.shape[:3]
+    fm = _c(fmap, np.float64) if fmap is not None else None
+    gp = _c(g_prior, np.float64)
+    gs = _c(g_sal, np.float64) if g_sal is not None else None
+    P = params(cfg, **over)
+    grgb, gw = np.empty((T, H, W, 3)), np.empty(4)
+    gQ, gR = C.c_double(), C.c_double()
+    lib().orc_prior_clip_grad(C.byref(P), T, t0, H, W, _p(rgb), _p(fm) if fm is not None else None, Q, R,
+                              _p(gp), _p(gs) if gs is not None else None, _p(grgb), _p(gw), C.byref(gQ),
+                              C.byref(gR))
+    return grgb, gw, gQ.value, gR.value
 
 
 def colour_models(prior_map, rgb):

@@ -105,6 +105,14 @@ int64_t orc_cut_energy(int H, int W, int nbr, const int32_t* cs, const int32_t* 
 int64_t orc_bruteforce(int H, int W, int nbr, const int32_t* cs, const int32_t* ct,
                        const int32_t* ncap, uint8_t* mask_min, int32_t* n_argmin);
 
+/* --- backward form (oracle_grad.c): float frames in [0, 255], Q = sigma1^2, R = sigma2^2 --- */
+void orc_kalman_chain(int t0, int T, double Q, double R, double* wf, double* dwf_dQ, double* dwf_dR);
+void orc_prior_clip_f(const orc_params* P, int T, int t0, int H, int W, const double* rgb, const double* fmap,
+                      double Q, double R, double* saliency, double* prior);
+void orc_prior_clip_grad(const orc_params* P, int T, int t0, int H, int W, const double* rgb, const double* fmap,
+                         double Q, double R, const double* g_prior, const double* g_sal, double* grgb, double* gw,
+                         double* gQ, double* gR);
+
 /* --- one frame of the whole method --- */
 typedef struct orc_state {
   int t;               /* frame index */

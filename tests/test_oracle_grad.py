@@ -1,0 +1,148 @@
+"""Pins of the oracle's reverse pass (oracle_grad.c) for the backward form:
+saliency (Sec. 3 / Sec. 7.2) and the Kalman-updated prior (Sec. 6) differentiated
+with respect to the frames, the channel weights w, Q = sigma1^2 and R = sigma2^2.
+
+The reverse pass is checked against FP64 central differences of the oracle's own
+forward (a different code path: the forward never runs an adjoint), against the
+already pinned integer-frame oracle, closed forms and linearity."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+Q0, R0 = 0.03 ** 2, 0.035 ** 2
+CFG = dict(O.CONFIG_SMALL)
+
+
+def _case(T=2, H=48, W=64, seed=3):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(20, 235, (T, H, W, 3))
+    x[:, 10:30, 20:40, 0] += 15
+    f = rng.uniform(0, 1, (T, H, W))
+    gp, gs = rng.normal(size=(T, H, W)), rng.normal(size=(T, H, W))
+    return rng, x, f, gp, gs
+
+
+def _loss(x, f, gp, gs, Q=Q0, R=R0, w=None, t0=1):
+    cfg = dict(CFG)
+    if w is not None:
+        cfg["w"] = list(w)
+    s, p = O.prior_clip(x, Q, R, fmap=f, t0=t0, cfg=cfg)
+    return (gp * p).sum() + (gs * s).sum()
+
+
+def test_kalman_chain_matches_step_recursion_and_differences():
+    T = 7
+    wf, dq, dr = O.kalman_chain(T, Q0, R0)
+
+    def run(Q, R):
+        out, P = [], 0.0
+        for t in range(T):
+            P, w = O.kalman_step(t, P, np.sqrt(Q), np.sqrt(R))
+            out.append(w)
+        return np.array(out)
+
+    np.testing.assert_allclose(wf, run(Q0, R0), rtol=1e-14, atol=0)
+    h = 1e-6
+    fq = (run(Q0 * (1 + h), R0) - run(Q0 * (1 - h), R0)) / (2 * h * Q0)
+    fr = (run(Q0, R0 * (1 + h)) - run(Q0, R0 * (1 - h))) / (2 * h * R0)
+    np.testing.assert_allclose(dq, fq, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(dr, fr, rtol=1e-7, atol=1e-9)
+    wf2, dq2, _ = O.kalman_chain(3, Q0, R0, t0=4)
+    np.testing.assert_array_equal(wf2, wf[4:7])
+    np.testing.assert_array_equal(dq2, dq[4:7])
+    assert wf[0] == 0 and dq[0] == 0 and dr[0] == 0  # P(-1) = inf: no previous mask
+
+
+def test_float_forward_equals_integer_oracle():
+    """On an integer-valued frame the backward form's forward is the plain method."""
+    rgb = np.stack([f for f, _ in O_clip()])
+    T, H, W = rgb.shape[:3]
+    masks = [(np.add.outer(np.arange(H), np.arange(W)) % 37 < 11).astype(np.uint8) for _ in range(T)]
+    fm = np.stack([O.smooth_mask(m) for m in masks])
+    sal, pr = O.prior_clip(rgb.astype(np.float64), Q0, R0, fmap=fm, t0=1, cfg=CFG)
+    wf, _, _ = O.kalman_chain(T, Q0, R0, t0=1)
+    for t in range(T):
+        s_ref = O.saliency(rgb[t], CFG)
+        np.testing.assert_array_equal(sal[t], s_ref)
+        _, p_ref = O.prior(s_ref, masks[t], wf[t], CFG)
+        np.testing.assert_allclose(pr[t], p_ref, rtol=0, atol=1e-15)
+
+
+def O_clip():
+    from paper_1008_0502_b300 import synth
+    frames, _ = synth.clip_small(2, seed=synth.SEED_BASE + 5)
+    return [(f, None) for f in frames]
+
+
+def test_frame_gradient_matches_central_differences():
+    rng, x, f, gp, gs = _case()
+    g, _, _, _ = O.prior_clip_grad(x, Q0, R0, gp, gs, fmap=f, t0=1, cfg=CFG)
+    # random directions (small step: many kinks lie within 1e-3 along a dense direction)
+    for _ in range(2):
+        v = rng.normal(size=x.shape)
+        h = 1e-5
+        fd = (_loss(x + h * v, f, gp, gs) - _loss(x - h * v, f, gp, gs)) / (2 * h)
+        assert abs(fd - (g * v).sum()) <= 1e-6 * abs(fd)
+    # single coordinates at h = 1e-3, including frame corners and both frames
+    H, W = x.shape[1:3]
+    for idx in [(0, 0, 0, 0), (0, 5, 5, 1), (1, 20, 30, 0), (1, H - 1, W - 1, 2), (0, 24, 32, 2), (1, 0, W - 1, 1)]:
+        e = np.zeros_like(x)
+        e[idx] = 1.0
+        h = 1e-3
+        fd = (_loss(x + h * e, f, gp, gs) - _loss(x - h * e, f, gp, gs)) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g).max()), idx
+
+
+def test_parameter_gradients_match_central_differences():
+    _, x, f, gp, gs = _case()
+    _, gw, gQ, gR = O.prior_clip_grad(x, Q0, R0, gp, gs, fmap=f, t0=1, cfg=CFG)
+    w0 = np.array(CFG["w"], float)
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = 1e-4
+        fd = (_loss(x, f, gp, gs, w=w0 + e) - _loss(x, f, gp, gs, w=w0 - e)) / 2e-4
+        assert abs(fd - gw[k]) <= 1e-6 * max(abs(fd), 1.0), k
+    h = 1e-6
+    fq = (_loss(x, f, gp, gs, Q=Q0 * (1 + h)) - _loss(x, f, gp, gs, Q=Q0 * (1 - h))) / (2 * h * Q0)
+    fr = (_loss(x, f, gp, gs, R=R0 * (1 + h)) - _loss(x, f, gp, gs, R=R0 * (1 - h))) / (2 * h * R0)
+    assert abs(fq - gQ) <= 1e-6 * abs(fq)
+    assert abs(fr - gR) <= 1e-6 * abs(fr)
+
+
+def test_gradient_is_linear_in_the_cotangent():
+    rng, x, f, gp, gs = _case(T=1, H=40, W=56, seed=9)
+    gp2 = rng.normal(size=gp.shape)
+    a, b = 0.7, -1.3
+    g1 = O.prior_clip_grad(x, Q0, R0, gp, gs, fmap=f, cfg=CFG)
+    g2 = O.prior_clip_grad(x, Q0, R0, gp2, None, fmap=f, cfg=CFG)
+    g3 = O.prior_clip_grad(x, Q0, R0, a * gp + b * gp2, a * gs, fmap=f, cfg=CFG)
+    np.testing.assert_allclose(g3[0], a * g1[0] + b * g2[0], rtol=1e-9, atol=1e-12 * np.abs(g1[0]).max())
+    np.testing.assert_allclose(g3[1], a * g1[1] + b * g2[1], rtol=1e-9, atol=1e-12)
+    assert abs(g3[2] - (a * g1[2] + b * g2[2])) <= 1e-9 * abs(g1[2])
+
+
+def test_constant_frame_closed_form():
+    """A constant frame has a flat saliency (N(.) of a constant map is 0), so q is eps
+    on the border and 0 inside, nothing reaches the frame, and dL/dQ, dL/dR follow
+    from w_f alone: dL/dw_f = sum g (f - q)."""
+    T, H, W = 2, 40, 48
+    rng = np.random.default_rng(4)
+    x = np.full((T, H, W, 3), 128.0)
+    f = rng.uniform(0, 1, (T, H, W))
+    gp = rng.normal(size=(T, H, W))
+    g, gw, gQ, gR = O.prior_clip_grad(x, Q0, R0, gp, None, fmap=f, t0=1, cfg=CFG)
+    assert not g.any() and not gw.any()
+    b = CFG.get("border_px", O.params(CFG).border_px)
+    q = np.zeros((H, W))
+    q[:b, :] = q[-b:, :] = q[:, :b] = q[:, -b:] = O.params(CFG).eps
+    _, dq, dr = O.kalman_chain(T, Q0, R0, t0=1)
+    gwf = np.array([(gp[t] * (f[t] - q)).sum() for t in range(T)])
+    assert abs(gQ - (gwf * dq).sum()) <= 1e-12 * abs(gQ)
+    assert abs(gR - (gwf * dr).sum()) <= 1e-12 * abs(gR)
+
+
+def test_saliency_cotangent_leaves_kalman_untouched():
+    _, x, f, gp, gs = _case(T=1, H=40, W=56, seed=11)
+    g, gw, gQ, gR = O.prior_clip_grad(x, Q0, R0, np.zeros_like(gp), gs, fmap=f, cfg=CFG)
+    assert gQ == 0 and gR == 0 and np.abs(g).max() > 0
