@@ -239,6 +239,58 @@ int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* 
 /* Size of pyramid level `level` along an n-pixel axis: ceil-halving. */
 int seg_level_dim(int n, int level);
 
+/* ------------------------------------------------------------------------
+ * Backward form: the saliency map (Sec. 3, Sec. 7.2) and the Kalman-updated
+ * prior (Sec. 6) of B floating-point frames, differentiated with respect to
+ * the frames, the four channel weights and the Kalman noise variances.
+ *
+ * theta (dev, 6 doubles) = (w_I, w_RG, w_BY, w_O, Q, R): the weights of
+ * S = sum_k w_k N(C_k) (Sec. 3) and Q = sigma1^2, R = sigma2^2 of the
+ * sequential update (Sec. 6); the context's params supply everything else
+ * (their w, sigma1 and sigma2 are not used).
+ *
+ * Frames (dev, float, B x H x W x 3, values nominally in [0, 255]) are clip
+ * times t0 .. t0+B-1 of one video: w_f(t) = Q / (Q + R + P(t-1)) with
+ * P(t) = Q (R + P(t-1)) / (Q + R + P(t-1)) and P(-1) = inf, so w_f(0) = 0.
+ * fmap (dev, float, B x H x W, or NULL for zeros) holds the previous masks
+ * smoothed as in Sec. 6 (constants: no derivative is taken through them).
+ *
+ * Derivatives are those of the forward as written, with one-sided choices at
+ * its kinks: N(.) through the first index (row-major) attaining the minimum,
+ * the maximum and each tile maximum; |a| through sign(a), 0 at a = 0; max(0, a)
+ * through a > 0; the hue-normalisation mask (10 (r+g+b) > max) held fixed.
+ * The paper trains nothing and has no derivative; this form exists so that the
+ * weights and variances can be fitted by gradient descent.
+ * ------------------------------------------------------------------------ */
+typedef struct seg_diff seg_diff;
+
+/* Device bytes of a backward-form context.  Errors as seg_diff_create. */
+int seg_diff_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes);
+
+/* Allocates a context for batches of B frames of H x W on the current device;
+ * its work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ * Errors: SEG_EINVAL (params as seg_create; B < 1; B*H*W > 2^26; more than 4096
+ * N(.) tiles in a center-surround map or 1024 at sigma_S; W > 5120),
+ * SEG_ENOMEM, SEG_ECUDA. */
+int seg_diff_create(void* stream, int B, int H, int W, const seg_params* p, seg_diff** out);
+int seg_diff_destroy(seg_diff* d);
+
+/* Forward: saliency (dev, B x H x W, or NULL) and prior (dev, B x H x W) of the
+ * frames at clip times t0 .. t0+B-1 (0 <= t0 <= 2^24).  Keeps what the backward
+ * needs in the context (the pyramid, the Gabor responses, the accumulators and
+ * conspicuity maps at sigma_S, w_f(t) and its derivatives).
+ * Errors: SEG_EINVAL (NULL rgb/theta/prior, t0 out of range), SEG_ECUDA. */
+int seg_diff_forward(seg_diff* d, const float* rgb_dev, const float* fmap_dev, const double* theta_dev, int t0,
+                     float* saliency_dev, float* prior_dev);
+
+/* Backward of the last seg_diff_forward (same rgb, fmap and theta):
+ * L = sum_b <g_prior_b, prior_b> + <g_sal_b, saliency_b>; g_prior (dev,
+ * B x H x W), g_sal (dev, B x H x W, or NULL for zeros).  Writes dL/dframes into
+ * g_rgb (dev, B x H x W x 3) and dL/dtheta into g_theta (dev, 6 doubles).
+ * Errors: SEG_EINVAL (NULL pointers; no forward yet), SEG_ECUDA. */
+int seg_diff_backward(seg_diff* d, const float* rgb_dev, const float* fmap_dev, const double* theta_dev,
+                      const float* g_prior_dev, const float* g_sal_dev, float* g_rgb_dev, double* g_theta_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -110,6 +110,8 @@ def lib():
         L.orc_prior_clip_grad.argtypes = [P(OrcParams), C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, C.c_double,
                                           C.c_double, vp, vp, vp, vp, P(C.c_double), P(C.c_double)]
         L.orc_prior_clip_grad.restype = None
+        L.orc_prior_clip_ties.argtypes = [P(OrcParams), C.c_int, C.c_int, C.c_int, vp, C.c_double, vp]
+        L.orc_prior_clip_ties.restype = None
         L.orc_push_frame.argtypes = [P(OrcParams), C.c_int, C.c_int, P(OrcState), vp, vp, vp, vp]
         L.orc_push_frame.restype = C.c_int64
         _lib = L
@@ -269,6 +271,18 @@ def prior_clip(rgb, Q, R, fmap=None, t0=0, cfg=None, **over):
     lib().orc_prior_clip_f(C.byref(P), T, t0, H, W, _p(rgb), _p(fm) if fm is not None else None, Q, R,
                            _p(sal), _p(pr))
     return sal, pr
+
+
+def prior_clip_ties(rgb, delta, cfg=None, **over):
+    """Near-tie census of the forward on frames (T, H, W, 3): counts of decisions with
+    margin below delta times the map's range -- N(.) minimum/maximum, tile maxima,
+    center-surround signs (test support: FP32 and FP64 can disagree on those)."""
+    rgb = _c(rgb, np.float64)
+    T, H, W = rgb.shape[:3]
+    P = params(cfg, **over)
+    out = np.zeros(3, dtype=np.int64)
+    lib().orc_prior_clip_ties(C.byref(P), T, H, W, _p(rgb), delta, _p(out))
+    return out
 
 
 def prior_clip_grad(rgb, Q, R, g_prior, g_sal=None, fmap=None, t0=0, cfg=None, **over):

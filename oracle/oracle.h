@@ -109,6 +109,7 @@ int64_t orc_bruteforce(int H, int W, int nbr, const int32_t* cs, const int32_t* 
 void orc_kalman_chain(int t0, int T, double Q, double R, double* wf, double* dwf_dQ, double* dwf_dR);
 void orc_prior_clip_f(const orc_params* P, int T, int t0, int H, int W, const double* rgb, const double* fmap,
                       double Q, double R, double* saliency, double* prior);
+void orc_prior_clip_ties(const orc_params* P, int T, int H, int W, const double* rgb, double delta, long* ties);
 void orc_prior_clip_grad(const orc_params* P, int T, int t0, int H, int W, const double* rgb, const double* fmap,
                          double Q, double R, const double* g_prior, const double* g_sal, double* grgb, double* gw,
                          double* gQ, double* gR);

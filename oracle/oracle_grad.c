@@ -105,6 +105,24 @@ typedef struct {
   int* targ; /* per tile: first index of its maximum */
 } nstat;
 
+/* Near-tie census (test support): decisions of the forward whose margin,
+ * relative to the map's range, is below g_tie_delta: [0] minimum / maximum of an
+ * N(.) map, [1] a tile maximum, [2] the sign of a center-surround value. */
+static double g_tie_delta = 0.0;
+static long g_ties[3];
+
+static void count_ties(int h, int w, const double* v, int T, const nstat* st) {
+  if (!(g_tie_delta > 0) || st->flat) return;
+  int n = h * w, ntx = (w + T - 1) / T;
+  double D = st->mx - st->mn, lim = g_tie_delta * D;
+  for (int i = 0; i < n; ++i) {
+    if (i != st->amin && v[i] - st->mn < lim) g_ties[0]++;
+    if (i != st->amax && st->mx - v[i] < lim) g_ties[0]++;
+    int y = i / w, x = i - y * w, t = (y / T) * ntx + x / T;
+    if (i != st->targ[t] && v[st->targ[t]] - v[i] < lim) g_ties[1]++;
+  }
+}
+
 static void norm_fw(int h, int w, const double* v, int T, double flat, double* out, nstat* st) {
   int n = h * w, ntx = (w + T - 1) / T, nty = (h + T - 1) / T;
   st->nt = ntx * nty;
@@ -136,6 +154,7 @@ static void norm_fw(int h, int w, const double* v, int T, double flat, double* o
   st->mbar = st->nt > 1 ? (sum - 1.0) / (st->nt - 1) : 0.0;
   st->F = (1 - st->mbar) * (1 - st->mbar);
   for (int i = 0; i < n; ++i) out[i] = (v[i] - st->mn) / D * st->F;
+  count_ties(h, w, v, T, st);
 }
 /* g_v += N^T g_out */
 static void norm_bw(int h, int w, const double* v, const nstat* st, const double* g_out, double* g_v) {
@@ -233,10 +252,12 @@ static void features_bw(int H, int W, const double* rgb, double smax, const doub
     double r = rgb[3 * i], g = rgb[3 * i + 1], b = rgb[3 * i + 2], s = r + g + b;
     double gs = gI[i] / 765.0, gr = gs, gg = gs, gb = gs;
     if (10 * s > smax) {
-      double rn = 3 * r / s, gn = 3 * g / s, bn = 3 * b / s;
-      double aR = rn - (gn + bn) / 2 > 0, aG = gn - (rn + bn) / 2 > 0, aB = bn - (rn + gn) / 2 > 0;
-      double aY = (rn + gn) / 2 - fabs(rn - gn) / 2 - bn > 0;
-      double sg = rn - gn > 0 ? 1.0 : (rn - gn < 0 ? -1.0 : 0.0);
+      /* the clamps' decisions: s > 0 scales out of every sign, so they are the signs
+       * of linear forms of (r, g, b) (e.g. R > 0 iff 2r - g - b > 0), taken on
+       * those forms, which are exact for single-precision inputs */
+      double aR = 2 * r - g - b > 0, aG = 2 * g - r - b > 0, aB = 2 * b - r - g > 0;
+      double aY = fmin(r, g) - b > 0; /* (rn + gn)/2 - |rn - gn|/2 = min(rn, gn) */
+      double sg = r > g ? 1.0 : (r < g ? -1.0 : 0.0);
       double gR = gRG[i], gG = -gRG[i], gB = gBY[i], gY = -gBY[i];
       double grn = gR * aR - 0.5 * gG * aG - 0.5 * gB * aB + gY * aY * (0.5 - 0.5 * sg);
       double ggn = -0.5 * gR * aR + gG * aG - 0.5 * gB * aB + gY * aY * (0.5 + 0.5 * sg);
@@ -306,6 +327,9 @@ static void fwd_run(fwd_t* F, const orc_params* P, int H, int W, const double* r
         for (int i = 0; i < nc; ++i) map[i] = fabs(opp ? cen[i] + up[i] : cen[i] - up[i]);
         nstat st;
         norm_fw(F->hl[c], F->wl[c], map, P->norm_tile, P->norm_flat, nm, &st);
+        if (g_tie_delta > 0 && !st.flat)
+          for (int i = 0; i < nc; ++i)
+            if (map[i] > 0 && map[i] < g_tie_delta * (st.mx - st.mn)) g_ties[2]++;
         free(st.targ);
         for (int l = c; l < F->sS; ++l) {
           reduce_fw(F->hl[l], F->wl[l], nm, tmp);
@@ -406,6 +430,21 @@ void orc_kalman_chain(int t0, int T, double Q, double R, double* wf, double* dwf
     dPq = Pq;
     dPr = Pr;
   }
+}
+
+/* Public (test support): counts of the forward's near-tie decisions over the
+ * frames, margin below delta times the map's range (see g_ties). */
+void orc_prior_clip_ties(const orc_params* P, int T, int H, int W, const double* rgb, double delta, long* ties) {
+  size_t n = (size_t)H * W;
+  g_tie_delta = delta;
+  g_ties[0] = g_ties[1] = g_ties[2] = 0;
+  for (int t = 0; t < T; ++t) {
+    fwd_t F;
+    fwd_run(&F, P, H, W, rgb + 3 * n * t);
+    fwd_free(&F);
+  }
+  for (int k = 0; k < 3; ++k) ties[k] = g_ties[k];
+  g_tie_delta = 0.0;
 }
 
 /* Public: saliency and prior of T consecutive floating-point frames (clip times

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libseg.so")
-SOURCES = ["saliency.cu", "prior_terms.cu", "maxflow.cu", "seg_api.cu", "mincut_static.cu"]
+SOURCES = ["saliency.cu", "prior_terms.cu", "maxflow.cu", "seg_api.cu", "mincut_static.cu", "diff.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

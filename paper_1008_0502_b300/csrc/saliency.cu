@@ -34,9 +34,15 @@
 __constant__ float c_binom[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
 
 // ------------------------------------------------------------------ k_rgb_max
-__global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, unsigned* mm,
+// TIn = uint8_t (RGB8) or float (values in [0, 255], the backward form); for
+// float frames smax holds the maximum's float bits (non-negative floats order
+// like their bit patterns).
+template <typename TIn>
+__global__ void k_rgb_max(const TIn* __restrict__ rgb, int n, int* smax, unsigned* mm,
                           int nmaps, const SegIO* io) {
-  if (!rgb) rgb = io->rgb;
+  if constexpr (std::is_same<TIn, uint8_t>::value) {
+    if (!rgb) rgb = io->rgb;
+  }
   const int fb = blockIdx.y;  // frame of the batch
   rgb += (size_t)fb * 3 * n;
   smax += fb;
@@ -48,8 +54,13 @@ __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, uns
   }
   int m = 0;
   for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
-    int s = rgb[3 * (size_t)i] + rgb[3 * (size_t)i + 1] + rgb[3 * (size_t)i + 2];
-    m = max(m, s);
+    if constexpr (std::is_same<TIn, uint8_t>::value) {
+      int s = rgb[3 * (size_t)i] + rgb[3 * (size_t)i + 1] + rgb[3 * (size_t)i + 2];
+      m = max(m, s);
+    } else {
+      float s = rgb[3 * (size_t)i] + rgb[3 * (size_t)i + 1] + rgb[3 * (size_t)i + 2];
+      m = max(m, s > 0.f ? __float_as_int(s) : 0);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ int wm[32];
@@ -65,12 +76,16 @@ __global__ void k_rgb_max(const uint8_t* __restrict__ rgb, int n, int* smax, uns
 // Sec. 7.2 step 1 (features) and step 2 (pyramid).  I = (r+g+b)/765; where
 // 10*(r+g+b) > max(r+g+b) the normalised colour rn = 3r/(r+g+b) etc. (else
 // 0); R, G, B, Y broadly tuned channels clamped at 0; RG = R-G, BY = B-Y.
-__global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict__ rgb, int H, int W,
+template <typename TIn>
+__global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rgb, int H, int W,
                                                       const int* __restrict__ smax_p,
                                                       float* __restrict__ I1, float* __restrict__ RG1,
                                                       float* __restrict__ BY1, int h1, int w1,
                                                       const SegIO* io) {
-  if (!rgb) rgb = io->rgb;
+  constexpr bool U8 = std::is_same<TIn, uint8_t>::value;
+  if constexpr (U8) {
+    if (!rgb) rgb = io->rgb;
+  }
   __shared__ float sF[3][RED_IN_Y][RED_IN_X];
   __shared__ float sH[3][RED_IN_Y][RED_TX];
   const int fb = blockIdx.z;  // frame of the batch
@@ -85,15 +100,21 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict_
   // all of this thread's input pixels are loaded first (independent loads in
   // flight together), then turned into features
   constexpr int NIN = RED_IN_Y * RED_IN_X, PER = (NIN + 255) / 256;
-  unsigned pk[PER];
+  constexpr int NW = U8 ? 1 : 3;  // registers per input pixel
+  unsigned pk[PER][NW];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     int i = threadIdx.x + k * 256;
     if (i < NIN) {
       int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
       int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
-      const uint8_t* p = rgb + 3 * ((size_t)gy * W + gx);
-      pk[k] = (unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16);
+      const TIn* p = rgb + 3 * ((size_t)gy * W + gx);
+      if constexpr (U8) {
+        pk[k][0] = (unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) pk[k][j] = __float_as_uint(p[j]);
+      }
     }
   }
 #pragma unroll
@@ -101,20 +122,35 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const uint8_t* __restrict_
     int i = threadIdx.x + k * 256;
     if (i >= NIN) break;
     int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
-    int r = pk[k] & 255, g = (pk[k] >> 8) & 255, b = pk[k] >> 16;
-    int s = r + g + b;
+    float r, g, b, s;
+    bool hue;
+    if constexpr (U8) {
+      int ri = pk[k][0] & 255, gi = (pk[k][0] >> 8) & 255, bi = pk[k][0] >> 16;
+      int si = ri + gi + bi;
+      hue = 10 * si > smax;
+      r = (float)ri;
+      g = (float)gi;
+      b = (float)bi;
+      s = (float)si;
+    } else {
+      r = __uint_as_float(pk[k][0]);
+      g = __uint_as_float(pk[k][1]);
+      b = __uint_as_float(pk[k][2]);
+      s = r + g + b;
+      hue = 10.f * s > __int_as_float(smax);
+    }
     float rn = 0.f, gn = 0.f, bn = 0.f;
-    if (10 * s > smax) {
-      float inv = 3.f / (float)s;
-      rn = (float)r * inv;
-      gn = (float)g * inv;
-      bn = (float)b * inv;
+    if (hue) {
+      float inv = 3.f / s;
+      rn = r * inv;
+      gn = g * inv;
+      bn = b * inv;
     }
     float R = fmaxf(0.f, rn - (gn + bn) / 2.f);
     float G = fmaxf(0.f, gn - (rn + bn) / 2.f);
     float B = fmaxf(0.f, bn - (rn + gn) / 2.f);
     float Y = fmaxf(0.f, (rn + gn) / 2.f - fabsf(rn - gn) / 2.f - bn);
-    sF[0][ry][rx] = (float)s / 765.f;
+    sF[0][ry][rx] = s / 765.f;
     sF[1][ry][rx] = R - G;
     sF[2][ry][rx] = B - Y;
   }
@@ -222,6 +258,7 @@ __global__ void __launch_bounds__(1024) k_pyr_tail(PyrTailArgs a) {
 struct GaborArgs {
   const float* in[SEG_MAX_LEVELS];
   float* out[SEG_MAX_ORIENT][SEG_MAX_LEVELS];
+  float2* out_c[SEG_MAX_ORIENT][SEG_MAX_LEVELS];  // optional complex responses (backward form)
   int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
   int lvl_first, lvl_last;
   int blk_off[SEG_MAX_LEVELS + 1];  // prefix of tile counts from lvl_first
@@ -286,6 +323,7 @@ __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
       re -= t.kap_re[k] * dc;
       im -= t.kap_im[k] * dc;
       out[(size_t)oy * w + ox] = sqrtf(re * re + im * im);
+      if (a.out_c[k][l]) a.out_c[k][l][fo + (size_t)oy * w + ox] = make_float2(re, im);
     }
   }
 }
@@ -497,14 +535,6 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
 
 // ------------------------------------------------------------------ conspicuity, S
 
-// Order-preserving map from float to unsigned (so atomicMax works for any sign).
-__device__ __forceinline__ unsigned f2key(float x) {
-  unsigned u = __float_as_uint(x);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float key2f(unsigned k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
 
 #define CONSP_TILES 1024  // N(.) tiles per map at sigma_S
 
@@ -573,6 +603,7 @@ struct ConspArgs {
   const int2* fcol;
   float flat;
   float wgt[4];
+  const double* wdev;  // if set: the channel weights are read from device memory
   float* csum;
   float* consp;
   float* S;
@@ -607,13 +638,16 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   v[2] = a.acc + 2 * (size_t)n;
   v[3] = a.csum;
   block_norm_multi(v, 4, a.h, a.w, a.tile, a.flat, ab, red, tmax);
+  float wk[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wk[k] = a.wdev ? (float)a.wdev[k] : a.wgt[k];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     float S = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       float nv = ab[2 * k] * v[k][i] + ab[2 * k + 1];
       a.consp[(size_t)k * n + i] = nv;
-      S += a.wgt[k] * nv;
+      S += wk[k] * nv;
     }
     a.S[i] = S;
   }
@@ -628,20 +662,10 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   __shared__ int nr, nc;
   if (threadIdx.x == 0) nr = nc = 0;
   __syncthreads();
-  auto cell = [](int d, int ns, int nd) {
-    int i0, i1;
-    float f;
-    seg_src_coord(d, ns, nd, i0, i1, f);
-    return (i0 == i1) ? (i0 == 0 && d < nd / 2 ? -1 : ns) : i0;
-  };
-  for (int y = threadIdx.x; y < a.H; y += blockDim.x) {
-    int id = cell(y, a.h, a.H);
-    if (y == 0 || y == a.H - 1 || cell(y - 1, a.h, a.H) != id || cell(y + 1, a.h, a.H) != id) crow[atomicAdd(&nr, 1)] = y;
-  }
-  for (int x = threadIdx.x; x < a.W; x += blockDim.x) {
-    int id = cell(x, a.w, a.W);
-    if (x == 0 || x == a.W - 1 || cell(x - 1, a.w, a.W) != id || cell(x + 1, a.w, a.W) != id) ccol[atomicAdd(&nc, 1)] = x;
-  }
+  for (int y = threadIdx.x; y < a.H; y += blockDim.x)
+    if (seg_up_candidate(y, a.h, a.H)) crow[atomicAdd(&nr, 1)] = y;
+  for (int x = threadIdx.x; x < a.W; x += blockDim.x)
+    if (seg_up_candidate(x, a.w, a.W)) ccol[atomicAdd(&nc, 1)] = x;
   __syncthreads();
   float mxv = 0.f;
   for (int k = threadIdx.x; k < nr * nc; k += blockDim.x)
@@ -700,7 +724,7 @@ static void make_taps(const seg_params& p, GaborTaps& t) {
   }
 }
 
-int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes) {
+int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes, bool keep_complex) {
   memset(&s, 0, sizeof(s));
   s.B = B;
   s.H = H;
@@ -757,6 +781,10 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
   for (int k = 0; k < s.no; ++k)
     for (int l = s.c_min; l <= s.s_max; ++l)
       s.ori[k][l] = (float*)take(Bz * sizeof(float) * s.hl[l] * s.wl[l]);
+  if (keep_complex)
+    for (int k = 0; k < s.no; ++k)
+      for (int l = s.c_min; l <= s.s_max; ++l)
+        s.oc[k][l] = (float2*)take(Bz * sizeof(float2) * s.hl[l] * s.wl[l]);
   s.mm = (unsigned*)take(Bz * sizeof(unsigned) * 2 * s.nmaps);
   s.tpart = (float*)take(Bz * sizeof(float) * s.nbands_total);
   s.nab = (float*)take(Bz * sizeof(float) * 2 * s.nmaps);
@@ -794,12 +822,16 @@ void sal_bind(SalWS& s, char* base) {
   for (int ch = 0; ch < 3; ++ch)
     for (int l = 1; l < s.L; ++l) fix(s.pyr[ch][l]);
   for (int k = 0; k < s.no; ++k)
-    for (int l = s.c_min; l <= s.s_max; ++l) fix(s.ori[k][l]);
+    for (int l = s.c_min; l <= s.s_max; ++l) {
+      fix(s.ori[k][l]);
+      if (s.oc[k][l]) fix(s.oc[k][l]);
+    }
   fix(s.mm);
   fix(s.tpart);
   fix(s.nab);
   fix(s.acc[0]);
   fix(s.acc[1]);
+  s.acc_final = s.acc[(s.c_max - s.c_min) & 1];
   fix(s.consp);
   fix(s.csum);
   fix(s.S);
@@ -856,17 +888,27 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
 }
 
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
-  SalWS& s = c->sal;
-  cudaStream_t st = c->stream;
+  return sal_run(c->sal, c->stream, rgb, false, c->io_mode ? c->io : nullptr, nullptr, sal_out, upsample);
+}
+
+int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegIO* io, const double* wdev,
+            float* sal_out, bool upsample) {
   const int H = s.H, W = s.W, N = H * W, B = s.B;
   SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, B * sizeof(int), st));
   int nb = min((N + 255) / 256, B > 1 ? 148 : 148 * 8);
   nb = max(nb, (s.nmaps + 255) / 256);
-  const SegIO* io = c->io_mode ? c->io : nullptr;
-  k_rgb_max<<<dim3(nb, B), 256, 0, st>>>(rgb, N, s.smax, s.mm, s.nmaps, io);
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);
-  k_feat_reduce1<<<g1, 256, 0, st>>>(rgb, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1], s.hl[1],
-                                     s.wl[1], io);
+  if (rgb_f32) {
+    const float* f = (const float*)rgb;
+    k_rgb_max<float><<<dim3(nb, B), 256, 0, st>>>(f, N, s.smax, s.mm, s.nmaps, nullptr);
+    k_feat_reduce1<float><<<g1, 256, 0, st>>>(f, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
+                                              s.hl[1], s.wl[1], nullptr);
+  } else {
+    const uint8_t* u = (const uint8_t*)rgb;
+    k_rgb_max<uint8_t><<<dim3(nb, B), 256, 0, st>>>(u, N, s.smax, s.mm, s.nmaps, io);
+    k_feat_reduce1<uint8_t><<<g1, 256, 0, st>>>(u, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
+                                                s.hl[1], s.wl[1], io);
+  }
   // tiled launches while the produced level is large; one tail launch for the rest
   int tail_from = s.L - 1;
   for (int l = 1; l + 1 < s.L; ++l)
@@ -908,7 +950,10 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
     ga.in[l] = s.pyr[0][l];
     ga.hl[l] = s.hl[l];
     ga.wl[l] = s.wl[l];
-    for (int k = 0; k < s.no; ++k) ga.out[k][l] = s.ori[k][l];
+    for (int k = 0; k < s.no; ++k) {
+      ga.out[k][l] = s.ori[k][l];
+      ga.out_c[k][l] = s.oc[k][l];
+    }
     ga.blk_off[l - s.c_min] = tot;
     tot += ((s.wl[l] + GB_TX - 1) / GB_TX) * ((s.hl[l] + GB_TY - 1) / GB_TY);
   }
@@ -970,6 +1015,7 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
   pa.tile = s.tile;
   pa.flat = s.flat;
   for (int k = 0; k < 4; ++k) pa.wgt[k] = s.w[k];
+  pa.wdev = wdev;
   pa.csum = s.csum;
   pa.consp = s.consp;
   pa.S = s.S;

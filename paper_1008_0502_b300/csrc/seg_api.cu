@@ -70,7 +70,7 @@ extern "C" const char* seg_strerror(int code) {
   }
 }
 
-static int check_params(const seg_params* p, int H, int W) {
+int seg_check_params(const seg_params* p, int H, int W) {
   if (!p) return SEG_EINVAL;
   if (H < 1 || W < 1 || (long long)H * W > (1LL << 26)) return SEG_EINVAL;
   if (p->levels < 2 || p->levels > SEG_MAX_LEVELS) return SEG_EINVAL;
@@ -138,7 +138,7 @@ static int arena_layout(SalWS& sal, int B, int H, int W, const seg_params& p, Ar
 
 extern "C" int seg_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes) {
   if (!bytes) return SEG_EINVAL;
-  int rc = check_params(p, H, W);
+  int rc = seg_check_params(p, H, W);
   if (rc) return rc;
   if (B < 1 || (long long)B * H * W > (1LL << 26)) return SEG_EINVAL;
   SalWS sal;
@@ -156,7 +156,7 @@ extern "C" int seg_create(void* stream, int H, int W, const seg_params* p, seg_c
 extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg_ctx** out) {
   if (!out) return SEG_EINVAL;
   *out = nullptr;
-  int rc = check_params(p, H, W);
+  int rc = seg_check_params(p, H, W);
   if (rc) return rc;
   if (B < 1 || (long long)B * H * W > (1LL << 26)) return SEG_EINVAL;
   seg_ctx* c = (seg_ctx*)calloc(1, sizeof(seg_ctx));

@@ -106,6 +106,30 @@ __device__ __forceinline__ float seg_bilinear_t(const float* src, int ws, int2 r
   return (1.f - fy) * top + fy * bot;
 }
 
+// Order-preserving map from float to unsigned (so atomicMax works for any sign).
+__device__ __forceinline__ unsigned f2key(float x) {
+  unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Output rows (or columns) d of a bilinear up-sampling ns -> nd at which the
+// interpolant can peak: the first and last samples of every source cell (within
+// one cell the interpolant is bilinear, so its maximum over the cell's samples
+// lies on those rows and columns), plus both ends.
+__device__ __forceinline__ int seg_up_cell(int d, int ns, int nd) {
+  int i0, i1;
+  float f;
+  seg_src_coord(d, ns, nd, i0, i1, f);
+  return (i0 == i1) ? (i0 == 0 && d < nd / 2 ? -1 : ns) : i0;
+}
+__device__ __forceinline__ bool seg_up_candidate(int d, int ns, int nd) {
+  int id = seg_up_cell(d, ns, nd);
+  return d == 0 || d == nd - 1 || seg_up_cell(d - 1, ns, nd) != id || seg_up_cell(d + 1, ns, nd) != id;
+}
+
 __device__ __forceinline__ double seg_warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -148,6 +172,7 @@ struct SalWS {
   int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
   float* pyr[3][SEG_MAX_LEVELS];              // levels 1..L-1
   float* ori[SEG_MAX_ORIENT][SEG_MAX_LEVELS];  // levels c_min..s_max
+  float2* oc[SEG_MAX_ORIENT][SEG_MAX_LEVELS];  // complex Gabor responses (backward form only, else null)
   int npairs, nch, nmaps;                      // nch = 3 + no channels, nmaps = npairs * nch
   int pair_c[SEG_MAX_PAIRS], pair_s[SEG_MAX_PAIRS];
   unsigned* mm;  // [nmaps][2]: min and max as float bits (maps are >= 0)
@@ -155,6 +180,7 @@ struct SalWS {
   int nbands_total;
   float* nab;     // [frame][map][2]: N(.) as the affine map a*v + b
   float* acc[2];  // ping-pong channel accumulators at scale c (nch planes)
+  float* acc_final;  // the accumulator holding scale c_max (sigma_S): acc[(c_max - c_min) & 1]
   float* consp;   // 4 planes at sigma_S: N(C_I), N(C_RG), N(C_BY), N(C_O)
   float* csum;    // scratch plane at sigma_S
   float* S;       // combined map at sigma_S
@@ -300,12 +326,18 @@ struct seg_ctx {
 };
 
 // ---------------------------------------------------------------- launchers
-int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes);
+int seg_check_params(const seg_params* p, int H, int W);
+int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes, bool keep_complex = false);
 void sal_bind(SalWS& s, char* base);
 int sal_upload_tables(const SalWS& s);
 // upsample == false: stop at S and the saliency maximum (the prior kernel then
 // evaluates the saliency map itself); nullptr + c->io_mode: pointers from c->io
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample);
+// The saliency pipeline on a workspace: rgb is RGB8 (rgb_f32 = false) or float
+// RGB in [0, 255]; io supplies a null rgb / sal_out (RGB8 only); wdev, if set,
+// holds the four channel weights (double) on the device.
+int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegIO* io, const double* wdev,
+            float* sal_out, bool upsample);
 
 int pt_mom_blocks(int H, int W);
 int pt_launch_salmax(seg_ctx* c, const float* sal);

@@ -78,6 +78,11 @@ def _load():
         "seg_profile_enable": ([vp, i32], i32),
         "seg_profile_read": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, i32], i32),
         "seg_profile_read_ex": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, vp, i32], i32),
+        "seg_diff_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
+        "seg_diff_create": ([vp, i32, i32, i32, P(seg_params), P(vp)], i32),
+        "seg_diff_destroy": ([vp], i32),
+        "seg_diff_forward": ([vp, vp, vp, vp, i32, vp, vp], i32),
+        "seg_diff_backward": ([vp, vp, vp, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -352,3 +357,145 @@ def mincut_grid_static(cs, ct, ncap, max_cycles: int = 0, stream=None, mask=None
     if code not in (SEG_OK, SEG_ENOTCONVERGED, SEG_ETIMEOUT, SEG_ECAPACITY):
         raise SegError(code, "seg_mincut_grid_static")
     return mask, cut, code, cyc.value
+
+
+# ---------------------------------------------------------------- backward form
+def diff_workspace_bytes(B: int, H: int, W: int, params: seg_params) -> int:
+    n = C.c_size_t(0)
+    _check(lib.seg_diff_workspace_bytes(B, H, W, C.byref(params), C.byref(n)), "seg_diff_workspace_bytes")
+    return n.value
+
+
+def theta_from(params: seg_params, device=None) -> torch.Tensor:
+    """theta = (w_I, w_RG, w_BY, w_O, Q = sigma1^2, R = sigma2^2) of a params struct, float64 on the device."""
+    v = [float(params.w[k]) for k in range(4)] + [params.sigma1 ** 2, params.sigma2 ** 2]
+    return torch.tensor(v, dtype=torch.float64, device=device if device is not None else "cuda")
+
+
+class DiffContext:
+    """Backward-form context (seg_diff) for batches of B float frames of H x W:
+    saliency and Kalman-updated prior of clip times t0..t0+B-1, and their reverse
+    pass with respect to the frames and theta."""
+
+    def __init__(self, B: int, H: int, W: int, params: seg_params | None = None, device=None):
+        self.B, self.H, self.W = B, H, W
+        self.device = torch.device(device) if device is not None else torch.device("cuda",
+                                                                                   torch.cuda.current_device())
+        self.params = params if params is not None else default_params()
+        self.generation = 0  # counts forwards: the context holds the checkpoints of the last one
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(self.device)
+            h = C.c_void_p()
+            _check(lib.seg_diff_create(_stream_handle(self.stream), B, H, W, C.byref(self.params), C.byref(h)),
+                   "seg_diff_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.seg_diff_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _begin(self):
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        return cur
+
+    def _end(self, cur):
+        cur.wait_stream(self.stream)
+
+    def _args(self, rgb, theta, fmap):
+        B, H, W = self.B, self.H, self.W
+        r = _dev(rgb, torch.float32, (B, H, W, 3), "rgb")
+        th = _dev(theta, torch.float64, (6,), "theta")
+        f = _dev(fmap, torch.float32, (B, H, W), "fmap") if fmap is not None else None
+        return r, th, f
+
+    def forward(self, rgb, theta, fmap=None, t0: int = 0, saliency=None, prior=None):
+        B, H, W = self.B, self.H, self.W
+        r, th, f = self._args(rgb, theta, fmap)
+        if saliency is None:
+            saliency = torch.empty(B, H, W, dtype=torch.float32, device=self.device)
+        if prior is None:
+            prior = torch.empty(B, H, W, dtype=torch.float32, device=self.device)
+        cur = self._begin()
+        _check(lib.seg_diff_forward(self.handle, r, f, th, int(t0), _dev(saliency, torch.float32, (B, H, W), "sal"),
+                                    _dev(prior, torch.float32, (B, H, W), "prior")), "seg_diff_forward")
+        self._end(cur)
+        for t in (rgb, theta, fmap, saliency, prior):
+            if t is not None:
+                t.record_stream(self.stream)
+        self.generation += 1
+        return saliency, prior
+
+    def backward(self, rgb, theta, g_prior, g_sal=None, fmap=None, g_rgb=None, g_theta=None):
+        """Reverse pass of the last forward (same rgb, theta, fmap)."""
+        B, H, W = self.B, self.H, self.W
+        r, th, f = self._args(rgb, theta, fmap)
+        gp = _dev(g_prior, torch.float32, (B, H, W), "g_prior")
+        gs = _dev(g_sal, torch.float32, (B, H, W), "g_sal") if g_sal is not None else None
+        if g_rgb is None:
+            g_rgb = torch.empty(B, H, W, 3, dtype=torch.float32, device=self.device)
+        if g_theta is None:
+            g_theta = torch.empty(6, dtype=torch.float64, device=self.device)
+        cur = self._begin()
+        _check(lib.seg_diff_backward(self.handle, r, f, th, gp, gs, _dev(g_rgb, torch.float32, (B, H, W, 3), "g_rgb"),
+                                     _dev(g_theta, torch.float64, (6,), "g_theta")), "seg_diff_backward")
+        self._end(cur)
+        for t in (rgb, theta, fmap, g_prior, g_sal, g_rgb, g_theta):
+            if t is not None:
+                t.record_stream(self.stream)
+        return g_rgb, g_theta
+
+
+class SaliencyFn(torch.autograd.Function):
+    """(saliency, prior) = f(rgb, theta) as a torch.autograd.Function over a DiffContext.
+
+    rgb: (B, H, W, 3) float32 frames at clip times t0..t0+B-1; theta: (6,) float64
+    (w_I, w_RG, w_BY, w_O, Q, R); fmap: (B, H, W) float32 smoothed previous masks or
+    None (a constant).  If the context ran another forward before this backward,
+    the backward first recomputes this forward's checkpoints."""
+
+    @staticmethod
+    def forward(ctx, rgb, theta, fmap, t0, dctx):
+        rgb, theta = rgb.contiguous(), theta.contiguous()
+        fmap = fmap.contiguous() if fmap is not None else None
+        sal, prior = dctx.forward(rgb, theta, fmap, t0)
+        ctx.dctx, ctx.generation, ctx.t0, ctx.has_fmap = dctx, dctx.generation, t0, fmap is not None
+        ctx.save_for_backward(rgb, theta, fmap if fmap is not None else rgb.new_empty(0))
+        return sal, prior
+
+    @staticmethod
+    def backward(ctx, g_sal, g_prior):
+        rgb, theta, fmap = ctx.saved_tensors
+        fmap = fmap if ctx.has_fmap else None
+        d = ctx.dctx
+        if d.generation != ctx.generation:
+            d.forward(rgb, theta, fmap, ctx.t0)
+            ctx.generation = d.generation
+        if g_prior is None:
+            g_prior = torch.zeros(d.B, d.H, d.W, dtype=torch.float32, device=d.device)
+        g_rgb, g_theta = d.backward(rgb, theta, g_prior.contiguous(),
+                                    g_sal.contiguous() if g_sal is not None else None, fmap)
+        return (g_rgb if ctx.needs_input_grad[0] else None, g_theta if ctx.needs_input_grad[1] else None,
+                None, None, None)
+
+
+_diff_cache: dict = {}
+
+
+def saliency_prior(rgb, theta, fmap=None, t0: int = 0, params: seg_params | None = None):
+    """Differentiable saliency and prior of a clip batch (see SaliencyFn).  Contexts
+    are cached per (B, H, W, device, params)."""
+    B, H, W = int(rgb.shape[0]), int(rgb.shape[1]), int(rgb.shape[2])
+    p = params if params is not None else default_params()
+    key = (B, H, W, str(rgb.device), bytes(p))
+    d = _diff_cache.get(key)
+    if d is None:
+        d = _diff_cache[key] = DiffContext(B, H, W, p, device=rgb.device)
+    return SaliencyFn.apply(rgb, theta, fmap, t0, d)
