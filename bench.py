@@ -57,7 +57,7 @@ def args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the batched-context measurements")
-    ap.add_argument("--only", choices=["saliency_b32"], default=None,
+    ap.add_argument("--only", choices=["saliency_b32", "diff_b32"], default=None,
                     help="run one sub-measurement alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -219,6 +219,20 @@ def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
                    "status": sg3.sync()[0]}
     sg3.close()
 
+    # the backward form (differentiation of saliency and Kalman prior): a 32-frame 640x480
+    # clip, forward + hand-written reverse pass
+    d, fwd, bwd, byts = diff_setup(seg, torch, clip_dev)
+    reps = 10
+    tf = timed(fwd, reps)
+    tfb = timed(lambda: (fwd(), bwd()), reps)
+    tb = tfb - tf
+    out["diff_b32"] = {"frames": "32 x 640x480 float, forward + backward (frames, w, Q, R)",
+                       "frames_per_s": 32 * reps / tfb, "ms_forward": tf / reps * 1e3,
+                       "ms_backward": tb / reps * 1e3,
+                       "backward_achieved_GBps": byts["bwd"] * reps / tb / 1e9,
+                       "backward_frac_of_hbm": byts["bwd"] * reps / tb / 1e9 / hbm}
+    d.close()
+
     # the mixed 64-stream workload: one batch context per resolution, each on its own CUDA stream
     groups = [(24, 240, 320), (24, 480, 640), (16, 720, 1280)]
     nfr = 4
@@ -335,11 +349,53 @@ def run_reference(a):
     }))
 
 
+def diff_setup(seg, torch, clip_dev, B=32):
+    """The backward form on a clip batch: B float frames of 640x480 (clip times 0..B-1),
+    smoothed previous masks, cotangents on both outputs."""
+    p = seg.params_from(VGA)
+    d = seg.DiffContext(B, H, W, p)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.stack([clip_dev[k % clip_dev.shape[0]] for k in range(B)]).float()
+    x += torch.rand(x.shape, generator=g, device="cuda") - 0.5
+    fmap = torch.rand(B, H, W, generator=g, device="cuda")
+    gp = torch.randn(B, H, W, generator=g, device="cuda")
+    gs = torch.randn(B, H, W, generator=g, device="cuda")
+    theta = seg.theta_from(p)
+    outs = [torch.empty(B, H, W, device="cuda") for _ in range(2)]
+    g_rgb = torch.empty(B, H, W, 3, device="cuda")
+    g_th = torch.empty(6, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        d.forward(x, theta, fmap, 0, *outs)
+
+    def bwd():
+        d.backward(x, theta, gp, gs, fmap, g_rgb, g_th)
+
+    # minimal traffic per pixel: forward rgb 12 B + fmap 4 B in, saliency and prior 8 B
+    # out; backward rgb 12 B + fmap 4 B + two cotangents 8 B in, dL/drgb 12 B out
+    return d, fwd, bwd, {"fwd": 24 * B * H * W, "bwd": 36 * B * H * W}
+
+
 def run_only(a):
     import torch
     from paper_1008_0502_b300 import seg
     pk, _ = peaks()
     clip_dev = torch.from_numpy(make_clip(40)).cuda()
+    if a.only == "diff_b32":
+        d, fwd, bwd, byts = diff_setup(seg, torch, clip_dev)
+        for _ in range(a.warmup):
+            fwd()
+            bwd()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            fwd()
+            bwd()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        print(json.dumps({"only": a.only, "ms_per_fwd_bwd": t / a.steps * 1e3, "frames_per_s": 32 * a.steps / t}))
+        d.close()
+        return
     B = 32
     sgs = seg.Segmenter(H, W, seg.params_from(VGA), batch=B)
     fr32 = torch.stack([clip_dev[k] for k in range(B)])

@@ -23,8 +23,9 @@
 //                  up-sampling along x; partial sums of dL/dw_f and of the
 //                  saliency-maximum term
 //   k_db_top       one CTA per frame at sigma_S: transposed up-sampling along y,
-//                  the maximum's term, dL/dw, dL/dQ, dL/dR, then N(.)^T of the four
-//                  conspicuity maps and of the orientation accumulators
+//                  the maximum's term, dL/dw, dL/dQ, dL/dR
+//   k_db_nbwd      N(.)^T of the four conspicuity maps, then of the orientation
+//                  accumulators (one CTA per map and frame)
 //   k_db_reduceT   transposed REDUCE (across-scale sums, then the pyramid)
 //   k_db_cs_stats  per center-surround map: N(.) statistics of the recomputed map
 //                  and the reductions its derivative needs
@@ -51,8 +52,14 @@ typedef unsigned long long u64;
 #define DB_TX 32
 #define DB_TY 16
 #define GB_MAXR_T 8  // largest Gabor radius (taps <= 17)
+#define SURT_CAP 8192  // floats of the row-transposed surround field staged per chunk
 
 __constant__ float c_kb[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+
+struct DiffPart {  // N(.) statistics of one band of T rows of a center-surround map
+  u64 kmin, kmax;
+  double sg, sgv, st;
+};
 
 struct DiffCoef {
   float aG, at, smin, smax;  // dN^T: aG g_i + at [i tile argmax] + smin [i = argmin] + smax [i = argmax]
@@ -74,6 +81,7 @@ struct seg_diff {
   float* gC3;   // [B][nS]
   float* G[SEG_MAX_LEVELS];  // scales c_min..c_max: [B][nch][hl*wl]
   DiffCoef* coef;            // [B][nmaps]
+  DiffPart* dpart;           // [B][bands of all center-surround maps]
   int* targ;                 // [B][ntarg]
   int ntarg;
   int targ_off[SEG_MAX_PAIRS];
@@ -86,6 +94,9 @@ struct seg_diff {
   size_t grad_bytes;
   double* gpar;  // [B][6]
   int2* rsT;     // transposed resampling ranges {first, last + 1}
+  int* rt_lo;    // transposed REDUCE tables, per level l -> l+1: rows then columns
+  float4* rt_w;
+  int rt_row[SEG_MAX_LEVELS], rt_col[SEG_MAX_LEVELS], rt_n;
   int rsT_row[SEG_MAX_PAIRS], rsT_col[SEG_MAX_PAIRS], rsT_frow, rsT_fcol, rsT_n;
   int forward_done;
 };
@@ -117,15 +128,23 @@ __device__ __forceinline__ u64 warp_max_u64(u64 v) {
 }
 
 // Block-wide reductions (every thread gets the result).  red must hold 32
-// entries of the reduced type; the call ends with a barrier.
-__device__ double block_sum_d(double v, double* red) {
-  v = seg_warp_sum_d(v);
+// entries of the reduced type; the call ends with a barrier.  Sums take one float
+// per thread (each thread's share is a few terms): float within a warp, the warp
+// partials added in double by one thread -- the FP64 pipe of this part is narrow.
+__device__ double block_sum_d(float v, double* red) {
+  v = seg_warp_sum_f(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();
-  if (lane == 0) red[wid] = v;
+  float* rf = (float*)(red + 1);  // 31 doubles of room: 62 floats >= 32 warps
+  if (lane == 0) rf[wid] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < nw; ++w) t += red[w];  // fixed order: deterministic
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += rf[w];  // fixed order: deterministic
+    red[0] = t;
+  }
+  __syncthreads();
+  const double t = red[0];
   __syncthreads();
   return t;
 }
@@ -202,12 +221,13 @@ __global__ void k_df_kalman(const double* __restrict__ theta, int t0, int B, dou
     double w = 0, wq = 0, wr = 0, Pn = Q, Pq = 1, Pr = 0;
     if (t > 0) {
       const double den = Q + R + P, dq = 1 + dPq, dr = 1 + dPr, num = Q * (R + P);
-      w = Q / den;
-      wq = (den - Q * dq) / (den * den);
-      wr = -Q * dr / (den * den);
-      Pn = num / den;
-      Pq = ((R + P + Q * dPq) * den - num * dq) / (den * den);
-      Pr = (Q * dr * den - num * dr) / (den * den);
+      const double inv = 1.0 / den, inv2 = inv * inv;  // one division per step
+      w = Q * inv;
+      wq = (den - Q * dq) * inv2;
+      wr = -Q * dr * inv2;
+      Pn = num * inv;
+      Pq = ((R + P + Q * dPq) * den - num * dq) * inv2;
+      Pr = (Q * dr * den - num * dr) * inv2;
     }
     if (t >= t0) {
       kal[3 * (t - t0)] = w;
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(256) k_db_rows(const float* __restrict__ S, in
   const float mx = __uint_as_float(salmax[b]);
   const float wf = (float)kal[3 * b];
   const float* Sb = S + (size_t)b * hs * ws;
-  double a_wf = 0.0, a_m = 0.0;
+  float a_wf = 0.f, a_m = 0.f;  // a few pixels per thread; the block sums are double
   for (int k = threadIdx.x; k < DB_RB * W; k += blockDim.x) {
     const int r = k / W, x = k - r * W, y = Y0 + r;
     if (y >= H) continue;
@@ -270,12 +290,12 @@ __global__ void __launch_bounds__(256) k_db_rows(const float* __restrict__ S, in
     const float q = edge ? eps : (mx > 0.f ? v / mx : 0.f);
     const float gp = g_prior[i];
     const float f = fmap ? fmap[i] : 0.f;
-    a_wf += (double)gp * (double)(f - q);
+    a_wf += gp * (f - q);
     float gs = g_sal ? g_sal[i] : 0.f;
     if (!edge && mx > 0.f) {
       const float gq = gp * (1.f - wf);
       gs += gq / mx;
-      a_m += (double)gq * v;
+      a_m += gq * v;
     }
     sg[r * W + x] = gs;
   }
@@ -296,11 +316,10 @@ __global__ void __launch_bounds__(256) k_db_rows(const float* __restrict__ S, in
     }
     Tx[((size_t)b * H + y) * ws + X] = acc;
   }
-  a_wf = block_sum_d(a_wf, red);
-  a_m = block_sum_d(a_m, red);
+  const double s_wf = block_sum_d(a_wf, red), s_m = block_sum_d(a_m, red);
   if (threadIdx.x == 0) {
-    part[2 * ((size_t)b * gridDim.x + blockIdx.x)] = a_wf;
-    part[2 * ((size_t)b * gridDim.x + blockIdx.x) + 1] = a_m;
+    part[2 * ((size_t)b * gridDim.x + blockIdx.x)] = s_wf;
+    part[2 * ((size_t)b * gridDim.x + blockIdx.x) + 1] = s_m;
   }
 }
 
@@ -312,7 +331,7 @@ __device__ void block_norm_bwd(const float* v, const float* g, float scale, floa
   for (int t = threadIdx.x; t < nt; t += blockDim.x) tk[t] = 0ull;
   __syncthreads();
   u64 kmin = ~0ull, kmax = 0ull;
-  double sg = 0.0, sgv = 0.0;
+  float sg = 0.f, sgv = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float x = v[i], gi = scale * g[i];
     const int yy = i / w, xx = i - yy * w;
@@ -321,16 +340,15 @@ __device__ void block_norm_bwd(const float* v, const float* g, float scale, floa
     kmax = kx > kmax ? kx : kmax;
     atomicMax(&tk[(yy / T) * ntx + xx / T], kx);
     sg += gi;
-    sgv += (double)gi * x;
+    sgv += gi * x;
   }
   kmin = block_min_u64(kmin, redk);
   kmax = block_max_u64(kmax, redk);
-  sg = block_sum_d(sg, redd);
-  sgv = block_sum_d(sgv, redd);
-  double st = 0.0;
+  const double sgd = block_sum_d(sg, redd), sgvd = block_sum_d(sgv, redd);
+  float st = 0.f;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) st += key_val(tk[t]);
-  st = block_sum_d(st, redd);
-  const DiffCoef c = norm_coef(kmin, kmax, st, nt, sg, sgv, flat);
+  const double std_ = block_sum_d(st, redd);
+  const DiffCoef c = norm_coef(kmin, kmax, std_, nt, sgd, sgvd, flat);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int yy = i / w, xx = i - yy * w;
     out[i] = coef_apply(c, scale * g[i], i, key_max_idx(tk[(yy / T) * ntx + xx / T]));
@@ -362,7 +380,6 @@ struct TopArgs {
 
 // One CTA per frame, at sigma_S.
 __global__ void __launch_bounds__(1024) k_db_top(TopArgs a) {
-  __shared__ u64 tk[DB_MAXT_S];
   __shared__ double redd[32];
   __shared__ u64 redk[32];
   __shared__ int crow[2048], ccol[2048];
@@ -372,13 +389,18 @@ __global__ void __launch_bounds__(1024) k_db_top(TopArgs a) {
   const float* Sb = a.S + (size_t)b * nS;
   float* gS = a.gS + (size_t)b * nS;
   // sums of the row partials (fixed order)
-  double gwf = 0.0, gmq = 0.0;
-  for (int k = threadIdx.x; k < a.nbx; k += blockDim.x) {
-    gwf += a.part[2 * ((size_t)b * a.nbx + k)];
-    gmq += a.part[2 * ((size_t)b * a.nbx + k) + 1];
+  if (threadIdx.x == 0) {  // row partials in order (one thread: deterministic)
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < a.nbx; ++k) {
+      s0 += a.part[2 * ((size_t)b * a.nbx + k)];
+      s1 += a.part[2 * ((size_t)b * a.nbx + k) + 1];
+    }
+    redd[0] = s0;
+    redd[1] = s1;
   }
-  gwf = block_sum_d(gwf, redd);
-  gmq = block_sum_d(gmq, redd);
+  __syncthreads();
+  const double gwf = redd[0], gmq = redd[1];
+  __syncthreads();
   // transposed up-sampling along y
   const float* Tx = a.Tx + (size_t)b * a.H * a.ws;
   for (int k = threadIdx.x; k < nS; k += blockDim.x) {
@@ -428,28 +450,37 @@ __global__ void __launch_bounds__(1024) k_db_top(TopArgs a) {
   // dL/dw_k = <gS, N(C_k)>; dL/dQ, dL/dR through w_f(t)
   const float* consp = a.consp + (size_t)b * 4 * nS;
   for (int k = 0; k < 4; ++k) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nS; i += blockDim.x) s += (double)gS[i] * consp[(size_t)k * nS + i];
-    s = block_sum_d(s, redd);
+    float sf = 0.f;
+    for (int i = threadIdx.x; i < nS; i += blockDim.x) sf += gS[i] * consp[(size_t)k * nS + i];
+    const double s = block_sum_d(sf, redd);
     if (threadIdx.x == 0) a.gpar[6 * b + k] = s;
   }
   if (threadIdx.x == 0) {
     a.gpar[6 * b + 4] = gwf * a.kal[3 * b + 1];
     a.gpar[6 * b + 5] = gwf * a.kal[3 * b + 2];
   }
-  // S = sum_k w_k N(C_k): C_I, C_RG, C_BY are the accumulators, C_O = csum
+}
+
+// N(.)^T at sigma_S, one CTA per (map, frame).  stage 0: S = sum_k w_k N(C_k)
+// with C_I, C_RG, C_BY the accumulators and C_O = csum (map k = blockIdx.x);
+// stage 1: C_O = sum_theta N(accumulator_theta) (theta = blockIdx.x).
+__global__ void __launch_bounds__(512) k_db_nbwd(TopArgs a, int stage) {
+  __shared__ u64 tk[DB_MAXT_S];
+  __shared__ double redd[32];
+  __shared__ u64 redk[32];
+  const int b = blockIdx.y, nS = a.hs * a.ws, k = blockIdx.x;
   const float* acc = a.acc + (size_t)b * a.nch * nS;
   float* gacc = a.gacc + (size_t)b * a.nch * nS;
   float* gC3 = a.gC3 + (size_t)b * nS;
-  for (int k = 0; k < 4; ++k) {
+  if (stage == 0) {
     const float* v = k < 3 ? acc + (size_t)k * nS : a.csum + (size_t)b * nS;
     float* out = k < 3 ? gacc + (size_t)k * nS : gC3;
-    block_norm_bwd(v, gS, (float)a.theta[k], out, a.hs, a.ws, a.tile, a.flat, tk, redd, redk);
-  }
-  // C_O = sum_theta N(accumulator_theta)
-  for (int f = 3; f < a.nch; ++f)
+    block_norm_bwd(v, a.gS + (size_t)b * nS, (float)a.theta[k], out, a.hs, a.ws, a.tile, a.flat, tk, redd, redk);
+  } else {
+    const int f = 3 + k;
     block_norm_bwd(acc + (size_t)f * nS, gC3, 1.f, gacc + (size_t)f * nS, a.hs, a.ws, a.tile, a.flat, tk, redd,
                    redk);
+  }
 }
 
 // Transposed REDUCE (5x5 binomial, clamp-to-edge, even samples): out (+)= R^T in,
@@ -459,40 +490,36 @@ struct RTArgs {
   const float* in[3];
   float* out[3];
   int K, h, w, h2, w2, accumulate;
+  const int* lo_y;  // per output row: first level-(l+1) row reaching it
+  const float4* w_y;  // its four weights (0 past the level)
+  const int* lo_x;
+  const float4* w_x;
 };
 
-__device__ __forceinline__ int rt_weights(int y, int h, int h2, int* Ys, float* ws) {
-  int n = 0;
-  const int lo = max(0, y / 2 - 1), hi = min(h2 - 1, (y + 3) / 2);
-  for (int Y = lo; Y <= hi; ++Y) {
-    float w = 0.f;
+// sum_{j,i < 4} wy[j] wx[i] in[lo_y + j][lo_x + i] (zero-weight taps past the
+// level are read at a clamped address)
+__device__ __forceinline__ float rt_apply(const float* in, int w2, int h2, int ylo, float4 wy, int xlo, float4 wx) {
+  const float wya[4] = {wy.x, wy.y, wy.z, wy.w}, wxa[4] = {wx.x, wx.y, wx.z, wx.w};
+  int xs[4];
 #pragma unroll
-    for (int t = -2; t <= 2; ++t)
-      if (seg_clampi(2 * Y + t, 0, h - 1) == y) w += c_kb[t + 2];
-    if (w != 0.f) {
-      Ys[n] = Y;
-      ws[n] = w;
-      ++n;
-    }
+  for (int i = 0; i < 4; ++i) xs[i] = min(xlo + i, w2 - 1);
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float* row = in + (size_t)min(ylo + j, h2 - 1) * w2;
+    acc += wya[j] * (wxa[0] * row[xs[0]] + wxa[1] * row[xs[1]] + wxa[2] * row[xs[2]] + wxa[3] * row[xs[3]]);
   }
-  return n;
+  return acc;
 }
 
 __global__ void __launch_bounds__(256) k_db_reduceT(RTArgs a) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= a.w || y >= a.h) return;
   const int slot = blockIdx.z % a.K, pl = blockIdx.z / a.K;
-  const float* in = a.in[slot] + (size_t)pl * a.h2 * a.w2;
-  float* out = a.out[slot] + (size_t)pl * a.h * a.w;
-  int Ys[4], Xs[4];
-  float wy[4], wx[4];
-  const int ny = rt_weights(y, a.h, a.h2, Ys, wy), nx = rt_weights(x, a.w, a.w2, Xs, wx);
-  float acc = 0.f;
-  for (int j = 0; j < ny; ++j) {
-    float r = 0.f;
-    for (int i = 0; i < nx; ++i) r += wx[i] * in[(size_t)Ys[j] * a.w2 + Xs[i]];
-    acc += wy[j] * r;
-  }
+  // (select the slot without indexing the parameter arrays at run time)
+  const float* in = (slot == 0 ? a.in[0] : slot == 1 ? a.in[1] : a.in[2]) + (size_t)pl * a.h2 * a.w2;
+  float* out = (slot == 0 ? a.out[0] : slot == 1 ? a.out[1] : a.out[2]) + (size_t)pl * a.h * a.w;
+  const float acc = rt_apply(in, a.w2, a.h2, a.lo_y[y], a.w_y[y], a.lo_x[x], a.w_x[x]);
   const size_t o = (size_t)y * a.w + x;
   out[o] = a.accumulate ? out[o] + acc : acc;
 }
@@ -517,6 +544,10 @@ struct DCSArgs {
   float* hsur;
   size_t nhsur;
   size_t hsur_off[SEG_MAX_PAIRS];
+  int slist[SEG_MAX_LEVELS], nsl;  // distinct surround scales
+  int band_off[SEG_MAX_PAIRS + 1];  // prefix of (channels x bands of T rows) per pair
+  int nbands_total;
+  DiffPart* dpart;  // [B][nbands_total]
 };
 
 __device__ __forceinline__ float cs_signed(const DCSArgs& a, int p, int f, int b, int y, int x) {
@@ -527,40 +558,78 @@ __device__ __forceinline__ float cs_signed(const DCSArgs& a, int p, int f, int b
   return (a.opp_sum && (f == 1 || f == 2)) ? v0 + u : v0 - u;
 }
 
-// One CTA per (map, frame): N(.) statistics of the recomputed map |a| and the
-// reductions of its incoming derivative.
-__global__ void __launch_bounds__(512) k_db_cs_stats(DCSArgs a) {
-  __shared__ u64 tk[DB_MAXT];
+// One CTA per (band of T rows of a center-surround map, frame): the N(.)
+// statistics of the recomputed map |a| over the band and the reductions of its
+// incoming derivative; warps take the band's T x T tiles in turn and reduce
+// each tile's maximum (value, first index) with shuffles.
+__global__ void __launch_bounds__(256) k_db_cs_stats(DCSArgs a) {
   __shared__ double redd[32];
   __shared__ u64 redk[32];
-  const int m = blockIdx.x, b = blockIdx.y, p = m / a.nch, f = m - p * a.nch;
-  const int c = a.pair_c[p], hc = a.hl[c], wc = a.wl[c], n = hc * wc, T = a.tile;
-  const int ntx = (wc + T - 1) / T, nt = ntx * ((hc + T - 1) / T);
-  const float* G = a.G[c] + ((size_t)b * a.nch + f) * n;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) tk[t] = 0ull;
-  __syncthreads();
+  int bx = blockIdx.x, p = 0;
+  while (p < a.npairs - 1 && bx >= a.band_off[p + 1]) ++p;
+  const int b = blockIdx.y, c = a.pair_c[p], hc = a.hl[c], wc = a.wl[c], T = a.tile;
+  const int nb = (hc + T - 1) / T, ntx = (wc + T - 1) / T, nt = ntx * nb;
+  const int rem = bx - a.band_off[p], f = rem / nb, band = rem - f * nb;
+  const float* G = a.G[c] + ((size_t)b * a.nch + f) * hc * wc;
+  int* targ = a.targ + (size_t)b * a.ntarg + a.targ_off[p] + (size_t)f * nt;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int y0 = band * T, rows = min(T, hc - y0);
   u64 kmin = ~0ull, kmax = 0ull;
-  double sg = 0.0, sgv = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int y = i / wc, x = i - y * wc;
-    const float v = fabsf(cs_signed(a, p, f, b, y, x)), g = G[i];
-    const u64 kx = key_max(v, i), kn = key_min(v, i);
-    kmin = kn < kmin ? kn : kmin;
-    kmax = kx > kmax ? kx : kmax;
-    atomicMax(&tk[(y / T) * ntx + x / T], kx);
-    sg += g;
-    sgv += (double)g * v;
+  float sg = 0.f, sgv = 0.f, st = 0.f;
+  for (int tx = wid; tx < ntx; tx += nw) {
+    const int x0 = tx * T, cols = min(T, wc - x0);
+    u64 kt = 0ull;
+    float sgt = 0.f, sgvt = 0.f;
+    for (int k = lane; k < rows * cols; k += 32) {
+      const int yy = k / cols, y = y0 + yy, x = x0 + (k - yy * cols), i = y * wc + x;
+      const float v = fabsf(cs_signed(a, p, f, b, y, x)), g = G[i];
+      const u64 kn = key_min(v, i), kx = key_max(v, i);
+      kmin = kn < kmin ? kn : kmin;
+      kt = kx > kt ? kx : kt;
+      sgt += g;
+      sgvt += g * v;
+    }
+    sg += sgt;
+    sgv += sgvt;
+    kt = warp_max_u64(kt);
+    kmax = kt > kmax ? kt : kmax;
+    if (lane == 0) {
+      targ[band * ntx + tx] = key_max_idx(kt);
+      st += key_val(kt);
+    }
   }
   kmin = block_min_u64(kmin, redk);
   kmax = block_max_u64(kmax, redk);
-  sg = block_sum_d(sg, redd);
-  sgv = block_sum_d(sgv, redd);
-  double st = 0.0;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) st += key_val(tk[t]);
-  st = block_sum_d(st, redd);
-  if (threadIdx.x == 0) a.coef[(size_t)b * a.nmaps + m] = norm_coef(kmin, kmax, st, nt, sg, sgv, a.flat);
-  int* targ = a.targ + (size_t)b * a.ntarg + a.targ_off[p] + (size_t)f * nt;
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) targ[t] = key_max_idx(tk[t]);
+  const double sgd = block_sum_d(sg, redd), sgvd = block_sum_d(sgv, redd), std_ = block_sum_d(st, redd);
+  if (threadIdx.x == 0) {
+    DiffPart q;
+    q.kmin = kmin;
+    q.kmax = kmax;
+    q.sg = sgd;
+    q.sgv = sgvd;
+    q.st = std_;
+    a.dpart[(size_t)b * a.nbands_total + bx] = q;
+  }
+}
+
+// N(.)^T coefficients of every center-surround map from its band statistics
+// (bands summed in order: deterministic).
+__global__ void k_db_cs_coef(DCSArgs a, int B) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.nmaps * B) return;
+  const int b = j / a.nmaps, m = j - b * a.nmaps, p = m / a.nch, f = m - p * a.nch;
+  const int c = a.pair_c[p], T = a.tile, nb = (a.hl[c] + T - 1) / T, nt = nb * ((a.wl[c] + T - 1) / T);
+  const DiffPart* q = a.dpart + (size_t)b * a.nbands_total + a.band_off[p] + f * nb;
+  u64 kmin = ~0ull, kmax = 0ull;
+  double sg = 0.0, sgv = 0.0, st = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    kmin = q[i].kmin < kmin ? q[i].kmin : kmin;
+    kmax = q[i].kmax > kmax ? q[i].kmax : kmax;
+    sg += q[i].sg;
+    sgv += q[i].sgv;
+    st += q[i].st;
+  }
+  a.coef[(size_t)b * a.nmaps + m] = norm_coef(kmin, kmax, st, nt, sg, sgv, a.flat);
 }
 
 // dL/dmap per pixel of scale c: the center level receives sign(a) times it, the
@@ -589,41 +658,62 @@ __global__ void __launch_bounds__(256) k_db_cs_apply(DCSArgs a, int c) {
   *gx += gsum;
 }
 
-// Transposed bilinear up-sampling of the surround fields of every pair whose
-// surround scale is s.
-__global__ void __launch_bounds__(256) k_db_surT(DCSArgs a, int s) {
-  const int X = blockIdx.x * 32 + (threadIdx.x & 31), Y = blockIdx.y * 8 + (threadIdx.x >> 5);
+// Transposed bilinear up-sampling of the surround fields, one CTA per (surround
+// scale s, channel f, frame b), over every pair whose surround scale is s:
+// separably, T1[y][X] = sum_x wx(x, X) h[y][x] for the rows y a chunk of output
+// rows needs (shared memory), then out[Y][X] += sum_y wy(y, Y) T1[y][X].
+__global__ void __launch_bounds__(256) k_db_surT(DCSArgs a) {
+  __shared__ float sT[SURT_CAP];
+  const int s = a.slist[blockIdx.x], f = blockIdx.y, b = blockIdx.z;
   const int hs = a.hl[s], ws = a.wl[s];
-  if (X >= ws || Y >= hs) return;
-  const int f = blockIdx.z % a.nch, b = blockIdx.z / a.nch;
-  float acc = 0.f;
+  float* gx = a.GX[f][s] + (size_t)b * hs * ws;
   for (int p = 0; p < a.npairs; ++p) {
     if (a.pair_s[p] != s) continue;
-    const int c = a.pair_c[p], wc = a.wl[c], n = a.hl[c] * wc;
-    const float* h = a.hsur + (size_t)b * a.nhsur + a.hsur_off[p] + (size_t)f * n;
-    const int2 ry = a.rsT[a.rsT_row[p] + Y], rx = a.rsT[a.rsT_col[p] + X];
+    const int c = a.pair_c[p], hc = a.hl[c], wc = a.wl[c];
+    const float* h = a.hsur + (size_t)b * a.nhsur + a.hsur_off[p] + (size_t)f * hc * wc;
+    const int2* rT = a.rsT + a.rsT_row[p];
+    const int2* cT = a.rsT + a.rsT_col[p];
     const int2* trow = a.rs + a.rs_row[p];
     const int2* tcol = a.rs + a.rs_col[p];
-    for (int y = ry.x; y < ry.y; ++y) {
-      const int2 ey = trow[y];
-      const float fy = __int_as_float(ey.y);
-      float wy = 0.f;
-      if ((ey.x & 0xffff) == Y) wy += 1.f - fy;
-      if ((ey.x >> 16) == Y) wy += fy;
-      float r = 0.f;
-      for (int x = rx.x; x < rx.y; ++x) {
-        const int2 ex = tcol[x];
-        const float fx = __int_as_float(ex.y);
-        float wx = 0.f;
-        if ((ex.x & 0xffff) == X) wx += 1.f - fx;
-        if ((ex.x >> 16) == X) wx += fx;
-        r += wx * h[(size_t)y * wc + x];
+    for (int Y0 = 0; Y0 < hs;) {
+      const int ya = rT[Y0].x;
+      int Y1 = Y0 + 1;
+      while (Y1 < hs && (rT[Y1].y - ya) * ws <= SURT_CAP) ++Y1;
+      const int yb = max(ya, rT[Y1 - 1].y);
+      for (int k = threadIdx.x; k < (yb - ya) * ws; k += blockDim.x) {
+        const int y = ya + k / ws, X = k % ws;
+        const int2 rg = cT[X];
+        const float* row = h + (size_t)y * wc;
+        float r = 0.f;
+        for (int x = rg.x; x < rg.y; ++x) {
+          const int2 ex = tcol[x];
+          const float fx = __int_as_float(ex.y);
+          float wx = 0.f;
+          if ((ex.x & 0xffff) == X) wx += 1.f - fx;
+          if ((ex.x >> 16) == X) wx += fx;
+          r += wx * row[x];
+        }
+        sT[k] = r;
       }
-      acc += wy * r;
+      __syncthreads();
+      for (int k = threadIdx.x; k < (Y1 - Y0) * ws; k += blockDim.x) {
+        const int Y = Y0 + k / ws, X = k % ws;
+        const int2 rg = rT[Y];
+        float acc = 0.f;
+        for (int y = rg.x; y < rg.y; ++y) {
+          const int2 ey = trow[y];
+          const float fy = __int_as_float(ey.y);
+          float wy = 0.f;
+          if ((ey.x & 0xffff) == Y) wy += 1.f - fy;
+          if ((ey.x >> 16) == Y) wy += fy;
+          acc += wy * sT[(y - ya) * ws + X];
+        }
+        gx[(size_t)Y * ws + X] += acc;
+      }
+      __syncthreads();
+      Y0 = Y1;
     }
   }
-  float* gx = a.GX[f][s] + (size_t)b * hs * ws + (size_t)Y * ws + X;
-  *gx += acc;
 }
 
 // Weight of input sample x in output X of the transposed clamped correlation
@@ -713,13 +803,26 @@ __global__ void __launch_bounds__(256) k_db_gaborT(GTArgs a, GaborTaps t) {
     for (int i = threadIdx.x; i < iny * DB_TX; i += blockDim.x) {
       const int ry = i / DB_TX, lx = i - ry * DB_TX, X = X0 + lx;
       float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-      if (X < w) {
+      if (X > 0 && X < w - 1) {
+        // interior output: plain correlation with the reversed taps (samples
+        // outside the level are staged as zeros)
+        const float* pr = &sGr[ry][lx + R];
+        const float* pi = &sGi[ry][lx + R];
+        for (int u = -R; u <= R; ++u) {
+          const float whr = t.hx_re[k][u + R], whi = t.hx_im[k][u + R], w0 = t.g0[u + R];
+          const float gr = pr[-u], gi = pi[-u];
+          ar += whr * gr + whi * gi;  // (whr + i whi)(gr - i gi)
+          ai += whi * gr - whr * gi;
+          br += w0 * gr;
+          bi += w0 * gi;
+        }
+      } else if (X < w) {
         const int xlo = max(0, X - R), xhi = min(w - 1, X + R);
         for (int x = xlo; x <= xhi; ++x) {
           const float whr = tap_T(t.hx_re[k], chr, R, w, X, x), whi = tap_T(t.hx_im[k], chi, R, w, X, x);
           const float w0 = tap_T(t.g0, cg0, R, w, X, x);
           const float gr = sGr[ry][x - X0 + R], gi = sGi[ry][x - X0 + R];
-          ar += whr * gr + whi * gi;  // (whr + i whi)(gr - i gi)
+          ar += whr * gr + whi * gi;
           ai += whi * gr - whr * gi;
           br += w0 * gr;
           bi += w0 * gi;
@@ -736,13 +839,23 @@ __global__ void __launch_bounds__(256) k_db_gaborT(GTArgs a, GaborTaps t) {
     for (int j = 0; j < 2; ++j) {
       const int Y = Y0 + ty + 8 * j, X = X0 + tx;
       if (Y >= h || X >= w) continue;
-      const int ylo = max(0, Y - R), yhi = min(h - 1, Y + R);
       float acc = 0.f;
-      for (int y = ylo; y <= yhi; ++y) {
-        const int ry = y - Y0 + R;
-        const float wvr = tap_T(t.vy_re[k], cvr, R, h, Y, y), wvi = tap_T(t.vy_im[k], cvi, R, h, Y, y);
-        const float w0 = tap_T(t.g0, cg0, R, h, Y, y);
-        acc += wvr * sAr[ry][tx] - wvi * sAi[ry][tx] - w0 * (kr * sBr[ry][tx] + ki * sBi[ry][tx]);
+      if (Y > 0 && Y < h - 1) {
+        // rows outside the level hold zeros (staged as zero gradients)
+        const int ry0 = Y - Y0 + R;
+        for (int v = -R; v <= R; ++v) {
+          const int ry = ry0 - v;
+          acc += t.vy_re[k][v + R] * sAr[ry][tx] - t.vy_im[k][v + R] * sAi[ry][tx] -
+                 t.g0[v + R] * (kr * sBr[ry][tx] + ki * sBi[ry][tx]);
+        }
+      } else {
+        const int ylo = max(0, Y - R), yhi = min(h - 1, Y + R);
+        for (int y = ylo; y <= yhi; ++y) {
+          const int ry = y - Y0 + R;
+          const float wvr = tap_T(t.vy_re[k], cvr, R, h, Y, y), wvi = tap_T(t.vy_im[k], cvi, R, h, Y, y);
+          const float w0 = tap_T(t.g0, cg0, R, h, Y, y);
+          acc += wvr * sAr[ry][tx] - wvi * sAi[ry][tx] - w0 * (kr * sBr[ry][tx] + ki * sBi[ry][tx]);
+        }
       }
       out[j] += acc;
     }
@@ -753,6 +866,19 @@ __global__ void __launch_bounds__(256) k_db_gaborT(GTArgs a, GaborTaps t) {
   }
 }
 
+__device__ __noinline__ bool pos3_exact(float a, float b, float c) {
+  return 2.0 * (double)a - (double)b - (double)c > 0.0;
+}
+
+// Exact test 2a - b - c > 0 for floats a, b, c (the double evaluation is a call, so
+// that it runs only on the rare operands near the kink).
+__device__ __forceinline__ bool pos3(float a, float b, float c) {
+  const float f = 2.f * a - b - c;
+  // two roundings, each within 2^-24 of a partial sum bounded by 2|a| + |b| + |c|
+  if (fabsf(f) > 1e-6f * (2.f * fabsf(a) + fabsf(b) + fabsf(c))) return f > 0.f;
+  return pos3_exact(a, b, c);
+}
+
 // Level 1 -> level 0 transposed REDUCE of the three feature gradients, fused with
 // the derivative of the features (Sec. 7.2 step 1):
 //   I = s/765, s = r+g+b; where 10 s > max s: rn = 3r/s (gn, bn likewise),
@@ -761,23 +887,18 @@ __global__ void __launch_bounds__(256) k_db_gaborT(GTArgs a, GaborTaps t) {
 __global__ void __launch_bounds__(256) k_db_feat(const float* __restrict__ rgb, const int* __restrict__ smax_p,
                                                  const float* __restrict__ gI1, const float* __restrict__ gRG1,
                                                  const float* __restrict__ gBY1, int H, int W, int h1, int w1,
+                                                 const int* __restrict__ lo_y, const float4* __restrict__ w_y,
+                                                 const int* __restrict__ lo_x, const float4* __restrict__ w_x,
                                                  float* __restrict__ g_rgb) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
   const int b = blockIdx.z;
   const size_t o1 = (size_t)b * h1 * w1;
-  int Ys[4], Xs[4];
-  float wy[4], wx[4];
-  const int ny = rt_weights(y, H, h1, Ys, wy), nx = rt_weights(x, W, w1, Xs, wx);
-  float gI = 0.f, gRG = 0.f, gBY = 0.f;
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      const float w = wy[j] * wx[i];
-      const size_t o = o1 + (size_t)Ys[j] * w1 + Xs[i];
-      gI += w * gI1[o];
-      gRG += w * gRG1[o];
-      gBY += w * gBY1[o];
-    }
+  const int ylo = lo_y[y], xlo = lo_x[x];
+  const float4 wy = w_y[y], wx = w_x[x];
+  const float gI = rt_apply(gI1 + o1, w1, h1, ylo, wy, xlo, wx);
+  const float gRG = rt_apply(gRG1 + o1, w1, h1, ylo, wy, xlo, wx);
+  const float gBY = rt_apply(gBY1 + o1, w1, h1, ylo, wy, xlo, wx);
   const size_t p = ((size_t)b * H + y) * W + x;
   const float r = rgb[3 * p], g = rgb[3 * p + 1], bl = rgb[3 * p + 2], s = r + g + bl;
   const float smax = __int_as_float(smax_p[b]);
@@ -786,10 +907,11 @@ __global__ void __launch_bounds__(256) k_db_feat(const float* __restrict__ rgb, 
     // the clamps' decisions are signs of linear forms of (r, g, b) (s > 0 scales
     // out), evaluated exactly in double: R > 0 iff 2r - g - b > 0, Y > 0 iff
     // min(r, g) > b, sign(rn - gn) = sign(r - g)
+    // (a 3-term form in float is re-evaluated in double only when it lies within
+    // its rounding bound of zero; min(r, g) > b and r > g are exact comparisons)
     const float inv = 3.f / s;
-    const double rd = r, gd = g, bd = bl;
-    const float aR = 2.0 * rd - gd - bd > 0.0, aG = 2.0 * gd - rd - bd > 0.0, aB = 2.0 * bd - rd - gd > 0.0;
-    const float aY = fmin(rd, gd) - bd > 0.0;
+    const float aR = pos3(r, g, bl), aG = pos3(g, r, bl), aB = pos3(bl, r, g);
+    const float aY = fminf(r, g) > bl;
     const float sd = r > g ? 1.f : (r < g ? -1.f : 0.f);
     const float dR = gRG, dG = -gRG, dB = gBY, dY = -gBY;
     const float grn = dR * aR - 0.5f * dG * aG - 0.5f * dB * aB + dY * aY * (0.5f - 0.5f * sd);
@@ -815,7 +937,7 @@ __global__ void k_db_final(const double* __restrict__ gpar, int B, double* __res
 
 // ------------------------------------------------------------------ host side
 struct DiffLayout {
-  size_t kal, Tx, part, gS, gC3, G[SEG_MAX_LEVELS], coef, targ, hsur, grad, gpar, rsT, total;
+  size_t kal, Tx, part, gS, gC3, G[SEG_MAX_LEVELS], coef, dpart, targ, hsur, grad, gpar, rsT, rtlo, rtw, total;
   size_t gpyr[3][SEG_MAX_LEVELS], gori[SEG_MAX_ORIENT][SEG_MAX_LEVELS], grad_bytes;
 };
 
@@ -832,6 +954,10 @@ static int diff_layout(seg_diff* d, int B, int H, int W, const seg_params& p, Di
     if (((s.hl[c] + T - 1) / T) * ((s.wl[c] + T - 1) / T) > DB_MAXT) return SEG_EINVAL;
   }
   if ((size_t)DB_RB * W * sizeof(float) > 40 * 1024) return SEG_EINVAL;  // W <= 5120
+  for (int q = 0; q < s.npairs; ++q) {  // one surround row's transposed field fits a chunk
+    const int d = s.pair_s[q] - s.pair_c[q];
+    if ((long long)((1 << d) + 3) * s.wl[s.pair_s[q]] > SURT_CAP) return SEG_EINVAL;
+  }
   size_t off = seg_align(sal_bytes);
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -847,6 +973,7 @@ static int diff_layout(seg_diff* d, int B, int H, int W, const seg_params& p, Di
   L.gC3 = take(Bz * nS * sizeof(float));
   for (int c = s.c_min; c <= s.c_max; ++c) L.G[c] = take(Bz * s.nch * s.hl[c] * s.wl[c] * sizeof(float));
   L.coef = take(Bz * s.nmaps * sizeof(DiffCoef));
+  L.dpart = take(Bz * s.nbands_total * sizeof(DiffPart));
   d->ntarg = 0;
   d->nhsur = 0;
   for (int q = 0; q < s.npairs; ++q) {
@@ -879,6 +1006,16 @@ static int diff_layout(seg_diff* d, int B, int H, int W, const seg_params& p, Di
   n += wS;
   d->rsT_n = n;
   L.rsT = take(n * sizeof(int2));
+  int nr = 0;
+  for (int l = 0; l + 1 < s.L; ++l) {
+    d->rt_row[l] = nr;
+    nr += s.hl[l];
+    d->rt_col[l] = nr;
+    nr += s.wl[l];
+  }
+  d->rt_n = nr;
+  L.rtlo = take(nr * sizeof(int));
+  L.rtw = take(nr * sizeof(float4));
   L.total = off;
   return SEG_OK;
 }
@@ -897,6 +1034,25 @@ static void transposed_ranges(int ns, int nd, int2* ranges) {
   }
   for (int i = 0; i < ns; ++i)
     if (ranges[i].y == 0) ranges[i] = make_int2(0, 0);
+}
+
+// Transposed REDUCE along one axis (n samples -> n2 = ceil(n/2)): output sample
+// y receives level-(l+1) samples Y = lo + j (j < 4) with weight
+// sum_t k(t) [clamp(2Y + t, 0, n-1) = y], k = [1 4 6 4 1]/16.
+static void reduceT_table(int n, int n2, int* lo, float4* w) {
+  static const float kb[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+  for (int y = 0; y < n; ++y) {
+    lo[y] = std::max(0, y / 2 - 1);
+    float ws[4];
+    for (int j = 0; j < 4; ++j) {
+      const int Y = lo[y] + j;
+      float acc = 0.f;
+      for (int t = -2; t <= 2 && Y < n2; ++t)
+        if (std::min(std::max(2 * Y + t, 0), n - 1) == y) acc += kb[t + 2];
+      ws[j] = acc;
+    }
+    w[y] = make_float4(ws[0], ws[1], ws[2], ws[3]);
+  }
 }
 
 extern "C" int seg_diff_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes) {
@@ -948,6 +1104,7 @@ extern "C" int seg_diff_create(void* stream, int B, int H, int W, const seg_para
   d->gC3 = (float*)(base + L.gC3);
   for (int c = s.c_min; c <= s.c_max; ++c) d->G[c] = (float*)(base + L.G[c]);
   d->coef = (DiffCoef*)(base + L.coef);
+  d->dpart = (DiffPart*)(base + L.dpart);
   d->targ = (int*)(base + L.targ);
   d->hsur = (float*)(base + L.hsur);
   for (int ch = 0; ch < 3; ++ch)
@@ -958,6 +1115,8 @@ extern "C" int seg_diff_create(void* stream, int B, int H, int W, const seg_para
   d->grad_bytes = L.grad_bytes;
   d->gpar = (double*)(base + L.gpar);
   d->rsT = (int2*)(base + L.rsT);
+  d->rt_lo = (int*)(base + L.rtlo);
+  d->rt_w = (float4*)(base + L.rtw);
   rc = sal_upload_tables(s);
   if (!rc) {
     std::vector<int2> t(d->rsT_n);
@@ -969,6 +1128,15 @@ extern "C" int seg_diff_create(void* stream, int B, int H, int W, const seg_para
     transposed_ranges(s.hl[s.sS], H, &t[d->rsT_frow]);
     transposed_ranges(s.wl[s.sS], W, &t[d->rsT_fcol]);
     if (cudaMemcpy(d->rsT, t.data(), sizeof(int2) * d->rsT_n, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = SEG_ECUDA;
+    std::vector<int> lo(d->rt_n);
+    std::vector<float4> wt(d->rt_n);
+    for (int l = 0; l + 1 < s.L; ++l) {
+      reduceT_table(s.hl[l], s.hl[l + 1], &lo[d->rt_row[l]], &wt[d->rt_row[l]]);
+      reduceT_table(s.wl[l], s.wl[l + 1], &lo[d->rt_col[l]], &wt[d->rt_col[l]]);
+    }
+    if (!rc && (cudaMemcpy(d->rt_lo, lo.data(), sizeof(int) * d->rt_n, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(d->rt_w, wt.data(), sizeof(float4) * d->rt_n, cudaMemcpyHostToDevice) != cudaSuccess))
       rc = SEG_ECUDA;
   }
   if (rc) {
@@ -1043,6 +1211,20 @@ static void fill_dcs(const seg_diff* d, DCSArgs& a) {
   a.ntarg = d->ntarg;
   a.hsur = d->hsur;
   a.nhsur = d->nhsur;
+  int off = 0;
+  for (int q = 0; q < s.npairs; ++q) {
+    a.band_off[q] = off;
+    off += s.nch * ((s.hl[s.pair_c[q]] + s.tile - 1) / s.tile);
+  }
+  a.band_off[s.npairs] = off;
+  a.nbands_total = off;
+  a.dpart = d->dpart;
+  a.nsl = 0;
+  for (int sv = 0; sv < s.L; ++sv) {
+    bool any = false;
+    for (int q = 0; q < s.npairs; ++q) any |= s.pair_s[q] == sv;
+    if (any) a.slist[a.nsl++] = sv;
+  }
 }
 
 extern "C" int seg_diff_backward(seg_diff* d, const float* rgb, const float* fmap, const double* theta,
@@ -1083,6 +1265,8 @@ extern "C" int seg_diff_backward(seg_diff* d, const float* rgb, const float* fma
   ta.gacc = d->G[s.c_max];
   ta.gpar = d->gpar;
   k_db_top<<<B, 1024, 0, st>>>(ta);
+  k_db_nbwd<<<dim3(4, B), 512, 0, st>>>(ta, 0);
+  k_db_nbwd<<<dim3(s.no, B), 512, 0, st>>>(ta, 1);
   // across-scale sums: G_c = REDUCE^T G_{c+1}
   for (int c = s.c_max - 1; c >= s.c_min; --c) {
     RTArgs ra;
@@ -1095,18 +1279,19 @@ extern "C" int seg_diff_backward(seg_diff* d, const float* rgb, const float* fma
     ra.h2 = s.hl[c + 1];
     ra.w2 = s.wl[c + 1];
     ra.accumulate = 0;
+    ra.lo_y = d->rt_lo + d->rt_row[c];
+    ra.w_y = d->rt_w + d->rt_row[c];
+    ra.lo_x = d->rt_lo + d->rt_col[c];
+    ra.w_x = d->rt_w + d->rt_col[c];
     k_db_reduceT<<<dim3((ra.w + 31) / 32, (ra.h + 7) / 8, s.nch * B), 256, 0, st>>>(ra);
   }
   DCSArgs ca;
   fill_dcs(d, ca);
-  k_db_cs_stats<<<dim3(s.nmaps, B), 512, 0, st>>>(ca);
+  k_db_cs_stats<<<dim3(ca.nbands_total, B), 256, 0, st>>>(ca);
+  k_db_cs_coef<<<(s.nmaps * B + 127) / 128, 128, 0, st>>>(ca, B);
   for (int c = s.c_min; c <= s.c_max; ++c)
     k_db_cs_apply<<<dim3((s.wl[c] + 31) / 32, (s.hl[c] + 7) / 8, s.nch * B), 256, 0, st>>>(ca, c);
-  for (int sv = 0; sv < s.L; ++sv) {
-    bool any = false;
-    for (int q = 0; q < s.npairs; ++q) any |= s.pair_s[q] == sv;
-    if (any) k_db_surT<<<dim3((s.wl[sv] + 31) / 32, (s.hl[sv] + 7) / 8, s.nch * B), 256, 0, st>>>(ca, sv);
-  }
+  k_db_surT<<<dim3(ca.nsl, s.nch, B), 256, 0, st>>>(ca);
   GTArgs ga;
   memset(&ga, 0, sizeof(ga));
   ga.lvl_first = s.c_min;
@@ -1140,10 +1325,15 @@ extern "C" int seg_diff_backward(seg_diff* d, const float* rgb, const float* fma
     ra.h2 = s.hl[l];
     ra.w2 = s.wl[l];
     ra.accumulate = 1;
+    ra.lo_y = d->rt_lo + d->rt_row[l - 1];
+    ra.w_y = d->rt_w + d->rt_row[l - 1];
+    ra.lo_x = d->rt_lo + d->rt_col[l - 1];
+    ra.w_x = d->rt_w + d->rt_col[l - 1];
     k_db_reduceT<<<dim3((ra.w + 31) / 32, (ra.h + 7) / 8, 3 * B), 256, 0, st>>>(ra);
   }
-  k_db_feat<<<dim3((W + 31) / 32, (H + 7) / 8, B), 256, 0, st>>>(rgb, s.smax, d->gpyr[0][1], d->gpyr[1][1],
-                                                                 d->gpyr[2][1], H, W, s.hl[1], s.wl[1], g_rgb);
+  k_db_feat<<<dim3((W + 31) / 32, (H + 7) / 8, B), 256, 0, st>>>(
+      rgb, s.smax, d->gpyr[0][1], d->gpyr[1][1], d->gpyr[2][1], H, W, s.hl[1], s.wl[1], d->rt_lo + d->rt_row[0],
+      d->rt_w + d->rt_row[0], d->rt_lo + d->rt_col[0], d->rt_w + d->rt_col[0], g_rgb);
   k_db_final<<<1, 32, 0, st>>>(d->gpar, B, g_theta);
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
