@@ -131,7 +131,9 @@ def kernels_per_frame(p, H=480, W=640, graph=True):
             break
         tiled += 1
     tail = 1 if 1 + tiled < p["levels"] - 1 else 0
-    sal = 2 + tiled + tail + 1 + 1 + (p["c_max"] - p["c_min"] + 1) + 1 + 1
+    # rgb max, features + first REDUCE, tiled REDUCEs, tail, Gabor, cs stats,
+    # one accumulation per center scale, conspicuity
+    sal = 2 + tiled + tail + 1 + 1 + (p["c_max"] - p["c_min"] + 1) + 1
     return sal + 3 + 1 + (1 if graph else 0)  # prior, moments, terms; min cut; frame-pointer record
 
 

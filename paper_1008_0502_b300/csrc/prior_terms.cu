@@ -44,8 +44,8 @@ struct PriorArgs {
   float* prior;
   // fused first moment pass (rgb == nullptr: off)
   const uint8_t* rgb;
-  double* part;
-  int part_stride;     // doubles of partials per frame
+  float* part;
+  int part_stride;     // partials per frame
   unsigned* counter;
   GaussDev* gauss;
   KalmanDev* kal_adv;  // nullable: advance the variance recursion
@@ -53,8 +53,8 @@ struct PriorArgs {
 };
 
 struct MomFinArgs {
-  double* part;
-  int part_stride;  // doubles of partials per frame
+  float* part;
+  int part_stride;  // partials per frame
   unsigned* counter;
   GaussDev* gauss;
   KalmanDev* kal;  // nullable: advance the variance recursion
@@ -78,9 +78,9 @@ __device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
 }
 
 template <int NV>
-__device__ void reduce_parts(const double* part, int nblocks, double* out);
+__device__ void reduce_parts(const float* part, int nblocks, double* out);
 template <int NV>
-__device__ bool block_partial_last(const float* v, double* part, unsigned* counter, int bid,
+__device__ bool block_partial_last(const float* v, float* part, unsigned* counter, int bid,
                                    int nblocks);
 __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b);
 
@@ -170,11 +170,11 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
 
 // Writes this CTA's NV partial sums to part[bid*NV ..] and returns true in
 // every thread of exactly one CTA, the last to finish (threadfence reduction).
-// Sums inside the CTA are FP32 (a CTA covers at most a few thousand pixels);
-// the per-CTA partials and everything across CTAs are FP64.
+// A CTA covers at most a few thousand pixels, so its sums are plain FP32; the
+// sum across CTAs (reduce_parts) is an error-free float-float sum, which keeps
+// about 44 bits without the FP64 pipe (narrow on this part).
 template <int NV>
-__device__ bool block_partial_last(const float* v, double* part, unsigned* counter, int bid,
-                                   int nblocks) {
+__device__ bool block_partial_last(const float* v, float* part, unsigned* counter, int bid, int nblocks) {
   __shared__ float red[32][NV];
   __shared__ int is_last;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -184,10 +184,10 @@ __device__ bool block_partial_last(const float* v, double* part, unsigned* count
     if (lane == 0) red[wid][k] = s;
   }
   __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    part[bid * NV + threadIdx.x] = s;
+  for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][k];
+    part[bid * NV + k] = s;
   }
   __threadfence();
   __syncthreads();
@@ -201,23 +201,35 @@ __device__ bool block_partial_last(const float* v, double* part, unsigned* count
   return is_last != 0;
 }
 
-// Deterministic fixed-order reduction of the per-CTA partials (one CTA).
+// (hi, lo) float pairs: two_sum gives s + e = a + b exactly (Knuth).
+__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
+  const float s = x.x + y.x, bb = s - x.x;
+  float e = (x.x - (s - bb)) + (y.x - bb);
+  e += x.y + y.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+
+// Deterministic fixed-order float-float sums of the NV per-CTA partials (one CTA):
+// warp k (mod the CTA's warps) sums value k, lanes striding over the CTAs, then
+// a shuffle tree; out[k] = hi + lo.
 template <int NV>
-__device__ void reduce_parts(const double* part, int nblocks, double* out) {
-  __shared__ double red[256][NV];
-  double s[NV];
-  for (int k = 0; k < NV; ++k) s[k] = 0.0;
-  for (int bk = threadIdx.x; bk < nblocks; bk += blockDim.x)
-    for (int k = 0; k < NV; ++k) s[k] += ((volatile double*)part)[bk * NV + k];
-  for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = s[k];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w)
-      for (int k = 0; k < NV; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
-    __syncthreads();
+__device__ void reduce_parts(const float* part, int nblocks, double* out) {
+  const int lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < ((NV + 7) / 8) * 8 * 32; t += blockDim.x) {
+    const int k = t >> 5;
+    float2 acc = make_float2(0.f, 0.f);
+    if (k < NV)
+      for (int b = lane; b < nblocks; b += 32) acc = ff_add(acc, make_float2(((volatile float*)part)[b * NV + k], 0.f));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 other;
+      other.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
+      other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
+      acc = lane < (lane ^ o) ? ff_add(acc, other) : ff_add(other, acc);  // same order in both lanes
+    }
+    if (lane == 0 && k < NV) out[k] = (double)acc.x + (double)acc.y;
   }
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NV; ++k) out[k] = red[0][k];
   __syncthreads();
 }
 
@@ -267,13 +279,13 @@ __device__ double chol_inv(double c00, double c10, double c11, double c20, doubl
 // the paper's k-means start): means on the grey axis through the weighted mean
 // at (m - (M-1)/2) * 1.5 sigma_g, sigma_g^2 = g^T Sigma g, g = (1,1,1)/sqrt3;
 // every covariance = Sigma; every weight = 1/M.
-__device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M) {
-  for (int lab = 0; lab < 2; ++lab) {
+__device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M, int lab) {
+  {
     double sw = g->sw[lab];
     if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
       for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
       g->lconst[lab] = 0.f;
-      continue;
+      return;
     }
     const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
     double c00 = m[0] / sw + 1e-4, c10 = m[1] / sw, c11 = m[2] / sw + 1e-4;
@@ -369,7 +381,8 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
   if (block_partial_last<12>(s, f.part, f.counter, blockIdx.x, gridDim.x)) {
     __shared__ double tot[12];
     reduce_parts<12>(f.part, gridDim.x, tot);
-    if (threadIdx.x == 0) finalize_cov(tot, f.gauss, f.gmm ? f.gmm + 2 * fb : nullptr, f.M);
+    if (threadIdx.x < 2)  // one thread per label
+      finalize_cov(tot, f.gauss, f.gmm ? f.gmm + 2 * fb : nullptr, f.M, threadIdx.x);
   }
 }
 
@@ -382,22 +395,11 @@ struct EMArgs {
   int N, M;
   GmmDev* gmm;        // [frame][label]
   const GaussDev* gauss;
-  double* part;       // [frame][label][blocks * EM_NV]
+  float* part;        // [frame][label][blocks * EM_NV]
   int part_stride;
   unsigned* counter;  // [frame][label]
   const SegIO* io;
 };
-
-// Fixed-order sum of NV partials over the CTAs, one thread per value.
-template <int NV>
-__device__ void reduce_parts_serial(const double* part, int nblocks, double* out) {
-  if ((int)threadIdx.x < NV) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += ((volatile double*)part)[b * NV + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
 
 // One EM iteration for label a of frame fb (blockIdx.y = 2 fb + a): E-step
 // responsibilities from the current mixture, moments of every component about
@@ -458,10 +460,10 @@ __global__ void __launch_bounds__(256) k_em_step(EMArgs a) {
       t[9] += wr * d[m][2] * d[m][2];
     }
   }
-  double* part = a.part + (size_t)(2 * fb + lab) * a.part_stride;
+  float* part = a.part + (size_t)(2 * fb + lab) * a.part_stride;
   if (block_partial_last<EM_NV>(s, part, a.counter + 2 * fb + lab, blockIdx.x, gridDim.x)) {
     __shared__ double tot[EM_NV];
-    reduce_parts_serial<EM_NV>(part, gridDim.x, tot);
+    reduce_parts<EM_NV>(part, gridDim.x, tot);
     if (threadIdx.x == 0) {
       double ntot = 0.0;
       for (int m = 0; m < M; ++m) ntot += tot[10 * m];
@@ -648,7 +650,7 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   for (int u = 0; u <= 2 * p.f_radius; ++u) a.ftap[u] = (float)(g[u] / sg);
   a.prior = prior;
   a.rgb = rgb_moments;
-  a.part = c->mom_part;
+  a.part = (float*)c->mom_part;
   a.counter = c->mom_counter;
   a.gauss = c->gauss;
   a.part_stride = pt_part_doubles(c->H, c->W);
@@ -666,7 +668,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   cudaStream_t st = c->stream;
   int N = c->N;
   MomFinArgs fa;
-  fa.part = c->mom_part;
+  fa.part = (float*)c->mom_part;
   fa.part_stride = pt_part_doubles(c->H, c->W);
   fa.counter = c->mom_counter;
   fa.gauss = c->gauss;
@@ -687,7 +689,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     ea.M = M;
     ea.gmm = c->gmm;
     ea.gauss = c->gauss;
-    ea.part = c->em_part;
+    ea.part = (float*)c->em_part;
     ea.part_stride = pt_em_part_doubles(c->H, c->W);
     ea.counter = c->em_counter;
     ea.io = c->io_mode ? c->io : nullptr;

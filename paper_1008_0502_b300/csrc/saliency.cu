@@ -10,8 +10,9 @@
 //                   evaluated as a rank-2 separable filter from shared memory
 //   k_cs_stats      center-surround maps |X(c) -/+ up X(s)| computed on the fly;
 //                   per-map min, max and T x T tile maxima for N(.)
-//   k_cs_norm       N(.) of every map as an affine map a*v + b
-//   k_cs_accum      across-scale sum: B_c = sum_s N(CS(c,s)) + REDUCE(B_{c-1})
+//   k_cs_accum      across-scale sum: B_c = sum_s N(CS(c,s)) + REDUCE(B_{c-1}),
+//                   each map's N(.) taken as an affine map a*v + b from its
+//                   statistics in the CTA's prologue
 //                   (REDUCE is linear, so reducing the sum equals summing the
 //                   reduced maps)
 //   k_consp         one CTA per frame at sigma_S: orientation conspicuity,
@@ -338,7 +339,7 @@ struct CSArgs {
   int nbands_total;
   unsigned* mm;
   float* tpart;
-  float* nab;  // [frame][map][2]: N(.) as a*v + b
+  float flat;  // N(.) flat-map threshold
   const int2* rs;
   int rs_row[SEG_MAX_PAIRS], rs_col[SEG_MAX_PAIRS];
 };
@@ -458,17 +459,11 @@ __device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* 
   norm_affine(__uint_as_float(mm[2 * m]), __uint_as_float(mm[2 * m + 1]), sum, nb * ntx, flat, ab);
 }
 
-__global__ void k_cs_norm(CSArgs a, float flat, float* nab, int nframes) {
-  const int nm = a.npairs * a.nch;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nm * nframes) return;
-  const int fb = i / nm, m = i - fb * nm;
-  cs_map_affine(a, m / a.nch, m % a.nch, flat, nab + 2 * (size_t)i, fb);
-}
 
 // B_c(f) = sum over pairs (c, s) of N(CS_f(c, s)) + REDUCE(B_{c-1}(f)).
 #define ACC_TX 32
 #define ACC_TY 8
+#define ACC_MAX_PC 16  // center-surround pairs per center scale
 // B_c = sum over pairs (c, s) of N(CS(c, s)) + REDUCE(B_{c-1}), all NCH channels
 // of a 32 x 8 output tile per CTA; the REDUCE input tile (with its 2-pixel
 // halo) is staged in shared memory one channel at a time.
@@ -477,11 +472,25 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
                                                   int wp, float* __restrict__ out) {
   __shared__ float sP[2 * ACC_TY + 3][2 * ACC_TX + 3];
   __shared__ float sH[2 * ACC_TY + 3][ACC_TX];
+  __shared__ float sab[2 * ACC_MAX_PC * CPB];  // N(.) of this CTA's maps as a*v + b
   constexpr int G = NCH / CPB;                  // channel groups
   const int fb = blockIdx.z / G;                // frame of the batch
   const int f0 = (blockIdx.z % G) * CPB;        // first channel of this CTA
-  const float* nab = a.nab + (size_t)fb * 2 * a.npairs * NCH;
   const int hc = a.hl[c], wc = a.wl[c];
+  {
+    // the affine form of N(.) of every (pair with center c, channel) map this CTA
+    // adds, from the statistics of k_cs_stats
+    int npc = 0;
+    for (int p = 0; p < a.npairs; ++p) npc += a.pair_c[p] == c;
+    for (int j = threadIdx.x; j < npc * CPB; j += blockDim.x) {
+      const int slot = j / CPB, f = j - slot * CPB;
+      int p = 0;
+      for (int k = -1; p < a.npairs; ++p)
+        if (a.pair_c[p] == c && ++k == slot) break;
+      cs_map_affine(a, p, f0 + f, a.flat, &sab[2 * j], fb);
+    }
+    __syncthreads();
+  }
   if (prev) prev += (size_t)fb * NCH * hp * wp;
   out += (size_t)fb * NCH * hc * wc;
   const int X0 = blockIdx.x * ACC_TX, Y0 = blockIdx.y * ACC_TY;
@@ -492,17 +501,18 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
 #pragma unroll
   for (int f = 0; f < CPB; ++f) acc[f] = 0.f;
   if (in) {
-    for (int p = 0; p < a.npairs; ++p) {
+    for (int p = 0, slot = 0; p < a.npairs; ++p) {
       if (a.pair_c[p] != c) continue;
+      const float* ab = &sab[2 * CPB * slot++];
       const int sv = a.pair_s[p], hs = a.hl[sv], ws = a.wl[sv];
       const int2 ry = a.rs[a.rs_row[p] + y], rx = a.rs[a.rs_col[p] + x];
 #pragma unroll
       for (int f = 0; f < CPB; ++f) {
-        const int ch = f0 + f, m = p * NCH + ch;
+        const int ch = f0 + f;
         float u = seg_bilinear_t(a.X[ch][sv] + (size_t)fb * hs * ws, ws, ry, rx);
         float v0 = a.X[ch][c][(size_t)fb * hc * wc + (size_t)y * wc + x];
         float v = (a.opp_sum && (ch == 1 || ch == 2)) ? fabsf(v0 + u) : fabsf(v0 - u);
-        acc[f] += nab[2 * m] * v + nab[2 * m + 1];
+        acc[f] += ab[2 * f] * v + ab[2 * f + 1];
       }
     }
   }
@@ -755,6 +765,7 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
       s.npairs++;
     }
   s.nmaps = s.npairs * s.nch;
+  if (s.d_max - s.d_min + 1 > ACC_MAX_PC) return SEG_EINVAL;
   s.nbands_total = 0;
   for (int i = 0; i < s.npairs; ++i) {
     int c = s.pair_c[i];
@@ -787,7 +798,6 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
         s.oc[k][l] = (float2*)take(Bz * sizeof(float2) * s.hl[l] * s.wl[l]);
   s.mm = (unsigned*)take(Bz * sizeof(unsigned) * 2 * s.nmaps);
   s.tpart = (float*)take(Bz * sizeof(float) * s.nbands_total);
-  s.nab = (float*)take(Bz * sizeof(float) * 2 * s.nmaps);
   size_t big = (size_t)s.hl[s.c_min] * s.wl[s.c_min] * s.nch;
   s.acc[0] = (float*)take(Bz * sizeof(float) * big);
   s.acc[1] = (float*)take(Bz * sizeof(float) * big);
@@ -828,7 +838,6 @@ void sal_bind(SalWS& s, char* base) {
     }
   fix(s.mm);
   fix(s.tpart);
-  fix(s.nab);
   fix(s.acc[0]);
   fix(s.acc[1]);
   s.acc_final = s.acc[(s.c_max - s.c_min) & 1];
@@ -879,7 +888,7 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
   a.pair_band_off[s.npairs] = off;
   a.mm = s.mm;
   a.tpart = s.tpart;
-  a.nab = s.nab;
+  a.flat = s.flat;
   a.rs = s.rs;
   for (int i = 0; i < s.npairs; ++i) {
     a.rs_row[i] = s.rs_row[i];
@@ -981,7 +990,6 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
         return SEG_EINVAL;
     }
   }
-  k_cs_norm<<<(s.nmaps * B + 127) / 128, 128, 0, st>>>(ca, s.flat, s.nab, B);
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;

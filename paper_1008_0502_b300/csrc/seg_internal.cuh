@@ -178,7 +178,6 @@ struct SalWS {
   unsigned* mm;  // [nmaps][2]: min and max as float bits (maps are >= 0)
   float* tpart;  // [nbands_total]: per-band sums of tile maxima
   int nbands_total;
-  float* nab;     // [frame][map][2]: N(.) as the affine map a*v + b
   float* acc[2];  // ping-pong channel accumulators at scale c (nch planes)
   float* acc_final;  // the accumulator holding scale c_max (sigma_S): acc[(c_max - c_min) & 1]
   float* consp;   // 4 planes at sigma_S: N(C_I), N(C_RG), N(C_BY), N(C_O)
