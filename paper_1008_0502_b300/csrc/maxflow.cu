@@ -65,32 +65,37 @@ __device__ __forceinline__ long long mf_now() {
 }
 
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of
-// the CTA) once any CTA has recorded a timeout.
+// the CTA) once any CTA has recorded a timeout.  Arrival is an acq_rel atomic on
+// a counter, release a release-add on a generation word in another cache line,
+// polled with acquire loads; the CTA barriers before and after carry the other
+// threads' writes (release and acquire are cumulative), so no full fences are
+// needed.  The timer is read every 256 polls.
 __device__ bool mf_grid_sync(const MFArgs& a, MFShared& s) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* genp = &a.bar->gen;
-    unsigned int g = *genp;
-    __threadfence();
-    unsigned int arrived = atomicAdd(&a.bar->count, 1u) + 1u;
+    unsigned int g, old;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&a.bar->gen) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&a.bar->count) : "memory");
     int ok = 1;
-    if (arrived == gridDim.x) {
-      atomicExch(&a.bar->count, 0u);
-      __threadfence();
-      atomicAdd(&a.bar->gen, 1u);
+    if (old + 1u == gridDim.x) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&a.bar->count) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.bar->gen) : "memory");
     } else {
-      long long t0 = mf_now();
-      while (*genp == g) {
-        if (mf_now() - t0 > a.timeout_ns) {
+      const long long t0 = mf_now();
+      for (unsigned int k = 0;; ++k) {
+        unsigned int cur;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&a.bar->gen) : "memory");
+        if (cur != g) break;
+        if ((k & 255u) == 255u && mf_now() - t0 > a.timeout_ns) {
           atomicCAS(&a.status[0], 0, SEG_ETIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
-    if (*(volatile int*)&a.status[0] == SEG_ETIMEOUT) ok = 0;
+    int st;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(st) : "l"(&a.status[0]) : "memory");
+    if (st == SEG_ETIMEOUT) ok = 0;
     s.ok = ok;
   }
   __syncthreads();
@@ -120,20 +125,35 @@ __device__ bool mf_tile_dirty(const MFArgs& a, MFShared& s, int tx, int ty, int 
 // ---------------------------------------------------------------- BFS to the sink
 // d(u) = 1 if u has residual to t, else 1 + min over residual arcs u->v of d(v):
 // relaxed to the local fixpoint with the halo fixed at its current global value.
+// first: the round that starts a global relabel -- the initial distances (1 on
+// nodes with a residual arc to t, INF elsewhere) and the residual bitmasks are
+// formed here from rt and r (no separate pass and grid barrier), and every node
+// of the tile is written.
 template <int ND>
-__device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty) {
+__device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool first) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
     int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
-    s.h[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) ? a.h[gy * a.W + gx] : SEG_INF_H;
+    const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    const int gg = gy * a.W + gx;
+    s.h[i] = !in ? SEG_INF_H : first ? (a.rt[gg] > 0 ? 1 : SEG_INF_H) : a.h[gg];
   }
   const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
   const int gy = Y0 + ly, gx = X0 + lx;
   const bool valid = gy < a.H && gx < a.W;
   const int g = gy * a.W + gx;
   const int hi = (ly + 1) * MF_HX + lx + 1;
-  const unsigned bits = valid ? a.rm[g] : 0u;
+  unsigned bits = 0u;
+  if (valid) {
+    if (first) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d) bits |= (a.r[d * a.N + g] > 0 ? 1u : 0u) << d;
+      a.rm[g] = (unsigned char)bits;
+    } else {
+      bits = a.rm[g];
+    }
+  }
   __syncthreads();
   bool any = false;
   for (;;) {
@@ -151,21 +171,36 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty) {
     if (!__syncthreads_or(ch)) break;
     any = true;
   }
-  if (valid && any) a.h[g] = s.h[hi];
+  if (valid && (any || first)) a.h[g] = s.h[hi];
   __syncthreads();  // the next tile reuses the shared arrays
   return any;
 }
 
 // z(v) = 1 if some residual arc u->v has z(u) = 1 (pull form, halo bitmasks).
+// first: the first round -- the seeds (z = 1 where excess remains) and the
+// residual bitmasks of the tile and its halo come from e and r (no separate pass
+// and grid barrier), and every node of the tile is written.
 template <int ND>
-__device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty) {
+__device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool first) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
     int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
     bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-    s.z[i] = in ? a.z[gy * a.W + gx] : 0;
-    s.b[i] = in ? a.rm[gy * a.W + gx] : 0;
+    const int gg = gy * a.W + gx;
+    if (!in) {
+      s.z[i] = 0;
+      s.b[i] = 0;
+    } else if (first) {
+      unsigned bits = 0u;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) bits |= (a.r[d * a.N + gg] > 0 ? 1u : 0u) << d;
+      s.z[i] = a.e[gg] > 0 ? 1 : 0;
+      s.b[i] = (unsigned char)bits;
+    } else {
+      s.z[i] = a.z[gg];
+      s.b[i] = a.rm[gg];
+    }
   }
   const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
   const int gy = Y0 + ly, gx = X0 + lx;
@@ -190,7 +225,8 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty) {
     if (!__syncthreads_or(ch)) break;
     any = true;
   }
-  if (valid && any) a.z[gy * a.W + gx] = s.z[hi];
+  if (valid && (any || first)) a.z[gy * a.W + gx] = s.z[hi];
+  if (valid && first) a.rm[gy * a.W + gx] = s.b[hi];
   __syncthreads();  // the next tile reuses the shared arrays
   return any;
 }
@@ -389,21 +425,13 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   for (;;) {
     // ---- 3. global relabel
     if (cycle % a.gr_every == 0) {
-      for (int u = gtid; u < N; u += nthr) {
-        unsigned bits = 0;
-#pragma unroll
-        for (int d = 0; d < ND; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
-        a.rm[u] = (unsigned char)bits;
-        a.h[u] = a.rt[u] > 0 ? 1 : SEG_INF_H;
-      }
-      if (!mf_grid_sync(a, s)) return;
       for (bool first = true;; first = false) {
         mf_flag_begin(a, epoch);
         bool ch = false;
         for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
           int tx = k % a.ntx, ty = k / a.ntx;
           if (!first && !mf_tile_dirty(a, s, tx, ty, (int)epoch - 1)) continue;
-          if (mf_tile_bfs<ND>(a, s, tx, ty)) {
+          if (mf_tile_bfs<ND>(a, s, tx, ty, first)) {
             ch = true;
             if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
           }
@@ -453,13 +481,6 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
 
   // ---- 4. minimal source set and cut value (the flow that reached t, per frame
   // of a stacked batch: rows fb*frame_h .. fb*frame_h + frame_h - 1)
-  for (int u = gtid; u < N; u += nthr) {
-    unsigned bits = 0;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) bits |= (a.r[d * N + u] > 0 ? 1u : 0u) << d;
-    a.rm[u] = (unsigned char)bits;
-    a.z[u] = a.e[u] > 0 ? 1 : 0;
-  }
   {
     const int nf = a.frame_h * W;  // nodes per frame
     for (int fb = 0; fb < a.nframes; ++fb) {
@@ -469,14 +490,13 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
       if ((threadIdx.x & 31) == 0 && flow_t != 0) atomicAdd(&a.cut_acc[fb], (unsigned long long)flow_t);
     }
   }
-  if (!mf_grid_sync(a, s)) return;
   for (bool first = true;; first = false) {
     mf_flag_begin(a, epoch);
     bool ch = false;
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
       int tx = k % a.ntx, ty = k / a.ntx;
       if (!first && !mf_tile_dirty(a, s, tx, ty, (int)epoch - 1)) continue;
-      if (mf_tile_reach<ND>(a, s, tx, ty)) {
+      if (mf_tile_reach<ND>(a, s, tx, ty, first)) {
         ch = true;
         if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
       }
@@ -574,7 +594,7 @@ int mf_grid_size(int H, int W, int* grid) {
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io, int* flow, unsigned char* warm) {
+              const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
   a.flow = flow;
@@ -611,9 +631,11 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   a.gr_every = gr_every < 1 ? 1 : gr_every;
   a.local_iters = local_iters < 1 ? 1 : local_iters;
   a.timeout_ns = 4000000000LL;
-  SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, st));
-  SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));
-  SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), st));
+  if (!words_zeroed) {  // (else the caller's frame-start kernel has zeroed them)
+    SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, st));
+    SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));
+    SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), st));
+  }
   void* args[] = {&a};
   SEG_CUDA_TRY(cudaLaunchCooperativeKernel(nbr == 8 ? (const void*)k_maxflow<8> : (const void*)k_maxflow<4>,
                                            dim3(grid), dim3(MF_THREADS), args,

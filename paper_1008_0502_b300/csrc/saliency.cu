@@ -897,13 +897,15 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
 }
 
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
-  return sal_run(c->sal, c->stream, rgb, false, c->io_mode ? c->io : nullptr, nullptr, sal_out, upsample);
+  // under graph capture the frame's k_set_io has zeroed the frame maxima
+  return sal_run(c->sal, c->stream, rgb, false, c->io_mode ? c->io : nullptr, nullptr, sal_out, upsample,
+                 c->io_mode != 0);
 }
 
 int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegIO* io, const double* wdev,
-            float* sal_out, bool upsample) {
+            float* sal_out, bool upsample, bool smax_zeroed) {
   const int H = s.H, W = s.W, N = H * W, B = s.B;
-  SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, B * sizeof(int), st));
+  if (!smax_zeroed) SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, B * sizeof(int), st));
   int nb = min((N + 255) / 256, B > 1 ? 148 : 148 * 8);
   nb = max(nb, (s.nmaps + 255) / 256);
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);

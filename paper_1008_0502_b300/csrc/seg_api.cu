@@ -271,10 +271,10 @@ static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const in
   // the per-stream path (mask_state set) warm-starts from the stream's last cut
   int* flow = (mask_state && c->p.warm_start) ? c->flow : nullptr;
   unsigned char* warm = flow ? c->warm : nullptr;
-  if (c->io_mode)  // mask and cut come from the frame's SegIO
+  if (c->io_mode)  // mask and cut come from the frame's SegIO; k_set_io zeroed the words
     return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
                      nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
-                     c->p.local_iters, c->io, flow, warm);
+                     c->p.local_iters, c->io, flow, warm, true);
   return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
                    c->p.global_relabel_every, c->p.local_iters, nullptr, flow, warm);
@@ -291,7 +291,30 @@ static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, ui
   return rc;
 }
 
-__global__ void k_set_io(SegIO* io, SegIO v) { *io = v; }
+// Starts a replay of the captured frame: records the frame's pointers and zeroes
+// the per-frame words the graph's kernels accumulate into (frame maxima of
+// r+g+b, the min cut's per-frame cut sums, work flags and barrier counter), in
+// place of memset nodes inside the graph.
+struct FrameWords {
+  int* smax;
+  int B;
+  unsigned long long* cut_acc;
+  unsigned int* flags;
+  GridBar* bar;
+};
+
+__global__ void k_set_io(SegIO* io, SegIO v, FrameWords w) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    *io = v;
+    w.bar->count = 0u;
+  }
+  if (t < 4) w.flags[t] = 0u;
+  for (int b = t; b < w.B; b += blockDim.x) {
+    w.smax[b] = 0;
+    w.cut_acc[b] = 0ull;
+  }
+}
 
 // Captures push_launches once into a CUDA graph (needs a stream that can be
 // captured, i.e. not the legacy default stream).  On any failure the context
@@ -335,7 +358,8 @@ extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float*
     if (c->graph_state == 0) build_graph(c);
     if (c->graph_state == 1) {
       SegIO v = {rgb, s, pr, mask, (long long*)(cut ? cut : c->cut_buf)};
-      k_set_io<<<1, 1, 0, c->stream>>>(c->io, v);
+      FrameWords w = {c->sal.smax, c->B, c->mf.cut_acc, c->mf.flags, c->mf.bar};
+      k_set_io<<<1, 32, 0, c->stream>>>(c->io, v, w);
       SEG_CUDA_TRY(cudaGetLastError());
       SEG_CUDA_TRY(cudaGraphLaunch(c->gexec, c->stream));
       return SEG_OK;

@@ -233,9 +233,13 @@ struct GmmDev {
 #define MF_TH 16
 #define MF_THREADS (MF_TW * MF_TH)
 
+// Grid barrier words: the arrival counter and the generation that waiters poll
+// sit in separate 128-byte lines.
 struct GridBar {
   unsigned int count;
+  unsigned int pad0[31];
   unsigned int gen;
+  unsigned int pad1[31];
 };
 
 struct MFArgs {
@@ -336,7 +340,7 @@ int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample);
 // RGB in [0, 255]; io supplies a null rgb / sal_out (RGB8 only); wdev, if set,
 // holds the four channel weights (double) on the device.
 int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegIO* io, const double* wdev,
-            float* sal_out, bool upsample);
+            float* sal_out, bool upsample, bool smax_zeroed = false);
 
 int pt_mom_blocks(int H, int W);
 int pt_launch_salmax(seg_ctx* c, const float* sal);
@@ -359,6 +363,7 @@ int mf_grid_size(int H, int W, int* grid);
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr);
+              const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr,
+              bool words_zeroed = false);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }
