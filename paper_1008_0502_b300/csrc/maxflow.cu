@@ -14,13 +14,14 @@
 //     phase is a set of independent region discharges (each CTA runs up to
 //     local_iters synchronous push / relabel sweeps over its tile in shared
 //     memory; pushes into a neighbouring, idle tile go straight to global
-//     memory).  A grid barrier separates phases.
+//     memory).  A grid barrier separates phases; a colour with no tile that can
+//     hold an active node is skipped, barrier included.
 //  3. Global relabel every gr_every cycles: exact BFS distances to the sink in
 //     the residual graph, computed as a monotone fixpoint (tile-local
 //     relaxation in shared memory, rounds of tiles until no value changes);
 //     unreachable nodes get height INF and never become active again.
-//  4. Stop when a whole cycle does no push and no relabel: no active node is
-//     left, the preflow is maximum.  The minimal source set is then the
+//  4. Stop when no tile of any colour can hold an active node: the preflow is
+//     maximum.  The minimal source set is then the
 //     residual closure of the nodes that still hold excess (their height is
 //     >= N, so they cannot reach t); every minimum cut contains it and it is
 //     itself a minimum cut, so the mask is unique.  The cut value is the flow
@@ -56,6 +57,7 @@ struct MFShared {
   unsigned char b[MF_HN];  // residual bitmasks with halo
   unsigned char z[MF_HN];  // reach flags with halo
   int ok;
+  unsigned int setmask;  // colours of the tiles this CTA pushed into during a phase
 };
 
 __device__ __forceinline__ long long mf_now() {
@@ -291,7 +293,9 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, bool*
           int gv = g + mf_dy(d) * W + mf_dx(d);
           atomicAdd(&a.e[gv], dl);
           atomicAdd(&a.r[(d ^ 1) * N + gv], dl);
-          a.tact[((gy + mf_dy(d)) / MF_TH) * a.ntx + (gx + mf_dx(d)) / MF_TW] = 1;
+          const int nty = (gy + mf_dy(d)) / MF_TH, ntx = (gx + mf_dx(d)) / MF_TW;
+          a.tact[nty * a.ntx + ntx] = 1;
+          atomicOr(&s.setmask, 1u << (((nty & 1) << 1) | (ntx & 1)));  // its colour
         }
       }
       if (ex != e0) {
@@ -422,9 +426,31 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     }
   };
   lap(0);
+  // Phase scheduling.  flag[c]: some tile of colour c may hold an active node.
+  // Every CTA keeps the same copy, updated only from the word the phase's CTAs
+  // OR together before its barrier (bit c': a push entered a tile of colour c';
+  // bit 4: a tile of the discharged colour is still active), so skipping a
+  // colour -- and its barrier -- is decided identically everywhere.  The
+  // preflow is maximum once no colour is flagged.  A global relabel runs first
+  // and then after every 4 * gr_every executed phases.
+  bool flag[4] = {true, true, true, true};
+  int color = 0, executed = 0, since_gr = 0;
+  bool relabel = true;
   for (;;) {
+    int tries = 0;
+    while (tries < 4 && !flag[color]) {
+      color = (color + 1) & 3;
+      ++tries;
+    }
+    if (tries == 4) {
+      converged = true;
+      break;
+    }
+    if (executed >= 4 * a.max_cycles) break;
     // ---- 3. global relabel
-    if (cycle % a.gr_every == 0) {
+    if (relabel || since_gr >= 4 * a.gr_every) {
+      relabel = false;
+      since_gr = 0;
       for (bool first = true;; first = false) {
         mf_flag_begin(a, epoch);
         bool ch = false;
@@ -450,33 +476,39 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
       ++n_gr;
       lap(1);
     }
-    // ---- 2. one cycle of the four colour phases
-    mf_flag_begin(a, epoch);
-    for (int color = 0; color < 4; ++color) {
+    // ---- 2. one colour phase
+    {
+      mf_flag_begin(a, epoch);
+      if (threadIdx.x == 0) s.setmask = 0u;
+      __syncthreads();
       const int cy = color >> 1, cx = color & 1;
       const int ntx_c = (a.ntx - cx + 1) / 2, nty_c = (a.nty - cy + 1) / 2;
       const int ntc = ntx_c * nty_c;
-      bool work = false;
+      bool any_remain = false;
       for (int k = blockIdx.x; k < ntc; k += gridDim.x) {
         const int tx = 2 * (k % ntx_c) + cx, ty = 2 * (k / ntx_c) + cy, t = ty * a.ntx + tx;
         if (!*(volatile unsigned char*)&a.tact[t]) continue;  // no active node can be in it
         bool remain;
-        work |= mf_discharge<ND>(a, s, tx, ty, &remain);
+        mf_discharge<ND>(a, s, tx, ty, &remain);
         __syncthreads();
         if (threadIdx.x == 0) a.tact[t] = remain ? 1 : 0;
+        any_remain |= remain;
       }
-      if (work && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
+      __syncthreads();
+      const unsigned int bits = s.setmask | (any_remain ? 16u : 0u);
+      if (bits && threadIdx.x == 0) atomicOr(&a.flags[epoch % 3], bits);
       if (!mf_grid_sync(a, s)) return;
+      const unsigned int f = mf_flag_read(a, epoch);
+      ++epoch;
+      for (int c2 = 0; c2 < 4; ++c2)
+        if (c2 != color) flag[c2] = flag[c2] || ((f >> c2) & 1u);
+      flag[color] = (f >> 4) & 1u;
+      color = (color + 1) & 3;
+      ++executed;
+      ++since_gr;
+      cycle = (executed + 3) / 4;
     }
     lap(2);
-    unsigned int w = mf_flag_read(a, epoch);
-    ++epoch;
-    ++cycle;
-    if (w == 0u) {
-      converged = true;
-      break;
-    }
-    if (cycle >= a.max_cycles) break;
   }
 
   // ---- 4. minimal source set and cut value (the flow that reached t, per frame
