@@ -127,7 +127,7 @@ def kernels_per_frame(p, H=480, W=640, graph=True):
         dims.append(((h + 1) // 2, (w + 1) // 2))
     tiled = 0
     for l in range(1, p["levels"] - 1):
-        if dims[l + 1][0] * dims[l + 1][1] <= 8192:
+        if dims[l + 1][0] * dims[l + 1][1] <= 2048:
             break
         tiled += 1
     tail = 1 if 1 + tiled < p["levels"] - 1 else 0

@@ -431,20 +431,21 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
 
 // N(v) = a v + b with a = (1 - mbar)^2 / (max - min), b = -min a, where mbar is
 // the mean of the tile maxima of the rescaled map without one copy of its
-// maximum 1; a flat map (range <= flat) gives a = b = 0.
-__device__ __forceinline__ void norm_affine(double mn, double mx, double sum_tmax, int nt,
-                                            double flat, float* ab) {
-  double range = mx - mn;
+// maximum 1; a flat map (range <= flat) gives a = b = 0.  Single precision: the
+// few threads that form it would otherwise hold the whole CTA at its next
+// barrier on the narrow FP64 pipe.
+__device__ __forceinline__ void norm_affine(float mn, float mx, float sum_tmax, int nt, float flat, float* ab) {
+  const float range = mx - mn;
   if (!(range > flat)) {
     ab[0] = 0.f;
     ab[1] = 0.f;
     return;
   }
-  double st = (sum_tmax - nt * mn) / range;
-  double mbar = nt > 1 ? (st - 1.0) / (nt - 1) : 0.0;
-  double a = (1.0 - mbar) * (1.0 - mbar) / range;
-  ab[0] = (float)a;
-  ab[1] = (float)(-mn * a);
+  const float st = (sum_tmax - (float)nt * mn) / range;
+  const float mbar = nt > 1 ? (st - 1.f) / (float)(nt - 1) : 0.f;
+  const float a = (1.f - mbar) * (1.f - mbar) / range;
+  ab[0] = a;
+  ab[1] = -mn * a;
 }
 
 // N(.) of map m = (pair p, channel f) as a*v + b from its statistics.
@@ -453,7 +454,7 @@ __device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* 
   int T = a.tile, nb = (a.hl[c] + T - 1) / T, ntx = (a.wl[c] + T - 1) / T;
   int m = p * a.nch + f;
   const unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * a.nch;
-  double sum = 0.0;
+  float sum = 0.f;
   const float* tp = a.tpart + (size_t)fb * a.nbands_total + a.pair_band_off[p] + f * nb;
   for (int i = 0; i < nb; ++i) sum += tp[i];
   norm_affine(__uint_as_float(mm[2 * m]), __uint_as_float(mm[2 * m + 1]), sum, nb * ntx, flat, ab);
@@ -593,7 +594,7 @@ __device__ void block_norm_multi(const float* const* v, int nm, int h, int w, in
   if ((int)threadIdx.x < nm) {
     const int m = threadIdx.x;
     float a0 = red[(3 * m) * 32], a1 = red[(3 * m + 1) * 32];
-    double a2 = 0.0;
+    float a2 = 0.f;
     for (int i = 0; i < nw; ++i) {
       a0 = fminf(a0, red[(3 * m) * 32 + i]);
       a1 = fmaxf(a1, red[(3 * m + 1) * 32 + i]);
@@ -621,16 +622,31 @@ struct ConspArgs {
 
 // Orientation conspicuity sum_theta N(B_theta), then N of the four conspicuity
 // maps and S = sum_k w_k N(C_k): two normalisation passes of up to 4 maps each.
+// STAGED: the accumulators, C_O and S live in shared memory during the kernel
+// (one load, every later pass at shared-memory latency) and C_O and S are
+// written out at the end.
+template <bool STAGED>
 __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
+  extern __shared__ float dsm[];
   __shared__ float ab[8];
   __shared__ float red[12 * 32];
   __shared__ unsigned tmax[4 * CONSP_TILES];
   const int n = a.h * a.w;
   const int fb = blockIdx.x;  // frame of the batch
   a.acc += (size_t)fb * a.nch * n;
-  a.csum += (size_t)fb * n;
+  float* const csum_g = a.csum + (size_t)fb * n;
+  float* const S_g = a.S + (size_t)fb * n;
   a.consp += (size_t)fb * 4 * n;
-  a.S += (size_t)fb * n;
+  if (STAGED) {
+    for (int i = threadIdx.x; i < a.nch * n; i += blockDim.x) dsm[i] = a.acc[i];
+    a.acc = dsm;
+    a.csum = dsm + (size_t)a.nch * n;
+    a.S = dsm + (size_t)(a.nch + 1) * n;
+    __syncthreads();
+  } else {
+    a.csum = csum_g;
+    a.S = S_g;
+  }
   const float* v[4];
   for (int k0 = 3; k0 < a.nch; k0 += 4) {
     const int nm = min(4, a.nch - k0);
@@ -667,6 +683,12 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   // the output samples of that cell it peaks at its first or last sample row and
   // column.  Only those rows and columns are evaluated (same arithmetic as the
   // up-sampling itself, so the value is identical).
+  if (STAGED) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      csum_g[i] = a.csum[i];
+      S_g[i] = a.S[i];
+    }
+  }
   int* crow = (int*)tmax;
   int* ccol = crow + 2048;
   __shared__ int nr, nc;
@@ -778,6 +800,15 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
     if (2 * hS + 4 > 2048 || 2 * wS + 4 > 2048) return SEG_EINVAL;  // candidate rows / columns of the max
   }
   make_taps(p, s.taps);
+  {
+    // k_consp keeps the nch accumulators, C_O and S in shared memory when they fit
+    const size_t need = sizeof(float) * (s.nch + 2) * (size_t)s.hl[s.sS] * s.wl[s.sS];
+    const size_t cap = 160 * 1024;
+    s.consp_staged = need <= cap && cudaFuncSetAttribute(k_consp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)cap) == cudaSuccess;
+    s.consp_smem = s.consp_staged ? need : 0;
+    cudaGetLastError();
+  }
   size_t off = 0;
   auto take = [&](size_t b) {
     size_t o = off;
@@ -923,7 +954,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   // tiled launches while the produced level is large; one tail launch for the rest
   int tail_from = s.L - 1;
   for (int l = 1; l + 1 < s.L; ++l)
-    if ((long long)s.hl[l + 1] * s.wl[l + 1] <= 8192) {
+    if ((long long)s.hl[l + 1] * s.wl[l + 1] <= 2048) {
       tail_from = l;
       break;
     }
@@ -1034,7 +1065,10 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   pa.salmax = s.salmax;
   pa.frow = s.rs + s.rs_frow;
   pa.fcol = s.rs + s.rs_fcol;
-  k_consp<<<B, 1024, 0, st>>>(pa);
+  if (s.consp_staged)
+    k_consp<true><<<B, 1024, s.consp_smem, st>>>(pa);
+  else
+    k_consp<false><<<B, 1024, 0, st>>>(pa);
   if (upsample) {
     dim3 gu((W + 63) / 64, (H + 3) / 4, B);
     k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,

@@ -185,6 +185,8 @@ struct SalWS {
   float* S;       // combined map at sigma_S
   unsigned* salmax;  // max of the upsampled saliency (float bits)
   int* smax;         // frame max of r+g+b
+  int consp_staged;  // k_consp stages its maps in shared memory
+  size_t consp_smem; // its dynamic shared memory
   GaborTaps taps;
   // resampling tables (seg_rs_entry): per center-surround pair p, rows
   // hl[s]->hl[c] at rs + rs_row[p] and columns wl[s]->wl[c] at rs + rs_col[p];

@@ -61,4 +61,4 @@ def test_single_process_aggregate():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate(2.0, 10, 1) == (5.0, 2.0)
-    assert bench.kernels_per_frame(bench.VGA) == 15
+    assert bench.kernels_per_frame(bench.VGA) == 16
