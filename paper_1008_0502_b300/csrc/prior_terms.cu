@@ -24,7 +24,7 @@
 #define PR_TX 32
 #define PR_TY 16
 #define PR_MAXR 8
-#define MOM_PX 8  // pixels per thread in the moment passes
+#define MOM_PX 2  // pixels per thread in the moment passes (many CTAs: latency-bound loads)
 
 struct PriorArgs {
   float* sal;      // input map, or (from_S) the saliency output (nullable)
