@@ -617,9 +617,10 @@ int mf_grid_size(int H, int W, int* grid) {
   per_sm = per_sm4 < per_sm ? per_sm4 : per_sm;
   if (per_sm < 1) return SEG_ECUDA;
   int ntx = (W + MF_TW - 1) / MF_TW, nty = (H + MF_TH - 1) / MF_TH;
-  int per_color = ((ntx + 1) / 2) * ((nty + 1) / 2);
   int g = per_sm * nsm;
-  *grid = per_color < g ? per_color : g;
+  // every co-resident CTA: a colour phase leaves some idle, but the relabel and
+  // reach rounds (all tiles) spread over all of them
+  *grid = g < ntx * nty ? g : ntx * nty;
   return SEG_OK;
 }
 

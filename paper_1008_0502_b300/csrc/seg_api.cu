@@ -48,8 +48,8 @@ extern "C" int seg_default_params(seg_params* p) {
   p->cap_scale = 1000.0;
   p->neighbourhood = 8;
   p->max_cycles = 20000;
-  p->global_relabel_every = 2;
-  p->local_iters = 16;
+  p->global_relabel_every = 1;
+  p->local_iters = 10;
   p->use_graph = 1;
   p->gmm_components = 1;
   p->em_iters = 5;
