@@ -85,6 +85,7 @@ __device__ bool block_partial_last(const float* v, float* part, unsigned* counte
 __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b);
 
 __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
+  seg_pdl_enter();
   if (a.io) {
     if (!a.sal) a.sal = a.io->sal;
     if (!a.prior) a.prior = a.io->prior;
@@ -324,6 +325,7 @@ __device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M,
 
 __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
                                               const float* __restrict__ prior, int N, MomFinArgs f) {
+  seg_pdl_enter();
   const int fb = blockIdx.y;  // frame of the batch
   rgb += (size_t)fb * 3 * N;
   prior += (size_t)fb * N;
@@ -343,6 +345,7 @@ __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
 
 __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
                                               const float* __restrict__ prior, int N, MomFinArgs f) {
+  seg_pdl_enter();
   if (!rgb) rgb = f.io->rgb;
   if (!prior) prior = f.io->prior;
   const int fb = blockIdx.y;  // frame of the batch
@@ -408,6 +411,7 @@ struct EMArgs {
 // below 1e-6 of the label's total keep their mean and covariance.
 template <int M>
 __global__ void __launch_bounds__(256) k_em_step(EMArgs a) {
+  seg_pdl_enter();
   const int lab = blockIdx.y & 1, fb = blockIdx.y >> 1;
   const GaussDev* gd = a.gauss + fb;
   if (gd->degenerate & (1 << lab)) return;  // uniform over the grid: no partials, no finalise
@@ -506,6 +510,7 @@ __device__ __forceinline__ int32_t quant_cap(float K, float x) {
 }
 
 __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
+  seg_pdl_enter();
   if (!a.rgb) a.rgb = a.io->rgb;
   if (!a.prior) a.prior = a.io->prior;
   __shared__ int sLut[766 * 2];
@@ -602,6 +607,7 @@ int pt_mom_blocks(int H, int W) {
 }
 
 __global__ void k_map_max(const float* __restrict__ v, int n, unsigned* out) {
+  seg_pdl_enter();
   float m = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     m = fmaxf(m, v[i]);
@@ -614,7 +620,7 @@ int pt_launch_salmax(seg_ctx* c, const float* sal) {
   SEG_CUDA_TRY(cudaMemsetAsync(c->sal.salmax, 0, sizeof(unsigned), c->stream));
   int nb = (c->N + 1023) / 1024;
   nb = nb > 1184 ? 1184 : nb;
-  k_map_max<<<nb, 256, 0, c->stream>>>(sal, c->N, c->sal.salmax);
+  SEG_CUDA_TRY(seg_launch(k_map_max, nb, 256, 0, c->stream, sal, c->N, c->sal.salmax));
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }
@@ -657,7 +663,7 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   a.kal_adv = (use_kalman && (rgb_moments || c->io_mode)) ? c->kal : nullptr;
   a.io = c->io_mode ? c->io : nullptr;
   dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY, c->B);
-  k_prior<<<grid, 256, 0, c->stream>>>(a);
+  SEG_CUDA_TRY(seg_launch(k_prior, grid, 256, 0, c->stream, a));
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }
@@ -679,8 +685,8 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   const int M = p.gmm_components;
   fa.gmm = M > 1 ? c->gmm : nullptr;
   fa.M = M;
-  if (first_pass) k_mom1<<<dim3(c->mom_blocks, c->B), 256, 0, st>>>(rgb, prior, N, fa);
-  k_mom2<<<dim3(c->mom_blocks, c->B), 256, 0, st>>>(rgb, prior, N, fa);
+  if (first_pass) SEG_CUDA_TRY(seg_launch(k_mom1, dim3(c->mom_blocks, c->B), 256, 0, st, rgb, prior, N, fa));
+  SEG_CUDA_TRY(seg_launch(k_mom2, dim3(c->mom_blocks, c->B), 256, 0, st, rgb, prior, N, fa));
   if (M > 1) {  // Sec. 4 / Sec. 7.3: EM of the M-component colour mixtures
     EMArgs ea;
     ea.rgb = rgb;
@@ -695,9 +701,9 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     ea.io = c->io_mode ? c->io : nullptr;
     for (int it = 0; it < p.em_iters; ++it) {
       if (M == 2)
-        k_em_step<2><<<dim3(c->mom_blocks, 2 * c->B), 256, 0, st>>>(ea);
+        SEG_CUDA_TRY(seg_launch(k_em_step<2>, dim3(c->mom_blocks, 2 * c->B), 256, 0, st, ea));
       else
-        k_em_step<3><<<dim3(c->mom_blocks, 2 * c->B), 256, 0, st>>>(ea);
+        SEG_CUDA_TRY(seg_launch(k_em_step<3>, dim3(c->mom_blocks, 2 * c->B), 256, 0, st, ea));
     }
   }
   TermsArgs ta;
@@ -719,7 +725,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.gmm = c->gmm;
   ta.M = p.gmm_components;
   dim3 grid((c->W + 31) / 32, (c->H + 7) / 8, c->B);
-  k_terms<<<grid, 256, 0, st>>>(ta);
+  SEG_CUDA_TRY(seg_launch(k_terms, grid, 256, 0, st, ta));
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }

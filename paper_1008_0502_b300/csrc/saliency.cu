@@ -41,6 +41,7 @@ __constant__ float c_binom[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
 template <typename TIn>
 __global__ void k_rgb_max(const TIn* __restrict__ rgb, int n, int* smax, unsigned* mm,
                           int nmaps, const SegIO* io) {
+  seg_pdl_enter();
   if constexpr (std::is_same<TIn, uint8_t>::value) {
     if (!rgb) rgb = io->rgb;
   }
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
                                                       float* __restrict__ I1, float* __restrict__ RG1,
                                                       float* __restrict__ BY1, int h1, int w1,
                                                       const SegIO* io) {
+  seg_pdl_enter();
   constexpr bool U8 = std::is_same<TIn, uint8_t>::value;
   if constexpr (U8) {
     if (!rgb) rgb = io->rgb;
@@ -187,6 +189,7 @@ struct Reduce3Args {
 
 // One REDUCE step of one channel per CTA (blockIdx.z = channel + 3 * frame).
 __global__ void __launch_bounds__(256) k_reduce3(Reduce3Args a) {
+  seg_pdl_enter();
   __shared__ float sF[RED_IN_Y][RED_IN_X];
   __shared__ float sH[RED_IN_Y][RED_TX];
   const int ch = blockIdx.z % 3, fb = blockIdx.z / 3;
@@ -226,6 +229,7 @@ struct PyrTailArgs {
 };
 
 __global__ void __launch_bounds__(1024) k_pyr_tail(PyrTailArgs a) {
+  seg_pdl_enter();
   const int ch = blockIdx.x % 3, fb = blockIdx.x / 3;
   for (int l = a.from; l < a.to; ++l) {
     const int h = a.hl[l], w = a.wl[l], h2 = a.hl[l + 1], w2 = a.wl[l + 1];
@@ -268,6 +272,7 @@ struct GaborArgs {
 // Sec. 7.2 (edge orientation): O(sigma, theta) = |k_theta * I(sigma)| with the
 // zero-mean complex Gabor factored into two separable complex terms.
 __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
+  seg_pdl_enter();
   __shared__ float sIn[GB_IN_Y][GB_IN_X];
   __shared__ float sH0[GB_IN_Y][GB_TX];
   __shared__ float sHr[GB_IN_Y][GB_TX], sHi[GB_IN_Y][GB_TX];
@@ -354,6 +359,7 @@ struct CSArgs {
 // float bit patterns order like the values for the global min/max atomics.
 template <int NCH, int CPB>
 __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
+  seg_pdl_enter();
   __shared__ float sMin[8][CPB], sMax[8][CPB], sTs[8][CPB];
   constexpr int G = NCH / CPB;  // channel groups per (pair, band)
   const int f0 = (blockIdx.x % G) * CPB;
@@ -471,6 +477,7 @@ __device__ void cs_map_affine(const CSArgs& a, int p, int f, float flat, float* 
 template <int NCH, int CPB>
 __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* __restrict__ prev, int hp,
                                                   int wp, float* __restrict__ out) {
+  seg_pdl_enter();
   __shared__ float sP[2 * ACC_TY + 3][2 * ACC_TX + 3];
   __shared__ float sH[2 * ACC_TY + 3][ACC_TX];
   __shared__ float sab[2 * ACC_MAX_PC * CPB];  // N(.) of this CTA's maps as a*v + b
@@ -627,6 +634,7 @@ struct ConspArgs {
 // written out at the end.
 template <bool STAGED>
 __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
+  seg_pdl_enter();
   extern __shared__ float dsm[];
   __shared__ float ab[8];
   __shared__ float red[12 * 32];
@@ -714,6 +722,7 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
 __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, int hs, int ws, int H,
                                                   int W, float* __restrict__ sal, const SegIO* io,
                                                   const int2* __restrict__ frow, const int2* __restrict__ fcol) {
+  seg_pdl_enter();
   if (!sal) sal = io->sal;
   const int fb = blockIdx.z;  // frame of the batch
   S += (size_t)fb * hs * ws;
@@ -942,14 +951,14 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);
   if (rgb_f32) {
     const float* f = (const float*)rgb;
-    k_rgb_max<float><<<dim3(nb, B), 256, 0, st>>>(f, N, s.smax, s.mm, s.nmaps, nullptr);
-    k_feat_reduce1<float><<<g1, 256, 0, st>>>(f, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
-                                              s.hl[1], s.wl[1], nullptr);
+    SEG_CUDA_TRY(seg_launch(k_rgb_max<float>, dim3(nb, B), 256, 0, st, f, N, s.smax, s.mm, s.nmaps, nullptr));
+    SEG_CUDA_TRY(seg_launch(k_feat_reduce1<float>, g1, 256, 0, st, f, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
+                                              s.hl[1], s.wl[1], nullptr));
   } else {
     const uint8_t* u = (const uint8_t*)rgb;
-    k_rgb_max<uint8_t><<<dim3(nb, B), 256, 0, st>>>(u, N, s.smax, s.mm, s.nmaps, io);
-    k_feat_reduce1<uint8_t><<<g1, 256, 0, st>>>(u, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
-                                                s.hl[1], s.wl[1], io);
+    SEG_CUDA_TRY(seg_launch(k_rgb_max<uint8_t>, dim3(nb, B), 256, 0, st, u, N, s.smax, s.mm, s.nmaps, io));
+    SEG_CUDA_TRY(seg_launch(k_feat_reduce1<uint8_t>, g1, 256, 0, st, u, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
+                                                s.hl[1], s.wl[1], io));
   }
   // tiled launches while the produced level is large; one tail launch for the rest
   int tail_from = s.L - 1;
@@ -969,7 +978,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     ra.h2 = s.hl[l + 1];
     ra.w2 = s.wl[l + 1];
     dim3 g((ra.w2 + RED_TX - 1) / RED_TX, (ra.h2 + RED_TY - 1) / RED_TY, 3 * B);
-    k_reduce3<<<g, 256, 0, st>>>(ra);
+    SEG_CUDA_TRY(seg_launch(k_reduce3, g, 256, 0, st, ra));
   }
   if (tail_from < s.L - 1) {
     PyrTailArgs ta;
@@ -981,7 +990,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     }
     ta.from = tail_from;
     ta.to = s.L - 1;
-    k_pyr_tail<<<3 * B, 1024, 0, st>>>(ta);
+    SEG_CUDA_TRY(seg_launch(k_pyr_tail, 3 * B, 1024, 0, st, ta));
   }
   GaborArgs ga;
   memset(&ga, 0, sizeof(ga));
@@ -1000,7 +1009,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     tot += ((s.wl[l] + GB_TX - 1) / GB_TX) * ((s.hl[l] + GB_TY - 1) / GB_TY);
   }
   ga.blk_off[s.s_max - s.c_min + 1] = tot;
-  k_gabor<<<dim3(tot, B, B == 1 ? s.no : 1), 256, 0, st>>>(ga, s.taps);
+  SEG_CUDA_TRY(seg_launch(k_gabor, dim3(tot, B, B == 1 ? s.no : 1), 256, 0, st, ga, s.taps));
   CSArgs ca;
   fill_cs_args(s, ca);
   {
@@ -1012,9 +1021,9 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
 #define SEG_CS_STATS(n)                                 \
   case n:                                               \
     if (per_ch)                                         \
-      k_cs_stats<n, 1><<<g, 256, 0, st>>>(ca);          \
+      SEG_CUDA_TRY(seg_launch(k_cs_stats<n, 1>, g, 256, 0, st, ca));          \
     else                                                \
-      k_cs_stats<n, n><<<g, 256, 0, st>>>(ca);          \
+      SEG_CUDA_TRY(seg_launch(k_cs_stats<n, n>, g, 256, 0, st, ca));          \
     break;
       SEG_CS_STATS(4) SEG_CS_STATS(5) SEG_CS_STATS(6) SEG_CS_STATS(7)
       SEG_CS_STATS(8) SEG_CS_STATS(9) SEG_CS_STATS(10) SEG_CS_STATS(11)
@@ -1033,9 +1042,9 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
 #define SEG_CS_ACC(n)                                                          \
   case n:                                                                      \
     if (per_ch)                                                                \
-      k_cs_accum<n, 1><<<g, 256, 0, st>>>(ca, cc, prev, hp, wp, s.acc[cur]);   \
+      SEG_CUDA_TRY(seg_launch(k_cs_accum<n, 1>, g, 256, 0, st, ca, cc, prev, hp, wp, s.acc[cur]));   \
     else                                                                       \
-      k_cs_accum<n, n><<<g, 256, 0, st>>>(ca, cc, prev, hp, wp, s.acc[cur]);   \
+      SEG_CUDA_TRY(seg_launch(k_cs_accum<n, n>, g, 256, 0, st, ca, cc, prev, hp, wp, s.acc[cur]));   \
     break;
       SEG_CS_ACC(4) SEG_CS_ACC(5) SEG_CS_ACC(6) SEG_CS_ACC(7)
       SEG_CS_ACC(8) SEG_CS_ACC(9) SEG_CS_ACC(10) SEG_CS_ACC(11)
@@ -1066,13 +1075,13 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   pa.frow = s.rs + s.rs_frow;
   pa.fcol = s.rs + s.rs_fcol;
   if (s.consp_staged)
-    k_consp<true><<<B, 1024, s.consp_smem, st>>>(pa);
+    SEG_CUDA_TRY(seg_launch(k_consp<true>, B, 1024, s.consp_smem, st, pa));
   else
-    k_consp<false><<<B, 1024, 0, st>>>(pa);
+    SEG_CUDA_TRY(seg_launch(k_consp<false>, B, 1024, 0, st, pa));
   if (upsample) {
     dim3 gu((W + 63) / 64, (H + 3) / 4, B);
-    k_upsample<<<gu, 256, 0, st>>>(s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,
-                                   s.rs + s.rs_fcol);
+    SEG_CUDA_TRY(seg_launch(k_upsample, gu, 256, 0, st, s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,
+                                   s.rs + s.rs_fcol));
   }
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;

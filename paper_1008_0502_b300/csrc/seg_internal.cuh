@@ -18,6 +18,32 @@
 #define SEG_MAX_MAPS (SEG_MAX_PAIRS * (3 + SEG_MAX_ORIENT))
 #define SEG_INF_H 0x3fffffff
 
+// Programmatic dependent launch: the frame's kernels are launched with
+// programmatic stream serialisation, so each one is scheduled while its
+// predecessor is still running.  Each such kernel first waits for its
+// predecessor's completion and memory (griddepcontrol.wait: a no-op without a
+// programmatic dependency), then lets its own successor be scheduled.
+__device__ __forceinline__ void seg_pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t seg_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                     cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 #define SEG_CUDA_TRY(expr)                   \
   do {                                       \
     cudaError_t _e = (expr);                 \
