@@ -108,13 +108,21 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     a.part += (size_t)fb * a.part_stride;
     a.counter += fb;
   }
-  double wf = a.wf_host;
-  if (a.kal) {
-    int t = a.kal->t;
-    double P = a.kal->P;
-    wf = t == 0 ? 0.0 : a.a / (a.a + a.b + P);  // Sec. 6: weight on f(A_{t-1})
+  // Sec. 6: weight on f(A_{t-1}), formed once per CTA (FP64 division on one
+  // thread; every thread dividing would queue on the narrow FP64 pipe)
+  __shared__ float s_wf;
+  if (threadIdx.x == 0) {
+    double wf = a.wf_host;
+    if (a.kal) {
+      int t = a.kal->t;
+      double P = a.kal->P;
+      wf = t == 0 ? 0.0 : a.a / (a.a + a.b + P);
+    }
+    s_wf = (float)wf;
   }
-  const float wff = (float)wf;
+  __syncthreads();
+  const float wff = s_wf;
+  const double wf = wff;
   const int X0 = blockIdx.x * PR_TX, Y0 = blockIdx.y * PR_TY;
   const int R = a.fR, iny = PR_TY + 2 * R;
   const bool use_f = wf != 0.0 && a.prev != nullptr;
