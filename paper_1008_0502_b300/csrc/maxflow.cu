@@ -127,6 +127,8 @@ __device__ bool mf_tile_dirty(const MFArgs& a, MFShared& s, int tx, int ty, int 
 // ---------------------------------------------------------------- BFS to the sink
 // d(u) = 1 if u has residual to t, else 1 + min over residual arcs u->v of d(v):
 // relaxed to the local fixpoint with the halo fixed at its current global value.
+// Returns whether a node on the tile's rim changed (the only change other tiles
+// can see): a round in which no rim changed anywhere is the global fixpoint.
 // first: the round that starts a global relabel -- the initial distances (1 on
 // nodes with a residual arc to t, INF elsewhere) and the residual bitmasks are
 // formed here from rt and r (no separate pass and grid barrier), and every node
@@ -157,6 +159,7 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool f
     }
   }
   __syncthreads();
+  const int h0 = s.h[hi];
   bool any = false;
   for (;;) {
     int ch = 0;
@@ -174,11 +177,13 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool f
     any = true;
   }
   if (valid && (any || first)) a.h[g] = s.h[hi];
-  __syncthreads();  // the next tile reuses the shared arrays
-  return any;
+  // only a change on the tile's rim is seen by other tiles (their halo)
+  const bool rim = ly == 0 || ly == MF_TH - 1 || lx == 0 || lx == MF_TW - 1;
+  return __syncthreads_or(valid && rim && s.h[hi] != h0) != 0;  // (also orders the next tile's reuse)
 }
 
 // z(v) = 1 if some residual arc u->v has z(u) = 1 (pull form, halo bitmasks).
+// Returns whether a node on the tile's rim changed, as mf_tile_bfs.
 // first: the first round -- the seeds (z = 1 where excess remains) and the
 // residual bitmasks of the tile and its halo come from e and r (no separate pass
 // and grid barrier), and every node of the tile is written.
@@ -209,6 +214,7 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool
   const bool valid = gy < a.H && gx < a.W;
   const int hi = (ly + 1) * MF_HX + lx + 1;
   __syncthreads();
+  const unsigned char z0 = s.z[hi];
   bool any = false;
   for (;;) {
     int ch = 0;
@@ -229,8 +235,8 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool
   }
   if (valid && (any || first)) a.z[gy * a.W + gx] = s.z[hi];
   if (valid && first) a.rm[gy * a.W + gx] = s.b[hi];
-  __syncthreads();  // the next tile reuses the shared arrays
-  return any;
+  const bool rim = ly == 0 || ly == MF_TH - 1 || lx == 0 || lx == MF_TW - 1;
+  return __syncthreads_or(valid && rim && s.z[hi] != z0) != 0;  // (also orders the next tile's reuse)
 }
 
 // ---------------------------------------------------------------- region discharge
