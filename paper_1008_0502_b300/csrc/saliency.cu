@@ -345,6 +345,7 @@ struct CSArgs {
   unsigned* mm;
   float* tpart;
   float flat;  // N(.) flat-map threshold
+  int c_lo, c_hi;  // center scales c_min .. c_max (= sigma_S)
   const int2* rs;
   int rs_row[SEG_MAX_PAIRS], rs_col[SEG_MAX_PAIRS];
 };
@@ -549,6 +550,97 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
   if (in)
 #pragma unroll
     for (int f = 0; f < CPB; ++f) out[(size_t)(f0 + f) * hc * wc + (size_t)y * wc + x] = acc[f];
+}
+
+// ------------------------------------------------------------------ fused across-scale sum
+// B_{c_max} over one 16 x 8 tile of sigma_S per CTA (one channel, one frame),
+// level by level from c_min over the tile's halo regions: the region of level
+// c_max - k starts at 2^k (Y0, X0) - 3 (2^k - 1) and holds 2^k 8 + 3 (2^k - 1)
+// rows (resp. 16 columns), each entry at its clamped level coordinate, so every
+// REDUCE input the next level needs is in shared memory.  Same sums as the
+// level-by-level kernel: B_c = sum over pairs (c, s) of N(CS(c, s)) + REDUCE(B_{c-1}).
+// Up to two REDUCE steps (c_max - c_min <= 2).
+#define FA_TX 16
+#define FA_TY 8
+#define FA_N(t, k) (((t) << (k)) + 3 * ((1 << (k)) - 1))
+
+__device__ __forceinline__ float fa_eval(const CSArgs& a, const float* sab, int c, int f, int fb, int y, int x) {
+  float acc = 0.f;
+  for (int p = 0; p < a.npairs; ++p) {
+    if (a.pair_c[p] != c) continue;
+    const int sv = a.pair_s[p], hs = a.hl[sv], ws = a.wl[sv];
+    const float u = seg_bilinear_t(a.X[f][sv] + (size_t)fb * hs * ws, ws, a.rs[a.rs_row[p] + y], a.rs[a.rs_col[p] + x]);
+    const float v0 = a.X[f][c][(size_t)fb * a.hl[c] * a.wl[c] + (size_t)y * a.wl[c] + x];
+    const float v = (a.opp_sum && (f == 1 || f == 2)) ? fabsf(v0 + u) : fabsf(v0 - u);
+    acc += sab[2 * p] * v + sab[2 * p + 1];
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(1024) k_cs_accum_fused(CSArgs a, float* __restrict__ out) {
+  seg_pdl_enter();
+  __shared__ float sR2[FA_N(FA_TY, 2) * FA_N(FA_TX, 2)];  // region two levels below sigma_S
+  __shared__ float sR1[FA_N(FA_TY, 1) * FA_N(FA_TX, 1)];  // one level below
+  __shared__ float sT[FA_N(FA_TY, 2) * FA_N(FA_TX, 1)];   // horizontal REDUCE pass
+  __shared__ float sab[2 * SEG_MAX_PAIRS];
+  const int f = blockIdx.z % a.nch, fb = blockIdx.z / a.nch;
+  const int cmax = a.c_hi, D = a.c_hi - a.c_lo;
+  for (int p = threadIdx.x; p < a.npairs; p += blockDim.x) cs_map_affine(a, p, f, a.flat, &sab[2 * p], fb);
+  int RY[3], RX[3], NY[3], NX[3];
+  RY[0] = blockIdx.y * FA_TY;
+  RX[0] = blockIdx.x * FA_TX;
+  NY[0] = FA_TY;
+  NX[0] = FA_TX;
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    RY[k] = 2 * RY[k - 1] - 2;
+    RX[k] = 2 * RX[k - 1] - 2;
+    NY[k] = 2 * NY[k - 1] + 3;
+    NX[k] = 2 * NX[k - 1] + 3;
+  }
+  float* const buf[3] = {nullptr, sR1, sR2};
+  __syncthreads();
+  for (int k = D; k >= 0; --k) {
+    const int c = cmax - k, hc = a.hl[c], wc = a.wl[c];
+    if (k < D) {
+      // horizontal pass of REDUCE(B_{c-1}): rows of the finer region x this region's columns
+      const int hf = a.hl[c - 1], wf = a.wl[c - 1];
+      const float* F = buf[k + 1];
+      for (int i = threadIdx.x; i < NY[k + 1] * NX[k]; i += blockDim.x) {
+        const int r = i / NX[k], q = i - r * NX[k];
+        const int xc = seg_clampi(RX[k] + q, 0, wc - 1);
+        const float* row = F + r * NX[k + 1];
+        float h = 0.f;
+#pragma unroll
+        for (int t = 0; t < 5; ++t)
+          h += c_binom[t] * row[seg_clampi(seg_clampi(2 * xc + t - 2, 0, wf - 1) - RX[k + 1], 0, NX[k + 1] - 1)];
+        sT[i] = h;
+      }
+      (void)hf;
+      __syncthreads();
+    }
+    const int n = NY[k] * NX[k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = i / NX[k], q = i - r * NX[k];
+      const int yy = RY[k] + r, xx = RX[k] + q;
+      if (k == 0 && (yy >= hc || xx >= wc)) continue;
+      const int y = seg_clampi(yy, 0, hc - 1), x = seg_clampi(xx, 0, wc - 1);
+      float v = fa_eval(a, sab, c, f, fb, y, x);
+      if (k < D) {
+        const int hf = a.hl[c - 1];
+        float s2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < 5; ++t)
+          s2 += c_binom[t] * sT[seg_clampi(seg_clampi(2 * y + t - 2, 0, hf - 1) - RY[k + 1], 0, NY[k + 1] - 1) * NX[k] + q];
+        v += s2;
+      }
+      if (k == 0)
+        out[((size_t)fb * a.nch + f) * hc * wc + (size_t)y * wc + x] = v;
+      else
+        buf[k][i] = v;
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ conspicuity, S
@@ -929,6 +1021,8 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
   a.mm = s.mm;
   a.tpart = s.tpart;
   a.flat = s.flat;
+  a.c_lo = s.c_min;
+  a.c_hi = s.c_max;
   a.rs = s.rs;
   for (int i = 0; i < s.npairs; ++i) {
     a.rs_row[i] = s.rs_row[i];
@@ -1035,7 +1129,13 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;
-  for (int cc = s.c_min; cc <= s.c_max; ++cc) {
+  if (s.c_max - s.c_min <= 2) {
+    // one launch: every tile of sigma_S rebuilds its halo regions of the lower scales
+    const dim3 g((s.wl[s.sS] + FA_TX - 1) / FA_TX, (s.hl[s.sS] + FA_TY - 1) / FA_TY, s.nch * B);
+    SEG_CUDA_TRY(seg_launch(k_cs_accum_fused, g, 1024, 0, st, ca, s.acc_final));
+    prev = s.acc_final;
+  }
+  for (int cc = s.c_min; cc <= s.c_max && s.c_max - s.c_min > 2; ++cc) {
     const bool per_ch = B == 1;
     dim3 g((s.wl[cc] + ACC_TX - 1) / ACC_TX, (s.hl[cc] + ACC_TY - 1) / ACC_TY, B * (per_ch ? s.nch : 1));
     switch (s.nch) {
