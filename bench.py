@@ -119,7 +119,7 @@ def peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
-def kernels_per_frame(p, H=480, W=640, graph=True):
+def kernels_per_frame(p, H=480, W=640, graph=True, pipeline=False):
     """Kernels one seg_push_frame launches (memsets excluded), as the library sequences them."""
     dims = [(H, W)]
     for _ in range(p["levels"] - 1):
@@ -134,7 +134,8 @@ def kernels_per_frame(p, H=480, W=640, graph=True):
     # rgb max, features + first REDUCE, tiled REDUCEs, tail, Gabor, cs stats,
     # one accumulation per center scale, conspicuity
     sal = 2 + tiled + tail + 1 + 1 + (p["c_max"] - p["c_min"] + 1) + 1
-    return sal + 3 + 1 + (1 if graph else 0)  # prior, moments, terms; min cut; frame-pointer record
+    # prior, moments, terms; min cut; frame-pointer record(s): one per captured half
+    return sal + 3 + 1 + (1 if graph else 0) + (1 if graph and pipeline else 0)
 
 
 def cpu_baseline(clip, seconds, max_frames=None):
@@ -423,45 +424,67 @@ def run_b300(a):
     clip = make_clip(a.frames)
     clip_dev = torch.from_numpy(clip).cuda()
     p = seg.params_from(VGA)
-    sg = seg.Segmenter(H, W, p)
-    sal, pr, mask, cut = sg.empty_outputs()
-    st = sg.stream
-    for i in range(a.warmup):
-        f = i % len(clip)
-        if f == 0:
-            sg.reset()
-        sg.push_frame(clip_dev[f], sal, pr, mask, cut)
-    code, _ = sg.sync()
     if ws > 1:
         import torch.distributed as dist
-        dist.barrier()
-    # timed region: per-frame CUDA graph replays on the context's stream, one
-    # event pair per frame for the latency distribution
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    clk = Clocks(local)
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(st)
-    for i in range(a.steps):
-        f = (a.warmup + i) % len(clip)
-        if f == 0:
-            sg.reset()
-        evs[i][0].record(st)
-        sg.push_frame(clip_dev[f], sal, pr, mask, cut)
-        evs[i][1].record(st)
-    ev1.record(st)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = clk.stop()
-    code, _ = sg.sync()
-    if code != 0:
-        raise RuntimeError(f"device status {seg.strerror(code)}")
-    value, t = aggregate(ev0.elapsed_time(ev1) / 1e3, a.steps, ws, device="cuda")
-    lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+
+    def timed_pass(pipeline, clocks=False):
+        """W warm-up frames, then K timed frames (CUDA graph replays, pipelined or not) on
+        the context's stream; one event pair per frame on that stream."""
+        sg = seg.Segmenter(H, W, p, pipeline=pipeline)
+        sal, pr, mask, cut = sg.empty_outputs()
+        st = sg.stream
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        # the clock sampler starts first; the warm-up frames keep the GPU busy while it
+        # comes up (an idle gap before the timed frames lets the clocks drop)
+        clk = Clocks(local) if clocks else None
+        t_w = time.perf_counter()
+        i = 0
+        while i < a.warmup or (clocks and time.perf_counter() - t_w < 0.3):
+            f = i % len(clip)
+            if f == 0:
+                sg.reset()
+            sg.push_frame(clip_dev[f], sal, pr, mask, cut)
+            i += 1
+            if i % 50 == 0:
+                sg.outputs_ready()
+                torch.cuda.current_stream().synchronize()
+        sg.outputs_ready()
+        sg.sync()
+        if ws > 1:
+            dist.barrier()
+        sg.reset()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(st)
+        for i in range(a.steps):
+            f = i % len(clip)
+            if f == 0 and i > 0:
+                sg.reset()
+            evs[i][0].record(st)
+            sg.push_frame(clip_dev[f], sal, pr, mask, cut)
+            evs[i][1].record(st)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ck = clk.stop() if clk else None
+        code, _ = sg.sync()
+        if code != 0:
+            raise RuntimeError(f"device status {seg.strerror(code)}")
+        v, tt = aggregate(ev0.elapsed_time(ev1) / 1e3, a.steps, ws, device="cuda")
+        lt = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+        sg.close()
+        return v, tt, lt, ck
+
+    # headline: pipelined frames (frame t's saliency overlaps frame t-1's prior, terms
+    # and cut; same results bit for bit); then the same frames unpipelined, whose
+    # per-frame event pairs give the full per-frame latency
+    value, t, period, clocks = timed_pass(True, clocks=True)
+    value_plain, _, lat, _ = timed_pass(False)
+    sg = seg.Segmenter(H, W, p)
+    sal, pr, mask, cut = sg.empty_outputs()
 
     # per-stage split and min-cut statistics: a second pass over the clip with
     # events between the stages (eager launches)
@@ -510,7 +533,10 @@ def run_b300(a):
         "config": {"workload": WORKLOAD, "H": H, "W": W, "frames": a.frames, "parallelism": "replicas",
                    "l2": "inputs larger than L2 (276 MB resident clip, cycled)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
+                       "max": float(lat.max()), "of": "unpipelined frames (full per-frame device time)"},
+        "pipelined": {"frames_per_s": value, "frame_period_ms": {"p50": float(np.percentile(period, 50)),
+                      "p99": float(np.percentile(period, 99))},
+                      "unpipelined_frames_per_s": value_plain},
         "stages_ms": dict(zip(names, stage)), "mincut_cycles_mean": cycles,
         "roofline": roof,
         "cpu_baseline": {"value": n_cpu / dt_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
@@ -519,7 +545,7 @@ def run_b300(a):
                 "d2h_bytes_per_step": H * W + 8},
         "batched": batched,
         "serving": serving,
-        "gpu_launches": a.steps * kernels_per_frame(VGA),
+        "gpu_launches": a.steps * kernels_per_frame(VGA, pipeline=True),
         "clocks": clocks,
     }
     print(json.dumps(out))

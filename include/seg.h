@@ -236,6 +236,26 @@ int seg_profile_read(seg_ctx* ctx, double* stage_ms, int* frames, long long* cyc
 int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* cycles, float* frame_ms,
                         int* mincut_stats, int max_frames);
 
+/* Pipelined frames.  A frame's saliency map (Sec. 3) does not depend on the
+ * previous frame -- only its prior does (Sec. 6) -- so with pipelining on, the
+ * saliency of frame t runs on an internal stream while the context stream still
+ * computes frame t-1's prior, terms and cut.  Results are identical to the
+ * unpipelined path, frame order and temporal state are unchanged, and outputs
+ * are valid once the context stream passes them, as for seg_push_frame.
+ * seg_pipeline_enable(ctx, 1) allocates a second buffer for S and the saliency
+ * maximum (even and odd frames alternate) plus the internal stream, and limits
+ * the min cut to one CTA per SM; seg_pipeline_enable(ctx, 0) synchronises and
+ * releases them.  Profiled frames (seg_profile_enable) run unpipelined.
+ * seg_push_frame_ev: as seg_push_frame, where the frame's saliency starts once
+ * `rgb_ready` (a cudaEvent_t recorded after the RGB8 data was written) has
+ * completed -- NULL: once the context stream reaches this call, which gives no
+ * overlap.  The rgb buffer must stay unchanged until the context stream passes
+ * the frame.  Errors as seg_push_frame; seg_pipeline_enable: SEG_ENOMEM,
+ * SEG_ECUDA. */
+int seg_pipeline_enable(seg_ctx* ctx, int on);
+int seg_push_frame_ev(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev, float* prior_dev,
+                      uint8_t* mask_dev, int64_t* cut_dev, void* rgb_ready_event);
+
 /* Size of pyramid level `level` along an n-pixel axis: ceil-halving. */
 int seg_level_dim(int n, int level);
 

@@ -236,9 +236,12 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   return SEG_OK;
 }
 
+static void pipe_free(seg_ctx* c);
+
 extern "C" int seg_destroy(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
   cudaStreamSynchronize(c->stream);
+  pipe_free(c);
   if (c->graph_state == 1) cudaGraphExecDestroy(c->gexec);
   prof_free(c);
   cudaFree(c->arena);
@@ -311,9 +314,15 @@ __global__ void k_set_io(SegIO* io, SegIO v, FrameWords w) {
   }
   if (t < 4) w.flags[t] = 0u;
   for (int b = t; b < w.B; b += blockDim.x) {
-    w.smax[b] = 0;
+    if (w.smax) w.smax[b] = 0;  // (null: the pipelined front zeroes them)
     w.cut_acc[b] = 0ull;
   }
+}
+
+// Front of a pipelined frame: its RGB8 pointer and zeroed frame maxima.
+__global__ void k_set_front(SegIO* io, const uint8_t* rgb, int* smax, int B) {
+  if (threadIdx.x == 0) io->rgb = rgb;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) smax[b] = 0;
 }
 
 // Captures push_launches once into a CUDA graph (needs a stream that can be
@@ -349,9 +358,13 @@ static void prof_mark(seg_ctx* c, int k) {
   if (c->prof_on && c->prof_n < c->prof_cap) cudaEventRecord(c->prof_ev[5 * c->prof_n + k], c->stream);
 }
 
+extern "C" int seg_push_frame_ev(seg_ctx* c, const uint8_t* rgb, float* sal, float* prior, uint8_t* mask,
+                                 int64_t* cut, void* rgb_ready);
+
 extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float* prior, uint8_t* mask,
                               int64_t* cut) {
   if (!c || !rgb || !mask) return SEG_EINVAL;
+  if (c->pipe_on && !c->prof_on) return seg_push_frame_ev(c, rgb, sal, prior, mask, cut, nullptr);
   float* s = sal ? sal : c->sal_buf;
   float* pr = prior ? prior : c->prior_buf;
   if (!c->prof_on) {
@@ -457,12 +470,194 @@ extern "C" int seg_profile_read_ex(seg_ctx* c, double* stage_ms, int* frames, lo
 
 extern "C" int seg_sync(seg_ctx* c, int* cycles) {
   if (!c) return SEG_EINVAL;
+  if (c->pipe_on) SEG_CUDA_TRY(cudaStreamSynchronize(c->s_front));
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
   SEG_CUDA_TRY(cudaMemcpy(c->status_host, c->status, 32, cudaMemcpyDeviceToHost));
   if (cycles) *cycles = c->status_host[1];
   int code = c->status_host[0];
   if (code) SEG_CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
   return code;
+}
+
+// ---------------------------------------------------------------- pipelined frames
+// Frame t's saliency map does not depend on frame t-1 (only its prior does), so
+// it runs on an internal stream ("front") while the context stream finishes
+// frame t-1's prior, terms and min cut ("back").  Even and odd frames write their
+// S and saliency maximum into separate buffers; the front of frame t waits for
+// the back of frame t-2, the last reader of its buffer.
+static void pipe_free(seg_ctx* c) {
+  if (!c->pipe_mem && !c->s_front) return;
+  if (c->s_front) cudaStreamSynchronize(c->s_front);
+  for (int k = 0; k < 2; ++k) {
+    if (c->pipe_graph == 1) {
+      cudaGraphExecDestroy(c->gf[k]);
+      cudaGraphExecDestroy(c->gb[k]);
+    }
+    if (c->ev_front[k]) cudaEventDestroy(c->ev_front[k]);
+    if (c->ev_back[k]) cudaEventDestroy(c->ev_back[k]);
+    c->ev_front[k] = c->ev_back[k] = nullptr;
+  }
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  c->ev_in = nullptr;
+  if (c->s_front) cudaStreamDestroy(c->s_front);
+  c->s_front = nullptr;
+  if (c->pipe_mem) cudaFree(c->pipe_mem);
+  c->pipe_mem = nullptr;
+  c->pipe_on = 0;
+  c->pipe_graph = 0;
+  if (c->mf_grid_full) c->mf_grid = c->mf_grid_full;
+  c->mf_grid_full = 0;
+  c->sal.S = c->pS[0] ? c->pS[0] : c->sal.S;
+  c->sal.salmax = c->psalmax[0] ? c->psalmax[0] : c->sal.salmax;
+}
+
+extern "C" int seg_pipeline_enable(seg_ctx* c, int on) {
+  if (!c) return SEG_EINVAL;
+  if (!on) {
+    SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    pipe_free(c);
+    return SEG_OK;
+  }
+  if (c->pipe_on) return SEG_OK;
+  const size_t nS = (size_t)c->sal.hl[c->sal.sS] * c->sal.wl[c->sal.sS] * c->B;
+  const size_t o_salmax = seg_align(nS * sizeof(float)), o_io = o_salmax + seg_align(c->B * sizeof(unsigned));
+  char* m = nullptr;
+  if (cudaMalloc((void**)&m, o_io + seg_align(sizeof(SegIO))) != cudaSuccess) return SEG_ENOMEM;
+  c->pipe_mem = m;
+  c->pS[0] = c->sal.S;
+  c->psalmax[0] = c->sal.salmax;
+  c->pS[1] = (float*)m;
+  c->psalmax[1] = (unsigned*)(m + o_salmax);
+  c->io_front = (SegIO*)(m + o_io);
+  bool ok = cudaStreamCreateWithFlags(&c->s_front, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k)
+    ok = cudaEventCreateWithFlags(&c->ev_front[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_back[k], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    pipe_free(c);
+    return SEG_ECUDA;
+  }
+  // the min cut keeps one CTA per SM, leaving room for the next frame's saliency
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && nsm > 0 &&
+      c->mf_grid > nsm) {
+    c->mf_grid_full = c->mf_grid;
+    c->mf_grid = nsm;
+  }
+  c->pipe_on = 1;
+  c->pipe_graph = 0;
+  c->pipe_t = 0;
+  return SEG_OK;
+}
+
+static void pipe_select(seg_ctx* c, int k) {
+  c->sal.S = c->pS[k];
+  c->sal.salmax = c->psalmax[k];
+}
+
+// Captures the front and back of even and odd frames (four graphs); on any
+// failure the context stays on eager launches.
+static void pipe_build_graphs(seg_ctx* c) {
+  c->pipe_graph = -1;
+  if (!c->p.use_graph || c->stream == nullptr) return;
+  cudaGraph_t g[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool ok = true;
+  SegIO* io_back = c->io;
+  for (int k = 0; k < 2 && ok; ++k) {
+    pipe_select(c, k);
+    c->io_mode = 1;
+    c->io = c->io_front;
+    ok = cudaStreamBeginCapture(c->s_front, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = ok ? sal_run(c->sal, c->s_front, nullptr, false, c->io_front, nullptr, nullptr, false, true) : 0;
+    ok = cudaStreamEndCapture(c->s_front, &g[2 * k]) == cudaSuccess && ok && !rc && g[2 * k];
+    c->io = io_back;
+    if (ok) ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      rc = pt_launch_prior(c, nullptr, c->prev_mask, 1, 0.0, nullptr, nullptr, true);
+      if (!rc) rc = pt_launch_moments_terms(c, nullptr, nullptr, 0, c->cs, c->ct, c->ncap);
+      if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, nullptr, c->prev_mask, nullptr);
+      ok = cudaStreamEndCapture(c->stream, &g[2 * k + 1]) == cudaSuccess && !rc && g[2 * k + 1];
+    }
+    c->io_mode = 0;
+  }
+  int built = 0;
+  for (int k = 0; k < 2 && ok; ++k) {
+    ok = cudaGraphInstantiate(&c->gf[k], g[2 * k], 0) == cudaSuccess;
+    if (ok) {
+      ++built;
+      ok = cudaGraphInstantiate(&c->gb[k], g[2 * k + 1], 0) == cudaSuccess;
+      if (!ok) cudaGraphExecDestroy(c->gf[k]);
+      else ++built;
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    if (g[i]) cudaGraphDestroy(g[i]);
+  pipe_select(c, 0);
+  if (!ok) {
+    for (int k = 0; 2 * k + 1 < built; ++k) {
+      cudaGraphExecDestroy(c->gf[k]);
+      cudaGraphExecDestroy(c->gb[k]);
+    }
+    cudaGetLastError();
+    return;
+  }
+  c->pipe_graph = 1;
+}
+
+extern "C" int seg_push_frame_ev(seg_ctx* c, const uint8_t* rgb, float* sal, float* prior, uint8_t* mask,
+                                 int64_t* cut, void* rgb_ready) {
+  if (!c || !rgb || !mask) return SEG_EINVAL;
+  if (!c->pipe_on || c->prof_on) {
+    if (rgb_ready) SEG_CUDA_TRY(cudaStreamWaitEvent(c->stream, (cudaEvent_t)rgb_ready, 0));
+    return seg_push_frame(c, rgb, sal, prior, mask, cut);
+  }
+  float* s = sal ? sal : c->sal_buf;
+  float* pr = prior ? prior : c->prior_buf;
+  int64_t* ct = cut ? cut : c->cut_buf;
+  if (c->pipe_graph == 0) pipe_build_graphs(c);
+  const int k = (int)(c->pipe_t & 1);
+  // front: after the frame's data and after the back of frame t-2 (last reader of buffer k)
+  if (rgb_ready) {
+    SEG_CUDA_TRY(cudaStreamWaitEvent(c->s_front, (cudaEvent_t)rgb_ready, 0));
+  } else {
+    SEG_CUDA_TRY(cudaEventRecord(c->ev_in, c->stream));
+    SEG_CUDA_TRY(cudaStreamWaitEvent(c->s_front, c->ev_in, 0));
+  }
+  SEG_CUDA_TRY(cudaStreamWaitEvent(c->s_front, c->ev_back[k], 0));
+  int rc = SEG_OK;
+  if (c->pipe_graph == 1) {
+    k_set_front<<<1, 32, 0, c->s_front>>>(c->io_front, rgb, c->sal.smax, c->B);
+    SEG_CUDA_TRY(cudaGetLastError());
+    SEG_CUDA_TRY(cudaGraphLaunch(c->gf[k], c->s_front));
+  } else {
+    pipe_select(c, k);
+    rc = sal_run(c->sal, c->s_front, rgb, false, nullptr, nullptr, nullptr, false, false);
+  }
+  if (rc) {
+    pipe_select(c, 0);
+    return rc;
+  }
+  SEG_CUDA_TRY(cudaEventRecord(c->ev_front[k], c->s_front));
+  // back, in frame order on the context stream
+  SEG_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_front[k], 0));
+  if (c->pipe_graph == 1) {
+    SegIO v = {rgb, s, pr, mask, (long long*)ct};
+    FrameWords w = {nullptr, c->B, c->mf.cut_acc, c->mf.flags, c->mf.bar};
+    k_set_io<<<1, 32, 0, c->stream>>>(c->io, v, w);
+    SEG_CUDA_TRY(cudaGetLastError());
+    SEG_CUDA_TRY(cudaGraphLaunch(c->gb[k], c->stream));
+  } else {
+    pipe_select(c, k);
+    rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb, true);
+    if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
+    if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, (int64_t*)ct);
+    pipe_select(c, 0);
+    if (rc) return rc;
+  }
+  SEG_CUDA_TRY(cudaEventRecord(c->ev_back[k], c->stream));
+  c->pipe_t++;
+  return SEG_OK;
 }
 
 extern "C" int seg_push_frame_host(seg_ctx* c, const uint8_t* rgb_host, float* sal_host,

@@ -350,6 +350,19 @@ struct seg_ctx {
   int* status_host;  // pinned [8]
   int* flow;            // warm start: nbr/2 planes of B*N n-link flows
   unsigned char* warm;  // [B] flow valid for the stream
+  // pipelined frames (seg_pipeline_enable): frame t+1's saliency on s_front
+  // while frame t's prior, terms and cut run on stream
+  int pipe_on;
+  cudaStream_t s_front;
+  cudaEvent_t ev_front[2], ev_back[2], ev_in;
+  float* pS[2];           // S of even / odd frames ([0] is sal.S)
+  unsigned* psalmax[2];   // saliency maxima of even / odd frames ([0] is sal.salmax)
+  SegIO* io_front;        // the front's frame pointers (graph replays)
+  void* pipe_mem;
+  int pipe_graph;         // 0 not built, 1 ready, -1 eager launches
+  cudaGraphExec_t gf[2], gb[2];
+  unsigned long long pipe_t;
+  int mf_grid_full;       // the min cut's grid before pipelining reduced it
   // optional per-stage timing (seg_profile_enable)
   int prof_on, prof_n, prof_cap;
   cudaEvent_t* prof_ev;  // 5 per frame

@@ -78,6 +78,8 @@ def _load():
         "seg_profile_enable": ([vp, i32], i32),
         "seg_profile_read": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, i32], i32),
         "seg_profile_read_ex": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, vp, i32], i32),
+        "seg_pipeline_enable": ([vp, i32], i32),
+        "seg_push_frame_ev": ([vp, vp, vp, vp, vp, vp, vp], i32),
         "seg_diff_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
         "seg_diff_create": ([vp, i32, i32, i32, P(seg_params), P(vp)], i32),
         "seg_diff_destroy": ([vp], i32),
@@ -157,7 +159,7 @@ class Segmenter:
     """One video stream: owns a seg_ctx (workspace + temporal state) on a CUDA stream."""
 
     def __init__(self, H: int, W: int, params: seg_params | None = None, stream=None, device=None,
-                 batch: int = 1):
+                 batch: int = 1, pipeline: bool = False):
         self.H, self.W, self.B = H, W, batch
         self.device = torch.device(device) if device is not None else torch.device("cuda",
                                                                                    torch.cuda.current_device())
@@ -172,6 +174,12 @@ class Segmenter:
                                         C.byref(h)), "seg_create_batch")
         self.handle = h
         self.nk = self.params.neighbourhood // 2
+        # pipelined frames: frame t's saliency overlaps frame t-1's prior, terms and cut.
+        # push_frame then does not order the caller's stream after the outputs: call
+        # outputs_ready() (or sync()) before using them.
+        self.pipeline = bool(pipeline)
+        if self.pipeline:
+            _check(lib.seg_pipeline_enable(h, 1), "seg_pipeline_enable")
 
     # The context runs on its own stream; every call orders it after the caller's
     # current stream (inputs ready) and the caller's stream after it (outputs ready),
@@ -219,16 +227,33 @@ class Segmenter:
         """One frame of every stream (rgb (H,W,3), or (B,H,W,3) for a batch)."""
         if mask is None:
             saliency, prior, mask, cut = self.empty_outputs()
+        args = (_dev(rgb, torch.uint8, self._shape(3), "rgb"),
+                _dev(saliency, torch.float32, self._shape(), "saliency") if saliency is not None else None,
+                _dev(prior, torch.float32, self._shape(), "prior") if prior is not None else None,
+                _dev(mask, torch.uint8, self._shape(), "mask"),
+                _dev(cut, torch.int64, (self.B,), "cut") if cut is not None else None)
+        if self.pipeline:
+            cur = torch.cuda.current_stream(self.device)
+            ready = torch.cuda.Event()
+            ready.record(cur)  # the frame's data is ready on the caller's stream
+            if cur != self.stream:
+                self.stream.wait_stream(cur)  # outputs: earlier readers on the caller's stream come first
+            _check(lib.seg_push_frame_ev(self.handle, *args, C.c_void_p(ready.cuda_event)), "seg_push_frame_ev")
+            for t in (rgb, saliency, prior, mask, cut):
+                if t is not None:
+                    t.record_stream(self.stream)
+            self._ready_events = getattr(self, "_ready_events", [])[-7:] + [ready]  # keep alive until used
+            return saliency, prior, mask, cut
         cur = self._begin()
-        _check(lib.seg_push_frame(self.handle, _dev(rgb, torch.uint8, self._shape(3), "rgb"),
-                                  _dev(saliency, torch.float32, self._shape(), "saliency") if saliency is not None
-                                  else None,
-                                  _dev(prior, torch.float32, self._shape(), "prior") if prior is not None else None,
-                                  _dev(mask, torch.uint8, self._shape(), "mask"),
-                                  _dev(cut, torch.int64, (self.B,), "cut") if cut is not None else None),
-               "seg_push_frame")
+        _check(lib.seg_push_frame(self.handle, *args), "seg_push_frame")
         self._end(cur)
         return saliency, prior, mask, cut
+
+    def outputs_ready(self, stream=None):
+        """Orders `stream` (default: the current stream) after every frame pushed so far."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if s != self.stream:
+            s.wait_stream(self.stream)
 
     def push_frame_host(self, rgb_host, mask_host, cut_host=None, saliency_host=None, prior_host=None):
         for t in (rgb_host, mask_host, cut_host, saliency_host, prior_host):

@@ -1,0 +1,53 @@
+"""Pipelined frames: a frame's saliency overlaps the previous frame's prior, terms
+and cut.  The results must equal the unpipelined path bit for bit (same kernels,
+same frame order, same temporal state)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1008_0502_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S(cuda_ok):
+    from paper_1008_0502_b300 import build
+    build.build()
+    from paper_1008_0502_b300 import seg
+    return seg
+
+
+def _run(S, p, frames, B, pipeline):
+    H, W = frames.shape[-3:-1]
+    sg = S.Segmenter(H, W, p, batch=B, pipeline=pipeline)
+    outs = []
+    dev = torch.from_numpy(frames).cuda()
+    for t in range(frames.shape[0]):
+        o = sg.empty_outputs()
+        sg.push_frame(dev[t], *o)
+        outs.append(o)
+    sg.outputs_ready()
+    code, _ = sg.sync()
+    assert code == 0
+    sg.close()
+    return [[x.cpu() for x in o] for o in outs]
+
+
+@pytest.mark.parametrize("case", ["vga", "small_b3", "small_eager"])
+def test_pipelined_equals_unpipelined(S, case):
+    if case == "vga":
+        p = S.params_from(O.CONFIG_VGA)
+        frames = np.stack([f for f, _ in synth.clip_vga_frames(9)])
+        B = 1
+    else:
+        p = S.params_from(O.CONFIG_SMALL, use_graph=0 if case == "small_eager" else 1)
+        clips = [synth.clip_small(7, seed=synth.SEED_BASE + 3 + 11 * k)[0] for k in range(3)]
+        B = 3 if case == "small_b3" else 1
+        frames = np.stack(clips, axis=1) if B == 3 else clips[0]
+    a = _run(S, p, frames, B, False)
+    b = _run(S, p, frames, B, True)
+    for t, (x, y) in enumerate(zip(a, b)):
+        for u, v in zip(x, y):
+            assert torch.equal(u, v), t
