@@ -253,6 +253,13 @@ int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* 
  * the frame.  Errors as seg_push_frame; seg_pipeline_enable: SEG_ENOMEM,
  * SEG_ECUDA. */
 int seg_pipeline_enable(seg_ctx* ctx, int on);
+/* Host-buffer frames on a pipelined context, without waiting on the host: the
+ * RGB8 frame (host, B x H x W x 3, pinned for overlap) is copied into a
+ * three-frame device ring, pushed as by seg_push_frame_ev, and the mask (host,
+ * B x H x W) and cut (host, B int64, or NULL) are copied back in frame order.
+ * Results are complete after seg_sync; the host buffers must stay untouched until
+ * then.  Errors: SEG_EINVAL (NULL rgb/mask, pipelining off), as seg_push_frame. */
+int seg_push_frame_host_async(seg_ctx* ctx, const uint8_t* rgb_host, uint8_t* mask_host, int64_t* cut_host);
 int seg_push_frame_ev(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev, float* prior_dev,
                       uint8_t* mask_dev, int64_t* cut_dev, void* rgb_ready_event);
 

@@ -499,6 +499,11 @@ static void pipe_free(seg_ctx* c) {
   }
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   c->ev_in = nullptr;
+  for (int j = 0; j < 3; ++j) {
+    if (c->ev_ring[j]) cudaEventDestroy(c->ev_ring[j]);
+    c->ev_ring[j] = nullptr;
+    c->ring[j] = nullptr;
+  }
   if (c->s_front) cudaStreamDestroy(c->s_front);
   c->s_front = nullptr;
   if (c->pipe_mem) cudaFree(c->pipe_mem);
@@ -521,8 +526,11 @@ extern "C" int seg_pipeline_enable(seg_ctx* c, int on) {
   if (c->pipe_on) return SEG_OK;
   const size_t nS = (size_t)c->sal.hl[c->sal.sS] * c->sal.wl[c->sal.sS] * c->B;
   const size_t o_salmax = seg_align(nS * sizeof(float)), o_io = o_salmax + seg_align(c->B * sizeof(unsigned));
+  const size_t o_ring = o_io + seg_align(sizeof(SegIO)), ring_bytes = seg_align((size_t)3 * c->N * c->B);
   char* m = nullptr;
-  if (cudaMalloc((void**)&m, o_io + seg_align(sizeof(SegIO))) != cudaSuccess) return SEG_ENOMEM;
+  if (cudaMalloc((void**)&m, o_ring + 3 * ring_bytes) != cudaSuccess) return SEG_ENOMEM;
+  for (int j = 0; j < 3; ++j) c->ring[j] = (uint8_t*)(m + o_ring + j * ring_bytes);
+  c->ring_t = 0;
   c->pipe_mem = m;
   c->pS[0] = c->sal.S;
   c->psalmax[0] = c->sal.salmax;
@@ -534,6 +542,8 @@ extern "C" int seg_pipeline_enable(seg_ctx* c, int on) {
     ok = cudaEventCreateWithFlags(&c->ev_front[k], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_back[k], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess;
+  for (int j = 0; j < 3 && ok; ++j)
+    ok = cudaEventCreateWithFlags(&c->ev_ring[j], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     pipe_free(c);
     return SEG_ECUDA;
@@ -657,6 +667,29 @@ extern "C" int seg_push_frame_ev(seg_ctx* c, const uint8_t* rgb, float* sal, flo
   }
   SEG_CUDA_TRY(cudaEventRecord(c->ev_back[k], c->stream));
   c->pipe_t++;
+  return SEG_OK;
+}
+
+// Asynchronous host-buffer frames (pipelined contexts): the RGB8 frame is copied
+// into a slot of a three-frame device ring on the front stream (after the back
+// of the frame that last used the slot), the frame is pushed pipelined, and the
+// mask and cut are copied back on the context stream.  Nothing waits on the
+// host; the host buffers must stay untouched until seg_sync.
+extern "C" int seg_push_frame_host_async(seg_ctx* c, const uint8_t* rgb_host, uint8_t* mask_host,
+                                         int64_t* cut_host) {
+  if (!c || !rgb_host || !mask_host) return SEG_EINVAL;
+  if (!c->pipe_on) return SEG_EINVAL;
+  const size_t N = (size_t)c->N * c->B;
+  const int j = (int)(c->ring_t % 3);
+  SEG_CUDA_TRY(cudaStreamWaitEvent(c->s_front, c->ev_ring[j], 0));
+  SEG_CUDA_TRY(cudaMemcpyAsync(c->ring[j], rgb_host, 3 * N, cudaMemcpyHostToDevice, c->s_front));
+  SEG_CUDA_TRY(cudaEventRecord(c->ev_in, c->s_front));
+  int rc = seg_push_frame_ev(c, c->ring[j], c->sal_buf, c->prior_buf, c->mask_buf, c->cut_buf, c->ev_in);
+  if (rc) return rc;
+  SEG_CUDA_TRY(cudaEventRecord(c->ev_ring[j], c->stream));
+  SEG_CUDA_TRY(cudaMemcpyAsync(mask_host, c->mask_buf, N, cudaMemcpyDeviceToHost, c->stream));
+  if (cut_host) SEG_CUDA_TRY(cudaMemcpyAsync(cut_host, c->cut_buf, 8 * c->B, cudaMemcpyDeviceToHost, c->stream));
+  c->ring_t++;
   return SEG_OK;
 }
 

@@ -363,6 +363,9 @@ struct seg_ctx {
   cudaGraphExec_t gf[2], gb[2];
   unsigned long long pipe_t;
   int mf_grid_full;       // the min cut's grid before pipelining reduced it
+  uint8_t* ring[3];       // RGB8 staging ring of the asynchronous host-buffer entry point
+  cudaEvent_t ev_ring[3]; // back of the frame that last read each slot
+  unsigned long long ring_t;
   // optional per-stage timing (seg_profile_enable)
   int prof_on, prof_n, prof_cap;
   cudaEvent_t* prof_ev;  // 5 per frame

@@ -80,6 +80,7 @@ def _load():
         "seg_profile_read_ex": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, vp, i32], i32),
         "seg_pipeline_enable": ([vp, i32], i32),
         "seg_push_frame_ev": ([vp, vp, vp, vp, vp, vp, vp], i32),
+        "seg_push_frame_host_async": ([vp, vp, vp, vp], i32),
         "seg_diff_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
         "seg_diff_create": ([vp, i32, i32, i32, P(seg_params), P(vp)], i32),
         "seg_diff_destroy": ([vp], i32),
@@ -248,6 +249,15 @@ class Segmenter:
         _check(lib.seg_push_frame(self.handle, *args), "seg_push_frame")
         self._end(cur)
         return saliency, prior, mask, cut
+
+    def push_frame_host_async(self, rgb_host, mask_host, cut_host=None):
+        """Pipelined host-buffer frame: no host wait; results complete after sync().
+        The host buffers must stay untouched until then."""
+        for t in (rgb_host, mask_host, cut_host):
+            if t is not None and (t.device.type != "cpu" or not t.is_contiguous()):
+                raise ValueError("host buffers must be contiguous CPU tensors")
+        _check(lib.seg_push_frame_host_async(self.handle, _ptr(rgb_host), _ptr(mask_host), _ptr(cut_host)),
+               "seg_push_frame_host_async")
 
     def outputs_ready(self, stream=None):
         """Orders `stream` (default: the current stream) after every frame pushed so far."""

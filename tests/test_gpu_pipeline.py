@@ -51,3 +51,21 @@ def test_pipelined_equals_unpipelined(S, case):
     for t, (x, y) in enumerate(zip(a, b)):
         for u, v in zip(x, y):
             assert torch.equal(u, v), t
+
+
+def test_async_host_frames_equal_device_frames(S):
+    p = S.params_from(O.CONFIG_SMALL)
+    frames = synth.clip_small(8, seed=synth.SEED_BASE + 21)[0]
+    ref = _run(S, p, frames, 1, False)
+    sg = S.Segmenter(120, 160, p, pipeline=True)
+    rgb_h = torch.from_numpy(frames).pin_memory()
+    masks = torch.empty(len(frames), 120, 160, dtype=torch.uint8).pin_memory()
+    cuts = torch.empty(len(frames), 1, dtype=torch.int64).pin_memory()
+    for t in range(len(frames)):
+        sg.push_frame_host_async(rgb_h[t], masks[t], cuts[t])
+    code, _ = sg.sync()
+    assert code == 0
+    for t in range(len(frames)):
+        assert torch.equal(masks[t], ref[t][2]), t
+        assert int(cuts[t][0]) == int(ref[t][3][0]), t
+    sg.close()
