@@ -197,8 +197,8 @@ __device__ bool block_partial_last(const float* v, float* part, unsigned* counte
     float s = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][k];
     part[bid * NV + k] = s;
+    __threadfence();  // (only the writers need to fence)
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned prev = atomicAdd(counter, 1u);
@@ -229,7 +229,17 @@ __device__ void reduce_parts(const float* part, int nblocks, double* out) {
     const int k = t >> 5;
     float2 acc = make_float2(0.f, 0.f);
     if (k < NV)
-      for (int b = lane; b < nblocks; b += 32) acc = ff_add(acc, make_float2(((volatile float*)part)[b * NV + k], 0.f));
+      for (int b0 = lane; b0 < nblocks; b0 += 32 * 4) {
+        // four loads in flight (L2 reads: other CTAs' partials are not in this L1)
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int b = b0 + 32 * u;
+          v[u] = b < nblocks ? __ldcg(part + b * NV + k) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = ff_add(acc, make_float2(v[u], 0.f));
+      }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       float2 other;
