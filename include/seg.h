@@ -159,6 +159,12 @@ const char* seg_strerror(int code);
 /* Sec. 3 / Sec. 7.2: saliency map of one frame into saliency_dev (H*W float). */
 int seg_saliency(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev);
 
+/* Sec. 3 / Sec. 7.2: standalone saliency map of one H x W RGB8 frame, without a
+ * context: allocates and frees its own workspace (about 40 B/pixel), enqueues on
+ * `stream` and synchronises it.  Errors as seg_create. */
+int seg_saliency_grid(void* stream, int H, int W, const seg_params* p, const uint8_t* rgb_dev,
+                      float* saliency_dev);
+
 /* Sec. 5 + Sec. 6: p-hat = w_f * f(prev_mask) + (1 - w_f) * q(saliency), with
  * q = saliency / max(saliency) and eps on the border band.  prev_mask_dev may be
  * NULL when w_f == 0. */

@@ -1129,13 +1129,15 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   int cur = 0;
   const float* prev = nullptr;
   int hp = 0, wp = 0;
-  if (s.c_max - s.c_min <= 2) {
+  const bool fused = s.c_max - s.c_min <= 2 && B <= 4;
+  if (fused) {
     // one launch: every tile of sigma_S rebuilds its halo regions of the lower scales
+    // (for larger batches the level-by-level launches have enough CTAs and no halo work)
     const dim3 g((s.wl[s.sS] + FA_TX - 1) / FA_TX, (s.hl[s.sS] + FA_TY - 1) / FA_TY, s.nch * B);
     SEG_CUDA_TRY(seg_launch(k_cs_accum_fused, g, 1024, 0, st, ca, s.acc_final));
     prev = s.acc_final;
   }
-  for (int cc = s.c_min; cc <= s.c_max && s.c_max - s.c_min > 2; ++cc) {
+  for (int cc = s.c_min; cc <= s.c_max && !fused; ++cc) {
     const bool per_ch = B == 1;
     dim3 g((s.wl[cc] + ACC_TX - 1) / ACC_TX, (s.hl[cc] + ACC_TY - 1) / ACC_TY, B * (per_ch ? s.nch : 1));
     switch (s.nch) {

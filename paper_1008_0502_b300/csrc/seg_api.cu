@@ -767,6 +767,26 @@ extern "C" int seg_saliency(seg_ctx* c, const uint8_t* rgb, float* sal) {
   return sal_launch(c, rgb, sal, true);
 }
 
+extern "C" int seg_saliency_grid(void* stream, int H, int W, const seg_params* p, const uint8_t* rgb,
+                                 float* sal) {
+  if (!rgb || !sal) return SEG_EINVAL;
+  int rc = seg_check_params(p, H, W);
+  if (rc) return rc;
+  SalWS s;
+  size_t bytes = 0;
+  rc = sal_layout(s, 1, H, W, *p, &bytes);
+  if (rc) return rc;
+  char* base = nullptr;
+  if (cudaMalloc((void**)&base, bytes) != cudaSuccess) return SEG_ENOMEM;
+  sal_bind(s, base);
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = sal_upload_tables(s);
+  if (!rc) rc = sal_run(s, st, rgb, false, nullptr, nullptr, sal, true);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = SEG_ECUDA;
+  cudaFree(base);
+  return rc;
+}
+
 extern "C" int seg_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, double w_f,
                          float* prior) {
   if (!c || !sal || !prior || !(w_f >= 0.0 && w_f <= 1.0) || c->B != 1) return SEG_EINVAL;

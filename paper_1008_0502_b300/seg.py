@@ -79,6 +79,7 @@ def _load():
         "seg_profile_read": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, i32], i32),
         "seg_profile_read_ex": ([vp, P(C.c_double), P(C.c_int), P(C.c_longlong), vp, vp, i32], i32),
         "seg_pipeline_enable": ([vp, i32], i32),
+        "seg_saliency_grid": ([vp, i32, i32, P(seg_params), vp, vp], i32),
         "seg_push_frame_ev": ([vp, vp, vp, vp, vp, vp, vp], i32),
         "seg_push_frame_host_async": ([vp, vp, vp, vp], i32),
         "seg_diff_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
@@ -357,6 +358,18 @@ class Segmenter:
         out = torch.empty(*shape, dtype=torch.float32)
         _check(lib.seg_debug_copy(self.handle, which, index, _ptr(out), out.numel()), "seg_debug_copy")
         return out
+
+
+def saliency_grid(rgb, params: seg_params | None = None, stream=None, out=None):
+    """Saliency map of one (H, W, 3) uint8 CUDA frame without a context (own workspace)."""
+    H, W = int(rgb.shape[0]), int(rgb.shape[1])
+    p = params if params is not None else default_params()
+    if out is None:
+        out = torch.empty(H, W, dtype=torch.float32, device=rgb.device)
+    st = stream if stream is not None else torch.cuda.current_stream(rgb.device)
+    _check(lib.seg_saliency_grid(C.c_void_p(st.cuda_stream), H, W, C.byref(p), _dev(rgb, torch.uint8, (H, W, 3), "rgb"),
+                                 _dev(out, torch.float32, (H, W), "out")), "seg_saliency_grid")
+    return out
 
 
 def mincut_grid(cs, ct, ncap, max_cycles: int = 0, stream=None):

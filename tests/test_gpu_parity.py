@@ -309,3 +309,17 @@ def test_warm_start_equals_cold_start(S, start):
             assert torch.equal(a, b), t
     warm.close()
     cold.close()
+
+
+def test_saliency_grid_equals_context_saliency(S):
+    """The context-free saliency entry point runs the same kernels."""
+    frames, _ = synth.clip_small(2, seed=synth.SEED_BASE + 77)
+    p = S.params_from(O.CONFIG_SMALL)
+    sg = S.Segmenter(120, 160, p)
+    for f in frames:
+        x = torch.from_numpy(f).cuda()
+        a = sg.saliency(x)
+        b = S.saliency_grid(x, p)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+    sg.close()
