@@ -77,6 +77,34 @@ __device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
   s[7] += p * b;
 }
 
+// Finalisation arithmetic (one or two threads while the rest of the grid has
+// finished).  FP64 divide, square root and log are long dependent sequences on
+// this part's narrow FP64 pipe (hundreds to thousands of cycles each), so they
+// are formed by Newton's iteration from a float seed: reciprocal r <- r (2 - x r)
+// and reciprocal square root y <- y (3 - x y^2) / 2 each square the relative
+// error per step, so two steps take the ~1e-7 seed below the double rounding.
+#define LOG_2PI 1.8378770664093453
+__device__ __forceinline__ double nr_rcp(double x) {
+  if (!(fabs(x) > 1e-30 && fabs(x) < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ double nr_rsqrt(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  const double h = 0.5 * x;
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-h * y, y, 1.5);
+  return y * fma(-h * y, y, 1.5);
+}
+// log x to float accuracy (the results are stored as float): logf of the float
+// rounding xf plus the first-order term of log(x / xf), |x / xf - 1| < 2^-24.
+__device__ __forceinline__ double log_f(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return log(x);
+  const float xf = (float)x;
+  return (double)logf(xf) + (x - (double)xf) * (double)__frcp_rn(xf);
+}
+
 template <int NV>
 __device__ void reduce_parts(const float* part, int nblocks, double* out);
 template <int NV>
@@ -108,15 +136,14 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     a.part += (size_t)fb * a.part_stride;
     a.counter += fb;
   }
-  // Sec. 6: weight on f(A_{t-1}), formed once per CTA (FP64 division on one
-  // thread; every thread dividing would queue on the narrow FP64 pipe)
+  // Sec. 6: weight on f(A_{t-1}), formed once per CTA on one thread
   __shared__ float s_wf;
   if (threadIdx.x == 0) {
     double wf = a.wf_host;
     if (a.kal) {
       int t = a.kal->t;
       double P = a.kal->P;
-      wf = t == 0 ? 0.0 : a.a / (a.a + a.b + P);
+      wf = t == 0 ? 0.0 : a.a * nr_rcp(a.a + a.b + P);
     }
     s_wf = (float)wf;
   }
@@ -177,8 +204,9 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
   }
 }
 
-// Writes this CTA's NV partial sums to part[bid*NV ..] and returns true in
-// every thread of exactly one CTA, the last to finish (threadfence reduction).
+// Writes this CTA's NV partial sums to part[k * nblocks + bid] (value-major, so
+// the final sum reads them coalesced) and returns true in every thread of
+// exactly one CTA, the last to finish (threadfence reduction).
 // A CTA covers at most a few thousand pixels, so its sums are plain FP32; the
 // sum across CTAs (reduce_parts) is an error-free float-float sum, which keeps
 // about 44 bits without the FP64 pipe (narrow on this part).
@@ -196,7 +224,7 @@ __device__ bool block_partial_last(const float* v, float* part, unsigned* counte
   for (int k = threadIdx.x; k < NV; k += blockDim.x) {
     float s = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][k];
-    part[bid * NV + k] = s;
+    part[k * nblocks + bid] = s;
     __threadfence();  // (only the writers need to fence)
   }
   __syncthreads();
@@ -220,34 +248,46 @@ __device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
 }
 
 // Deterministic fixed-order float-float sums of the NV per-CTA partials (one CTA):
-// warp k (mod the CTA's warps) sums value k, lanes striding over the CTAs, then
-// a shuffle tree; out[k] = hi + lo.
+// warp w sums values w, w + nw, .. (G of them in one pass, so their loads are in
+// flight together), lanes striding over the CTAs, then a shuffle tree;
+// out[k] = hi + lo.
 template <int NV>
 __device__ void reduce_parts(const float* part, int nblocks, double* out) {
-  const int lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < ((NV + 7) / 8) * 8 * 32; t += blockDim.x) {
-    const int k = t >> 5;
-    float2 acc = make_float2(0.f, 0.f);
-    if (k < NV)
-      for (int b0 = lane; b0 < nblocks; b0 += 32 * 4) {
-        // four loads in flight (L2 reads: other CTAs' partials are not in this L1)
-        float v[4];
+  constexpr int G = NV <= 8 ? 1 : NV <= 16 ? 2 : 4;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, wid = threadIdx.x >> 5;
+  for (int k0 = wid; k0 < NV; k0 += G * nw) {
+    float2 acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = make_float2(0.f, 0.f);
+    for (int b0 = lane; b0 < nblocks; b0 += 32 * 4) {
+      // L2 reads (other CTAs' partials are not in this L1), 4 G in flight
+      float v[G][4];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int k = k0 + g * nw;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int b = b0 + 32 * u;
-          v[u] = b < nblocks ? __ldcg(part + b * NV + k) : 0.f;
+          v[g][u] = k < NV && b < nblocks ? __ldcg(part + (size_t)k * nblocks + b) : 0.f;
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc = ff_add(acc, make_float2(v[u], 0.f));
       }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      float2 other;
-      other.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
-      other.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
-      acc = lane < (lane ^ o) ? ff_add(acc, other) : ff_add(other, acc);  // same order in both lanes
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[g] = ff_add(acc[g], make_float2(v[g][u], 0.f));
     }
-    if (lane == 0 && k < NV) out[k] = (double)acc.x + (double)acc.y;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float2 other;
+        other.x = __shfl_xor_sync(0xffffffffu, acc[g].x, o);
+        other.y = __shfl_xor_sync(0xffffffffu, acc[g].y, o);
+        acc[g] = lane < (lane ^ o) ? ff_add(acc[g], other) : ff_add(other, acc[g]);  // same order in both lanes
+      }
+      const int k = k0 + g * nw;
+      if (lane == 0 && k < NV) out[k] = (double)acc[g].x + (double)acc[g].y;
+    }
   }
   __syncthreads();
 }
@@ -257,10 +297,11 @@ __device__ void reduce_parts(const float* part, int nblocks, double* out) {
 __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b) {
   g->degenerate = 0;
   for (int lab = 0; lab < 2; ++lab) {
-    double sw = tot[4 * lab];
+    const double sw = tot[4 * lab];
     if (!(sw > 0.0)) g->degenerate |= 1 << lab;
+    const double rsw = sw > 0.0 ? nr_rcp(sw) : 0.0;
     for (int k = 0; k < 3; ++k) {
-      double m = sw > 0.0 ? tot[4 * lab + 1 + k] / sw : 0.0;
+      const double m = tot[4 * lab + 1 + k] * rsw;
       g->mu[lab][k] = m;
       g->muf[lab][k] = (float)m;
     }
@@ -268,29 +309,30 @@ __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, d
   }
   if (kal) {
     double P = kal->P;
-    kal->P = kal->t == 0 ? a : a * (b + P) / (a + b + P);
+    kal->P = kal->t == 0 ? a : a * (b + P) * nr_rcp(a + b + P);
     kal->t += 1;
   }
 }
 
-// Cholesky factor of a 3x3 covariance, the inverse factor (6 floats) and log det.
+// Cholesky factor of a 3x3 covariance (+ 1e-4 I already added), written as
+// the inverse factor L^-1 (6 floats), and log det.  Pivots come from
+// reciprocal square roots (L^-1 is what the data term needs): i_jj = 1/l_jj.
 __device__ double chol_inv(double c00, double c10, double c11, double c20, double c21, double c22, float* li) {
-  double l00 = sqrt(c00);
-  double l10 = c10 / l00, l20 = c20 / l00;
-  double l11 = sqrt(c11 - l10 * l10);
-  double l21 = (c21 - l20 * l10) / l11;
-  double l22 = sqrt(c22 - l20 * l20 - l21 * l21);
-  double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
-  double i10 = -l10 * i00 / l11;
-  double i21 = -l21 * i11 / l22;
-  double i20 = -(l20 * i00 + l21 * i10) / l22;
+  const double i00 = nr_rsqrt(c00);
+  const double l10 = c10 * i00, l20 = c20 * i00;
+  const double i11 = nr_rsqrt(c11 - l10 * l10);
+  const double l21 = (c21 - l20 * l10) * i11;
+  const double i22 = nr_rsqrt(c22 - l20 * l20 - l21 * l21);
+  const double i10 = -l10 * i00 * i11;
+  const double i21 = -l21 * i11 * i22;
+  const double i20 = -(l20 * i00 + l21 * i10) * i22;
   li[0] = (float)i00;
   li[1] = (float)i10;
   li[2] = (float)i11;
   li[3] = (float)i20;
   li[4] = (float)i21;
   li[5] = (float)i22;
-  return 2.0 * log(l00 * l11 * l22);
+  return -2.0 * log_f(i00 * i11 * i22);  // log det = 2 log(l00 l11 l22)
 }
 
 // Covariance + 1e-4 I, Cholesky factor L, L^-1 and 1/2 log det + 3/2 log 2 pi.
@@ -299,45 +341,30 @@ __device__ double chol_inv(double c00, double c10, double c11, double c20, doubl
 // at (m - (M-1)/2) * 1.5 sigma_g, sigma_g^2 = g^T Sigma g, g = (1,1,1)/sqrt3;
 // every covariance = Sigma; every weight = 1/M.
 __device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M, int lab) {
-  {
-    double sw = g->sw[lab];
-    if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
-      for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
-      g->lconst[lab] = 0.f;
-      return;
+  if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
+    for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
+    g->lconst[lab] = 0.f;
+    return;
+  }
+  const double rsw = nr_rcp(g->sw[lab]);
+  const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
+  const double c00 = m[0] * rsw + 1e-4, c10 = m[1] * rsw, c11 = m[2] * rsw + 1e-4;
+  const double c20 = m[3] * rsw, c21 = m[4] * rsw, c22 = m[5] * rsw + 1e-4;
+  const double ld = chol_inv(c00, c10, c11, c20, c21, c22, g->linv[lab]);
+  g->lconst[lab] = (float)(0.5 * ld + 1.5 * LOG_2PI);
+  if (gmm) {
+    GmmDev& q = gmm[lab];
+    // sigma_g / sqrt 3 = sqrt(sg2 / 3), sg2 = g^T Sigma g (> 0: Sigma carries 1e-4 I)
+    const double v = (c00 + c11 + c22 + 2.0 * (c10 + c20 + c21)) * (1.0 / 9.0);
+    const double sd = v * nr_rsqrt(v);
+    const float lw = (float)(log_f(1.0 / M) - 0.5 * ld - 1.5 * LOG_2PI);
+    for (int k = 0; k < M; ++k) {
+      const double off = (k - (M - 1) / 2.0) * 1.5 * sd;
+      for (int j = 0; j < 3; ++j) q.mu[k][j] = (float)(g->mu[lab][j] + off);
+      for (int j = 0; j < 6; ++j) q.linv[k][j] = g->linv[lab][j];
+      q.logdet[k] = ld;
+      q.lc[k] = lw;
     }
-    const double* m = tot + 6 * lab;  // rr, gr, gg, br, bg, bb
-    double c00 = m[0] / sw + 1e-4, c10 = m[1] / sw, c11 = m[2] / sw + 1e-4;
-    double c20 = m[3] / sw, c21 = m[4] / sw, c22 = m[5] / sw + 1e-4;
-    if (gmm) {
-      GmmDev& q = gmm[lab];
-      double sg2 = (c00 + c11 + c22 + 2.0 * (c10 + c20 + c21)) / 3.0;
-      float li[6];
-      double ld = chol_inv(c00, c10, c11, c20, c21, c22, li);
-      for (int k = 0; k < M; ++k) {
-        double off = (k - (M - 1) / 2.0) * 1.5 * sqrt(sg2) / sqrt(3.0);
-        for (int j = 0; j < 3; ++j) q.mu[k][j] = (float)(g->mu[lab][j] + off);
-        for (int j = 0; j < 6; ++j) q.linv[k][j] = li[j];
-        q.logdet[k] = ld;
-        q.lc[k] = (float)(log(1.0 / M) - 0.5 * ld - 1.5 * log(2.0 * M_PI));
-      }
-    }
-    double l00 = sqrt(c00);
-    double l10 = c10 / l00, l20 = c20 / l00;
-    double l11 = sqrt(c11 - l10 * l10);
-    double l21 = (c21 - l20 * l10) / l11;
-    double l22 = sqrt(c22 - l20 * l20 - l21 * l21);
-    double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
-    double i10 = -l10 * i00 / l11;
-    double i21 = -l21 * i11 / l22;
-    double i20 = -(l20 * i00 + l21 * i10) / l22;
-    g->linv[lab][0] = (float)i00;
-    g->linv[lab][1] = (float)i10;
-    g->linv[lab][2] = (float)i11;
-    g->linv[lab][3] = (float)i20;
-    g->linv[lab][4] = (float)i21;
-    g->linv[lab][5] = (float)i22;
-    g->lconst[lab] = (float)(log(l00 * l11 * l22) + 1.5 * log(2.0 * M_PI));
   }
 }
 
@@ -489,18 +516,20 @@ __global__ void __launch_bounds__(256) k_em_step(EMArgs a) {
     if (threadIdx.x == 0) {
       double ntot = 0.0;
       for (int m = 0; m < M; ++m) ntot += tot[10 * m];
+      const double rtot = nr_rcp(ntot);
       for (int m = 0; m < M; ++m) {
         const double* t = tot + 10 * m;
-        const double nm = t[0], pim = nm / ntot;
+        const double nm = t[0], pim = nm * rtot;
         double ld = g->logdet[m];
         if (nm >= 1e-6 * ntot) {
-          double dx = t[1] / nm, dy = t[2] / nm, dz = t[3] / nm;
+          const double rn = nr_rcp(nm);
+          double dx = t[1] * rn, dy = t[2] * rn, dz = t[3] * rn;
           for (int k = 0; k < 3; ++k) g->mu[m][k] = (float)((double)mu[m][k] + (k == 0 ? dx : k == 1 ? dy : dz));
-          ld = chol_inv(t[4] / nm - dx * dx + 1e-4, t[5] / nm - dy * dx, t[6] / nm - dy * dy + 1e-4,
-                        t[7] / nm - dz * dx, t[8] / nm - dz * dy, t[9] / nm - dz * dz + 1e-4, g->linv[m]);
+          ld = chol_inv(t[4] * rn - dx * dx + 1e-4, t[5] * rn - dy * dx, t[6] * rn - dy * dy + 1e-4,
+                        t[7] * rn - dz * dx, t[8] * rn - dz * dy, t[9] * rn - dz * dz + 1e-4, g->linv[m]);
           g->logdet[m] = ld;
         }
-        g->lc[m] = (float)(log(pim) - 0.5 * ld - 1.5 * log(2.0 * M_PI));
+        g->lc[m] = (float)(log_f(pim) - 0.5 * ld - 1.5 * LOG_2PI);
       }
     }
   }
