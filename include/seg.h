@@ -249,8 +249,8 @@ int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* 
  * unpipelined path, frame order and temporal state are unchanged, and outputs
  * are valid once the context stream passes them, as for seg_push_frame.
  * seg_pipeline_enable(ctx, 1) allocates a second buffer for S and the saliency
- * maximum (even and odd frames alternate) plus the internal stream, and limits
- * the min cut to one CTA per SM; seg_pipeline_enable(ctx, 0) synchronises and
+ * maximum (even and odd frames alternate) plus the internal stream;
+ * seg_pipeline_enable(ctx, 0) synchronises and
  * releases them.  Profiled frames (seg_profile_enable) run unpipelined.
  * seg_push_frame_ev: as seg_push_frame, where the frame's saliency starts once
  * `rgb_ready` (a cudaEvent_t recorded after the RGB8 data was written) has

@@ -622,11 +622,18 @@ int mf_grid_size(int H, int W, int* grid) {
   SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, k_maxflow<4>, MF_THREADS, 0));
   per_sm = per_sm4 < per_sm ? per_sm4 : per_sm;
   if (per_sm < 1) return SEG_ECUDA;
-  int ntx = (W + MF_TW - 1) / MF_TW, nty = (H + MF_TH - 1) / MF_TH;
-  int g = per_sm * nsm;
-  // every co-resident CTA: a colour phase leaves some idle, but the relabel and
-  // reach rounds (all tiles) spread over all of them
-  *grid = g < ntx * nty ? g : ntx * nty;
+  const int ntx = (W + MF_TW - 1) / MF_TW, nty = (H + MF_TH - 1) / MF_TH;
+  const int ntiles = ntx * nty, ntc = ((ntx + 1) / 2) * ((nty + 1) / 2);  // tiles; of the largest colour
+  // A phase walks its colour's tiles and a relabel / reach round all tiles, CTA
+  // k taking tiles k, k + grid, ..; the step lasts as long as the CTA with the
+  // most tiles.  With every co-resident CTA those counts are at their minimum
+  // (rp per phase, ra per round); the grid is the fewest CTAs that still reach
+  // both (fewer arrivals per barrier, and idle SMs for concurrent work), e.g.
+  // 640 x 480: 150 tiles per colour, 600 in all -> 200 CTAs (1 and 3 tiles).
+  const int gmax = per_sm * nsm;
+  const int rp = (ntc + gmax - 1) / gmax, ra = (ntiles + gmax - 1) / gmax;
+  const int gp = (ntc + rp - 1) / rp, ga = (ntiles + ra - 1) / ra;
+  *grid = gp > ga ? gp : ga;
   return SEG_OK;
 }
 

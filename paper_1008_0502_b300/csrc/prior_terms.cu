@@ -138,7 +138,10 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
   }
   // Sec. 6: weight on f(A_{t-1}), formed once per CTA on one thread
   __shared__ float s_wf;
+  __shared__ float sTap[2 * PR_MAXR + 1];  // (indexed by a runtime tap: not from the parameter block)
   if (threadIdx.x == 0) {
+#pragma unroll
+    for (int u = 0; u < 2 * PR_MAXR + 1; ++u) sTap[u] = a.ftap[u];
     double wf = a.wf_host;
     if (a.kal) {
       int t = a.kal->t;
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     for (int i = threadIdx.x; i < iny * PR_TX; i += blockDim.x) {
       int ry = i / PR_TX, x = i - ry * PR_TX;
       float acc = 0.f;
-      for (int u = 0; u <= 2 * R; ++u) acc += a.ftap[u] * sM[ry][x + u];
+      for (int u = 0; u <= 2 * R; ++u) acc += sTap[u] * sM[ry][x + u];
       sH[ry][x] = acc;
     }
     __syncthreads();
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     float p = (1.f - wff) * q;
     if (use_f) {
       float f = 0.f;
-      for (int v = 0; v <= 2 * R; ++v) f += a.ftap[v] * sH[y + v][x];
+      for (int v = 0; v <= 2 * R; ++v) f += sTap[v] * sH[y + v][x];
       p += wff * f;
     }
     a.prior[g] = p;
@@ -556,6 +559,8 @@ __device__ __forceinline__ int32_t quant_cap(float K, float x) {
   return (int32_t)fmaxf(v, 0.f);
 }
 
+#define TM_ROWS 1  // rows per thread (more than one: a serial chain of loads per thread, measured slower)
+
 __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   seg_pdl_enter();
   if (!a.rgb) a.rgb = a.io->rgb;
@@ -563,8 +568,6 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   __shared__ int sLut[766 * 2];
   for (int i = threadIdx.x; i < 766 * 2; i += blockDim.x) sLut[i] = a.lut[i];
   __syncthreads();
-  int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (x >= a.W || y >= a.H) return;
   // frame fb of the batch: its n-link planes are rows fb*H .. fb*H+H-1 of the
   // stacked (B*H) x W grid the min cut sees; links leaving the frame stay 0
   const int fb = blockIdx.z;
@@ -576,56 +579,72 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   a.ct += fb * N;
   a.ncap += fb * N;
   const size_t NB = N * a.B;  // plane stride of the stacked n-link planes
-  size_t g = (size_t)y * a.W + x;
-  const uint8_t* p = a.rgb + 3 * g;
-  int r8 = p[0], g8 = p[1], b8 = p[2];
-  float C[3] = {r8 / 255.f, g8 / 255.f, b8 / 255.f};
-  float pr = a.prior[g];
-  float D[2];
-  for (int lab = 0; lab < 2; ++lab) {
-    float psi;
-    if (a.M > 1 && !(a.gauss->degenerate & (1 << lab))) {  // -log sum_m pi_m N_m(C)
-      const GmmDev& q = a.gmm[2 * fb + lab];
-      float lp[SEG_MAX_GMM], mx = -3.0e38f;
-      for (int m = 0; m < a.M; ++m) {
-        const float* li = q.linv[m];
-        float d0 = C[0] - q.mu[m][0], d1 = C[1] - q.mu[m][1], d2 = C[2] - q.mu[m][2];
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (x >= a.W) return;
+#pragma unroll
+  for (int j = 0; j < TM_ROWS; ++j) {
+    const int y = blockIdx.y * (8 * TM_ROWS) + (threadIdx.x >> 5) + 8 * j;
+    if (y >= a.H) return;
+    const size_t g = (size_t)y * a.W + x;
+    const uint8_t* p = a.rgb + 3 * g;
+    const int r8 = p[0], g8 = p[1], b8 = p[2];
+    const float C[3] = {r8 / 255.f, g8 / 255.f, b8 / 255.f};
+    const float pr = a.prior[g];
+    float D[2];
+#pragma unroll
+    for (int lab = 0; lab < 2; ++lab) {
+      float psi;
+      if (a.M > 1 && !(a.gauss->degenerate & (1 << lab))) {  // -log sum_m pi_m N_m(C)
+        const GmmDev& q = a.gmm[2 * fb + lab];
+        float lp[SEG_MAX_GMM], mx = -3.0e38f;
+#pragma unroll
+        for (int m = 0; m < SEG_MAX_GMM; ++m) {
+          if (m >= a.M) break;
+          const float* li = q.linv[m];
+          float d0 = C[0] - q.mu[m][0], d1 = C[1] - q.mu[m][1], d2 = C[2] - q.mu[m][2];
+          float y0 = li[0] * d0;
+          float y1 = li[1] * d0 + li[2] * d1;
+          float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
+          lp[m] = q.lc[m] - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2);
+          mx = fmaxf(mx, lp[m]);
+        }
+        float z = 0.f;
+#pragma unroll
+        for (int m = 0; m < SEG_MAX_GMM; ++m) {
+          if (m >= a.M) break;
+          z += expf(lp[m] - mx);
+        }
+        psi = -(mx + logf(z));
+      } else {
+        const float* li = a.gauss->linv[lab];
+        float d0 = C[0] - a.gauss->muf[lab][0], d1 = C[1] - a.gauss->muf[lab][1],
+              d2 = C[2] - a.gauss->muf[lab][2];
         float y0 = li[0] * d0;
         float y1 = li[1] * d0 + li[2] * d1;
         float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
-        lp[m] = q.lc[m] - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2);
-        mx = fmaxf(mx, lp[m]);
+        psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + a.gauss->lconst[lab];
       }
-      float z = 0.f;
-      for (int m = 0; m < a.M; ++m) z += expf(lp[m] - mx);
-      psi = -(mx + logf(z));
-    } else {
-      const float* li = a.gauss->linv[lab];
-      float d0 = C[0] - a.gauss->muf[lab][0], d1 = C[1] - a.gauss->muf[lab][1],
-            d2 = C[2] - a.gauss->muf[lab][2];
-      float y0 = li[0] * d0;
-      float y1 = li[1] * d0 + li[2] * d1;
-      float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
-      psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + a.gauss->lconst[lab];
+      float pl = lab ? pr : 1.f - pr;
+      float xi = -logf(fminf(fmaxf(pl, a.eps), 1.f - a.eps));
+      D[lab] = a.lambda_u * psi + xi;
     }
-    float pl = lab ? pr : 1.f - pr;
-    float xi = -logf(fminf(fmaxf(pl, a.eps), 1.f - a.eps));
-    D[lab] = a.lambda_u * psi + xi;
-  }
-  float m = fminf(D[0], D[1]);
-  a.cs[g] = quant_cap(a.K, D[0] - m);  // c(s, v) = D(0): paid when v is background
-  a.ct[g] = quant_cap(a.K, D[1] - m);  // c(v, t) = D(1): paid when v is object
-  int s0 = r8 + g8 + b8;
-  const int dx[4] = {1, 0, 1, -1}, dy[4] = {0, 1, 1, 1};
-  for (int k = 0; k < a.nk; ++k) {
-    int xx = x + dx[k], yy = y + dy[k];
-    int32_t c = 0;
-    if (xx >= 0 && xx < a.W && yy < a.H) {
-      const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
-      int ds = abs(s0 - (q[0] + q[1] + q[2]));
-      c = sLut[2 * ds + (k >= 2)];
+    const float m = fminf(D[0], D[1]);
+    a.cs[g] = quant_cap(a.K, D[0] - m);  // c(s, v) = D(0): paid when v is background
+    a.ct[g] = quant_cap(a.K, D[1] - m);  // c(v, t) = D(1): paid when v is object
+    const int s0 = r8 + g8 + b8;
+    // neighbour k: (+1, 0), (0, +1), (+1, +1), (-1, +1); k >= 2 diagonal
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k >= a.nk) break;
+      const int xx = x + (k == 1 ? 0 : k == 3 ? -1 : 1), yy = y + (k == 0 ? 0 : 1);
+      int32_t c = 0;
+      if (xx >= 0 && xx < a.W && yy < a.H) {
+        const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
+        const int ds = abs(s0 - (q[0] + q[1] + q[2]));
+        c = sLut[2 * ds + (k >= 2)];
+      }
+      a.ncap[k * NB + g] = c;
     }
-    a.ncap[k * NB + g] = c;
   }
 }
 
@@ -771,7 +790,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.io = c->io_mode ? c->io : nullptr;
   ta.gmm = c->gmm;
   ta.M = p.gmm_components;
-  dim3 grid((c->W + 31) / 32, (c->H + 7) / 8, c->B);
+  dim3 grid((c->W + 31) / 32, (c->H + 8 * TM_ROWS - 1) / (8 * TM_ROWS), c->B);
   SEG_CUDA_TRY(seg_launch(k_terms, grid, 256, 0, st, ta));
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;

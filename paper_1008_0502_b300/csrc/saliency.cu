@@ -193,8 +193,9 @@ __global__ void __launch_bounds__(256) k_reduce3(Reduce3Args a) {
   __shared__ float sF[RED_IN_Y][RED_IN_X];
   __shared__ float sH[RED_IN_Y][RED_TX];
   const int ch = blockIdx.z % 3, fb = blockIdx.z / 3;
-  const float* __restrict__ in = a.in[ch] + (size_t)fb * a.h * a.w;
-  float* __restrict__ out = a.out[ch] + (size_t)fb * a.h2 * a.w2;
+  // (selects, not a runtime index into the parameter block, which would copy it to local memory)
+  const float* __restrict__ in = (ch == 0 ? a.in[0] : ch == 1 ? a.in[1] : a.in[2]) + (size_t)fb * a.h * a.w;
+  float* __restrict__ out = (ch == 0 ? a.out[0] : ch == 1 ? a.out[1] : a.out[2]) + (size_t)fb * a.h2 * a.w2;
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
   const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
   for (int i = threadIdx.x; i < RED_IN_Y * RED_IN_X; i += blockDim.x) {
@@ -600,7 +601,10 @@ __global__ void __launch_bounds__(1024) k_cs_accum_fused(CSArgs a, float* __rest
   }
   float* const buf[3] = {nullptr, sR1, sR2};
   __syncthreads();
-  for (int k = D; k >= 0; --k) {
+  // unrolled over the level offset so the region arrays stay in registers
+#pragma unroll
+  for (int k = 2; k >= 0; --k) {
+    if (k > D) continue;
     const int c = cmax - k, hc = a.hl[c], wc = a.wl[c];
     if (k < D) {
       // horizontal pass of REDUCE(B_{c-1}): rows of the finer region x this region's columns

@@ -510,8 +510,6 @@ static void pipe_free(seg_ctx* c) {
   c->pipe_mem = nullptr;
   c->pipe_on = 0;
   c->pipe_graph = 0;
-  if (c->mf_grid_full) c->mf_grid = c->mf_grid_full;
-  c->mf_grid_full = 0;
   c->sal.S = c->pS[0] ? c->pS[0] : c->sal.S;
   c->sal.salmax = c->psalmax[0] ? c->psalmax[0] : c->sal.salmax;
 }
@@ -547,13 +545,6 @@ extern "C" int seg_pipeline_enable(seg_ctx* c, int on) {
   if (!ok) {
     pipe_free(c);
     return SEG_ECUDA;
-  }
-  // the min cut keeps one CTA per SM, leaving room for the next frame's saliency
-  int nsm = 0;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && nsm > 0 &&
-      c->mf_grid > nsm) {
-    c->mf_grid_full = c->mf_grid;
-    c->mf_grid = nsm;
   }
   c->pipe_on = 1;
   c->pipe_graph = 0;

@@ -362,7 +362,6 @@ struct seg_ctx {
   int pipe_graph;         // 0 not built, 1 ready, -1 eager launches
   cudaGraphExec_t gf[2], gb[2];
   unsigned long long pipe_t;
-  int mf_grid_full;       // the min cut's grid before pipelining reduced it
   uint8_t* ring[3];       // RGB8 staging ring of the asynchronous host-buffer entry point
   cudaEvent_t ev_ring[3]; // back of the frame that last read each slot
   unsigned long long ring_t;
