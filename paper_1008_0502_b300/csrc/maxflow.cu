@@ -58,6 +58,7 @@ struct MFShared {
   unsigned char z[MF_HN];  // reach flags with halo
   int ok;
   unsigned int setmask;  // colours of the tiles this CTA pushed into during a phase
+  long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
 };
 
 __device__ __forceinline__ long long mf_now() {
@@ -269,12 +270,6 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, bool*
     // push
     const int e0 = s.e[tid], hu = s.h[hi];
     if (valid && e0 > 0 && hu < N) {
-      int hn[ND], rr[ND];
-#pragma unroll
-      for (int d = 0; d < ND; ++d) {
-        hn[d] = s.h[hi + mf_hoff(d)];
-        rr[d] = s.r[d][tid];
-      }
       int ex = e0;
       if (hu == 1) {
         int rtv = s.rt[tid];
@@ -286,9 +281,10 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, bool*
       }
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
-        if (ex <= 0 || rr[d] <= 0 || hu != hn[d] + 1) continue;
-        int dl = min(ex, rr[d]);
-        s.r[d][tid] = rr[d] - dl;
+        const int rd = s.r[d][tid];
+        if (ex <= 0 || rd <= 0 || hu != s.h[hi + mf_hoff(d)] + 1) continue;
+        int dl = min(ex, rd);
+        s.r[d][tid] = rd - dl;
         ex -= dl;
         int nly = ly + mf_dy(d), nlx = lx + mf_dx(d);
         if (nly >= 0 && nly < MF_TH && nlx >= 0 && nlx < MF_TW) {
@@ -422,29 +418,31 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   bool converged = false;
   // phase timing on one thread (the grid moves in lock-step between barriers):
   // [0] init, [1] global relabels, [2] discharge cycles, [3] final reach + mask
-  long long t_acc[4] = {0, 0, 0, 0};
-  long long t_last = t_start;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) s.t_acc[k] = 0;
+    s.t_last = t_start;
+  }
   auto lap = [&](int slot) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       long long t = mf_now();
-      t_acc[slot] += t - t_last;
-      t_last = t;
+      s.t_acc[slot] += t - s.t_last;
+      s.t_last = t;
     }
   };
   lap(0);
-  // Phase scheduling.  flag[c]: some tile of colour c may hold an active node.
+  // Phase scheduling.  Bit c of flag: some tile of colour c may hold an active node.
   // Every CTA keeps the same copy, updated only from the word the phase's CTAs
   // OR together before its barrier (bit c': a push entered a tile of colour c';
   // bit 4: a tile of the discharged colour is still active), so skipping a
   // colour -- and its barrier -- is decided identically everywhere.  The
   // preflow is maximum once no colour is flagged.  A global relabel runs first
   // and then after every 4 * gr_every executed phases.
-  bool flag[4] = {true, true, true, true};
+  unsigned int flag = 15u;
   int color = 0, executed = 0, since_gr = 0;
   bool relabel = true;
   for (;;) {
     int tries = 0;
-    while (tries < 4 && !flag[color]) {
+    while (tries < 4 && !((flag >> color) & 1u)) {
       color = (color + 1) & 3;
       ++tries;
     }
@@ -506,9 +504,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
       if (!mf_grid_sync(a, s)) return;
       const unsigned int f = mf_flag_read(a, epoch);
       ++epoch;
-      for (int c2 = 0; c2 < 4; ++c2)
-        if (c2 != color) flag[c2] = flag[c2] || ((f >> c2) & 1u);
-      flag[color] = (f >> 4) & 1u;
+      flag = ((flag | f) & 15u & ~(1u << color)) | (((f >> 4) & 1u) << color);
       color = (color + 1) & 3;
       ++executed;
       ++since_gr;
@@ -577,7 +573,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     a.status[2] = n_gr;
     a.status[3] = n_rounds;
     lap(3);
-    for (int k = 0; k < 4; ++k) a.status[4 + k] = (int)(t_acc[k] / 100);  // units of 0.1 us
+    for (int k = 0; k < 4; ++k) a.status[4 + k] = (int)(s.t_acc[k] / 100);  // units of 0.1 us
   }
 }
 
