@@ -61,48 +61,12 @@ struct MFShared {
   long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
 };
 
-__device__ __forceinline__ long long mf_now() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
+__device__ __forceinline__ long long mf_now() { return seg_now(); }
 
-// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
-// the CTA) once any CTA has recorded a timeout.  Arrival is an acq_rel atomic on
-// a counter, release a release-add on a generation word in another cache line,
-// polled with acquire loads; the CTA barriers before and after carry the other
-// threads' writes (release and acquire are cumulative), so no full fences are
-// needed.  The timer is read every 256 polls.
-__device__ bool mf_grid_sync(const MFArgs& a, MFShared& s) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int g, old;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&a.bar->gen) : "memory");
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&a.bar->count) : "memory");
-    int ok = 1;
-    if (old + 1u == gridDim.x) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&a.bar->count) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.bar->gen) : "memory");
-    } else {
-      const long long t0 = mf_now();
-      for (unsigned int k = 0;; ++k) {
-        unsigned int cur;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&a.bar->gen) : "memory");
-        if (cur != g) break;
-        if ((k & 255u) == 255u && mf_now() - t0 > a.timeout_ns) {
-          atomicCAS(&a.status[0], 0, SEG_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    int st;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(st) : "l"(&a.status[0]) : "memory");
-    if (st == SEG_ETIMEOUT) ok = 0;
-    s.ok = ok;
-  }
-  __syncthreads();
-  return s.ok != 0;
+// Grid-wide barrier with a bounded wait (seg_grid_sync); false once any CTA
+// has recorded a timeout.
+__device__ __forceinline__ bool mf_grid_sync(const MFArgs& a, MFShared& s) {
+  return seg_grid_sync(a.bar, a.status, a.timeout_ns, &s.ok);
 }
 
 __device__ __forceinline__ unsigned int mf_flag_read(const MFArgs& a, unsigned int epoch) {

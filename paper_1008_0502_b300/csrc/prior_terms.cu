@@ -64,8 +64,8 @@ struct MomFinArgs {
   int M;
 };
 
-__device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
-  float r = px[0] / 255.f, g = px[1] / 255.f, b = px[2] / 255.f;
+__device__ __forceinline__ void mom1_add_rgb(float p, int r8, int g8, int b8, float* s) {
+  float r = r8 / 255.f, g = g8 / 255.f, b = b8 / 255.f;
   float w0 = 1.f - p;
   s[0] += w0;
   s[1] += w0 * r;
@@ -75,6 +75,30 @@ __device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) {
   s[5] += p * r;
   s[6] += p * g;
   s[7] += p * b;
+}
+__device__ __forceinline__ void mom1_add(float p, const uint8_t* px, float* s) { mom1_add_rgb(p, px[0], px[1], px[2], s); }
+
+// Centred second moments about the label means muf[label][channel] (Sec. 5):
+// rr, gr, gg, br, bg, bb for the background (weight 1 - p), then the object (p).
+__device__ __forceinline__ void mom2_add(float p, const uint8_t* px, const float* muf, float* s) {
+  float r = px[0] / 255.f, g = px[1] / 255.f, b = px[2] / 255.f;
+  float w0 = 1.f - p;
+  float dr = r - muf[0], dg = g - muf[1], db = b - muf[2];
+  s[0] += w0 * dr * dr;
+  s[1] += w0 * dg * dr;
+  s[2] += w0 * dg * dg;
+  s[3] += w0 * db * dr;
+  s[4] += w0 * db * dg;
+  s[5] += w0 * db * db;
+  dr = r - muf[3];
+  dg = g - muf[4];
+  db = b - muf[5];
+  s[6] += p * dr * dr;
+  s[7] += p * dg * dr;
+  s[8] += p * dg * dg;
+  s[9] += p * db * dr;
+  s[10] += p * db * dg;
+  s[11] += p * db * db;
 }
 
 // Finalisation arithmetic (one or two threads while the rest of the grid has
@@ -112,33 +136,30 @@ __device__ bool block_partial_last(const float* v, float* part, unsigned* counte
                                    int nblocks);
 __device__ void finalize_means(const double* tot, GaussDev* g, KalmanDev* kal, double a, double b);
 
-__global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
-  seg_pdl_enter();
+// Pointers of frame fb of a batch (and, when captured, the frame's I/O).
+__device__ __forceinline__ void prior_frame(PriorArgs& a, int fb) {
   if (a.io) {
     if (!a.sal) a.sal = a.io->sal;
     if (!a.prior) a.prior = a.io->prior;
     if (!a.rgb) a.rgb = a.io->rgb;
   }
-  __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
-  __shared__ float sH[PR_TY + 2 * PR_MAXR][PR_TX];
-  {  // frame of the batch
-    const int fb = blockIdx.z;
-    const size_t n = (size_t)a.H * a.W;
-    if (a.sal) a.sal += fb * n;
-    if (a.from_S) a.S += (size_t)fb * a.hS * a.wS;
-    a.prior += fb * n;
-    if (a.prev) a.prev += fb * n;
-    if (a.rgb) a.rgb += fb * 3 * n;
-    a.salmax += fb;
-    if (a.kal) a.kal += fb;
-    if (a.kal_adv) a.kal_adv += fb;
-    a.gauss += fb;
-    a.part += (size_t)fb * a.part_stride;
-    a.counter += fb;
-  }
-  // Sec. 6: weight on f(A_{t-1}), formed once per CTA on one thread
-  __shared__ float s_wf;
-  __shared__ float sTap[2 * PR_MAXR + 1];  // (indexed by a runtime tap: not from the parameter block)
+  const size_t n = (size_t)a.H * a.W;
+  if (a.sal) a.sal += fb * n;
+  if (a.from_S) a.S += (size_t)fb * a.hS * a.wS;
+  a.prior += fb * n;
+  if (a.prev) a.prev += fb * n;
+  if (a.rgb) a.rgb += fb * 3 * n;
+  a.salmax += fb;
+  if (a.kal) a.kal += fb;
+  if (a.kal_adv) a.kal_adv += fb;
+  a.gauss += fb;
+  a.part += (size_t)fb * a.part_stride;
+  a.counter += fb;
+}
+
+// Thread 0: the blur taps into shared memory (indexed by a runtime tap, so not
+// read from the parameter block) and, Sec. 6, the weight on f(A_{t-1}).
+__device__ __forceinline__ void prior_setup(const PriorArgs& a, float* sTap, float* s_wf) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int u = 0; u < 2 * PR_MAXR + 1; ++u) sTap[u] = a.ftap[u];
@@ -148,22 +169,37 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
       double P = a.kal->P;
       wf = t == 0 ? 0.0 : a.a * nr_rcp(a.a + a.b + P);
     }
-    s_wf = (float)wf;
+    *s_wf = (float)wf;
   }
-  __syncthreads();
-  const float wff = s_wf;
-  const double wf = wff;
-  const int X0 = blockIdx.x * PR_TX, Y0 = blockIdx.y * PR_TY;
+}
+
+typedef float PrTileM[PR_TX + 2 * PR_MAXR];
+typedef float PrTileH[PR_TX];
+
+// The previous mask on a tile and its halo, into sM (no barrier).
+__device__ __forceinline__ void prior_tile_mask(const PriorArgs& a, int X0, int Y0, PrTileM* sM) {
+  const int R = a.fR, iny = PR_TY + 2 * R, inx = PR_TX + 2 * R;
+  for (int i = threadIdx.x; i < iny * inx; i += blockDim.x) {
+    int ry = i / inx, rx = i - ry * inx;
+    int gy = seg_clampi(Y0 - R + ry, 0, a.H - 1), gx = seg_clampi(X0 - R + rx, 0, a.W - 1);
+    sM[ry][rx] = (float)a.prev[(size_t)gy * a.W + gx];
+  }
+}
+
+// The prior on one PR_TX x PR_TY tile (whole CTA, any block size), adding the
+// first-moment sums of its pixels to ms when a.rgb is set.  Consecutive calls
+// may reuse sM / sH: each call's barriers order them.  mask_loaded: sM already
+// holds the tile's mask (prior_tile_mask, before a barrier).  A thread's two
+// pixels (i, i + blockDim.x) issue all their loads before any store.
+__device__ __forceinline__ void prior_tile(const PriorArgs& a, int X0, int Y0, float wff, bool use_f, float mx,
+                                           const float* sTap, PrTileM* sM, PrTileH* sH, float* ms,
+                                           bool mask_loaded = false) {
   const int R = a.fR, iny = PR_TY + 2 * R;
-  const bool use_f = wf != 0.0 && a.prev != nullptr;
   if (use_f) {
-    const int inx = PR_TX + 2 * R;
-    for (int i = threadIdx.x; i < iny * inx; i += blockDim.x) {
-      int ry = i / inx, rx = i - ry * inx;
-      int gy = seg_clampi(Y0 - R + ry, 0, a.H - 1), gx = seg_clampi(X0 - R + rx, 0, a.W - 1);
-      sM[ry][rx] = (float)a.prev[(size_t)gy * a.W + gx];
+    if (!mask_loaded) {
+      prior_tile_mask(a, X0, Y0, sM);
+      __syncthreads();
     }
-    __syncthreads();
     for (int i = threadIdx.x; i < iny * PR_TX; i += blockDim.x) {
       int ry = i / PR_TX, x = i - ry * PR_TX;
       float acc = 0.f;
@@ -172,31 +208,67 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
     }
     __syncthreads();
   }
-  const float mx = __uint_as_float(*a.salmax);
-  float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < PR_TY * PR_TX; i += blockDim.x) {
-    int y = i / PR_TX, x = i - y * PR_TX;
-    int gy = Y0 + y, gx = X0 + x;
-    if (gy >= a.H || gx >= a.W) continue;
-    size_t g = (size_t)gy * a.W + gx;
-    bool edge = gy < a.border || gy >= a.H - a.border || gx < a.border || gx >= a.W - a.border;
-    float sv;
-    if (a.from_S) {  // the saliency map at this pixel: bilinear up-sampling of S
-      sv = seg_bilinear_t(a.S, a.wS, a.frow[gy], a.fcol[gx]);
-      if (a.sal) a.sal[g] = sv;
-    } else {
-      sv = a.sal[g];
+  for (int i0 = threadIdx.x; i0 < PR_TY * PR_TX; i0 += 2 * blockDim.x) {
+    float sv[2], fv[2];
+    int px[2][3];
+    bool ok[2], edge[2];
+    size_t gg[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const int y = i / PR_TX, x = i - y * PR_TX;
+      const int gy = Y0 + y, gx = X0 + x;
+      ok[u] = i < PR_TY * PR_TX && gy < a.H && gx < a.W;
+      gg[u] = ok[u] ? (size_t)gy * a.W + gx : 0;
+      edge[u] = gy < a.border || gy >= a.H - a.border || gx < a.border || gx >= a.W - a.border;
+      sv[u] = 0.f;
+      fv[u] = 0.f;
+      px[u][0] = px[u][1] = px[u][2] = 0;
+      if (ok[u]) {
+        // the saliency map at this pixel (from_S: bilinear up-sampling of S)
+        sv[u] = a.from_S ? seg_bilinear_t(a.S, a.wS, a.frow[gy], a.fcol[gx]) : a.sal[gg[u]];
+        if (use_f) {
+          float f = 0.f;
+          for (int v = 0; v <= 2 * R; ++v) f += sTap[v] * sH[y + v][x];
+          fv[u] = f;
+        }
+        if (a.rgb) {
+          const uint8_t* q = a.rgb + 3 * gg[u];
+          px[u][0] = q[0];
+          px[u][1] = q[1];
+          px[u][2] = q[2];
+        }
+      }
     }
-    float q = edge ? a.eps : (mx > 0.f ? sv / mx : 0.f);
-    float p = (1.f - wff) * q;
-    if (use_f) {
-      float f = 0.f;
-      for (int v = 0; v <= 2 * R; ++v) f += sTap[v] * sH[y + v][x];
-      p += wff * f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!ok[u]) continue;
+      if (a.from_S && a.sal) a.sal[gg[u]] = sv[u];
+      float q = edge[u] ? a.eps : (mx > 0.f ? sv[u] / mx : 0.f);
+      float p = (1.f - wff) * q;
+      if (use_f) p += wff * fv[u];
+      a.prior[gg[u]] = p;
+      if (a.rgb) mom1_add_rgb(p, px[u][0], px[u][1], px[u][2], ms);
     }
-    a.prior[g] = p;
-    if (a.rgb) mom1_add(p, a.rgb + 3 * g, ms);
   }
+}
+
+__global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
+  seg_pdl_enter();
+  __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
+  __shared__ float sH[PR_TY + 2 * PR_MAXR][PR_TX];
+  __shared__ float s_wf;
+  __shared__ float sTap[2 * PR_MAXR + 1];
+  prior_frame(a, blockIdx.z);
+  prior_setup(a, sTap, &s_wf);
+  // (the mask tile is fetched while the weight is formed; unused when w_f = 0)
+  if (a.prev) prior_tile_mask(a, blockIdx.x * PR_TX, blockIdx.y * PR_TY, sM);
+  const float mx = __uint_as_float(*a.salmax);
+  __syncthreads();
+  const float wff = s_wf;
+  const bool use_f = wff != 0.f && a.prev != nullptr;
+  float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  prior_tile(a, blockIdx.x * PR_TX, blockIdx.y * PR_TY, wff, use_f, mx, sTap, sM, sH, ms, true);
   if (a.rgb) {
     const int nb = gridDim.x * gridDim.y;
     if (block_partial_last<8>(ms, a.part, a.counter, blockIdx.y * gridDim.x + blockIdx.x, nb)) {
@@ -214,9 +286,8 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
 // sum across CTAs (reduce_parts) is an error-free float-float sum, which keeps
 // about 44 bits without the FP64 pipe (narrow on this part).
 template <int NV>
-__device__ bool block_partial_last(const float* v, float* part, unsigned* counter, int bid, int nblocks) {
+__device__ void block_partial_write(const float* v, float* part, int bid, int nblocks) {
   __shared__ float red[32][NV];
-  __shared__ int is_last;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -231,6 +302,12 @@ __device__ bool block_partial_last(const float* v, float* part, unsigned* counte
     __threadfence();  // (only the writers need to fence)
   }
   __syncthreads();
+}
+
+template <int NV>
+__device__ bool block_partial_last(const float* v, float* part, unsigned* counter, int bid, int nblocks) {
+  __shared__ int is_last;
+  block_partial_write<NV>(v, part, bid, nblocks);
   if (threadIdx.x == 0) {
     unsigned prev = atomicAdd(counter, 1u);
     is_last = prev == (unsigned)nblocks - 1u;
@@ -257,19 +334,20 @@ __device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
 template <int NV>
 __device__ void reduce_parts(const float* part, int nblocks, double* out) {
   constexpr int G = NV <= 8 ? 1 : NV <= 16 ? 2 : 4;
+  constexpr int U = G >= 4 ? 8 : 16;  // loads in flight per value (the sum order is b order either way)
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, wid = threadIdx.x >> 5;
   for (int k0 = wid; k0 < NV; k0 += G * nw) {
     float2 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float2(0.f, 0.f);
-    for (int b0 = lane; b0 < nblocks; b0 += 32 * 4) {
-      // L2 reads (other CTAs' partials are not in this L1), 4 G in flight
-      float v[G][4];
+    for (int b0 = lane; b0 < nblocks; b0 += 32 * U) {
+      // L2 reads (other CTAs' partials are not in this L1), U x G in flight
+      float v[G][U];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int k = k0 + g * nw;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int b = b0 + 32 * u;
           v[g][u] = k < NV && b < nblocks ? __ldcg(part + (size_t)k * nblocks + b) : 0.f;
         }
@@ -277,7 +355,7 @@ __device__ void reduce_parts(const float* part, int nblocks, double* out) {
 #pragma unroll
       for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[g] = ff_add(acc[g], make_float2(v[g][u], 0.f));
+        for (int u = 0; u < U; ++u) acc[g] = ff_add(acc[g], make_float2(v[g][u], 0.f));
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -402,33 +480,13 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
   f.part += (size_t)fb * f.part_stride;
   f.counter += fb;
   f.gauss += fb;
-  const GaussDev* gauss = f.gauss;
-  float m0r = gauss->muf[0][0], m0g = gauss->muf[0][1], m0b = gauss->muf[0][2];
-  float m1r = gauss->muf[1][0], m1g = gauss->muf[1][1], m1b = gauss->muf[1][2];
   float s[12];
   for (int k = 0; k < 12; ++k) s[k] = 0.f;
+  float muf[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) muf[k] = f.gauss->muf[k / 3][k % 3];
   int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    float p = prior[i];
-    float r = rgb[3 * i] / 255.f, g = rgb[3 * i + 1] / 255.f, b = rgb[3 * i + 2] / 255.f;
-    float w0 = 1.f - p;
-    float dr = r - m0r, dg = g - m0g, db = b - m0b;
-    s[0] += w0 * dr * dr;
-    s[1] += w0 * dg * dr;
-    s[2] += w0 * dg * dg;
-    s[3] += w0 * db * dr;
-    s[4] += w0 * db * dg;
-    s[5] += w0 * db * db;
-    dr = r - m1r;
-    dg = g - m1g;
-    db = b - m1b;
-    s[6] += p * dr * dr;
-    s[7] += p * dg * dr;
-    s[8] += p * dg * dg;
-    s[9] += p * db * dr;
-    s[10] += p * db * dg;
-    s[11] += p * db * db;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) mom2_add(prior[i], rgb + 3 * (size_t)i, muf, s);
   if (block_partial_last<12>(s, f.part, f.counter, blockIdx.x, gridDim.x)) {
     __shared__ double tot[12];
     reduce_parts<12>(f.part, gridDim.x, tot);
@@ -559,18 +617,97 @@ __device__ __forceinline__ int32_t quant_cap(float K, float x) {
   return (int32_t)fmaxf(v, 0.f);
 }
 
-#define TM_ROWS 1  // rows per thread (more than one: a serial chain of loads per thread, measured slower)
+// What the terms of one pixel read: its colour, its prior and r + g + b of its
+// forward neighbours (-1 outside the frame).
+struct TermsIn {
+  int r8, g8, b8;
+  float pr;
+  int nsum[4];
+};
 
-__global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
-  seg_pdl_enter();
+__device__ __forceinline__ void terms_load(const TermsArgs& a, int x, int y, TermsIn& t) {
+  const size_t g = (size_t)y * a.W + x;
+  const uint8_t* p = a.rgb + 3 * g;
+  t.r8 = p[0];
+  t.g8 = p[1];
+  t.b8 = p[2];
+  t.pr = __ldcg(a.prior + g);  // (L2: in the fused kernel other CTAs wrote it)
+  // neighbour k: (+1, 0), (0, +1), (+1, +1), (-1, +1); k >= 2 diagonal
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    t.nsum[k] = -1;
+    if (k >= a.nk) continue;
+    const int xx = x + (k == 1 ? 0 : k == 3 ? -1 : 1), yy = y + (k == 0 ? 0 : 1);
+    if (xx >= 0 && xx < a.W && yy < a.H) {
+      const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
+      t.nsum[k] = q[0] + q[1] + q[2];
+    }
+  }
+}
+
+// t-links and n-links of pixel (x, y) of one frame from what terms_load read:
+// rgb, prior, cs, ct and ncap point at the frame, NB is the plane stride of the
+// stacked n-link planes, lut the n-link table (shared memory), gs / gmm the
+// frame's colour model.
+__device__ __forceinline__ void terms_store(const TermsArgs& a, const GaussDev& gs, const GmmDev* gmm, size_t NB,
+                                            const int* lut, int x, int y, const TermsIn& t) {
+  const size_t g = (size_t)y * a.W + x;
+  const float C[3] = {t.r8 / 255.f, t.g8 / 255.f, t.b8 / 255.f};
+  const float pr = t.pr;
+  float D[2];
+#pragma unroll
+  for (int lab = 0; lab < 2; ++lab) {
+    float psi;
+    if (a.M > 1 && !(gs.degenerate & (1 << lab))) {  // -log sum_m pi_m N_m(C)
+      const GmmDev& q = gmm[lab];
+      float lp[SEG_MAX_GMM], mx = -3.0e38f;
+#pragma unroll
+      for (int m = 0; m < SEG_MAX_GMM; ++m) {
+        if (m >= a.M) break;
+        const float* li = q.linv[m];
+        float d0 = C[0] - q.mu[m][0], d1 = C[1] - q.mu[m][1], d2 = C[2] - q.mu[m][2];
+        float y0 = li[0] * d0;
+        float y1 = li[1] * d0 + li[2] * d1;
+        float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
+        lp[m] = q.lc[m] - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2);
+        mx = fmaxf(mx, lp[m]);
+      }
+      float z = 0.f;
+#pragma unroll
+      for (int m = 0; m < SEG_MAX_GMM; ++m) {
+        if (m >= a.M) break;
+        z += expf(lp[m] - mx);
+      }
+      psi = -(mx + logf(z));
+    } else {
+      const float* li = gs.linv[lab];
+      float d0 = C[0] - gs.muf[lab][0], d1 = C[1] - gs.muf[lab][1], d2 = C[2] - gs.muf[lab][2];
+      float y0 = li[0] * d0;
+      float y1 = li[1] * d0 + li[2] * d1;
+      float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
+      psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + gs.lconst[lab];
+    }
+    float pl = lab ? pr : 1.f - pr;
+    float xi = -logf(fminf(fmaxf(pl, a.eps), 1.f - a.eps));
+    D[lab] = a.lambda_u * psi + xi;
+  }
+  const float m = fminf(D[0], D[1]);
+  a.cs[g] = quant_cap(a.K, D[0] - m);  // c(s, v) = D(0): paid when v is background
+  a.ct[g] = quant_cap(a.K, D[1] - m);  // c(v, t) = D(1): paid when v is object
+  const int s0 = t.r8 + t.g8 + t.b8;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= a.nk) break;
+    a.ncap[k * NB + g] = t.nsum[k] < 0 ? 0 : lut[2 * abs(s0 - t.nsum[k]) + (k >= 2)];
+  }
+}
+
+// Frame fb's pointers (and, when captured, the frame's I/O).  The frame's n-link
+// planes are rows fb*H .. fb*H+H-1 of the stacked (B*H) x W grid the min cut
+// sees; links leaving the frame stay 0.
+__device__ __forceinline__ void terms_frame(TermsArgs& a, int fb) {
   if (!a.rgb) a.rgb = a.io->rgb;
   if (!a.prior) a.prior = a.io->prior;
-  __shared__ int sLut[766 * 2];
-  for (int i = threadIdx.x; i < 766 * 2; i += blockDim.x) sLut[i] = a.lut[i];
-  __syncthreads();
-  // frame fb of the batch: its n-link planes are rows fb*H .. fb*H+H-1 of the
-  // stacked (B*H) x W grid the min cut sees; links leaving the frame stay 0
-  const int fb = blockIdx.z;
   const size_t N = (size_t)a.H * a.W;
   a.rgb += fb * 3 * N;
   a.prior += fb * N;
@@ -578,74 +715,20 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   a.cs += fb * N;
   a.ct += fb * N;
   a.ncap += fb * N;
-  const size_t NB = N * a.B;  // plane stride of the stacked n-link planes
-  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-  if (x >= a.W) return;
-#pragma unroll
-  for (int j = 0; j < TM_ROWS; ++j) {
-    const int y = blockIdx.y * (8 * TM_ROWS) + (threadIdx.x >> 5) + 8 * j;
-    if (y >= a.H) return;
-    const size_t g = (size_t)y * a.W + x;
-    const uint8_t* p = a.rgb + 3 * g;
-    const int r8 = p[0], g8 = p[1], b8 = p[2];
-    const float C[3] = {r8 / 255.f, g8 / 255.f, b8 / 255.f};
-    const float pr = a.prior[g];
-    float D[2];
-#pragma unroll
-    for (int lab = 0; lab < 2; ++lab) {
-      float psi;
-      if (a.M > 1 && !(a.gauss->degenerate & (1 << lab))) {  // -log sum_m pi_m N_m(C)
-        const GmmDev& q = a.gmm[2 * fb + lab];
-        float lp[SEG_MAX_GMM], mx = -3.0e38f;
-#pragma unroll
-        for (int m = 0; m < SEG_MAX_GMM; ++m) {
-          if (m >= a.M) break;
-          const float* li = q.linv[m];
-          float d0 = C[0] - q.mu[m][0], d1 = C[1] - q.mu[m][1], d2 = C[2] - q.mu[m][2];
-          float y0 = li[0] * d0;
-          float y1 = li[1] * d0 + li[2] * d1;
-          float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
-          lp[m] = q.lc[m] - 0.5f * (y0 * y0 + y1 * y1 + y2 * y2);
-          mx = fmaxf(mx, lp[m]);
-        }
-        float z = 0.f;
-#pragma unroll
-        for (int m = 0; m < SEG_MAX_GMM; ++m) {
-          if (m >= a.M) break;
-          z += expf(lp[m] - mx);
-        }
-        psi = -(mx + logf(z));
-      } else {
-        const float* li = a.gauss->linv[lab];
-        float d0 = C[0] - a.gauss->muf[lab][0], d1 = C[1] - a.gauss->muf[lab][1],
-              d2 = C[2] - a.gauss->muf[lab][2];
-        float y0 = li[0] * d0;
-        float y1 = li[1] * d0 + li[2] * d1;
-        float y2 = li[3] * d0 + li[4] * d1 + li[5] * d2;
-        psi = 0.5f * (y0 * y0 + y1 * y1 + y2 * y2) + a.gauss->lconst[lab];
-      }
-      float pl = lab ? pr : 1.f - pr;
-      float xi = -logf(fminf(fmaxf(pl, a.eps), 1.f - a.eps));
-      D[lab] = a.lambda_u * psi + xi;
-    }
-    const float m = fminf(D[0], D[1]);
-    a.cs[g] = quant_cap(a.K, D[0] - m);  // c(s, v) = D(0): paid when v is background
-    a.ct[g] = quant_cap(a.K, D[1] - m);  // c(v, t) = D(1): paid when v is object
-    const int s0 = r8 + g8 + b8;
-    // neighbour k: (+1, 0), (0, +1), (+1, +1), (-1, +1); k >= 2 diagonal
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k >= a.nk) break;
-      const int xx = x + (k == 1 ? 0 : k == 3 ? -1 : 1), yy = y + (k == 0 ? 0 : 1);
-      int32_t c = 0;
-      if (xx >= 0 && xx < a.W && yy < a.H) {
-        const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
-        const int ds = abs(s0 - (q[0] + q[1] + q[2]));
-        c = sLut[2 * ds + (k >= 2)];
-      }
-      a.ncap[k * NB + g] = c;
-    }
-  }
+  a.gmm += 2 * fb;
+}
+
+__global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
+  seg_pdl_enter();
+  __shared__ int sLut[766 * 2];
+  for (int i = threadIdx.x; i < 766 * 2; i += blockDim.x) sLut[i] = a.lut[i];
+  __syncthreads();
+  terms_frame(a, blockIdx.z);
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= a.W || y >= a.H) return;
+  TermsIn t;
+  terms_load(a, x, y, t);
+  terms_store(a, *a.gauss, a.gmm, (size_t)a.H * a.W * a.B, sLut, x, y, t);
 }
 
 // ------------------------------------------------------------------ host side
@@ -691,10 +774,9 @@ int pt_launch_salmax(seg_ctx* c, const float* sal) {
   return SEG_OK;
 }
 
-int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
-                    double wf_host, float* prior, const uint8_t* rgb_moments, bool from_S) {
+static void prior_args(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman, double wf_host,
+                       float* prior, const uint8_t* rgb_moments, bool from_S, PriorArgs& a) {
   const seg_params& p = c->p;
-  PriorArgs a;
   memset(&a, 0, sizeof(a));
   a.sal = const_cast<float*>(sal);
   a.from_S = from_S ? 1 : 0;
@@ -728,11 +810,20 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
   a.part_stride = pt_part_doubles(c->H, c->W);
   a.kal_adv = (use_kalman && (rgb_moments || c->io_mode)) ? c->kal : nullptr;
   a.io = c->io_mode ? c->io : nullptr;
+}
+
+int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
+                    double wf_host, float* prior, const uint8_t* rgb_moments, bool from_S) {
+  PriorArgs a;
+  prior_args(c, sal, prev_mask, use_kalman, wf_host, prior, rgb_moments, from_S, a);
   dim3 grid((c->W + PR_TX - 1) / PR_TX, (c->H + PR_TY - 1) / PR_TY, c->B);
   SEG_CUDA_TRY(seg_launch(k_prior, grid, 256, 0, c->stream, a));
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;
 }
+
+static void terms_args(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct, int32_t* ncap,
+                       TermsArgs& ta);
 
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
                             int32_t* cs, int32_t* ct, int32_t* ncap) {
@@ -773,6 +864,16 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     }
   }
   TermsArgs ta;
+  terms_args(c, rgb, prior, cs, ct, ncap, ta);
+  dim3 grid((c->W + 31) / 32, (c->H + 7) / 8, c->B);
+  SEG_CUDA_TRY(seg_launch(k_terms, grid, 256, 0, st, ta));
+  SEG_CUDA_TRY(cudaGetLastError());
+  return SEG_OK;
+}
+
+static void terms_args(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct, int32_t* ncap,
+                       TermsArgs& ta) {
+  const seg_params& p = c->p;
   ta.rgb = rgb;
   ta.prior = prior;
   ta.gauss = c->gauss;
@@ -790,10 +891,13 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   ta.io = c->io_mode ? c->io : nullptr;
   ta.gmm = c->gmm;
   ta.M = p.gmm_components;
-  dim3 grid((c->W + 31) / 32, (c->H + 8 * TM_ROWS - 1) / (8 * TM_ROWS), c->B);
-  SEG_CUDA_TRY(seg_launch(k_terms, grid, 256, 0, st, ta));
-  SEG_CUDA_TRY(cudaGetLastError());
-  return SEG_OK;
+}
+
+// A frame's prior, first moments (fused into k_prior), second moments and
+// terms: the launches of one frame's back half.
+int pt_launch_back(seg_ctx* c, const float* sal, float* prior, const uint8_t* rgb) {
+  int rc = pt_launch_prior(c, sal, c->prev_mask, 1, 0.0, prior, rgb, true);
+  return rc ? rc : pt_launch_moments_terms(c, rgb, prior, 0, c->cs, c->ct, c->ncap);
 }
 
 int pt_em_part_doubles(int H, int W) { return EM_NV * pt_mom_blocks(H, W); }

@@ -288,8 +288,7 @@ static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const in
 static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, uint8_t* mask,
                          int64_t* cut) {
   int rc = sal_launch(c, rgb, s, false);
-  if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb, true);
-  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
+  if (!rc) rc = pt_launch_back(c, s, pr, rgb);
   if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
   return rc;
 }
@@ -575,8 +574,7 @@ static void pipe_build_graphs(seg_ctx* c) {
     c->io = io_back;
     if (ok) ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      rc = pt_launch_prior(c, nullptr, c->prev_mask, 1, 0.0, nullptr, nullptr, true);
-      if (!rc) rc = pt_launch_moments_terms(c, nullptr, nullptr, 0, c->cs, c->ct, c->ncap);
+      rc = pt_launch_back(c, nullptr, nullptr, nullptr);
       if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, nullptr, c->prev_mask, nullptr);
       ok = cudaStreamEndCapture(c->stream, &g[2 * k + 1]) == cudaSuccess && !rc && g[2 * k + 1];
     }
@@ -650,8 +648,7 @@ extern "C" int seg_push_frame_ev(seg_ctx* c, const uint8_t* rgb, float* sal, flo
     SEG_CUDA_TRY(cudaGraphLaunch(c->gb[k], c->stream));
   } else {
     pipe_select(c, k);
-    rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb, true);
-    if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
+    rc = pt_launch_back(c, s, pr, rgb);
     if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, (int64_t*)ct);
     pipe_select(c, 0);
     if (rc) return rc;

@@ -270,6 +270,51 @@ struct GridBar {
   unsigned int pad1[31];
 };
 
+__device__ __forceinline__ long long seg_now() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Returns false
+// (in every thread of the CTA) once any CTA has recorded a timeout in status[0].
+// Arrival is an acq_rel atomic on the counter, release a release-add on the
+// generation word in another cache line, polled with acquire loads; the CTA
+// barriers before and after carry the other threads' writes (release and
+// acquire are cumulative), so no full fences are needed.  The timer is read
+// every 256 polls.  ok: a shared-memory word of the CTA.
+__device__ __forceinline__ bool seg_grid_sync(GridBar* bar, int* status, long long timeout_ns, int* ok_smem) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int g, old;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&bar->gen) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&bar->count) : "memory");
+    int ok = 1;
+    if (old + 1u == gridDim.x) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&bar->count) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->gen) : "memory");
+    } else {
+      const long long t0 = seg_now();
+      for (unsigned int k = 0;; ++k) {
+        unsigned int cur;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
+        if (cur != g) break;
+        if ((k & 255u) == 255u && seg_now() - t0 > timeout_ns) {
+          atomicCAS(&status[0], 0, SEG_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    int st;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(st) : "l"(&status[0]) : "memory");
+    if (st == SEG_ETIMEOUT) ok = 0;
+    *ok_smem = ok;
+  }
+  __syncthreads();
+  return *ok_smem != 0;
+}
+
 struct MFArgs {
   int H, W, N, ndir;
   int nframes, frame_h;  // a batch of frames stacked vertically: H = nframes * frame_h
@@ -396,6 +441,7 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
                             int32_t* cs, int32_t* ct, int32_t* ncap);
 int pt_part_doubles(int H, int W);
+int pt_launch_back(seg_ctx* c, const float* sal, float* prior, const uint8_t* rgb);
 int pt_em_part_doubles(int H, int W);
 void pt_fill_lut(const seg_params& p, int* lut_host);
 
