@@ -58,6 +58,7 @@ struct MFShared {
   unsigned char z[MF_HN];  // reach flags with halo
   int ok;
   unsigned int setmask;  // colours of the tiles this CTA pushed into during a phase
+  unsigned int dmask;    // dirty tiles of a round (mf_dirty_mask)
   long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
 };
 
@@ -78,15 +79,27 @@ __device__ __forceinline__ void mf_flag_begin(const MFArgs& a, unsigned int epoc
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(epoch + 1) % 3] = 0u;
 }
 
-// Block-uniform: did this tile or one of its 8 neighbours change in a round
-// with epoch >= since?  (A tile's fixpoint can only move when its halo moved.)
-__device__ bool mf_tile_dirty(const MFArgs& a, MFShared& s, int tx, int ty, int since) {
-  int d = 0;
-  if (threadIdx.x < 9) {
-    int x = tx + (int)threadIdx.x % 3 - 1, y = ty + (int)threadIdx.x / 3 - 1;
-    if (x >= 0 && x < a.ntx && y >= 0 && y < a.nty) d = *(volatile int*)&a.tstamp[y * a.ntx + x] >= since;
+// Block-uniform: bit i set if tile k0 + i * gridDim.x (i < 32, below ntiles) or
+// one of its 8 neighbours changed in a round with epoch >= since (a tile's
+// fixpoint can only move when its halo moved).  One read of all the tiles'
+// stamps at the start of a round, instead of one dependent read per tile; a
+// change made during this round is seen in the next one, which every change
+// triggers anyway.
+__device__ unsigned mf_dirty_mask(const MFArgs& a, MFShared& s, int k0, int since) {
+  if (threadIdx.x == 0) s.dmask = 0u;
+  __syncthreads();
+  if (threadIdx.x < 9 * 32) {
+    const int i = threadIdx.x / 9, n = threadIdx.x - 9 * i;
+    const int k = k0 + i * (int)gridDim.x;
+    if (k < a.ntx * a.nty) {
+      const int ty = k / a.ntx, tx = k - ty * a.ntx;
+      const int x = tx + n % 3 - 1, y = ty + n / 3 - 1;
+      if (x >= 0 && x < a.ntx && y >= 0 && y < a.nty && *(volatile int*)&a.tstamp[y * a.ntx + x] >= since)
+        atomicOr(&s.dmask, 1u << i);
+    }
   }
-  return __syncthreads_or(d) != 0;
+  __syncthreads();
+  return s.dmask;
 }
 
 // ---------------------------------------------------------------- BFS to the sink
@@ -323,42 +336,50 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   // to both of its terminal links, which adds the same constant to every cut
   // (minimum cuts unchanged), and the cut value sum(ct - residual to t) with the
   // original ct removes that constant again.
+  {  // (restrict, in this block only: the capacity, flow and residual planes never
+     // alias, so the unrolled iterations' loads can be issued ahead of the stores)
+  const int32_t* __restrict__ in_cs = a.cs;
+  const int32_t* __restrict__ in_ct = a.ct;
+  const int32_t* __restrict__ ncap = a.ncap;
+  const int* __restrict__ flow_in = a.flow;
+  int* __restrict__ r_out = a.r;
+#pragma unroll 2
   for (int u = gtid; u < N; u += nthr) {
     int y = u / W, x = u - y * W;
-    int cs = a.cs[u], ct = a.ct[u];
+    int cs = in_cs[u], ct = in_ct[u];
     bool bad = !cap_ok(cs) || !cap_ok(ct);
-    const int cE = x + 1 < W ? a.ncap[u] : 0;
-    const int cW = x > 0 ? a.ncap[u - 1] : 0;
-    const int cS = y + 1 < H ? a.ncap[N + u] : 0;
-    const int cN = y > 0 ? a.ncap[N + u - W] : 0;
+    const int cE = x + 1 < W ? ncap[u] : 0;
+    const int cW = x > 0 ? ncap[u - 1] : 0;
+    const int cS = y + 1 < H ? ncap[N + u] : 0;
+    const int cN = y > 0 ? ncap[N + u - W] : 0;
     bad |= !cap_ok(cE) || !cap_ok(cS);
     const bool warm = a.flow != nullptr && a.warm[y / a.frame_h];
     auto clampf = [](int f, int c) { return f > c ? c : (f < -c ? -c : f); };
     // forward flows leave u (E, S, SE, SW); backward ones (W, N, NW, NE) enter u
-    const int fE = warm && x + 1 < W ? clampf(a.flow[u], cE) : 0;
-    const int fW = warm && x > 0 ? clampf(a.flow[u - 1], cW) : 0;
-    const int fS = warm && y + 1 < H ? clampf(a.flow[N + u], cS) : 0;
-    const int fN = warm && y > 0 ? clampf(a.flow[N + u - W], cN) : 0;
+    const int fE = warm && x + 1 < W ? clampf(flow_in[u], cE) : 0;
+    const int fW = warm && x > 0 ? clampf(flow_in[u - 1], cW) : 0;
+    const int fS = warm && y + 1 < H ? clampf(flow_in[N + u], cS) : 0;
+    const int fN = warm && y > 0 ? clampf(flow_in[N + u - W], cN) : 0;
     int net_out = fE - fW + fS - fN;
-    a.r[0 * N + u] = cE - fE;
-    a.r[1 * N + u] = cW + fW;
-    a.r[2 * N + u] = cS - fS;
-    a.r[3 * N + u] = cN + fN;
+    r_out[0 * N + u] = cE - fE;
+    r_out[1 * N + u] = cW + fW;
+    r_out[2 * N + u] = cS - fS;
+    r_out[3 * N + u] = cN + fN;
     if (ND == 8) {
-      const int cSE = (x + 1 < W && y + 1 < H) ? a.ncap[2 * N + u] : 0;
-      const int cNW = (x > 0 && y > 0) ? a.ncap[2 * N + u - W - 1] : 0;
-      const int cSW = (x > 0 && y + 1 < H) ? a.ncap[3 * N + u] : 0;
-      const int cNE = (x + 1 < W && y > 0) ? a.ncap[3 * N + u - W + 1] : 0;
+      const int cSE = (x + 1 < W && y + 1 < H) ? ncap[2 * N + u] : 0;
+      const int cNW = (x > 0 && y > 0) ? ncap[2 * N + u - W - 1] : 0;
+      const int cSW = (x > 0 && y + 1 < H) ? ncap[3 * N + u] : 0;
+      const int cNE = (x + 1 < W && y > 0) ? ncap[3 * N + u - W + 1] : 0;
       bad |= !cap_ok(cSE) || !cap_ok(cSW);
-      const int fSE = warm && x + 1 < W && y + 1 < H ? clampf(a.flow[2 * N + u], cSE) : 0;
-      const int fNW = warm && x > 0 && y > 0 ? clampf(a.flow[2 * N + u - W - 1], cNW) : 0;
-      const int fSW = warm && x > 0 && y + 1 < H ? clampf(a.flow[3 * N + u], cSW) : 0;
-      const int fNE = warm && x + 1 < W && y > 0 ? clampf(a.flow[3 * N + u - W + 1], cNE) : 0;
+      const int fSE = warm && x + 1 < W && y + 1 < H ? clampf(flow_in[2 * N + u], cSE) : 0;
+      const int fNW = warm && x > 0 && y > 0 ? clampf(flow_in[2 * N + u - W - 1], cNW) : 0;
+      const int fSW = warm && x > 0 && y + 1 < H ? clampf(flow_in[3 * N + u], cSW) : 0;
+      const int fNE = warm && x + 1 < W && y > 0 ? clampf(flow_in[3 * N + u - W + 1], cNE) : 0;
       net_out += fSE - fNW + fSW - fNE;
-      a.r[4 * N + u] = cSE - fSE;
-      a.r[5 * N + u] = cNW + fNW;
-      a.r[6 * N + u] = cSW - fSW;
-      a.r[7 * N + u] = cNE + fNE;
+      r_out[4 * N + u] = cSE - fSE;
+      r_out[5 * N + u] = cNW + fNW;
+      r_out[6 * N + u] = cSW - fSW;
+      r_out[7 * N + u] = cNE + fNE;
     }
     int e0 = cs - net_out, cte = ct;
     if (e0 < 0) {  // deficit
@@ -369,6 +390,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     a.e[u] = e0 - m;
     a.rt[u] = cte - m;
     if (bad) atomicCAS(&a.status[0], 0, SEG_ECAPACITY);
+  }
   }
   for (int t = gtid; t < ntiles; t += nthr) {
     a.tstamp[t] = -2;
@@ -422,9 +444,13 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
       for (bool first = true;; first = false) {
         mf_flag_begin(a, epoch);
         bool ch = false;
-        for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        unsigned dm = 0u;
+        for (int k = blockIdx.x, i = 0; k < ntiles; k += gridDim.x, ++i) {
           int tx = k % a.ntx, ty = k / a.ntx;
-          if (!first && !mf_tile_dirty(a, s, tx, ty, (int)epoch - 1)) continue;
+          if (!first) {
+            if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
+            if (!((dm >> (i & 31)) & 1u)) continue;
+          }
           if (mf_tile_bfs<ND>(a, s, tx, ty, first)) {
             ch = true;
             if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
@@ -491,9 +517,13 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   for (bool first = true;; first = false) {
     mf_flag_begin(a, epoch);
     bool ch = false;
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    unsigned dm = 0u;
+    for (int k = blockIdx.x, i = 0; k < ntiles; k += gridDim.x, ++i) {
       int tx = k % a.ntx, ty = k / a.ntx;
-      if (!first && !mf_tile_dirty(a, s, tx, ty, (int)epoch - 1)) continue;
+      if (!first) {
+        if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
+        if (!((dm >> (i & 31)) & 1u)) continue;
+      }
       if (mf_tile_reach<ND>(a, s, tx, ty, first)) {
         ch = true;
         if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
