@@ -55,7 +55,25 @@ __global__ void k_rgb_max(const TIn* __restrict__ rgb, int n, int* smax, unsigne
     mm[2 * tid + 1] = 0u;
   }
   int m = 0;
-  for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
+  bool done = false;
+  if constexpr (std::is_same<TIn, uint8_t>::value) {
+    if ((n & 15) == 0 && ((uintptr_t)rgb & 15) == 0) {  // 16 pixels = three 16-byte loads
+      const uint4* q = reinterpret_cast<const uint4*>(rgb);
+      for (int g = tid; g < (n >> 4); g += gridDim.x * blockDim.x) {
+        const uint4 v0 = q[3 * (size_t)g], v1 = q[3 * (size_t)g + 1], v2 = q[3 * (size_t)g + 2];
+        const unsigned w[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          int s = 0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) s += (w[(3 * k + c) >> 2] >> (8 * ((3 * k + c) & 3))) & 255u;
+          m = max(m, s);
+        }
+      }
+      done = true;
+    }
+  }
+  for (int i = tid; !done && i < n; i += gridDim.x * blockDim.x) {
     if constexpr (std::is_same<TIn, uint8_t>::value) {
       int s = rgb[3 * (size_t)i] + rgb[3 * (size_t)i + 1] + rgb[3 * (size_t)i + 2];
       m = max(m, s);
@@ -100,48 +118,8 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
   const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
   const int smax = smax_p[fb];
-  // all of this thread's input pixels are loaded first (independent loads in
-  // flight together), then turned into features
-  constexpr int NIN = RED_IN_Y * RED_IN_X, PER = (NIN + 255) / 256;
-  constexpr int NW = U8 ? 1 : 3;  // registers per input pixel
-  unsigned pk[PER][NW];
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    int i = threadIdx.x + k * 256;
-    if (i < NIN) {
-      int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
-      int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
-      const TIn* p = rgb + 3 * ((size_t)gy * W + gx);
-      if constexpr (U8) {
-        pk[k][0] = (unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) pk[k][j] = __float_as_uint(p[j]);
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    int i = threadIdx.x + k * 256;
-    if (i >= NIN) break;
-    int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
-    float r, g, b, s;
-    bool hue;
-    if constexpr (U8) {
-      int ri = pk[k][0] & 255, gi = (pk[k][0] >> 8) & 255, bi = pk[k][0] >> 16;
-      int si = ri + gi + bi;
-      hue = 10 * si > smax;
-      r = (float)ri;
-      g = (float)gi;
-      b = (float)bi;
-      s = (float)si;
-    } else {
-      r = __uint_as_float(pk[k][0]);
-      g = __uint_as_float(pk[k][1]);
-      b = __uint_as_float(pk[k][2]);
-      s = r + g + b;
-      hue = 10.f * s > __int_as_float(smax);
-    }
+  // features of input pixel (ry, rx) of the tile into sF
+  auto feat = [&](int ry, int rx, float r, float g, float b, float s, bool hue) {
     float rn = 0.f, gn = 0.f, bn = 0.f;
     if (hue) {
       float inv = 3.f / s;
@@ -156,6 +134,68 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
     sF[0][ry][rx] = s / 765.f;
     sF[1][ry][rx] = R - G;
     sF[2][ry][rx] = B - Y;
+  };
+  constexpr int NIN = RED_IN_Y * RED_IN_X, PER = (NIN + 255) / 256;
+  // RGB8 tile away from the frame border, rows 4-byte aligned: the tile's rows
+  // as 32-bit words (RED_IN_X pixels = 201 bytes from byte 3 gx0, read from the
+  // aligned byte 3 gx0 - 2) staged in sH's space, a quarter of the byte loads
+  constexpr int RWORDS = (3 * RED_IN_X + 2 + 3) / 4;
+  static_assert(RED_IN_Y * RWORDS * 4 <= (int)sizeof(sH), "staged rows fit sH");
+  bool staged = false;
+  if constexpr (U8)
+    staged = (W & 3) == 0 && ((uintptr_t)rgb & 3) == 0 && gx0 >= 1 && gy0 >= 0 &&
+             4 * RWORDS + 3 * gx0 - 2 <= 3 * W && gy0 + RED_IN_Y <= H;
+  if (staged) {
+    unsigned* sw = reinterpret_cast<unsigned*>(&sH[0][0][0]);
+    const unsigned* gw = reinterpret_cast<const unsigned*>(rgb);
+    for (int i = threadIdx.x; i < RED_IN_Y * RWORDS; i += blockDim.x) {
+      const int ry = i / RWORDS, c = i - ry * RWORDS;
+      sw[i] = gw[((size_t)(gy0 + ry) * 3 * W + 3 * gx0 - 2) / 4 + c];
+    }
+    __syncthreads();
+    const unsigned char* sb = reinterpret_cast<const unsigned char*>(sw);
+    for (int i = threadIdx.x; i < NIN; i += blockDim.x) {
+      const int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
+      const unsigned char* q = sb + ry * 4 * RWORDS + 2 + 3 * rx;
+      const int ri = q[0], gi = q[1], bi = q[2], si = ri + gi + bi;
+      feat(ry, rx, (float)ri, (float)gi, (float)bi, (float)si, 10 * si > smax);
+    }
+    __syncthreads();  // (sH is overwritten next)
+  } else {
+    // all of this thread's input pixels are loaded first (independent loads in
+    // flight together), then turned into features
+    constexpr int NW = U8 ? 1 : 3;  // registers per input pixel
+    unsigned pk[PER][NW];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      int i = threadIdx.x + k * 256;
+      if (i < NIN) {
+        int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
+        int gy = seg_clampi(gy0 + ry, 0, H - 1), gx = seg_clampi(gx0 + rx, 0, W - 1);
+        const TIn* p = rgb + 3 * ((size_t)gy * W + gx);
+        if constexpr (U8) {
+          pk[k][0] = (unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) pk[k][j] = __float_as_uint(p[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      int i = threadIdx.x + k * 256;
+      if (i >= NIN) break;
+      int ry = i / RED_IN_X, rx = i - ry * RED_IN_X;
+      if constexpr (U8) {
+        int ri = pk[k][0] & 255, gi = (pk[k][0] >> 8) & 255, bi = pk[k][0] >> 16;
+        int si = ri + gi + bi;
+        feat(ry, rx, (float)ri, (float)gi, (float)bi, (float)si, 10 * si > smax);
+      } else {
+        float r = __uint_as_float(pk[k][0]), g = __uint_as_float(pk[k][1]), b = __uint_as_float(pk[k][2]);
+        float sum = r + g + b;
+        feat(ry, rx, r, g, b, sum, 10.f * sum > __int_as_float(smax));
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 3 * RED_IN_Y * RED_TX; i += blockDim.x) {
@@ -823,8 +863,22 @@ __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, i
   const int fb = blockIdx.z;  // frame of the batch
   S += (size_t)fb * hs * ws;
   sal += (size_t)fb * H * W;
-  int x = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
-  if (x < W && y < H) sal[(size_t)y * W + x] = seg_bilinear_t(S, ws, frow[y], fcol[x]);
+  const int xq = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
+  if (y >= H) return;
+  const int2 ry = frow[y];
+  float* row = sal + (size_t)y * W;
+  if ((W & 3) == 0 && ((uintptr_t)sal & 15) == 0) {  // four pixels, one 16-byte store
+    const int x = 4 * xq;
+    if (x >= W) return;
+    float4 v;
+    v.x = seg_bilinear_t(S, ws, ry, fcol[x]);
+    v.y = seg_bilinear_t(S, ws, ry, fcol[x + 1]);
+    v.z = seg_bilinear_t(S, ws, ry, fcol[x + 2]);
+    v.w = seg_bilinear_t(S, ws, ry, fcol[x + 3]);
+    *reinterpret_cast<float4*>(row + x) = v;
+  } else {
+    for (int x = 4 * xq; x < 4 * xq + 4 && x < W; ++x) row[x] = seg_bilinear_t(S, ws, ry, fcol[x]);
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -1185,7 +1239,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   else
     SEG_CUDA_TRY(seg_launch(k_consp<false>, B, 1024, 0, st, pa));
   if (upsample) {
-    dim3 gu((W + 63) / 64, (H + 3) / 4, B);
+    dim3 gu((W + 255) / 256, (H + 3) / 4, B);  // 4 pixels per thread
     SEG_CUDA_TRY(seg_launch(k_upsample, gu, 256, 0, st, s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,
                                    s.rs + s.rs_fcol));
   }
