@@ -148,10 +148,19 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
   if (staged) {
     unsigned* sw = reinterpret_cast<unsigned*>(&sH[0][0][0]);
     const unsigned* gw = reinterpret_cast<const unsigned*>(rgb);
-    for (int i = threadIdx.x; i < RED_IN_Y * RWORDS; i += blockDim.x) {
-      const int ry = i / RWORDS, c = i - ry * RWORDS;
-      sw[i] = gw[((size_t)(gy0 + ry) * 3 * W + 3 * gx0 - 2) / 4 + c];
+    constexpr int NWD = RED_IN_Y * RWORDS, PW = (NWD + 255) / 256;  // (256 threads)
+    unsigned wv[PW];
+#pragma unroll
+    for (int k = 0; k < PW; ++k) {  // every load in flight before the first store
+      const int i = threadIdx.x + 256 * k;
+      if (i < NWD) {
+        const int ry = i / RWORDS, c = i - ry * RWORDS;
+        wv[k] = gw[((size_t)(gy0 + ry) * 3 * W + 3 * gx0 - 2) / 4 + c];
+      }
     }
+#pragma unroll
+    for (int k = 0; k < PW; ++k)
+      if (threadIdx.x + 256 * k < NWD) sw[threadIdx.x + 256 * k] = wv[k];
     __syncthreads();
     const unsigned char* sb = reinterpret_cast<const unsigned char*>(sw);
     for (int i = threadIdx.x; i < NIN; i += blockDim.x) {
