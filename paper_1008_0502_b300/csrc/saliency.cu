@@ -23,6 +23,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "seg_internal.cuh"
@@ -890,6 +891,119 @@ __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, i
   }
 }
 
+// The same maps on a cluster of four CTAs per frame (one conspicuity map each),
+// exchanging the N(.) coefficients through distributed shared memory:
+//   1. CTA r: N(.) statistics of orientation maps r, r + 4, ..; every CTA
+//      receives every orientation map's affine form.
+//   2. CTA 3: C_O = sum_theta N(B_theta) (same order and arithmetic as
+//      k_consp) and its N(.) form; CTAs 0-2: the N(.) forms of I, RG, BY.
+//   3. Every CTA: S = sum_k w_k N(C_k) over the whole map in shared memory (C_O
+//      read from CTA 3), writing a quarter of N(C_k) and S out, and a quarter
+//      of the up-sampling's candidate samples for the maximum; CTA 0 takes the
+//      cluster's maximum.
+// Per map the statistics are those of k_consp (the same sums in the same
+// order while a map has at most 512 N(.) tiles), so the outputs match it.
+#define CC_CTAS 4
+#define CC_THREADS 512
+
+__global__ void __cluster_dims__(CC_CTAS, 1, 1) __launch_bounds__(CC_THREADS) k_consp_cl(ConspArgs a) {
+  seg_pdl_enter();
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank(), fb = blockIdx.x / CC_CTAS;
+  extern __shared__ float dsm[];  // C_O (CTA 3), then S: n floats each
+  __shared__ float ab[8];
+  __shared__ float red[12 * 32];
+  __shared__ unsigned tmax[4 * CONSP_TILES];
+  __shared__ float abO[2 * SEG_MAX_ORIENT];  // every orientation map's N(.) form
+  __shared__ float abC[8];                   // the four conspicuity maps' forms
+  __shared__ unsigned smx;                   // (CTA 0) the cluster's maximum, float bits >= 0
+  const int n = a.h * a.w, no = a.nch - 3;
+  const float* acc = a.acc + (size_t)fb * a.nch * n;
+  float* const csum_g = a.csum + (size_t)fb * n;
+  float* const S_g = a.S + (size_t)fb * n;
+  float* const consp = a.consp + (size_t)fb * 4 * n;
+  float* const csum_s = dsm;
+  float* const S_s = dsm + n;
+  if (r == 0 && threadIdx.x == 0) smx = 0u;
+  {  // 1. orientation maps r, r + 4, ..
+    const float* v[4];
+    int nm = 0;
+    for (int m = r; m < no && nm < 4; m += CC_CTAS) v[nm++] = acc + (size_t)(3 + m) * n;
+    if (nm > 0) block_norm_multi(v, nm, a.h, a.w, a.tile, a.flat, ab, red, tmax);
+    if ((int)threadIdx.x < nm) {
+      const int m = r + CC_CTAS * threadIdx.x;
+      for (int q = 0; q < CC_CTAS; ++q) {
+        float* d = cl.map_shared_rank(abO, q);
+        d[2 * m] = ab[2 * threadIdx.x];
+        d[2 * m + 1] = ab[2 * threadIdx.x + 1];
+      }
+    }
+  }
+  cl.sync();
+  {  // 2. C_O on CTA 3; each CTA's conspicuity map's N(.) form
+    const float* v[1];
+    if (r == 3) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float c = 0.f;
+        for (int m = 0; m < no; ++m) c += abO[2 * m] * acc[(size_t)(3 + m) * n + i] + abO[2 * m + 1];
+        csum_s[i] = c;
+        csum_g[i] = c;
+      }
+      __syncthreads();
+      v[0] = csum_s;
+    } else {
+      v[0] = acc + (size_t)r * n;
+    }
+    block_norm_multi(v, 1, a.h, a.w, a.tile, a.flat, ab, red, tmax);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < CC_CTAS; ++q) {
+        float* d = cl.map_shared_rank(abC, q);
+        d[2 * r] = ab[0];
+        d[2 * r + 1] = ab[1];
+      }
+  }
+  cl.sync();
+  // 3. S over the whole map; this CTA's quarter of N(C_k) and S written out
+  float wk[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wk[k] = a.wdev ? (float)a.wdev[k] : a.wgt[k];
+  const float* co = cl.map_shared_rank(csum_s, 3);
+  const int q0 = (int)(((long long)n * r) / CC_CTAS), q1 = (int)(((long long)n * (r + 1)) / CC_CTAS);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float x[4] = {acc[i], acc[(size_t)n + i], acc[2 * (size_t)n + i], co[i]};
+    float S = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float nv = abC[2 * k] * x[k] + abC[2 * k + 1];
+      if (i >= q0 && i < q1) consp[(size_t)k * n + i] = nv;
+      S += wk[k] * nv;
+    }
+    S_s[i] = S;
+    if (i >= q0 && i < q1) S_g[i] = S;
+  }
+  // maximum of the bilinear up-sampling over its candidate samples (k_consp):
+  // this CTA takes the candidate rows y with y mod 4 = r, against every
+  // candidate column (the lists' order, set by atomics, does not matter)
+  int* crow = (int*)tmax;
+  int* ccol = crow + 2048;
+  __shared__ int nr, nc;
+  if (threadIdx.x == 0) nr = nc = 0;
+  __syncthreads();
+  for (int y = r + CC_CTAS * (int)threadIdx.x; y < a.H; y += CC_CTAS * blockDim.x)
+    if (seg_up_candidate(y, a.h, a.H)) crow[atomicAdd(&nr, 1)] = y;
+  for (int x = threadIdx.x; x < a.W; x += blockDim.x)
+    if (seg_up_candidate(x, a.w, a.W)) ccol[atomicAdd(&nc, 1)] = x;
+  __syncthreads();
+  float mxv = 0.f;
+  for (int k = threadIdx.x; k < nr * nc; k += blockDim.x)
+    mxv = fmaxf(mxv, seg_bilinear_t(S_s, a.w, a.frow[crow[k / nc]], a.fcol[ccol[k % nc]]));
+  mxv = seg_warp_max_f(mxv);
+  if ((threadIdx.x & 31) == 0) atomicMax(cl.map_shared_rank(&smx, 0), __float_as_uint(mxv));
+  cl.sync();
+  if (r == 0 && threadIdx.x == 0) a.salmax[fb] = smx;
+}
+
 // ------------------------------------------------------------------ host side
 static void make_taps(const seg_params& p, GaborTaps& t) {
   memset(&t, 0, sizeof(t));
@@ -975,6 +1089,11 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
     s.consp_staged = need <= cap && cudaFuncSetAttribute(k_consp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)cap) == cudaSuccess;
     s.consp_smem = s.consp_staged ? need : 0;
+    // the cluster form: C_O and S (2 maps) in dynamic shared memory
+    const size_t need_cl = sizeof(float) * 2 * (size_t)s.hl[s.sS] * s.wl[s.sS];
+    s.consp_cl = s.nch - 3 <= SEG_MAX_ORIENT && need_cl <= cap &&
+                 cudaFuncSetAttribute(k_consp_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) == cudaSuccess;
+    s.consp_cl_smem = s.consp_cl ? need_cl : 0;
     cudaGetLastError();
   }
   size_t off = 0;
@@ -1243,7 +1362,9 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   pa.salmax = s.salmax;
   pa.frow = s.rs + s.rs_frow;
   pa.fcol = s.rs + s.rs_fcol;
-  if (s.consp_staged)
+  if (s.consp_cl)
+    SEG_CUDA_TRY(seg_launch(k_consp_cl, CC_CTAS * B, CC_THREADS, s.consp_cl_smem, st, pa));
+  else if (s.consp_staged)
     SEG_CUDA_TRY(seg_launch(k_consp<true>, B, 1024, s.consp_smem, st, pa));
   else
     SEG_CUDA_TRY(seg_launch(k_consp<false>, B, 1024, 0, st, pa));

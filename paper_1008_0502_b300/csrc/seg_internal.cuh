@@ -213,6 +213,8 @@ struct SalWS {
   int* smax;         // frame max of r+g+b
   int consp_staged;  // k_consp stages its maps in shared memory
   size_t consp_smem; // its dynamic shared memory
+  int consp_cl;       // the four-CTA cluster form of k_consp runs instead
+  size_t consp_cl_smem;
   GaborTaps taps;
   // resampling tables (seg_rs_entry): per center-surround pair p, rows
   // hl[s]->hl[c] at rs + rs_row[p] and columns wl[s]->wl[c] at rs + rs_col[p];
