@@ -604,14 +604,14 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
 }
 
 // ------------------------------------------------------------------ fused across-scale sum
-// B_{c_max} over one 16 x 8 tile of sigma_S per CTA (one channel, one frame),
+// B_{c_max} over one 8 x 8 tile of sigma_S per CTA (one channel, one frame),
 // level by level from c_min over the tile's halo regions: the region of level
 // c_max - k starts at 2^k (Y0, X0) - 3 (2^k - 1) and holds 2^k 8 + 3 (2^k - 1)
-// rows (resp. 16 columns), each entry at its clamped level coordinate, so every
+// rows and columns, each entry at its clamped level coordinate, so every
 // REDUCE input the next level needs is in shared memory.  Same sums as the
 // level-by-level kernel: B_c = sum over pairs (c, s) of N(CS(c, s)) + REDUCE(B_{c-1}).
 // Up to two REDUCE steps (c_max - c_min <= 2).
-#define FA_TX 16
+#define FA_TX 8  // (16 x 8: 84 CTAs at 640x480 and 67.5 us for the saliency; 8 x 4: 71.0; 8 x 8: 65.2)
 #define FA_TY 8
 #define FA_N(t, k) (((t) << (k)) + 3 * ((1 << (k)) - 1))
 
