@@ -336,6 +336,17 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   // to both of its terminal links, which adds the same constant to every cut
   // (minimum cuts unchanged), and the cut value sum(ct - residual to t) with the
   // original ct removes that constant again.
+  if (a.init_done) {
+    // the terms kernel formed e, rt and r (same arithmetic); each CTA clears the
+    // flags of the tiles it takes in the relabel and reach rounds, so no barrier
+    // is needed before the first one
+    if (threadIdx.x == 0)
+      for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        a.tstamp[k] = -2;
+        a.tact[k] = 1;
+      }
+    __syncthreads();
+  } else {
   {  // (restrict, in this block only: the capacity, flow and residual planes never
      // alias, so the unrolled iterations' loads can be issued ahead of the stores)
   const int32_t* __restrict__ in_cs = a.cs;
@@ -398,6 +409,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   }
   if (!mf_grid_sync(a, s)) return;
   if (*(volatile int*)&a.status[0] == SEG_ECAPACITY) return;
+  }
 
   unsigned int epoch = 0;
   int cycle = 0, n_gr = 0, n_rounds = 0;
@@ -630,7 +642,7 @@ int mf_grid_size(int H, int W, int* grid) {
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed) {
+              const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed, bool init_done) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
   a.flow = flow;
@@ -667,6 +679,7 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   a.gr_every = gr_every < 1 ? 1 : gr_every;
   a.local_iters = local_iters < 1 ? 1 : local_iters;
   a.timeout_ns = 4000000000LL;
+  a.init_done = init_done ? 1 : 0;
   if (!words_zeroed) {  // (else the caller's frame-start kernel has zeroed them)
     SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, st));
     SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));

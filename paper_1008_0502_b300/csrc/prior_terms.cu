@@ -609,6 +609,14 @@ struct TermsArgs {
   const SegIO* io;  // rgb / prior == nullptr: take them from here
   const GmmDev* gmm;  // M > 1: [frame][label] colour mixtures
   int M;
+  // the min cut's initial residual graph, formed here (seg_push_frame; nullptr:
+  // off): residual planes e, rt and r[2 nk] over the stacked grid (plane stride
+  // N B); flow / warm: the warm start's previous n-link flows and per-frame flag
+  int* mf_e;
+  int* mf_rt;
+  int* mf_r;
+  const int* flow;
+  const unsigned char* warm;
 };
 
 __device__ __forceinline__ int32_t quant_cap(float K, float x) {
@@ -623,6 +631,8 @@ struct TermsIn {
   int r8, g8, b8;
   float pr;
   int nsum[4];
+  int bsum[4];  // (fused initialisation) r + g + b of the backward neighbours W, N, NW, NE, -1 outside
+  int fl[8];    // (fused warm start) the flows of the eight links, forward ones first
 };
 
 __device__ __forceinline__ void terms_load(const TermsArgs& a, int x, int y, TermsIn& t) {
@@ -641,6 +651,33 @@ __device__ __forceinline__ void terms_load(const TermsArgs& a, int x, int y, Ter
     if (xx >= 0 && xx < a.W && yy < a.H) {
       const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
       t.nsum[k] = q[0] + q[1] + q[2];
+    }
+  }
+  if (a.mf_r) {
+    // backward neighbour k: W (-1, 0), N (0, -1), NW (-1, -1), NE (+1, -1)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      t.bsum[k] = -1;
+      if (k >= a.nk) continue;
+      const int xx = x + (k == 1 ? 0 : k == 3 ? 1 : -1), yy = y - (k == 0 ? 0 : 1);
+      if (xx >= 0 && xx < a.W && yy >= 0) {
+        const uint8_t* q = a.rgb + 3 * ((size_t)yy * a.W + xx);
+        t.bsum[k] = q[0] + q[1] + q[2];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d) t.fl[d] = 0;
+    if (a.flow) {
+      // forward link k of this node, and the backward one: forward link k of the
+      // neighbour it comes from (its plane k)
+      const size_t NB = (size_t)a.H * a.W * a.B;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k >= a.nk) continue;
+        if (t.nsum[k] >= 0) t.fl[k] = a.flow[k * NB + g];
+        const int xx = x + (k == 1 ? 0 : k == 3 ? 1 : -1), yy = y - (k == 0 ? 0 : 1);
+        if (t.bsum[k] >= 0) t.fl[4 + k] = a.flow[k * NB + (size_t)yy * a.W + xx];
+      }
     }
   }
 }
@@ -692,13 +729,44 @@ __device__ __forceinline__ void terms_store(const TermsArgs& a, const GaussDev& 
     D[lab] = a.lambda_u * psi + xi;
   }
   const float m = fminf(D[0], D[1]);
-  a.cs[g] = quant_cap(a.K, D[0] - m);  // c(s, v) = D(0): paid when v is background
-  a.ct[g] = quant_cap(a.K, D[1] - m);  // c(v, t) = D(1): paid when v is object
+  const int32_t csq = quant_cap(a.K, D[0] - m), ctq = quant_cap(a.K, D[1] - m);
+  a.cs[g] = csq;  // c(s, v) = D(0): paid when v is background
+  a.ct[g] = ctq;  // c(v, t) = D(1): paid when v is object
   const int s0 = t.r8 + t.g8 + t.b8;
+  int cf[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (k >= a.nk) break;
-    a.ncap[k * NB + g] = t.nsum[k] < 0 ? 0 : lut[2 * abs(s0 - t.nsum[k]) + (k >= 2)];
+    cf[k] = t.nsum[k] < 0 ? 0 : lut[2 * abs(s0 - t.nsum[k]) + (k >= 2)];
+    a.ncap[k * NB + g] = cf[k];
+  }
+  if (a.mf_r) {
+    // the min cut's initial state (its init pass, done here): residuals of the
+    // eight directed links from the capacities (a backward link's capacity is the
+    // neighbour's forward one, the same table entry) and, warm, the previous
+    // flows clamped to them; source arcs saturated and s->v->t flow cancelled.
+    // Directions E W S N SE NW SW NE: forward link k is direction 2k, and
+    // backward link k (from W, N, NW, NE) direction 2k + 1.
+    const bool warm = a.flow != nullptr && a.warm[0];
+    auto clampf = [](int f, int c) { return f > c ? c : (f < -c ? -c : f); };
+    int net_out = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k >= a.nk) break;
+      const int cb = t.bsum[k] < 0 ? 0 : lut[2 * abs(s0 - t.bsum[k]) + (k >= 2)];
+      const int ff = warm ? clampf(t.fl[k], cf[k]) : 0, fb = warm ? clampf(t.fl[4 + k], cb) : 0;
+      a.mf_r[(2 * k) * NB + g] = cf[k] - ff;
+      a.mf_r[(2 * k + 1) * NB + g] = cb + fb;
+      net_out += ff - fb;
+    }
+    int e0 = csq - net_out, cte = ctq;
+    if (e0 < 0) {  // deficit
+      cte = ctq - e0;
+      e0 = 0;
+    }
+    const int m = min(e0, cte);
+    a.mf_e[g] = e0 - m;
+    a.mf_rt[g] = cte - m;
   }
 }
 
@@ -716,6 +784,15 @@ __device__ __forceinline__ void terms_frame(TermsArgs& a, int fb) {
   a.ct += fb * N;
   a.ncap += fb * N;
   a.gmm += 2 * fb;
+  if (a.mf_r) {
+    a.mf_e += fb * N;
+    a.mf_rt += fb * N;
+    a.mf_r += fb * N;
+    if (a.flow) {
+      a.flow += fb * N;
+      a.warm += fb;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
@@ -823,10 +900,10 @@ int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int 
 }
 
 static void terms_args(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct, int32_t* ncap,
-                       TermsArgs& ta);
+                       TermsArgs& ta, bool mf_init);
 
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
-                            int32_t* cs, int32_t* ct, int32_t* ncap) {
+                            int32_t* cs, int32_t* ct, int32_t* ncap, bool mf_init) {
   const seg_params& p = c->p;
   cudaStream_t st = c->stream;
   int N = c->N;
@@ -864,7 +941,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     }
   }
   TermsArgs ta;
-  terms_args(c, rgb, prior, cs, ct, ncap, ta);
+  terms_args(c, rgb, prior, cs, ct, ncap, ta, mf_init);
   dim3 grid((c->W + 31) / 32, (c->H + 7) / 8, c->B);
   SEG_CUDA_TRY(seg_launch(k_terms, grid, 256, 0, st, ta));
   SEG_CUDA_TRY(cudaGetLastError());
@@ -872,8 +949,13 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
 }
 
 static void terms_args(seg_ctx* c, const uint8_t* rgb, const float* prior, int32_t* cs, int32_t* ct, int32_t* ncap,
-                       TermsArgs& ta) {
+                       TermsArgs& ta, bool mf_init) {
   const seg_params& p = c->p;
+  ta.mf_e = mf_init ? c->mf.e : nullptr;
+  ta.mf_rt = mf_init ? c->mf.rt : nullptr;
+  ta.mf_r = mf_init ? c->mf.r : nullptr;
+  ta.flow = mf_init && p.warm_start ? c->flow : nullptr;
+  ta.warm = mf_init && p.warm_start ? c->warm : nullptr;
   ta.rgb = rgb;
   ta.prior = prior;
   ta.gauss = c->gauss;
@@ -894,10 +976,12 @@ static void terms_args(seg_ctx* c, const uint8_t* rgb, const float* prior, int32
 }
 
 // A frame's prior, first moments (fused into k_prior), second moments and
-// terms: the launches of one frame's back half.
+// terms, the terms kernel also forming the min cut's initial residual graph
+// (the cut then runs with init_done): the launches of one frame's back half
+// before the cut.
 int pt_launch_back(seg_ctx* c, const float* sal, float* prior, const uint8_t* rgb) {
   int rc = pt_launch_prior(c, sal, c->prev_mask, 1, 0.0, prior, rgb, true);
-  return rc ? rc : pt_launch_moments_terms(c, rgb, prior, 0, c->cs, c->ct, c->ncap);
+  return rc ? rc : pt_launch_moments_terms(c, rgb, prior, 0, c->cs, c->ct, c->ncap, true);
 }
 
 int pt_em_part_doubles(int H, int W) { return EM_NV * pt_mom_blocks(H, W); }

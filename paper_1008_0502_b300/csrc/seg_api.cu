@@ -270,17 +270,17 @@ extern "C" int seg_reset_stream(seg_ctx* c, int b) {
 // would join two frames have capacity 0 (the terms kernel writes 0 for every
 // neighbour outside the frame), so the stacked cut is the B cuts side by side.
 static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
-                      uint8_t* mask, uint8_t* mask_state, int64_t* cut) {
+                      uint8_t* mask, uint8_t* mask_state, int64_t* cut, bool init_done = false) {
   // the per-stream path (mask_state set) warm-starts from the stream's last cut
   int* flow = (mask_state && c->p.warm_start) ? c->flow : nullptr;
   unsigned char* warm = flow ? c->warm : nullptr;
   if (c->io_mode)  // mask and cut come from the frame's SegIO; k_set_io zeroed the words
     return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
                      nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
-                     c->p.local_iters, c->io, flow, warm, true);
+                     c->p.local_iters, c->io, flow, warm, true, init_done);
   return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
-                   c->p.global_relabel_every, c->p.local_iters, nullptr, flow, warm);
+                   c->p.global_relabel_every, c->p.local_iters, nullptr, flow, warm, false, init_done);
 }
 
 // The launch sequence of one frame.  With c->io_mode set (graph capture) every
@@ -289,7 +289,7 @@ static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, ui
                          int64_t* cut) {
   int rc = sal_launch(c, rgb, s, false);
   if (!rc) rc = pt_launch_back(c, s, pr, rgb);
-  if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
+  if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut, true);
   return rc;
 }
 
@@ -382,9 +382,9 @@ extern "C" int seg_push_frame(seg_ctx* c, const uint8_t* rgb, float* sal, float*
   prof_mark(c, 1);
   if (!rc) rc = pt_launch_prior(c, s, c->prev_mask, 1, 0.0, pr, rgb, true);
   prof_mark(c, 2);
-  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap);
+  if (!rc) rc = pt_launch_moments_terms(c, rgb, pr, 0, c->cs, c->ct, c->ncap, true);
   prof_mark(c, 3);
-  if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut);
+  if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut, true);
   prof_mark(c, 4);
   if (!rc && c->prof_on && c->prof_n < c->prof_cap) {
     SEG_CUDA_TRY(cudaMemcpyAsync(c->prof_cycles + 7 * c->prof_n, c->status + 1, 7 * sizeof(int),
@@ -575,7 +575,7 @@ static void pipe_build_graphs(seg_ctx* c) {
     if (ok) ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       rc = pt_launch_back(c, nullptr, nullptr, nullptr);
-      if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, nullptr, c->prev_mask, nullptr);
+      if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, nullptr, c->prev_mask, nullptr, true);
       ok = cudaStreamEndCapture(c->stream, &g[2 * k + 1]) == cudaSuccess && !rc && g[2 * k + 1];
     }
     c->io_mode = 0;
@@ -649,7 +649,7 @@ extern "C" int seg_push_frame_ev(seg_ctx* c, const uint8_t* rgb, float* sal, flo
   } else {
     pipe_select(c, k);
     rc = pt_launch_back(c, s, pr, rgb);
-    if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, (int64_t*)ct);
+    if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, (int64_t*)ct, true);
     pipe_select(c, 0);
     if (rc) return rc;
   }

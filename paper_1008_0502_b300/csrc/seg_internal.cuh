@@ -345,6 +345,7 @@ struct MFArgs {
                // [4..7] time in init / global relabel / discharge / reach, 0.1 us units
   int max_cycles, gr_every, local_iters;
   long long timeout_ns;
+  int init_done;  // e, rt and r already hold the initial residual graph (formed by the terms kernel)
 };
 
 struct MFWS {
@@ -441,7 +442,7 @@ int pt_launch_salmax(seg_ctx* c, const float* sal);
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
                     double wf_host, float* prior, const uint8_t* rgb_moments, bool from_S = false);
 int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, int first_pass,
-                            int32_t* cs, int32_t* ct, int32_t* ncap);
+                            int32_t* cs, int32_t* ct, int32_t* ncap, bool mf_init = false);
 int pt_part_doubles(int H, int W);
 int pt_launch_back(seg_ctx* c, const float* sal, float* prior, const uint8_t* rgb);
 int pt_em_part_doubles(int H, int W);
@@ -455,6 +456,6 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
               const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr,
-              bool words_zeroed = false);
+              bool words_zeroed = false, bool init_done = false);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }
