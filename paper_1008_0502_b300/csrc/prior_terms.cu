@@ -254,15 +254,17 @@ __device__ __forceinline__ void prior_tile(const PriorArgs& a, int X0, int Y0, f
 }
 
 __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
-  seg_pdl_enter();
   __shared__ float sM[PR_TY + 2 * PR_MAXR][PR_TX + 2 * PR_MAXR];
   __shared__ float sH[PR_TY + 2 * PR_MAXR][PR_TX];
   __shared__ float s_wf;
   __shared__ float sTap[2 * PR_MAXR + 1];
+  // Before waiting for the preceding kernel (the saliency's last, which writes S
+  // and its maximum): the I/O pointers, the Kalman state and the previous mask
+  // tile, none of which it writes (the mask tile is unused when w_f = 0).
   prior_frame(a, blockIdx.z);
   prior_setup(a, sTap, &s_wf);
-  // (the mask tile is fetched while the weight is formed; unused when w_f = 0)
   if (a.prev) prior_tile_mask(a, blockIdx.x * PR_TX, blockIdx.y * PR_TY, sM);
+  seg_pdl_enter();
   const float mx = __uint_as_float(*a.salmax);
   __syncthreads();
   const float wff = s_wf;
@@ -796,6 +798,9 @@ __device__ __forceinline__ void terms_frame(TermsArgs& a, int fb) {
 }
 
 __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
+  // (Loading the inputs the preceding kernel does not write before waiting for
+  // it took 3 us off this kernel alone but slowed pipelined frames: its early
+  // CTAs' loads competed with the next frame's saliency.)
   seg_pdl_enter();
   __shared__ int sLut[766 * 2];
   for (int i = threadIdx.x; i < 766 * 2; i += blockDim.x) sLut[i] = a.lut[i];

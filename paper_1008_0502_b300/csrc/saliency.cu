@@ -103,7 +103,6 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
                                                       float* __restrict__ I1, float* __restrict__ RG1,
                                                       float* __restrict__ BY1, int h1, int w1,
                                                       const SegIO* io) {
-  seg_pdl_enter();
   constexpr bool U8 = std::is_same<TIn, uint8_t>::value;
   if constexpr (U8) {
     if (!rgb) rgb = io->rgb;
@@ -118,7 +117,7 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
   BY1 += o1;
   const int X0 = blockIdx.x * RED_TX, Y0 = blockIdx.y * RED_TY;
   const int gx0 = 2 * X0 - 2, gy0 = 2 * Y0 - 2;
-  const int smax = smax_p[fb];
+  int smax = 0;  // (read once the preceding kernel, which forms it, is complete)
   // features of input pixel (ry, rx) of the tile into sF
   auto feat = [&](int ry, int rx, float r, float g, float b, float s, bool hue) {
     float rn = 0.f, gn = 0.f, bn = 0.f;
@@ -162,6 +161,8 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
 #pragma unroll
     for (int k = 0; k < PW; ++k)
       if (threadIdx.x + 256 * k < NWD) sw[threadIdx.x + 256 * k] = wv[k];
+    seg_pdl_enter();
+    smax = smax_p[fb];
     __syncthreads();
     const unsigned char* sb = reinterpret_cast<const unsigned char*>(sw);
     for (int i = threadIdx.x; i < NIN; i += blockDim.x) {
@@ -191,6 +192,8 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
         }
       }
     }
+    seg_pdl_enter();
+    smax = smax_p[fb];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       int i = threadIdx.x + k * 256;
