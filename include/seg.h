@@ -76,7 +76,7 @@ typedef struct seg_params {
   int32_t neighbourhood;   /* 4 or 8 */
   int32_t max_cycles;      /* min-cut cycle cap -> SEG_ENOTCONVERGED (20000) */
   int32_t global_relabel_every; /* min-cut cycles between global relabels (1) */
-  int32_t local_iters;     /* push/relabel iterations per tile visit (10) */
+  int32_t local_iters;     /* push/relabel iterations per tile visit (12) */
   int32_t use_graph;       /* 1: seg_push_frame replays one captured CUDA graph per frame (when the
                               context's stream is not the legacy default stream); 0: eager launches */
   int32_t gmm_components;  /* Gaussians per label in the colour likelihood psi_1: 1 (closed form) or 3

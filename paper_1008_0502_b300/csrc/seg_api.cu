@@ -49,7 +49,7 @@ extern "C" int seg_default_params(seg_params* p) {
   p->neighbourhood = 8;
   p->max_cycles = 20000;
   p->global_relabel_every = 1;
-  p->local_iters = 10;
+  p->local_iters = 12;
   p->use_graph = 1;
   p->gmm_components = 1;
   p->em_iters = 5;
