@@ -325,6 +325,17 @@ struct GaborArgs {
 
 // Sec. 7.2 (edge orientation): O(sigma, theta) = |k_theta * I(sigma)| with the
 // zero-mean complex Gabor factored into two separable complex terms.
+// Orientation groups: {0}, {k, no - k} for 0 < k < no / 2, and {no / 2} when no
+// is even.  theta and pi - theta have conjugate horizontal factors and the same
+// vertical one, so a pair shares one horizontal pass and four vertical sums.
+__host__ __device__ __forceinline__ int gb_ngroups(int no) { return no / 2 + 1 < no ? no / 2 + 1 : no; }
+__device__ __forceinline__ void gb_group(int g, int no, int& k0, int& k1) {
+  k0 = g;
+  k1 = (g > 0 && 2 * g != no && no - g != g) ? no - g : -1;
+}
+
+// RT > 0: the radius at compile time (loops unrolled); 0: t.R at run time.
+template <int RT>
 __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
   seg_pdl_enter();
   __shared__ float sIn[GB_IN_Y][GB_IN_X];
@@ -337,7 +348,7 @@ __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
   const size_t fo = (size_t)blockIdx.y * h * w;  // frame of the batch
   const int ntx = (w + GB_TX - 1) / GB_TX;
   const int X0 = (b % ntx) * GB_TX, Y0 = (b / ntx) * GB_TY;
-  const int R = t.R, K = 2 * R + 1;
+  const int R = RT > 0 ? RT : t.R, K = 2 * R + 1;
   const int iny = GB_TY + 2 * R, inx = GB_TX + 2 * R;
   const float* __restrict__ in = a.in[l] + fo;
   for (int i = threadIdx.x; i < iny * inx; i += blockDim.x) {
@@ -348,42 +359,80 @@ __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
   for (int i = threadIdx.x; i < iny * GB_TX; i += blockDim.x) {
     int ry = i / GB_TX, x = i - ry * GB_TX;
     float acc = 0.f;
-    for (int u = 0; u < K; ++u) acc += t.g0[u] * sIn[ry][x + u];
+#pragma unroll
+    for (int u = 0; u < (RT > 0 ? 2 * RT + 1 : GB_MAXR * 2 + 1); ++u) {
+      if (RT == 0 && u >= K) break;
+      acc += t.g0[u] * sIn[ry][x + u];
+    }
     sH0[ry][x] = acc;
   }
-  // one orientation per CTA when the grid has one z-slice per orientation (single
-  // frame), otherwise every orientation in turn from the same staged tile
-  const int k_begin = gridDim.z == 1 ? 0 : blockIdx.z, k_end = gridDim.z == 1 ? t.no : blockIdx.z + 1;
-  for (int k = k_begin; k < k_end; ++k) {
+  __syncthreads();
+  // this thread's output pixels (i = tid, tid + 256) and their Gaussian (DC) term,
+  // the same for every orientation
+  constexpr int NPX = GB_TY * GB_TX / 256;
+  float dcv[NPX];
+#pragma unroll
+  for (int j = 0; j < NPX; ++j) {
+    const int i = threadIdx.x + 256 * j, y = i / GB_TX, x = i - y * GB_TX;
+    float dc = 0.f;
+#pragma unroll
+    for (int v = 0; v < (RT > 0 ? 2 * RT + 1 : GB_MAXR * 2 + 1); ++v) {
+      if (RT == 0 && v >= K) break;
+      dc += t.g0[v] * sH0[y + v][x];
+    }
+    dcv[j] = dc;
+  }
+  // one orientation group per CTA when the grid has one z-slice per group (single
+  // frame), otherwise every group in turn from the same staged tile
+  const int ng = gb_ngroups(t.no);
+  const int g_begin = gridDim.z == 1 ? 0 : blockIdx.z, g_end = gridDim.z == 1 ? ng : blockIdx.z + 1;
+  for (int gi = g_begin; gi < g_end; ++gi) {
+    int k0, k1;
+    gb_group(gi, t.no, k0, k1);
     __syncthreads();
     for (int i = threadIdx.x; i < iny * GB_TX; i += blockDim.x) {
       int ry = i / GB_TX, x = i - ry * GB_TX;
       float re = 0.f, im = 0.f;
-      for (int u = 0; u < K; ++u) {
+#pragma unroll
+      for (int u = 0; u < (RT > 0 ? 2 * RT + 1 : GB_MAXR * 2 + 1); ++u) {
+        if (RT == 0 && u >= K) break;
         float p = sIn[ry][x + u];
-        re += t.hx_re[k][u] * p;
-        im += t.hx_im[k][u] * p;
+        re += t.hx_re[k0][u] * p;
+        im += t.hx_im[k0][u] * p;
       }
       sHr[ry][x] = re;
       sHi[ry][x] = im;
     }
     __syncthreads();
-    float* __restrict__ out = a.out[k][l] + fo;
-    for (int i = threadIdx.x; i < GB_TY * GB_TX; i += blockDim.x) {
-      int y = i / GB_TX, x = i - y * GB_TX;
-      int oy = Y0 + y, ox = X0 + x;
+#pragma unroll
+    for (int j = 0; j < NPX; ++j) {
+      const int i = threadIdx.x + 256 * j, y = i / GB_TX, x = i - y * GB_TX;
+      const int oy = Y0 + y, ox = X0 + x;
       if (oy >= h || ox >= w) continue;
-      float re = 0.f, im = 0.f, dc = 0.f;
-      for (int v = 0; v < K; ++v) {
-        float hr = sHr[y + v][x], hi = sHi[y + v][x];
-        re += t.vy_re[k][v] * hr - t.vy_im[k][v] * hi;
-        im += t.vy_re[k][v] * hi + t.vy_im[k][v] * hr;
-        dc += t.g0[v] * sH0[y + v][x];
+      // P = sum vre hr, Q = sum vim hi, Rr = sum vre hi, Sr = sum vim hr: theta gives
+      // (P - Q, Rr + Sr); pi - theta (conjugate horizontal factor) gives (P + Q, Sr - Rr)
+      float P = 0.f, Q = 0.f, Rr = 0.f, Sr = 0.f;
+#pragma unroll
+      for (int v = 0; v < (RT > 0 ? 2 * RT + 1 : GB_MAXR * 2 + 1); ++v) {
+        if (RT == 0 && v >= K) break;
+        const float hr = sHr[y + v][x], hi = sHi[y + v][x];
+        const float vr = t.vy_re[k0][v], vi = t.vy_im[k0][v];
+        P += vr * hr;
+        Q += vi * hi;
+        Rr += vr * hi;
+        Sr += vi * hr;
       }
-      re -= t.kap_re[k] * dc;
-      im -= t.kap_im[k] * dc;
-      out[(size_t)oy * w + ox] = sqrtf(re * re + im * im);
-      if (a.out_c[k][l]) a.out_c[k][l][fo + (size_t)oy * w + ox] = make_float2(re, im);
+      const size_t o = fo + (size_t)oy * w + ox;
+      {
+        const float re = P - Q - t.kap_re[k0] * dcv[j], im = Rr + Sr - t.kap_im[k0] * dcv[j];
+        a.out[k0][l][o] = sqrtf(re * re + im * im);
+        if (a.out_c[k0][l]) a.out_c[k0][l][o] = make_float2(re, im);
+      }
+      if (k1 >= 0) {
+        const float re = P + Q - t.kap_re[k1] * dcv[j], im = Sr - Rr - t.kap_im[k1] * dcv[j];
+        a.out[k1][l][o] = sqrtf(re * re + im * im);
+        if (a.out_c[k1][l]) a.out_c[k1][l][o] = make_float2(re, im);
+      }
     }
   }
 }
@@ -1292,7 +1341,11 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     tot += ((s.wl[l] + GB_TX - 1) / GB_TX) * ((s.hl[l] + GB_TY - 1) / GB_TY);
   }
   ga.blk_off[s.s_max - s.c_min + 1] = tot;
-  SEG_CUDA_TRY(seg_launch(k_gabor, dim3(tot, B, B == 1 ? s.no : 1), 256, 0, st, ga, s.taps));
+  const dim3 gg(tot, B, B == 1 ? gb_ngroups(s.no) : 1);
+  if (s.taps.R == 6)
+    SEG_CUDA_TRY(seg_launch(k_gabor<6>, gg, 256, 0, st, ga, s.taps));
+  else
+    SEG_CUDA_TRY(seg_launch(k_gabor<0>, gg, 256, 0, st, ga, s.taps));
   CSArgs ca;
   fill_cs_args(s, ca);
   {
