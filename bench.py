@@ -119,7 +119,7 @@ def peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
-def kernels_per_frame(p, H=480, W=640, graph=True, pipeline=False):
+def kernels_per_frame(p, H=480, W=640, graph=True, pipeline=False, B=1):
     """Kernels one seg_push_frame launches (memsets excluded), as the library sequences them."""
     dims = [(H, W)]
     for _ in range(p["levels"] - 1):
@@ -131,9 +131,12 @@ def kernels_per_frame(p, H=480, W=640, graph=True, pipeline=False):
             break
         tiled += 1
     tail = 1 if 1 + tiled < p["levels"] - 1 else 0
-    # rgb max, features + first REDUCE, tiled REDUCEs, tail, Gabor, cs stats,
-    # one accumulation per center scale, conspicuity
-    sal = 2 + tiled + tail + 1 + 1 + (p["c_max"] - p["c_min"] + 1) + 1
+    # rgb max, features + first REDUCE, tiled REDUCEs, tail, Gabor, cs stats, the
+    # across-scale accumulation (one fused launch for up to two REDUCE steps and
+    # batches of up to 4 frames, else one per center scale), conspicuity
+    span = p["c_max"] - p["c_min"]
+    accum = 1 if span <= 2 and B <= 4 else span + 1
+    sal = 2 + tiled + tail + 1 + 1 + accum + 1
     # prior, moments, terms; min cut; frame-pointer record(s): one per captured half
     return sal + 3 + 1 + (1 if graph else 0) + (1 if graph and pipeline else 0)
 
