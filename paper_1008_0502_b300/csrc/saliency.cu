@@ -1305,6 +1305,9 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   if (!smax_zeroed) SEG_CUDA_TRY(cudaMemsetAsync(s.smax, 0, B * sizeof(int), st));
   int nb = min((N + 255) / 256, B > 1 ? 148 : 148 * 8);
   nb = max(nb, (s.nmaps + 255) / 256);
+  // RGB8 frames go 16 pixels per thread (three 16-byte loads): a grid for that,
+  // not one thread per pixel (idle CTAs would crowd the concurrent back half)
+  const int nb8 = max((N / 16 + 255) / 256, (s.nmaps + 255) / 256);
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);
   if (rgb_f32) {
     const float* f = (const float*)rgb;
@@ -1313,7 +1316,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
                                               s.hl[1], s.wl[1], nullptr));
   } else {
     const uint8_t* u = (const uint8_t*)rgb;
-    SEG_CUDA_TRY(seg_launch(k_rgb_max<uint8_t>, dim3(nb, B), 256, 0, st, u, N, s.smax, s.mm, s.nmaps, io));
+    SEG_CUDA_TRY(seg_launch(k_rgb_max<uint8_t>, dim3(nb8, B), 256, 0, st, u, N, s.smax, s.mm, s.nmaps, io));
     SEG_CUDA_TRY(seg_launch(k_feat_reduce1<uint8_t>, g1, 256, 0, st, u, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
                                                 s.hl[1], s.wl[1], io));
   }
