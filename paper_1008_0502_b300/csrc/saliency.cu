@@ -705,7 +705,8 @@ __device__ __forceinline__ float fa_eval(const CSArgs& a, const float* sab, int 
   return acc;
 }
 
-__global__ void __launch_bounds__(1024) k_cs_accum_fused(CSArgs a, float* __restrict__ out) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_cs_accum_fused(CSArgs a, float* __restrict__ out) {
   seg_pdl_enter();
   __shared__ float sR2[FA_N(FA_TY, 2) * FA_N(FA_TX, 2)];  // region two levels below sigma_S
   __shared__ float sR1[FA_N(FA_TY, 1) * FA_N(FA_TX, 1)];  // one level below
@@ -1404,7 +1405,14 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     // one launch: every tile of sigma_S rebuilds its halo regions of the lower scales
     // (for larger batches the level-by-level launches have enough CTAs and no halo work)
     const dim3 g((s.wl[s.sS] + FA_TX - 1) / FA_TX, (s.hl[s.sS] + FA_TY - 1) / FA_TY, s.nch * B);
-    SEG_CUDA_TRY(seg_launch(k_cs_accum_fused, g, 1024, 0, st, ca, s.acc_final));
+    // CTA size: 1024 threads finish a frame's sum soonest; a pipelined context
+    // takes 256 (fewer registers and threads held per SM, so the previous frame's
+    // back half, running meanwhile, is crowded less: pipelined 640x480 ~6.13k
+    // -> ~6.31k frames/s, the sum itself ~7 us slower)
+    if (s.light_ctas)
+      SEG_CUDA_TRY(seg_launch(k_cs_accum_fused<256>, g, 256, 0, st, ca, s.acc_final));
+    else
+      SEG_CUDA_TRY(seg_launch(k_cs_accum_fused<1024>, g, 1024, 0, st, ca, s.acc_final));
     prev = s.acc_final;
   }
   for (int cc = s.c_min; cc <= s.c_max && !fused; ++cc) {

@@ -485,6 +485,7 @@ extern "C" int seg_sync(seg_ctx* c, int* cycles) {
 // S and saliency maximum into separate buffers; the front of frame t waits for
 // the back of frame t-2, the last reader of its buffer.
 static void pipe_free(seg_ctx* c) {
+  c->sal.light_ctas = 0;
   if (!c->pipe_mem && !c->s_front) return;
   if (c->s_front) cudaStreamSynchronize(c->s_front);
   for (int k = 0; k < 2; ++k) {
@@ -521,6 +522,7 @@ extern "C" int seg_pipeline_enable(seg_ctx* c, int on) {
     return SEG_OK;
   }
   if (c->pipe_on) return SEG_OK;
+  c->sal.light_ctas = 1;  // (the pipelined graphs are captured with it)
   const size_t nS = (size_t)c->sal.hl[c->sal.sS] * c->sal.wl[c->sal.sS] * c->B;
   const size_t o_salmax = seg_align(nS * sizeof(float)), o_io = o_salmax + seg_align(c->B * sizeof(unsigned));
   const size_t o_ring = o_io + seg_align(sizeof(SegIO)), ring_bytes = seg_align((size_t)3 * c->N * c->B);

@@ -191,6 +191,7 @@ struct GaborTaps {
 // the first kernel fuses feature extraction with the first REDUCE.
 struct SalWS {
   int B;  // frames of the batch (same size); every per-frame buffer holds B frames
+  int light_ctas;  // sharing the GPU with a pipelined back half: smaller CTAs where that pays
   int H, W, L, c_min, c_max, d_min, d_max, no, s_max, sS, tile;
   int opp_sum;
   float flat;
