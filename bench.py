@@ -16,6 +16,9 @@ cycled and the temporal state reset when it wraps).  Reported:
   roofline   the dominant stage's kernel against the measured HBM peak
   cpu_baseline  the FP64 C oracle on a bounded sample of the same clip, one
              core; cpu_baseline_all_cores: one oracle stream per host core
+  accuracy   Sec. 8.1's error rate, recall, precision and F-value of the
+             masks against the clip's synthetic ground truth (sanity only,
+             computed on the host after the timed regions)
 
 --impl reference runs that oracle as the reference arm (rank 0 only).
 Multi-GPU: independent replicas (each rank segments its own copy of the clip;
@@ -66,9 +69,37 @@ def args():
     return ap.parse_args()
 
 
-def make_clip(n):
+def make_clip(n, with_gt=False):
     from paper_1008_0502_b300 import synth
+    if with_gt:
+        return synth.clip_vga(n)  # (frames, ground-truth masks), the same frames
     return np.stack([f for f, _ in synth.clip_vga_frames(n)])
+
+
+def confusion(mask, gt):
+    """(TP, TN, FP, FN) pixel counts of a 0/1 mask against a 0/1 ground truth."""
+    m = np.asarray(mask).astype(bool)
+    g = np.asarray(gt).astype(bool)
+    if m.shape != g.shape:
+        raise ValueError(f"mask {m.shape} vs ground truth {g.shape}")
+    tp = int(np.count_nonzero(m & g))
+    fp = int(np.count_nonzero(m & ~g))
+    fn = int(np.count_nonzero(~m & g))
+    return np.array([tp, m.size - tp - fp - fn, fp, fn], np.int64)
+
+
+def seg_accuracy(counts):
+    """Sec. 8.1's accuracy measures from summed (TP, TN, FP, FN): the error rate is
+    the fraction of mislabelled pixels, recall the share of object pixels labelled
+    object, precision the share of object labels that are right, and the F-value
+    their harmonic mean.  A ratio whose denominator is zero is None."""
+    tp, tn, fp, fn = (int(c) for c in counts)
+    tot = tp + tn + fp + fn
+    err = (fp + fn) / tot if tot else None
+    rec = tp / (tp + fn) if tp + fn else None
+    prec = tp / (tp + fp) if tp + fp else None
+    f = 2 * rec * prec / (rec + prec) if rec is not None and prec is not None and rec + prec > 0 else None
+    return {"error": err, "recall": rec, "precision": prec, "f_value": f}
 
 
 class Clocks:
@@ -455,7 +486,7 @@ def run_b300(a):
     ws, rank, local = dist_setup("nccl")
     torch.cuda.set_device(local)
     from paper_1008_0502_b300 import seg
-    clip = make_clip(a.frames)
+    clip, gt = make_clip(a.frames, with_gt=True)
     clip_dev = torch.from_numpy(clip).cuda()
     p = seg.params_from(VGA)
     if ws > 1:
@@ -566,6 +597,13 @@ def run_b300(a):
     for i in range(n_sync):
         sg.push_frame_host(rgb_h[i], mask_h, cut_h)
     e2e_sync, _ = aggregate(time.perf_counter() - t0, n_sync, ws, device="cuda")
+    # accuracy of the masks against the clip's synthetic ground truth (Sec. 8.1's
+    # measures; a sanity figure, outside every timed region): the same frames again
+    sg.reset()
+    conf = np.zeros(4, np.int64)
+    for i in range(n_sync):
+        sg.push_frame_host(rgb_h[i], mask_h, cut_h)
+        conf += confusion(mask_h.numpy(), gt[i])
     sg.close()
     if rank != 0:
         return
@@ -605,6 +643,10 @@ def run_b300(a):
         "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": H * W + 8, "path": "seg_push_frame_host_async, pinned host frames, "
                 "one sync at the end", "frame_by_frame": e2e_sync},
+        "accuracy": dict(seg_accuracy(conf), frames=n_sync,
+                         of="masks against the clip's synthetic ground truth (ellipse, grating, and the disk "
+                         "while its contrast is at least half), pixel counts summed over the frames; "
+                         "a sanity figure"),
         "batched": batched,
         "serving": serving,
         "gpu_launches": a.steps * kernels_per_frame(VGA, pipeline=True),

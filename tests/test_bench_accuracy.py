@@ -1,0 +1,68 @@
+"""Host-side accuracy measures that bench.py reports next to the throughput:
+Sec. 8.1's error rate, recall, precision and F-value of a mask against ground
+truth, checked on hand-counted cases (no GPU)."""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_confusion_counts_by_hand():
+    gt = np.array([[1, 1, 0, 0],
+                   [1, 1, 0, 0]], np.uint8)
+    m = np.array([[1, 0, 1, 0],
+                  [1, 1, 0, 0]], np.uint8)
+    tp, tn, fp, fn = bench.confusion(m, gt)
+    assert (tp, tn, fp, fn) == (3, 3, 1, 1)
+
+
+def test_measures_by_hand():
+    # TP 3, TN 3, FP 1, FN 1: error 2/8, recall 3/4, precision 3/4, F 3/4
+    a = bench.seg_accuracy([3, 3, 1, 1])
+    assert a["error"] == pytest.approx(0.25)
+    assert a["recall"] == pytest.approx(0.75)
+    assert a["precision"] == pytest.approx(0.75)
+    assert a["f_value"] == pytest.approx(0.75)
+    # recall 1/2, precision 1: F = 2 * 0.5 / 1.5
+    a = bench.seg_accuracy([1, 6, 0, 1])
+    assert a["f_value"] == pytest.approx(2.0 / 3.0)
+    assert a["error"] == pytest.approx(1.0 / 8.0)
+
+
+def test_perfect_and_degenerate_masks():
+    gt = np.zeros((5, 7), np.uint8)
+    gt[1:3, 2:6] = 1
+    a = bench.seg_accuracy(bench.confusion(gt, gt))
+    assert a == {"error": 0.0, "recall": 1.0, "precision": 1.0, "f_value": 1.0}
+    # an empty mask: nothing labelled object, so precision (and F) are undefined
+    a = bench.seg_accuracy(bench.confusion(np.zeros_like(gt), gt))
+    assert a["recall"] == 0.0 and a["precision"] is None and a["f_value"] is None
+    assert a["error"] == pytest.approx(8 / 35)
+    # the complement: every pixel wrong
+    a = bench.seg_accuracy(bench.confusion(1 - gt, gt))
+    assert a["error"] == 1.0 and a["recall"] == 0.0 and a["precision"] == 0.0 and a["f_value"] is None
+
+
+def test_counts_sum_over_frames_and_shapes_checked():
+    rng = np.random.default_rng(7)
+    gts = rng.integers(0, 2, (4, 6, 9)).astype(np.uint8)
+    ms = rng.integers(0, 2, (4, 6, 9)).astype(np.uint8)
+    tot = sum(bench.confusion(m, g) for m, g in zip(ms, gts))
+    assert tot.sum() == gts.size
+    assert (tot == bench.confusion(ms, gts)).all()
+    a = bench.seg_accuracy(tot)
+    assert math.isclose(a["error"], float(np.mean(ms != gts)))
+    with pytest.raises(ValueError):
+        bench.confusion(ms[0], gts[0, :5])
+
+
+def test_clip_with_ground_truth_has_the_same_frames():
+    f1 = bench.make_clip(3)
+    f2, gt = bench.make_clip(3, with_gt=True)
+    assert f1.shape == f2.shape == (3, 480, 640, 3) and (f1 == f2).all()
+    assert gt.shape == (3, 480, 640) and gt.dtype == np.uint8 and set(np.unique(gt)) <= {0, 1}
