@@ -214,6 +214,11 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   c->warm = (unsigned char*)(base + o_warm);
   mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
+  if (!lut) {
+    cudaFree(base);
+    free(c);
+    return SEG_ENOMEM;
+  }
   pt_fill_lut(*p, lut);
   bool ok = cudaMemcpy(c->lut, lut, sizeof(int) * 766 * 2, cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && sal_upload_tables(c->sal) == SEG_OK;
@@ -452,15 +457,20 @@ extern "C" int seg_profile_read_ex(seg_ctx* c, double* stage_ms, int* frames, lo
     *cycles += cyc[7 * f];
     if (mincut_stats && f < max_frames)
       for (int k = 0; k < 7; ++k) mincut_stats[7 * f + k] = cyc[7 * f + k];
-    for (int k = 0; k < 4; ++k) {
+    bool ok = true;
+    for (int k = 0; k < 4 && ok; ++k) {
       float ms = 0.f;
-      SEG_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[5 * f + k], c->prof_ev[5 * f + k + 1]));
+      ok = cudaEventElapsedTime(&ms, c->prof_ev[5 * f + k], c->prof_ev[5 * f + k + 1]) == cudaSuccess;
       stage_ms[k] += ms;
     }
-    if (frame_ms && f < max_frames) {
+    if (ok && frame_ms && f < max_frames) {
       float ms = 0.f;
-      SEG_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof_ev[5 * f], c->prof_ev[5 * f + 4]));
+      ok = cudaEventElapsedTime(&ms, c->prof_ev[5 * f], c->prof_ev[5 * f + 4]) == cudaSuccess;
       frame_ms[f] = ms;
+    }
+    if (!ok) {
+      free(cyc);
+      return SEG_ECUDA;
     }
   }
   free(cyc);
