@@ -370,7 +370,7 @@ def serving_suite(seg, torch, horizon_s=1.0, budget_gb=32.0):
         reqs.append(serve.Request(len(reqs), (lambda tt, pool=pool, off=off: pool[(off + tt) % 8]), n, t))
     srv = serve.Server(seg.params_from(VGA), int(budget_gb * 2**30), slots=8)
     stats = srv.run(reqs, clock="wall")
-    waits = [r.admitted - r.arrival for r in srv.results.values()]
+    waits = [r.admitted - r.arrival for r in srv.results.values() if r.admitted >= 0] or [0.0]
     srv.close()
     stats.update({"arrivals_per_s": 20, "horizon_s": horizon_s, "hbm_budget_gb": budget_gb,
                   "admission_wait_ms": {"p50": float(np.percentile(waits, 50)) * 1e3,

@@ -7,8 +7,12 @@ on a CUDA stream of its own, so the groups' work overlaps on the device.
 
 * Admission by HBM footprint: a request whose resolution has a free slot takes
   it; otherwise a new group is created if its workspace
-  (``seg_workspace_bytes``) fits the remaining budget; otherwise the request
-  waits in the queue.
+  (``seg_workspace_bytes``) fits the remaining budget, after freeing idle
+  groups (no stream in any slot) when that makes it fit; otherwise the request
+  waits in the queue.  A request whose group could never fit the budget, or
+  whose group's device allocation fails while no other group is running (so
+  nothing here will free memory), is refused (``StreamResult.refused``)
+  instead of waiting forever.
 * Continuous batching: requests are admitted at every step as slots and memory
   free up, while the other streams keep running; a finished stream frees its
   slot, and the next stream admitted there starts a new video
@@ -59,11 +63,13 @@ class StreamResult:
     masks: list = dataclasses.field(default_factory=list)
     priors: list = dataclasses.field(default_factory=list)
     cuts: list = dataclasses.field(default_factory=list)
+    refused: str = ""  # why the stream was never admitted ("" once admitted or while waiting)
 
 
 class _Group:
     def __init__(self, H, W, slots, params):
         self.H, self.W, self.B = H, W, slots
+        self.bytes = 0  # its workspace, charged to the server's budget
         self.stream = torch.cuda.Stream()
         self.ctx = seg.Segmenter(H, W, params, stream=self.stream, batch=slots)
         self.inbuf = torch.zeros(slots, H, W, 3, dtype=torch.uint8, device="cuda")
@@ -81,6 +87,9 @@ class _Group:
     def active(self):
         return any(s is not None for s in self.sid)
 
+    def close(self):
+        self.ctx.close()
+
 
 class Server:
     def __init__(self, params: seg.seg_params, hbm_budget_bytes: int, slots: int = 8, keep_outputs: bool = False):
@@ -94,7 +103,8 @@ class Server:
         self.requests: dict[int, Request] = {}
         self.results: dict[int, StreamResult] = {}
         self.steps = 0
-        self.rejected_groups = 0
+        self.rejected_groups = 0  # times a new group could not be created (the request waited)
+        self.evicted_groups = 0
 
     # -- admission
     def submit(self, req: Request):
@@ -118,10 +128,16 @@ class Server:
                         break
             if slot is None:
                 need = seg.workspace_bytes(self.slots, H, W, self.params)
-                if self.used + need <= self.budget:
-                    g = _Group(H, W, self.slots, self.params)
-                    self.groups.append(g)
-                    self.used += need
+                if need > self.budget:
+                    self.results[req.sid].refused = "its group's workspace exceeds the HBM budget"
+                    continue
+                if self.used + need > self.budget:
+                    self._evict_idle(need)
+                g = self._new_group(H, W, need) if self.used + need <= self.budget else None
+                if g is None and self.used + need <= self.budget and not any(x.active() for x in self.groups):
+                    self.results[req.sid].refused = "device allocation failed with no other group running"
+                    continue
+                if g is not None:
                     slot = (g, 0)
                 else:
                     self.rejected_groups += 1
@@ -134,6 +150,44 @@ class Server:
             g.fresh[b] = True
             self.results[req.sid].admitted = now
         self.queue = waiting
+
+    def _evict_idle(self, need: int):
+        """Frees idle groups, oldest first, if that lets a new group of `need`
+        bytes fit the budget; frees none otherwise."""
+        idle = [g for g in self.groups if not g.active()]
+        if self.used - sum(g.bytes for g in idle) + need > self.budget:
+            return
+        for g in idle:
+            if self.used + need <= self.budget:
+                break
+            self._drop(g)
+
+    def _drop(self, g: _Group):
+        g.close()
+        self.groups.remove(g)
+        self.used -= g.bytes
+        self.evicted_groups += 1
+
+    def _new_group(self, H: int, W: int, need: int):
+        """A new group, or None when its device allocation fails (after one retry
+        with the idle groups freed)."""
+        for attempt in range(2):
+            try:
+                g = _Group(H, W, self.slots, self.params)
+            except seg.SegError as e:
+                if e.code != seg.SEG_ENOMEM:
+                    raise
+                idle = [x for x in self.groups if not x.active()]
+                if attempt or not idle:
+                    return None
+                for x in idle:
+                    self._drop(x)
+                continue
+            g.bytes = need
+            self.groups.append(g)
+            self.used += need
+            return g
+        return None
 
     # -- one step of every group with an active slot
     def step(self, now: float):
@@ -211,9 +265,11 @@ class Server:
         return {"wall_s": wall, "frames": frames, "frames_per_s": frames / wall if wall > 0 else 0.0,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "streams": len(self.results), "groups": len(self.groups), "hbm_bytes": self.used,
-                "steps": self.steps}
+                "steps": self.steps, "refused": sum(1 for r in self.results.values() if r.refused),
+                "evicted_groups": self.evicted_groups}
 
     def close(self):
         for g in self.groups:
-            g.ctx.close()
+            g.close()
         self.groups = []
+        self.used = 0

@@ -16,14 +16,24 @@ class _FakeFrames:
 
 
 class _FakeGroup:
+    fail_allocs = 0  # the next n creations fail as a device allocation would (host-side fault injection)
+    closed = []
+
     def __init__(self, H, W, slots, params):
+        if _FakeGroup.fail_allocs > 0:
+            _FakeGroup.fail_allocs -= 1
+            raise seg.SegError(seg.SEG_ENOMEM, "seg_create_batch")
         self.H, self.W, self.B = H, W, slots
+        self.bytes = 0
         self.sid = [None] * slots
         self.pos = [0] * slots
         self.fresh = [False] * slots
 
     free_slot = serve._Group.free_slot
     active = serve._Group.active
+
+    def close(self):
+        _FakeGroup.closed.append((self.H, self.W))
 
 
 def _req(sid, H, W, arrival, n=5):
@@ -33,6 +43,8 @@ def _req(sid, H, W, arrival, n=5):
 @pytest.fixture
 def server(monkeypatch):
     monkeypatch.setattr(serve, "_Group", _FakeGroup)
+    _FakeGroup.fail_allocs = 0
+    _FakeGroup.closed = []
     p = seg.default_params()
     one = seg.workspace_bytes(2, 120, 160, p)
     # room for two groups of 160x120 streams, not for a third
@@ -77,10 +89,10 @@ def test_budget_refuses_a_group_until_a_slot_frees(server):
     s._admit(now=1.0)
     assert [r.sid for r in s.queue] == [4] and s.rejected_groups == 1 and len(s.groups) == 2
     assert s.used == 2 * one
-    # a different resolution is refused too (its group would not fit either)
-    s.submit(_req(5, 240, 320, arrival=0.0))
+    # a different resolution waits too (its group would not fit beside the two running ones)
+    s.submit(_req(5, 90, 120, arrival=0.0))
     s._admit(now=1.0)
-    assert sorted(r.sid for r in s.queue) == [4, 5] and len(s.groups) == 2
+    assert sorted(r.sid for r in s.queue) == [4, 5] and len(s.groups) == 2 and s.results[5].refused == ""
     # stream 1 finishes: its slot goes to the next waiting stream of that size, as a new video
     g = s.groups[0]
     g.sid[1] = None
@@ -98,3 +110,87 @@ def test_workspace_grows_with_slots_and_pixels():
     a = seg.workspace_bytes(1, 120, 160, p)
     assert seg.workspace_bytes(2, 120, 160, p) > a
     assert seg.workspace_bytes(1, 240, 320, p) > 3 * a
+
+
+def _finish(g, b):
+    g.sid[b] = None
+
+
+def test_a_group_that_can_never_fit_is_refused_not_queued(server):
+    s, one = server
+    big = seg.workspace_bytes(2, 480, 640, s.params)
+    assert big > s.budget
+    s.submit(_req(0, 480, 640, arrival=0.0))
+    s._admit(now=0.0)
+    assert s.queue == [] and s.groups == [] and s.used == 0
+    assert "exceeds" in s.results[0].refused and s.results[0].admitted < 0
+
+
+def test_idle_groups_are_freed_for_a_new_resolution(server):
+    s, one = server
+    other = seg.workspace_bytes(2, 90, 120, s.params)
+    for i in range(4):
+        s.submit(_req(i, 120, 160, arrival=0.0))
+    s._admit(now=0.0)
+    assert len(s.groups) == 2
+    # a 90x120 stream cannot get a group while both 160x120 groups run
+    s.submit(_req(9, 90, 120, arrival=0.0))
+    s._admit(now=1.0)
+    assert [r.sid for r in s.queue] == [9] and s.evicted_groups == 0
+    # group 2 goes idle: freeing it makes room, group 1 keeps running
+    g0, g1 = s.groups
+    _finish(g1, 0)
+    _finish(g1, 1)
+    s._admit(now=2.0)
+    assert s.queue == [] and s.evicted_groups == 1 and _FakeGroup.closed == [(120, 160)]
+    assert s.groups[0] is g0 and (s.groups[1].H, s.groups[1].W) == (90, 120)
+    assert s.used == one + other and s.results[9].admitted == 2.0
+
+
+def test_no_group_is_freed_when_that_would_not_make_room(server):
+    s, one = server
+    for i in range(4):
+        s.submit(_req(i, 120, 160, arrival=0.0))
+    s._admit(now=0.0)
+    g0, g1 = s.groups
+    _finish(g1, 0)
+    _finish(g1, 1)
+    # a resolution whose group fits the budget, but not beside the running group even
+    # with the idle one freed: the idle group stays and the stream waits
+    H, W = next((h, w) for h, w in [(150, 200), (160, 200), (180, 220), (200, 240)]
+                if s.budget - one < seg.workspace_bytes(2, h, w, s.params) <= s.budget)
+    s.submit(_req(9, H, W, arrival=0.0))
+    s._admit(now=1.0)
+    assert [r.sid for r in s.queue] == [9] and s.results[9].refused == ""
+    assert s.groups == [g0, g1] and s.evicted_groups == 0 and _FakeGroup.closed == []
+    # once the running group goes idle too, both are freed and the stream is admitted
+    _finish(g0, 0)
+    _finish(g0, 1)
+    s._admit(now=2.0)
+    assert s.queue == [] and s.evicted_groups == 2 and [(g.H, g.W) for g in s.groups] == [(H, W)]
+
+
+def test_allocation_failure_waits_while_others_run_and_is_refused_otherwise(server):
+    s, one = server
+    s.submit(_req(0, 120, 160, arrival=0.0, n=3))
+    s._admit(now=0.0)
+    assert len(s.groups) == 1
+    # a second resolution: the device allocation fails while group 1 runs -> it waits
+    _FakeGroup.fail_allocs = 2
+    s.submit(_req(1, 90, 120, arrival=0.0))
+    s._admit(now=1.0)
+    assert [r.sid for r in s.queue] == [1] and s.rejected_groups == 1 and s.results[1].refused == ""
+    # group 1 finishes; the allocation fails again, is retried once with the idle group
+    # freed, and succeeds
+    _finish(s.groups[0], 0)
+    _FakeGroup.fail_allocs = 1
+    s._admit(now=2.0)
+    assert s.queue == [] and s.evicted_groups == 1 and [(g.H, g.W) for g in s.groups] == [(90, 120)]
+    assert s.used == seg.workspace_bytes(2, 90, 120, s.params)
+    # nothing running and every allocation failing: refused instead of waiting forever
+    _finish(s.groups[0], 0)
+    _FakeGroup.fail_allocs = 5
+    s.submit(_req(2, 240, 320, arrival=0.0))
+    s.budget = 10 ** 12
+    s._admit(now=3.0)
+    assert s.queue == [] and "allocation failed" in s.results[2].refused
