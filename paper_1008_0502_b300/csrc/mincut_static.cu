@@ -22,10 +22,12 @@
 #define SEG_STATIC_MAX_DEVICES 64
 
 // Workspace bytes the min-cut needs per pixel at the 8-neighbourhood (excess,
-// height, sink residual, 8 directed residuals, two flag bytes), each array
-// padded to 256 bytes, plus status words.
+// height, sink residual, 8 directed residuals, two flag bytes), plus one byte
+// per pixel for the per-tile words (5 bytes a 32x16 tile; even a one-row or
+// one-column grid, one tile per 32 or 16 pixels, stays under that), the
+// padding of every array to 256 bytes, and the status words.
 static const size_t kStaticBytes =
-    4 * 256 + (size_t)SEG_MINCUT_STATIC_MAX_PIXELS * (3 * 4 + 8 * 4 + 2) + 4096;
+    4 * 256 + (size_t)SEG_MINCUT_STATIC_MAX_PIXELS * (3 * 4 + 8 * 4 + 2 + 1) + 8192;
 
 static __device__ __align__(256) unsigned char g_mincut_scratch[kStaticBytes];
 

@@ -71,3 +71,20 @@ def test_host_validation_rejects_bad_arguments(seg):
     assert seg.lib.seg_mincut_grid(None, 4, 4, 5, None, None, None, None, None, 0, None) == seg.SEG_EINVAL
     assert seg.lib.seg_mincut_grid(None, 0, 4, 4, None, None, None, None, None, 0, None) == seg.SEG_EINVAL
     assert h.value is None
+
+
+def test_static_min_cut_accepts_every_shape_up_to_its_pixel_limit(seg):
+    """seg_mincut_grid_static checks its sizes before touching the device: long thin
+    grids within SEG_MINCUT_STATIC_MAX_PIXELS (many tiles per pixel) pass the size
+    check, larger ones get SEG_EINVAL.  Without a GPU the accepted calls then stop at
+    the device lookup (SEG_ECUDA); the pointers are never dereferenced."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check: with a GPU these placeholder pointers would reach a kernel")
+    f = C.c_void_p(256)
+    M = seg.SEG_MINCUT_STATIC_MAX_PIXELS
+    for H, W in [(1, M), (M, 1), (3, M // 3), (17, M // 17), (256, 512)]:
+        for nbr in (4, 8):
+            assert seg.lib.seg_mincut_grid_static(None, H, W, nbr, f, f, f, f, f, 0, None) == seg.SEG_ECUDA, (H, W)
+    for H, W in [(1, M + 1), (512, 257)]:
+        assert seg.lib.seg_mincut_grid_static(None, H, W, 8, f, f, f, f, f, 0, None) == seg.SEG_EINVAL
