@@ -124,6 +124,18 @@ def _dev(t, dtype, shape, name):
     return _ptr(t)
 
 
+def _host(t, dtype, numel, name):
+    """Pointer to a host buffer, after checking that it holds exactly what the
+    library copies through it (the C side trusts the size it derives from H, W, B)."""
+    if t is None:
+        return None
+    if t.device.type != "cpu":
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype or t.numel() != numel:
+        raise ValueError(f"{name}: expected {dtype} with {numel} elements, got {t.dtype} {tuple(t.shape)}")
+    return _ptr(t)
+
+
 def default_params(**over) -> seg_params:
     p = seg_params()
     _check(lib.seg_default_params(C.byref(p)), "seg_default_params")
@@ -254,11 +266,10 @@ class Segmenter:
     def push_frame_host_async(self, rgb_host, mask_host, cut_host=None):
         """Pipelined host-buffer frame: no host wait; results complete after sync().
         The host buffers must stay untouched until then."""
-        for t in (rgb_host, mask_host, cut_host):
-            if t is not None and (t.device.type != "cpu" or not t.is_contiguous()):
-                raise ValueError("host buffers must be contiguous CPU tensors")
-        _check(lib.seg_push_frame_host_async(self.handle, _ptr(rgb_host), _ptr(mask_host), _ptr(cut_host)),
-               "seg_push_frame_host_async")
+        n = self.B * self.H * self.W
+        args = (_host(rgb_host, torch.uint8, 3 * n, "rgb_host"), _host(mask_host, torch.uint8, n, "mask_host"),
+                _host(cut_host, torch.int64, self.B, "cut_host"))
+        _check(lib.seg_push_frame_host_async(self.handle, *args), "seg_push_frame_host_async")
 
     def outputs_ready(self, stream=None):
         """Orders `stream` (default: the current stream) after every frame pushed so far."""
@@ -267,11 +278,12 @@ class Segmenter:
             s.wait_stream(self.stream)
 
     def push_frame_host(self, rgb_host, mask_host, cut_host=None, saliency_host=None, prior_host=None):
-        for t in (rgb_host, mask_host, cut_host, saliency_host, prior_host):
-            if t is not None and t.device.type != "cpu":
-                raise ValueError("push_frame_host takes host tensors")
-        return _check(lib.seg_push_frame_host(self.handle, _ptr(rgb_host), _ptr(saliency_host), _ptr(prior_host),
-                                              _ptr(mask_host), _ptr(cut_host)), "seg_push_frame_host")
+        n = self.B * self.H * self.W
+        args = (_host(rgb_host, torch.uint8, 3 * n, "rgb_host"),
+                _host(saliency_host, torch.float32, n, "saliency_host"),
+                _host(prior_host, torch.float32, n, "prior_host"),
+                _host(mask_host, torch.uint8, n, "mask_host"), _host(cut_host, torch.int64, self.B, "cut_host"))
+        return _check(lib.seg_push_frame_host(self.handle, *args), "seg_push_frame_host")
 
     def sync(self, check=True):
         cyc = C.c_int(0)

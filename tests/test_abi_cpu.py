@@ -21,7 +21,8 @@ def seg():
 
 
 def declared_symbols():
-    txt = open(HEADER).read()
+    with open(HEADER) as f:
+        txt = f.read()
     return sorted(set(re.findall(r"^(?:int|const char\*)\s+(seg_\w+)\s*\(", txt, re.M)))
 
 
@@ -88,3 +89,34 @@ def test_static_min_cut_accepts_every_shape_up_to_its_pixel_limit(seg):
             assert seg.lib.seg_mincut_grid_static(None, H, W, nbr, f, f, f, f, f, 0, None) == seg.SEG_ECUDA, (H, W)
     for H, W in [(1, M + 1), (512, 257)]:
         assert seg.lib.seg_mincut_grid_static(None, H, W, 8, f, f, f, f, f, 0, None) == seg.SEG_EINVAL
+
+
+def test_host_buffers_are_checked_before_the_library_copies(seg):
+    """The host-buffer entry points copy B*H*W*3 input bytes and B*H*W mask bytes
+    through the given pointers, so the binding checks every host tensor's dtype and
+    size first (a short buffer would be read or written past its end)."""
+    import torch
+    sg = object.__new__(seg.Segmenter)  # no context: the checks run before any library call
+    sg.H, sg.W, sg.B, sg.handle = 6, 8, 1, None
+    rgb = torch.zeros(6, 8, 3, dtype=torch.uint8)
+    mask = torch.zeros(6, 8, dtype=torch.uint8)
+    cut = torch.zeros(1, dtype=torch.int64)
+    bad = [dict(rgb_host=rgb[:5]), dict(mask_host=torch.zeros(6, 7, dtype=torch.uint8)),
+           dict(mask_host=mask.float()), dict(cut_host=torch.zeros(2, dtype=torch.int64)),
+           dict(rgb_host=rgb.transpose(0, 1)), dict(saliency_host=torch.zeros(6, 8, dtype=torch.float64))]
+    for over in bad:
+        kw = dict(rgb_host=rgb, mask_host=mask, cut_host=cut)
+        kw.update(over)
+        with pytest.raises(ValueError):
+            sg.push_frame_host(**kw)
+        if "saliency_host" not in over:
+            with pytest.raises(ValueError):
+                sg.push_frame_host_async(**kw)
+    # well-formed buffers reach the library, which rejects the missing context
+    with pytest.raises(seg.SegError):
+        sg.push_frame_host(rgb, mask, cut, torch.zeros(6, 8), torch.zeros(6, 8))
+    with pytest.raises(seg.SegError):
+        sg.push_frame_host_async(rgb, mask, cut)
+    sg.B = 2  # a batch of two streams needs twice the bytes
+    with pytest.raises(ValueError):
+        sg.push_frame_host(rgb, mask, cut)
