@@ -61,7 +61,9 @@ CONFIG_SMALL = dict(CONFIG_VGA, levels=6, c_min=1, c_max=2, d_min=2, d_max=3, ne
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # ORACLE_LIB_OVERRIDE: a separately built copy of the oracle (the planted-mistake
+        # test builds copies with one deliberate slip each and checks that the pins fail)
+        path = os.environ.get("ORACLE_LIB_OVERRIDE") or _build.build()
         L = C.CDLL(path)
         P = C.POINTER
         vp = C.c_void_p

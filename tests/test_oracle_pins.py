@@ -44,6 +44,13 @@ def test_features_hue_threshold_is_integer_exact():
     px = np.array([[[255, 255, 255], [76, 0, 0], [77, 0, 0]]], np.uint8)
     _, RG, _ = O.features(px)
     assert RG[0, 1] == 0.0 and RG[0, 2] == 3.0
+    # the boundary itself: max sum 300, a pixel with sum exactly 30 (10 x 30 = 300) is
+    # not above a tenth, so it gets no hue (the test is strict); sum 31 does
+    px = np.array([[[100, 100, 100], [30, 0, 0], [0, 31, 0], [0, 0, 30]]], np.uint8)
+    _, RG, BY = O.features(px)
+    assert RG[0, 1] == 0.0 and BY[0, 1] == 0.0
+    assert RG[0, 2] == -3.0
+    assert RG[0, 3] == 0.0 and BY[0, 3] == 0.0
 
 
 def test_grey_image_has_no_colour_opponents():
@@ -331,10 +338,13 @@ def test_ncap_closed_form():
 
 def test_terms_ncap_layout():
     rng = np.random.default_rng(14)
-    rgb = rng.integers(0, 256, (6, 7, 3)).astype(np.uint8)
+    # low contrast, so that every n-link is well above zero and a straight link and
+    # a diagonal one of the same colour step differ (high contrast quantises to 0)
+    rgb = rng.integers(100, 106, (6, 7, 3)).astype(np.uint8)
     _, _, nc, _, _ = O.terms(rgb, np.full((6, 7), 0.5), O.CONFIG_VGA)
     s = rgb.astype(int).sum(2)
     assert nc.shape == (4, 6, 7)
+    assert nc[0, :, :6].min() > 1000 and nc[2, :5, :6].min() > 700
     assert nc[0, 2, 3] == O.ncap_value(s[2, 3] - s[2, 4], 0)
     assert nc[1, 2, 3] == O.ncap_value(s[2, 3] - s[3, 3], 0)
     assert nc[2, 2, 3] == O.ncap_value(s[2, 3] - s[3, 4], 1)
