@@ -19,7 +19,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 
-# (file, original text, planted text, what the slip is)
+# (file, original text, planted text, what the slip is); every site occurs in the file
 MUTANTS = [
     ("oracle.c", "I[i] = s / 765.0;", "I[i] = s / 755.0;", "intensity scale"),
     ("oracle.c", "if (10 * s > smax) {", "if (10 * s >= smax) {", "hue threshold boundary"),
@@ -72,6 +72,36 @@ MUTANTS = [
     ("oracle.c", "g_add(g, y * W + x, yy * W + xx, c, c);", "g_add(g, y * W + x, yy * W + xx, c, 0);",
      "n-links one-way"),
     ("oracle.c", "NB_DX[4] = {1, 0, 1, -1}", "NB_DX[4] = {1, 0, 1, 1}", "second diagonal offset"),
+    ("oracle.c", "for (int l = 0; l < level; ++l) n = (n + 1) / 2;", "for (int l = 0; l < level; ++l) n = n / 2 + 1;",
+     "level size rounding"),
+    ("oracle.c", "out[1][2] = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) / d;",
+     "out[1][2] = (m[0][0] * m[1][2] - m[0][2] * m[1][0]) / d;", "3x3 inverse cofactor sign"),
+    ("oracle.c", "m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);\n}",
+     "m[0][2] * (m[1][1] * m[2][0] - m[1][0] * m[2][1]);\n}", "3x3 determinant term sign"),
+    ("oracle.c", "logp[m] = log(g->pi[m]) - 0.5 * q", "logp[m] = -0.5 * q", "mixture weight dropped"),
+    ("oracle.c", "q += dv[k] * Ai[k][j] * dv[j];", "q += dv[k] * Ai[j][j] * dv[j];", "mixture Mahalanobis index"),
+    ("oracle.c", "r[(size_t)i * M + m] = exp(lp[m] - mx) / s;", "r[(size_t)i * M + m] = exp(lp[m] - mx);",
+     "responsibilities not normalised"),
+    ("oracle.c", "g->pi[m] = Nm[m] / Ntot;", "g->pi[m] = 1.0 / M;", "mixture weights never updated"),
+    ("oracle.c", "g->cov[m][k][j] = cv[k][j] / Nm[m] + (k == j ? 1e-4 : 0.0);",
+     "g->cov[m][k][j] = cv[k][j] / sw + (k == j ? 1e-4 : 0.0);", "component covariance normaliser"),
+    ("oracle.c", "for (int k = 0; k < 3; ++k) mu[k] /= Nm[m];", "for (int k = 0; k < 3; ++k) mu[k] /= sw;",
+     "component mean normaliser"),
+    ("oracle.c", "int nty = (h + tile - 1) / tile, ntx = (w + tile - 1) / tile;",
+     "int nty = h / tile, ntx = w / tile;", "N(.) partial edge tiles dropped"),
+    ("oracle.c", "for (int u = -radius; u <= radius; ++u) sg += exp(-(u * u + v * v) / (2 * sigma * sigma));",
+     "for (int u = -radius; u <= radius; ++u) sg += exp(-(u * u + v * v) / (sigma * sigma));",
+     "mask smoothing normaliser"),
+    ("oracle.c", "double p = in[clampi(y + v, 0, h - 1) * w + clampi(x + u, 0, w - 1)];",
+     "double p = in[clampi(y + u, 0, h - 1) * w + clampi(x + v, 0, w - 1)];", "Gabor applied transposed"),
+    ("oracle.c", "double fx = sx - x0;", "double fx = x1 - sx;", "upsample weight side"),
+    ("oracle.c", "for (int k = 0; k < 3; ++k) mu[a][k] = m[k] / sw;", "for (int k = 0; k < 3; ++k) mu[a][k] = m[k] / n;",
+     "colour mean normaliser"),
+    ("oracle.c", "double xi = -log(mind(maxd(p, eps), 1.0 - eps));", "double xi = -log(maxd(p, eps));",
+     "prior clamp at 1 - eps dropped"),
+    ("oracle.c", "    *w_f = 0.0;\n    return a;", "    *w_f = 0.0;\n    return a + b;", "first-frame variance"),
+    ("oracle.c", "    if (tr[x] < delta) delta = tr[x];\n", "\n", "BK bottleneck ignores the source arc"),
+    ("oracle.c", "flow += m; /* s -> v -> t directly */", "/* s -> v -> t dropped */", "BK direct terminal flow"),
     ("oracle_grad.c", "+= KB[j + 2] * KB[i + 2] * g_out[y * w2 + x];", "+= KB[j + 2] * g_out[y * w2 + x];",
      "REDUCE adjoint drops a tap factor"),
     ("oracle_grad.c", "g_src[y0 * ws + x1] += (1 - fy) * fx * g;", "g_src[y0 * ws + x1] += (1 - fy) * (1 - fx) * g;",
@@ -98,9 +128,12 @@ def _build_mutant(tmp, fname, old, new):
 
 def _pins_on(lib):
     env = dict(os.environ, ORACLE_LIB_OVERRIDE=lib)
-    r = subprocess.run([sys.executable, "-m", "pytest", *PIN_TESTS, "-x", "-q", "-p", "no:cacheprovider",
-                        "-k", "not regression_golden"], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
+    try:
+        r = subprocess.run([sys.executable, "-m", "pytest", *PIN_TESTS, "-x", "-q", "-p", "no:cacheprovider",
+                            "-k", "not regression_golden"], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=300)
+    except subprocess.TimeoutExpired:
+        return "timeout", ""
     return r.returncode, r.stdout[-400:]
 
 

@@ -498,6 +498,24 @@ def test_em_recovers_separated_clusters():
     np.testing.assert_allclose(pi[order], np.bincount(lab) / lab.size, atol=0.01)
 
 
+def test_em_components_are_the_weighted_cluster_gaussians():
+    # clusters 13 standard deviations apart: at convergence every responsibility is 0
+    # or 1 to FP64 precision, so each component must be its cluster's prior-weighted
+    # Gaussian (numpy, from the known membership) with the 1e-4 ridge, and its weight
+    # the cluster's share of the total pixel weight
+    rgb, lab, _ = _clustered_rgb(35)
+    w = np.random.default_rng(36).uniform(0.2, 1.0, lab.size)
+    pi, mu, cov = O.gmm_fit(rgb, w, M=3, iters=40)
+    order = np.argsort(mu[:, 0])
+    c = rgb.astype(float) / 255.0
+    for m, k in zip(order, range(3)):
+        sel = lab == k
+        np.testing.assert_allclose(mu[m], np.average(c[sel], axis=0, weights=w[sel]), rtol=1e-9)
+        ref = np.cov(c[sel].T, aweights=w[sel], bias=True) + 1e-4 * np.eye(3)
+        np.testing.assert_allclose(cov[m], ref, rtol=1e-6, atol=1e-12)
+        assert pi[m] == pytest.approx(w[sel].sum() / w.sum(), rel=1e-9)
+
+
 def test_gmm_logpdf_and_terms_match_scipy():
     from scipy.special import logsumexp
     rgb, _, _ = _clustered_rgb(35, n=1200)
