@@ -104,6 +104,18 @@ MUTANTS = [
     ("oracle.c", "flow += m; /* s -> v -> t directly */", "/* s -> v -> t dropped */", "BK direct terminal flow"),
     ("oracle_grad.c", "+= KB[j + 2] * KB[i + 2] * g_out[y * w2 + x];", "+= KB[j + 2] * g_out[y * w2 + x];",
      "REDUCE adjoint drops a tap factor"),
+    ("oracle_grad.c", "double dm = sgv * (-2.0 * (1 - st->mbar)) / (st->nt - 1);",
+     "double dm = sgv * (-2.0 * (1 - st->mbar)) / st->nt;", "N(.) adjoint tile-mean count"),
+    ("oracle_grad.c", "smin += gp[i] * (vp - 1) / D;", "smin += gp[i] * vp / D;", "N(.) adjoint of the minimum"),
+    ("oracle_grad.c", "kre[(v + R) * n + (u + R)] * gr + kim[(v + R) * n + (u + R)] * gi;",
+     "kre[(v + R) * n + (u + R)] * gr - kim[(v + R) * n + (u + R)] * gi;", "Gabor adjoint odd-part sign"),
+    ("oracle_grad.c", "double t = (grn * r + ggn * g + gbn * b) * 3.0 / (s * s);",
+     "double t = (grn * r + ggn * g + gbn * b) * 3.0 / s;", "hue normalisation adjoint power"),
+    ("oracle_grad.c", "double gs = gI[i] / 765.0,", "double gs = gI[i] / 255.0,", "intensity adjoint scale"),
+    ("oracle_grad.c", "double aY = fmin(r, g) - b > 0;", "double aY = fmax(r, g) - b > 0;", "yellow clamp decision"),
+    ("oracle_grad.c", "wr = -Q * dr / (den * den);", "wr = Q * dr / (den * den);", "Kalman gain tangent sign"),
+    ("oracle_grad.c", "Pr = (Q * dr * den - num * dr) / (den * den);", "Pr = (Q * dr * den + num * dr) / (den * den);",
+     "Kalman variance tangent sign"),
     ("oracle_grad.c", "g_src[y0 * ws + x1] += (1 - fy) * fx * g;", "g_src[y0 * ws + x1] += (1 - fy) * (1 - fx) * g;",
      "upsample adjoint weight"),
 ]
