@@ -384,8 +384,13 @@ def dist_setup(backend):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import datetime
+
         import torch.distributed as dist
-        dist.init_process_group(backend=backend)
+        # a rank that dies makes the others' next collective fail within this bound
+        # instead of waiting out the library default
+        timeout = datetime.timedelta(seconds=float(os.environ.get("SEG_DIST_TIMEOUT_S", "600")))
+        dist.init_process_group(backend=backend, timeout=timeout)
     return ws, rank, local
 
 

@@ -56,6 +56,39 @@ def test_two_gloo_replicas_aggregate_max_time_and_total_frames():
     assert all(c >= 0 for c in res[0][4] + res[1][4])
 
 
+def _rank_failing(rank, ws, port, q):
+    import sys
+    import time
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank), SEG_DIST_TIMEOUT_S="10")
+    import bench
+    bench.dist_setup("gloo")
+    if rank == 1:
+        raise SystemExit(3)  # this replica fails between steps, before the aggregation
+    t0 = time.perf_counter()
+    try:
+        bench.aggregate(1.0, 3, ws)
+        q.put(("no error", time.perf_counter() - t0))
+    except Exception as e:  # the surviving rank learns of it from its collective
+        q.put((type(e).__name__, time.perf_counter() - t0))
+
+
+def test_a_failed_replica_ends_the_others_collective_with_an_error():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_failing, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    what, waited = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=60)
+    assert ps[1].exitcode == 3
+    assert what != "no error" and waited < 60, (what, waited)
+    assert ps[0].exitcode == 0
+
+
 def test_single_process_aggregate():
     import sys
     sys.path.insert(0, ROOT)
