@@ -110,13 +110,16 @@ int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg
  * (for admission control by HBM footprint).  Errors as seg_create_batch. */
 int seg_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes);
 
-/* Frees the context and its workspace (synchronises its stream first). */
+/* Frees the context and its workspace (synchronises its stream first).
+ * Errors: SEG_EINVAL (ctx NULL). */
 int seg_destroy(seg_ctx* ctx);
 
 /* Starts a new video: forgets the previous mask and the prior variance, so the
- * next frame is t = 0 (Sec. 6 with P_{-1} = +inf: p-hat = q). */
+ * next frame is t = 0 (Sec. 6 with P_{-1} = +inf: p-hat = q).  Enqueued on the
+ * context's stream.  Errors: SEG_EINVAL (ctx NULL), SEG_ECUDA. */
 int seg_reset(seg_ctx* ctx);
-/* seg_reset for stream b of a batch context only (a new video on that slot). */
+/* seg_reset for stream b of a batch context only (a new video on that slot).
+ * Errors: SEG_EINVAL (ctx NULL, b outside 0..B-1), SEG_ECUDA. */
 int seg_reset_stream(seg_ctx* ctx, int b);
 
 /* One frame of the whole method (Fig. 3; Secs. 3-6).
@@ -134,7 +137,10 @@ int seg_push_frame(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev, fl
 
 /* seg_push_frame with HOST buffers: copies the frame to the device, runs the
  * frame, copies mask and cut value (and saliency/prior when non-NULL) back,
- * then synchronises the stream.  Returns the frame's device status. */
+ * then synchronises the stream.  The buffers hold B*H*W*3 bytes (rgb), B*H*W
+ * bytes (mask), B*H*W floats (saliency, prior) and B int64 (cut); pinned memory
+ * makes the copies asynchronous.  Returns the frame's device status, or
+ * SEG_EINVAL (ctx, rgb_host or mask_host NULL) or SEG_ECUDA. */
 int seg_push_frame_host(seg_ctx* ctx, const uint8_t* rgb_host, float* saliency_host,
                         float* prior_host, uint8_t* mask_host, int64_t* cut_host);
 
@@ -156,7 +162,8 @@ const char* seg_strerror(int code);
  * time, with every input explicit.  They use the context's workspace and do
  * not touch its temporal state. ---- */
 
-/* Sec. 3 / Sec. 7.2: saliency map of one frame into saliency_dev (H*W float). */
+/* Sec. 3 / Sec. 7.2: saliency map of one frame into saliency_dev (H*W float,
+ * B*H*W for a batch context).  Errors: SEG_EINVAL (NULL argument), SEG_ECUDA. */
 int seg_saliency(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev);
 
 /* Sec. 3 / Sec. 7.2: standalone saliency map of one H x W RGB8 frame, without a
@@ -167,17 +174,21 @@ int seg_saliency_grid(void* stream, int H, int W, const seg_params* p, const uin
 
 /* Sec. 5 + Sec. 6: p-hat = w_f * f(prev_mask) + (1 - w_f) * q(saliency), with
  * q = saliency / max(saliency) and eps on the border band.  prev_mask_dev may be
- * NULL when w_f == 0. */
+ * NULL when w_f == 0.  Errors: SEG_EINVAL (NULL ctx, saliency or prior; w_f
+ * outside [0, 1]; prev_mask NULL with w_f != 0; a batch context), SEG_ECUDA. */
 int seg_prior(seg_ctx* ctx, const float* saliency_dev, const uint8_t* prev_mask_dev, double w_f,
               float* prior_dev);
 
 /* Sec. 4 Eqs. 1-4 + Sec. 5: int32 t-links cs = c(s,v), ct = c(v,t) (H*W each)
- * and n-links ncap (nbr/2 planes) from the frame and the prior. */
+ * and n-links ncap (nbr/2 planes of H*W: E, S[, SE, SW]) from the frame and the
+ * prior.  Errors: SEG_EINVAL (NULL argument, a batch context), SEG_ECUDA. */
 int seg_terms(seg_ctx* ctx, const uint8_t* rgb_dev, const float* prior_dev, int32_t* cs_dev,
               int32_t* ct_dev, int32_t* ncap_dev);
 
 /* Sec. 4: exact minimum cut of the context's H x W grid (its neighbourhood)
- * with the given capacities; writes mask and cut value.  Device-side status is
+ * with the given capacities; writes mask and cut value (cut_dev may be NULL).
+ * Errors: SEG_EINVAL (NULL ctx, capacity or mask pointer; a batch context),
+ * SEG_ECUDA; device-side status (cycle cap, capacity range, wait timeout) is
  * reported by seg_sync. */
 int seg_mincut(seg_ctx* ctx, const int32_t* cs_dev, const int32_t* ct_dev, const int32_t* ncap_dev,
                uint8_t* mask_dev, int64_t* cut_dev);
@@ -238,7 +249,7 @@ int seg_profile_read(seg_ctx* ctx, double* stage_ms, int* frames, long long* cyc
  * non-NULL), seven int32 min-cut statistics in mincut_stats[7f .. 7f+6]:
  * cycles, global relabels, fixpoint rounds, then the time spent in
  * initialisation, global relabels, discharge cycles and the final reach pass
- * (units of 0.1 us, read from the device timer). */
+ * (units of 0.1 us, read from the device timer).  Errors as seg_profile_read. */
 int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* cycles, float* frame_ms,
                         int* mincut_stats, int max_frames);
 
@@ -269,7 +280,8 @@ int seg_push_frame_host_async(seg_ctx* ctx, const uint8_t* rgb_host, uint8_t* ma
 int seg_push_frame_ev(seg_ctx* ctx, const uint8_t* rgb_dev, float* saliency_dev, float* prior_dev,
                       uint8_t* mask_dev, int64_t* cut_dev, void* rgb_ready_event);
 
-/* Size of pyramid level `level` along an n-pixel axis: ceil-halving. */
+/* Size of pyramid level `level` along an n-pixel axis: ceil-halving (Sec. 7.2;
+ * level 0 is n itself).  Pure host arithmetic; no error codes. */
 int seg_level_dim(int n, int level);
 
 /* ------------------------------------------------------------------------
