@@ -16,6 +16,8 @@ cycled and the temporal state reset when it wraps).  Reported:
   roofline   the dominant stage's kernel against the measured HBM peak
   cpu_baseline  the FP64 C oracle on a bounded sample of the same clip, one
              core; cpu_baseline_all_cores: one oracle stream per host core
+  mincut_profile  the cut's in-kernel time by push-relabel cycles per frame
+             and per phase (device timer, profiled frames)
   accuracy   Sec. 8.1's error rate, recall, precision and F-value of the
              masks against the clip's synthetic ground truth (sanity only,
              computed on the host after the timed regions)
@@ -74,6 +76,27 @@ def make_clip(n, with_gt=False):
     if with_gt:
         return synth.clip_vga(n)  # (frames, ground-truth masks), the same frames
     return np.stack([f for f, _ in synth.clip_vga_frames(n)])
+
+
+def mincut_profile(stats):
+    """Summary of per-frame min-cut statistics (seg_profile_read_ex: cycles, global
+    relabels, fixpoint rounds, then device-timer time in initialisation, global
+    relabels, discharge cycles and the final reach, in units of 0.1 us): the cut's
+    in-kernel time by the number of push-relabel cycles a frame needed, and the
+    mean time per phase."""
+    a = np.asarray(stats, np.float64).reshape(-1, 7)
+    out = {"frames": int(a.shape[0]), "by_cycles": {}, "phase_us_mean": {},
+           "of": "device-timer spans inside the cut kernel, profiled frames"}
+    if not a.shape[0]:
+        return out
+    span = a[:, 3:7].sum(1) / 10.0
+    for name, sel in (("<=1", a[:, 0] <= 1), ("2", a[:, 0] == 2), (">=3", a[:, 0] >= 3)):
+        if sel.any():
+            out["by_cycles"][name] = {"frames": int(sel.sum()), "mean_us": float(span[sel].mean()),
+                                      "share_of_time": float(span[sel].sum() / span.sum()) if span.sum() else 0.0}
+    out["phase_us_mean"] = dict(zip(["init", "global_relabel", "discharge", "final_reach"],
+                                    (a[:, 3:7].mean(0) / 10.0).tolist()))
+    return out
 
 
 def confusion(mask, gt):
@@ -639,6 +662,7 @@ def run_b300(a):
                       "p99": float(np.percentile(period, 99))},
                       "unpipelined_frames_per_s": value_plain},
         "stages_ms": dict(zip(names, stage)), "mincut_cycles_mean": cycles,
+        "mincut_profile": mincut_profile(prof["mincut_stats"]),
         "roofline": roof,
         "cpu_baseline": {"value": n_cpu / dt_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {n_cpu} frames of the same clip, single-threaded FP64 C oracle"},

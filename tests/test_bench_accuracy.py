@@ -66,3 +66,22 @@ def test_clip_with_ground_truth_has_the_same_frames():
     f2, gt = bench.make_clip(3, with_gt=True)
     assert f1.shape == f2.shape == (3, 480, 640, 3) and (f1 == f2).all()
     assert gt.shape == (3, 480, 640) and gt.dtype == np.uint8 and set(np.unique(gt)) <= {0, 1}
+
+
+def test_mincut_profile_summary():
+    # (cycles, relabels, rounds, init, relabel, discharge, final) in 0.1 us
+    stats = [(1, 1, 3, 3, 90, 250, 150), (1, 1, 3, 3, 92, 248, 146), (2, 2, 6, 3, 290, 600, 157),
+             (4, 4, 12, 3, 1100, 1900, 200)]
+    p = bench.mincut_profile(stats)
+    assert p["frames"] == 4
+    assert p["by_cycles"]["<=1"]["frames"] == 2 and p["by_cycles"]["<=1"]["mean_us"] == pytest.approx(49.1)
+    assert p["by_cycles"]["2"]["mean_us"] == pytest.approx(105.0)
+    assert p["by_cycles"][">=3"]["mean_us"] == pytest.approx(320.3)
+    total = 49.3 + 48.9 + 105.0 + 320.3
+    assert p["by_cycles"][">=3"]["share_of_time"] == pytest.approx(320.3 / total)
+    assert sum(g["share_of_time"] for g in p["by_cycles"].values()) == pytest.approx(1.0)
+    assert p["phase_us_mean"]["discharge"] == pytest.approx((250 + 248 + 600 + 1900) / 40)
+    assert bench.mincut_profile([]) == {"frames": 0, "by_cycles": {}, "phase_us_mean": {},
+                                        "of": "device-timer spans inside the cut kernel, profiled frames"}
+    # the binding's format: a list of 7-tuples, as many as frames were recorded
+    assert bench.mincut_profile([(0, 1, 1, 2, 10, 0, 100)])["by_cycles"]["<=1"]["frames"] == 1
