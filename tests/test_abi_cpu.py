@@ -120,3 +120,24 @@ def test_host_buffers_are_checked_before_the_library_copies(seg):
     sg.B = 2  # a batch of two streams needs twice the bytes
     with pytest.raises(ValueError):
         sg.push_frame_host(rgb, mask, cut)
+
+
+def test_header_is_plain_c_and_links(seg, tmp_path):
+    """A C caller: include/seg.h compiles as pedantic C99 (no C++ in the ABI), links
+    against libseg.so and the host-only calls work without a GPU."""
+    src = tmp_path / "caller.c"
+    src.write_text(
+        '#include "seg.h"\n#include <stdio.h>\n'
+        "int main(void) {\n"
+        "  seg_params p; size_t b = 0;\n"
+        "  if (seg_default_params(&p) != SEG_OK) return 1;\n"
+        "  if (seg_default_params(NULL) != SEG_EINVAL) return 2;\n"
+        "  if (seg_workspace_bytes(1, 120, 160, &p, &b) != SEG_OK || b == 0) return 3;\n"
+        "  printf(\"%d %d %zu %s\\n\", p.levels, p.neighbourhood, b, seg_strerror(SEG_EINVAL));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(seg.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lseg", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out[:2] == ["9", "8"] and int(out[2]) > 100 * 120 * 160
