@@ -102,6 +102,12 @@ MUTANTS = [
     ("oracle.c", "    *w_f = 0.0;\n    return a;", "    *w_f = 0.0;\n    return a + b;", "first-frame variance"),
     ("oracle.c", "    if (tr[x] < delta) delta = tr[x];\n", "\n", "BK bottleneck ignores the source arc"),
     ("oracle.c", "flow += m; /* s -> v -> t directly */", "/* s -> v -> t dropped */", "BK direct terminal flow"),
+    ("oracle.c", "  memcpy(st->prev_mask, mask, n);\n  st->P = Pt;", "  st->P = Pt;", "previous mask never carried over"),
+    ("oracle.c", "  st->P = Pt;\n  st->t += 1;", "  st->t += 1;", "Kalman variance never carried over"),
+    ("oracle.c", "st->t > 0 ? st->prev_mask : NULL, w_f, q, prior);", "NULL, w_f, q, prior);",
+     "previous segmentation ignored by the prior"),
+    ("oracle.c", "int64_t cut = orc_maxflow_bk(H, W, P->neighbourhood, cs, ct, nc, mask);",
+     "int64_t cut = orc_maxflow_bk(H, W, 4, cs, ct, nc, mask);", "frame cut on the wrong neighbourhood"),
     ("oracle_grad.c", "+= KB[j + 2] * KB[i + 2] * g_out[y * w2 + x];", "+= KB[j + 2] * g_out[y * w2 + x];",
      "REDUCE adjoint drops a tap factor"),
     ("oracle_grad.c", "double dm = sgv * (-2.0 * (1 - st->mbar)) / (st->nt - 1);",
@@ -139,7 +145,8 @@ def _build_mutant(tmp, fname, old, new):
 
 
 def _pins_on(lib):
-    env = dict(os.environ, ORACLE_LIB_OVERRIDE=lib)
+    # the concurrent runs share the source tree: none of them writes bytecode there
+    env = dict(os.environ, ORACLE_LIB_OVERRIDE=lib, PYTHONDONTWRITEBYTECODE="1")
     try:
         r = subprocess.run([sys.executable, "-m", "pytest", *PIN_TESTS, "-x", "-q", "-p", "no:cacheprovider",
                             "-k", "not regression_golden"], cwd=ROOT, env=env, capture_output=True, text=True,

@@ -446,6 +446,32 @@ def test_maxflow_edge_cases():
 
 
 # ---------------------------------------------------------------- regression guard
+@pytest.mark.parametrize("cfg", [O.CONFIG_SMALL, O.CONFIG_VGA], ids=["4-neighbour", "8-neighbour"])
+def test_frame_sequence_carries_mask_and_variance(cfg):
+    # Sec. 6 wiring of the per-frame method: frame t's prior is built from frame t's
+    # saliency, the mask the method returned for frame t-1 and the Kalman weight of
+    # step t; the cut is the exact cut of the terms of that prior (each part pinned
+    # on its own above)
+    frames, _ = synth.clip_small(4, seed=synth.SEED_BASE + 9)
+    H, W = frames.shape[1:3]
+    sg = O.Segmenter(H, W, cfg)
+    P, prev = 0.0, None
+    for t in range(4):
+        sal, pr, mask, cut = sg.push(frames[t])
+        P, wf = O.kalman_step(t, P)
+        assert sg.t == t + 1 and sg.P_var == P
+        np.testing.assert_array_equal(sal, O.saliency(frames[t], cfg))
+        _, pr_ref = O.prior(sal, prev if t else None, wf, cfg)
+        np.testing.assert_array_equal(pr, pr_ref)
+        cs, ct, nc, _, _ = O.terms(frames[t], pr_ref, cfg)
+        v, m = O.maxflow(cs, ct, nc)
+        assert cut == v
+        np.testing.assert_array_equal(mask, m)
+        if t:
+            assert wf > 0 and prev.any()  # the previous mask really enters from the second frame on
+        prev = mask.copy()
+
+
 def test_small_clip_regression_golden():
     import json
     import os
