@@ -85,3 +85,23 @@ def test_mincut_profile_summary():
                                         "of": "device-timer spans inside the cut kernel, profiled frames"}
     # the binding's format: a list of 7-tuples, as many as frames were recorded
     assert bench.mincut_profile([(0, 1, 1, 2, 10, 0, 100)])["by_cycles"]["<=1"]["frames"] == 1
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the oracle on the host cores, rank 0) prints one JSON
+    line with the same metric and config as the CUDA arm, impl = reference, and an e2e
+    object with no host-device bytes."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0"))
+    assert r.returncode == 0, r.stderr[-800:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "frames/s"
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1 and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["config"]["workload"] == bench.WORKLOAD
+    assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
