@@ -1,6 +1,6 @@
-"""Host-side accuracy measures that bench.py reports next to the throughput:
-Sec. 8.1's error rate, recall, precision and F-value of a mask against ground
-truth, checked on hand-counted cases (no GPU)."""
+"""The host-side parts of bench.py (no GPU): Sec. 8.1's error rate, recall,
+precision and F-value of a mask against ground truth on hand-counted cases, the
+summary of the min cut's per-frame statistics, and the reference arm's JSON line."""
 import math
 import os
 import sys
