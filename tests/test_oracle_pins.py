@@ -199,6 +199,25 @@ def test_saliency_grey_frame_has_no_colour_conspicuity():
     assert dbg["consp"][0].max() > 0 and dbg["consp"][3].max() > 0
 
 
+def test_opponent_center_surround_makes_a_uniform_red_region_conspicuous():
+    # Itti's RG center-surround is (R-G)(c) minus (G-R)(s), i.e. |RG(c) + RG(s)|: inside a
+    # uniform red region both terms are the same positive value, so the whole region is
+    # conspicuous in the RG channel, and a grey region is not.  With a plain difference
+    # |RG(c) - RG(s)| the interior cancels and only the boundary remains.
+    H, W = 120, 160
+    img = np.full((H, W, 3), 120, np.uint8)
+    img[:, :W // 2] = (200, 50, 50)
+    _, d = O.saliency(img, O.CONFIG_SMALL, debug=True)
+    rg = d["consp"][1]
+    wS = rg.shape[1]
+    red_inside, grey_inside = rg[:, : wS // 2 - 6], rg[:, wS // 2 + 8:]
+    assert red_inside.min() >= 0.95 * rg.max() and grey_inside.max() <= 0.05 * rg.max()
+    _, d = O.saliency(img, O.CONFIG_SMALL, debug=True, cs_opponent_sum=0)
+    rg = d["consp"][1]
+    assert rg[:, : wS // 2 - 8].max() <= 0.05 * rg.max()
+    assert wS // 2 - 4 <= int(np.argmax(rg.max(0))) <= wS // 2 + 4
+
+
 def test_saliency_transpose_equivariance():
     rgb = synth.random_frame(64, 64, 11)
     a = O.saliency(rgb, O.CONFIG_SMALL)
