@@ -108,6 +108,8 @@ MUTANTS = [
      "previous segmentation ignored by the prior"),
     ("oracle.c", "int64_t cut = orc_maxflow_bk(H, W, P->neighbourhood, cs, ct, nc, mask);",
      "int64_t cut = orc_maxflow_bk(H, W, 4, cs, ct, nc, mask);", "frame cut on the wrong neighbourhood"),
+    ("oracle.c", "  if (v > 16777216.0) v = 16777216.0;\n", "\n", "capacity cap at 2^24 dropped"),
+    ("oracle.c", "if (!(mx - mn > flat)) {", "if (!(mx - mn > 10.0 * flat)) {", "N(.) flat-map threshold"),
     ("oracle_grad.c", "+= KB[j + 2] * KB[i + 2] * g_out[y * w2 + x];", "+= KB[j + 2] * g_out[y * w2 + x];",
      "REDUCE adjoint drops a tap factor"),
     ("oracle_grad.c", "double dm = sgv * (-2.0 * (1 - st->mbar)) / (st->nt - 1);",

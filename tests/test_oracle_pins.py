@@ -181,6 +181,12 @@ def test_normalize_flat_map_is_zero():
     v = np.full((9, 9), 2.0)
     v[0, 0] += 1e-7  # range below the flat threshold
     assert not O.normalize(v, flat=1e-5).any()
+    # just above the threshold the map is normalised: its single peak rescales to 1, the
+    # other three 8x8 tiles have maximum 0, so mbar = 0 and the peak keeps N = 1
+    v = np.full((9, 9), 2.0)
+    v[4, 4] += 2e-5
+    n = O.normalize(v, flat=1e-5)
+    assert n[4, 4] == pytest.approx(1.0) and np.count_nonzero(n) == 1
 
 
 # ---------------------------------------------------------------- saliency map
@@ -353,6 +359,17 @@ def test_ncap_closed_form():
     assert O.ncap_value(d, 0) == O.ncap_value(-d, 0) == math.floor(
         1500 * math.exp(-(d / 765) ** 2 / (2 * 0.05 ** 2)) + 0.5)
     assert O.ncap_value(0, 0, lambda_p=0.25) == 1750
+
+
+def test_capacities_are_capped_at_2_pow_24():
+    # integer capacities are min(2^24, floor(K cost + 1/2)): a huge Potts constant or
+    # capacity scale saturates at exactly 2^24, never beyond
+    assert O.ncap_value(0, 0, lambda_p=1e5) == 1 << 24
+    assert O.ncap_value(0, 1, lambda_p=1e5) == 1 << 24
+    rng = np.random.default_rng(15)
+    rgb = rng.integers(0, 256, (6, 7, 3)).astype(np.uint8)
+    cs, ct, nc, _, _ = O.terms(rgb, rng.uniform(0.01, 0.99, (6, 7)), O.CONFIG_VGA, cap_scale=1e9)
+    assert max(cs.max(), ct.max(), nc.max()) == 1 << 24 and min(cs.min(), ct.min(), nc.min()) >= 0
 
 
 def test_terms_ncap_layout():
