@@ -205,18 +205,20 @@ int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_t* cs_dev,
 /* seg_mincut_grid without any device allocation, for callers that are not
  * allowed to call cudaMalloc (code living under another framework's memory
  * pool, processes with a fixed device-memory quota, real-time loops that must
- * not allocate after start-up).  The paper has no counterpart: this is a
- * deployment variant of the Sec. 4 min-cut entry point above.
+ * not allocate after start-up).  The paper has no counterpart.
  *   Same arguments, results and return codes as seg_mincut_grid, except that
  *   cut_dev must not be NULL and H*W may be at most
  *   SEG_MINCUT_STATIC_MAX_PIXELS (SEG_EINVAL otherwise).
  *   The workspace is one fixed device array inside the library (about 6 MB on
  *   every GPU that loads it, held until the process exits).  The first call on
- *   each device looks up that array's device address (cudaGetSymbolAddress),
- *   so make that first call before any stream capture.
+ *   each device looks up that array's device address (cudaGetSymbolAddress)
+ *   and keeps it for the life of the process, so make that first call before
+ *   any stream capture; a cudaDeviceReset makes the kept address stale, and
+ *   the entry point must not be used on that device afterwards.
  *   All calls share the one array: calls that overlap on the GPU (two streams,
  *   or two host threads on the same device) race and corrupt each other's
- *   results.  The call synchronises `stream` before returning. */
+ *   results.  Every call waits for its cut: it synchronises `stream` and
+ *   copies the device status word to the host before returning. */
 #define SEG_MINCUT_STATIC_MAX_PIXELS 131072
 int seg_mincut_grid_static(void* stream, int H, int W, int nbr, const int32_t* cs_dev,
                            const int32_t* ct_dev, const int32_t* ncap_dev, uint8_t* mask_dev,

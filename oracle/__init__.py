@@ -77,6 +77,7 @@ def lib():
             "orc_upsample": [C.c_int, C.c_int, vp, C.c_int, C.c_int, vp],
             "orc_normalize": [C.c_int, C.c_int, vp, C.c_int, C.c_double, vp],
             "orc_saliency_ex": [P(OrcParams), C.c_int, C.c_int, vp, vp, P(OrcDebug)],
+            "orc_saliency_compose": [P(OrcParams), C.c_int, C.c_int, vp, vp, vp, vp],
             "orc_smooth_mask": [C.c_int, C.c_int, vp, C.c_double, C.c_int, vp],
             "orc_prior": [P(OrcParams), C.c_int, C.c_int, vp, vp, C.c_double, vp, vp],
             "orc_terms": [P(OrcParams), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp],
@@ -228,6 +229,23 @@ def saliency(rgb, cfg=None, debug=False, **over):
     res["consp"] = bufs["consp"].reshape(4, hS, wS)
     res["S"] = bufs["S"].reshape(hS, wS)
     return out, res
+
+
+def saliency_compose(pyr, ori, H, W, cfg=None, **over):
+    """Steps 4-6 of the saliency map on given pyramids: pyr[c][l] (c = I, RG, BY; every level
+    0..levels-1 of an H x W frame) and ori[k][l] (orientation k, levels c_min..c_max+d_max).
+    Returns (consp (4, hS, wS): N(C_I), N(C_RG), N(C_BY), N(C_O); S (hS, wS))."""
+    P = params(cfg, **over)
+    dims = [(level_dim(H, l), level_dim(W, l)) for l in range(P.levels)]
+    s_max = P.c_max + P.d_max
+    flat_p = np.concatenate([np.asarray(pyr[c][l], np.float64).reshape(dims[l]).ravel()
+                             for c in range(3) for l in range(P.levels)])
+    flat_o = np.concatenate([np.asarray(ori[k][l], np.float64).reshape(dims[l]).ravel()
+                             for k in range(P.n_orient) for l in range(P.c_min, s_max + 1)])
+    hS, wS = dims[P.c_max]
+    consp, S = np.empty((4, hS, wS)), np.empty((hS, wS))
+    lib().orc_saliency_compose(C.byref(P), H, W, _p(flat_p), _p(flat_o), _p(consp), _p(S))
+    return consp, S
 
 
 def kalman_step(t, P_prev, sigma1=0.03, sigma2=0.035):

@@ -14,10 +14,11 @@
  * is named in the comment ("Reading: ...").
  *
  * Parity status: every function below is pinned by tests against closed
- * forms, invariants, library routines or brute force, except the end-to-end
- * composition of the saliency map (orc_saliency_ex), which is pinned through
- * its pinned parts, constant/grey/transpose invariants and the N(.) affine
- * invariance, but has no printed worked example in the paper.
+ * forms, invariants, library routines or brute force.  The composition of
+ * the saliency map from its pyramids (orc_saliency_compose) is pinned on
+ * hand-built pyramids whose conspicuity maps and S follow in closed form
+ * (single and double peaks, two center scales, per-orientation N(.), the
+ * source of each surround); the paper prints no worked example.
  */
 #include "oracle.h"
 
@@ -196,45 +197,45 @@ void orc_normalize(int h, int w, const double* v, int tile, double flat, double*
   for (int i = 0; i < n; ++i) out[i] *= f;
 }
 
-/* Sec. 3 / Sec. 7.2: the saliency map.
- *   1. features at level 0; 2. pyramids of I, RG, BY; 3. Gabor orientation
- *   maps O(sigma, theta) on the intensity pyramid; 4. center-surround maps at
- *   scale c for every (c, s = c + d): |X(c) - up X(s)| for I and O(theta),
- *   |X(c) + up X(s)| for RG and BY (Itti's (R-G)(c) minus (G-R)(s)); 5. N(.)
- *   of every map; 6. "weighted addition": REDUCE every normalised map down to
- *   sigma_S = c_max and add per channel; the orientation conspicuity is
- *   sum_theta N(sum_{c,s} N(O)); S = sum_k w_k N(C_k); the saliency map is S
- *   upsampled to the frame size. */
-void orc_saliency_ex(const orc_params* P, int H, int W, const uint8_t* rgb, double* saliency,
-                     orc_saliency_debug* dbg) {
-  int L = P->levels;
+/* Sec. 3 / Sec. 7.2 steps 4-6, the composition of the saliency map from its
+ * feature pyramids (the Itti-Koch model cited in Sec. 3; Sec. 7.2 calls the
+ * last step "weighted addition" of normalised maps):
+ *   4. center-surround maps at scale c for every (c, s = c + d):
+ *      |X(c) - up X(s)| for I and for each O(theta) (the surround of O(theta)
+ *      is O(s, theta)); |X(c) + up X(s)| for RG and BY (Itti's (R-G)(c)
+ *      minus (G-R)(s));
+ *   5. N(.) of every center-surround map;
+ *   6. REDUCE every normalised map down to sigma_S = c_max and add per
+ *      channel: C_I, C_RG, C_BY; the orientation conspicuity is
+ *      C_O = sum_theta N(sum_{c,s} N(O(c, s, theta)));
+ *      S = sum_k w_k N(C_k) over k = I, RG, BY, O.
+ * Inputs use the layout of orc_saliency_debug: pyr holds the three channels'
+ * levels 0..levels-1 back to back, ori holds n_orient blocks of the levels
+ * c_min..c_max+d_max; level l of an H x W frame is orc_level_dim(H, l) x
+ * orc_level_dim(W, l).  Outputs: consp (4 maps N(C_k) at sigma_S, may be
+ * NULL) and S (the map at sigma_S). */
+void orc_saliency_compose(const orc_params* P, int H, int W, const double* pyr, const double* ori,
+                          double* consp, double* S) {
+  int L = P->levels, s_max = P->c_max + P->d_max, no = P->n_orient;
   int hl[64], wl[64];
   for (int l = 0; l < L; ++l) {
     hl[l] = orc_level_dim(H, l);
     wl[l] = orc_level_dim(W, l);
   }
-  double* pyr[3][64];
+  const double* X[3][64];
+  const double* Ot[16][64];
+  size_t off = 0;
   for (int c = 0; c < 3; ++c)
-    for (int l = 0; l < L; ++l) pyr[c][l] = (double*)malloc(sizeof(double) * hl[l] * wl[l]);
-  orc_features(H, W, rgb, pyr[0][0], pyr[1][0], pyr[2][0]);
-  for (int c = 0; c < 3; ++c)
-    for (int l = 1; l < L; ++l) orc_reduce(hl[l - 1], wl[l - 1], pyr[c][l - 1], pyr[c][l]);
-
-  int s_max = P->c_max + P->d_max;
-  int no = P->n_orient;
-  int R = P->gabor_radius, kn = 2 * R + 1;
-  double* ori[64][16];
-  double* kre = (double*)malloc(sizeof(double) * kn * kn);
-  double* kim = (double*)malloc(sizeof(double) * kn * kn);
-  for (int k = 0; k < no; ++k) {
-    orc_gabor_kernel(k * M_PI / no, P->gabor_lambda, P->gabor_sigma, R, kre, kim);
-    for (int l = P->c_min; l <= s_max; ++l) {
-      ori[l][k] = (double*)malloc(sizeof(double) * hl[l] * wl[l]);
-      orc_gabor(hl[l], wl[l], pyr[0][l], kre, kim, R, ori[l][k]);
+    for (int l = 0; l < L; ++l) {
+      X[c][l] = pyr + off;
+      off += (size_t)hl[l] * wl[l];
     }
-  }
-  free(kre);
-  free(kim);
+  off = 0;
+  for (int k = 0; k < no; ++k)
+    for (int l = P->c_min; l <= s_max; ++l) {
+      Ot[k][l] = ori + off;
+      off += (size_t)hl[l] * wl[l];
+    }
 
   int sS = P->c_max;
   int hS = hl[sS], wS = wl[sS], nS = hS * wS;
@@ -250,8 +251,8 @@ void orc_saliency_ex(const orc_params* P, int H, int W, const uint8_t* rgb, doub
       int s = c + d;
       int nc = hl[c] * wl[c];
       for (int f = 0; f < nacc; ++f) {
-        const double* cen = f < 3 ? pyr[f][c] : ori[c][f - 3];
-        const double* sur = f < 3 ? pyr[f][s] : ori[s][f - 3];
+        const double* cen = f < 3 ? X[f][c] : Ot[f - 3][c];
+        const double* sur = f < 3 ? X[f][s] : Ot[f - 3][s];
         orc_upsample(hl[s], wl[s], sur, hl[c], wl[c], up);
         int opp = (f == 1 || f == 2) && P->cs_opponent_sum;
         for (int i = 0; i < nc; ++i) map[i] = fabs(opp ? cen[i] + up[i] : cen[i] - up[i]);
@@ -272,41 +273,70 @@ void orc_saliency_ex(const orc_params* P, int H, int W, const uint8_t* rgb, doub
     orc_normalize(hS, wS, acc + (size_t)(3 + k) * nS, P->norm_tile, P->norm_flat, tmp);
     for (int i = 0; i < nS; ++i) C[3][i] += tmp[i];
   }
-  double* S = (double*)calloc(nS, sizeof(double));
+  for (int i = 0; i < nS; ++i) S[i] = 0.0;
   for (int k = 0; k < 4; ++k) {
     orc_normalize(hS, wS, C[k], P->norm_tile, P->norm_flat, tmp);
-    if (dbg && dbg->consp) memcpy(dbg->consp + (size_t)k * nS, tmp, sizeof(double) * nS);
+    if (consp) memcpy(consp + (size_t)k * nS, tmp, sizeof(double) * nS);
     for (int i = 0; i < nS; ++i) S[i] += P->w[k] * tmp[i];
   }
-  if (dbg && dbg->S) memcpy(dbg->S, S, sizeof(double) * nS);
-  orc_upsample(hS, wS, S, H, W, saliency);
-
-  if (dbg && dbg->pyr) {
-    size_t off = 0;
-    for (int c = 0; c < 3; ++c)
-      for (int l = 0; l < L; ++l) {
-        memcpy(dbg->pyr + off, pyr[c][l], sizeof(double) * hl[l] * wl[l]);
-        off += (size_t)hl[l] * wl[l];
-      }
-  }
-  if (dbg && dbg->ori) {
-    size_t off = 0;
-    for (int k = 0; k < no; ++k)
-      for (int l = P->c_min; l <= s_max; ++l) {
-        memcpy(dbg->ori + off, ori[l][k], sizeof(double) * hl[l] * wl[l]);
-        off += (size_t)hl[l] * wl[l];
-      }
-  }
-  for (int c = 0; c < 3; ++c)
-    for (int l = 0; l < L; ++l) free(pyr[c][l]);
-  for (int k = 0; k < no; ++k)
-    for (int l = P->c_min; l <= s_max; ++l) free(ori[l][k]);
   for (int k = 0; k < 4; ++k) free(C[k]);
   free(acc);
   free(up);
   free(map);
   free(nm);
   free(tmp);
+}
+
+/* Sec. 3 / Sec. 7.2: the saliency map.
+ *   1. features at level 0; 2. pyramids of I, RG, BY; 3. Gabor orientation
+ *   maps O(sigma, theta) on the intensity pyramid, sigma in [c_min, c_max +
+ *   d_max]; 4-6. the composition above (center-surround, N(.), weighted
+ *   addition) gives S at sigma_S; the saliency map is S upsampled to the
+ *   frame size. */
+void orc_saliency_ex(const orc_params* P, int H, int W, const uint8_t* rgb, double* saliency,
+                     orc_saliency_debug* dbg) {
+  int L = P->levels, s_max = P->c_max + P->d_max, no = P->n_orient;
+  int hl[64], wl[64];
+  size_t lev_off[65], ori_area = 0;
+  lev_off[0] = 0;
+  for (int l = 0; l < L; ++l) {
+    hl[l] = orc_level_dim(H, l);
+    wl[l] = orc_level_dim(W, l);
+    lev_off[l + 1] = lev_off[l] + (size_t)hl[l] * wl[l];
+    if (l >= P->c_min && l <= s_max) ori_area += (size_t)hl[l] * wl[l];
+  }
+  size_t pyr_area = lev_off[L];
+  /* pyr: channel c, level l at c * pyr_area + lev_off[l] */
+  double* pyr = (double*)malloc(sizeof(double) * 3 * pyr_area);
+  orc_features(H, W, rgb, pyr, pyr + pyr_area, pyr + 2 * pyr_area);
+  for (int c = 0; c < 3; ++c)
+    for (int l = 1; l < L; ++l)
+      orc_reduce(hl[l - 1], wl[l - 1], pyr + c * pyr_area + lev_off[l - 1], pyr + c * pyr_area + lev_off[l]);
+
+  /* ori: orientation k, level l at k * ori_area + (lev_off[l] - lev_off[c_min]) */
+  int R = P->gabor_radius, kn = 2 * R + 1;
+  double* ori = (double*)malloc(sizeof(double) * (no > 0 ? no : 1) * (ori_area > 0 ? ori_area : 1));
+  double* kre = (double*)malloc(sizeof(double) * kn * kn);
+  double* kim = (double*)malloc(sizeof(double) * kn * kn);
+  for (int k = 0; k < no; ++k) {
+    orc_gabor_kernel(k * M_PI / no, P->gabor_lambda, P->gabor_sigma, R, kre, kim);
+    for (int l = P->c_min; l <= s_max; ++l)
+      orc_gabor(hl[l], wl[l], pyr + lev_off[l], kre, kim, R,
+                ori + k * ori_area + (lev_off[l] - lev_off[P->c_min]));
+  }
+  free(kre);
+  free(kim);
+
+  int nS = hl[P->c_max] * wl[P->c_max];
+  double* S = (double*)malloc(sizeof(double) * nS);
+  orc_saliency_compose(P, H, W, pyr, ori, dbg ? dbg->consp : NULL, S);
+  if (dbg && dbg->S) memcpy(dbg->S, S, sizeof(double) * nS);
+  orc_upsample(hl[P->c_max], wl[P->c_max], S, H, W, saliency);
+
+  if (dbg && dbg->pyr) memcpy(dbg->pyr, pyr, sizeof(double) * 3 * pyr_area);
+  if (dbg && dbg->ori) memcpy(dbg->ori, ori, sizeof(double) * no * ori_area);
+  free(pyr);
+  free(ori);
   free(S);
 }
 

@@ -73,6 +73,11 @@ void orc_gabor(int h, int w, const double* in, const double* kre, const double* 
                double* out);
 void orc_upsample(int hs, int ws, const double* src, int hd, int wd, double* dst);
 void orc_normalize(int h, int w, const double* v, int tile, double flat, double* out);
+/* Steps 4-6 (center-surround, N(.), weighted addition) on given pyramids laid out as
+ * orc_saliency_debug's pyr and ori; writes the four N(C_k) maps (consp, may be NULL) and S at
+ * sigma_S = c_max. */
+void orc_saliency_compose(const orc_params* P, int H, int W, const double* pyr, const double* ori,
+                          double* consp, double* S);
 void orc_saliency_ex(const orc_params* P, int H, int W, const uint8_t* rgb, double* saliency,
                      orc_saliency_debug* dbg);
 void orc_saliency(const orc_params* P, int H, int W, const uint8_t* rgb, double* saliency);

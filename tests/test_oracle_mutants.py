@@ -110,6 +110,16 @@ MUTANTS = [
      "int64_t cut = orc_maxflow_bk(H, W, 4, cs, ct, nc, mask);", "frame cut on the wrong neighbourhood"),
     ("oracle.c", "  if (v > 16777216.0) v = 16777216.0;\n", "\n", "capacity cap at 2^24 dropped"),
     ("oracle.c", "if (!(mx - mn > flat)) {", "if (!(mx - mn > 10.0 * flat)) {", "N(.) flat-map threshold"),
+    ("oracle.c", "orc_normalize(hS, wS, acc + (size_t)(3 + k) * nS, P->norm_tile, P->norm_flat, tmp);",
+     "memcpy(tmp, acc + (size_t)(3 + k) * nS, sizeof(double) * nS);", "per-orientation N(.) dropped"),
+    ("oracle.c", "orc_normalize(hl[c], wl[c], map, P->norm_tile, P->norm_flat, nm);",
+     "memcpy(nm, map, sizeof(double) * nc);", "feature-map N(.) dropped"),
+    ("oracle.c", "const double* sur = f < 3 ? X[f][s] : Ot[f - 3][s];",
+     "const double* sur = f < 3 ? X[f][s] : X[0][s];", "orientation surround from the intensity pyramid"),
+    ("oracle.c", "orc_normalize(hS, wS, C[k], P->norm_tile, P->norm_flat, tmp);",
+     "memcpy(tmp, C[k], sizeof(double) * nS);", "conspicuity N(.) dropped"),
+    ("oracle.c", "for (int l = c; l < sS; ++l) {", "for (int l = c + 1; l < sS; ++l) {",
+     "one REDUCE too few to sigma_S"),
     ("oracle_grad.c", "+= KB[j + 2] * KB[i + 2] * g_out[y * w2 + x];", "+= KB[j + 2] * g_out[y * w2 + x];",
      "REDUCE adjoint drops a tap factor"),
     ("oracle_grad.c", "double dm = sgv * (-2.0 * (1 - st->mbar)) / (st->nt - 1);",
@@ -128,7 +138,12 @@ MUTANTS = [
      "upsample adjoint weight"),
 ]
 
-PIN_TESTS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_oracle_grad.py")]
+# A slip in the forward oracle must fail a pin of test_oracle_pins.py (tied to closed forms,
+# library routines and brute force), not only the agreement of the forward with the backward
+# oracle's second forward implementation; a slip in the backward oracle must fail
+# test_oracle_grad.py (central differences and closed forms of the adjoints).
+PIN_TESTS = {"oracle.c": [os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+             "oracle_grad.c": [os.path.join(ROOT, "tests", "test_oracle_grad.py")]}
 
 
 def _build_mutant(tmp, fname, old, new):
@@ -146,11 +161,11 @@ def _build_mutant(tmp, fname, old, new):
     return lib
 
 
-def _pins_on(lib):
+def _pins_on(lib, fname):
     # the concurrent runs share the source tree: none of them writes bytecode there
     env = dict(os.environ, ORACLE_LIB_OVERRIDE=lib, PYTHONDONTWRITEBYTECODE="1")
     try:
-        r = subprocess.run([sys.executable, "-m", "pytest", *PIN_TESTS, "-x", "-q", "-p", "no:cacheprovider",
+        r = subprocess.run([sys.executable, "-m", "pytest", *PIN_TESTS[fname], "-x", "-q", "-p", "no:cacheprovider",
                             "-k", "not regression_golden"], cwd=ROOT, env=env, capture_output=True, text=True,
                            timeout=300)
     except subprocess.TimeoutExpired:
@@ -164,7 +179,7 @@ def test_every_planted_mistake_fails_a_pin():
             fname, old, new, what = MUTANTS[i]
             tmp = os.path.join(base, str(i))
             os.mkdir(tmp)
-            return what, _pins_on(_build_mutant(tmp, fname, old, new))
+            return what, _pins_on(_build_mutant(tmp, fname, old, new), fname)
 
         with ThreadPoolExecutor(max_workers=min(4, os.cpu_count() or 1)) as ex:
             results = list(ex.map(one, range(len(MUTANTS))))
@@ -177,5 +192,6 @@ def test_every_planted_mistake_fails_a_pin():
 def test_the_unmodified_copy_passes_the_pins():
     with tempfile.TemporaryDirectory() as tmp:
         lib = _build_mutant(tmp, "oracle.c", "I[i] = s / 765.0;", "I[i] = s / 765.0;")
-        rc, tail = _pins_on(lib)
-    assert rc == 0, tail
+        for fname in PIN_TESTS:
+            rc, tail = _pins_on(lib, fname)
+            assert rc == 0, tail

@@ -243,6 +243,153 @@ def test_saliency_debug_pyramid_consistent():
     np.testing.assert_allclose(sum(w[k] * dbg["consp"][k] for k in range(4)), dbg["S"], atol=1e-14)
 
 
+# ---------------------------------------------------------------- saliency composition
+# Steps 4-6 of the saliency map (center-surround, N(.), weighted addition; Itti's model as
+# cited in Sec. 3, "weighted addition" of normalised maps in Sec. 7.2) on hand-built
+# pyramids whose conspicuity maps follow in closed form.  The 160x120 configuration's
+# scales are used on a 128x128 frame: centers c in {1, 2} (64x64, 32x32), surrounds
+# s = c + {2, 3} in {3, 4, 5}, disjoint from the centers; sigma_S = 2 (32x32, 4x4 tiles of
+# 8).  With zero surrounds a center map that is a single positive peak normalises to the
+# unit impulse (rescaled peak 1, every other tile maximum 0, so mbar = 0).
+_CW = (0.1, 0.2, 0.3, 0.4)
+_CCFG = dict(O.CONFIG_SMALL, w=_CW)
+_CN = 128
+_NT = 16  # tiles of 8x8 at sigma_S
+
+
+def _cpyr():
+    dims = [(O.level_dim(_CN, l),) * 2 for l in range(6)]
+    pyr = [[np.zeros(dims[l]) for l in range(6)] for _ in range(3)]
+    ori = [{l: np.zeros(dims[l]) for l in range(1, 6)} for _ in range(4)]
+    return pyr, ori
+
+
+def _delta(*pts, shape=(32, 32)):
+    d = np.zeros(shape)
+    for p in pts:
+        d[p] = 1.0
+    return d
+
+
+def _reduced_impulse(y, x, shape=(32, 32)):
+    # REDUCE of a unit impulse at the even position (2y, 2x): only the taps at even
+    # offsets -2, 0, 2 of [1 4 6 4 1]/16 reach the kept samples, so the result is the
+    # outer product of [1 6 1]/16 with itself centred at (y, x)
+    r = np.zeros(shape)
+    r[y - 1:y + 2, x - 1:x + 2] = np.outer([1, 6, 1], [1, 6, 1]) / 256.0
+    return r
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_compose_single_peak_in_one_channel(k):
+    # one channel, one peak at sigma_S: each of its two center-surround maps normalises to
+    # the impulse, their sum 2 delta normalises back to delta; every other map is zero
+    # (flat, N = 0), so S = w_k delta
+    pyr, ori = _cpyr()
+    p = (13, 18)
+    if k < 3:
+        pyr[k][2][p] = 0.7
+    else:
+        ori[2][2][p] = 0.7
+    consp, S = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    for j in range(4):
+        np.testing.assert_allclose(consp[j], _delta(p) if j == k else 0.0, atol=1e-15)
+    np.testing.assert_allclose(S, _CW[k] * _delta(p), atol=1e-15)
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_compose_two_equal_peaks(k):
+    # two equal peaks in different tiles: every N(.) keeps them equal and scales by
+    # (1 - mbar)^2 with mbar = (2 - 1) / (n_tiles - 1); the two center-surround maps add to
+    # 2g(delta_p + delta_q) and the conspicuity N(.) maps that back to g(delta_p + delta_q)
+    pyr, ori = _cpyr()
+    p, q = (3, 4), (27, 20)
+    pyr[k][2][p] = pyr[k][2][q] = 0.25
+    g = (1 - 1 / (_NT - 1)) ** 2
+    consp, S = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    np.testing.assert_allclose(consp[k], g * _delta(p, q), atol=1e-15)
+    np.testing.assert_allclose(S, _CW[k] * g * _delta(p, q), atol=1e-15)
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_compose_two_center_scales(k):
+    # a peak of height 3 at level 1 (even position) and one of height 0.5 at sigma_S = 2:
+    # each center-surround map is normalised before it is REDUCEd, so the level-1 map
+    # reaches sigma_S as the REDUCEd unit impulse r (peak 36/256), whatever its height; the
+    # sum is 2(r + delta); its N(.) has maximum 1 at delta and tile maxima {1, 36/256, 0..}
+    pyr, ori = _cpyr()
+    (y1, x1), p2 = (5, 6), (22, 25)
+    pyr[k][1][2 * y1, 2 * x1] = 3.0
+    pyr[k][2][p2] = 0.5
+    r = _reduced_impulse(y1, x1)
+    mbar = (36 / 256) / (_NT - 1)
+    want = (r + _delta(p2)) * (1 - mbar) ** 2
+    consp, S = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    np.testing.assert_allclose(consp[k], want, atol=1e-15)
+    np.testing.assert_allclose(S, _CW[k] * want, atol=1e-15)
+
+
+def test_compose_each_orientation_normalised_before_the_sum():
+    # orientation 0 has a peak at sigma_S only, orientation 1 a peak at level 1 only: the
+    # orientation conspicuity takes N(.) of each orientation's sum first, so both reach the
+    # sum over theta with peak 1 (delta and r / (36/256)); then two tiles hold maximum 1
+    pyr, ori = _cpyr()
+    (y1, x1), p2 = (9, 10), (24, 27)
+    ori[0][2][p2] = 0.9
+    ori[1][1][2 * y1, 2 * x1] = 0.2
+    rhat = _reduced_impulse(y1, x1) / (36 / 256)
+    want = (_delta(p2) + rhat) * (1 - 1 / (_NT - 1)) ** 2
+    consp, S = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    np.testing.assert_allclose(consp[3], want, atol=1e-15)
+    assert not consp[:3].any()
+    np.testing.assert_allclose(S, _CW[3] * want, atol=1e-15)
+
+
+def test_compose_surround_sources():
+    # the surround of O(c, theta) is O(s, theta) of the same orientation and the surround
+    # of X(c) is X(s) of the same channel.  A constant surround k larger than a center peak
+    # a makes the map k everywhere except k - a at the peak: rescaled, every tile maximum
+    # is 1, mbar = 1 and N = 0.  Intensity surrounds of 0.8 must not reach the
+    # orientation maps (their own surrounds are 0), and an orientation-0 surround of 0.8
+    # must leave orientation 2 alone.
+    pyr, ori = _cpyr()
+    p = (14, 9)
+    for s in (3, 4, 5):
+        pyr[0][s][:] = 0.8
+        ori[0][s][:] = 0.8
+    ori[2][2][p] = 0.3
+    consp, S = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    np.testing.assert_allclose(consp[3], _delta(p), atol=1e-15)
+    assert not consp[:3].any()
+    # the same peak in orientation 0, whose own surrounds are 0.8: everything is flat
+    ori[2][2][p] = 0.0
+    ori[0][2][p] = 0.3
+    consp, S = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    assert not consp.any() and not S.any()
+    # colour opponents: the surround enters with its sign flipped (|X(c) + X(s)|), so a
+    # surround of -0.8 under a center peak of 0.3 gives the flat case, +0.8 the impulse
+    pyr, ori = _cpyr()
+    pyr[1][2][p] = 0.3
+    for s in (3, 4, 5):
+        pyr[1][s][:] = -0.8
+    consp, _ = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    assert not consp.any()
+    for s in (3, 4, 5):
+        pyr[1][s][:] = 0.8
+    consp, _ = O.saliency_compose(pyr, ori, _CN, _CN, _CCFG)
+    np.testing.assert_allclose(consp[1], _delta(p), atol=1e-15)
+
+
+def test_compose_is_the_saliency_maps_last_steps():
+    # orc_saliency_ex's S is the composition of its own pyramids (wiring of steps 1-3 to 4-6)
+    frames, _ = synth.clip_small(2)
+    _, d = O.saliency(frames[1], O.CONFIG_SMALL, debug=True)
+    ori = [{l: d["ori"][k][l] for l in range(1, 6)} for k in range(4)]
+    consp, S = O.saliency_compose(d["pyr"], ori, 120, 160, O.CONFIG_SMALL)
+    np.testing.assert_array_equal(S, d["S"])
+    np.testing.assert_array_equal(consp, d["consp"])
+
+
 def test_saliency_finds_the_red_disk():
     frames, gt = synth.clip_small(3)
     for t in range(3):
