@@ -85,6 +85,10 @@ typedef struct seg_params {
   int32_t warm_start;      /* 1: each stream's min cut starts from its previous frame's n-link flows
                               (dynamic graph cuts, Sec. 1 / Sec. 8.2 prior art); results are identical
                               to a cold start; 0: cold start every frame */
+  int32_t barrier_timeout_us; /* time limit of every wait at a grid barrier of the min cut, in
+                              microseconds (1 .. 60e6; 4e6): a CTA that waits longer records
+                              SEG_ETIMEOUT, every CTA then returns at its next barrier, and the
+                              context stays usable (failure detection; no wait is unbounded) */
 } seg_params;
 
 /* Fills *p with the defaults above.  Returns SEG_EINVAL if p is NULL. */
@@ -109,6 +113,14 @@ int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg
 /* Device bytes seg_create_batch(B, H, W, p) would allocate for its workspace
  * (for admission control by HBM footprint).  Errors as seg_create_batch. */
 int seg_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes);
+
+/* Changes the min cut's grid-barrier time limit (seg_params.barrier_timeout_us)
+ * of an existing context, e.g. a watchdog tightened after start-up.  Waits for
+ * the context's stream and drops its captured CUDA graphs (the limit is a
+ * kernel argument; the next seg_push_frame captures them again).  No
+ * paper counterpart: failure detection of the device-side waits.
+ * Errors: SEG_EINVAL (ctx NULL, us outside 1 .. 60e6), SEG_ECUDA. */
+int seg_set_barrier_timeout(seg_ctx* ctx, int us);
 
 /* Frees the context and its workspace (synchronises its stream first).
  * Errors: SEG_EINVAL (ctx NULL). */
@@ -151,8 +163,13 @@ int seg_push_frame_host(seg_ctx* ctx, const uint8_t* rgb_host, float* saliency_h
 int seg_sync(seg_ctx* ctx, int* cycles);
 
 /* Temporal state (Sec. 6: A_{t-1} and sigma^2_xi1(t-1), plus the frame index)
- * as an opaque byte string.  seg_get_state with buf == NULL stores the needed
- * size in *n.  Both synchronise the stream.  Errors: SEG_EINVAL (size). */
+ * as a byte string: a 16-byte header of four uint32 (0x53454732, H, W, B);
+ * then per stream 16 bytes (int32 frame index t, int32 0, double variance
+ * P_{t-1}); then the B previous masks, H*W bytes each (0/1).  Host byte
+ * order.  seg_get_state with buf == NULL stores the needed size in *n.  Both
+ * synchronise the stream; seg_set_state makes the next cut start cold (the
+ * warm-start flows are not part of the state).  Errors: SEG_EINVAL (size,
+ * header not matching the context). */
 int seg_get_state(seg_ctx* ctx, void* buf, size_t* n);
 int seg_set_state(seg_ctx* ctx, const void* buf, size_t n);
 

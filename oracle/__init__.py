@@ -435,6 +435,12 @@ class Segmenter:
                                    _p(sal), _p(pr), _p(mask))
         return sal, pr, mask, int(cut)
 
+    def set_state(self, t, P_var, prev_mask):
+        """Temporal state of Sec. 6 (frame index, variance P_{t-1}, previous mask)."""
+        self.prev[:] = _c(prev_mask, np.uint8).reshape(self.H, self.W)
+        self.st.t = int(t)
+        self.st.P = float(P_var)
+
     @property
     def t(self):
         return self.st.t

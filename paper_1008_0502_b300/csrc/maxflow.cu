@@ -642,7 +642,7 @@ int mf_grid_size(int H, int W, int* grid) {
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed, bool init_done) {
+              long long timeout_ns, const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed, bool init_done) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
   a.flow = flow;
@@ -678,7 +678,7 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
   a.max_cycles = max_cycles;
   a.gr_every = gr_every < 1 ? 1 : gr_every;
   a.local_iters = local_iters < 1 ? 1 : local_iters;
-  a.timeout_ns = 4000000000LL;
+  a.timeout_ns = timeout_ns;
   a.init_done = init_done ? 1 : 0;
   if (!words_zeroed) {  // (else the caller's frame-start kernel has zeroed them)
     SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, st));

@@ -72,7 +72,8 @@ extern "C" int seg_mincut_grid_static(void* stream, int H, int W, int nbr, const
   seg_params d;
   seg_default_params(&d);
   rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, (long long*)cut, status,
-                 max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every, d.local_iters);
+                 max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every, d.local_iters,
+                 1000LL * d.barrier_timeout_us);
   if (rc) return rc;
   int hs[4] = {0, 0, 0, 0};
   if (cudaStreamSynchronize(st) != cudaSuccess) return SEG_ECUDA;

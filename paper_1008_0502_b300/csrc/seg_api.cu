@@ -54,6 +54,7 @@ extern "C" int seg_default_params(seg_params* p) {
   p->gmm_components = 1;
   p->em_iters = 5;
   p->warm_start = 1;
+  p->barrier_timeout_us = 4000000;
   return SEG_OK;
 }
 
@@ -86,6 +87,7 @@ int seg_check_params(const seg_params* p, int H, int W) {
   if (!(p->sigma1 >= 0) || !(p->sigma2 >= 0) || !(p->sigma_I > 0) || !(p->cap_scale > 0)) return SEG_EINVAL;
   if (!(p->eps > 0) || !(p->eps < 0.5f)) return SEG_EINVAL;
   if (p->max_cycles < 1 || p->global_relabel_every < 1 || p->local_iters < 1) return SEG_EINVAL;
+  if (p->barrier_timeout_us < 1 || p->barrier_timeout_us > 60000000) return SEG_EINVAL;
   if (p->gmm_components < 1 || p->gmm_components > SEG_MAX_GMM || p->em_iters < 0 || p->em_iters > 100)
     return SEG_EINVAL;
   return SEG_OK;
@@ -255,6 +257,23 @@ extern "C" int seg_destroy(seg_ctx* c) {
   return SEG_OK;
 }
 
+extern "C" int seg_set_barrier_timeout(seg_ctx* c, int us) {
+  if (!c || us < 1 || us > 60000000) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->s_front) SEG_CUDA_TRY(cudaStreamSynchronize(c->s_front));
+  c->p.barrier_timeout_us = us;
+  // the limit is baked into the captured graphs' kernel arguments: capture again
+  if (c->graph_state == 1) cudaGraphExecDestroy(c->gexec);
+  if (c->graph_state != 0) c->graph_state = 0;
+  if (c->pipe_graph == 1)
+    for (int k = 0; k < 2; ++k) {
+      cudaGraphExecDestroy(c->gf[k]);
+      cudaGraphExecDestroy(c->gb[k]);
+    }
+  if (c->pipe_graph != 0) c->pipe_graph = 0;
+  return SEG_OK;
+}
+
 extern "C" int seg_reset(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, c->B * sizeof(KalmanDev), c->stream));
@@ -282,10 +301,11 @@ static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const in
   if (c->io_mode)  // mask and cut come from the frame's SegIO; k_set_io zeroed the words
     return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
                      nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
-                     c->p.local_iters, c->io, flow, warm, true, init_done);
+                     c->p.local_iters, 1000LL * c->p.barrier_timeout_us, c->io, flow, warm, true, init_done);
   return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
-                   c->p.global_relabel_every, c->p.local_iters, nullptr, flow, warm, false, init_done);
+                   c->p.global_relabel_every, c->p.local_iters, 1000LL * c->p.barrier_timeout_us, nullptr, flow,
+                   warm, false, init_done);
 }
 
 // The launch sequence of one frame.  With c->io_mode set (graph capture) every
@@ -830,7 +850,7 @@ extern "C" int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_
   if (!rc)
     rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, cut ? (long long*)cut : cut_tmp,
                    status, max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every,
-                   d.local_iters);
+                   d.local_iters, 1000LL * d.barrier_timeout_us);
   int hs[4] = {0, 0, 0, 0};
   if (cudaStreamSynchronize(st) != cudaSuccess) rc = SEG_ECUDA;
   if (!rc && cudaMemcpy(hs, status, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SEG_ECUDA;

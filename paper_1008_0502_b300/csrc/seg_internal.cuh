@@ -285,7 +285,8 @@ __device__ __forceinline__ long long seg_now() {
 // generation word in another cache line, polled with acquire loads; the CTA
 // barriers before and after carry the other threads' writes (release and
 // acquire are cumulative), so no full fences are needed.  The timer is read
-// every 256 polls.  ok: a shared-memory word of the CTA.
+// every 8 polls (a few microseconds of waiting at most).  ok: a shared-memory
+// word of the CTA.
 __device__ __forceinline__ bool seg_grid_sync(GridBar* bar, int* status, long long timeout_ns, int* ok_smem) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -302,7 +303,7 @@ __device__ __forceinline__ bool seg_grid_sync(GridBar* bar, int* status, long lo
         unsigned int cur;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
         if (cur != g) break;
-        if ((k & 255u) == 255u && seg_now() - t0 > timeout_ns) {
+        if ((k & 7u) == 7u && seg_now() - t0 > timeout_ns) {
           atomicCAS(&status[0], 0, SEG_ETIMEOUT);
           ok = 0;
           break;
@@ -456,7 +457,7 @@ int mf_grid_size(int H, int W, int* grid);
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr,
+              long long timeout_ns, const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr,
               bool words_zeroed = false, bool init_done = false);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }

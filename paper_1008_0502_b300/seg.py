@@ -44,7 +44,7 @@ class seg_params(C.Structure):
         ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int32),
         ("max_cycles", C.c_int32), ("global_relabel_every", C.c_int32), ("local_iters", C.c_int32),
         ("use_graph", C.c_int32), ("gmm_components", C.c_int32), ("em_iters", C.c_int32),
-        ("warm_start", C.c_int32),
+        ("warm_start", C.c_int32), ("barrier_timeout_us", C.c_int32),
     ]
 
 
@@ -61,6 +61,7 @@ def _load():
         "seg_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
         "seg_destroy": ([vp], i32),
         "seg_reset": ([vp], i32),
+        "seg_set_barrier_timeout": ([vp, i32], i32),
         "seg_push_frame": ([vp, vp, vp, vp, vp, vp], i32),
         "seg_push_frame_host": ([vp, vp, vp, vp, vp, vp], i32),
         "seg_sync": ([vp, P(C.c_int)], i32),
@@ -299,6 +300,12 @@ class Segmenter:
         else:
             _check(lib.seg_reset_stream(self.handle, int(stream_index)), "seg_reset_stream")
         self._end(cur)
+
+    def set_barrier_timeout(self, us: int):
+        """Time limit of the min cut's grid-barrier waits (seg_set_barrier_timeout); waits for
+        the context's stream and re-captures its graphs on the next frame."""
+        _check(lib.seg_set_barrier_timeout(self.handle, int(us)), "seg_set_barrier_timeout")
+        self.params.barrier_timeout_us = int(us)
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)

@@ -87,6 +87,14 @@ def test_mincut_profile_summary():
     assert bench.mincut_profile([(0, 1, 1, 2, 10, 0, 100)])["by_cycles"]["<=1"]["frames"] == 1
 
 
+def test_spread_frames_cover_the_clip():
+    assert bench.spread_frames(1) == [0]
+    assert bench.spread_frames(4) == [0, 75, 150, 225]
+    idx = bench.spread_frames(20)
+    assert len(set(idx)) == 20 and max(idx) >= 280 and any(200 <= f < 250 for f in idx)
+    assert bench.spread_frames(300) == list(range(300))
+
+
 def test_reference_arm_prints_the_contract_line():
     """bench.py --impl reference (the oracle on the host cores, rank 0) prints one JSON
     line with the same metric and config as the CUDA arm, impl = reference, and an e2e
@@ -102,6 +110,6 @@ def test_reference_arm_prints_the_contract_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "frames/s"
     assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1 and d["higher_is_better"] is True
-    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["config"]["workload"] == bench.WORKLOAD
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["config"] == bench.bench_config()
     assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
