@@ -969,6 +969,59 @@ __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, i
   }
 }
 
+// S -> H x W saliency for a band of UP_ROWS output rows per CTA: the few rows of
+// S the band touches are first interpolated along x into shared memory (each
+// once per band instead of once per output row), then every output pixel is
+// the interpolation of two of those rows along y, four pixels per 16-byte
+// store.  The arithmetic and its order are seg_bilinear_t's: along x within a
+// source row, then along y.
+#define UP_ROWS 8
+__global__ void __launch_bounds__(256) k_upsample_rows(const float* __restrict__ S, int hs, int ws, int H, int W,
+                                                       float* __restrict__ sal, const SegIO* io,
+                                                       const int2* __restrict__ frow,
+                                                       const int2* __restrict__ fcol) {
+  seg_pdl_enter();
+  extern __shared__ __align__(16) float up_smem[];  // [rows of S touched][W]
+  if (!sal) sal = io->sal;
+  const int fb = blockIdx.y;  // frame of the batch
+  S += (size_t)fb * hs * ws;
+  sal += (size_t)fb * H * W;
+  const int y_first = blockIdx.x * UP_ROWS, y_last = min(y_first + UP_ROWS, H) - 1;
+  const int s0 = frow[y_first].x & 0xffff, s1 = frow[y_last].x >> 16;  // source rows s0 .. s1
+  const int nr = s1 - s0 + 1;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    const int2 rx = fcol[x];
+    const int x0 = rx.x & 0xffff, x1 = rx.x >> 16;
+    const float fx = __int_as_float(rx.y);
+    for (int r = 0; r < nr; ++r) {
+      const float* row = S + (size_t)(s0 + r) * ws;
+      up_smem[r * W + x] = (1.f - fx) * row[x0] + fx * row[x1];
+    }
+  }
+  __syncthreads();
+  const bool vec = (W & 3) == 0 && ((uintptr_t)sal & 15) == 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int y = y_first + wid; y <= y_last; y += nw) {  // one warp per output row
+    const int2 ry = frow[y];
+    const float* t = up_smem + (size_t)((ry.x & 0xffff) - s0) * W;
+    const float* b = up_smem + (size_t)((ry.x >> 16) - s0) * W;
+    const float fy = __int_as_float(ry.y);
+    float* out = sal + (size_t)y * W;
+    if (vec) {
+      for (int x = 4 * lane; x < W; x += 128) {
+        float4 v;
+        v.x = (1.f - fy) * t[x] + fy * b[x];
+        v.y = (1.f - fy) * t[x + 1] + fy * b[x + 1];
+        v.z = (1.f - fy) * t[x + 2] + fy * b[x + 2];
+        v.w = (1.f - fy) * t[x + 3] + fy * b[x + 3];
+        *reinterpret_cast<float4*>(out + x) = v;
+      }
+    } else {
+      for (int x = lane; x < W; x += 32) out[x] = (1.f - fy) * t[x] + fy * b[x];
+    }
+  }
+}
+
 // The same maps on a cluster of four CTAs per frame (one conspicuity map each),
 // exchanging the N(.) coefficients through distributed shared memory:
 //   1. CTA r: N(.) statistics of orientation maps r, r + 4, ..; every CTA
@@ -1172,6 +1225,21 @@ int sal_layout(SalWS& s, int B, int H, int W, const seg_params& p, size_t* bytes
     s.consp_cl = s.nch - 3 <= SEG_MAX_ORIENT && need_cl <= cap &&
                  cudaFuncSetAttribute(k_consp_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) == cudaSuccess;
     s.consp_cl_smem = s.consp_cl ? need_cl : 0;
+    cudaGetLastError();
+  }
+  // row-staged up-sampling: the most rows of S one band of UP_ROWS output rows touches
+  {
+    const int hS = s.hl[s.sS];
+    int nr = 0;
+    for (int y = 0; y < H; y += UP_ROWS) {
+      const int yl = (y + UP_ROWS < H ? y + UP_ROWS : H) - 1;
+      const int r = (seg_rs_entry(yl, hS, H).x >> 16) - (seg_rs_entry(y, hS, H).x & 0xffff) + 1;
+      nr = r > nr ? r : nr;
+    }
+    s.up_smem = sizeof(float) * (size_t)nr * W;
+    if (s.up_smem > 160 * 1024 ||
+        cudaFuncSetAttribute(k_upsample_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.up_smem) != cudaSuccess)
+      s.up_smem = 0;
     cudaGetLastError();
   }
   size_t off = 0;
@@ -1460,7 +1528,11 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     SEG_CUDA_TRY(seg_launch(k_consp<true>, B, 1024, s.consp_smem, st, pa));
   else
     SEG_CUDA_TRY(seg_launch(k_consp<false>, B, 1024, 0, st, pa));
-  if (upsample) {
+  if (upsample && s.up_smem) {
+    const dim3 gu((H + UP_ROWS - 1) / UP_ROWS, B);
+    SEG_CUDA_TRY(seg_launch(k_upsample_rows, gu, 256, s.up_smem, st, s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io,
+                            s.rs + s.rs_frow, s.rs + s.rs_fcol));
+  } else if (upsample) {
     dim3 gu((W + 255) / 256, (H + 3) / 4, B);  // 4 pixels per thread
     SEG_CUDA_TRY(seg_launch(k_upsample, gu, 256, 0, st, s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,
                                    s.rs + s.rs_fcol));

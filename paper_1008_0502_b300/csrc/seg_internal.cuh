@@ -217,6 +217,9 @@ struct SalWS {
   int consp_cl;       // the four-CTA cluster form of k_consp runs instead
   size_t consp_cl_smem;
   GaborTaps taps;
+  // row-staged up-sampling (k_upsample_rows): its dynamic shared memory (0: the
+  // per-pixel kernel)
+  size_t up_smem;
   // resampling tables (seg_rs_entry): per center-surround pair p, rows
   // hl[s]->hl[c] at rs + rs_row[p] and columns wl[s]->wl[c] at rs + rs_col[p];
   // the final up-sampling S -> H x W at rs + rs_frow / rs + rs_fcol
