@@ -89,6 +89,11 @@ typedef struct seg_params {
                               microseconds (1 .. 60e6; 4e6): a CTA that waits longer records
                               SEG_ETIMEOUT, every CTA then returns at its next barrier, and the
                               context stays usable (failure detection; no wait is unbounded) */
+  int32_t kmeans_iters;    /* Lloyd iterations of the k-means start of the EM (gmm_components > 1;
+                              Sec. 7.3); the seeds are k-means++ taken in expectation (3; 0 .. 100) */
+  int32_t gmm_update;      /* 1: a stream's EM starts from its previous frame's fitted mixtures (the
+                              likelihood update of Sec. 2 / Sec. 6), the k-means start only on a
+                              video's first frame; 0: every frame starts from the k-means start */
 } seg_params;
 
 /* Fills *p with the defaults above.  Returns SEG_EINVAL if p is NULL. */

@@ -29,7 +29,7 @@ class OrcParams(C.Structure):
         ("f_sigma", C.c_double), ("f_radius", C.c_int), ("eps", C.c_double),
         ("lambda_u", C.c_double), ("lambda_p", C.c_double), ("lambda_s", C.c_double),
         ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int),
-        ("gmm_components", C.c_int), ("em_iters", C.c_int),
+        ("gmm_components", C.c_int), ("em_iters", C.c_int), ("kmeans_iters", C.c_int), ("gmm_update", C.c_int),
     ]
 
 
@@ -43,7 +43,8 @@ class OrcDebug(C.Structure):
 
 
 class OrcState(C.Structure):
-    _fields_ = [("t", C.c_int), ("P", C.c_double), ("prev_mask", C.c_void_p)]
+    _fields_ = [("t", C.c_int), ("P", C.c_double), ("prev_mask", C.c_void_p), ("gmm_valid", C.c_int),
+                ("gmm", OrcGmm * 2)]
 
 
 # The 640x480 workload's parameters (9 images, centers 2..4, surrounds c+3..c+4,
@@ -54,7 +55,7 @@ CONFIG_VGA = dict(levels=9, c_min=2, c_max=4, d_min=3, d_max=4, n_orient=4, gabo
                   w=(1 / 3, 1 / 6, 1 / 6, 1 / 3), cs_opponent_sum=1, border_px=1, sigma1=0.03,
                   sigma2=0.035, f_sigma=2.0, f_radius=6, eps=1e-4, lambda_u=1.0, lambda_p=0.0,
                   lambda_s=1.5, sigma_I=0.05, cap_scale=1000.0, neighbourhood=8, gmm_components=1,
-                  em_iters=5)
+                  em_iters=5, kmeans_iters=3, gmm_update=1)
 CONFIG_SMALL = dict(CONFIG_VGA, levels=6, c_min=1, c_max=2, d_min=2, d_max=3, neighbourhood=4)
 
 
@@ -81,6 +82,7 @@ def lib():
             "orc_smooth_mask": [C.c_int, C.c_int, vp, C.c_double, C.c_int, vp],
             "orc_prior": [P(OrcParams), C.c_int, C.c_int, vp, vp, C.c_double, vp, vp],
             "orc_terms": [P(OrcParams), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp],
+            "orc_terms_ex": [P(OrcParams), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int],
         }.items():
             getattr(L, name).argtypes = args
             getattr(L, name).restype = None
@@ -97,8 +99,8 @@ def lib():
         L.orc_bruteforce.restype = C.c_int64
         for name in ("orc_gmm_init", "orc_gmm_fit"):
             getattr(L, name).restype = None
-        L.orc_gmm_init.argtypes = [vp, vp, C.c_int, C.c_int, P(OrcGmm)]
-        L.orc_gmm_fit.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, P(OrcGmm)]
+        L.orc_gmm_init.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, P(OrcGmm)]
+        L.orc_gmm_fit.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, P(OrcGmm)]
         L.orc_gmm_em_step.argtypes = [vp, vp, C.c_int, P(OrcGmm)]
         L.orc_gmm_em_step.restype = None
         L.orc_gmm_loglik.argtypes = [vp, vp, C.c_int, P(OrcGmm)]
@@ -343,32 +345,76 @@ def terms(rgb, prior_map, cfg=None, **over):
     return cs, ct, nc, D0, D1
 
 
+def terms_from(rgb, prior_map, mix=None, cfg=None, **over):
+    """terms() with the colour mixtures carried between frames: the EM of each label starts
+    from mix (a pair of OrcGmm, e.g. the previous frame's) when it is given, else from the
+    k-means start.  Returns (cs, ct, ncap, mixtures fitted here)."""
+    rgb = _c(rgb, np.uint8)
+    prior_map = _c(prior_map, np.float64)
+    H, W = prior_map.shape
+    P = params(cfg, **over)
+    cs, ct = np.empty((H, W), np.int32), np.empty((H, W), np.int32)
+    nc = np.empty((P.neighbourhood // 2, H, W), np.int32)
+    out = (OrcGmm * 2)()
+    if mix is not None:
+        out[0], out[1] = mix[0], mix[1]
+    lib().orc_terms_ex(C.byref(P), H, W, _p(rgb), _p(prior_map), _p(cs), _p(ct), _p(nc), None, None, out,
+                       1 if mix is not None else 0)
+    return cs, ct, nc, (out[0], out[1])
+
+
 def _gmm_out(g):
     M = g.M
     return (np.array(g.pi[:M]), np.array([[g.mu[m][k] for k in range(3)] for m in range(M)]),
             np.array([[[g.cov[m][k][j] for j in range(3)] for k in range(3)] for m in range(M)]))
 
 
-def gmm_fit(rgb, w, M=3, iters=5):
+def gmm_fit(rgb, w, M=3, iters=5, km_iters=3):
     """Prior-weighted GMM over C = RGB/255: returns (pi, mu, cov)."""
     rgb = _c(rgb, np.uint8).reshape(-1, 3)
     w = _c(w, np.float64).ravel()
     g = OrcGmm()
-    lib().orc_gmm_fit(_p(rgb), _p(w), w.size, M, iters, C.byref(g))
+    lib().orc_gmm_fit(_p(rgb), _p(w), w.size, M, km_iters, iters, C.byref(g))
     return _gmm_out(g)
 
 
-def gmm_em_trace(rgb, w, M=3, iters=5):
+def gmm_init(rgb, w, M=3, km_iters=3):
+    """The EM's k-means start (seeds, Lloyd iterations, mixture of the partition): (pi, mu, cov)."""
+    rgb = _c(rgb, np.uint8).reshape(-1, 3)
+    w = _c(w, np.float64).ravel()
+    g = OrcGmm()
+    lib().orc_gmm_init(_p(rgb), _p(w), w.size, M, km_iters, C.byref(g))
+    return _gmm_out(g)
+
+
+def gmm_em_trace(rgb, w, M=3, iters=5, km_iters=3):
     """Weighted log-likelihood after init and after each EM step."""
     rgb = _c(rgb, np.uint8).reshape(-1, 3)
     w = _c(w, np.float64).ravel()
     g = OrcGmm()
-    lib().orc_gmm_init(_p(rgb), _p(w), w.size, M, C.byref(g))
+    lib().orc_gmm_init(_p(rgb), _p(w), w.size, M, km_iters, C.byref(g))
     out = [lib().orc_gmm_loglik(_p(rgb), _p(w), w.size, C.byref(g))]
     for _ in range(iters):
         lib().orc_gmm_em_step(_p(rgb), _p(w), w.size, C.byref(g))
         out.append(lib().orc_gmm_loglik(_p(rgb), _p(w), w.size, C.byref(g)))
     return out
+
+
+def gmm_em_from(rgb, w, pi, mu, cov, iters=1):
+    """iters EM steps from the mixture (pi, mu, cov): returns (pi, mu, cov)."""
+    rgb = _c(rgb, np.uint8).reshape(-1, 3)
+    w = _c(w, np.float64).ravel()
+    g = OrcGmm()
+    g.M = len(pi)
+    for m in range(g.M):
+        g.pi[m] = pi[m]
+        for k in range(3):
+            g.mu[m][k] = mu[m][k]
+            for j in range(3):
+                g.cov[m][k][j] = cov[m][k][j]
+    for _ in range(iters):
+        lib().orc_gmm_em_step(_p(rgb), _p(w), w.size, C.byref(g))
+    return _gmm_out(g)
 
 
 def gmm_logpdf(pi, mu, cov, c):

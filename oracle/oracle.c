@@ -510,7 +510,34 @@ double orc_gmm_logpdf(const orc_gmm* g, const double c[3]) {
   return mx + log(s);
 }
 
-void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, orc_gmm* g) {
+/* Sec. 7.3: EM of the colour mixtures starts from a k-means partition.
+ * Reading (the paper names a CPU k-means but not its start): the seeds are
+ * k-means++ taken in expectation instead of drawn at random -- c_1 is the
+ * weighted mean of the colours, c_m (m > 1) the mean of the colours weighted by
+ * w_i D_i^2, D_i the distance of C_i to its nearest earlier seed (the expected
+ * position of a k-means++ draw, which picks C_i with probability proportional
+ * to w_i D_i^2).  Then km_iters weighted Lloyd iterations: every pixel joins its
+ * nearest center (the lowest index on equal distances), every center whose
+ * cluster carries at least 1e-6 of the weight moves to its cluster's weighted
+ * mean.  The mixture is the final partition's: pi_m = cluster weight / total,
+ * mu_m and Sigma_m (+ 1e-4 I) the cluster's weighted mean and covariance; a
+ * cluster below 1e-6 of the weight keeps its center, the label's covariance and
+ * its (tiny or zero) weight. */
+static int nearest_center(const double c[3], const double (*ctr)[3], int M) {
+  int best = 0;
+  double bd = DBL_MAX;
+  for (int m = 0; m < M; ++m) {
+    double d = 0;
+    for (int k = 0; k < 3; ++k) d += (c[k] - ctr[m][k]) * (c[k] - ctr[m][k]);
+    if (d < bd) {
+      bd = d;
+      best = m;
+    }
+  }
+  return best;
+}
+
+void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, int km_iters, orc_gmm* g) {
   double sw = 0, mu[3] = {0, 0, 0}, cv[3][3] = {{0}};
   for (int i = 0; i < n; ++i) {
     sw += w[i];
@@ -521,19 +548,71 @@ void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, orc_gmm* g)
     for (int k = 0; k < 3; ++k)
       for (int j = 0; j < 3; ++j)
         cv[k][j] += w[i] * (rgb[3 * i + k] / 255.0 - mu[k]) * (rgb[3 * i + j] / 255.0 - mu[j]);
-  double sg2 = 0;
   for (int k = 0; k < 3; ++k)
-    for (int j = 0; j < 3; ++j) {
-      cv[k][j] = cv[k][j] / sw + (k == j ? 1e-4 : 0.0);
-      sg2 += cv[k][j] / 3.0;  /* g^T Sigma g with g = (1,1,1)/sqrt3 */
+    for (int j = 0; j < 3; ++j) cv[k][j] = cv[k][j] / sw + (k == j ? 1e-4 : 0.0);
+  /* seeds */
+  double ctr[3][3];
+  memcpy(ctr[0], mu, sizeof(mu));
+  for (int m = 1; m < M; ++m) {
+    double s = 0, acc[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+      double c[3] = {rgb[3 * i] / 255.0, rgb[3 * i + 1] / 255.0, rgb[3 * i + 2] / 255.0};
+      double d2 = DBL_MAX;
+      for (int j = 0; j < m; ++j) {
+        double d = 0;
+        for (int k = 0; k < 3; ++k) d += (c[k] - ctr[j][k]) * (c[k] - ctr[j][k]);
+        d2 = mind(d2, d);
+      }
+      s += w[i] * d2;
+      for (int k = 0; k < 3; ++k) acc[k] += w[i] * d2 * c[k];
     }
+    for (int k = 0; k < 3; ++k) ctr[m][k] = s > 0 ? acc[k] / s : mu[k];
+  }
+  /* Lloyd iterations */
+  for (int it = 0; it < km_iters; ++it) {
+    double W[3] = {0, 0, 0}, S[3][3] = {{0}};
+    for (int i = 0; i < n; ++i) {
+      double c[3] = {rgb[3 * i] / 255.0, rgb[3 * i + 1] / 255.0, rgb[3 * i + 2] / 255.0};
+      int m = nearest_center(c, (const double(*)[3])ctr, M);
+      W[m] += w[i];
+      for (int k = 0; k < 3; ++k) S[m][k] += w[i] * c[k];
+    }
+    for (int m = 0; m < M; ++m)
+      if (W[m] >= 1e-6 * sw)
+        for (int k = 0; k < 3; ++k) ctr[m][k] = S[m][k] / W[m];
+  }
+  /* the mixture of the final partition (two passes per cluster) */
+  double W[3] = {0, 0, 0}, S[3][3] = {{0}};
+  int* lab = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i) {
+    double c[3] = {rgb[3 * i] / 255.0, rgb[3 * i + 1] / 255.0, rgb[3 * i + 2] / 255.0};
+    lab[i] = nearest_center(c, (const double(*)[3])ctr, M);
+    W[lab[i]] += w[i];
+    for (int k = 0; k < 3; ++k) S[lab[i]][k] += w[i] * c[k];
+  }
   g->M = M;
   for (int m = 0; m < M; ++m) {
-    double off = (m - (M - 1) / 2.0) * 1.5 * sqrt(sg2) / sqrt(3.0);
-    g->pi[m] = 1.0 / M;
-    for (int k = 0; k < 3; ++k) g->mu[m][k] = mu[k] + off;
-    memcpy(g->cov[m], cv, sizeof(cv));
+    g->pi[m] = W[m] / sw;
+    if (!(W[m] >= 1e-6 * sw)) {
+      memcpy(g->mu[m], ctr[m], sizeof(ctr[m]));
+      memcpy(g->cov[m], cv, sizeof(cv));
+      continue;
+    }
+    double cm[3];
+    for (int k = 0; k < 3; ++k) cm[k] = S[m][k] / W[m];
+    double cc[3][3] = {{0}};
+    for (int i = 0; i < n; ++i) {
+      if (lab[i] != m) continue;
+      for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j)
+          cc[k][j] += w[i] * (rgb[3 * i + k] / 255.0 - cm[k]) * (rgb[3 * i + j] / 255.0 - cm[j]);
+    }
+    for (int k = 0; k < 3; ++k) {
+      g->mu[m][k] = cm[k];
+      for (int j = 0; j < 3; ++j) g->cov[m][k][j] = cc[k][j] / W[m] + (k == j ? 1e-4 : 0.0);
+    }
   }
+  free(lab);
 }
 
 double orc_gmm_loglik(const uint8_t* rgb, const double* w, int n, const orc_gmm* g) {
@@ -583,8 +662,8 @@ void orc_gmm_em_step(const uint8_t* rgb, const double* w, int n, orc_gmm* g) {
   free(r);
 }
 
-void orc_gmm_fit(const uint8_t* rgb, const double* w, int n, int M, int iters, orc_gmm* g) {
-  orc_gmm_init(rgb, w, n, M, g);
+void orc_gmm_fit(const uint8_t* rgb, const double* w, int n, int M, int km_iters, int iters, orc_gmm* g) {
+  orc_gmm_init(rgb, w, n, M, km_iters, g);
   for (int it = 0; it < iters; ++it) orc_gmm_em_step(rgb, w, n, g);
 }
 
@@ -619,8 +698,14 @@ int32_t orc_ncap_value(const orc_params* P, int dsum, int diagonal) {
  * sentence is the reverse of its capacity equations).  Both t-links are
  * shifted by min(D(0), D(1)), a per-pixel constant that leaves every minimum
  * cut unchanged, then quantised. */
-void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const double* prior,
-               int32_t* cs, int32_t* ct, int32_t* ncap, double* D0, double* D1) {
+/* mix (nullable): the two labels' colour mixtures carried between frames.  With
+ * from_mix the EM of a label starts from mix[a] (Sec. 2 / Sec. 6: feature
+ * likelihoods updated to reflect the dominant feature components of the previous
+ * segmentation; reading: the previous frame's fitted mixture is the current
+ * frame's EM start, and the k-means start runs only on a video's first frame);
+ * the fitted mixtures are written back to mix. */
+void orc_terms_ex(const orc_params* P, int H, int W, const uint8_t* rgb, const double* prior,
+                  int32_t* cs, int32_t* ct, int32_t* ncap, double* D0, double* D1, orc_gmm* mix, int from_mix) {
   int n = H * W;
   double mu[2][3], cov[2][3][3], icov[2][3][3], lconst[2];
   int degenerate = orc_colour_models(prior, rgb, n, mu, cov);
@@ -630,7 +715,13 @@ void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const doub
     for (int a = 0; a < 2; ++a) {
       if (degenerate & (1 << a)) continue;
       for (int i = 0; i < n; ++i) w[i] = a ? prior[i] : 1.0 - prior[i];
-      orc_gmm_fit(rgb, w, n, P->gmm_components, P->em_iters, &gm[a]);
+      if (from_mix && mix && mix[a].M == P->gmm_components) {
+        gm[a] = mix[a];
+        for (int it = 0; it < P->em_iters; ++it) orc_gmm_em_step(rgb, w, n, &gm[a]);
+      } else {
+        orc_gmm_fit(rgb, w, n, P->gmm_components, P->kmeans_iters, P->em_iters, &gm[a]);
+      }
+      if (mix) mix[a] = gm[a];
     }
     free(w);
   }
@@ -680,6 +771,11 @@ void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const doub
         }
         ncap[(size_t)k * n + y * W + x] = c;
       }
+}
+
+void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const double* prior,
+               int32_t* cs, int32_t* ct, int32_t* ncap, double* D0, double* D1) {
+  orc_terms_ex(P, H, W, rgb, prior, cs, ct, ncap, D0, D1, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1056,7 +1152,9 @@ int64_t orc_push_frame(const orc_params* P, int H, int W, orc_state* st, const u
   int32_t* cs = (int32_t*)malloc(sizeof(int32_t) * n);
   int32_t* ct = (int32_t*)malloc(sizeof(int32_t) * n);
   int32_t* nc = (int32_t*)malloc(sizeof(int32_t) * (size_t)n * nk);
-  orc_terms(P, H, W, rgb, prior, cs, ct, nc, NULL, NULL);
+  orc_terms_ex(P, H, W, rgb, prior, cs, ct, nc, NULL, NULL, st->gmm,
+               P->gmm_update && st->gmm_valid && st->t > 0);
+  if (P->gmm_components > 1) st->gmm_valid = 1;
   int64_t cut = orc_maxflow_bk(H, W, P->neighbourhood, cs, ct, nc, mask);
   memcpy(st->prev_mask, mask, n);
   st->P = Pt;

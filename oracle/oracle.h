@@ -45,6 +45,8 @@ typedef struct orc_params {
   int neighbourhood;   /* 4 or 8 */
   int gmm_components;  /* Gaussians per label in the colour likelihood: 1 or 3 */
   int em_iters;        /* EM iterations when gmm_components > 1 */
+  int kmeans_iters;    /* Lloyd iterations of the k-means start of the EM */
+  int gmm_update;      /* 1: a frame's EM starts from the previous frame's mixtures */
 } orc_params;
 
 /* A prior-weighted Gaussian mixture over C = RGB/255 (one label). */
@@ -93,10 +95,12 @@ int orc_colour_models(const double* prior, const uint8_t* rgb, int n, double mu[
                       double cov[2][3][3]);
 void orc_terms(const orc_params* P, int H, int W, const uint8_t* rgb, const double* prior,
                int32_t* cs, int32_t* ct, int32_t* ncap, double* D0, double* D1);
-void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, orc_gmm* g);
+void orc_gmm_init(const uint8_t* rgb, const double* w, int n, int M, int km_iters, orc_gmm* g);
 double orc_gmm_loglik(const uint8_t* rgb, const double* w, int n, const orc_gmm* g);
 void orc_gmm_em_step(const uint8_t* rgb, const double* w, int n, orc_gmm* g);
-void orc_gmm_fit(const uint8_t* rgb, const double* w, int n, int M, int iters, orc_gmm* g);
+void orc_gmm_fit(const uint8_t* rgb, const double* w, int n, int M, int km_iters, int iters, orc_gmm* g);
+void orc_terms_ex(const orc_params* P, int H, int W, const uint8_t* rgb, const double* prior,
+                  int32_t* cs, int32_t* ct, int32_t* ncap, double* D0, double* D1, orc_gmm* mix, int from_mix);
 double orc_gmm_logpdf(const orc_gmm* g, const double c[3]);
 int32_t orc_ncap_value(const orc_params* P, int dsum, int diagonal);
 
@@ -124,6 +128,8 @@ typedef struct orc_state {
   int t;               /* frame index */
   double P;            /* sigma^2_xi1(t-1) */
   uint8_t* prev_mask;  /* H*W, caller-owned */
+  int gmm_valid;       /* gmm holds the previous frame's colour mixtures */
+  orc_gmm gmm[2];      /* labels 0 and 1 */
 } orc_state;
 
 int64_t orc_push_frame(const orc_params* P, int H, int W, orc_state* st, const uint8_t* rgb,

@@ -61,8 +61,6 @@ struct MomFinArgs {
   KalmanDev* kal;  // nullable: advance the variance recursion
   double a, b;
   const SegIO* io;  // rgb / prior == nullptr: take them from here
-  GmmDev* gmm;      // nullable: initialise the M-component mixtures from the M = 1 fit
-  int M;
 };
 
 __device__ __forceinline__ void mom1_add_rgb(float p, int r8, int g8, int b8, float* s) {
@@ -420,11 +418,7 @@ __device__ double chol_inv(double c00, double c10, double c11, double c20, doubl
 }
 
 // Covariance + 1e-4 I, Cholesky factor L, L^-1 and 1/2 log det + 3/2 log 2 pi.
-// With gmm: also the EM initialisation of the M-component mixtures (reading of
-// the paper's k-means start): means on the grey axis through the weighted mean
-// at (m - (M-1)/2) * 1.5 sigma_g, sigma_g^2 = g^T Sigma g, g = (1,1,1)/sqrt3;
-// every covariance = Sigma; every weight = 1/M.
-__device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M, int lab) {
+__device__ void finalize_cov(const double* tot, GaussDev* g, int lab) {
   if (g->degenerate & (1 << lab)) {  // no pixel carries weight: psi_1 = 0 for this label
     for (int k = 0; k < 6; ++k) g->linv[lab][k] = 0.f;
     g->lconst[lab] = 0.f;
@@ -436,20 +430,6 @@ __device__ void finalize_cov(const double* tot, GaussDev* g, GmmDev* gmm, int M,
   const double c20 = m[3] * rsw, c21 = m[4] * rsw, c22 = m[5] * rsw + 1e-4;
   const double ld = chol_inv(c00, c10, c11, c20, c21, c22, g->linv[lab]);
   g->lconst[lab] = (float)(0.5 * ld + 1.5 * LOG_2PI);
-  if (gmm) {
-    GmmDev& q = gmm[lab];
-    // sigma_g / sqrt 3 = sqrt(sg2 / 3), sg2 = g^T Sigma g (> 0: Sigma carries 1e-4 I)
-    const double v = (c00 + c11 + c22 + 2.0 * (c10 + c20 + c21)) * (1.0 / 9.0);
-    const double sd = v * nr_rsqrt(v);
-    const float lw = (float)(log_f(1.0 / M) - 0.5 * ld - 1.5 * LOG_2PI);
-    for (int k = 0; k < M; ++k) {
-      const double off = (k - (M - 1) / 2.0) * 1.5 * sd;
-      for (int j = 0; j < 3; ++j) q.mu[k][j] = (float)(g->mu[lab][j] + off);
-      for (int j = 0; j < 6; ++j) q.linv[k][j] = g->linv[lab][j];
-      q.logdet[k] = ld;
-      q.lc[k] = lw;
-    }
-  }
 }
 
 __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
@@ -494,7 +474,7 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
     __shared__ double tot[12];
     reduce_parts<12>(f.part, gridDim.x, tot);
     if (threadIdx.x < 2)  // one thread per label
-      finalize_cov(tot, f.gauss, f.gmm ? f.gmm + 2 * fb : nullptr, f.M, threadIdx.x);
+      finalize_cov(tot, f.gauss, threadIdx.x);
   }
 }
 
@@ -594,6 +574,152 @@ __global__ void __launch_bounds__(256) k_em_step(EMArgs a) {
           g->logdet[m] = ld;
         }
         g->lc[m] = (float)(log_f(pim) - 0.5 * ld - 1.5 * LOG_2PI);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ k-means start of the EM
+// Sec. 7.3: the EM starts from a k-means partition of the label's prior-weighted
+// colours.  Reading (the paper's CPU k-means is not specified): seeds by
+// k-means++ taken in expectation -- c_1 = the weighted mean (the M = 1 fit's),
+// c_m = the mean weighted by w D^2, D the distance to the nearest earlier seed;
+// then Lloyd iterations (nearest center, lowest index on equal distances; a
+// center whose cluster carries >= 1e-6 of the weight moves to its weighted
+// mean); the mixture is the final partition's weight shares, means and
+// covariances (+ 1e-4 I), a (nearly) empty cluster keeping its center and the
+// label's covariance.  Sec. 2 / Sec. 6 likelihood update: with gmm_update a
+// label that already holds a fitted mixture (the previous frame's) skips these
+// passes and its EM continues from that mixture; valid[frame][label] records
+// it (cleared when a stream starts a new video).  One pass per launch, grid
+// (blocks, 2 frames) like the EM; partial sums through the EM's buffers.
+enum { KM_SEED = 0, KM_LLOYD = 1, KM_MIX = 2 };
+struct KMArgs {
+  const uint8_t* rgb;
+  const float* prior;
+  int N;
+  GmmDev* gmm;  // [frame][label]: centers in mu during the passes, then the mixture
+  const GaussDev* gauss;
+  float* part;
+  int part_stride;
+  unsigned* counter;
+  int* valid;  // [frame][label] (nullable: the stateless stage entry point)
+  int update;
+  int mseed;   // KM_SEED: seeds already placed (the pass places seed mseed)
+  const SegIO* io;
+};
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(256) k_km_pass(KMArgs a) {
+  constexpr int NV = MODE == KM_SEED ? 4 : MODE == KM_LLOYD ? 4 * M : 10 * M;
+  seg_pdl_enter();
+  const int lab = blockIdx.y & 1, fb = blockIdx.y >> 1;
+  const GaussDev* gd = a.gauss + fb;
+  if (gd->degenerate & (1 << lab)) return;  // no weight: no mixture to start
+  if (a.update && a.valid && a.valid[2 * fb + lab]) return;  // EM continues from the previous frame's mixture
+  const uint8_t* rgb = (a.rgb ? a.rgb : a.io->rgb) + (size_t)fb * 3 * a.N;
+  const float* prior = (a.prior ? a.prior : a.io->prior) + (size_t)fb * a.N;
+  GmmDev* g = a.gmm + 2 * fb + lab;
+  float ctr[M][3];
+  const int nc = MODE == KM_SEED ? a.mseed : M;
+  for (int m = 0; m < M; ++m)
+    for (int k = 0; k < 3; ++k) ctr[m][k] = (m == 0 && MODE == KM_SEED) ? gd->muf[lab][k] : g->mu[m][k];
+  float s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+    const float p = prior[i];
+    const float w = lab ? p : 1.f - p;
+    const float c[3] = {rgb[3 * (size_t)i] / 255.f, rgb[3 * (size_t)i + 1] / 255.f, rgb[3 * (size_t)i + 2] / 255.f};
+    float bd = 3.0e38f;
+    int best = 0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      if (m >= nc) break;
+      const float d0 = c[0] - ctr[m][0], d1 = c[1] - ctr[m][1], d2 = c[2] - ctr[m][2];
+      const float d = d0 * d0 + d1 * d1 + d2 * d2;
+      if (d < bd) {
+        bd = d;
+        best = m;
+      }
+    }
+    if (MODE == KM_SEED) {
+      const float wd = w * bd;
+      s[0] += wd;
+      s[1] += wd * c[0];
+      s[2] += wd * c[1];
+      s[3] += wd * c[2];
+    } else if (MODE == KM_LLOYD) {
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+        if (m == best) {
+          s[4 * m] += w;
+          s[4 * m + 1] += w * c[0];
+          s[4 * m + 2] += w * c[1];
+          s[4 * m + 3] += w * c[2];
+        }
+    } else {
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+        if (m == best) {  // moments about the center (no large cancellation)
+          const float d0 = c[0] - ctr[m][0], d1 = c[1] - ctr[m][1], d2 = c[2] - ctr[m][2];
+          float* t = s + 10 * m;
+          t[0] += w;
+          t[1] += w * d0;
+          t[2] += w * d1;
+          t[3] += w * d2;
+          t[4] += w * d0 * d0;
+          t[5] += w * d1 * d0;
+          t[6] += w * d1 * d1;
+          t[7] += w * d2 * d0;
+          t[8] += w * d2 * d1;
+          t[9] += w * d2 * d2;
+        }
+    }
+  }
+  float* part = a.part + (size_t)(2 * fb + lab) * a.part_stride;
+  if (block_partial_last<NV>(s, part, a.counter + 2 * fb + lab, blockIdx.x, gridDim.x)) {
+    __shared__ double tot[NV];
+    reduce_parts<NV>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      if (MODE == KM_SEED) {
+        if (a.mseed == 1)
+          for (int k = 0; k < 3; ++k) g->mu[0][k] = gd->muf[lab][k];
+        const bool ok = tot[0] > 0.0;
+        const double r = ok ? nr_rcp(tot[0]) : 0.0;
+        for (int k = 0; k < 3; ++k) g->mu[a.mseed][k] = ok ? (float)(tot[1 + k] * r) : gd->muf[lab][k];
+      } else if (MODE == KM_LLOYD) {
+        double sw = 0.0;
+        for (int m = 0; m < M; ++m) sw += tot[4 * m];
+        for (int m = 0; m < M; ++m)
+          if (tot[4 * m] >= 1e-6 * sw) {
+            const double r = nr_rcp(tot[4 * m]);
+            for (int k = 0; k < 3; ++k) g->mu[m][k] = (float)(tot[4 * m + 1 + k] * r);
+          }
+      } else {
+        double sw = 0.0;
+        for (int m = 0; m < M; ++m) sw += tot[10 * m];
+        const double rsw = nr_rcp(sw);
+        for (int m = 0; m < M; ++m) {
+          const double* t = tot + 10 * m;
+          const double pim = t[0] * rsw;
+          double ld;
+          if (t[0] >= 1e-6 * sw) {
+            const double rn = nr_rcp(t[0]);
+            const double dx = t[1] * rn, dy = t[2] * rn, dz = t[3] * rn;
+            g->mu[m][0] = (float)((double)ctr[m][0] + dx);
+            g->mu[m][1] = (float)((double)ctr[m][1] + dy);
+            g->mu[m][2] = (float)((double)ctr[m][2] + dz);
+            ld = chol_inv(t[4] * rn - dx * dx + 1e-4, t[5] * rn - dy * dx, t[6] * rn - dy * dy + 1e-4,
+                          t[7] * rn - dz * dx, t[8] * rn - dz * dy, t[9] * rn - dz * dz + 1e-4, g->linv[m]);
+          } else {  // (nearly) empty: its center and the label's covariance
+            for (int k = 0; k < 6; ++k) g->linv[m][k] = gd->linv[lab][k];
+            ld = 2.0 * ((double)gd->lconst[lab] - 1.5 * LOG_2PI);
+          }
+          g->logdet[m] = ld;
+          g->lc[m] = (float)(log_f(pim) - 0.5 * ld - 1.5 * LOG_2PI);
+        }
+        if (a.valid) a.valid[2 * fb + lab] = 1;
       }
     }
   }
@@ -923,8 +1049,6 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   fa.b = p.sigma2 * p.sigma2;
   fa.io = c->io_mode ? c->io : nullptr;
   const int M = p.gmm_components;
-  fa.gmm = M > 1 ? c->gmm : nullptr;
-  fa.M = M;
   if (first_pass) SEG_CUDA_TRY(seg_launch(k_mom1, dim3(c->mom_blocks, c->B), 256, 0, st, rgb, prior, N, fa));
   SEG_CUDA_TRY(seg_launch(k_mom2, dim3(c->mom_blocks, c->B), 256, 0, st, rgb, prior, N, fa));
   if (M > 1) {  // Sec. 4 / Sec. 7.3: EM of the M-component colour mixtures
@@ -939,6 +1063,38 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     ea.part_stride = pt_em_part_doubles(c->H, c->W);
     ea.counter = c->em_counter;
     ea.io = c->io_mode ? c->io : nullptr;
+    KMArgs ka;
+    ka.rgb = rgb;
+    ka.prior = prior;
+    ka.N = N;
+    ka.gmm = c->gmm;
+    ka.gauss = c->gauss;
+    ka.part = (float*)c->em_part;
+    ka.part_stride = pt_em_part_doubles(c->H, c->W);
+    ka.counter = c->em_counter;
+    // the stage entry point (first_pass) is stateless: always the k-means start, and the
+    // stream's mixtures are not marked as the next frame's start
+    ka.valid = first_pass ? nullptr : c->gmm_valid;
+    ka.update = first_pass ? 0 : p.gmm_update;
+    ka.io = ea.io;
+    const dim3 gk(c->mom_blocks, 2 * c->B);
+    for (int m = 1; m < M; ++m) {
+      ka.mseed = m;
+      if (M == 2)
+        SEG_CUDA_TRY(seg_launch(k_km_pass<2, KM_SEED>, gk, 256, 0, st, ka));
+      else
+        SEG_CUDA_TRY(seg_launch(k_km_pass<3, KM_SEED>, gk, 256, 0, st, ka));
+    }
+    for (int it = 0; it < p.kmeans_iters; ++it) {
+      if (M == 2)
+        SEG_CUDA_TRY(seg_launch(k_km_pass<2, KM_LLOYD>, gk, 256, 0, st, ka));
+      else
+        SEG_CUDA_TRY(seg_launch(k_km_pass<3, KM_LLOYD>, gk, 256, 0, st, ka));
+    }
+    if (M == 2)
+      SEG_CUDA_TRY(seg_launch(k_km_pass<2, KM_MIX>, gk, 256, 0, st, ka));
+    else
+      SEG_CUDA_TRY(seg_launch(k_km_pass<3, KM_MIX>, gk, 256, 0, st, ka));
     for (int it = 0; it < p.em_iters; ++it) {
       if (M == 2)
         SEG_CUDA_TRY(seg_launch(k_em_step<2>, dim3(c->mom_blocks, 2 * c->B), 256, 0, st, ea));

@@ -55,6 +55,8 @@ extern "C" int seg_default_params(seg_params* p) {
   p->em_iters = 5;
   p->warm_start = 1;
   p->barrier_timeout_us = 4000000;
+  p->kmeans_iters = 3;
+  p->gmm_update = 1;
   return SEG_OK;
 }
 
@@ -88,6 +90,7 @@ int seg_check_params(const seg_params* p, int H, int W) {
   if (!(p->eps > 0) || !(p->eps < 0.5f)) return SEG_EINVAL;
   if (p->max_cycles < 1 || p->global_relabel_every < 1 || p->local_iters < 1) return SEG_EINVAL;
   if (p->barrier_timeout_us < 1 || p->barrier_timeout_us > 60000000) return SEG_EINVAL;
+  if (p->kmeans_iters < 0 || p->kmeans_iters > 100 || (p->gmm_update != 0 && p->gmm_update != 1)) return SEG_EINVAL;
   if (p->gmm_components < 1 || p->gmm_components > SEG_MAX_GMM || p->em_iters < 0 || p->em_iters > 100)
     return SEG_EINVAL;
   return SEG_OK;
@@ -96,7 +99,7 @@ int seg_check_params(const seg_params* p, int H, int W) {
 // Byte offsets of every buffer in a context's single device arena.
 struct ArenaLayout {
   size_t kal, gauss, mom, lut, cnt, prev, cs, ct, ncap, sal, prior, mask, cut, rgb, status, io, flow, warm, mf;
-  size_t gmm, empart, emcnt;
+  size_t gmm, empart, emcnt, gvalid;
   size_t total;
 };
 
@@ -134,6 +137,7 @@ static int arena_layout(SalWS& sal, int B, int H, int W, const seg_params& p, Ar
   L.gmm = take((size_t)B * 2 * sizeof(GmmDev));
   L.empart = take((size_t)B * 2 * sizeof(double) * pt_em_part_doubles(H, W));
   L.emcnt = take((size_t)B * 2 * sizeof(unsigned));
+  L.gvalid = take((size_t)B * 2 * sizeof(int));
   L.total = off;
   return SEG_OK;
 }
@@ -213,6 +217,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   c->gmm = (GmmDev*)(base + L.gmm);
   c->em_part = (double*)(base + L.empart);
   c->em_counter = (unsigned*)(base + L.emcnt);
+  c->gmm_valid = (int*)(base + L.gvalid);
   c->warm = (unsigned char*)(base + o_warm);
   mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
@@ -231,6 +236,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   ok = ok && cudaMemset(c->mom_counter, 0, B * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMemset(c->warm, 0, B) == cudaSuccess;
   ok = ok && cudaMemset(c->em_counter, 0, (size_t)B * 2 * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMemset(c->gmm_valid, 0, (size_t)B * 2 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
   ok = ok && mf_grid_size(B * H, W, &c->mf_grid) == SEG_OK;
   if (!ok) {
@@ -279,6 +285,7 @@ extern "C" int seg_reset(seg_ctx* c) {
   SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, c->B * sizeof(KalmanDev), c->stream));
   SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask, 0, (size_t)c->B * c->N, c->stream));
   SEG_CUDA_TRY(cudaMemsetAsync(c->warm, 0, c->B, c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->gmm_valid, 0, (size_t)c->B * 2 * sizeof(int), c->stream));
   return SEG_OK;
 }
 
@@ -287,6 +294,7 @@ extern "C" int seg_reset_stream(seg_ctx* c, int b) {
   SEG_CUDA_TRY(cudaMemsetAsync(c->kal + b, 0, sizeof(KalmanDev), c->stream));
   SEG_CUDA_TRY(cudaMemsetAsync(c->prev_mask + (size_t)b * c->N, 0, c->N, c->stream));
   SEG_CUDA_TRY(cudaMemsetAsync(c->warm + b, 0, 1, c->stream));
+  SEG_CUDA_TRY(cudaMemsetAsync(c->gmm_valid + 2 * b, 0, 2 * sizeof(int), c->stream));
   return SEG_OK;
 }
 
@@ -779,6 +787,8 @@ extern "C" int seg_set_state(seg_ctx* c, const void* buf, size_t n) {
   }
   SEG_CUDA_TRY(cudaMemcpy(c->prev_mask, b + 16 + 16 * (size_t)c->B, (size_t)c->B * c->N, cudaMemcpyHostToDevice));
   SEG_CUDA_TRY(cudaMemset(c->warm, 0, c->B));  // flows are not part of the state: next cut starts cold
+  // nor are the colour mixtures: the next frame's EM starts from the k-means start
+  SEG_CUDA_TRY(cudaMemset(c->gmm_valid, 0, (size_t)c->B * 2 * sizeof(int)));
   return SEG_OK;
 }
 

@@ -382,6 +382,7 @@ struct seg_ctx {
   double* mom_part;
   unsigned* mom_counter;  // last-CTA counter of the moment passes (returns to 0)
   GmmDev* gmm;            // [B][2] colour mixtures (gmm_components > 1)
+  int* gmm_valid;         // [B][2] the mixture is a fitted one (the next frame's EM may start from it)
   double* em_part;        // [B][2][em partial doubles]
   unsigned* em_counter;   // [B][2]
   int mom_blocks;

@@ -44,7 +44,8 @@ class seg_params(C.Structure):
         ("sigma_I", C.c_double), ("cap_scale", C.c_double), ("neighbourhood", C.c_int32),
         ("max_cycles", C.c_int32), ("global_relabel_every", C.c_int32), ("local_iters", C.c_int32),
         ("use_graph", C.c_int32), ("gmm_components", C.c_int32), ("em_iters", C.c_int32),
-        ("warm_start", C.c_int32), ("barrier_timeout_us", C.c_int32),
+        ("warm_start", C.c_int32), ("barrier_timeout_us", C.c_int32), ("kmeans_iters", C.c_int32),
+        ("gmm_update", C.c_int32),
     ]
 
 

@@ -54,10 +54,13 @@ def _run_batch(S, params, clips):
     return outs
 
 
-@pytest.mark.parametrize("cfg_name,B", [("small", 3), ("small", 1), ("vga", 2)])
+@pytest.mark.parametrize("cfg_name,B", [("small", 3), ("small", 1), ("vga", 2), ("small_gmm3", 2)])
 def test_batch_streams_equal_single_streams(S, cfg_name, B):
+    """small_gmm3: the M = 3 colour mixtures, each stream carrying its own from frame to frame."""
     if cfg_name == "small":
         cfg, clips = O.CONFIG_SMALL, _clips_small(B, 4)
+    elif cfg_name == "small_gmm3":
+        cfg, clips = dict(O.CONFIG_SMALL, gmm_components=3, em_iters=3), _clips_small(B, 4)
     else:
         cfg = O.CONFIG_VGA
         allf = np.stack([f for f, _ in synth.clip_vga_frames(110)])

@@ -298,6 +298,38 @@ def test_end_to_end_small_clip_gmm3(S):
     assert min(agree) >= 0.999, agree
 
 
+def test_end_to_end_vga_clip_gmm3(S):
+    """The paper's M = 3 colour mixtures at 640x480 (Sec. 8.1): the k-means start on the first
+    frame, then each frame's EM from the previous frame's mixtures (both sides)."""
+    frames = np.stack([f for f, _ in synth.clip_vga_frames(4)])
+    agree, _ = _run_clip(S, frames, dict(O.CONFIG_VGA, gmm_components=3, em_iters=5))
+    assert min(agree) >= 0.999, agree
+
+
+def test_gmm_update_and_reset(S):
+    """With gmm_update a frame's EM starts from the previous frame's mixtures (so frame 1
+    differs from a fresh start on the same prior); a reset returns to the k-means start, so
+    the first frame of the new video equals a fresh context's, bit for bit."""
+    cfg = dict(O.CONFIG_SMALL, gmm_components=3, em_iters=2)
+    frames, _ = synth.clip_small(3, seed=synth.SEED_BASE + 21)
+    H, W = frames.shape[1:3]
+    a = S.Segmenter(H, W, seg_params(S, cfg))
+    outs_a = [tuple(t.clone() for t in a.push_frame(dev(f))) for f in frames[:2]]
+    a.sync()
+    a.reset()
+    again = a.push_frame(dev(frames[0]))
+    fresh = S.Segmenter(H, W, seg_params(S, cfg))
+    f0 = fresh.push_frame(dev(frames[0]))
+    a.sync()
+    fresh.sync()
+    for x, y in zip(again, f0):
+        assert torch.equal(x, y)
+    for x, y in zip(outs_a[0], f0):
+        assert torch.equal(x, y)
+    a.close()
+    fresh.close()
+
+
 def test_end_to_end_vga_clip(S):
     frames = np.stack([f for f, _ in synth.clip_vga_frames(12)])
     agree, _ = _run_clip(S, frames, O.CONFIG_VGA, cut_on_oracle_caps=True)

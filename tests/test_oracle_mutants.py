@@ -120,6 +120,14 @@ MUTANTS = [
      "memcpy(tmp, C[k], sizeof(double) * nS);", "conspicuity N(.) dropped"),
     ("oracle.c", "for (int l = c; l < sS; ++l) {", "for (int l = c + 1; l < sS; ++l) {",
      "one REDUCE too few to sigma_S"),
+    ("oracle.c", "      s += w[i] * d2;\n      for (int k = 0; k < 3; ++k) acc[k] += w[i] * d2 * c[k];",
+     "      s += w[i] * sqrt(d2);\n      for (int k = 0; k < 3; ++k) acc[k] += w[i] * sqrt(d2) * c[k];",
+     "k-means seeds weighted by D instead of D^2"),
+    ("oracle.c", "        for (int k = 0; k < 3; ++k) ctr[m][k] = S[m][k] / W[m];\n  }", "        ;\n  }",
+     "Lloyd centers never move"),
+    ("oracle.c", "    g->pi[m] = W[m] / sw;", "    g->pi[m] = 1.0 / M;", "k-means start with uniform weights"),
+    ("oracle.c", "P->gmm_update && st->gmm_valid && st->t > 0);", "0);", "previous frame's mixtures ignored"),
+    ("oracle.c", "      if (mix) mix[a] = gm[a];", "", "fitted mixtures not carried to the next frame"),
     ("oracle_grad.c", "+= KB[j + 2] * KB[i + 2] * g_out[y * w2 + x];", "+= KB[j + 2] * g_out[y * w2 + x];",
      "REDUCE adjoint drops a tap factor"),
     ("oracle_grad.c", "double dm = sgv * (-2.0 * (1 - st->mbar)) / (st->nt - 1);",

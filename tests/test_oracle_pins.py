@@ -655,6 +655,36 @@ def test_frame_sequence_carries_mask_and_variance(cfg):
         prev = mask.copy()
 
 
+def test_frame_sequence_updates_the_colour_mixtures():
+    # Sec. 2 / Sec. 6 likelihood update (reading: a frame's EM starts from the previous
+    # frame's fitted mixtures; the k-means start runs on the first frame only), composed
+    # from separately pinned parts; with gmm_update = 0 every frame starts afresh
+    cfg = dict(O.CONFIG_SMALL, gmm_components=3, em_iters=3)
+    frames, _ = synth.clip_small(3, seed=synth.SEED_BASE + 11)
+    H, W = frames.shape[1:3]
+    for update in (1, 0):
+        sg = O.Segmenter(H, W, cfg, gmm_update=update)
+        P, prev, mix = 0.0, None, None
+        for t in range(3):
+            sal, pr, mask, cut = sg.push(frames[t])
+            P, wf = O.kalman_step(t, P)
+            _, pr_ref = O.prior(sal, prev if t else None, wf, cfg)
+            np.testing.assert_array_equal(pr, pr_ref)
+            cs, ct, nc, fitted = O.terms_from(frames[t], pr_ref, mix if update else None, cfg)
+            if t and update:  # the carried start really leads elsewhere than a fresh one
+                _, _, _, fresh = O.terms_from(frames[t], pr_ref, None, cfg)
+                d = max(abs(fresh[a].mu[m][k] - fitted[a].mu[m][k]) for a in range(2) for m in range(3)
+                        for k in range(3))
+                assert d > 1e-6
+            v, m = O.maxflow(cs, ct, nc)
+            assert cut == v
+            np.testing.assert_array_equal(mask, m)
+            for a in range(2):  # the mixtures the method carries are the ones composed here
+                assert [sg.st.gmm[a].pi[k] for k in range(3)] == [fitted[a].pi[k] for k in range(3)]
+                assert all(sg.st.gmm[a].mu[k][j] == fitted[a].mu[k][j] for k in range(3) for j in range(3))
+            prev, mix = mask.copy(), fitted
+
+
 def test_small_clip_regression_golden():
     import json
     import os
@@ -723,6 +753,81 @@ def test_em_components_are_the_weighted_cluster_gaussians():
         ref = np.cov(c[sel].T, aweights=w[sel], bias=True) + 1e-4 * np.eye(3)
         np.testing.assert_allclose(cov[m], ref, rtol=1e-6, atol=1e-12)
         assert pi[m] == pytest.approx(w[sel].sum() / w.sum(), rel=1e-9)
+
+
+def test_kmeans_start_seed_is_the_expected_kmeanspp_draw():
+    # Two point masses a = 0 (weight 0.6) and b = 1 (weight 0.4) on the red axis: the
+    # first seed is the weighted mean 0.4; a k-means++ draw picks a point with
+    # probability w D^2, so its expected position is (wa D_a^2 a + wb D_b^2 b) /
+    # (wa D_a^2 + wb D_b^2) = (wb a + wa b) / W = 0.6.  With no Lloyd iteration a light
+    # probe pixel joins the seed it is nearer to: below the midpoint 0.5 the first one
+    # (with a), above it the second (with b).
+    for probe, with_a in [(125, True), (130, False)]:
+        rgb = np.array([[0, 0, 0], [255, 0, 0], [probe, 0, 0]], np.uint8)
+        w = np.array([0.6, 0.4, 1e-6])
+        pi, mu, cov = O.gmm_init(rgb, w, M=2, km_iters=0)
+        ia = int(np.argmin(mu[:, 0]))
+        members_a = [0, 2] if with_a else [0]
+        c = rgb.astype(float) / 255.0
+        np.testing.assert_allclose(mu[ia], np.average(c[members_a], axis=0, weights=w[members_a]), atol=1e-15)
+        assert pi[ia] == pytest.approx(w[members_a].sum() / w.sum(), rel=1e-12)
+
+
+def test_kmeans_start_single_component_and_weight_scale():
+    rng = np.random.default_rng(41)
+    rgb = rng.integers(0, 256, (30, 40, 3)).astype(np.uint8)
+    w = rng.random((30, 40))
+    pi, mu, cov = O.gmm_init(rgb, w, M=1, km_iters=3)
+    mu1, cov1, _ = O.colour_models(w, rgb)
+    np.testing.assert_allclose(pi, [1.0])
+    np.testing.assert_allclose(mu[0], mu1[1], atol=1e-13)
+    np.testing.assert_allclose(cov[0], cov1[1], atol=1e-13)
+    a, b = O.gmm_init(rgb, w, M=3, km_iters=3), O.gmm_init(rgb, 2.5 * w, M=3, km_iters=3)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, rtol=1e-10, atol=1e-13)
+
+
+def test_kmeans_start_partitions_separated_clusters():
+    # three well-separated clusters of unequal weight: the seeds reach every cluster and
+    # a few Lloyd iterations settle on the true partition, so the start is already each
+    # cluster's weighted Gaussian (numpy, from the known membership) with the 1e-4 ridge
+    rgb, lab, _ = _clustered_rgb(42)
+    w = np.random.default_rng(43).uniform(0.2, 1.0, lab.size) * np.array([1.0, 0.3, 0.6])[lab]
+    pi, mu, cov = O.gmm_init(rgb, w, M=3, km_iters=3)
+    order = np.argsort(mu[:, 0])
+    c = rgb.astype(float) / 255.0
+    for m, k in zip(order, range(3)):
+        sel = lab == k
+        np.testing.assert_allclose(mu[m], np.average(c[sel], axis=0, weights=w[sel]), rtol=1e-12)
+        ref = np.cov(c[sel].T, aweights=w[sel], bias=True) + 1e-4 * np.eye(3)
+        np.testing.assert_allclose(cov[m], ref, rtol=1e-9, atol=1e-14)
+        assert pi[m] == pytest.approx(w[sel].sum() / w.sum(), rel=1e-12)
+
+
+def test_em_step_matches_its_definition_on_overlapping_clusters():
+    # one EM step from a given mixture, written from its definition: responsibilities by
+    # Bayes' rule from scipy's Gaussian densities, then each component's prior-weighted
+    # share, mean and covariance (numpy) plus the 1e-4 ridge.  Overlapping clusters keep
+    # the responsibilities fractional.
+    rng = np.random.default_rng(44)
+    centers = np.array([[90, 90, 90], [120, 110, 100], [150, 140, 120]], float)
+    lab = rng.integers(0, 3, 2000)
+    rgb = np.clip(np.rint(centers[lab] + rng.normal(0, 18, (2000, 3))), 0, 255).astype(np.uint8)
+    w = rng.uniform(0.1, 1.0, 2000)
+    pi0 = np.array([0.5, 0.3, 0.2])
+    mu0 = centers / 255.0 + 0.01
+    cov0 = np.stack([np.eye(3) * s for s in (0.004, 0.006, 0.005)])
+    pi, mu, cov = O.gmm_em_from(rgb, w, pi0, mu0, cov0, iters=1)
+    c = rgb.astype(float) / 255.0
+    dens = np.stack([pi0[m] * stats.multivariate_normal(mu0[m], cov0[m]).pdf(c) for m in range(3)], 1)
+    r = dens / dens.sum(1, keepdims=True)
+    assert 0.05 < r.max(1).mean() < 0.95  # fractional responsibilities
+    for m in range(3):
+        wr = w * r[:, m]
+        assert pi[m] == pytest.approx(wr.sum() / w.sum(), rel=1e-10)
+        np.testing.assert_allclose(mu[m], np.average(c, axis=0, weights=wr), rtol=1e-10)
+        ref = np.cov(c.T, aweights=wr, bias=True) + 1e-4 * np.eye(3)
+        np.testing.assert_allclose(cov[m], ref, rtol=1e-8, atol=1e-14)
 
 
 def test_gmm_logpdf_and_terms_match_scipy():
