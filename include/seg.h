@@ -115,6 +115,19 @@ int seg_create(void* stream, int H, int W, const seg_params* p, seg_ctx** out);
  * Errors as seg_create, plus SEG_EINVAL for B < 1 or B*H*W > 2^26. */
 int seg_create_batch(void* stream, int B, int H, int W, const seg_params* p, seg_ctx** out);
 
+/* Marks slot b of a batch context as holding a stream (on = 1, the state at
+ * creation) or empty (on = 0).  The per-frame kernels skip an empty slot's
+ * frame: no kernel reads or writes its rows (the stacked cut treats them as
+ * outside the grid), its outputs are then undefined, and the slot's state
+ * (previous mask, Kalman variance, warm-start flows, colour mixtures) keeps its
+ * values, so a stream switched off and on again without seg_reset_stream
+ * continues where it stopped.  Enqueued on the context's stream, so it
+ * applies from the next seg_push_frame on, also inside captured graphs.  No
+ * paper counterpart: continuous batching of many streams.  A single-stream
+ * context always runs its frame.  Errors: SEG_EINVAL (ctx NULL, b out of
+ * range, on not 0 or 1), SEG_ECUDA. */
+int seg_set_stream_active(seg_ctx* ctx, int b, int on);
+
 /* Device bytes seg_create_batch(B, H, W, p) would allocate for its workspace
  * (for admission control by HBM footprint).  Errors as seg_create_batch. */
 int seg_workspace_bytes(int B, int H, int W, const seg_params* p, size_t* bytes);

@@ -27,6 +27,11 @@
 //     itself a minimum cut, so the mask is unique.  The cut value is the flow
 //     that reached t.
 //
+// Empty slots of a batch (a.on[fb] == 0) are left out: their rows are treated
+// like nodes outside the grid (never read or written), tiles lying wholly in them
+// are skipped, and the slot's mask state and warm-start flows keep their values.
+// No arc joins two frames, so the other frames' cuts are unchanged.
+//
 // Every grid barrier waits with a time limit; on expiry the kernel records
 // SEG_ETIMEOUT and every CTA returns.  A cycle cap records SEG_ENOTCONVERGED.
 #include <string.h>
@@ -37,6 +42,7 @@
 #define MF_HY (MF_TH + 2)
 #define MF_HN (MF_HX * MF_HY)
 #define MF_ROUND_CAP (1 << 20)  // fixpoint rounds per cut; uniform across CTAs
+#define MF_ON_CACHE 512         // frames whose run flags each CTA keeps in shared memory
 
 // Directions E W S N SE NW SW NE; the opposite of d is d ^ 1.  The kernel is
 // instantiated for 4 and 8 neighbours so every direction loop unrolls and these
@@ -60,6 +66,8 @@ struct MFShared {
   unsigned int setmask;  // colours of the tiles this CTA pushed into during a phase
   unsigned int dmask;    // dirty tiles of a round (mf_dirty_mask)
   long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
+  unsigned char onf[MF_ON_CACHE];  // the frames' run flags (a.on) when there are at most MF_ON_CACHE
+  int on_mode;  // 0: every frame runs, 1: some frame does not (flags in onf), 2: as 1 with the flags in a.on
 };
 
 __device__ __forceinline__ long long mf_now() { return seg_now(); }
@@ -77,6 +85,42 @@ __device__ __forceinline__ unsigned int mf_flag_read(const MFArgs& a, unsigned i
 // Block-uniform: start a flag round (clears the slot the NEXT round will use).
 __device__ __forceinline__ void mf_flag_begin(const MFArgs& a, unsigned int epoch) {
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(epoch + 1) % 3] = 0u;
+}
+
+// Whether frame f of the batch is run.
+__device__ __forceinline__ bool mf_frame_on(const MFArgs& a, const MFShared& s, int f) {
+  return s.on_mode == 0 || (s.on_mode == 1 ? s.onf[f] : a.on[f]) != 0;
+}
+
+// Whether row gy (of the stacked grid) belongs to a frame that is run.
+__device__ __forceinline__ bool mf_row_on(const MFArgs& a, const MFShared& s, int gy) {
+  return s.on_mode == 0 || mf_frame_on(a, s, gy / a.frame_h);
+}
+
+// Block-uniform, for the tile at rows Y0 .. Y0 + MF_TH - 1: bit hy set if halo
+// row Y0 - 1 + hy (hy < MF_HY) lies in the grid and in a frame that is run
+// (every bit set when every frame runs); *any = some row of the tile itself is
+// run (else the tile is skipped).
+__device__ __forceinline__ unsigned mf_tile_rows(const MFArgs& a, const MFShared& s, bool all_on, int Y0,
+                                                  bool* any) {
+  if (all_on) {
+    *any = true;
+    return ~0u;
+  }
+  const int g0 = max(Y0 - 1, 0);
+  int f = g0 / a.frame_h, next = (f + 1) * a.frame_h;
+  bool o = mf_frame_on(a, s, f);
+  unsigned m = 0u;
+  for (int gy = g0; gy <= min(Y0 + MF_TH, a.H - 1); ++gy) {
+    if (gy >= next) {  // (frame_h may be below MF_HY)
+      f = gy / a.frame_h;
+      next = (f + 1) * a.frame_h;
+      o = mf_frame_on(a, s, f);
+    }
+    if (o) m |= 1u << (gy - (Y0 - 1));
+  }
+  *any = ((m >> 1) & ((1u << MF_TH) - 1u)) != 0u;
+  return m;
 }
 
 // Block-uniform: bit i set if tile k0 + i * gridDim.x (i < 32, below ntiles) or
@@ -112,18 +156,18 @@ __device__ unsigned mf_dirty_mask(const MFArgs& a, MFShared& s, int k0, int sinc
 // formed here from rt and r (no separate pass and grid barrier), and every node
 // of the tile is written.
 template <int ND>
-__device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool first) {
+__device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
     int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
-    const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W && ((rows >> hy) & 1u);
     const int gg = gy * a.W + gx;
     s.h[i] = !in ? SEG_INF_H : first ? (a.rt[gg] > 0 ? 1 : SEG_INF_H) : a.h[gg];
   }
   const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
   const int gy = Y0 + ly, gx = X0 + lx;
-  const bool valid = gy < a.H && gx < a.W;
+  const bool valid = gy < a.H && gx < a.W && ((rows >> (ly + 1)) & 1u);
   const int g = gy * a.W + gx;
   const int hi = (ly + 1) * MF_HX + lx + 1;
   unsigned bits = 0u;
@@ -166,12 +210,12 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool f
 // residual bitmasks of the tile and its halo come from e and r (no separate pass
 // and grid barrier), and every node of the tile is written.
 template <int ND>
-__device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool first) {
+__device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
     int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
-    bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W && ((rows >> hy) & 1u);
     const int gg = gy * a.W + gx;
     if (!in) {
       s.z[i] = 0;
@@ -189,7 +233,7 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool
   }
   const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
   const int gy = Y0 + ly, gx = X0 + lx;
-  const bool valid = gy < a.H && gx < a.W;
+  const bool valid = gy < a.H && gx < a.W && ((rows >> (ly + 1)) & 1u);
   const int hi = (ly + 1) * MF_HX + lx + 1;
   __syncthreads();
   const unsigned char z0 = s.z[hi];
@@ -222,18 +266,18 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool
 // arcs (h(u) = h(v) + 1, t has height 0), then relabel every node still active
 // to 1 + min over residual arcs.  Returns whether any push or relabel happened.
 template <int ND>
-__device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, bool* still_active) {
+__device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, unsigned rows, bool* still_active) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   const int N = a.N, W = a.W;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
     int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
-    s.h[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < W) ? a.h[gy * W + gx] : SEG_INF_H;
+    s.h[i] = (gy >= 0 && gy < a.H && gx >= 0 && gx < W && ((rows >> hy) & 1u)) ? a.h[gy * W + gx] : SEG_INF_H;
   }
   const int tid = threadIdx.x;
   const int ly = tid / MF_TW, lx = tid - ly * MF_TW;
   const int gy = Y0 + ly, gx = X0 + lx;
-  const bool valid = gy < a.H && gx < W;
+  const bool valid = gy < a.H && gx < W && ((rows >> (ly + 1)) & 1u);
   const int g = gy * W + gx;
   const int hi = (ly + 1) * MF_HX + lx + 1;
   s.e[tid] = valid ? a.e[g] : 0;
@@ -321,13 +365,16 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, bool*
 // ---------------------------------------------------------------- the kernel
 __device__ __forceinline__ bool cap_ok(int c) { return c >= 0 && c <= (1 << 24); }
 
-template <int ND>
-__global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
-  __shared__ MFShared s;
+// The whole cut, for one CTA.  SKIP: some frame of the batch is not run (its
+// rows are left out); without it every test of the run flags folds away and the
+// code is that of a single frame.
+template <int ND, bool SKIP>
+__device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   const int N = a.N, W = a.W, H = a.H;
   const int nthr = gridDim.x * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int ntiles = a.ntx * a.nty;
+  constexpr bool all_on = !SKIP;
 
   const long long t_start = mf_now();
   // ---- 1. init.  Cold: all n-link flows 0.  Warm (a.flow and the frame's warm
@@ -342,8 +389,10 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     // is needed before the first one
     if (threadIdx.x == 0)
       for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        bool any;
+        mf_tile_rows(a, s, all_on, (k / a.ntx) * MF_TH, &any);
         a.tstamp[k] = -2;
-        a.tact[k] = 1;
+        a.tact[k] = any ? 1 : 0;
       }
     __syncthreads();
   } else {
@@ -357,12 +406,14 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
 #pragma unroll 2
   for (int u = gtid; u < N; u += nthr) {
     int y = u / W, x = u - y * W;
+    if (SKIP && !mf_row_on(a, s, y)) continue;
     int cs = in_cs[u], ct = in_ct[u];
     bool bad = !cap_ok(cs) || !cap_ok(ct);
+    const bool up = y > 0 && (!SKIP || mf_row_on(a, s, y - 1));  // (an empty slot's rows above: outside)
     const int cE = x + 1 < W ? ncap[u] : 0;
     const int cW = x > 0 ? ncap[u - 1] : 0;
     const int cS = y + 1 < H ? ncap[N + u] : 0;
-    const int cN = y > 0 ? ncap[N + u - W] : 0;
+    const int cN = up ? ncap[N + u - W] : 0;
     bad |= !cap_ok(cE) || !cap_ok(cS);
     const bool warm = a.flow != nullptr && a.warm[y / a.frame_h];
     auto clampf = [](int f, int c) { return f > c ? c : (f < -c ? -c : f); };
@@ -370,7 +421,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     const int fE = warm && x + 1 < W ? clampf(flow_in[u], cE) : 0;
     const int fW = warm && x > 0 ? clampf(flow_in[u - 1], cW) : 0;
     const int fS = warm && y + 1 < H ? clampf(flow_in[N + u], cS) : 0;
-    const int fN = warm && y > 0 ? clampf(flow_in[N + u - W], cN) : 0;
+    const int fN = warm && up ? clampf(flow_in[N + u - W], cN) : 0;
     int net_out = fE - fW + fS - fN;
     r_out[0 * N + u] = cE - fE;
     r_out[1 * N + u] = cW + fW;
@@ -378,14 +429,14 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     r_out[3 * N + u] = cN + fN;
     if (ND == 8) {
       const int cSE = (x + 1 < W && y + 1 < H) ? ncap[2 * N + u] : 0;
-      const int cNW = (x > 0 && y > 0) ? ncap[2 * N + u - W - 1] : 0;
+      const int cNW = (x > 0 && up) ? ncap[2 * N + u - W - 1] : 0;
       const int cSW = (x > 0 && y + 1 < H) ? ncap[3 * N + u] : 0;
-      const int cNE = (x + 1 < W && y > 0) ? ncap[3 * N + u - W + 1] : 0;
+      const int cNE = (x + 1 < W && up) ? ncap[3 * N + u - W + 1] : 0;
       bad |= !cap_ok(cSE) || !cap_ok(cSW);
       const int fSE = warm && x + 1 < W && y + 1 < H ? clampf(flow_in[2 * N + u], cSE) : 0;
-      const int fNW = warm && x > 0 && y > 0 ? clampf(flow_in[2 * N + u - W - 1], cNW) : 0;
+      const int fNW = warm && x > 0 && up ? clampf(flow_in[2 * N + u - W - 1], cNW) : 0;
       const int fSW = warm && x > 0 && y + 1 < H ? clampf(flow_in[3 * N + u], cSW) : 0;
-      const int fNE = warm && x + 1 < W && y > 0 ? clampf(flow_in[3 * N + u - W + 1], cNE) : 0;
+      const int fNE = warm && x + 1 < W && up ? clampf(flow_in[3 * N + u - W + 1], cNE) : 0;
       net_out += fSE - fNW + fSW - fNE;
       r_out[4 * N + u] = cSE - fSE;
       r_out[5 * N + u] = cNW + fNW;
@@ -404,8 +455,10 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   }
   }
   for (int t = gtid; t < ntiles; t += nthr) {
+    bool any;
+    mf_tile_rows(a, s, all_on, (t / a.ntx) * MF_TH, &any);
     a.tstamp[t] = -2;
-    a.tact[t] = 1;
+    a.tact[t] = any ? 1 : 0;
   }
   if (!mf_grid_sync(a, s)) return;
   if (*(volatile int*)&a.status[0] == SEG_ECAPACITY) return;
@@ -463,7 +516,10 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
             if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
             if (!((dm >> (i & 31)) & 1u)) continue;
           }
-          if (mf_tile_bfs<ND>(a, s, tx, ty, first)) {
+          bool any;
+          const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+          if (!any) continue;
+          if (mf_tile_bfs<ND>(a, s, tx, ty, first, rows)) {
             ch = true;
             if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
           }
@@ -494,8 +550,9 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
       for (int k = blockIdx.x; k < ntc; k += gridDim.x) {
         const int tx = 2 * (k % ntx_c) + cx, ty = 2 * (k / ntx_c) + cy, t = ty * a.ntx + tx;
         if (!*(volatile unsigned char*)&a.tact[t]) continue;  // no active node can be in it
-        bool remain;
-        mf_discharge<ND>(a, s, tx, ty, &remain);
+        bool remain, any;
+        const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+        mf_discharge<ND>(a, s, tx, ty, rows, &remain);
         __syncthreads();
         if (threadIdx.x == 0) a.tact[t] = remain ? 1 : 0;
         any_remain |= remain;
@@ -520,6 +577,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   {
     const int nf = a.frame_h * W;  // nodes per frame
     for (int fb = 0; fb < a.nframes; ++fb) {
+      if (SKIP && !mf_frame_on(a, s, fb)) continue;
       long long flow_t = 0;
       for (int u = fb * nf + gtid; u < (fb + 1) * nf; u += nthr) flow_t += (long long)a.ct[u] - a.rt[u];
       for (int o = 16; o > 0; o >>= 1) flow_t += __shfl_xor_sync(0xffffffffu, flow_t, o);
@@ -536,7 +594,10 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
         if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
         if (!((dm >> (i & 31)) & 1u)) continue;
       }
-      if (mf_tile_reach<ND>(a, s, tx, ty, first)) {
+      bool any;
+      const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+      if (!any) continue;
+      if (mf_tile_reach<ND>(a, s, tx, ty, first, rows)) {
         ch = true;
         if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
       }
@@ -554,6 +615,7 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
   }
   uint8_t* mask_out = a.mask_out ? a.mask_out : a.io->mask;
   for (int u = gtid; u < N; u += nthr) {
+    if (!all_on && !mf_row_on(a, s, u / W)) continue;  // (an empty slot's state is kept)
     uint8_t v = a.z[u];
     mask_out[u] = v;
     if (a.mask_state) a.mask_state[u] = v;
@@ -568,7 +630,8 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     }
   }
   if (a.flow && blockIdx.x == 0)
-    for (int fb = threadIdx.x; fb < a.nframes; fb += blockDim.x) a.warm[fb] = 1;
+    for (int fb = threadIdx.x; fb < a.nframes; fb += blockDim.x)
+      if (!SKIP || mf_frame_on(a, s, fb)) a.warm[fb] = 1;
   long long* cut_out = a.cut_out ? a.cut_out : (a.io ? a.io->cut : nullptr);
   if (cut_out && blockIdx.x == 0)
     for (int fb = threadIdx.x; fb < a.nframes; fb += blockDim.x)
@@ -581,6 +644,26 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     lap(3);
     for (int k = 0; k < 4; ++k) a.status[4 + k] = (int)(s.t_acc[k] / 100);  // units of 0.1 us
   }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
+  __shared__ MFShared s;
+  int off = 0;
+  if (a.on) {  // a batch: its frames' run flags, read once per CTA
+    for (int f = threadIdx.x; f < a.nframes; f += blockDim.x) {
+      const unsigned char v = a.on[f];
+      if (f < MF_ON_CACHE) s.onf[f] = v;
+      off |= v == 0;
+    }
+    off = __syncthreads_or(off);
+    if (threadIdx.x == 0) s.on_mode = !off ? 0 : (a.nframes <= MF_ON_CACHE ? 1 : 2);
+    __syncthreads();
+  }
+  if (off)
+    mf_run<ND, true>(a, s);
+  else
+    mf_run<ND, false>(a, s);
 }
 
 // ---------------------------------------------------------------- host side
@@ -642,9 +725,11 @@ int mf_grid_size(int H, int W, int* grid) {
 int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              long long timeout_ns, const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed, bool init_done) {
+              long long timeout_ns, const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed, bool init_done,
+              const uint8_t* on) {
   MFArgs a;
   memset(&a, 0, sizeof(a));
+  a.on = on;
   a.flow = flow;
   a.warm = warm;
   if (H % m.nframes) return SEG_EINVAL;

@@ -51,6 +51,7 @@ struct PriorArgs {
   GaussDev* gauss;
   KalmanDev* kal_adv;  // nullable: advance the variance recursion
   const SegIO* io;     // sal / prior / rgb == nullptr: take them from here
+  const uint8_t* on;   // [B] slots holding a stream (nullptr: all)
 };
 
 struct MomFinArgs {
@@ -61,6 +62,7 @@ struct MomFinArgs {
   KalmanDev* kal;  // nullable: advance the variance recursion
   double a, b;
   const SegIO* io;  // rgb / prior == nullptr: take them from here
+  const uint8_t* on;
 };
 
 __device__ __forceinline__ void mom1_add_rgb(float p, int r8, int g8, int b8, float* s) {
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(256) k_prior(PriorArgs a) {
   // Before waiting for the preceding kernel (the saliency's last, which writes S
   // and its maximum): the I/O pointers, the Kalman state and the previous mask
   // tile, none of which it writes (the mask tile is unused when w_f = 0).
+  if (SEG_SLOT_OFF(a.on, blockIdx.z)) return;
   prior_frame(a, blockIdx.z);
   prior_setup(a, sTap, &s_wf);
   if (a.prev) prior_tile_mask(a, blockIdx.x * PR_TX, blockIdx.y * PR_TY, sM);
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__(256) k_mom1(const uint8_t* __restrict__ rgb,
                                               const float* __restrict__ prior, int N, MomFinArgs f) {
   seg_pdl_enter();
   const int fb = blockIdx.y;  // frame of the batch
+  if (SEG_SLOT_OFF(f.on, fb)) return;
   rgb += (size_t)fb * 3 * N;
   prior += (size_t)fb * N;
   f.part += (size_t)fb * f.part_stride;
@@ -458,6 +462,7 @@ __global__ void __launch_bounds__(256) k_mom2(const uint8_t* __restrict__ rgb,
   if (!rgb) rgb = f.io->rgb;
   if (!prior) prior = f.io->prior;
   const int fb = blockIdx.y;  // frame of the batch
+  if (SEG_SLOT_OFF(f.on, fb)) return;
   rgb += (size_t)fb * 3 * N;
   prior += (size_t)fb * N;
   f.part += (size_t)fb * f.part_stride;
@@ -491,6 +496,7 @@ struct EMArgs {
   int part_stride;
   unsigned* counter;  // [frame][label]
   const SegIO* io;
+  const uint8_t* on;
 };
 
 // One EM iteration for label a of frame fb (blockIdx.y = 2 fb + a): E-step
@@ -502,6 +508,7 @@ template <int M>
 __global__ void __launch_bounds__(256) k_em_step(EMArgs a) {
   seg_pdl_enter();
   const int lab = blockIdx.y & 1, fb = blockIdx.y >> 1;
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   const GaussDev* gd = a.gauss + fb;
   if (gd->degenerate & (1 << lab)) return;  // uniform over the grid: no partials, no finalise
   const uint8_t* rgb = (a.rgb ? a.rgb : a.io->rgb) + (size_t)fb * 3 * a.N;
@@ -607,6 +614,7 @@ struct KMArgs {
   int update;
   int mseed;   // KM_SEED: seeds already placed (the pass places seed mseed)
   const SegIO* io;
+  const uint8_t* on;
 };
 
 template <int M, int MODE>
@@ -614,6 +622,7 @@ __global__ void __launch_bounds__(256) k_km_pass(KMArgs a) {
   constexpr int NV = MODE == KM_SEED ? 4 : MODE == KM_LLOYD ? 4 * M : 10 * M;
   seg_pdl_enter();
   const int lab = blockIdx.y & 1, fb = blockIdx.y >> 1;
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   const GaussDev* gd = a.gauss + fb;
   if (gd->degenerate & (1 << lab)) return;  // no weight: no mixture to start
   if (a.update && a.valid && a.valid[2 * fb + lab]) return;  // EM continues from the previous frame's mixture
@@ -746,6 +755,7 @@ struct TermsArgs {
   int* mf_r;
   const int* flow;
   const unsigned char* warm;
+  const uint8_t* on;  // [B] slots holding a stream (nullptr: all); an empty slot is not written
 };
 
 __device__ __forceinline__ int32_t quant_cap(float K, float x) {
@@ -935,6 +945,7 @@ __global__ void __launch_bounds__(256) k_terms(TermsArgs a) {
   terms_frame(a, blockIdx.z);
   const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= a.W || y >= a.H) return;
+  if (SEG_SLOT_OFF(a.on, blockIdx.z)) return;  // no stream in the slot: the cut skips its rows
   TermsIn t;
   terms_load(a, x, y, t);
   terms_store(a, *a.gauss, a.gmm, (size_t)a.H * a.W * a.B, sLut, x, y, t);
@@ -1019,6 +1030,7 @@ static void prior_args(seg_ctx* c, const float* sal, const uint8_t* prev_mask, i
   a.part_stride = pt_part_doubles(c->H, c->W);
   a.kal_adv = (use_kalman && (rgb_moments || c->io_mode)) ? c->kal : nullptr;
   a.io = c->io_mode ? c->io : nullptr;
+  a.on = c->sal.on;
 }
 
 int pt_launch_prior(seg_ctx* c, const float* sal, const uint8_t* prev_mask, int use_kalman,
@@ -1048,6 +1060,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
   fa.a = p.sigma1 * p.sigma1;
   fa.b = p.sigma2 * p.sigma2;
   fa.io = c->io_mode ? c->io : nullptr;
+  fa.on = c->sal.on;
   const int M = p.gmm_components;
   if (first_pass) SEG_CUDA_TRY(seg_launch(k_mom1, dim3(c->mom_blocks, c->B), 256, 0, st, rgb, prior, N, fa));
   SEG_CUDA_TRY(seg_launch(k_mom2, dim3(c->mom_blocks, c->B), 256, 0, st, rgb, prior, N, fa));
@@ -1063,6 +1076,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     ea.part_stride = pt_em_part_doubles(c->H, c->W);
     ea.counter = c->em_counter;
     ea.io = c->io_mode ? c->io : nullptr;
+    ea.on = c->sal.on;
     KMArgs ka;
     ka.rgb = rgb;
     ka.prior = prior;
@@ -1077,6 +1091,7 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
     ka.valid = first_pass ? nullptr : c->gmm_valid;
     ka.update = first_pass ? 0 : p.gmm_update;
     ka.io = ea.io;
+    ka.on = c->sal.on;
     const dim3 gk(c->mom_blocks, 2 * c->B);
     for (int m = 1; m < M; ++m) {
       ka.mseed = m;
@@ -1135,6 +1150,7 @@ static void terms_args(seg_ctx* c, const uint8_t* rgb, const float* prior, int32
   ta.io = c->io_mode ? c->io : nullptr;
   ta.gmm = c->gmm;
   ta.M = p.gmm_components;
+  ta.on = c->sal.on;
 }
 
 // A frame's prior, first moments (fused into k_prior), second moments and

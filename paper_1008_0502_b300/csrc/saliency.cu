@@ -41,8 +41,9 @@ __constant__ float c_binom[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
 // like their bit patterns).
 template <typename TIn>
 __global__ void k_rgb_max(const TIn* __restrict__ rgb, int n, int* smax, unsigned* mm,
-                          int nmaps, const SegIO* io) {
+                          int nmaps, const SegIO* io, const uint8_t* on) {
   seg_pdl_enter();
+  if (SEG_SLOT_OFF(on, blockIdx.y)) return;
   if constexpr (std::is_same<TIn, uint8_t>::value) {
     if (!rgb) rgb = io->rgb;
   }
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
                                                       const int* __restrict__ smax_p,
                                                       float* __restrict__ I1, float* __restrict__ RG1,
                                                       float* __restrict__ BY1, int h1, int w1,
-                                                      const SegIO* io) {
+                                                      const SegIO* io, const uint8_t* on) {
   constexpr bool U8 = std::is_same<TIn, uint8_t>::value;
   if constexpr (U8) {
     if (!rgb) rgb = io->rgb;
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
   __shared__ float sF[3][RED_IN_Y][RED_IN_X];
   __shared__ float sH[3][RED_IN_Y][RED_TX];
   const int fb = blockIdx.z;  // frame of the batch
+  if (SEG_SLOT_OFF(on, fb)) return;
   rgb += (size_t)fb * 3 * H * W;
   const size_t o1 = (size_t)fb * h1 * w1;
   I1 += o1;
@@ -238,6 +240,7 @@ struct Reduce3Args {
   const float* in[3];
   float* out[3];
   int h, w, h2, w2;
+  const uint8_t* on;
 };
 
 // One REDUCE step of one channel per CTA (blockIdx.z = channel + 3 * frame).
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(256) k_reduce3(Reduce3Args a) {
   __shared__ float sF[RED_IN_Y][RED_IN_X];
   __shared__ float sH[RED_IN_Y][RED_TX];
   const int ch = blockIdx.z % 3, fb = blockIdx.z / 3;
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   // (selects, not a runtime index into the parameter block, which would copy it to local memory)
   const float* __restrict__ in = (ch == 0 ? a.in[0] : ch == 1 ? a.in[1] : a.in[2]) + (size_t)fb * a.h * a.w;
   float* __restrict__ out = (ch == 0 ? a.out[0] : ch == 1 ? a.out[1] : a.out[2]) + (size_t)fb * a.h2 * a.w2;
@@ -280,11 +284,13 @@ struct PyrTailArgs {
   float* lvl[3][SEG_MAX_LEVELS];
   int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
   int from, to;  // produce levels from+1 .. to
+  const uint8_t* on;
 };
 
 __global__ void __launch_bounds__(1024) k_pyr_tail(PyrTailArgs a) {
   seg_pdl_enter();
   const int ch = blockIdx.x % 3, fb = blockIdx.x / 3;
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   for (int l = a.from; l < a.to; ++l) {
     const int h = a.hl[l], w = a.wl[l], h2 = a.hl[l + 1], w2 = a.wl[l + 1];
     const float* __restrict__ in = a.lvl[ch][l] + (size_t)fb * h * w;
@@ -321,6 +327,7 @@ struct GaborArgs {
   int hl[SEG_MAX_LEVELS], wl[SEG_MAX_LEVELS];
   int lvl_first, lvl_last;
   int blk_off[SEG_MAX_LEVELS + 1];  // prefix of tile counts from lvl_first
+  const uint8_t* on;
 };
 
 // Sec. 7.2 (edge orientation): O(sigma, theta) = |k_theta * I(sigma)| with the
@@ -338,6 +345,7 @@ __device__ __forceinline__ void gb_group(int g, int no, int& k0, int& k1) {
 template <int RT>
 __global__ void __launch_bounds__(256) k_gabor(GaborArgs a, GaborTaps t) {
   seg_pdl_enter();
+  if (SEG_SLOT_OFF(a.on, blockIdx.y)) return;
   __shared__ float sIn[GB_IN_Y][GB_IN_X];
   __shared__ float sH0[GB_IN_Y][GB_TX];
   __shared__ float sHr[GB_IN_Y][GB_TX], sHi[GB_IN_Y][GB_TX];
@@ -451,6 +459,7 @@ struct CSArgs {
   int c_lo, c_hi;  // center scales c_min .. c_max (= sigma_S)
   const int2* rs;
   int rs_row[SEG_MAX_PAIRS], rs_col[SEG_MAX_PAIRS];
+  const uint8_t* on;
 };
 
 
@@ -474,6 +483,7 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
   const int nb = (hc + T - 1) / T, ntx = (wc + T - 1) / T;
   const int band = b - a.pair_band_off[p] / NCH;
   const int fb = blockIdx.y;  // frame of the batch
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   unsigned* mm = a.mm + (size_t)fb * 2 * a.npairs * NCH;
   float* tpart = a.tpart + (size_t)fb * a.nbands_total;
   const float* cen[CPB];
@@ -591,6 +601,7 @@ __global__ void __launch_bounds__(256) k_cs_accum(CSArgs a, int c, const float* 
   __shared__ float sab[2 * ACC_MAX_PC * CPB];  // N(.) of this CTA's maps as a*v + b
   constexpr int G = NCH / CPB;                  // channel groups
   const int fb = blockIdx.z / G;                // frame of the batch
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   const int f0 = (blockIdx.z % G) * CPB;        // first channel of this CTA
   const int hc = a.hl[c], wc = a.wl[c];
   {
@@ -713,6 +724,7 @@ __global__ void __launch_bounds__(NT) k_cs_accum_fused(CSArgs a, float* __restri
   __shared__ float sT[FA_N(FA_TY, 2) * FA_N(FA_TX, 1)];   // horizontal REDUCE pass
   __shared__ float sab[2 * SEG_MAX_PAIRS];
   const int f = blockIdx.z % a.nch, fb = blockIdx.z / a.nch;
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   const int cmax = a.c_hi, D = a.c_hi - a.c_lo;
   for (int p = threadIdx.x; p < a.npairs; p += blockDim.x) cs_map_affine(a, p, f, a.flat, &sab[2 * p], fb);
   int RY[3], RX[3], NY[3], NX[3];
@@ -849,6 +861,7 @@ struct ConspArgs {
   float* csum;
   float* consp;
   float* S;
+  const uint8_t* on;
 };
 
 // Orientation conspicuity sum_theta N(B_theta), then N of the four conspicuity
@@ -865,6 +878,7 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
   __shared__ unsigned tmax[4 * CONSP_TILES];
   const int n = a.h * a.w;
   const int fb = blockIdx.x;  // frame of the batch
+  if (SEG_SLOT_OFF(a.on, fb)) return;
   a.acc += (size_t)fb * a.nch * n;
   float* const csum_g = a.csum + (size_t)fb * n;
   float* const S_g = a.S + (size_t)fb * n;
@@ -945,10 +959,12 @@ __global__ void __launch_bounds__(1024) k_consp(ConspArgs a) {
 
 __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, int hs, int ws, int H,
                                                   int W, float* __restrict__ sal, const SegIO* io,
-                                                  const int2* __restrict__ frow, const int2* __restrict__ fcol) {
+                                                  const int2* __restrict__ frow, const int2* __restrict__ fcol,
+                                                  const uint8_t* on) {
   seg_pdl_enter();
   if (!sal) sal = io->sal;
   const int fb = blockIdx.z;  // frame of the batch
+  if (SEG_SLOT_OFF(on, fb)) return;
   S += (size_t)fb * hs * ws;
   sal += (size_t)fb * H * W;
   const int xq = blockIdx.x * 64 + (threadIdx.x & 63), y = blockIdx.y * 4 + (threadIdx.x >> 6);
@@ -979,11 +995,12 @@ __global__ void __launch_bounds__(256) k_upsample(const float* __restrict__ S, i
 __global__ void __launch_bounds__(256) k_upsample_rows(const float* __restrict__ S, int hs, int ws, int H, int W,
                                                        float* __restrict__ sal, const SegIO* io,
                                                        const int2* __restrict__ frow,
-                                                       const int2* __restrict__ fcol) {
+                                                       const int2* __restrict__ fcol, const uint8_t* on) {
   seg_pdl_enter();
   extern __shared__ __align__(16) float up_smem[];  // [rows of S touched][W]
   if (!sal) sal = io->sal;
   const int fb = blockIdx.y;  // frame of the batch
+  if (SEG_SLOT_OFF(on, fb)) return;
   S += (size_t)fb * hs * ws;
   sal += (size_t)fb * H * W;
   const int y_first = blockIdx.x * UP_ROWS, y_last = min(y_first + UP_ROWS, H) - 1;
@@ -1042,6 +1059,7 @@ __global__ void __cluster_dims__(CC_CTAS, 1, 1) __launch_bounds__(CC_THREADS) k_
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank(), fb = blockIdx.x / CC_CTAS;
+  if (SEG_SLOT_OFF(a.on, fb)) return;  // (every CTA of the cluster: one frame)
   extern __shared__ float dsm[];  // C_O (CTA 3), then S: n floats each
   __shared__ float ab[8];
   __shared__ float red[12 * 32];
@@ -1360,6 +1378,7 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
     a.rs_row[i] = s.rs_row[i];
     a.rs_col[i] = s.rs_col[i];
   }
+  a.on = s.on;
 }
 
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
@@ -1380,14 +1399,14 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);
   if (rgb_f32) {
     const float* f = (const float*)rgb;
-    SEG_CUDA_TRY(seg_launch(k_rgb_max<float>, dim3(nb, B), 256, 0, st, f, N, s.smax, s.mm, s.nmaps, nullptr));
+    SEG_CUDA_TRY(seg_launch(k_rgb_max<float>, dim3(nb, B), 256, 0, st, f, N, s.smax, s.mm, s.nmaps, nullptr, s.on));
     SEG_CUDA_TRY(seg_launch(k_feat_reduce1<float>, g1, 256, 0, st, f, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
-                                              s.hl[1], s.wl[1], nullptr));
+                                              s.hl[1], s.wl[1], nullptr, s.on));
   } else {
     const uint8_t* u = (const uint8_t*)rgb;
-    SEG_CUDA_TRY(seg_launch(k_rgb_max<uint8_t>, dim3(nb8, B), 256, 0, st, u, N, s.smax, s.mm, s.nmaps, io));
+    SEG_CUDA_TRY(seg_launch(k_rgb_max<uint8_t>, dim3(nb8, B), 256, 0, st, u, N, s.smax, s.mm, s.nmaps, io, s.on));
     SEG_CUDA_TRY(seg_launch(k_feat_reduce1<uint8_t>, g1, 256, 0, st, u, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
-                                                s.hl[1], s.wl[1], io));
+                                                s.hl[1], s.wl[1], io, s.on));
   }
   // tiled launches while the produced level is large; one tail launch for the rest
   int tail_from = s.L - 1;
@@ -1406,6 +1425,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     ra.w = s.wl[l];
     ra.h2 = s.hl[l + 1];
     ra.w2 = s.wl[l + 1];
+    ra.on = s.on;
     dim3 g((ra.w2 + RED_TX - 1) / RED_TX, (ra.h2 + RED_TY - 1) / RED_TY, 3 * B);
     SEG_CUDA_TRY(seg_launch(k_reduce3, g, 256, 0, st, ra));
   }
@@ -1419,12 +1439,14 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
     }
     ta.from = tail_from;
     ta.to = s.L - 1;
+    ta.on = s.on;
     SEG_CUDA_TRY(seg_launch(k_pyr_tail, 3 * B, 1024, 0, st, ta));
   }
   GaborArgs ga;
   memset(&ga, 0, sizeof(ga));
   ga.lvl_first = s.c_min;
   ga.lvl_last = s.s_max;
+  ga.on = s.on;
   int tot = 0;
   for (int l = s.c_min; l <= s.s_max; ++l) {
     ga.in[l] = s.pyr[0][l];
@@ -1522,6 +1544,7 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   pa.salmax = s.salmax;
   pa.frow = s.rs + s.rs_frow;
   pa.fcol = s.rs + s.rs_fcol;
+  pa.on = s.on;
   if (s.consp_cl)
     SEG_CUDA_TRY(seg_launch(k_consp_cl, CC_CTAS * B, CC_THREADS, s.consp_cl_smem, st, pa));
   else if (s.consp_staged)
@@ -1531,11 +1554,11 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   if (upsample && s.up_smem) {
     const dim3 gu((H + UP_ROWS - 1) / UP_ROWS, B);
     SEG_CUDA_TRY(seg_launch(k_upsample_rows, gu, 256, s.up_smem, st, s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io,
-                            s.rs + s.rs_frow, s.rs + s.rs_fcol));
+                            s.rs + s.rs_frow, s.rs + s.rs_fcol, s.on));
   } else if (upsample) {
     dim3 gu((W + 255) / 256, (H + 3) / 4, B);  // 4 pixels per thread
     SEG_CUDA_TRY(seg_launch(k_upsample, gu, 256, 0, st, s.S, s.hl[s.sS], s.wl[s.sS], H, W, sal_out, io, s.rs + s.rs_frow,
-                                   s.rs + s.rs_fcol));
+                                   s.rs + s.rs_fcol, s.on));
   }
   SEG_CUDA_TRY(cudaGetLastError());
   return SEG_OK;

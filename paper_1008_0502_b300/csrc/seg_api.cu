@@ -99,7 +99,7 @@ int seg_check_params(const seg_params* p, int H, int W) {
 // Byte offsets of every buffer in a context's single device arena.
 struct ArenaLayout {
   size_t kal, gauss, mom, lut, cnt, prev, cs, ct, ncap, sal, prior, mask, cut, rgb, status, io, flow, warm, mf;
-  size_t gmm, empart, emcnt, gvalid;
+  size_t gmm, empart, emcnt, gvalid, slots;
   size_t total;
 };
 
@@ -138,6 +138,7 @@ static int arena_layout(SalWS& sal, int B, int H, int W, const seg_params& p, Ar
   L.empart = take((size_t)B * 2 * sizeof(double) * pt_em_part_doubles(H, W));
   L.emcnt = take((size_t)B * 2 * sizeof(unsigned));
   L.gvalid = take((size_t)B * 2 * sizeof(int));
+  L.slots = take((size_t)B);
   L.total = off;
   return SEG_OK;
 }
@@ -218,6 +219,8 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   c->em_part = (double*)(base + L.empart);
   c->em_counter = (unsigned*)(base + L.emcnt);
   c->gmm_valid = (int*)(base + L.gvalid);
+  c->slot_on = (uint8_t*)(base + L.slots);
+  c->sal.on = B > 1 ? c->slot_on : nullptr;  // (a single stream is always on)
   c->warm = (unsigned char*)(base + o_warm);
   mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
@@ -237,6 +240,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   ok = ok && cudaMemset(c->warm, 0, B) == cudaSuccess;
   ok = ok && cudaMemset(c->em_counter, 0, (size_t)B * 2 * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaMemset(c->gmm_valid, 0, (size_t)B * 2 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMemset(c->slot_on, 1, (size_t)B) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
   ok = ok && mf_grid_size(B * H, W, &c->mf_grid) == SEG_OK;
   if (!ok) {
@@ -280,6 +284,20 @@ extern "C" int seg_set_barrier_timeout(seg_ctx* c, int us) {
   return SEG_OK;
 }
 
+extern "C" int seg_set_stream_active(seg_ctx* c, int b, int on) {
+  if (!c || b < 0 || b >= c->B || (on != 0 && on != 1)) return SEG_EINVAL;
+  SEG_CUDA_TRY(cudaMemsetAsync(c->slot_on + b, on, 1, c->stream));
+  if (c->pipe_on) {  // the next frame's saliency (on the front stream) comes after the change too
+    cudaEvent_t e;
+    SEG_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, c->stream);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(c->s_front, e, 0);
+    cudaEventDestroy(e);
+    SEG_CUDA_TRY(r);
+  }
+  return SEG_OK;
+}
+
 extern "C" int seg_reset(seg_ctx* c) {
   if (!c) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaMemsetAsync(c->kal, 0, c->B * sizeof(KalmanDev), c->stream));
@@ -309,11 +327,12 @@ static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const in
   if (c->io_mode)  // mask and cut come from the frame's SegIO; k_set_io zeroed the words
     return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
                      nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
-                     c->p.local_iters, 1000LL * c->p.barrier_timeout_us, c->io, flow, warm, true, init_done);
+                     c->p.local_iters, 1000LL * c->p.barrier_timeout_us, c->io, flow, warm, true, init_done,
+                     c->sal.on);
   return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
                    mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
                    c->p.global_relabel_every, c->p.local_iters, 1000LL * c->p.barrier_timeout_us, nullptr, flow,
-                   warm, false, init_done);
+                   warm, false, init_done, c->sal.on);
 }
 
 // The launch sequence of one frame.  With c->io_mode set (graph capture) every

@@ -18,6 +18,10 @@
 #define SEG_MAX_MAPS (SEG_MAX_PAIRS * (3 + SEG_MAX_ORIENT))
 #define SEG_INF_H 0x3fffffff
 
+// Slots of a batch that hold no stream (on[fb] == 0) are skipped: a kernel's
+// CTAs of such a frame return at once (on == nullptr: every frame is on).
+#define SEG_SLOT_OFF(on, fb) ((on) != nullptr && !(on)[fb])
+
 // Programmatic dependent launch: the frame's kernels are launched with
 // programmatic stream serialisation, so each one is scheduled while its
 // predecessor is still running.  Each such kernel first waits for its
@@ -191,6 +195,7 @@ struct GaborTaps {
 // the first kernel fuses feature extraction with the first REDUCE.
 struct SalWS {
   int B;  // frames of the batch (same size); every per-frame buffer holds B frames
+  const uint8_t* on;  // [B] slots holding a stream (nullptr: all; batch contexts only)
   int light_ctas;  // sharing the GPU with a pipelined back half: smaller CTAs where that pays
   int H, W, L, c_min, c_max, d_min, d_max, no, s_max, sS, tile;
   int opp_sum;
@@ -351,6 +356,7 @@ struct MFArgs {
   int max_cycles, gr_every, local_iters;
   long long timeout_ns;
   int init_done;  // e, rt and r already hold the initial residual graph (formed by the terms kernel)
+  const uint8_t* on;  // [nframes] nullable: 0 = an empty slot, its frame's rows are neither read nor written
 };
 
 struct MFWS {
@@ -383,6 +389,7 @@ struct seg_ctx {
   unsigned* mom_counter;  // last-CTA counter of the moment passes (returns to 0)
   GmmDev* gmm;            // [B][2] colour mixtures (gmm_components > 1)
   int* gmm_valid;         // [B][2] the mixture is a fitted one (the next frame's EM may start from it)
+  uint8_t* slot_on;       // [B] 1: the slot holds a stream (batch contexts: empty slots are skipped)
   double* em_part;        // [B][2][em partial doubles]
   unsigned* em_counter;   // [B][2]
   int mom_blocks;
@@ -462,6 +469,6 @@ int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, c
               const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
               long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
               long long timeout_ns, const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr,
-              bool words_zeroed = false, bool init_done = false);
+              bool words_zeroed = false, bool init_done = false, const uint8_t* on = nullptr);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -59,6 +59,7 @@ def _load():
         "seg_create": ([vp, i32, i32, P(seg_params), P(vp)], i32),
         "seg_create_batch": ([vp, i32, i32, i32, P(seg_params), P(vp)], i32),
         "seg_reset_stream": ([vp, i32], i32),
+        "seg_set_stream_active": ([vp, i32, i32], i32),
         "seg_workspace_bytes": ([i32, i32, i32, P(seg_params), P(C.c_size_t)], i32),
         "seg_destroy": ([vp], i32),
         "seg_reset": ([vp], i32),
@@ -307,6 +308,12 @@ class Segmenter:
         the context's stream and re-captures its graphs on the next frame."""
         _check(lib.seg_set_barrier_timeout(self.handle, int(us)), "seg_set_barrier_timeout")
         self.params.barrier_timeout_us = int(us)
+
+    def set_stream_active(self, b: int, on: bool):
+        """Slot b of a batch holds a stream (True) or is empty (False: its frame is skipped)."""
+        cur = self._begin()
+        _check(lib.seg_set_stream_active(self.handle, int(b), int(bool(on))), "seg_set_stream_active")
+        self._end(cur)
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)

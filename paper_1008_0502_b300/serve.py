@@ -3,7 +3,10 @@
 Streams of the same resolution share a batch context (``seg_create_batch``):
 its B slots are B independent streams advanced together by one
 ``seg_push_frame`` (one CUDA-graph replay) per step.  Each resolution group runs
-on a CUDA stream of its own, so the groups' work overlaps on the device.
+on a CUDA stream of its own, so the groups' work overlaps on the device.  B
+follows the resolution (``slots_for``): the stacked min cut of a batch lasts as
+long as its slowest frame, so small frames, each of which leaves most of the GPU
+idle, are batched, and a frame that fills the GPU alone runs alone.
 
 * Admission by HBM footprint: a request whose resolution has a free slot takes
   it; otherwise a new group is created if its workspace
@@ -16,14 +19,25 @@ on a CUDA stream of its own, so the groups' work overlaps on the device.
 * Continuous batching: requests are admitted at every step as slots and memory
   free up, while the other streams keep running; a finished stream frees its
   slot, and the next stream admitted there starts a new video
-  (``seg_reset_stream``: previous mask, Kalman variance and warm-start flows
-  of that slot only).
+  (``seg_reset_stream``: previous mask, Kalman variance, warm-start flows and
+  colour mixtures of that slot only).  An empty slot is marked as such
+  (``seg_set_stream_active``), and the kernels skip its frame.
+* Steps overlap: the host does not wait for a step before launching the next
+  one; each group keeps up to ``depth`` steps in flight and collects a step's
+  results (latencies, kept outputs, device status) once its completion event
+  has passed.
+* Per-frame latency is client-side: from the frame's submission (the host
+  taking it for a step) to its mask and cut being ready on the device (the
+  step's completion event, read on the host clock through a reference event).
 * Per-stream state (previous mask, Kalman variance, the last cut's flows for the
-  warm start) stays on the device in the slot.
+  warm start, colour mixtures) stays on the device in the slot.
 
 A stream's results do not depend on which slot or group it runs in or on the
 other streams of the batch: every per-frame kernel treats the frames of a batch
-independently, so a served stream equals the same stream run alone.
+independently, so a served stream equals the same stream run alone.  With
+``slots=1`` every stream gets a context of its own: the plain per-stream launch
+the batched server is compared with; ``slots="auto"`` sizes each group by its
+resolution (``slots_for``).
 """
 from __future__ import annotations
 
@@ -77,6 +91,8 @@ class _Group:
         self.sid = [None] * slots
         self.pos = [0] * slots
         self.fresh = [False] * slots
+        self.on = [True] * slots  # the slots' flags on the device (all on at creation)
+        self.inflight = []        # launched steps not yet collected, oldest first
 
     def free_slot(self):
         for b in range(self.B):
@@ -92,11 +108,14 @@ class _Group:
 
 
 class Server:
-    def __init__(self, params: seg.seg_params, hbm_budget_bytes: int, slots: int = 8, keep_outputs: bool = False):
+    def __init__(self, params: seg.seg_params, hbm_budget_bytes: int, slots: int | str = "auto",
+                 keep_outputs: bool = False, depth: int = 3, group_pixels: int = 1_300_000):
         self.params = params
+        self.depth = max(1, int(depth))  # steps in flight per group
         self.budget = int(hbm_budget_bytes)
         self.used = 0
-        self.slots = slots
+        self.slots = slots  # slots per group, or "auto": group_pixels // (H * W), 1 to 8
+        self.group_pixels = int(group_pixels)
         self.keep = keep_outputs
         self.groups: list[_Group] = []
         self.queue: list[Request] = []
@@ -105,6 +124,15 @@ class Server:
         self.steps = 0
         self.rejected_groups = 0  # times a new group could not be created (the request waited)
         self.evicted_groups = 0
+
+    def slots_for(self, H: int, W: int) -> int:
+        """Slots of a new H x W group.  "auto": as many frames as fit a pixel budget
+        (at least 1, at most 8).  A batch's min cut lasts as long as its slowest
+        frame, so batching pays where one frame leaves most of the GPU idle (small
+        frames) and not where one frame already fills it."""
+        if self.slots == "auto":
+            return max(1, min(8, self.group_pixels // (H * W)))
+        return int(self.slots)
 
     # -- admission
     def submit(self, req: Request):
@@ -127,7 +155,7 @@ class Server:
                         slot = (g, b)
                         break
             if slot is None:
-                need = seg.workspace_bytes(self.slots, H, W, self.params)
+                need = seg.workspace_bytes(self.slots_for(H, W), H, W, self.params)
                 if need > self.budget:
                     self.results[req.sid].refused = "its group's workspace exceeds the HBM budget"
                     continue
@@ -163,6 +191,8 @@ class Server:
             self._drop(g)
 
     def _drop(self, g: _Group):
+        while g.inflight:  # its last steps' results first
+            self._collect(g)
         g.close()
         self.groups.remove(g)
         self.used -= g.bytes
@@ -173,7 +203,7 @@ class Server:
         with the idle groups freed)."""
         for attempt in range(2):
             try:
-                g = _Group(H, W, self.slots, self.params)
+                g = _Group(H, W, self.slots_for(H, W), self.params)
             except seg.SegError as e:
                 if e.code != seg.SEG_ENOMEM:
                     raise
@@ -190,65 +220,79 @@ class Server:
         return None
 
     # -- one step of every group with an active slot
+    def _collect(self, g: _Group):
+        """Waits for g's oldest step in flight and records its results."""
+        done, stamp, frames, kept = g.inflight.pop(0)
+        done.synchronize()
+        code, _ = g.ctx.sync()
+        if code != 0:
+            raise seg.SegError(code, "serve step")
+        t_done = self._t_ref + self._ev_ref.elapsed_time(done) / 1e3  # the host clock
+        for b, sid, t_sub in frames:
+            r = self.results[sid]
+            r.frame_ms.append((t_done - t_sub) * 1e3)
+            if b in kept:
+                m, p, c = kept[b]
+                r.masks.append(m)
+                r.priors.append(p)
+                r.cuts.append(int(c.item()))
+            if len(r.frame_ms) >= self.requests[sid].n_frames:
+                r.done = t_done - self._t0
+
     def step(self, now: float):
         self._admit(now)
         outer = torch.cuda.current_stream()
-        launched = []
+        launched = 0
         for g in self.groups:
             if not g.active():
                 continue
+            while len(g.inflight) >= self.depth:
+                self._collect(g)
             g.stream.wait_stream(outer)  # frames produced on the caller's stream are ready
             with torch.cuda.stream(g.stream):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
+                frames = []
                 for b in range(g.B):
                     sid = g.sid[b]
+                    if g.B > 1 and g.on[b] != (sid is not None):  # empty slots are skipped
+                        g.ctx.set_stream_active(b, sid is not None)
+                        g.on[b] = sid is not None
                     if sid is None:
                         continue
                     if g.fresh[b]:
                         g.ctx.reset(stream_index=b)
                         g.fresh[b] = False
                     g.inbuf[b].copy_(self.requests[sid].frame(g.pos[b]), non_blocking=True)
-                e0.record(g.stream)
-                sal, pr, mask, cut = g.ctx.push_frame(g.inbuf, *g.outs)
-                e1.record(g.stream)
+                    frames.append((b, sid, time.perf_counter()))
+                if g.B > 1:
+                    sal, pr, mask, cut = g.ctx.push_frame(g.inbuf, *g.outs)
+                else:  # a single-stream context takes one (H, W, 3) frame
+                    sal, pr, mask, cut = g.ctx.push_frame(g.inbuf[0], *g.outs)
+                    pr, mask = pr.unsqueeze(0), mask.unsqueeze(0)
+                done = torch.cuda.Event(enable_timing=True)
+                done.record(g.stream)
+                kept = {}
                 if self.keep:
-                    kept = [(b, mask[b].clone(), pr[b].clone(), cut[b].clone()) for b in range(g.B)
-                            if g.sid[b] is not None]
-                else:
-                    kept = []
-            launched.append((g, e0, e1, kept))
-        for g, e0, e1, kept in launched:
-            g.stream.synchronize()
-            code, _ = g.ctx.sync()
-            if code != 0:
-                raise seg.SegError(code, "serve step")
-            ms = e0.elapsed_time(e1)
-            kept_by_slot = {b: (m, p, c) for b, m, p, c in kept}
-            for b in range(g.B):
-                sid = g.sid[b]
-                if sid is None:
-                    continue
-                r = self.results[sid]
-                r.frame_ms.append(ms)
-                if b in kept_by_slot:
-                    m, p, c = kept_by_slot[b]
-                    r.masks.append(m)
-                    r.priors.append(p)
-                    r.cuts.append(int(c.item()))
+                    kept = {b: (mask[b].clone(), pr[b].clone(), cut[b].clone()) for b, _, _ in frames}
+            g.inflight.append((done, now, frames, kept))
+            for b, sid, _ in frames:  # frame count decides when a slot frees (no wait for the device)
                 g.pos[b] += 1
                 if g.pos[b] >= self.requests[sid].n_frames:
                     g.sid[b] = None
-                    r.done = now
+            launched += 1
         self.steps += 1
-        return len(launched)
+        return launched
 
     def run(self, requests, clock: str = "wall", max_steps: int = 1_000_000):
         """Serve every request to completion.  clock="wall": arrivals in seconds of
         wall time since the start; clock="steps": arrivals in steps."""
         for r in requests:
             self.submit(r)
-        t0 = time.perf_counter()
+        # reference event: device timestamps onto the host clock
+        self._ev_ref = torch.cuda.Event(enable_timing=True)
+        self._ev_ref.record()
+        self._ev_ref.synchronize()
+        self._t_ref = time.perf_counter()
+        t0 = self._t0 = time.perf_counter()
         while self.steps < max_steps:
             now = time.perf_counter() - t0 if clock == "wall" else float(self.steps)
             pending = self.queue or any(g.active() for g in self.groups)
@@ -259,11 +303,15 @@ class Server:
                 nxt = min(r.arrival for r in self.queue)
                 if clock == "wall" and nxt > now:
                     time.sleep(min(nxt - now, 0.01))
+        for g in self.groups:
+            while g.inflight:
+                self._collect(g)
         wall = time.perf_counter() - t0
         frames = sum(len(r.frame_ms) for r in self.results.values())
         lat = np.array([x for r in self.results.values() for x in r.frame_ms]) if frames else np.zeros(1)
         return {"wall_s": wall, "frames": frames, "frames_per_s": frames / wall if wall > 0 else 0.0,
-                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "of": "frame submission on the host to its mask and cut ready on the device"},
                 "streams": len(self.results), "groups": len(self.groups), "hbm_bytes": self.used,
                 "steps": self.steps, "refused": sum(1 for r in self.results.values() if r.refused),
                 "evicted_groups": self.evicted_groups}

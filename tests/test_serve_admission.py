@@ -28,6 +28,7 @@ class _FakeGroup:
         self.sid = [None] * slots
         self.pos = [0] * slots
         self.fresh = [False] * slots
+        self.inflight = []  # (no step is ever launched here)
 
     free_slot = serve._Group.free_slot
     active = serve._Group.active
@@ -194,3 +195,21 @@ def test_allocation_failure_waits_while_others_run_and_is_refused_otherwise(serv
     s.budget = 10 ** 12
     s._admit(now=3.0)
     assert s.queue == [] and "allocation failed" in s.results[2].refused
+
+
+def test_auto_slots_size_groups_by_resolution(monkeypatch):
+    """slots="auto": a group holds as many frames as fit the pixel budget (1 to 8), so
+    small frames batch and a frame that fills the GPU alone runs alone; the workspace
+    charged to the budget is that of the group's own slot count."""
+    monkeypatch.setattr(serve, "_Group", _FakeGroup)
+    _FakeGroup.fail_allocs = 0
+    p = seg.default_params()
+    s = serve.Server(p, hbm_budget_bytes=1 << 40, slots="auto", group_pixels=2_600_000)
+    assert [s.slots_for(h, w) for h, w in ((240, 320), (480, 640), (720, 1280), (1080, 1920), (2160, 3840))] == \
+        [8, 8, 2, 1, 1]
+    for i, (h, w) in enumerate(((480, 640), (720, 1280), (1080, 1920))):
+        s.submit(_req(i, h, w, arrival=0.0))
+    s._admit(now=0.0)
+    assert [g.B for g in s.groups] == [8, 2, 1]
+    assert s.used == sum(seg.workspace_bytes(g.B, g.H, g.W, p) for g in s.groups)
+    assert serve.Server(p, 1 << 40, slots=3).slots_for(1080, 1920) == 3
