@@ -352,28 +352,46 @@ def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
                        "backward_frac_of_hbm": byts["bwd"] * reps / tb / 1e9 / hbm}
     d.close()
 
-    # the mixed 64-stream workload: one batch context per resolution, each on its own CUDA stream
+    # the mixed 64-stream workload: one batch context per resolution, the three advanced
+    # by one CUDA graph launch per step (seg_group); each context's tile shape and
+    # schedule chosen by the autotuner on the group's own step frames (every candidate
+    # checked to give the same masks and cuts); against the same streams, each in a
+    # plain context of its own with the default (single-stream tuned) parameters
+    from paper_1008_0502_b300 import tune
     groups = [(24, 240, 320), (24, 480, 640), (16, 720, 1280)]
     nfr = 4
-    data, ctxs, plain = [], [], []
+    data, tuned, plain = [], [], []
     for gi, (nb, h, w) in enumerate(groups):
         clip = np.stack([f for f, _ in synth.clip_vga_frames(nfr + nb, h, w, seed=synth.SEED_BASE + 4 + gi)])
         # stream k of the group sees frames k .. k+nfr-1 of the group's clip
         fr = torch.from_numpy(np.stack([clip[t:t + nb] for t in range(nfr)])).cuda()  # (nfr, nb, h, w, 3)
-        sg = seg.Segmenter(h, w, p, batch=nb, stream=torch.cuda.Stream())
         data.append(fr)
-        ctxs.append((sg, sg.empty_outputs()))
+        tuned.append(tune.autotune_mincut(torch.cat([fr, fr]), p, batch=nb))
         plain.append([seg.Segmenter(h, w, p) for _ in range(nb)])
-    step = [0]
 
-    def batched_step():
-        t_ = step[0] % nfr
-        for (sg, o), fr in zip(ctxs, data):
-            sg.push_frame(fr[t_], *o)
-        step[0] += 1
+    def group_of(params):
+        ctxs = [seg.Segmenter(h, w, q, batch=nb, stream=torch.cuda.Stream())
+                for (nb, h, w), q in zip(groups, params)]
+        return ctxs, seg.Group(ctxs), [c.empty_outputs() for c in ctxs]
+
+    def run_group(params, steps):
+        ctxs, grp, outs = group_of(params)
+        step = [0]
+
+        def batched_step():
+            grp.push([fr[step[0] % nfr] for fr in data], outs)
+            step[0] += 1
+
+        t = timed(batched_step, steps)
+        codes = [c for c, _ in grp.sync()]
+        grp.close()
+        for c in ctxs:
+            c.close()
+        return t, max(codes, key=abs)
 
     steps = 12
-    tb = timed(batched_step, steps)
+    tb, code = run_group([r.params for r in tuned], steps)
+    tu, code_u = run_group([p] * len(groups), steps)
     pouts = [[sgp.empty_outputs() for sgp in grp] for grp in plain]
     pstep = [0]
 
@@ -386,12 +404,11 @@ def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
 
     tp = timed(plain_step, steps)
     n = sum(g[0] for g in groups)
-    codes = [sg.sync()[0] for sg, _ in ctxs]
     out["mixed64"] = {"streams": "24 x 320x240 + 24 x 640x480 + 16 x 1280x720", "frames_per_s": n * steps / tb,
-                      "plain_frames_per_s": n * steps / tp, "vs_plain": tp / tb, "steps": steps,
-                      "status": max(codes, key=abs)}
-    for sg, _ in ctxs:
-        sg.close()
+                      "launch": "one CUDA graph per step for the three batch contexts (seg_group)",
+                      "tuned": {f"{nb}x{w}x{h}": r.best for (nb, h, w), r in zip(groups, tuned)},
+                      "untuned_frames_per_s": n * steps / tu, "plain_frames_per_s": n * steps / tp,
+                      "vs_plain": tp / tb, "steps": steps, "status": max([code, code_u], key=abs)}
     for grp in plain:
         for sgp in grp:
             sgp.close()

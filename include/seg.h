@@ -94,6 +94,13 @@ typedef struct seg_params {
   int32_t gmm_update;      /* 1: a stream's EM starts from its previous frame's fitted mixtures (the
                               likelihood update of Sec. 2 / Sec. 6), the k-means start only on a
                               video's first frame; 0: every frame starts from the k-means start */
+  int32_t relabel_frontier; /* min cut schedule (results identical): 1 = the third and later fixpoint
+                              rounds of a global relabel (BFS from t) or of the final reach take
+                              only the tiles next to a tile that changed, from a queue compacted
+                              with warp ballots and spread over all CTAs; 0 = every CTA scans its
+                              own tiles for changed neighbours (0) */
+  int32_t cut_tile;        /* min cut tile shape (results identical; fixed for a context's life):
+                              0 = 32x16, 1 = 32x8, 2 = 64x8 nodes, one thread a node (0) */
 } seg_params;
 
 /* Fills *p with the defaults above.  Returns SEG_EINVAL if p is NULL. */
@@ -179,6 +186,65 @@ int seg_push_frame_host(seg_ctx* ctx, const uint8_t* rgb_host, float* saliency_h
  * SEG_ECAPACITY), or SEG_ECUDA.  *cycles (nullable) receives the last min-cut's
  * cycle count. */
 int seg_sync(seg_ctx* ctx, int* cycles);
+
+/* The last CUDA runtime call of this library that failed on the calling host
+ * thread (the call and CUDA's error name), "" if none: the detail behind
+ * SEG_ECUDA.  Owned by the library; valid until the next failure on the
+ * thread. */
+const char* seg_last_cuda_error(void);
+
+/* ---- groups: several contexts (e.g. batch contexts of different
+ * resolutions) advanced by one CUDA graph launch per frame step (many streams
+ * of uneven resolution in one launch; Sec. 7.1 processes one stream).
+ *
+ * seg_group_create captures every member's frame launch sequence (the one
+ * seg_push_frame runs) as parallel branches of one graph, on the members'
+ * own streams forked from and joined into `stream` (a cudaStream_t, not the
+ * legacy default stream).  A step (seg_group_push) writes every member's
+ * frame pointers through the graph's root node and launches the graph once on
+ * `stream`.  Results equal those of seg_push_frame on each member.  Members
+ * keep their state; their streams are ordered around every step, so
+ * seg_reset_stream, seg_set_stream_active or seg_sync on a member between
+ * steps apply in order.  The graph holds the members' parameters as at
+ * creation: after seg_set_barrier_timeout on a member, create the group
+ * again.  Destroy the group before its members; do not push frames to a
+ * member directly while its group has steps in flight.  No paper
+ * counterpart. */
+#define SEG_GROUP_MAX 16
+typedef struct seg_group seg_group;
+
+/* One member's frame of a step: device pointers laid out as seg_push_frame
+ * takes them for that member (rgb and mask required; sal, prior and cut
+ * nullable). */
+typedef struct seg_frame_io {
+  const uint8_t* rgb;
+  float* sal;
+  float* prior;
+  uint8_t* mask;
+  int64_t* cut;
+} seg_frame_io;
+
+/* ctxs: n distinct contexts (1 <= n <= SEG_GROUP_MAX), each on a stream of its
+ * own creation (not the legacy default stream), not pipelined, not profiling;
+ * the caller keeps ownership.  Synchronises the members' streams first.
+ * Errors: SEG_EINVAL, SEG_ENOMEM, SEG_ECUDA (capture or instantiation failed).
+ * *out is NULL on error. */
+int seg_group_create(void* stream, seg_ctx* const* ctxs, int n, seg_group** out);
+
+/* One frame step of every member: io[i] is member i's frame.  Enqueued on the
+ * group's stream after all work enqueued on the members' streams.  Errors:
+ * SEG_EINVAL (g or io NULL, a required pointer NULL), SEG_ECUDA. */
+int seg_group_push(seg_group* g, const seg_frame_io* io);
+
+/* Synchronises the group's stream and every member (seg_sync); codes[i] and
+ * cycles[i] (both nullable, n entries) receive each member's status and last
+ * cycle count.  Returns the first non-zero member status, SEG_OK, or
+ * SEG_EINVAL / SEG_ECUDA. */
+int seg_group_sync(seg_group* g, int* codes, int* cycles);
+
+/* Waits for the group's stream and frees the group (not its members).
+ * Errors: SEG_EINVAL (g NULL). */
+int seg_group_destroy(seg_group* g);
 
 /* Temporal state (Sec. 6: A_{t-1} and sigma^2_xi1(t-1), plus the frame index)
  * as a byte string: a 16-byte header of four uint32 (0x53454732, H, W, B);

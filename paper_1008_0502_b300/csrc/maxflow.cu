@@ -38,11 +38,36 @@
 
 #include "seg_internal.cuh"
 
+// The tile shape of this copy (seg_params.cut_tile; the build compiles the file
+// once per shape, each copy in a namespace of its own).
+#ifndef MF_SHAPE
+#define MF_SHAPE 0
+#endif
+#if MF_SHAPE == 0
+#define MF_TW 32
+#define MF_TH 16
+#define MF_NS mf_s32x16
+#elif MF_SHAPE == 1
+#define MF_TW 32
+#define MF_TH 8
+#define MF_NS mf_s32x8
+#elif MF_SHAPE == 2
+#define MF_TW 64
+#define MF_TH 8
+#define MF_NS mf_s64x8
+#else
+#error "MF_SHAPE must be 0, 1 or 2"
+#endif
+#define MF_THREADS (MF_TW * MF_TH)
+#define MF_MINB (1024 / MF_THREADS)  // CTAs per SM the kernels are built for (64 registers a thread)
+
 #define MF_HX (MF_TW + 2)
 #define MF_HY (MF_TH + 2)
 #define MF_HN (MF_HX * MF_HY)
 #define MF_ROUND_CAP (1 << 20)  // fixpoint rounds per cut; uniform across CTAs
 #define MF_ON_CACHE 512         // frames whose run flags each CTA keeps in shared memory
+
+namespace MF_NS {
 
 // Directions E W S N SE NW SW NE; the opposite of d is d ^ 1.  The kernel is
 // instantiated for 4 and 8 neighbours so every direction loop unrolls and these
@@ -68,6 +93,7 @@ struct MFShared {
   long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
   unsigned char onf[MF_ON_CACHE];  // the frames' run flags (a.on) when there are at most MF_ON_CACHE
   int on_mode;  // 0: every frame runs, 1: some frame does not (flags in onf), 2: as 1 with the flags in a.on
+  unsigned dirs;  // frontier rounds: directions of the neighbour tiles a tile's fixpoint changed
 };
 
 __device__ __forceinline__ long long mf_now() { return seg_now(); }
@@ -132,8 +158,8 @@ __device__ __forceinline__ unsigned mf_tile_rows(const MFArgs& a, const MFShared
 __device__ unsigned mf_dirty_mask(const MFArgs& a, MFShared& s, int k0, int since) {
   if (threadIdx.x == 0) s.dmask = 0u;
   __syncthreads();
-  if (threadIdx.x < 9 * 32) {
-    const int i = threadIdx.x / 9, n = threadIdx.x - 9 * i;
+  for (int j = threadIdx.x; j < 9 * 32; j += blockDim.x) {
+    const int i = j / 9, n = j - 9 * i;
     const int k = k0 + i * (int)gridDim.x;
     if (k < a.ntx * a.nty) {
       const int ty = k / a.ntx, tx = k - ty * a.ntx;
@@ -146,6 +172,53 @@ __device__ unsigned mf_dirty_mask(const MFArgs& a, MFShared& s, int k0, int sinc
   return s.dmask;
 }
 
+// ---------------------------------------------------------------- tile frontier
+// Block-uniform: bit d set if a node of the tile that changed lies in the halo of
+// the neighbour tile in direction d (E W S N SE NW SW NE, as mf_dx / mf_dy): the
+// column or row facing it, or the corner node facing a diagonal neighbour.
+template <int ND>
+__device__ __forceinline__ unsigned mf_rim_dirs(MFShared& s, bool changed, int lx, int ly) {
+  unsigned d = 0u;
+  if (changed) {
+    d = (lx == MF_TW - 1 ? 1u : 0u) | (lx == 0 ? 2u : 0u) | (ly == MF_TH - 1 ? 4u : 0u) | (ly == 0 ? 8u : 0u);
+    if (ND == 8)
+      d |= ((d & 5u) == 5u ? 16u : 0u) | ((d & 10u) == 10u ? 32u : 0u) | ((d & 6u) == 6u ? 64u : 0u) |
+           ((d & 9u) == 9u ? 128u : 0u);
+  }
+  d = __reduce_or_sync(0xffffffffu, d);
+  if ((threadIdx.x & 31) == 0 && d) atomicOr(&s.dirs, d);
+  __syncthreads();  // (also orders the next tile's reuse of shared memory)
+  return s.dirs;
+}
+
+// Block-uniform (warp 0 works): appends the neighbour tiles in directions dirs to
+// the queue of the round with this epoch.  A tile is queued at most once a round:
+// the lane whose atomicMax first raises the tile's stamp to the epoch claims it.
+// The claiming lanes of the warp take consecutive slots by their rank in the
+// ballot, reserved with one atomicAdd on the round's counter (which is also the
+// round's termination word: no tile queued, fixpoint reached).
+template <int ND>
+__device__ __forceinline__ void mf_enqueue(const MFArgs& a, unsigned dirs, int tx, int ty, unsigned epoch,
+                                           int ntiles) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  bool claim = false;
+  int t = 0;
+  if (lane < ND && ((dirs >> lane) & 1u)) {
+    const int nx = tx + mf_dx(lane), ny = ty + mf_dy(lane);
+    if (nx >= 0 && nx < a.ntx && ny >= 0 && ny < a.nty) {
+      t = ny * a.ntx + nx;
+      claim = atomicMax(&a.tqs[t], (int)epoch) < (int)epoch;
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, claim);
+  if (!m) return;
+  unsigned base = 0u;
+  if (lane == 0) base = atomicAdd(&a.flags[epoch % 3], (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (claim) a.tq[(size_t)(epoch & 1u) * ntiles + base + __popc(m & ((1u << lane) - 1u))] = t;
+}
+
 // ---------------------------------------------------------------- BFS to the sink
 // d(u) = 1 if u has residual to t, else 1 + min over residual arcs u->v of d(v):
 // relaxed to the local fixpoint with the halo fixed at its current global value.
@@ -155,8 +228,10 @@ __device__ unsigned mf_dirty_mask(const MFArgs& a, MFShared& s, int k0, int sinc
 // nodes with a residual arc to t, INF elsewhere) and the residual bitmasks are
 // formed here from rt and r (no separate pass and grid barrier), and every node
 // of the tile is written.
-template <int ND>
-__device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
+// Q: return the directions of the neighbours whose halo changed (mf_rim_dirs)
+// instead of whether any rim node changed.
+template <int ND, bool Q>
+__device__ unsigned mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
@@ -181,6 +256,7 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool f
     }
   }
   __syncthreads();
+  if (Q && threadIdx.x == 0) s.dirs = 0u;  // (every thread read the last tile's before the barrier)
   const int h0 = s.h[hi];
   bool any = false;
   for (;;) {
@@ -200,6 +276,7 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool f
   }
   if (valid && (any || first)) a.h[g] = s.h[hi];
   // only a change on the tile's rim is seen by other tiles (their halo)
+  if (Q) return mf_rim_dirs<ND>(s, valid && s.h[hi] != h0, lx, ly);
   const bool rim = ly == 0 || ly == MF_TH - 1 || lx == 0 || lx == MF_TW - 1;
   return __syncthreads_or(valid && rim && s.h[hi] != h0) != 0;  // (also orders the next tile's reuse)
 }
@@ -209,8 +286,8 @@ __device__ bool mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bool f
 // first: the first round -- the seeds (z = 1 where excess remains) and the
 // residual bitmasks of the tile and its halo come from e and r (no separate pass
 // and grid barrier), and every node of the tile is written.
-template <int ND>
-__device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
+template <int ND, bool Q>
+__device__ unsigned mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
@@ -236,6 +313,7 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool
   const bool valid = gy < a.H && gx < a.W && ((rows >> (ly + 1)) & 1u);
   const int hi = (ly + 1) * MF_HX + lx + 1;
   __syncthreads();
+  if (Q && threadIdx.x == 0) s.dirs = 0u;
   const unsigned char z0 = s.z[hi];
   bool any = false;
   for (;;) {
@@ -257,6 +335,7 @@ __device__ bool mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool
   }
   if (valid && (any || first)) a.z[gy * a.W + gx] = s.z[hi];
   if (valid && first) a.rm[gy * a.W + gx] = s.b[hi];
+  if (Q) return mf_rim_dirs<ND>(s, valid && s.z[hi] != z0, lx, ly);
   const bool rim = ly == 0 || ly == MF_TH - 1 || lx == 0 || lx == MF_TW - 1;
   return __syncthreads_or(valid && rim && s.z[hi] != z0) != 0;  // (also orders the next tile's reuse)
 }
@@ -368,7 +447,7 @@ __device__ __forceinline__ bool cap_ok(int c) { return c >= 0 && c <= (1 << 24);
 // The whole cut, for one CTA.  SKIP: some frame of the batch is not run (its
 // rows are left out); without it every test of the run flags folds away and the
 // code is that of a single frame.
-template <int ND, bool SKIP>
+template <int ND, bool SKIP, bool Q>
 __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   const int N = a.N, W = a.W, H = a.H;
   const int nthr = gridDim.x * blockDim.x;
@@ -392,6 +471,7 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
         bool any;
         mf_tile_rows(a, s, all_on, (k / a.ntx) * MF_TH, &any);
         a.tstamp[k] = -2;
+        if (Q) a.tqs[k] = -1;
         a.tact[k] = any ? 1 : 0;
       }
     __syncthreads();
@@ -458,6 +538,7 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
     bool any;
     mf_tile_rows(a, s, all_on, (t / a.ntx) * MF_TH, &any);
     a.tstamp[t] = -2;
+    if (Q) a.tqs[t] = -1;
     a.tact[t] = any ? 1 : 0;
   }
   if (!mf_grid_sync(a, s)) return;
@@ -506,22 +587,40 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
     if (relabel || since_gr >= 4 * a.gr_every) {
       relabel = false;
       since_gr = 0;
-      for (bool first = true;; first = false) {
+      for (int rnd = 0;; ++rnd) {
+        const bool first = rnd == 0;
         mf_flag_begin(a, epoch);
         bool ch = false;
-        unsigned dm = 0u;
-        for (int k = blockIdx.x, i = 0; k < ntiles; k += gridDim.x, ++i) {
-          int tx = k % a.ntx, ty = k / a.ntx;
-          if (!first) {
-            if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
-            if (!((dm >> (i & 31)) & 1u)) continue;
+        if (Q && rnd >= 2) {  // the tiles the previous round queued, spread over the CTAs
+          const int cnt = (int)mf_flag_read(a, epoch - 1);
+          const int* q = a.tq + (size_t)((epoch - 1) & 1u) * ntiles;
+          for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+            const int k = q[i], tx = k % a.ntx, ty = k / a.ntx;
+            bool any;
+            const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+            if (!any) continue;
+            const unsigned d = mf_tile_bfs<ND, true>(a, s, tx, ty, false, rows);
+            if (d) mf_enqueue<ND>(a, d, tx, ty, epoch, ntiles);
           }
-          bool any;
-          const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
-          if (!any) continue;
-          if (mf_tile_bfs<ND>(a, s, tx, ty, first, rows)) {
-            ch = true;
-            if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
+        } else {
+          unsigned dm = 0u;
+          for (int k = blockIdx.x, i = 0; k < ntiles; k += gridDim.x, ++i) {
+            int tx = k % a.ntx, ty = k / a.ntx;
+            if (!first) {
+              if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
+              if (!((dm >> (i & 31)) & 1u)) continue;
+            }
+            bool any;
+            const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+            if (!any) continue;
+            const unsigned d = mf_tile_bfs<ND, Q>(a, s, tx, ty, first, rows);
+            if (!d) continue;
+            if (Q && !first) {  // (claims start after a barrier: every stamp was reset by then)
+              mf_enqueue<ND>(a, d, tx, ty, epoch, ntiles);
+            } else {
+              ch = true;
+              if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
+            }
           }
         }
         if (ch && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
@@ -584,22 +683,40 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
       if ((threadIdx.x & 31) == 0 && flow_t != 0) atomicAdd(&a.cut_acc[fb], (unsigned long long)flow_t);
     }
   }
-  for (bool first = true;; first = false) {
+  for (int rnd = 0;; ++rnd) {
+    const bool first = rnd == 0;
     mf_flag_begin(a, epoch);
     bool ch = false;
-    unsigned dm = 0u;
-    for (int k = blockIdx.x, i = 0; k < ntiles; k += gridDim.x, ++i) {
-      int tx = k % a.ntx, ty = k / a.ntx;
-      if (!first) {
-        if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
-        if (!((dm >> (i & 31)) & 1u)) continue;
+    if (Q && rnd >= 2) {
+      const int cnt = (int)mf_flag_read(a, epoch - 1);
+      const int* q = a.tq + (size_t)((epoch - 1) & 1u) * ntiles;
+      for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int k = q[i], tx = k % a.ntx, ty = k / a.ntx;
+        bool any;
+        const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+        if (!any) continue;
+        const unsigned d = mf_tile_reach<ND, true>(a, s, tx, ty, false, rows);
+        if (d) mf_enqueue<ND>(a, d, tx, ty, epoch, ntiles);
       }
-      bool any;
-      const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
-      if (!any) continue;
-      if (mf_tile_reach<ND>(a, s, tx, ty, first, rows)) {
-        ch = true;
-        if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
+    } else {
+      unsigned dm = 0u;
+      for (int k = blockIdx.x, i = 0; k < ntiles; k += gridDim.x, ++i) {
+        int tx = k % a.ntx, ty = k / a.ntx;
+        if (!first) {
+          if ((i & 31) == 0) dm = mf_dirty_mask(a, s, k, (int)epoch - 1);
+          if (!((dm >> (i & 31)) & 1u)) continue;
+        }
+        bool any;
+        const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
+        if (!any) continue;
+        const unsigned d = mf_tile_reach<ND, Q>(a, s, tx, ty, first, rows);
+        if (!d) continue;
+        if (Q && !first) {
+          mf_enqueue<ND>(a, d, tx, ty, epoch, ntiles);
+        } else {
+          ch = true;
+          if (threadIdx.x == 0) a.tstamp[k] = (int)epoch;
+        }
       }
     }
     if (ch && threadIdx.x == 0) atomicAdd(&a.flags[epoch % 3], 1u);
@@ -646,11 +763,24 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   }
 }
 
+// One frame: only the schedule varies.
 template <int ND>
-__global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
+__global__ void __launch_bounds__(MF_THREADS, MF_MINB) k_maxflow(MFArgs a) {
+  __shared__ MFShared s;
+  if (a.frontier)
+    mf_run<ND, false, true>(a, s);
+  else
+    mf_run<ND, false, false>(a, s);
+}
+
+// A stack of frames (a batch context): empty slots are left out when a.on marks
+// some.  A kernel of its own, so that the single-frame code keeps its own
+// register allocation.
+template <int ND>
+__global__ void __launch_bounds__(MF_THREADS, MF_MINB) k_maxflow_batch(MFArgs a) {
   __shared__ MFShared s;
   int off = 0;
-  if (a.on) {  // a batch: its frames' run flags, read once per CTA
+  if (a.on) {  // its frames' run flags, read once per CTA
     for (int f = threadIdx.x; f < a.nframes; f += blockDim.x) {
       const unsigned char v = a.on[f];
       if (f < MF_ON_CACHE) s.onf[f] = v;
@@ -660,21 +790,25 @@ __global__ void __launch_bounds__(MF_THREADS, 2) k_maxflow(MFArgs a) {
     if (threadIdx.x == 0) s.on_mode = !off ? 0 : (a.nframes <= MF_ON_CACHE ? 1 : 2);
     __syncthreads();
   }
-  if (off)
-    mf_run<ND, true>(a, s);
-  else
-    mf_run<ND, false>(a, s);
+  if (off) {
+    if (a.frontier) mf_run<ND, true, true>(a, s);
+    else mf_run<ND, true, false>(a, s);
+  } else {
+    if (a.frontier) mf_run<ND, false, true>(a, s);
+    else mf_run<ND, false, false>(a, s);
+  }
 }
 
 // ---------------------------------------------------------------- host side
-size_t mf_bytes(int H, int W, int ndir, int nframes) {
+size_t bytes(int H, int W, int ndir, int nframes) {
   size_t N = (size_t)H * W;
   size_t nt = (size_t)((W + MF_TW - 1) / MF_TW) * ((H + MF_TH - 1) / MF_TH);
   return seg_align(N * 4) * 3 + seg_align(N * 4 * ndir) + seg_align(N) * 2 + seg_align(8 * nframes) +
-         seg_align(16) + seg_align(nt * 4) + seg_align(nt) + seg_align(sizeof(GridBar));
+         seg_align(16) + seg_align(nt * 4) + seg_align(nt) + seg_align(sizeof(GridBar)) + seg_align(nt * 8) +
+         seg_align(nt * 4);
 }
 
-void mf_bind(MFWS& m, char* base, int H, int W, int ndir, int nframes) {
+void bind(MFWS& m, char* base, int H, int W, int ndir, int nframes) {
   size_t N = (size_t)H * W, off = 0;
   auto take = [&](size_t b) {
     char* p = base + off;
@@ -694,18 +828,24 @@ void mf_bind(MFWS& m, char* base, int H, int W, int ndir, int nframes) {
   m.tstamp = (int*)take(nt * 4);
   m.tact = (unsigned char*)take(nt);
   m.bar = (GridBar*)take(sizeof(GridBar));
+  m.tq = (int*)take(nt * 8);
+  m.tqs = (int*)take(nt * 4);
 }
 
-int mf_grid_size(int H, int W, int* grid) {
+int grid_size(int H, int W, int* grid) {
   int dev, nsm, per_sm = 0, coop = 0;
   SEG_CUDA_TRY(cudaGetDevice(&dev));
   SEG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   SEG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return SEG_ECUDA;
   SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_maxflow<8>, MF_THREADS, 0));
-  int per_sm4 = 0;
-  SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, k_maxflow<4>, MF_THREADS, 0));
-  per_sm = per_sm4 < per_sm ? per_sm4 : per_sm;
+  const void* others[3] = {(const void*)k_maxflow<4>, (const void*)k_maxflow_batch<8>,
+                           (const void*)k_maxflow_batch<4>};
+  for (const void* k : others) {
+    int n = 0;
+    SEG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, MF_THREADS, 0));
+    per_sm = n < per_sm ? n : per_sm;
+  }
   if (per_sm < 1) return SEG_ECUDA;
   const int ntx = (W + MF_TW - 1) / MF_TW, nty = (H + MF_TH - 1) / MF_TH;
   const int ntiles = ntx * nty, ntc = ((ntx + 1) / 2) * ((nty + 1) / 2);  // tiles; of the largest colour
@@ -714,7 +854,8 @@ int mf_grid_size(int H, int W, int* grid) {
   // most tiles.  With every co-resident CTA those counts are at their minimum
   // (rp per phase, ra per round); the grid is the fewest CTAs that still reach
   // both (fewer arrivals per barrier, and idle SMs for concurrent work), e.g.
-  // 640 x 480: 150 tiles per colour, 600 in all -> 200 CTAs (1 and 3 tiles).
+  // 640 x 480 in 32x16 tiles: 150 tiles per colour, 600 in all -> 200 CTAs (1
+  // and 3 tiles).
   const int gmax = per_sm * nsm;
   const int rp = (ntc + gmax - 1) / gmax, ra = (ntiles + gmax - 1) / gmax;
   const int gp = (ntc + rp - 1) / rp, ga = (ntiles + ra - 1) / ra;
@@ -722,57 +863,59 @@ int mf_grid_size(int H, int W, int* grid) {
   return SEG_OK;
 }
 
-int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
-              const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
-              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              long long timeout_ns, const SegIO* io, int* flow, unsigned char* warm, bool words_zeroed, bool init_done,
-              const uint8_t* on) {
+int launch(const MFWS& m, const MFCall& c) {
+  if (c.H % m.nframes) return SEG_EINVAL;
   MFArgs a;
   memset(&a, 0, sizeof(a));
-  a.on = on;
-  a.flow = flow;
-  a.warm = warm;
-  if (H % m.nframes) return SEG_EINVAL;
+  a.on = c.on;
+  a.frontier = c.frontier ? 1 : 0;
+  a.tq = m.tq;
+  a.tqs = m.tqs;
+  a.flow = c.flow;
+  a.warm = c.warm;
   a.nframes = m.nframes;
-  a.frame_h = H / m.nframes;
-  a.H = H;
-  a.W = W;
-  a.N = H * W;
-  a.ndir = nbr;
-  a.ntx = (W + MF_TW - 1) / MF_TW;
-  a.nty = (H + MF_TH - 1) / MF_TH;
-  a.cs = cs;
-  a.ct = ct;
-  a.ncap = ncap;
+  a.frame_h = c.H / m.nframes;
+  a.H = c.H;
+  a.W = c.W;
+  a.N = c.H * c.W;
+  a.ndir = c.nbr;
+  a.ntx = (c.W + MF_TW - 1) / MF_TW;
+  a.nty = (c.H + MF_TH - 1) / MF_TH;
+  a.cs = c.cs;
+  a.ct = c.ct;
+  a.ncap = c.ncap;
   a.e = m.e;
   a.h = m.h;
   a.rt = m.rt;
   a.r = m.r;
   a.rm = m.rm;
   a.z = m.z;
-  a.mask_out = mask_out;
-  a.mask_state = mask_state;
-  a.cut_out = cut_out;
-  a.io = io;
+  a.mask_out = c.mask_out;
+  a.mask_state = c.mask_state;
+  a.cut_out = c.cut_out;
+  a.io = c.io;
   a.cut_acc = m.cut_acc;
   a.flags = m.flags;
   a.tstamp = m.tstamp;
   a.tact = m.tact;
   a.bar = m.bar;
-  a.status = status;
-  a.max_cycles = max_cycles;
-  a.gr_every = gr_every < 1 ? 1 : gr_every;
-  a.local_iters = local_iters < 1 ? 1 : local_iters;
-  a.timeout_ns = timeout_ns;
-  a.init_done = init_done ? 1 : 0;
-  if (!words_zeroed) {  // (else the caller's frame-start kernel has zeroed them)
-    SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, st));
-    SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, st));
-    SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), st));
+  a.status = c.status;
+  a.max_cycles = c.max_cycles;
+  a.gr_every = c.gr_every < 1 ? 1 : c.gr_every;
+  a.local_iters = c.local_iters < 1 ? 1 : c.local_iters;
+  a.timeout_ns = c.timeout_ns;
+  a.init_done = c.init_done ? 1 : 0;
+  if (!c.words_zeroed) {  // (else the caller's frame-start kernel has zeroed them)
+    SEG_CUDA_TRY(cudaMemsetAsync(m.cut_acc, 0, 8 * m.nframes, c.st));
+    SEG_CUDA_TRY(cudaMemsetAsync(m.flags, 0, 16, c.st));
+    SEG_CUDA_TRY(cudaMemsetAsync(m.bar, 0, sizeof(GridBar), c.st));
   }
   void* args[] = {&a};
-  SEG_CUDA_TRY(cudaLaunchCooperativeKernel(nbr == 8 ? (const void*)k_maxflow<8> : (const void*)k_maxflow<4>,
-                                           dim3(grid), dim3(MF_THREADS), args,
-                                           0, st));
+  const void* fn = m.nframes > 1
+                       ? (c.nbr == 8 ? (const void*)k_maxflow_batch<8> : (const void*)k_maxflow_batch<4>)
+                       : (c.nbr == 8 ? (const void*)k_maxflow<8> : (const void*)k_maxflow<4>);
+  SEG_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(c.grid), dim3(MF_THREADS), args, 0, c.st));
   return SEG_OK;
 }
+
+}  // namespace MF_NS

@@ -22,12 +22,13 @@
 #define SEG_STATIC_MAX_DEVICES 64
 
 // Workspace bytes the min-cut needs per pixel at the 8-neighbourhood (excess,
-// height, sink residual, 8 directed residuals, two flag bytes), plus one byte
-// per pixel for the per-tile words (5 bytes a 32x16 tile; even a one-row or
-// one-column grid, one tile per 32 or 16 pixels, stays under that), the
-// padding of every array to 256 bytes, and the status words.
+// height, sink residual, 8 directed residuals, two flag bytes), plus two bytes
+// per pixel for the per-tile words (17 bytes a 32x16 tile: stamp, flag, two
+// queue slots and a queue stamp; even a one-column grid, one tile per 16
+// pixels, stays under that), the padding of every array to 256 bytes, and the
+// status words.
 static const size_t kStaticBytes =
-    4 * 256 + (size_t)SEG_MINCUT_STATIC_MAX_PIXELS * (3 * 4 + 8 * 4 + 2 + 1) + 8192;
+    6 * 256 + (size_t)SEG_MINCUT_STATIC_MAX_PIXELS * (3 * 4 + 8 * 4 + 2 + 2) + 8192;
 
 static __device__ __align__(256) unsigned char g_mincut_scratch[kStaticBytes];
 
@@ -54,26 +55,41 @@ extern "C" int seg_mincut_grid_static(void* stream, int H, int W, int nbr, const
   if (H < 1 || W < 1 || (nbr != 4 && nbr != 8)) return SEG_EINVAL;
   if ((long long)H * W > SEG_MINCUT_STATIC_MAX_PIXELS) return SEG_EINVAL;
   if (!cs || !ct || !ncap || !mask || !cut) return SEG_EINVAL;
-  size_t mfb = mf_bytes(H, W, nbr);
+  size_t mfb = mf_bytes(H, W, nbr, 1, 0);  // (32x16 tiles: the size bound above assumes them)
   if (mfb + 512 > kStaticBytes) return SEG_EINVAL;
   char* base = nullptr;
   int rc = scratch_on_current_device(&base);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   int grid = 0;
-  rc = mf_grid_size(H, W, &grid);
+  rc = mf_grid_size(H, W, 0, &grid);
   if (rc) return rc;
   MFWS m;
-  mf_bind(m, base, H, W, nbr);
+  mf_bind(m, base, H, W, nbr, 1, 0);
   int* status = (int*)(base + seg_align(mfb));
   // every array the kernel reads before writing starts at zero: status words
   // here, the barrier, round flags and cut accumulator inside mf_launch
   if (cudaMemsetAsync(status, 0, 32, st) != cudaSuccess) return SEG_ECUDA;
   seg_params d;
   seg_default_params(&d);
-  rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, (long long*)cut, status,
-                 max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every, d.local_iters,
-                 1000LL * d.barrier_timeout_us);
+  MFCall k;
+  k.st = st;
+  k.grid = grid;
+  k.H = H;
+  k.W = W;
+  k.nbr = nbr;
+  k.cs = cs;
+  k.ct = ct;
+  k.ncap = ncap;
+  k.mask_out = mask;
+  k.cut_out = (long long*)cut;
+  k.status = status;
+  k.max_cycles = max_cycles > 0 ? max_cycles : d.max_cycles;
+  k.gr_every = d.global_relabel_every;
+  k.local_iters = d.local_iters;
+  k.timeout_ns = 1000LL * d.barrier_timeout_us;
+  k.frontier = d.relabel_frontier;
+  rc = mf_launch(m, k, 0);
   if (rc) return rc;
   int hs[4] = {0, 0, 0, 0};
   if (cudaStreamSynchronize(st) != cudaSuccess) return SEG_ECUDA;

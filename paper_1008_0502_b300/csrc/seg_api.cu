@@ -5,6 +5,7 @@
 // allocates device memory except seg_create and the standalone
 // seg_mincut_grid.
 #include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 
 #include "seg_internal.cuh"
@@ -57,8 +58,18 @@ extern "C" int seg_default_params(seg_params* p) {
   p->barrier_timeout_us = 4000000;
   p->kmeans_iters = 3;
   p->gmm_update = 1;
+  p->relabel_frontier = 0;
+  p->cut_tile = 0;
   return SEG_OK;
 }
+
+static thread_local char g_last_cuda_error[256];
+
+void seg_note_cuda_error(cudaError_t e, const char* call) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s in %s", cudaGetErrorName(e), call);
+}
+
+extern "C" const char* seg_last_cuda_error(void) { return g_last_cuda_error; }
 
 extern "C" const char* seg_strerror(int code) {
   switch (code) {
@@ -91,6 +102,8 @@ int seg_check_params(const seg_params* p, int H, int W) {
   if (p->max_cycles < 1 || p->global_relabel_every < 1 || p->local_iters < 1) return SEG_EINVAL;
   if (p->barrier_timeout_us < 1 || p->barrier_timeout_us > 60000000) return SEG_EINVAL;
   if (p->kmeans_iters < 0 || p->kmeans_iters > 100 || (p->gmm_update != 0 && p->gmm_update != 1)) return SEG_EINVAL;
+  if (p->relabel_frontier != 0 && p->relabel_frontier != 1) return SEG_EINVAL;
+  if (p->cut_tile < 0 || p->cut_tile >= SEG_CUT_TILES) return SEG_EINVAL;
   if (p->gmm_components < 1 || p->gmm_components > SEG_MAX_GMM || p->em_iters < 0 || p->em_iters > 100)
     return SEG_EINVAL;
   return SEG_OK;
@@ -133,7 +146,7 @@ static int arena_layout(SalWS& sal, int B, int H, int W, const seg_params& p, Ar
   L.io = take(sizeof(SegIO));
   L.flow = take(4 * BN * nk);
   L.warm = take(B);
-  L.mf = take(mf_bytes(B * H, W, p.neighbourhood, B));
+  L.mf = take(mf_bytes(B * H, W, p.neighbourhood, B, p.cut_tile));
   L.gmm = take((size_t)B * 2 * sizeof(GmmDev));
   L.empart = take((size_t)B * 2 * sizeof(double) * pt_em_part_doubles(H, W));
   L.emcnt = take((size_t)B * 2 * sizeof(unsigned));
@@ -222,7 +235,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   c->slot_on = (uint8_t*)(base + L.slots);
   c->sal.on = B > 1 ? c->slot_on : nullptr;  // (a single stream is always on)
   c->warm = (unsigned char*)(base + o_warm);
-  mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B);
+  mf_bind(c->mf, base + o_mf, B * H, W, p->neighbourhood, B, p->cut_tile);
   int* lut = (int*)malloc(sizeof(int) * 766 * 2);
   if (!lut) {
     cudaFree(base);
@@ -242,7 +255,7 @@ extern "C" int seg_create_batch(void* stream, int B, int H, int W, const seg_par
   ok = ok && cudaMemset(c->gmm_valid, 0, (size_t)B * 2 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMemset(c->slot_on, 1, (size_t)B) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&c->status_host, 32) == cudaSuccess;
-  ok = ok && mf_grid_size(B * H, W, &c->mf_grid) == SEG_OK;
+  ok = ok && mf_grid_size(B * H, W, p->cut_tile, &c->mf_grid) == SEG_OK;
   if (!ok) {
     if (c->status_host) cudaFreeHost(c->status_host);
     cudaFree(base);
@@ -322,23 +335,39 @@ extern "C" int seg_reset_stream(seg_ctx* c, int b) {
 static int run_mincut(seg_ctx* c, const int32_t* cs, const int32_t* ct, const int32_t* ncap,
                       uint8_t* mask, uint8_t* mask_state, int64_t* cut, bool init_done = false) {
   // the per-stream path (mask_state set) warm-starts from the stream's last cut
-  int* flow = (mask_state && c->p.warm_start) ? c->flow : nullptr;
-  unsigned char* warm = flow ? c->warm : nullptr;
-  if (c->io_mode)  // mask and cut come from the frame's SegIO; k_set_io zeroed the words
-    return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap,
-                     nullptr, mask_state, nullptr, c->status, c->p.max_cycles, c->p.global_relabel_every,
-                     c->p.local_iters, 1000LL * c->p.barrier_timeout_us, c->io, flow, warm, true, init_done,
-                     c->sal.on);
-  return mf_launch(c->stream, c->mf, c->mf_grid, c->B * c->H, c->W, c->p.neighbourhood, cs, ct, ncap, mask,
-                   mask_state, (long long*)(cut ? cut : c->cut_buf), c->status, c->p.max_cycles,
-                   c->p.global_relabel_every, c->p.local_iters, 1000LL * c->p.barrier_timeout_us, nullptr, flow,
-                   warm, false, init_done, c->sal.on);
+  MFCall m;
+  m.st = c->stream;
+  m.grid = c->mf_grid;
+  m.H = c->B * c->H;
+  m.W = c->W;
+  m.nbr = c->p.neighbourhood;
+  m.cs = cs;
+  m.ct = ct;
+  m.ncap = ncap;
+  m.mask_state = mask_state;
+  m.status = c->status;
+  m.max_cycles = c->p.max_cycles;
+  m.gr_every = c->p.global_relabel_every;
+  m.local_iters = c->p.local_iters;
+  m.timeout_ns = 1000LL * c->p.barrier_timeout_us;
+  m.flow = (mask_state && c->p.warm_start) ? c->flow : nullptr;
+  m.warm = m.flow ? c->warm : nullptr;
+  m.init_done = init_done;
+  m.on = c->sal.on;
+  m.frontier = c->p.relabel_frontier;
+  if (c->io_mode) {  // mask and cut come from the frame's SegIO; k_set_io zeroed the words
+    m.io = c->io;
+    m.words_zeroed = true;
+  } else {
+    m.mask_out = mask;
+    m.cut_out = (long long*)(cut ? cut : c->cut_buf);
+  }
+  return mf_launch(c->mf, m, c->p.cut_tile);
 }
 
 // The launch sequence of one frame.  With c->io_mode set (graph capture) every
 // frame pointer is nullptr and the kernels read them from c->io.
-static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, uint8_t* mask,
-                         int64_t* cut) {
+int seg_ctx_push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, uint8_t* mask, int64_t* cut) {
   int rc = sal_launch(c, rgb, s, false);
   if (!rc) rc = pt_launch_back(c, s, pr, rgb);
   if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, cut, true);
@@ -346,17 +375,8 @@ static int push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, ui
 }
 
 // Starts a replay of the captured frame: records the frame's pointers and zeroes
-// the per-frame words the graph's kernels accumulate into (frame maxima of
-// r+g+b, the min cut's per-frame cut sums, work flags and barrier counter), in
-// place of memset nodes inside the graph.
-struct FrameWords {
-  int* smax;
-  int B;
-  unsigned long long* cut_acc;
-  unsigned int* flags;
-  GridBar* bar;
-};
-
+// the per-frame words the graph's kernels accumulate into (FrameWords), in place
+// of memset nodes inside the graph.
 __global__ void k_set_io(SegIO* io, SegIO v, FrameWords w) {
   const int t = threadIdx.x;
   if (t == 0) {
@@ -388,7 +408,7 @@ static void build_graph(seg_ctx* c) {
     return;
   }
   c->io_mode = 1;
-  int rc = push_launches(c, nullptr, nullptr, nullptr, nullptr, nullptr);
+  int rc = seg_ctx_push_launches(c, nullptr, nullptr, nullptr, nullptr, nullptr);
   c->io_mode = 0;
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (rc || e != cudaSuccess || !g) {
@@ -865,21 +885,37 @@ extern "C" int seg_mincut_grid(void* stream, int H, int W, int nbr, const int32_
   seg_params d;
   seg_default_params(&d);
   int grid = 0;
-  int rc = mf_grid_size(H, W, &grid);
+  int rc = mf_grid_size(H, W, d.cut_tile, &grid);
   if (rc) return rc;
-  size_t mfb = mf_bytes(H, W, nbr);
+  size_t mfb = mf_bytes(H, W, nbr, 1, d.cut_tile);
   char* base = nullptr;
   if (cudaMalloc((void**)&base, seg_align(mfb) + 256) != cudaSuccess) return SEG_ENOMEM;
   MFWS m;
-  mf_bind(m, base, H, W, nbr);
+  mf_bind(m, base, H, W, nbr, 1, d.cut_tile);
   int* status = (int*)(base + seg_align(mfb));
   long long* cut_tmp = (long long*)(base + seg_align(mfb) + 128);
   rc = SEG_OK;
   if (cudaMemsetAsync(status, 0, 32, st) != cudaSuccess) rc = SEG_ECUDA;
-  if (!rc)
-    rc = mf_launch(st, m, grid, H, W, nbr, cs, ct, ncap, mask, nullptr, cut ? (long long*)cut : cut_tmp,
-                   status, max_cycles > 0 ? max_cycles : d.max_cycles, d.global_relabel_every,
-                   d.local_iters, 1000LL * d.barrier_timeout_us);
+  if (!rc) {
+    MFCall k;
+    k.st = st;
+    k.grid = grid;
+    k.H = H;
+    k.W = W;
+    k.nbr = nbr;
+    k.cs = cs;
+    k.ct = ct;
+    k.ncap = ncap;
+    k.mask_out = mask;
+    k.cut_out = cut ? (long long*)cut : cut_tmp;
+    k.status = status;
+    k.max_cycles = max_cycles > 0 ? max_cycles : d.max_cycles;
+    k.gr_every = d.global_relabel_every;
+    k.local_iters = d.local_iters;
+    k.timeout_ns = 1000LL * d.barrier_timeout_us;
+    k.frontier = d.relabel_frontier;
+    rc = mf_launch(m, k, d.cut_tile);
+  }
   int hs[4] = {0, 0, 0, 0};
   if (cudaStreamSynchronize(st) != cudaSuccess) rc = SEG_ECUDA;
   if (!rc && cudaMemcpy(hs, status, 16, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SEG_ECUDA;

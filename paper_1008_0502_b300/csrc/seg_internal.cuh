@@ -48,10 +48,17 @@ static inline cudaError_t seg_launch(void (*kernel)(KArgs...), dim3 grid, dim3 b
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-#define SEG_CUDA_TRY(expr)                   \
-  do {                                       \
-    cudaError_t _e = (expr);                 \
-    if (_e != cudaSuccess) return SEG_ECUDA; \
+// Records a failed CUDA call (its name and the call's text) for
+// seg_last_cuda_error, per host thread.
+void seg_note_cuda_error(cudaError_t e, const char* call);
+
+#define SEG_CUDA_TRY(expr)                 \
+  do {                                     \
+    cudaError_t _e = (expr);               \
+    if (_e != cudaSuccess) {               \
+      seg_note_cuda_error(_e, #expr);      \
+      return SEG_ECUDA;                    \
+    }                                      \
   } while (0)
 
 __device__ __forceinline__ int seg_clampi(int v, int lo, int hi) {
@@ -268,9 +275,9 @@ struct GmmDev {
 };
 
 // ---------------------------------------------------------------- max-flow
-#define MF_TW 32
-#define MF_TH 16
-#define MF_THREADS (MF_TW * MF_TH)
+// Tile shapes of the min cut (seg_params.cut_tile), one compiled copy of
+// maxflow.cu each: 0 = 32x16, 1 = 32x8, 2 = 64x8 nodes (one thread per node).
+#define SEG_CUT_TILES 3
 
 // Grid barrier words: the arrival counter and the generation that waiters poll
 // sit in separate 128-byte lines.
@@ -357,6 +364,9 @@ struct MFArgs {
   long long timeout_ns;
   int init_done;  // e, rt and r already hold the initial residual graph (formed by the terms kernel)
   const uint8_t* on;  // [nframes] nullable: 0 = an empty slot, its frame's rows are neither read nor written
+  int frontier;       // 1: fixpoint rounds from the third on take their tiles from a compacted queue
+  int* tq;            // [2][ntiles] the tile queues of consecutive rounds
+  int* tqs;           // [ntiles] epoch of the round that last queued the tile
 };
 
 struct MFWS {
@@ -371,6 +381,8 @@ struct MFWS {
   int* tstamp;
   unsigned char* tact;
   GridBar* bar;
+  int* tq;   // [2][ntiles]
+  int* tqs;  // [ntiles]
   int nframes;
 };
 
@@ -458,17 +470,52 @@ int pt_launch_moments_terms(seg_ctx* c, const uint8_t* rgb, const float* prior, 
                             int32_t* cs, int32_t* ct, int32_t* ncap, bool mf_init = false);
 int pt_part_doubles(int H, int W);
 int pt_launch_back(seg_ctx* c, const float* sal, float* prior, const uint8_t* rgb);
+// The launch sequence of one frame of c (saliency, prior, moments + terms, min
+// cut) on c->stream; with c->io_mode set every frame pointer is nullptr and the
+// kernels read them from c->io (graph capture).
+int seg_ctx_push_launches(seg_ctx* c, const uint8_t* rgb, float* s, float* pr, uint8_t* mask, int64_t* cut);
 int pt_em_part_doubles(int H, int W);
 void pt_fill_lut(const seg_params& p, int* lut_host);
 
-// H is the stacked height (nframes frames of H / nframes rows each)
-size_t mf_bytes(int H, int W, int ndir, int nframes = 1);
-void mf_bind(MFWS& m, char* base, int H, int W, int ndir, int nframes = 1);
-int mf_grid_size(int H, int W, int* grid);
-int mf_launch(cudaStream_t st, const MFWS& m, int grid, int H, int W, int nbr, const int32_t* cs,
-              const int32_t* ct, const int32_t* ncap, uint8_t* mask_out, uint8_t* mask_state,
-              long long* cut_out, int* status, int max_cycles, int gr_every, int local_iters,
-              long long timeout_ns, const SegIO* io = nullptr, int* flow = nullptr, unsigned char* warm = nullptr,
-              bool words_zeroed = false, bool init_done = false, const uint8_t* on = nullptr);
+// One min-cut launch.  H is the stacked height (nframes frames of H / nframes
+// rows each, nframes from the workspace).
+struct MFCall {
+  cudaStream_t st = nullptr;
+  int grid = 0, H = 0, W = 0, nbr = 8;
+  const int32_t* cs = nullptr;  // the capacities (read unless init_done)
+  const int32_t* ct = nullptr;
+  const int32_t* ncap = nullptr;
+  uint8_t* mask_out = nullptr;    // nullptr: io->mask
+  uint8_t* mask_state = nullptr;  // nullable second copy of the mask
+  long long* cut_out = nullptr;   // nullptr: io->cut (or none)
+  int* status = nullptr;          // [8] error code, cycles, relabels, rounds, phase times
+  int max_cycles = 1, gr_every = 1, local_iters = 1;
+  long long timeout_ns = 0;       // grid-barrier wait limit
+  const SegIO* io = nullptr;
+  int* flow = nullptr;            // warm start: n-link flows in and out (nullable)
+  unsigned char* warm = nullptr;  // per frame: flow holds the previous frame's flows
+  bool words_zeroed = false;      // the caller zeroed cut sums, round flags and barrier
+  bool init_done = false;         // the terms kernel formed the initial residual graph
+  const uint8_t* on = nullptr;    // [nframes] slots holding a stream (nullable: all)
+  int frontier = 0;               // seg_params.relabel_frontier
+};
+
+// The per-frame words a replay of a captured frame zeroes before its kernels
+// accumulate into them: frame maxima of r+g+b (nullable), the min cut's
+// per-frame cut sums, round flags and grid-barrier counter.
+struct FrameWords {
+  int* smax;
+  int B;
+  unsigned long long* cut_acc;
+  unsigned int* flags;
+  GridBar* bar;
+};
+
+// Dispatch on the tile shape (maxflow_shapes.cu); every other argument as in
+// the shape's own copy.
+size_t mf_bytes(int H, int W, int ndir, int nframes, int shape);
+void mf_bind(MFWS& m, char* base, int H, int W, int ndir, int nframes, int shape);
+int mf_grid_size(int H, int W, int shape, int* grid);
+int mf_launch(const MFWS& m, const MFCall& c, int shape);
 
 static inline size_t seg_align(size_t x) { return (x + 255) & ~(size_t)255; }

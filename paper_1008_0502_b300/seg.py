@@ -28,7 +28,10 @@ SEG_MINCUT_STATIC_MAX_PIXELS = 131072
 
 class SegError(RuntimeError):
     def __init__(self, code: int, where: str):
-        super().__init__(f"{where}: {strerror(code)} ({code})")
+        detail = ""
+        if code == SEG_ECUDA and "lib" in globals():
+            detail = ": " + lib.seg_last_cuda_error().decode(errors="replace")
+        super().__init__(f"{where}: {strerror(code)} ({code}){detail}")
         self.code = code
 
 
@@ -45,8 +48,13 @@ class seg_params(C.Structure):
         ("max_cycles", C.c_int32), ("global_relabel_every", C.c_int32), ("local_iters", C.c_int32),
         ("use_graph", C.c_int32), ("gmm_components", C.c_int32), ("em_iters", C.c_int32),
         ("warm_start", C.c_int32), ("barrier_timeout_us", C.c_int32), ("kmeans_iters", C.c_int32),
-        ("gmm_update", C.c_int32),
+        ("gmm_update", C.c_int32), ("relabel_frontier", C.c_int32), ("cut_tile", C.c_int32),
     ]
+
+
+class seg_frame_io(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("sal", C.c_void_p), ("prior", C.c_void_p), ("mask", C.c_void_p),
+                ("cut", C.c_void_p)]
 
 
 def _load():
@@ -67,6 +75,11 @@ def _load():
         "seg_push_frame": ([vp, vp, vp, vp, vp, vp], i32),
         "seg_push_frame_host": ([vp, vp, vp, vp, vp, vp], i32),
         "seg_sync": ([vp, P(C.c_int)], i32),
+        "seg_last_cuda_error": ([], C.c_char_p),
+        "seg_group_create": ([vp, P(vp), i32, P(vp)], i32),
+        "seg_group_push": ([vp, P(seg_frame_io)], i32),
+        "seg_group_sync": ([vp, P(C.c_int), P(C.c_int)], i32),
+        "seg_group_destroy": ([vp], i32),
         "seg_get_state": ([vp, vp, P(C.c_size_t)], i32),
         "seg_set_state": ([vp, vp, C.c_size_t], i32),
         "seg_strerror": ([i32], C.c_char_p),
@@ -574,3 +587,62 @@ def saliency_prior(rgb, theta, fmap=None, t0: int = 0, params: seg_params | None
     if d is None:
         d = _diff_cache[key] = DiffContext(B, H, W, p, device=rgb.device)
     return SaliencyFn.apply(rgb, theta, fmap, t0, d)
+
+
+class Group:
+    """seg_group: member Segmenters (batch contexts of different resolutions, say)
+    advanced by one CUDA graph launch per frame step on the group's own stream.
+    Results equal each member's push_frame; members keep their state and their
+    per-stream calls (reset, set_stream_active, sync) between steps stay ordered."""
+
+    def __init__(self, members, stream=None):
+        self.members = list(members)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = (C.c_void_p * len(self.members))(*[m.handle for m in self.members])
+        h = C.c_void_p()
+        _check(lib.seg_group_create(C.c_void_p(self.stream.cuda_stream), arr, len(self.members), C.byref(h)),
+               "seg_group_create")
+        self.handle = h
+
+    def push(self, frames, outs=None):
+        """frames[i]: member i's frame tensor(s), shaped as its push_frame takes them;
+        outs[i]: its (saliency, prior, mask, cut) buffers (allocated when None).
+        Returns the outs."""
+        if len(frames) != len(self.members):
+            raise ValueError(f"{len(frames)} frames for {len(self.members)} members")
+        outs = list(outs) if outs is not None else [m.empty_outputs() for m in self.members]
+        io = (seg_frame_io * len(self.members))()
+        for i, (m, f, o) in enumerate(zip(self.members, frames, outs)):
+            sal, pr, mask, cut = o
+            io[i].rgb = _dev(f, torch.uint8, m._shape(3), "rgb")
+            io[i].sal = _dev(sal, torch.float32, m._shape(), "saliency") if sal is not None else None
+            io[i].prior = _dev(pr, torch.float32, m._shape(), "prior") if pr is not None else None
+            io[i].mask = _dev(mask, torch.uint8, m._shape(), "mask")
+            io[i].cut = _dev(cut, torch.int64, (m.B,), "cut") if cut is not None else None
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            self.stream.wait_stream(cur)  # the frames are ready on the caller's stream
+        _check(lib.seg_group_push(self.handle, io), "seg_group_push")
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+        return outs
+
+    def sync(self):
+        """[(status, cycles)] of every member."""
+        n = len(self.members)
+        codes, cyc = (C.c_int * n)(), (C.c_int * n)()
+        code = lib.seg_group_sync(self.handle, codes, cyc)
+        if code == SEG_ECUDA or code == SEG_EINVAL:
+            raise SegError(code, "seg_group_sync")
+        return [(codes[i], cyc[i]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.seg_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,11 +1,20 @@
-"""Autotuner for the min cut's schedule on a given resolution and frame mix.
+"""Autotuner for the min cut on a given resolution, batch and frame mix.
 
-The cut is exact for every schedule, so the tuner only measures: it pushes the
-same sample frames through a context per candidate (local push/relabel sweeps
-per tile visit, global relabel interval), times them with CUDA events, checks
-that every candidate produced the same masks and cut values, and returns the
-parameters of the fastest one.  Typical use: once per resolution before serving
-(`serve.Server` takes the tuned params), or `python -m paper_1008_0502_b300.tune`.
+The cut is exact for every tile shape and schedule, so the tuner only measures:
+it pushes the same sample frames through a context per candidate, times them
+with CUDA events, checks that every candidate produced the same masks and cut
+values, and returns the parameters of the fastest one.  A candidate overrides
+any of
+
+* ``cut_tile``: the tile shape, one compiled copy of the cut each (0 = 32x16,
+  1 = 32x8, 2 = 64x8 nodes);
+* ``relabel_frontier``: fixpoint rounds from a compacted tile queue (1) or a
+  scan of every CTA's own tiles (0);
+* ``local_iters``: push/relabel sweeps per tile visit;
+* ``global_relabel_every``: cycles between global relabels.
+
+Typical use: once per resolution and batch size before serving (``serve.Server``
+takes the tuned params), or ``python -m paper_1008_0502_b300.tune [H W [B]]``.
 """
 from __future__ import annotations
 
@@ -15,15 +24,56 @@ import torch
 
 from . import seg
 
-CANDIDATES = ((16, 2), (12, 1), (10, 1), (8, 1), (8, 2), (6, 2), (4, 2))
+TUNED_FIELDS = ("cut_tile", "relabel_frontier", "local_iters", "global_relabel_every")
+
+CANDIDATES = (
+    {},  # the defaults: 32x16 tiles, scan, 12 sweeps, a relabel every cycle
+    {"local_iters": 16, "global_relabel_every": 2}, {"local_iters": 8},
+    {"local_iters": 8, "global_relabel_every": 2}, {"local_iters": 24},
+    {"cut_tile": 1}, {"cut_tile": 1, "local_iters": 8}, {"cut_tile": 1, "local_iters": 16},
+    {"cut_tile": 2}, {"cut_tile": 2, "local_iters": 16}, {"cut_tile": 2, "local_iters": 24},
+    {"relabel_frontier": 1}, {"cut_tile": 1, "relabel_frontier": 1},
+    # sparser global relabels with longer discharges (stacked batches: the relabel dominates their cut)
+    {"local_iters": 24, "global_relabel_every": 2}, {"local_iters": 16, "global_relabel_every": 3},
+    {"cut_tile": 2, "local_iters": 16, "global_relabel_every": 2},
+    {"cut_tile": 2, "local_iters": 24, "global_relabel_every": 2},
+)
 
 
 @dataclasses.dataclass
 class TuneResult:
     params: seg.seg_params
-    local_iters: int
-    global_relabel_every: int
-    ms_per_frame: dict  # (local_iters, global_relabel_every) -> ms
+    best: dict          # the winning candidate's overrides
+    ms_per_frame: dict  # candidate key -> ms per frame (key: the candidate as given, or its sorted items)
+
+    @property
+    def local_iters(self) -> int:
+        return int(self.params.local_iters)
+
+    @property
+    def global_relabel_every(self) -> int:
+        return int(self.params.global_relabel_every)
+
+
+def _overrides(cand) -> dict:
+    """A candidate as a dict of overrides; (local_iters, global_relabel_every) pairs too."""
+    if isinstance(cand, dict):
+        bad = set(cand) - set(TUNED_FIELDS)
+        if bad:
+            raise ValueError(f"not a tuned field: {sorted(bad)}")
+        return dict(cand)
+    li, gr = cand
+    return {"local_iters": int(li), "global_relabel_every": int(gr)}
+
+
+def _key(cand):
+    return tuple(sorted(cand.items())) if isinstance(cand, dict) else cand
+
+
+def _with(base: seg.seg_params, over: dict) -> seg.seg_params:
+    d = {f: getattr(base, f) for f, _ in seg.seg_params._fields_ if f != "w"}
+    d.update(over)
+    return seg.params_from(d, w=tuple(base.w))
 
 
 def autotune_mincut(frames: torch.Tensor, params: seg.seg_params | None = None, candidates=CANDIDATES,
@@ -32,11 +82,12 @@ def autotune_mincut(frames: torch.Tensor, params: seg.seg_params | None = None, 
     base = params if params is not None else seg.default_params()
     T = int(frames.shape[0])
     H, W = int(frames.shape[-3]), int(frames.shape[-2])
-    timings, ref = {}, None
-    for li, gr in candidates:
-        p = seg.params_from({f: getattr(base, f) for f, _ in seg.seg_params._fields_ if f != "w"},
-                            w=tuple(base.w), local_iters=li, global_relabel_every=gr)
-        sg = seg.Segmenter(H, W, p, batch=batch, pipeline=pipeline)
+    timings, ref, overs = {}, None, {}
+    for cand in candidates:
+        over = _overrides(cand)
+        key = _key(cand)
+        overs[key] = over
+        sg = seg.Segmenter(H, W, _with(base, over), batch=batch, pipeline=pipeline)
         outs = [sg.empty_outputs() for _ in range(T)]
         for t in range(min(T, 3)):  # warm-up (graph capture), then a fresh video
             sg.push_frame(frames[t], *outs[t])
@@ -52,18 +103,16 @@ def autotune_mincut(frames: torch.Tensor, params: seg.seg_params | None = None, 
         sg.outputs_ready()
         code, _ = sg.sync()
         if code != 0:
-            raise seg.SegError(code, f"autotune candidate {(li, gr)}")
-        timings[(li, gr)] = e0.elapsed_time(e1) / T
+            raise seg.SegError(code, f"autotune candidate {over}")
+        timings[key] = e0.elapsed_time(e1) / T
         res = [(o[2].cpu(), o[3].cpu()) for o in outs]
+        sg.close()
         if ref is None:
             ref = res
         elif any(not (torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])) for a, b in zip(ref, res)):
-            raise AssertionError(f"schedule {(li, gr)} changed the cut")
-        sg.close()
-    li, gr = min(timings, key=timings.get)
-    best = seg.params_from({f: getattr(base, f) for f, _ in seg.seg_params._fields_ if f != "w"},
-                           w=tuple(base.w), local_iters=li, global_relabel_every=gr)
-    return TuneResult(best, li, gr, timings)
+            raise AssertionError(f"candidate {over} changed the cut")
+    best = min(timings, key=timings.get)
+    return TuneResult(_with(base, overs[best]), overs[best], timings)
 
 
 if __name__ == "__main__":
@@ -74,8 +123,11 @@ if __name__ == "__main__":
 
     from . import synth
 
-    H, W = (int(sys.argv[1]), int(sys.argv[2])) if len(sys.argv) > 2 else (480, 640)
-    fr = torch.from_numpy(np.stack([f for f, _ in synth.clip_vga_frames(40, H, W)])).cuda()
-    r = autotune_mincut(fr)
-    print(json.dumps({"H": H, "W": W, "local_iters": r.local_iters, "global_relabel_every": r.global_relabel_every,
-                      "ms_per_frame": {f"{k[0]},{k[1]}": v for k, v in r.ms_per_frame.items()}}))
+    a = [int(x) for x in sys.argv[1:]]
+    H, W = (a[0], a[1]) if len(a) >= 2 else (480, 640)
+    B = a[2] if len(a) >= 3 else 1
+    clip = np.stack([f for f, _ in synth.clip_vga_frames(40 + B, H, W)])
+    fr = clip[:40] if B == 1 else np.stack([clip[t:t + B] for t in range(40)])
+    r = autotune_mincut(torch.from_numpy(fr).cuda(), batch=B)
+    print(json.dumps({"H": H, "W": W, "B": B, "best": r.best,
+                      "ms_per_frame": {json.dumps(dict(k)): v for k, v in r.ms_per_frame.items()}}))
