@@ -236,6 +236,230 @@ __global__ void __launch_bounds__(256) k_feat_reduce1(const TIn* __restrict__ rg
   }
 }
 
+// ------------------------------------------------------------------ features + REDUCE, 16-pixel runs
+// The same two steps for frames whose width is a multiple of 16, shaped to
+// spend few instructions per pixel.  A thread owns a run of 16 level-0 pixels
+// of one row (three 16-byte loads of RGB8), computes their features in
+// registers, takes the two pixels left and the one right of its run from the
+// neighbouring threads of the row by shuffles (the tile's outer neighbours
+// from a small shared table) and forms the horizontal REDUCE of its 8 level-1
+// columns; the vertical REDUCE reads those rows back from shared memory.
+// The features are Itti's broadly tuned channels written with integer
+// numerators (rn = 3r/s etc., and (x + y)/2 - |x - y|/2 = min(x, y)):
+//   R - G = (3 / 2s) (max(0, 2r - g - b) - max(0, 2g - r - b))
+//   B - Y = (3 / 2s) (max(0, 2b - r - g) - 2 max(0, min(r, g) - b))
+// for RGB8 the numerators are exact integers (byte dot products), then one
+// reciprocal per pixel; the REDUCE uses the binomial weights 1 4 6 4 1 as
+// integers and scales by 1/256 at the end (exact).  Float frames holding
+// integer values give the RGB8 result bit for bit, and the tile height does
+// not change any value.
+#define FV_TX 64    // level-1 columns per CTA (128 level-0 pixels per row)
+#define FV_LANES 8  // threads per level-0 row
+
+__device__ __forceinline__ int fv_dp4a(unsigned a, unsigned b) {
+  int d;
+  asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(0));
+  return d;
+}
+__device__ __forceinline__ float fv_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+struct FV3 {
+  float v[3];  // I, R - G, B - Y
+};
+__device__ __forceinline__ FV3 fv_finish(float sf, float nrg, float nby, bool hue) {
+  const float k = hue ? 1.5f * fv_rcp(sf) : 0.f;
+  return {{sf * (1.f / 765.f), nrg * k, nby * k}};
+}
+// RGB8 pixel whose r, g, b are the bytes SH/8, SH/8 + 1, SH/8 + 2 of P;
+// hue <=> 10 s > smax <=> s > floor(smax / 10) = thr
+template <int SH>
+__device__ __forceinline__ FV3 fv_px_u8(unsigned P, int thr) {
+  // byte weights (r, g, b, -) packed little-endian
+  const int s = fv_dp4a(P, 0x00010101u << SH);   // r + g + b
+  const int t1 = fv_dp4a(P, 0x00FFFF02u << SH);  // 2r - g - b
+  const int t2 = fv_dp4a(P, 0x00FF02FFu << SH);  // 2g - r - b
+  const int t3 = fv_dp4a(P, 0x0002FFFFu << SH);  // 2b - r - g
+  const int u1 = fv_dp4a(P, 0x00FF0001u << SH);  // r - b
+  const int u2 = fv_dp4a(P, 0x00FF0100u << SH);  // g - b
+  const int nrg = max(t1, 0) - max(t2, 0);
+  const int nby = max(t3, 0) - 2 * max(min(u1, u2), 0);
+  // exact int -> float for |n| < 2^22: the integer placed in the significand of 2^23 (or 1.5 * 2^23)
+  const float sf = __int_as_float(s | 0x4B000000) - 8388608.f;
+  const float rgf = __int_as_float(nrg + 0x4B400000) - 12582912.f;
+  const float byf = __int_as_float(nby + 0x4B400000) - 12582912.f;
+  return fv_finish(sf, rgf, byf, s > thr);
+}
+__device__ __forceinline__ FV3 fv_px_f32(float r, float g, float b, float smaxf) {
+  const float sf = r + g + b;
+  const float nrg = fmaxf(0.f, 2.f * r - g - b) - fmaxf(0.f, 2.f * g - r - b);
+  const float nby = fmaxf(0.f, 2.f * b - r - g) - 2.f * fmaxf(0.f, fminf(r, g) - b);
+  return fv_finish(sf, nrg, nby, 10.f * sf > smaxf);
+}
+// one REDUCE tap set, x16: f(-2) + 4 f(-1) + 6 f(0) + 4 f(1) + f(2)
+__device__ __forceinline__ float fv_h(float a, float b, float c, float d, float e) {
+  return fmaf(6.f, c, fmaf(4.f, b + d, a + e));
+}
+
+template <int TY>
+__host__ __device__ constexpr int fv_threads() {
+  return FV_LANES * (2 * TY + 4);
+}
+
+template <typename TIn, int TY>
+__global__ void __launch_bounds__(fv_threads<TY>()) k_feat_reduce1_v(
+    const TIn* __restrict__ rgb, int H, int W, const int* __restrict__ smax_p, float* __restrict__ I1,
+    float* __restrict__ RG1, float* __restrict__ BY1, int h1, int w1, const SegIO* io, const uint8_t* on) {
+  constexpr bool U8 = std::is_same<TIn, uint8_t>::value;
+  constexpr int ROWS = 2 * TY + 3;  // level-0 rows under TY level-1 rows
+  __shared__ __align__(16) float sH[3][ROWS][FV_TX];
+  __shared__ float sHalo[ROWS][3][3];  // [row][pixel -2, -1, +128 of the span][channel]
+  if constexpr (U8) {
+    if (!rgb) rgb = io->rgb;
+  }
+  const int fb = blockIdx.z;  // frame of the batch
+  if (SEG_SLOT_OFF(on, fb)) return;
+  rgb += (size_t)fb * 3 * H * W;
+  const size_t o1 = (size_t)fb * h1 * w1;
+  const int X0 = blockIdx.x * FV_TX, Y0 = blockIdx.y * TY;
+  const int cx0 = 2 * X0, ry0 = 2 * Y0 - 2;
+  const int tid = threadIdx.x, slot = tid >> 3, j = tid & 7;
+  const int nvalid = min(FV_LANES, (W - cx0) >> 4);  // threads of a row holding pixels
+  const bool act = slot < ROWS && j < nvalid;
+  const int row = seg_clampi(ry0 + slot, 0, H - 1);
+  const TIn* run = rgb + 3 * ((size_t)row * W + cx0 + 16 * j);
+  // RGB8: the run's 48 bytes, loaded before the wait for the frame maximum
+  unsigned wv[U8 ? 12 : 1];
+  if constexpr (U8) {
+    if (act && ((uintptr_t)run & 15) == 0) {
+      const uint4* q = reinterpret_cast<const uint4*>(run);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint4 v = __ldg(q + k);
+        wv[4 * k] = v.x;
+        wv[4 * k + 1] = v.y;
+        wv[4 * k + 2] = v.z;
+        wv[4 * k + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+        wv[k] = act ? (unsigned)run[4 * k] | ((unsigned)run[4 * k + 1] << 8) | ((unsigned)run[4 * k + 2] << 16) |
+                          ((unsigned)run[4 * k + 3] << 24)
+                    : 0u;
+    }
+  }
+  seg_pdl_enter();
+  const int smax = smax_p[fb];
+  const int thr = smax / 10;
+  const float smaxf = __int_as_float(smax);
+  // the span's outer neighbours, one pixel per thread (clamped to the frame)
+  if (tid < 3 * ROWS) {
+    const int hr = tid / 3, hw = tid - 3 * hr;
+    const int y = seg_clampi(ry0 + hr, 0, H - 1);
+    const int x = seg_clampi(hw == 0 ? cx0 - 2 : hw == 1 ? cx0 - 1 : cx0 + 2 * FV_TX, 0, W - 1);
+    const TIn* p = rgb + 3 * ((size_t)y * W + x);
+    FV3 f;
+    if constexpr (U8)
+      f = fv_px_u8<0>((unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16), thr);
+    else
+      f = fv_px_f32(p[0], p[1], p[2], smaxf);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) sHalo[hr][hw][ch] = f.v[ch];
+  }
+  // features of the run
+  float F[3][16];
+  if constexpr (U8) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const unsigned a = wv[3 * g], b = wv[3 * g + 1], c = wv[3 * g + 2];  // r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3
+      const FV3 f0 = fv_px_u8<0>(a, thr), f1 = fv_px_u8<0>(__byte_perm(a, b, 0x0543), thr),
+                f2 = fv_px_u8<0>(__byte_perm(b, c, 0x0432), thr), f3 = fv_px_u8<8>(c, thr);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        F[ch][4 * g] = f0.v[ch];
+        F[ch][4 * g + 1] = f1.v[ch];
+        F[ch][4 * g + 2] = f2.v[ch];
+        F[ch][4 * g + 3] = f3.v[ch];
+      }
+    }
+  } else {
+    const bool vec = ((uintptr_t)run & 15) == 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float e[12];
+      if (act && vec) {
+        const float4* q = reinterpret_cast<const float4*>(run) + 3 * g;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float4 v = __ldg(q + k);
+          e[4 * k] = v.x;
+          e[4 * k + 1] = v.y;
+          e[4 * k + 2] = v.z;
+          e[4 * k + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e[k] = act ? run[12 * g + k] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const FV3 f = fv_px_f32(e[3 * k], e[3 * k + 1], e[3 * k + 2], smaxf);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) F[ch][4 * g + k] = f.v[ch];
+      }
+    }
+  }
+  __syncthreads();  // sHalo
+  const int hs = min(slot, ROWS - 1);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    // pixels -2, -1 and 16 of the run: the neighbouring runs of the row, or the span's neighbours
+    float m2 = __shfl_up_sync(0xffffffffu, F[ch][14], 1, FV_LANES);
+    float m1 = __shfl_up_sync(0xffffffffu, F[ch][15], 1, FV_LANES);
+    float p16 = __shfl_down_sync(0xffffffffu, F[ch][0], 1, FV_LANES);
+    if (j == 0) {
+      m2 = sHalo[hs][0][ch];
+      m1 = sHalo[hs][1][ch];
+    }
+    if (j == nvalid - 1) p16 = sHalo[hs][2][ch];
+    if (slot < ROWS) {
+      float hv[8];
+      hv[0] = fv_h(m2, m1, F[ch][0], F[ch][1], F[ch][2]);
+#pragma unroll
+      for (int m = 1; m < 7; ++m) hv[m] = fv_h(F[ch][2 * m - 2], F[ch][2 * m - 1], F[ch][2 * m], F[ch][2 * m + 1], F[ch][2 * m + 2]);
+      hv[7] = fv_h(F[ch][12], F[ch][13], F[ch][14], F[ch][15], p16);
+      float4* d = reinterpret_cast<float4*>(&sH[ch][slot][8 * j]);
+      d[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      d[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+    }
+  }
+  __syncthreads();
+  // vertical REDUCE: 4 output rows x 4 columns per task
+  constexpr int NQ = FV_TX / 4, NG = TY / 4;
+  for (int t = tid; t < 3 * NQ * NG; t += blockDim.x) {
+    const int q = t % NQ, rg = (t / NQ) % NG, ch = t / (NQ * NG);
+    const int ox = X0 + 4 * q;
+    if (ox >= w1) continue;
+    float4 r[11];  // horizontal REDUCE rows 8 rg .. 8 rg + 10
+#pragma unroll
+    for (int i = 0; i < 11; ++i) r[i] = *reinterpret_cast<const float4*>(&sH[ch][8 * rg + i][4 * q]);
+    float* out = (ch == 0 ? I1 : ch == 1 ? RG1 : BY1) + o1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int oy = Y0 + 4 * rg + k;
+      if (oy >= h1) break;
+      const float4 a = r[2 * k], b = r[2 * k + 1], c = r[2 * k + 2], d = r[2 * k + 3], e = r[2 * k + 4];
+      constexpr float sc = 1.f / 256.f;
+      *reinterpret_cast<float4*>(out + (size_t)oy * w1 + ox) =
+          make_float4(fv_h(a.x, b.x, c.x, d.x, e.x) * sc, fv_h(a.y, b.y, c.y, d.y, e.y) * sc,
+                      fv_h(a.z, b.z, c.z, d.z, e.z) * sc, fv_h(a.w, b.w, c.w, d.w, e.w) * sc);
+    }
+  }
+}
+
 struct Reduce3Args {
   const float* in[3];
   float* out[3];
@@ -1397,16 +1621,38 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
   // not one thread per pixel (idle CTAs would crowd the concurrent back half)
   const int nb8 = max((N / 16 + 255) / 256, (s.nmaps + 255) / 256);
   dim3 g1((s.wl[1] + RED_TX - 1) / RED_TX, (s.hl[1] + RED_TY - 1) / RED_TY, B);
+  // widths that are a multiple of 16: 16-pixel runs; the shorter tile while a
+  // batch of the taller one would not give two CTAs per SM
+  const bool fv = (W & 15) == 0;
+  const int fvx = (s.wl[1] + FV_TX - 1) / FV_TX;
+  const bool fv8 = (long long)fvx * ((s.hl[1] + 15) / 16) * B < 2 * 148;
+  const dim3 gv(fvx, fv8 ? (s.hl[1] + 7) / 8 : (s.hl[1] + 15) / 16, B);
+  float *l1i = s.pyr[0][1], *l1rg = s.pyr[1][1], *l1by = s.pyr[2][1];
+  const int h1 = s.hl[1], w1 = s.wl[1];
   if (rgb_f32) {
     const float* f = (const float*)rgb;
     SEG_CUDA_TRY(seg_launch(k_rgb_max<float>, dim3(nb, B), 256, 0, st, f, N, s.smax, s.mm, s.nmaps, nullptr, s.on));
-    SEG_CUDA_TRY(seg_launch(k_feat_reduce1<float>, g1, 256, 0, st, f, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
-                                              s.hl[1], s.wl[1], nullptr, s.on));
+    if (!fv)
+      SEG_CUDA_TRY(seg_launch(k_feat_reduce1<float>, g1, 256, 0, st, f, H, W, s.smax, l1i, l1rg, l1by, h1, w1,
+                              nullptr, s.on));
+    else if (fv8)
+      SEG_CUDA_TRY(seg_launch(k_feat_reduce1_v<float, 8>, gv, fv_threads<8>(), 0, st, f, H, W, s.smax, l1i, l1rg,
+                              l1by, h1, w1, nullptr, s.on));
+    else
+      SEG_CUDA_TRY(seg_launch(k_feat_reduce1_v<float, 16>, gv, fv_threads<16>(), 0, st, f, H, W, s.smax, l1i, l1rg,
+                              l1by, h1, w1, nullptr, s.on));
   } else {
     const uint8_t* u = (const uint8_t*)rgb;
     SEG_CUDA_TRY(seg_launch(k_rgb_max<uint8_t>, dim3(nb8, B), 256, 0, st, u, N, s.smax, s.mm, s.nmaps, io, s.on));
-    SEG_CUDA_TRY(seg_launch(k_feat_reduce1<uint8_t>, g1, 256, 0, st, u, H, W, s.smax, s.pyr[0][1], s.pyr[1][1], s.pyr[2][1],
-                                                s.hl[1], s.wl[1], io, s.on));
+    if (!fv)
+      SEG_CUDA_TRY(seg_launch(k_feat_reduce1<uint8_t>, g1, 256, 0, st, u, H, W, s.smax, l1i, l1rg, l1by, h1, w1, io,
+                              s.on));
+    else if (fv8)
+      SEG_CUDA_TRY(seg_launch(k_feat_reduce1_v<uint8_t, 8>, gv, fv_threads<8>(), 0, st, u, H, W, s.smax, l1i, l1rg,
+                              l1by, h1, w1, io, s.on));
+    else
+      SEG_CUDA_TRY(seg_launch(k_feat_reduce1_v<uint8_t, 16>, gv, fv_threads<16>(), 0, st, u, H, W, s.smax, l1i, l1rg,
+                              l1by, h1, w1, io, s.on));
   }
   // tiled launches while the produced level is large; one tail launch for the rest
   int tail_from = s.L - 1;
