@@ -269,34 +269,31 @@ __device__ __forceinline__ float fv_rcp(float x) {
 struct FV3 {
   float v[3];  // I, R - G, B - Y
 };
-__device__ __forceinline__ FV3 fv_finish(float sf, float nrg, float nby, bool hue) {
-  const float k = hue ? 1.5f * fv_rcp(sf) : 0.f;
-  return {{sf * (1.f / 765.f), nrg * k, nby * k}};
+// s2 = 2 s, n3 = 3 x the numerators: R - G = 3 nrg / 2s = n3rg / s2, likewise B - Y
+__device__ __forceinline__ FV3 fv_finish(float s2f, float n3rg, float n3by, bool hue) {
+  const float k = hue ? fv_rcp(s2f) : 0.f;
+  return {{s2f * (1.f / 1530.f), n3rg * k, n3by * k}};
 }
 // RGB8 pixel whose r, g, b are the bytes SH/8, SH/8 + 1, SH/8 + 2 of P;
-// hue <=> 10 s > smax <=> s > floor(smax / 10) = thr
+// hue <=> 10 s > smax <=> s > floor(smax / 10) <=> 2s > thr2 = 2 floor(smax / 10)
 template <int SH>
-__device__ __forceinline__ FV3 fv_px_u8(unsigned P, int thr) {
+__device__ __forceinline__ FV3 fv_px_u8(unsigned P, int thr2) {
   // byte weights (r, g, b, -) packed little-endian
-  const int s = fv_dp4a(P, 0x00010101u << SH);   // r + g + b
-  const int t1 = fv_dp4a(P, 0x00FFFF02u << SH);  // 2r - g - b
-  const int t2 = fv_dp4a(P, 0x00FF02FFu << SH);  // 2g - r - b
-  const int t3 = fv_dp4a(P, 0x0002FFFFu << SH);  // 2b - r - g
-  const int u1 = fv_dp4a(P, 0x00FF0001u << SH);  // r - b
-  const int u2 = fv_dp4a(P, 0x00FF0100u << SH);  // g - b
-  const int nrg = max(t1, 0) - max(t2, 0);
-  const int nby = max(t3, 0) - 2 * max(min(u1, u2), 0);
-  // exact int -> float for |n| < 2^22: the integer placed in the significand of 2^23 (or 1.5 * 2^23)
-  const float sf = __int_as_float(s | 0x4B000000) - 8388608.f;
-  const float rgf = __int_as_float(nrg + 0x4B400000) - 12582912.f;
-  const float byf = __int_as_float(nby + 0x4B400000) - 12582912.f;
-  return fv_finish(sf, rgf, byf, s > thr);
+  const int s2 = fv_dp4a(P, 0x00020202u << SH);  // 2 (r + g + b)
+  const int t1 = fv_dp4a(P, 0x00FDFD06u << SH);  // 3 (2r - g - b)
+  const int t2 = fv_dp4a(P, 0x00FD06FDu << SH);  // 3 (2g - r - b)
+  const int t3 = fv_dp4a(P, 0x0006FDFDu << SH);  // 3 (2b - r - g)
+  const int u1 = fv_dp4a(P, 0x00FD0003u << SH);  // 3 (r - b)
+  const int u2 = fv_dp4a(P, 0x00FD0300u << SH);  // 3 (g - b)
+  const int n3rg = max(t1, 0) - max(t2, 0);
+  const int n3by = max(t3, 0) - 2 * __vimin_s32_relu(u1, u2);
+  return fv_finish((float)s2, (float)n3rg, (float)n3by, s2 > thr2);
 }
 __device__ __forceinline__ FV3 fv_px_f32(float r, float g, float b, float smaxf) {
   const float sf = r + g + b;
-  const float nrg = fmaxf(0.f, 2.f * r - g - b) - fmaxf(0.f, 2.f * g - r - b);
-  const float nby = fmaxf(0.f, 2.f * b - r - g) - 2.f * fmaxf(0.f, fminf(r, g) - b);
-  return fv_finish(sf, nrg, nby, 10.f * sf > smaxf);
+  const float n3rg = fmaxf(0.f, 3.f * (2.f * r - g - b)) - fmaxf(0.f, 3.f * (2.f * g - r - b));
+  const float n3by = fmaxf(0.f, 3.f * (2.f * b - r - g)) - 2.f * fmaxf(0.f, 3.f * (fminf(r, g) - b));
+  return fv_finish(2.f * sf, n3rg, n3by, 10.f * sf > smaxf);
 }
 // one REDUCE tap set, x16: f(-2) + 4 f(-1) + 6 f(0) + 4 f(1) + f(2)
 __device__ __forceinline__ float fv_h(float a, float b, float c, float d, float e) {
@@ -306,6 +303,62 @@ __device__ __forceinline__ float fv_h(float a, float b, float c, float d, float 
 template <int TY>
 __host__ __device__ constexpr int fv_threads() {
   return FV_LANES * (2 * TY + 4);
+}
+
+// The run's horizontal REDUCE into sH (pixels -2, -1 and 16 of the run from
+// the neighbouring runs of the row by shuffles, or from the span's neighbours
+// in sHalo, which the caller has made visible), a CTA barrier, then the
+// vertical REDUCE of the tile, 4 output rows x 4 columns per task.  I1, RG1,
+// BY1 point at the frame's level-1 maps.
+template <int TY>
+__device__ __forceinline__ void fv_reduce_tile(const float (&F)[3][16], float (*sH)[2 * TY + 3][FV_TX],
+                                               const float (*sHalo)[3][3], int slot, int j, int nvalid, int X0,
+                                               int Y0, int h1, int w1, float* __restrict__ I1,
+                                               float* __restrict__ RG1, float* __restrict__ BY1) {
+  constexpr int ROWS = 2 * TY + 3;
+  const int hs = min(slot, ROWS - 1);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float m2 = __shfl_up_sync(0xffffffffu, F[ch][14], 1, FV_LANES);
+    float m1 = __shfl_up_sync(0xffffffffu, F[ch][15], 1, FV_LANES);
+    float p16 = __shfl_down_sync(0xffffffffu, F[ch][0], 1, FV_LANES);
+    if (j == 0) {
+      m2 = sHalo[hs][0][ch];
+      m1 = sHalo[hs][1][ch];
+    }
+    if (j == nvalid - 1) p16 = sHalo[hs][2][ch];
+    if (slot < ROWS) {
+      float hv[8];
+      hv[0] = fv_h(m2, m1, F[ch][0], F[ch][1], F[ch][2]);
+#pragma unroll
+      for (int m = 1; m < 7; ++m) hv[m] = fv_h(F[ch][2 * m - 2], F[ch][2 * m - 1], F[ch][2 * m], F[ch][2 * m + 1], F[ch][2 * m + 2]);
+      hv[7] = fv_h(F[ch][12], F[ch][13], F[ch][14], F[ch][15], p16);
+      float4* d = reinterpret_cast<float4*>(&sH[ch][slot][8 * j]);
+      d[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      d[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+    }
+  }
+  __syncthreads();
+  constexpr int NQ = FV_TX / 4, NG = TY / 4;
+  for (int t = threadIdx.x; t < 3 * NQ * NG; t += blockDim.x) {
+    const int q = t % NQ, rg = (t / NQ) % NG, ch = t / (NQ * NG);
+    const int ox = X0 + 4 * q;
+    if (ox >= w1) continue;
+    float4 r[11];  // horizontal REDUCE rows 8 rg .. 8 rg + 10
+#pragma unroll
+    for (int i = 0; i < 11; ++i) r[i] = *reinterpret_cast<const float4*>(&sH[ch][8 * rg + i][4 * q]);
+    float* out = ch == 0 ? I1 : ch == 1 ? RG1 : BY1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int oy = Y0 + 4 * rg + k;
+      if (oy >= h1) break;
+      const float4 a = r[2 * k], b = r[2 * k + 1], c = r[2 * k + 2], d = r[2 * k + 3], e = r[2 * k + 4];
+      constexpr float sc = 1.f / 256.f;
+      *reinterpret_cast<float4*>(out + (size_t)oy * w1 + ox) =
+          make_float4(fv_h(a.x, b.x, c.x, d.x, e.x) * sc, fv_h(a.y, b.y, c.y, d.y, e.y) * sc,
+                      fv_h(a.z, b.z, c.z, d.z, e.z) * sc, fv_h(a.w, b.w, c.w, d.w, e.w) * sc);
+    }
+  }
 }
 
 template <typename TIn, int TY>
@@ -353,7 +406,7 @@ __global__ void __launch_bounds__(fv_threads<TY>()) k_feat_reduce1_v(
   }
   seg_pdl_enter();
   const int smax = smax_p[fb];
-  const int thr = smax / 10;
+  const int thr2 = 2 * (smax / 10);
   const float smaxf = __int_as_float(smax);
   // the span's outer neighbours, one pixel per thread (clamped to the frame)
   if (tid < 3 * ROWS) {
@@ -363,7 +416,7 @@ __global__ void __launch_bounds__(fv_threads<TY>()) k_feat_reduce1_v(
     const TIn* p = rgb + 3 * ((size_t)y * W + x);
     FV3 f;
     if constexpr (U8)
-      f = fv_px_u8<0>((unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16), thr);
+      f = fv_px_u8<0>((unsigned)p[0] | ((unsigned)p[1] << 8) | ((unsigned)p[2] << 16), thr2);
     else
       f = fv_px_f32(p[0], p[1], p[2], smaxf);
 #pragma unroll
@@ -375,8 +428,8 @@ __global__ void __launch_bounds__(fv_threads<TY>()) k_feat_reduce1_v(
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const unsigned a = wv[3 * g], b = wv[3 * g + 1], c = wv[3 * g + 2];  // r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3
-      const FV3 f0 = fv_px_u8<0>(a, thr), f1 = fv_px_u8<0>(__byte_perm(a, b, 0x0543), thr),
-                f2 = fv_px_u8<0>(__byte_perm(b, c, 0x0432), thr), f3 = fv_px_u8<8>(c, thr);
+      const FV3 f0 = fv_px_u8<0>(a, thr2), f1 = fv_px_u8<0>(__byte_perm(a, b, 0x0543), thr2),
+                f2 = fv_px_u8<0>(__byte_perm(b, c, 0x0432), thr2), f3 = fv_px_u8<8>(c, thr2);
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         F[ch][4 * g] = f0.v[ch];
@@ -413,51 +466,7 @@ __global__ void __launch_bounds__(fv_threads<TY>()) k_feat_reduce1_v(
     }
   }
   __syncthreads();  // sHalo
-  const int hs = min(slot, ROWS - 1);
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    // pixels -2, -1 and 16 of the run: the neighbouring runs of the row, or the span's neighbours
-    float m2 = __shfl_up_sync(0xffffffffu, F[ch][14], 1, FV_LANES);
-    float m1 = __shfl_up_sync(0xffffffffu, F[ch][15], 1, FV_LANES);
-    float p16 = __shfl_down_sync(0xffffffffu, F[ch][0], 1, FV_LANES);
-    if (j == 0) {
-      m2 = sHalo[hs][0][ch];
-      m1 = sHalo[hs][1][ch];
-    }
-    if (j == nvalid - 1) p16 = sHalo[hs][2][ch];
-    if (slot < ROWS) {
-      float hv[8];
-      hv[0] = fv_h(m2, m1, F[ch][0], F[ch][1], F[ch][2]);
-#pragma unroll
-      for (int m = 1; m < 7; ++m) hv[m] = fv_h(F[ch][2 * m - 2], F[ch][2 * m - 1], F[ch][2 * m], F[ch][2 * m + 1], F[ch][2 * m + 2]);
-      hv[7] = fv_h(F[ch][12], F[ch][13], F[ch][14], F[ch][15], p16);
-      float4* d = reinterpret_cast<float4*>(&sH[ch][slot][8 * j]);
-      d[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      d[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
-    }
-  }
-  __syncthreads();
-  // vertical REDUCE: 4 output rows x 4 columns per task
-  constexpr int NQ = FV_TX / 4, NG = TY / 4;
-  for (int t = tid; t < 3 * NQ * NG; t += blockDim.x) {
-    const int q = t % NQ, rg = (t / NQ) % NG, ch = t / (NQ * NG);
-    const int ox = X0 + 4 * q;
-    if (ox >= w1) continue;
-    float4 r[11];  // horizontal REDUCE rows 8 rg .. 8 rg + 10
-#pragma unroll
-    for (int i = 0; i < 11; ++i) r[i] = *reinterpret_cast<const float4*>(&sH[ch][8 * rg + i][4 * q]);
-    float* out = (ch == 0 ? I1 : ch == 1 ? RG1 : BY1) + o1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int oy = Y0 + 4 * rg + k;
-      if (oy >= h1) break;
-      const float4 a = r[2 * k], b = r[2 * k + 1], c = r[2 * k + 2], d = r[2 * k + 3], e = r[2 * k + 4];
-      constexpr float sc = 1.f / 256.f;
-      *reinterpret_cast<float4*>(out + (size_t)oy * w1 + ox) =
-          make_float4(fv_h(a.x, b.x, c.x, d.x, e.x) * sc, fv_h(a.y, b.y, c.y, d.y, e.y) * sc,
-                      fv_h(a.z, b.z, c.z, d.z, e.z) * sc, fv_h(a.w, b.w, c.w, d.w, e.w) * sc);
-    }
-  }
+  fv_reduce_tile<TY>(F, sH, sHalo, slot, j, nvalid, X0, Y0, h1, w1, I1 + o1, RG1 + o1, BY1 + o1);
 }
 
 struct Reduce3Args {
@@ -684,7 +693,20 @@ struct CSArgs {
   const int2* rs;
   int rs_row[SEG_MAX_PAIRS], rs_col[SEG_MAX_PAIRS];
   const uint8_t* on;
+  int sm_ws, sm_wc;  // widest surround and center level: the staged shared-memory layout
 };
+
+// The center-surround statistics kernel stages what its CTA reads of a pair's
+// surround level in shared memory: up to CS_SR rows of every channel it
+// handles (the rows the bilinear up-sampling of its band's center rows
+// touches), the pair's column table and the row-table entries of the band
+// (with the surround rows renumbered from the first staged one).  Values are unchanged: the same
+// interpolation reads the same numbers from shared memory.
+#define CS_SR 4
+#define CS_TR 32
+__host__ __device__ constexpr size_t cs_stage_bytes(int nf, int ws, int wc) {
+  return sizeof(float) * (size_t)nf * CS_SR * ws + sizeof(int2) * ((size_t)wc + CS_TR);
+}
 
 
 #define CS_MAX_TILES_X 1024
@@ -697,6 +719,7 @@ struct CSArgs {
 template <int NCH, int CPB>
 __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
   seg_pdl_enter();
+  extern __shared__ __align__(16) float cs_dyn[];
   __shared__ float sMin[8][CPB], sMax[8][CPB], sTs[8][CPB];
   constexpr int G = NCH / CPB;  // channel groups per (pair, band)
   const int f0 = (blockIdx.x % G) * CPB;
@@ -721,6 +744,22 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
   const int2* tcol = a.rs + a.rs_col[p];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int y0 = band * T, rows = min(T, hc - y0);
+  const int lo = trow[y0].x & 0xffff, nr = (trow[y0 + rows - 1].x >> 16) - lo + 1;
+  const bool staged = nr <= CS_SR && ws <= a.sm_ws && wc <= a.sm_wc && rows <= CS_TR;
+  float* sS = cs_dyn;                                                       // [CPB][CS_SR][ws]
+  int2* sTc = reinterpret_cast<int2*>(cs_dyn + (size_t)CPB * CS_SR * a.sm_ws);  // [wc]
+  int2* sTr = sTc + a.sm_wc;                                                 // [rows], renumbered
+  if (staged) {
+#pragma unroll
+    for (int f = 0; f < CPB; ++f)
+      for (int i = threadIdx.x; i < nr * ws; i += blockDim.x) sS[f * CS_SR * ws + i] = sur[f][lo * ws + i];
+    for (int i = threadIdx.x; i < wc; i += blockDim.x) sTc[i] = tcol[i];
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int2 r = trow[y0 + i];
+      sTr[i] = make_int2(r.x - lo - (lo << 16), r.y);
+    }
+    __syncthreads();
+  }
   float mn[CPB], mx[CPB], ts[CPB];
 #pragma unroll
   for (int f = 0; f < CPB; ++f) {
@@ -728,27 +767,41 @@ __global__ void __launch_bounds__(256) k_cs_stats(CSArgs a) {
     mx[f] = 0.f;
     ts[f] = 0.f;
   }
+  // one element: its |CS| value per channel into the running extrema and tile maxima
+#define CS_ELEMENT(RY, RX, SUR_F, Y, X)                                                      \
+  {                                                                                          \
+    float u = seg_bilinear_t(SUR_F, ws, RY, RX), v0 = cen[f][(Y) * wc + (X)];                \
+    const int ch = f0 + f;                                                                   \
+    float v = (a.opp_sum && (ch == 1 || ch == 2)) ? fabsf(v0 + u) : fabsf(v0 - u);           \
+    mn[f] = fminf(mn[f], v);                                                                 \
+    mx[f] = fmaxf(mx[f], v);                                                                 \
+    tm[f] = fmaxf(tm[f], v);                                                                 \
+  }
   for (int tx = wid; tx < ntx; tx += nw) {
     const int x0 = tx * T, cols = min(T, wc - x0);
     float tm[CPB];
 #pragma unroll
     for (int f = 0; f < CPB; ++f) tm[f] = 0.f;
-    for (int i = lane; i < rows * cols; i += 32) {
-      const int yy = i / cols, y = y0 + yy, x = x0 + (i - yy * cols);
-      const int2 ry = trow[y], rx = tcol[x];
+    if (staged) {
+#pragma unroll 2
+      for (int i = lane; i < rows * cols; i += 32) {
+        const int yy = i / cols, xx = i - yy * cols;
+        const int2 ry = sTr[yy], rx = sTc[x0 + xx];
 #pragma unroll
-      for (int f = 0; f < CPB; ++f) {
-        float u = seg_bilinear_t(sur[f], ws, ry, rx), v0 = cen[f][y * wc + x];
-        const int ch = f0 + f;
-        float v = (a.opp_sum && (ch == 1 || ch == 2)) ? fabsf(v0 + u) : fabsf(v0 - u);
-        mn[f] = fminf(mn[f], v);
-        mx[f] = fmaxf(mx[f], v);
-        tm[f] = fmaxf(tm[f], v);
+        for (int f = 0; f < CPB; ++f) CS_ELEMENT(ry, rx, sS + f * CS_SR * ws, y0 + yy, x0 + xx)
+      }
+    } else {
+      for (int i = lane; i < rows * cols; i += 32) {
+        const int yy = i / cols, y = y0 + yy, x = x0 + (i - yy * cols);
+        const int2 ry = trow[y], rx = tcol[x];
+#pragma unroll
+        for (int f = 0; f < CPB; ++f) CS_ELEMENT(ry, rx, sur[f], y, x)
       }
     }
 #pragma unroll
     for (int f = 0; f < CPB; ++f) ts[f] += seg_warp_max_f(tm[f]);  // every lane holds the tile maximum
   }
+#undef CS_ELEMENT
 #pragma unroll
   for (int f = 0; f < CPB; ++f) {
     float a0 = seg_warp_min_f(mn[f]), a1 = seg_warp_max_f(mx[f]);
@@ -1603,7 +1656,18 @@ static void fill_cs_args(const SalWS& s, CSArgs& a) {
     a.rs_col[i] = s.rs_col[i];
   }
   a.on = s.on;
+  // the staged center-surround layout: widest surround and center levels of the pairs
+  a.sm_ws = a.sm_wc = 0;
+  for (int i = 0; i < s.npairs; ++i) {
+    a.sm_ws = max(a.sm_ws, s.wl[s.pair_s[i]]);
+    a.sm_wc = max(a.sm_wc, s.wl[s.pair_c[i]]);
+  }
+  if (cs_stage_bytes(s.nch, a.sm_ws, a.sm_wc) > 48 * 1024)
+    a.sm_ws = a.sm_wc = 0;  // (reads from global memory instead)
 }
+
+// dynamic shared memory of the center-surround kernels for nf channels per CTA
+static size_t cs_stats_smem(const CSArgs& a, int nf) { return a.sm_ws ? cs_stage_bytes(nf, a.sm_ws, a.sm_wc) : 0; }
 
 int sal_launch(seg_ctx* c, const uint8_t* rgb, float* sal_out, bool upsample) {
   // under graph capture the frame's k_set_io has zeroed the frame maxima
@@ -1722,9 +1786,9 @@ int sal_run(SalWS& s, cudaStream_t st, const void* rgb, bool rgb_f32, const SegI
 #define SEG_CS_STATS(n)                                 \
   case n:                                               \
     if (per_ch)                                         \
-      SEG_CUDA_TRY(seg_launch(k_cs_stats<n, 1>, g, 256, 0, st, ca));          \
+      SEG_CUDA_TRY(seg_launch(k_cs_stats<n, 1>, g, 256, cs_stats_smem(ca, 1), st, ca));          \
     else                                                \
-      SEG_CUDA_TRY(seg_launch(k_cs_stats<n, n>, g, 256, 0, st, ca));          \
+      SEG_CUDA_TRY(seg_launch(k_cs_stats<n, n>, g, 256, cs_stats_smem(ca, n), st, ca));          \
     break;
       SEG_CS_STATS(4) SEG_CS_STATS(5) SEG_CS_STATS(6) SEG_CS_STATS(7)
       SEG_CS_STATS(8) SEG_CS_STATS(9) SEG_CS_STATS(10) SEG_CS_STATS(11)
