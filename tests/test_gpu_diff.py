@@ -13,7 +13,10 @@ Parity bars (FP32 kernels, FP64 oracle):
            (tens per frame lie within 1e-6 of the range of the minimum, see
            oracle.prior_clip_ties), so the point derivative through the minimum
            (and the sign there) can land on another pixel.  Either choice is a
-           valid one-sided derivative; the difference stays a local patch;
+           valid one-sided derivative; the difference stays a local patch.
+           The exact FP64 gradient itself moves by up to ~7e-3 on these frames
+           when every input changes by one FP32 ulp
+           (test_oracle_grad.py::test_frame_gradient_is_ill_conditioned_at_float32_scale);
   and the directional derivative <dL/dframes, v> within 1e-3 of the oracle's
   central difference at h = 1e-7 (inputs kept 0.01 away from the feature kinks)."""
 import numpy as np
