@@ -33,6 +33,7 @@ __global__ void k_group_set_io(const __grid_constant__ GroupSetIoArgs a) {
   if (t == 0) {
     *m.io = m.v;
     m.w.bar->count = 0u;
+    m.w.bar->err = 0u;
   }
   if (t < 4) m.w.flags[t] = 0u;
   for (int b = t; b < m.w.B; b += blockDim.x) {

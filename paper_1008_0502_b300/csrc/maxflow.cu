@@ -88,6 +88,7 @@ struct MFShared {
   unsigned char b[MF_HN];  // residual bitmasks with halo
   unsigned char z[MF_HN];  // reach flags with halo
   int ok;
+  unsigned int bar_epoch;  // grid barriers passed in this launch (thread 0)
   unsigned int setmask;  // colours of the tiles this CTA pushed into during a phase
   unsigned int dmask;    // dirty tiles of a round (mf_dirty_mask)
   long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
@@ -98,10 +99,10 @@ struct MFShared {
 
 __device__ __forceinline__ long long mf_now() { return seg_now(); }
 
-// Grid-wide barrier with a bounded wait (seg_grid_sync); false once any CTA
-// has recorded a timeout.
+// Grid-wide barrier with a bounded wait (seg_grid_sync); false once this CTA's
+// wait or another CTA's has timed out.
 __device__ __forceinline__ bool mf_grid_sync(const MFArgs& a, MFShared& s) {
-  return seg_grid_sync(a.bar, a.status, a.timeout_ns, &s.ok);
+  return seg_grid_sync(a.bar, a.status, a.timeout_ns, &s.ok, &s.bar_epoch);
 }
 
 __device__ __forceinline__ unsigned int mf_flag_read(const MFArgs& a, unsigned int epoch) {
@@ -456,6 +457,7 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   constexpr bool all_on = !SKIP;
 
   const long long t_start = mf_now();
+  if (threadIdx.x == 0) s.bar_epoch = 0u;  // (read by thread 0 only, in the barriers)
   // ---- 1. init.  Cold: all n-link flows 0.  Warm (a.flow and the frame's warm
   // flag): the previous frame's n-link flows, clamped to the new capacities; a
   // node left with more outflow than its source capacity gets the deficit added

@@ -382,6 +382,7 @@ __global__ void k_set_io(SegIO* io, SegIO v, FrameWords w) {
   if (t == 0) {
     *io = v;
     w.bar->count = 0u;
+    w.bar->err = 0u;
   }
   if (t < 4) w.flags[t] = 0u;
   for (int b = t; b < w.B; b += blockDim.x) {

@@ -279,13 +279,13 @@ struct GmmDev {
 // maxflow.cu each: 0 = 32x16, 1 = 32x8, 2 = 64x8 nodes (one thread per node).
 #define SEG_CUT_TILES 3
 
-// Grid barrier words: the arrival counter and the generation that waiters poll
-// sit in separate 128-byte lines.
+// Grid barrier words, one 128-byte line: the arrival counter (zeroed before
+// every launch, never reset inside one) and the error word a CTA sets when its
+// wait times out.
 struct GridBar {
   unsigned int count;
-  unsigned int pad0[31];
-  unsigned int gen;
-  unsigned int pad1[31];
+  unsigned int err;
+  unsigned int pad[30];
 };
 
 __device__ __forceinline__ long long seg_now() {
@@ -295,39 +295,46 @@ __device__ __forceinline__ long long seg_now() {
 }
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.  Returns false
-// (in every thread of the CTA) once any CTA has recorded a timeout in status[0].
-// Arrival is an acq_rel atomic on the counter, release a release-add on the
-// generation word in another cache line, polled with acquire loads; the CTA
-// barriers before and after carry the other threads' writes (release and
-// acquire are cumulative), so no full fences are needed.  The timer is read
-// every 8 polls (a few microseconds of waiting at most).  ok: a shared-memory
-// word of the CTA.
-__device__ __forceinline__ bool seg_grid_sync(GridBar* bar, int* status, long long timeout_ns, int* ok_smem) {
+// (in every thread of the CTA) once the wait timed out here or in another CTA.
+// Barrier k of a launch (k = 1, 2, ..; *epoch_smem counts them, thread 0 only)
+// is passed once the counter reaches k * gridDim.x (modulo 2^32): every CTA adds 1 with a
+// release reduction on arrival and polls the counter with acquire loads, so a
+// barrier costs the reduction and one poll round trip (no generation word to
+// read before arriving, no status word after).  The CTA barriers before and
+// after carry the other threads' writes (release and acquire are cumulative).
+// Every 8 polls the waiter reads the clock and the error word: on its own
+// timeout it records SEG_ETIMEOUT in status[0] and sets the error word; a CTA
+// that sees the error word set returns false too (a CTA that passed the barrier
+// before the error was set sees it at its next barrier, where the CTA that timed
+// out never arrives).  ok: a shared-memory word of the CTA.
+__device__ __forceinline__ bool seg_grid_sync(GridBar* bar, int* status, long long timeout_ns, int* ok_smem,
+                                              unsigned int* epoch_smem) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int g, old;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&bar->gen) : "memory");
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&bar->count) : "memory");
+    const unsigned int target = (*epoch_smem + 1u) * gridDim.x;
+    *epoch_smem += 1u;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
     int ok = 1;
-    if (old + 1u == gridDim.x) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&bar->count) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->gen) : "memory");
-    } else {
-      const long long t0 = seg_now();
-      for (unsigned int k = 0;; ++k) {
-        unsigned int cur;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
-        if (cur != g) break;
-        if ((k & 7u) == 7u && seg_now() - t0 > timeout_ns) {
+    const long long t0 = seg_now();
+    for (unsigned int k = 0;; ++k) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->count) : "memory");
+      if ((int)(cur - target) >= 0) break;  // (the count runs at most gridDim.x past target; wraps safely)
+      if ((k & 7u) == 7u) {
+        unsigned int e;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(&bar->err) : "memory");
+        if (e) {
+          ok = 0;
+          break;
+        }
+        if (seg_now() - t0 > timeout_ns) {
           atomicCAS(&status[0], 0, SEG_ETIMEOUT);
+          asm volatile("st.relaxed.gpu.global.u32 [%0], 1;" ::"l"(&bar->err) : "memory");
           ok = 0;
           break;
         }
       }
     }
-    int st;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(st) : "l"(&status[0]) : "memory");
-    if (st == SEG_ETIMEOUT) ok = 0;
     *ok_smem = ok;
   }
   __syncthreads();
