@@ -380,10 +380,17 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, unsig
           ex -= dl;
         }
       }
+      // the neighbour heights first: they do not change during the push half, but
+      // the reverse-arc stores below (s.r[d ^ 1][nt]) would otherwise keep later
+      // directions' loads behind them
+      int hnv[ND];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) hnv[d] = s.h[hi + mf_hoff(d)];
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
+        if (ex <= 0 || hu != hnv[d] + 1) continue;
         const int rd = s.r[d][tid];
-        if (ex <= 0 || rd <= 0 || hu != s.h[hi + mf_hoff(d)] + 1) continue;
+        if (rd <= 0) continue;
         int dl = min(ex, rd);
         s.r[d][tid] = rd - dl;
         ex -= dl;
