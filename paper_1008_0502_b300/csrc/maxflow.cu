@@ -284,35 +284,46 @@ __device__ unsigned mf_tile_bfs(const MFArgs& a, MFShared& s, int tx, int ty, bo
 
 // z(v) = 1 if some residual arc u->v has z(u) = 1 (pull form, halo bitmasks).
 // Returns whether a node on the tile's rim changed, as mf_tile_bfs.
-// first: the first round -- the seeds (z = 1 where excess remains) and the
-// residual bitmasks of the tile and its halo come from e and r (no separate pass
-// and grid barrier), and every node of the tile is written.
+// first: the first round -- the seeds are z = 1 where excess remains (no
+// separate pass and grid barrier), and every node of the tile is written.  A
+// tile with no flag in it or its halo returns at once; otherwise the residual
+// bitmasks of the tile and its halo are formed from the residual planes.
 template <int ND, bool Q>
 __device__ unsigned mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, bool first, unsigned rows) {
   const int X0 = tx * MF_TW, Y0 = ty * MF_TH;
+  int seed = 0;
   for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
     int hy = i / MF_HX, hx = i - hy * MF_HX;
     int gy = Y0 - 1 + hy, gx = X0 - 1 + hx;
     bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W && ((rows >> hy) & 1u);
     const int gg = gy * a.W + gx;
-    if (!in) {
-      s.z[i] = 0;
-      s.b[i] = 0;
-    } else if (first) {
-      unsigned bits = 0u;
-#pragma unroll
-      for (int d = 0; d < ND; ++d) bits |= (a.r[d * a.N + gg] > 0 ? 1u : 0u) << d;
-      s.z[i] = a.e[gg] > 0 ? 1 : 0;
-      s.b[i] = (unsigned char)bits;
-    } else {
-      s.z[i] = a.z[gg];
-      s.b[i] = a.rm[gg];
-    }
+    const unsigned char zz = !in ? 0 : first ? (a.e[gg] > 0 ? 1 : 0) : a.z[gg];
+    s.z[i] = zz;
+    seed |= zz;
   }
   const int ly = threadIdx.x / MF_TW, lx = threadIdx.x - ly * MF_TW;
   const int gy = Y0 + ly, gx = X0 + lx;
   const bool valid = gy < a.H && gx < a.W && ((rows >> (ly + 1)) & 1u);
   const int hi = (ly + 1) * MF_HX + lx + 1;
+  if (!__syncthreads_or(seed)) {
+    // no flag in the tile or its halo: the tile's flags stay 0 this round and its
+    // residual planes are not read (most tiles of a frame in the first round)
+    if (first && valid) a.z[gy * a.W + gx] = 0;
+    return 0u;
+  }
+  // residual bitmasks of the tile and its halo, from the residual planes
+  for (int i = threadIdx.x; i < MF_HN; i += blockDim.x) {
+    int hy = i / MF_HX, hx = i - hy * MF_HX;
+    int gy2 = Y0 - 1 + hy, gx2 = X0 - 1 + hx;
+    bool in = gy2 >= 0 && gy2 < a.H && gx2 >= 0 && gx2 < a.W && ((rows >> hy) & 1u);
+    const int gg = gy2 * a.W + gx2;
+    unsigned bits = 0u;
+    if (in) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d) bits |= (a.r[d * a.N + gg] > 0 ? 1u : 0u) << d;
+    }
+    s.b[i] = (unsigned char)bits;
+  }
   __syncthreads();
   if (Q && threadIdx.x == 0) s.dirs = 0u;
   const unsigned char z0 = s.z[hi];
@@ -335,7 +346,6 @@ __device__ unsigned mf_tile_reach(const MFArgs& a, MFShared& s, int tx, int ty, 
     any = true;
   }
   if (valid && (any || first)) a.z[gy * a.W + gx] = s.z[hi];
-  if (valid && first) a.rm[gy * a.W + gx] = s.b[hi];
   if (Q) return mf_rim_dirs<ND>(s, valid && s.z[hi] != z0, lx, ly);
   const bool rim = ly == 0 || ly == MF_TH - 1 || lx == 0 || lx == MF_TW - 1;
   return __syncthreads_or(valid && rim && s.z[hi] != z0) != 0;  // (also orders the next tile's reuse)
