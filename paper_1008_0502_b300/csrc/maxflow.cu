@@ -448,15 +448,17 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, unsig
     }
   }
   *still_active = remain;
-  __syncthreads();
-  if (valid) {
+  // a visit that pushed and relabelled nothing (most tiles of a cycle's first
+  // visits: no node with excess) leaves global memory as it was
+  const bool changed = __syncthreads_or(work) != 0;
+  if (valid && changed) {
     a.e[g] = s.e[tid];
     a.rt[g] = s.rt[tid];
     a.h[g] = s.h[hi];
 #pragma unroll
     for (int d = 0; d < ND; ++d) a.r[d * N + g] = s.r[d][tid];
   }
-  return __syncthreads_or(work);
+  return changed;  // (the caller's barrier orders the next tile's reuse of shared memory)
 }
 
 // ---------------------------------------------------------------- the kernel
