@@ -358,12 +358,14 @@ int seg_profile_read_ex(seg_ctx* ctx, double* stage_ms, int* frames, long long* 
 
 /* Pipelined frames.  A frame's saliency map (Sec. 3) does not depend on the
  * previous frame -- only its prior does (Sec. 6) -- so with pipelining on, the
- * saliency of frame t runs on an internal stream while the context stream still
- * computes frame t-1's prior, terms and cut.  Results are identical to the
+ * saliency of frame t runs on an internal stream while frame t-1's prior, terms
+ * and cut still run on a second internal stream (each frame's prior, terms and
+ * cut start after the work enqueued on the context stream before the call, and
+ * the context stream waits for them).  Results are identical to the
  * unpipelined path, frame order and temporal state are unchanged, and outputs
  * are valid once the context stream passes them, as for seg_push_frame.
  * seg_pipeline_enable(ctx, 1) allocates a second buffer for S and the saliency
- * maximum (even and odd frames alternate) plus the internal stream;
+ * maximum (even and odd frames alternate) plus the two internal streams;
  * seg_pipeline_enable(ctx, 0) synchronises and
  * releases them.  Profiled frames (seg_profile_enable) run unpipelined.
  * seg_push_frame_ev: as seg_push_frame, where the frame's saliency starts once

@@ -284,6 +284,7 @@ extern "C" int seg_set_barrier_timeout(seg_ctx* c, int us) {
   if (!c || us < 1 || us > 60000000) return SEG_EINVAL;
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (c->s_front) SEG_CUDA_TRY(cudaStreamSynchronize(c->s_front));
+  if (c->s_back) SEG_CUDA_TRY(cudaStreamSynchronize(c->s_back));
   c->p.barrier_timeout_us = us;
   // the limit is baked into the captured graphs' kernel arguments: capture again
   if (c->graph_state == 1) cudaGraphExecDestroy(c->gexec);
@@ -548,6 +549,7 @@ extern "C" int seg_profile_read_ex(seg_ctx* c, double* stage_ms, int* frames, lo
 extern "C" int seg_sync(seg_ctx* c, int* cycles) {
   if (!c) return SEG_EINVAL;
   if (c->pipe_on) SEG_CUDA_TRY(cudaStreamSynchronize(c->s_front));
+  if (c->pipe_on) SEG_CUDA_TRY(cudaStreamSynchronize(c->s_back));
   SEG_CUDA_TRY(cudaStreamSynchronize(c->stream));
   SEG_CUDA_TRY(cudaMemcpy(c->status_host, c->status, 32, cudaMemcpyDeviceToHost));
   if (cycles) *cycles = c->status_host[1];
@@ -564,8 +566,9 @@ extern "C" int seg_sync(seg_ctx* c, int* cycles) {
 // the back of frame t-2, the last reader of its buffer.
 static void pipe_free(seg_ctx* c) {
   c->sal.light_ctas = 0;
-  if (!c->pipe_mem && !c->s_front) return;
+  if (!c->pipe_mem && !c->s_front && !c->s_back) return;
   if (c->s_front) cudaStreamSynchronize(c->s_front);
+  if (c->s_back) cudaStreamSynchronize(c->s_back);
   for (int k = 0; k < 2; ++k) {
     if (c->pipe_graph == 1) {
       cudaGraphExecDestroy(c->gf[k]);
@@ -577,6 +580,8 @@ static void pipe_free(seg_ctx* c) {
   }
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   c->ev_in = nullptr;
+  if (c->ev_ctx) cudaEventDestroy(c->ev_ctx);
+  c->ev_ctx = nullptr;
   for (int j = 0; j < 3; ++j) {
     if (c->ev_ring[j]) cudaEventDestroy(c->ev_ring[j]);
     c->ev_ring[j] = nullptr;
@@ -584,6 +589,8 @@ static void pipe_free(seg_ctx* c) {
   }
   if (c->s_front) cudaStreamDestroy(c->s_front);
   c->s_front = nullptr;
+  if (c->s_back) cudaStreamDestroy(c->s_back);
+  c->s_back = nullptr;
   if (c->pipe_mem) cudaFree(c->pipe_mem);
   c->pipe_mem = nullptr;
   c->pipe_on = 0;
@@ -614,11 +621,16 @@ extern "C" int seg_pipeline_enable(seg_ctx* c, int on) {
   c->pS[1] = (float*)m;
   c->psalmax[1] = (unsigned*)(m + o_salmax);
   c->io_front = (SegIO*)(m + o_io);
+  // the front and the back half run on two internal streams created one after the
+  // other (the runtime then gives them different hardware queues whatever streams
+  // the caller made before)
   bool ok = cudaStreamCreateWithFlags(&c->s_front, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&c->s_back, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k)
     ok = cudaEventCreateWithFlags(&c->ev_front[k], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_back[k], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_ctx, cudaEventDisableTiming) == cudaSuccess;
   for (int j = 0; j < 3 && ok; ++j)
     ok = cudaEventCreateWithFlags(&c->ev_ring[j], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -718,15 +730,27 @@ extern "C" int seg_push_frame_ev(seg_ctx* c, const uint8_t* rgb, float* sal, flo
     return rc;
   }
   SEG_CUDA_TRY(cudaEventRecord(c->ev_front[k], c->s_front));
-  // back, in frame order on the context stream
-  SEG_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_front[k], 0));
   if (c->pipe_graph == 1) {
+    // back, in frame order on the internal back stream, after the frame's front
+    // and after the work enqueued on the context stream so far (readers of the
+    // output buffers, slot and stream resets); the context stream then waits for
+    // it, so the outputs are valid once the context stream passes them
+    SEG_CUDA_TRY(cudaEventRecord(c->ev_ctx, c->stream));
+    SEG_CUDA_TRY(cudaStreamWaitEvent(c->s_back, c->ev_ctx, 0));
+    SEG_CUDA_TRY(cudaStreamWaitEvent(c->s_back, c->ev_front[k], 0));
     SegIO v = {rgb, s, pr, mask, (long long*)ct};
     FrameWords w = {nullptr, c->B, c->mf.cut_acc, c->mf.flags, c->mf.bar};
-    k_set_io<<<1, 32, 0, c->stream>>>(c->io, v, w);
+    k_set_io<<<1, 32, 0, c->s_back>>>(c->io, v, w);
     SEG_CUDA_TRY(cudaGetLastError());
-    SEG_CUDA_TRY(cudaGraphLaunch(c->gb[k], c->stream));
-  } else {
+    SEG_CUDA_TRY(cudaGraphLaunch(c->gb[k], c->s_back));
+    SEG_CUDA_TRY(cudaEventRecord(c->ev_back[k], c->s_back));
+    SEG_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_back[k], 0));
+    c->pipe_t++;
+    return SEG_OK;
+  }
+  // eager launches: back, in frame order on the context stream
+  SEG_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_front[k], 0));
+  {
     pipe_select(c, k);
     rc = pt_launch_back(c, s, pr, rgb);
     if (!rc) rc = run_mincut(c, c->cs, c->ct, c->ncap, mask, c->prev_mask, (int64_t*)ct, true);

@@ -431,10 +431,11 @@ struct seg_ctx {
   int* flow;            // warm start: nbr/2 planes of B*N n-link flows
   unsigned char* warm;  // [B] flow valid for the stream
   // pipelined frames (seg_pipeline_enable): frame t+1's saliency on s_front
-  // while frame t's prior, terms and cut run on stream
+  // while frame t's prior, terms and cut run on s_back (captured graphs) or on
+  // stream (eager launches); stream waits for every frame's back
   int pipe_on;
-  cudaStream_t s_front;
-  cudaEvent_t ev_front[2], ev_back[2], ev_in;
+  cudaStream_t s_front, s_back;
+  cudaEvent_t ev_front[2], ev_back[2], ev_in, ev_ctx;
   float* pS[2];           // S of even / odd frames ([0] is sal.S)
   unsigned* psalmax[2];   // saliency maxima of even / odd frames ([0] is sal.salmax)
   SegIO* io_front;        // the front's frame pointers (graph replays)
