@@ -418,9 +418,11 @@ def batched_suite(seg, torch, clip_dev, plain_fps, hbm):
 def serving_suite(seg, torch, horizon_s=1.0, budget_gb=32.0):
     """The serving workload: Poisson arrivals (20 streams/s) of streams lasting
     60-600 frames at 640x480, 1280x720 or 1920x1080, served by the
-    continuous-batching server with admission by HBM footprint (8 slots per
-    group), and the same requests through plain per-stream contexts (one slot per
-    context, each stream on a CUDA stream of its own, the same admission)."""
+    continuous-batching server with admission by HBM footprint (slots per group
+    by resolution, pipelined groups; also unpipelined, and with 8 slots at every
+    resolution), and the same requests through plain per-stream contexts (one slot
+    per context, unpipelined, each stream on a CUDA stream of its own, the same
+    admission)."""
     from paper_1008_0502_b300 import serve, synth
     rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 5))
     sizes = [(480, 640), (720, 1280), (1080, 1920)]
@@ -449,8 +451,9 @@ def serving_suite(seg, torch, horizon_s=1.0, budget_gb=32.0):
     warm.close()
     torch.cuda.synchronize()
     out = {}
-    for name, slots in (("served", "auto"), ("served_8", 8), ("plain", 1)):
-        srv = serve.Server(seg.params_from(VGA), int(budget_gb * 2**30), slots=slots)
+    for name, slots, pipe in (("served", "auto", True), ("served_unpipelined", "auto", False),
+                              ("served_8", 8, False), ("plain", 1, False)):
+        srv = serve.Server(seg.params_from(VGA), int(budget_gb * 2**30), slots=slots, pipeline=pipe)
         stats = srv.run(requests(), clock="wall")
         waits = [r.admitted - r.arrival for r in srv.results.values() if r.admitted >= 0] or [0.0]
         srv.close()
@@ -461,12 +464,15 @@ def serving_suite(seg, torch, horizon_s=1.0, budget_gb=32.0):
     keys = ("frames_per_s", "latency_ms", "wall_s", "groups", "admission_wait_ms")
     res.update({"vs_plain": res["frames_per_s"] / out["plain"]["frames_per_s"],
                 "plain": {k: out["plain"][k] for k in keys},
+                "served_unpipelined": {k: out["served_unpipelined"][k] for k in keys},
                 "served_8_slots": {k: out["served_8"][k] for k in keys},
                 "arrivals_per_s": 20, "horizon_s": horizon_s, "hbm_budget_gb": budget_gb,
                 "mix": "Poisson arrivals, 60-600 frames, 640x480 / 1280x720 / 1920x1080; served: slots per "
                        "group by resolution (1.3 Mpx per group: 4 / 1 / 1), empty slots skipped, steps "
-                       "overlapping (3 in flight per group); served_8_slots: 8 slots at every resolution; "
-                       "plain: one context per stream"})
+                       "overlapping (3 in flight per group), pipelined groups (a step's saliency beside the "
+                       "previous step's prior, terms and cut); served_unpipelined: the same without "
+                       "pipelining; served_8_slots: 8 slots at every resolution, unpipelined; plain: one "
+                       "unpipelined context per stream"})
     return res
 
 

@@ -24,8 +24,14 @@ idle, are batched, and a frame that fills the GPU alone runs alone.
   (``seg_set_stream_active``), and the kernels skip its frame.
 * Steps overlap: the host does not wait for a step before launching the next
   one; each group keeps up to ``depth`` steps in flight and collects a step's
-  results (latencies, kept outputs, device status) once its completion event
-  has passed.
+  results (latencies, kept outputs) once its completion event has passed.  The
+  device status (sticky until read) is read every ``STATUS_EVERY`` steps and
+  whenever a group drains, since reading it waits for all of the group's work.
+* Pipelined groups (``pipeline=True``): each group's context runs a step's
+  saliency beside the previous step's prior, terms and cut (seg_pipeline_enable),
+  with the frames copied into a ring of three input buffers on a stream of the
+  group's own, so nothing of a step waits for the step before except what the
+  method orders (the prior needs the previous mask).
 * Per-frame latency is client-side: from the frame's submission (the host
   taking it for a step) to its mask and cut being ready on the device (the
   step's completion event, read on the host clock through a reference event).
@@ -81,18 +87,28 @@ class StreamResult:
 
 
 class _Group:
-    def __init__(self, H, W, slots, params):
+    def __init__(self, H, W, slots, params, pipeline=False):
         self.H, self.W, self.B = H, W, slots
         self.bytes = 0  # its workspace, charged to the server's budget
         self.stream = torch.cuda.Stream()
-        self.ctx = seg.Segmenter(H, W, params, stream=self.stream, batch=slots)
-        self.inbuf = torch.zeros(slots, H, W, 3, dtype=torch.uint8, device="cuda")
+        self.pipeline = bool(pipeline)
+        self.ctx = seg.Segmenter(H, W, params, stream=self.stream, batch=slots, pipeline=self.pipeline)
+        # a pipelined group's next frames are copied on a stream of their own into a
+        # ring of input buffers (a buffer is reused once the step that read it is done),
+        # so the copy does not wait for the step before, and a step's saliency can
+        # overlap the previous step's prior, terms and cut
+        nbuf = 3 if self.pipeline else 1
+        self.inbufs = [torch.zeros(slots, H, W, 3, dtype=torch.uint8, device="cuda") for _ in range(nbuf)]
+        self.buf_done = [None] * nbuf  # completion event of the last step that read each buffer
+        self.copy_stream = torch.cuda.Stream() if self.pipeline else self.stream
+        self.nstep = 0
         self.outs = self.ctx.empty_outputs()
         self.sid = [None] * slots
         self.pos = [0] * slots
         self.fresh = [False] * slots
         self.on = [True] * slots  # the slots' flags on the device (all on at creation)
         self.inflight = []        # launched steps not yet collected, oldest first
+        self.collected = 0        # steps collected (the device status is read every STATUS_EVERY)
 
     def free_slot(self):
         for b in range(self.B):
@@ -107,10 +123,15 @@ class _Group:
         self.ctx.close()
 
 
+STATUS_EVERY = 16  # steps of a group between reads of its device status (each read waits for the group)
+
+
 class Server:
     def __init__(self, params: seg.seg_params, hbm_budget_bytes: int, slots: int | str = "auto",
-                 keep_outputs: bool = False, depth: int = 3, group_pixels: int = 1_300_000):
+                 keep_outputs: bool = False, depth: int = 3, group_pixels: int = 1_300_000,
+                 pipeline: bool = False):
         self.params = params
+        self.pipeline = bool(pipeline)  # groups run pipelined contexts (seg_pipeline_enable)
         self.depth = max(1, int(depth))  # steps in flight per group
         self.budget = int(hbm_budget_bytes)
         self.used = 0
@@ -134,6 +155,16 @@ class Server:
             return max(1, min(8, self.group_pixels // (H * W)))
         return int(self.slots)
 
+    def group_bytes(self, H: int, W: int) -> int:
+        """Device bytes of a new H x W group: the context's workspace plus, when
+        pipelined, the library's second saliency buffers and frame ring and this
+        server's input ring (about 19 bytes per pixel of the batch, rounded up)."""
+        B = self.slots_for(H, W)
+        need = seg.workspace_bytes(B, H, W, self.params)
+        if self.pipeline:
+            need += 2 * 3 * 3 * B * H * W + 4 * B * H * W + (1 << 20)
+        return need
+
     # -- admission
     def submit(self, req: Request):
         self.queue.append(req)
@@ -155,7 +186,7 @@ class Server:
                         slot = (g, b)
                         break
             if slot is None:
-                need = seg.workspace_bytes(self.slots_for(H, W), H, W, self.params)
+                need = self.group_bytes(H, W)
                 if need > self.budget:
                     self.results[req.sid].refused = "its group's workspace exceeds the HBM budget"
                     continue
@@ -203,7 +234,7 @@ class Server:
         with the idle groups freed)."""
         for attempt in range(2):
             try:
-                g = _Group(H, W, self.slots_for(H, W), self.params)
+                g = _Group(H, W, self.slots_for(H, W), self.params, pipeline=self.pipeline)
             except seg.SegError as e:
                 if e.code != seg.SEG_ENOMEM:
                     raise
@@ -221,12 +252,17 @@ class Server:
 
     # -- one step of every group with an active slot
     def _collect(self, g: _Group):
-        """Waits for g's oldest step in flight and records its results."""
+        """Waits for g's oldest step in flight and records its results.  The device
+        status (sticky until read) is read every STATUS_EVERY steps and when the
+        group has nothing else in flight: reading it waits for all of the group's
+        work, which would otherwise keep only one step in flight."""
         done, stamp, frames, kept = g.inflight.pop(0)
         done.synchronize()
-        code, _ = g.ctx.sync()
-        if code != 0:
-            raise seg.SegError(code, "serve step")
+        g.collected += 1
+        if not g.inflight or g.collected % STATUS_EVERY == 0:
+            code, _ = g.ctx.sync()
+            if code != 0:
+                raise seg.SegError(code, "serve step")
         t_done = self._t_ref + self._ev_ref.elapsed_time(done) / 1e3  # the host clock
         for b, sid, t_sub in frames:
             r = self.results[sid]
@@ -248,8 +284,13 @@ class Server:
                 continue
             while len(g.inflight) >= self.depth:
                 self._collect(g)
-            g.stream.wait_stream(outer)  # frames produced on the caller's stream are ready
-            with torch.cuda.stream(g.stream):
+            j = g.nstep % len(g.inbufs)
+            inbuf = g.inbufs[j]
+            cs = g.copy_stream  # (the group's own stream unless pipelined)
+            cs.wait_stream(outer)  # frames produced on the caller's stream are ready
+            if g.buf_done[j] is not None:  # the step that last read this buffer is done
+                cs.wait_event(g.buf_done[j])
+            with torch.cuda.stream(cs):
                 frames = []
                 for b in range(g.B):
                     sid = g.sid[b]
@@ -261,18 +302,25 @@ class Server:
                     if g.fresh[b]:
                         g.ctx.reset(stream_index=b)
                         g.fresh[b] = False
-                    g.inbuf[b].copy_(self.requests[sid].frame(g.pos[b]), non_blocking=True)
+                    inbuf[b].copy_(self.requests[sid].frame(g.pos[b]), non_blocking=True)
                     frames.append((b, sid, time.perf_counter()))
+                # (pipelined: the saliency starts once the copies are done; the prior,
+                # terms and cut, and the group's stream, come after the previous step)
                 if g.B > 1:
-                    sal, pr, mask, cut = g.ctx.push_frame(g.inbuf, *g.outs)
+                    sal, pr, mask, cut = g.ctx.push_frame(inbuf, *g.outs)
                 else:  # a single-stream context takes one (H, W, 3) frame
-                    sal, pr, mask, cut = g.ctx.push_frame(g.inbuf[0], *g.outs)
+                    sal, pr, mask, cut = g.ctx.push_frame(inbuf[0], *g.outs)
                     pr, mask = pr.unsqueeze(0), mask.unsqueeze(0)
+            with torch.cuda.stream(g.stream):  # the step's outputs are ready on the group's stream
+                if cs is not g.stream:
+                    g.stream.wait_stream(cs)
                 done = torch.cuda.Event(enable_timing=True)
                 done.record(g.stream)
                 kept = {}
                 if self.keep:
                     kept = {b: (mask[b].clone(), pr[b].clone(), cut[b].clone()) for b, _, _ in frames}
+            g.buf_done[j] = done
+            g.nstep += 1
             g.inflight.append((done, now, frames, kept))
             for b, sid, _ in frames:  # frame count decides when a slot frees (no wait for the device)
                 g.pos[b] += 1
@@ -307,6 +355,10 @@ class Server:
             while g.inflight:
                 self._collect(g)
         wall = time.perf_counter() - t0
+        for g in self.groups:  # (every group drained above, so this only reads the status)
+            code, _ = g.ctx.sync()
+            if code != 0:
+                raise seg.SegError(code, "serve step")
         frames = sum(len(r.frame_ms) for r in self.results.values())
         lat = np.array([x for r in self.results.values() for x in r.frame_ms]) if frames else np.zeros(1)
         return {"wall_s": wall, "frames": frames, "frames_per_s": frames / wall if wall > 0 else 0.0,

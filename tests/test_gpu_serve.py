@@ -32,7 +32,11 @@ def _solo(seg, params, frames):
     return out
 
 
-def test_served_streams_equal_solo_runs(S):
+@pytest.mark.parametrize("pipeline", [False, True])
+def test_served_streams_equal_solo_runs(S, pipeline):
+    """Streams arriving over several steps, waiting for slots, finishing at different
+    steps (their slots switched off, then reset for the next stream): each served
+    stream equals the same stream run alone, with groups pipelined or not."""
     seg, serve = S
     params = seg.params_from(O.CONFIG_SMALL)
     specs = [  # (sid, H, W, n_frames, arrival step)
@@ -43,7 +47,10 @@ def test_served_streams_equal_solo_runs(S):
         f, _ = synth.clip_small(n, H=H, W=W, seed=synth.SEED_BASE + 50 + sid, radius=min(15, H // 5))
         clips[sid] = torch.from_numpy(f).cuda()
     budget = seg.workspace_bytes(2, 120, 160, params) + seg.workspace_bytes(2, 90, 120, params)
-    srv = serve.Server(params, budget, slots=2, keep_outputs=True)
+    if pipeline:
+        budget = sum(serve.Server(params, 0, slots=2, pipeline=True).group_bytes(h, w) for h, w in ((120, 160),
+                                                                                              (90, 120)))
+    srv = serve.Server(params, budget, slots=2, keep_outputs=True, pipeline=pipeline)
     reqs = [serve.Request(sid, clips[sid], n, arr) for sid, H, W, n, arr in specs]
     stats = srv.run(reqs, clock="steps")
     assert stats["groups"] == 2 and stats["frames"] == sum(s[3] for s in specs)

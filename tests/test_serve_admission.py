@@ -19,7 +19,7 @@ class _FakeGroup:
     fail_allocs = 0  # the next n creations fail as a device allocation would (host-side fault injection)
     closed = []
 
-    def __init__(self, H, W, slots, params):
+    def __init__(self, H, W, slots, params, pipeline=False):
         if _FakeGroup.fail_allocs > 0:
             _FakeGroup.fail_allocs -= 1
             raise seg.SegError(seg.SEG_ENOMEM, "seg_create_batch")
