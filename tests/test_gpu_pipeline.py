@@ -69,3 +69,40 @@ def test_async_host_frames_equal_device_frames(S):
         assert torch.equal(masks[t], ref[t][2]), t
         assert int(cuts[t][0]) == int(ref[t][3][0]), t
     sg.close()
+
+
+def test_context_stream_orders_reused_outputs(S):
+    """One set of output buffers for every frame, each frame's outputs copied on the
+    context stream right after the call: with pipelining the prior, terms and cut run
+    on an internal stream, yet the context stream must pass a frame's outputs only
+    once they are complete, and the next frame must not overwrite them before the
+    work enqueued on the context stream has read them.  Both the plain C call
+    (seg_push_frame, no input event) and seg_push_frame_ev are checked against the
+    unpipelined path."""
+    import ctypes as C
+    p = S.params_from(O.CONFIG_SMALL)
+    frames = synth.clip_small(8, seed=synth.SEED_BASE + 23)[0]
+    ref = _run(S, p, frames, 1, False)
+    dev = torch.from_numpy(frames).cuda()
+    torch.cuda.synchronize()  # (the frames are on the device before any context stream reads them)
+    for use_ev in (False, True):
+        sg = S.Segmenter(120, 160, p, pipeline=True)
+        sal, pr, mask, cut = sg.empty_outputs()
+        got = []
+        for t in range(len(frames)):
+            if use_ev:
+                sg.push_frame(dev[t], sal, pr, mask, cut)
+            else:
+                with torch.cuda.stream(sg.stream):
+                    code = S.lib.seg_push_frame(sg.handle, C.c_void_p(dev[t].data_ptr()), C.c_void_p(sal.data_ptr()),
+                                                C.c_void_p(pr.data_ptr()), C.c_void_p(mask.data_ptr()),
+                                                C.c_void_p(cut.data_ptr()))
+                assert code == 0
+            with torch.cuda.stream(sg.stream):
+                got.append([x.clone() for x in (sal, pr, mask, cut)])
+        code, _ = sg.sync()
+        assert code == 0
+        for t in range(len(frames)):
+            for u, v in zip(got[t], ref[t]):
+                assert torch.equal(u.cpu(), v), (use_ev, t)
+        sg.close()
