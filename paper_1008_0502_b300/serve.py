@@ -128,7 +128,7 @@ STATUS_EVERY = 16  # steps of a group between reads of its device status (each r
 
 class Server:
     def __init__(self, params: seg.seg_params, hbm_budget_bytes: int, slots: int | str = "auto",
-                 keep_outputs: bool = False, depth: int = 3, group_pixels: int = 1_300_000,
+                 keep_outputs: bool = False, depth: int = 2, group_pixels: int = 1_300_000,
                  pipeline: bool = False):
         self.params = params
         self.pipeline = bool(pipeline)  # groups run pipelined contexts (seg_pipeline_enable)
