@@ -469,7 +469,7 @@ def serving_suite(seg, torch, horizon_s=1.0, budget_gb=32.0):
                 "arrivals_per_s": 20, "horizon_s": horizon_s, "hbm_budget_gb": budget_gb,
                 "mix": "Poisson arrivals, 60-600 frames, 640x480 / 1280x720 / 1920x1080; served: slots per "
                        "group by resolution (1.3 Mpx per group: 4 / 1 / 1), empty slots skipped, steps "
-                       "overlapping (2 in flight per group), pipelined groups (a step's saliency beside the "
+                       "overlapping (2 in flight per group, 1 while 6 or more groups are active), pipelined groups (a step's saliency beside the "
                        "previous step's prior, terms and cut); served_unpipelined: the same without "
                        "pipelining; served_8_slots: 8 slots at every resolution, unpipelined; plain: one "
                        "unpipelined context per stream"})

@@ -24,7 +24,9 @@ idle, are batched, and a frame that fills the GPU alone runs alone.
   (``seg_set_stream_active``), and the kernels skip its frame.
 * Steps overlap: the host does not wait for a step before launching the next
   one; each group keeps up to ``depth`` steps in flight and collects a step's
-  results (latencies, kept outputs) once its completion event has passed.  The
+  results (latencies, kept outputs) once its completion event has passed.  With
+  ``busy_groups`` or more groups active the device is full and more steps in
+  flight would only queue, so each group then keeps one.  The
   device status (sticky until read) is read every ``STATUS_EVERY`` steps and
   whenever a group drains, since reading it waits for all of the group's work.
 * Pipelined groups (``pipeline=True``): each group's context runs a step's
@@ -129,10 +131,11 @@ STATUS_EVERY = 16  # steps of a group between reads of its device status (each r
 class Server:
     def __init__(self, params: seg.seg_params, hbm_budget_bytes: int, slots: int | str = "auto",
                  keep_outputs: bool = False, depth: int = 2, group_pixels: int = 1_300_000,
-                 pipeline: bool = False):
+                 pipeline: bool = False, busy_groups: int = 6):
         self.params = params
         self.pipeline = bool(pipeline)  # groups run pipelined contexts (seg_pipeline_enable)
         self.depth = max(1, int(depth))  # steps in flight per group
+        self.busy_groups = int(busy_groups)  # with at least this many active groups, one step in flight (0: off)
         self.budget = int(hbm_budget_bytes)
         self.used = 0
         self.slots = slots  # slots per group, or "auto": group_pixels // (H * W), 1 to 8
@@ -279,10 +282,13 @@ class Server:
         self._admit(now)
         outer = torch.cuda.current_stream()
         launched = 0
+        depth = self.depth
+        if self.busy_groups and sum(1 for g in self.groups if g.active()) >= self.busy_groups:
+            depth = 1  # the device is full: more steps in flight would only queue
         for g in self.groups:
             if not g.active():
                 continue
-            while len(g.inflight) >= self.depth:
+            while len(g.inflight) >= depth:
                 self._collect(g)
             j = g.nstep % len(g.inbufs)
             inbuf = g.inbufs[j]
