@@ -16,7 +16,8 @@
 //     memory; pushes into a neighbouring, idle tile go straight to global
 //     memory).  A grid barrier separates phases; a colour with no tile that can
 //     hold an active node is skipped, barrier included.
-//  3. Global relabel every gr_every cycles: exact BFS distances to the sink in
+//  3. Global relabel every gr_every cycles (one is skipped, never two in a row,
+//     after a cycle that left only a little work): exact BFS distances to the sink in
 //     the residual graph, computed as a monotone fixpoint (tile-local
 //     relaxation in shared memory, rounds of tiles until no value changes);
 //     unreachable nodes get height INF and never become active again.
@@ -65,6 +66,13 @@
 #define MF_HY (MF_TH + 2)
 #define MF_HN (MF_HX * MF_HY)
 #define MF_ROUND_CAP (1 << 20)  // fixpoint rounds per cut; uniform across CTAs
+#ifndef MF_SKIP_GR_TILES
+// A cycle with at most this much activity (tiles left active plus colours of tiles
+// pushed into, summed over its phases and CTAs) is not followed by a global relabel
+// (640x480 clip: 40 -> cut 96 -> 93 us per frame; 4 and 12 ~ no change; 80 and more
+// slower, two-cycle frames then need three).
+#define MF_SKIP_GR_TILES 40
+#endif
 #define MF_ON_CACHE 512         // frames whose run flags each CTA keeps in shared memory
 
 namespace MF_NS {
@@ -90,6 +98,7 @@ struct MFShared {
   int ok;
   unsigned int bar_epoch;  // grid barriers passed in this launch (thread 0)
   unsigned int setmask;  // colours of the tiles this CTA pushed into during a phase
+  unsigned int my_tiles;  // tiles this CTA left active during a phase (thread 0)
   unsigned int dmask;    // dirty tiles of a round (mf_dirty_mask)
   long long t_acc[4], t_last;  // phase timing (block 0, thread 0; not in registers)
   unsigned char onf[MF_ON_CACHE];  // the frames' run flags (a.on) when there are at most MF_ON_CACHE
@@ -416,6 +425,7 @@ __device__ bool mf_discharge(const MFArgs& a, MFShared& s, int tx, int ty, unsig
           const int nty = (gy + mf_dy(d)) / MF_TH, ntx = (gx + mf_dx(d)) / MF_TW;
           a.tact[nty * a.ntx + ntx] = 1;
           atomicOr(&s.setmask, 1u << (((nty & 1) << 1) | (ntx & 1)));  // its colour
+
         }
       }
       if (ex != e0) {
@@ -467,7 +477,9 @@ __device__ __forceinline__ bool cap_ok(int c) { return c >= 0 && c <= (1 << 24);
 // The whole cut, for one CTA.  SKIP: some frame of the batch is not run (its
 // rows are left out); without it every test of the run flags folds away and the
 // code is that of a single frame.
-template <int ND, bool SKIP, bool Q>
+// LEAN: the single-frame kernel, which also skips a relabel after a quiet cycle
+// (measured there; a stack of frames keeps its fixed relabel schedule).
+template <int ND, bool SKIP, bool Q, bool LEAN = false>
 __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   const int N = a.N, W = a.W, H = a.H;
   const int nthr = gridDim.x * blockDim.x;
@@ -593,6 +605,9 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   unsigned int flag = 15u;
   int color = 0, executed = 0, since_gr = 0;
   bool relabel = true;
+  // activity since the last relabel (tiles left active, colours pushed into, summed
+  // over the CTAs and phases), the same in every CTA; bit 31: the last relabel was skipped
+  unsigned act_since_gr = 0u;
   for (;;) {
     int tries = 0;
     while (tries < 4 && !((flag >> color) & 1u)) {
@@ -604,10 +619,17 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
       break;
     }
     if (executed >= 4 * a.max_cycles) break;
-    // ---- 3. global relabel
+    // ---- 3. global relabel (a cycle that left only a few tiles to work on goes on
+    // without one, at most once in a row: the labels stay valid, and a relabel of
+    // every tile would cost more than the few visits it could shorten)
+    if (LEAN && !relabel && since_gr >= 4 * a.gr_every && act_since_gr <= MF_SKIP_GR_TILES) {
+      since_gr = 0;
+      act_since_gr = 0x80000000u;
+    }
     if (relabel || since_gr >= 4 * a.gr_every) {
       relabel = false;
       since_gr = 0;
+      act_since_gr = 0u;
       for (int rnd = 0;; ++rnd) {
         const bool first = rnd == 0;
         mf_flag_begin(a, epoch);
@@ -661,7 +683,10 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
     // ---- 2. one colour phase
     {
       mf_flag_begin(a, epoch);
-      if (threadIdx.x == 0) s.setmask = 0u;
+      if (threadIdx.x == 0) {
+        s.setmask = 0u;
+        s.my_tiles = 0u;
+      }
       __syncthreads();
       const int cy = color >> 1, cx = color & 1;
       const int ntx_c = (a.ntx - cx + 1) / 2, nty_c = (a.nty - cy + 1) / 2;
@@ -674,14 +699,24 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
         const unsigned rows = mf_tile_rows(a, s, all_on, ty * MF_TH, &any);
         mf_discharge<ND>(a, s, tx, ty, rows, &remain);
         __syncthreads();
-        if (threadIdx.x == 0) a.tact[t] = remain ? 1 : 0;
+        if (threadIdx.x == 0) {
+          a.tact[t] = remain ? 1 : 0;
+          if (LEAN) s.my_tiles += remain ? 1u : 0u;
+        }
         any_remain |= remain;
       }
       __syncthreads();
       const unsigned int bits = s.setmask | (any_remain ? 16u : 0u);
-      if (bits && threadIdx.x == 0) atomicOr(&a.flags[epoch % 3], bits);
+      if (threadIdx.x == 0) {
+        if (bits) atomicOr(&a.flags[epoch % 3], bits);
+        // bits 8 and up: this CTA's activity (tiles left active, colours of tiles pushed into),
+        // added beside the OR-ed bits without touching them
+        const unsigned act = s.my_tiles + __popc(s.setmask);
+        if (LEAN && act) atomicAdd(&a.flags[epoch % 3], min(act, 0xffffu) << 8);
+      }
       if (!mf_grid_sync(a, s)) return;
       const unsigned int f = mf_flag_read(a, epoch);
+      if (LEAN) act_since_gr += f >> 8;
       ++epoch;
       flag = ((flag | f) & 15u & ~(1u << color)) | (((f >> 4) & 1u) << color);
       color = (color + 1) & 3;
@@ -789,9 +824,9 @@ template <int ND>
 __global__ void __launch_bounds__(MF_THREADS, MF_MINB) k_maxflow(MFArgs a) {
   __shared__ MFShared s;
   if (a.frontier)
-    mf_run<ND, false, true>(a, s);
+    mf_run<ND, false, true, true>(a, s);
   else
-    mf_run<ND, false, false>(a, s);
+    mf_run<ND, false, false, true>(a, s);
 }
 
 // A stack of frames (a batch context): empty slots are left out when a.on marks
