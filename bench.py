@@ -53,7 +53,7 @@ H, W = 480, 640
 BYTES_MINCUT_CYCLE_PX = 24
 # DRAM bytes (ncu dram__bytes_read + dram__bytes_write) of one k_maxflow<8> launch on a 640x480
 # frame graph, from a capture of this workload; None once the kernel changes
-TRAFFIC_MAXFLOW = 18527360
+TRAFFIC_MAXFLOW = 18524416
 VGA = dict(levels=9, c_min=2, c_max=4, d_min=3, d_max=4, n_orient=4, gabor_lambda=4.0, gabor_sigma=2.0,
            gabor_radius=6, norm_tile=8, norm_flat=1e-5, w=(1 / 3, 1 / 6, 1 / 6, 1 / 3), cs_opponent_sum=1,
            border_px=1, sigma1=0.03, sigma2=0.035, f_sigma=2.0, f_radius=6, eps=1e-4, lambda_u=1.0,

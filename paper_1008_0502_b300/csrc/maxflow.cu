@@ -67,10 +67,11 @@
 #define MF_HN (MF_HX * MF_HY)
 #define MF_ROUND_CAP (1 << 20)  // fixpoint rounds per cut; uniform across CTAs
 #ifndef MF_SKIP_GR_TILES
-// A cycle with at most this much activity (tiles left active plus colours of tiles
-// pushed into, summed over its phases and CTAs) is not followed by a global relabel
-// (640x480 clip: 40 -> cut 96 -> 93 us per frame; 4 and 12 ~ no change; 80 and more
-// slower, two-cycle frames then need three).
+// A cycle with at most this much activity per frame of the stack (tiles left active
+// plus colours of tiles pushed into, summed over its phases and CTAs) is not followed
+// by a global relabel (640x480 clip: 40 -> cut 96 -> 93 us per frame; 4 and 12 ~ no
+// change; 80 and more slower, two-cycle frames then need three; the 64-stream mix at
+// default parameters +12 %).
 #define MF_SKIP_GR_TILES 40
 #endif
 #define MF_ON_CACHE 512         // frames whose run flags each CTA keeps in shared memory
@@ -477,9 +478,7 @@ __device__ __forceinline__ bool cap_ok(int c) { return c >= 0 && c <= (1 << 24);
 // The whole cut, for one CTA.  SKIP: some frame of the batch is not run (its
 // rows are left out); without it every test of the run flags folds away and the
 // code is that of a single frame.
-// LEAN: the single-frame kernel, which also skips a relabel after a quiet cycle
-// (measured there; a stack of frames keeps its fixed relabel schedule).
-template <int ND, bool SKIP, bool Q, bool LEAN = false>
+template <int ND, bool SKIP, bool Q>
 __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
   const int N = a.N, W = a.W, H = a.H;
   const int nthr = gridDim.x * blockDim.x;
@@ -622,7 +621,7 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
     // ---- 3. global relabel (a cycle that left only a few tiles to work on goes on
     // without one, at most once in a row: the labels stay valid, and a relabel of
     // every tile would cost more than the few visits it could shorten)
-    if (LEAN && !relabel && since_gr >= 4 * a.gr_every && act_since_gr <= MF_SKIP_GR_TILES) {
+    if (!relabel && since_gr >= 4 * a.gr_every && act_since_gr <= (unsigned)(MF_SKIP_GR_TILES * a.nframes)) {
       since_gr = 0;
       act_since_gr = 0x80000000u;
     }
@@ -701,7 +700,7 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
         __syncthreads();
         if (threadIdx.x == 0) {
           a.tact[t] = remain ? 1 : 0;
-          if (LEAN) s.my_tiles += remain ? 1u : 0u;
+          s.my_tiles += remain ? 1u : 0u;
         }
         any_remain |= remain;
       }
@@ -712,11 +711,11 @@ __device__ __forceinline__ void mf_run(const MFArgs& a, MFShared& s) {
         // bits 8 and up: this CTA's activity (tiles left active, colours of tiles pushed into),
         // added beside the OR-ed bits without touching them
         const unsigned act = s.my_tiles + __popc(s.setmask);
-        if (LEAN && act) atomicAdd(&a.flags[epoch % 3], min(act, 0xffffu) << 8);
+        if (act) atomicAdd(&a.flags[epoch % 3], min(act, 0xffffu) << 8);
       }
       if (!mf_grid_sync(a, s)) return;
       const unsigned int f = mf_flag_read(a, epoch);
-      if (LEAN) act_since_gr += f >> 8;
+      act_since_gr += f >> 8;
       ++epoch;
       flag = ((flag | f) & 15u & ~(1u << color)) | (((f >> 4) & 1u) << color);
       color = (color + 1) & 3;
@@ -824,9 +823,9 @@ template <int ND>
 __global__ void __launch_bounds__(MF_THREADS, MF_MINB) k_maxflow(MFArgs a) {
   __shared__ MFShared s;
   if (a.frontier)
-    mf_run<ND, false, true, true>(a, s);
+    mf_run<ND, false, true>(a, s);
   else
-    mf_run<ND, false, false, true>(a, s);
+    mf_run<ND, false, false>(a, s);
 }
 
 // A stack of frames (a batch context): empty slots are left out when a.on marks
